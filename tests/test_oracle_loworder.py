@@ -1,0 +1,163 @@
+"""Pins of the oracle's low-order level (Section 3).
+
+The implicit update Eq. (implicit-local) is checked against a dense
+linearisation assembled here from complex-step Jacobians of the Euler flux:
+  D_i dU_i + sum_p S_p * 1/2 (A(U_ip; n_ip) - lambda_p I) dU_ip = R_i.
+The spectral radius used in the L-F split is checked against eigenvalues,
+and the two-level cycle against its FAS fixed-point property.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2109_09965_gb300 import meshgen as MG
+from tests import exact
+
+GAM = 1.4
+
+
+def cjac(W, n):
+    J = np.zeros((4, 4))
+    for k in range(4):
+        Wc = W.astype(complex)
+        Wc[k] += 1e-30j
+        J[:, k] = np.imag(exact.euler_flux(GAM, Wc, n)) / 1e-30
+    return J
+
+
+def small_case(oracle_lib, mu=0.0, n=3, seed=21):
+    O = oracle_lib
+    mesh = MG.box(n, n, 0.0, 1.0, 0.0, 1.0, jitter=0.2, seed=seed, cells="mixed",
+                  quad_mask=lambda i, j: (i + j) % 3 == 0, tags=(0, 1, 1, 0))
+    om = O.OracleMesh(mesh)
+    spec = dict(gamma=GAM, mu=mu, cfl_lo=1000.0,
+                bcs=[dict(kind="slip"), dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)])
+    s = O.OracleSolver(om, spec)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.8, 1.2, mesh.n_cells)
+    U = exact.cons_from_prim(GAM, rho, rng.uniform(-0.3, 0.3, mesh.n_cells),
+                             rng.uniform(-0.3, 0.3, mesh.n_cells), rho / GAM * rng.uniform(0.9, 1.1, mesh.n_cells))
+    return om, s, U
+
+
+def dense_system(om, U, lam, D):
+    """Block matrix of the linearised point-relaxation system."""
+    F = om.faces()
+    nc = U.shape[0]
+    A = np.zeros((nc, 4, nc, 4))
+    for i in range(nc):
+        A[i, :, i, :] = D[i] * np.eye(4)
+    for f in range(om.n_faces):
+        c0, c1 = F["c0"][f], F["c1"][f]
+        if c1 < 0:
+            continue
+        n = F["n"][f]
+        S = F["S"][f]
+        A[c0, :, c1, :] += S * 0.5 * (cjac(U[c1], n) - lam[f] * np.eye(4))
+        A[c1, :, c0, :] += S * 0.5 * (cjac(U[c0], -n) - lam[f] * np.eye(4))
+    return A
+
+
+def test_lambda_is_spectral_radius(oracle_lib):
+    """Inviscid: lambda_p = max over both sides of max |eig(dF_n/dU)|."""
+    om, s, U = small_case(oracle_lib, mu=0.0)
+    lam = s.lo_lambda(U)
+    F = om.faces()
+    for f in range(om.n_faces):
+        if F["c1"][f] < 0:
+            continue
+        n = F["n"][f]
+        r = max(np.abs(np.linalg.eigvals(cjac(U[F["c0"][f]], n))).max(),
+                np.abs(np.linalg.eigvals(cjac(U[F["c1"][f]], n))).max())
+        assert abs(lam[f] - r) < 1e-12 * r
+
+
+def test_diagonal_is_lf_split_of_closed_cell(oracle_lib):
+    """sum_p S_p A^+_p = sum_p S_p (A(U_i;n_p) + lambda_p I)/2 is the scalar
+    1/2 sum_p lambda_p S_p, because sum_p S_p n_p = 0; with dt_i from
+    CFL_lo the diagonal is D_i = |Omega_i|/dt_i + that scalar."""
+    om, s, U = small_case(oracle_lib, mu=0.01)
+    lam = s.lo_lambda(U)
+    D = s.lo_diag(U)
+    vol, _ = om.geometry()
+    F = om.faces()
+    for i in range(U.shape[0]):
+        M = np.zeros((4, 4))
+        lsum = 0.0
+        for f in range(om.n_faces):
+            for side, sg in (("c0", 1.0), ("c1", -1.0)):
+                if F[side][f] == i:
+                    n = sg * F["n"][f]
+                    M += F["S"][f] * 0.5 * (cjac(U[i], n) + lam[f] * np.eye(4))
+                    lsum += lam[f] * F["S"][f]
+        np.testing.assert_allclose(M, 0.5 * lsum * np.eye(4), atol=1e-12)
+        assert abs(D[i] - (vol[i] / (1000.0 * vol[i] / lsum) + 0.5 * lsum)) < 1e-12 * D[i]
+
+
+def test_forward_pass_is_block_gauss_seidel_in_colour_order(oracle_lib):
+    om, s, U = small_case(oracle_lib, mu=0.01)
+    rng = np.random.default_rng(22)
+    eps = 1e-7
+    R = eps * rng.normal(size=U.shape)
+    dU = s.lo_relax(U, R, -1)
+    lam, D = s.lo_lambda(U), s.lo_diag(U)
+    A = dense_system(om, U, lam, D)
+    _, colour = om.ordering()
+    x = np.zeros_like(U)
+    for c in range(om.n_colours):
+        for i in np.nonzero(colour == c)[0]:
+            r = R[i].copy()
+            for j in range(U.shape[0]):
+                if j != i:
+                    r -= A[i, :, j, :] @ x[j]
+            x[i] = np.linalg.solve(A[i, :, i, :], r)
+    np.testing.assert_allclose(dU / eps, x / eps, rtol=0, atol=1e-5 * np.abs(x / eps).max())
+
+
+def test_many_sweeps_converge_to_dense_solve(oracle_lib):
+    om, s, U = small_case(oracle_lib, mu=0.01)
+    rng = np.random.default_rng(23)
+    eps = 1e-8
+    R = eps * rng.normal(size=U.shape)
+    dU = s.lo_relax(U, R, 60)
+    A = dense_system(om, U, s.lo_lambda(U), s.lo_diag(U))
+    nc = U.shape[0]
+    x = np.linalg.solve(A.reshape(4 * nc, 4 * nc), R.reshape(-1)).reshape(nc, 4)
+    np.testing.assert_allclose(dU / eps, x / eps, rtol=0, atol=1e-5 * np.abs(x / eps).max())
+
+
+def test_low_order_residual_vanishes_for_free_stream(oracle_lib):
+    om, s, _ = small_case(oracle_lib)
+    U = np.tile(exact.cons_from_prim(GAM, 1.0, 0.3, 0.1, 1 / GAM), (om.n_cells, 1))
+    # slip walls at bottom/left change the normal velocity: only test the far-field box
+    O = oracle_lib
+    mesh = MG.box(4, 4, jitter=0.2, seed=3, cells="tri", tags=(0, 0, 0, 0))
+    om2 = O.OracleMesh(mesh)
+    s2 = O.OracleSolver(om2, dict(gamma=GAM, bcs=[dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)]))
+    U = np.tile(exact.cons_from_prim(GAM, 1.0, 0.3, 0.1, 1 / GAM), (mesh.n_cells, 1))
+    assert np.abs(s2.lo_residual(U)).max() < 1e-14
+
+
+def test_fas_fixed_point(oracle_lib):
+    """At a state the V-cycle has converged to machine precision, the
+    explicit high-order step also leaves the state unchanged: the low-order
+    correction does not move the high-order fixed point (Section 3, steps
+    2-5: R_p0 = 0 makes W_p0 solve the forced low-order equation).
+    Viscous cylinder, Re = 38 on a small hybrid O-mesh."""
+    O = oracle_lib
+    mesh = MG.cylinder(24, 4, 6, growth=1.2, R_far=5.0)
+    om = O.OracleMesh(mesh)
+    ma = 0.38
+    spec = dict(gamma=GAM, mu=0.01, cfl_hi=0.4,
+                bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(ma, 0.0), p=1 / GAM)])
+    s = O.OracleSolver(om, spec)
+    W0 = np.tile(exact.cons_from_prim(GAM, 1.0, ma, 0.0, 1 / GAM), (mesh.n_cells, 1))
+    s.set_state(W0)
+    res = s.pmg_cycles(500)
+    assert res[-1] < 1e-14, res[-5:]
+    W, Wx = s.get_state()
+    s.highorder_step()
+    W2, _ = s.get_state()
+    assert np.abs(W2 - W).max() < 1e-12
+    assert np.abs(W - W0).max() > 1e-2
