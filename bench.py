@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the p-multigrid compact GKS on GB300.
+
+Workload: 2-D inviscid flow past a cylinder, Ma 0.38, AoA 0, hybrid O-mesh
+(256 circumferential, 32 quad layers growing by 1.08, 96 split-triangle
+layers to 20 radii): 57,344 cells.  One step = one two-level V-cycle
+(high-order S1O2 step, R_p0 re-evaluated at W^{n+1}, 6 backward-Euler
+low-order steps of 2 coloured forward/backward relaxation pairs,
+prolongation, density residual), FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--scheme S1O2|S2O4] [--converge]
+
+Under torchrun every rank runs its own replica (the path has no exchange
+step on one mesh): scaling "weak", value = all ranks' cell
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BASELINE_METRIC = "cell-updates/s; time to 1e-8 residual drop vs explicit S2O4; p99 solve latency"
+GAMMA = 1.4
+MA = 0.38
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload():
+    from paper_2109_09965_gb300 import meshgen
+    mesh = meshgen.cylinder(256, 32, 96)
+    spec = dict(gamma=GAMMA, mu=0.0, cfl_hi=0.4, cfl_lo=1000.0, n_implicit=6, n_sweeps=2,
+                time_scheme="S1O2", bcs=[dict(kind="slip"),
+                                         dict(kind="farfield", rho=1.0, u=(MA, 0.0), p=1.0 / GAMMA)])
+    W = np.zeros((mesh.n_cells, 4))
+    W[:, 0] = 1.0
+    W[:, 1] = MA
+    W[:, 3] = 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * MA * MA
+    return mesh, spec, W
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                pass
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(mesh, spec, W0, cycles=2):
+    """The FP64 CPU oracle, serial, on a bounded sample of the same workload."""
+    from oracle import oracle as O
+    O.build()
+    om = O.OracleMesh(mesh)
+    s = O.OracleSolver(om, spec)
+    s.set_state(W0)
+    t = time.perf_counter()
+    s.pmg_cycles(cycles)
+    dt = time.perf_counter() - t
+    return {"value": mesh.n_cells * cycles / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cycles} V-cycles of the {mesh.n_cells}-cell cylinder, serial FP64 oracle, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the same workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mesh, spec, W0 = workload()
+    spec = dict(spec, time_scheme=args.scheme)
+    from oracle import oracle as O
+    O.build()
+    s = O.OracleSolver(O.OracleMesh(mesh), spec)
+    s.set_state(W0)
+    for _ in range(min(args.warmup, 1)):
+        s.pmg_cycles(1)
+    # bound the run to a few minutes of host time
+    t0 = time.perf_counter()
+    s.pmg_cycles(1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(150.0 / max(t1, 1e-3))))
+    t = time.perf_counter()
+    s.pmg_cycles(steps)
+    el = time.perf_counter() - t
+    value = mesh.n_cells * steps / el
+    line = {"impl": "reference", "metric": BASELINE_METRIC, "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(mesh, args),
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} V-cycles of the {mesh.n_cells}-cell cylinder (serial FP64 oracle)"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_block(mesh, args):
+    return {"workload": f"2-D inviscid cylinder Ma {MA}, AoA 0, hybrid O-mesh 256 x (32 quad + 96 split-triangle "
+                        f"layers), {mesh.n_cells} cells, p-multigrid V-cycle ({args.scheme} high-order step + "
+                        f"6 implicit low-order steps x 2 coloured sweep pairs), FP64",
+            "n_cells": mesh.n_cells, "scheme": args.scheme, "precision": "fp64", "parallelism": "replicas",
+            "l2": "flushed between timed steps (256 MiB write, outside the per-step events)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scheme", default="S1O2", choices=["S1O2", "S2O4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2109_09965_gb300 import cgks
+    cgks.lib()
+    mesh, spec, W0 = workload()
+    spec = dict(spec, time_scheme=args.scheme)
+    gm = cgks.Mesh(mesh)
+    solver = cgks.Solver(gm, spec)
+    solver.set_state(W0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+
+    # ---- device-resident timing: K V-cycles, per-step events, L2 flushed between
+    for _ in range(args.warmup):
+        solver.pmg_cycle(1, record=False)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    l0 = solver.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            solver.pmg_cycle(1, record=False)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = solver.launch_count() - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    dist_barrier(world)
+    ms = dist_max(ms, world)
+    value = world * mesh.n_cells * args.steps / (ms / 1000.0)
+    res, _ = solver.residual()
+
+    # ---- per-kernel timing pass (events around every launch, same K cycles)
+    solver.set_timing(True)
+    solver.reset_timing()
+    for k in range(args.steps):
+        flush.zero_()
+        solver.pmg_cycle(1, record=False)
+    torch.cuda.synchronize()
+    kt = solver.timing()
+    solver.set_timing(False)
+    total_k = sum(v[0] for v in kt.values())
+    top = max(kt, key=lambda k: kt[k][0])
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Wh = torch.from_numpy(W0.copy()).pin_memory()
+    Xh = torch.zeros((mesh.n_cells, 2, 4), dtype=torch.float64).pin_memory()
+    Wout = torch.zeros((mesh.n_cells, 4), dtype=torch.float64).pin_memory()
+    resh = np.zeros(1)
+    Wn, Xn = Wh.numpy(), Xh.numpy()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        cgks.lib().cgks_set_state(solver._h, Wn.ctypes.data, Xn.ctypes.data)
+        cgks.lib().cgks_pmg_cycle(solver._h, 1, resh.ctypes.data)
+        cgks.lib().cgks_get_state(solver._h, Wout.numpy().ctypes.data, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist_max(e0.elapsed_time(e1), world)
+    e2e = {"value": world * mesh.n_cells * args.steps / (e2e_ms / 1000.0), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": 12 * 8 * mesh.n_cells, "d2h_bytes_per_step": 4 * 8 * mesh.n_cells + 8}
+
+    if rank != 0:
+        return
+    hbm, hbm_src = peaks()
+    roof = roofline(top, kt, mesh, gm, hbm, hbm_src)
+    line = {"metric": BASELINE_METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(mesh, args), "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
+            "kernels": {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]}
+                        for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0},
+            "residual_last": res}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mesh, spec, W0)
+    if args.converge:
+        line["convergence"] = converge(cgks, mesh, spec, W0)
+    print(json.dumps(line), flush=True)
+
+
+# Algorithmic work per launch of each kernel (FP64 operation counts and
+# compulsory bytes; see the design doc for the derivation).
+FLOPS_PER_GAUSS_POINT = 1169          # smooth GKS flux incl. reconstruction evaluation, one side pair
+FP64_PEAK_TFLOPS = 1.25               # nominal FP64 of GB300 (2 FMA / clk / SM x 152 SM x ~2.06 GHz)
+
+
+def roofline(top, kt, mesh, gm, hbm, hbm_src):
+    ms, n = kt[top]
+    per_launch_s = ms / max(n, 1) / 1000.0
+    if top == "k_face":
+        flops = FLOPS_PER_GAUSS_POINT * 2 * gm.n_faces
+        ach = flops / per_launch_s / 1e12
+        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (recipe table); see DESIGN.md"}
+    bytes_per_launch = {"k_sweep": 8 * (4 * 4 + 4 + 1) * mesh.n_cells / 4}.get(top, 0.0)
+    ach = bytes_per_launch / per_launch_s / 1e9
+    return {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "peak_source": hbm_src}
+
+
+def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=400000):
+    """Wall time to a 1e-8 drop of Res relative to its first value:
+    p-multigrid (S1O2 high-order step) vs explicit S2O4."""
+    import torch
+    out = {}
+    for label, sp, fn, cap in (("pmg", dict(spec), "pmg_cycle", max_cycles),
+                               ("explicit_S2O4", dict(spec, time_scheme="S2O4"), "explicit_steps", max_steps)):
+        s = cgks.Solver(cgks.Mesh(mesh), sp)
+        s.set_state(W0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        done, first, its, hist = False, None, 0, []
+        chunk = 100 if label == "pmg" else 1000
+        while its < cap and not done:
+            r = getattr(s, fn)(chunk)
+            if first is None:
+                first = r[0]
+            hist.extend(r.tolist())
+            its += chunk
+            hit = np.nonzero(np.asarray(hist) <= drop * first)[0]
+            done = hit.size > 0
+        el = time.perf_counter() - t
+        n_hit = int(hit[0]) + 1 if done else None
+        out[label] = {"converged": done, "iterations": n_hit if done else its, "wall_s": el,
+                      "wall_s_to_drop": el * (n_hit / its) if done else None,
+                      "res_first": first, "res_last": hist[-1]}
+        s.close()
+    if out["pmg"]["converged"] and out["explicit_S2O4"]["converged"]:
+        out["speedup"] = out["explicit_S2O4"]["wall_s_to_drop"] / out["pmg"]["wall_s_to_drop"]
+    return out
+
+
+if __name__ == "__main__":
+    main()

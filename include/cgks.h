@@ -1,0 +1,199 @@
+/*
+ * cgks.h -- C ABI of libcgks: the GB300 (sm_103a) implementation of the
+ * p-multigrid compact gas-kinetic scheme of Ji, Shyy & Xu,
+ * "A p-multigrid compact gas-kinetic scheme for steady-state acceleration"
+ * (arXiv:2109.09965), for 2-D hybrid (triangle / quadrilateral) meshes.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns CGKS_OK (0) or a negative CGKS_E* status.
+ *    cgks_strerror() names a status.  Nothing aborts the process.
+ *  - Host arrays are owned by the caller and only read or written during
+ *    the call; the library copies what it keeps.  Device memory is owned
+ *    by the library (allocated through the optional allocator callback of
+ *    cgks_params, else cudaMalloc) and released by *_destroy.
+ *  - State arrays at the ABI are in the caller's cell order, array of
+ *    structs: W[c*4 + v] with v = (rho, rho*u, rho*v, rho*E) and
+ *    Wx[(c*2 + d)*4 + v] = cell-averaged d(W_v)/dx_d.  Internally the
+ *    library stores structure-of-arrays in its own cell order (reverse
+ *    Cuthill-McKee within graph colours, see cgks_mesh_ordering).
+ *  - All device work runs on the stream given in cgks_params (NULL = the
+ *    legacy default stream).  Calls that return host results synchronise
+ *    that stream.  A solver is not thread safe; use one per host thread.
+ *  - A device-side status word records non-finite or non-positive
+ *    density / pressure; once set, stepping calls return CGKS_EDIVERGED
+ *    until cgks_set_state() loads a new state.
+ *  - There is no CPU fallback: without a usable CUDA device the solver
+ *    constructor returns CGKS_ECUDA.
+ */
+#ifndef CGKS_H
+#define CGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CGKS_OK = 0,
+  CGKS_EINVAL = -1,     /* bad argument (NULL pointer, size, parameter) */
+  CGKS_ENOMEM = -2,     /* host or device allocation failed */
+  CGKS_EMESH = -3,      /* mesh rejected at creation */
+  CGKS_ECUDA = -4,      /* CUDA runtime error or no device */
+  CGKS_EDIVERGED = -5,  /* non-finite or non-positive rho / p on the device */
+  CGKS_ETIMEOUT = -6,   /* a bounded wait expired */
+  CGKS_EBUDGET = -7     /* request does not fit the memory budget */
+};
+
+/* cell types (node order counter-clockwise, as VTK) */
+enum { CGKS_TRI = 0, CGKS_QUAD = 1 };
+
+/* boundary conditions, Section 4 of the paper: reflective (slip) wall,
+ * non-slip adiabatic wall (optionally moving tangentially), far field with
+ * 1-D Riemann invariants against a free stream */
+enum { CGKS_BC_SLIP = 0, CGKS_BC_NOSLIP = 1, CGKS_BC_FARFIELD = 2 };
+
+/* explicit time schemes: S1O2 (Section 2.4) and the two-stage fourth-order
+ * S2O4 named in Section 1 (Li & Du 2016) */
+enum { CGKS_S1O2 = 0, CGKS_S2O4 = 1 };
+
+/* arithmetic of the hot path */
+enum { CGKS_FP64 = 0, CGKS_MIXED = 1 };
+
+#define CGKS_MAX_BC 16
+
+typedef struct {
+  int32_t kind;          /* CGKS_BC_* */
+  int32_t pad_;
+  double u_wall[2];      /* no-slip wall velocity (tangential) */
+  double rho, u[2], p;   /* far-field free stream (primitive variables) */
+} cgks_bc;
+
+typedef void *(*cgks_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*cgks_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+  double gamma;          /* ratio of specific heats (1.4) */
+  double mu;             /* constant dynamic viscosity; 0 = Euler */
+  double alpha;          /* jump coefficient of the equilibrium normal slope (4/3) */
+  double cfl_hi;         /* explicit CFL of the high-order level (0.3-0.5, Section 4) */
+  double cfl_lo;         /* local CFL of the low-order level (1000, Section 4) */
+  int32_t n_implicit;    /* backward-Euler steps per V-cycle (6, Section 3) */
+  int32_t n_sweeps;      /* forward+backward relaxation pairs per step (2) */
+  int32_t time_scheme;   /* CGKS_S1O2 or CGKS_S2O4 */
+  int32_t precision;     /* CGKS_FP64 or CGKS_MIXED */
+  int32_t n_bc;          /* entries used in bc[] (boundary tags index it) */
+  int32_t use_graph;     /* 1: capture each V-cycle in a CUDA graph */
+  cgks_bc bc[CGKS_MAX_BC];
+  void *stream;          /* cudaStream_t for all device work (NULL = default) */
+  cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */
+  cgks_free_fn free;     /* matching free */
+  void *alloc_ctx;       /* passed to alloc / free */
+} cgks_params;
+
+typedef struct {
+  int64_t n_cells, n_faces, n_bfaces;
+  int32_t n_colours;     /* colours of the sweep order */
+  int32_t dim;
+  int64_t device_bytes;  /* device memory a solver on this mesh holds */
+} cgks_mesh_info_t;
+
+typedef struct cgks_mesh cgks_mesh;
+typedef struct cgks_solver cgks_solver;
+
+/* Fill p with the defaults above (gamma 1.4, Euler, CFL 0.4 / 1000,
+ * 6 implicit steps, 2 sweeps, S1O2, FP64, graphs on, no boundaries). */
+void cgks_default_params(cgks_params *p);
+
+/* Build a mesh from nodes, cells and tagged boundary edges (the finite-
+ * volume setting of Section 2.1).
+ *   dim           2 (only 2-D is implemented; 3 returns CGKS_EINVAL)
+ *   xyz           [n_nodes*dim] node coordinates
+ *   cell_type     [n_cells] CGKS_TRI / CGKS_QUAD
+ *   cell_ptr      [n_cells+1] offsets into cell_nodes
+ *   cell_nodes    node indices, counter-clockwise per cell
+ *   bface_ptr     [n_bfaces+1] offsets into bface_nodes (2 nodes per edge)
+ *   bface_tag     [n_bfaces] index into cgks_params.bc[]
+ * Builds faces, areas, centroids, 2-point Gauss-Legendre quadrature per
+ * edge, the compact reconstruction operators, the reverse Cuthill-McKee
+ * order and the greedy colouring.  Returns CGKS_EMESH for clockwise or
+ * degenerate cells, edges shared by more than two cells, or boundary edges
+ * without a tag.  Host only; no device memory is touched. */
+int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cells,
+                     const uint8_t *cell_type, const int64_t *cell_ptr, const int64_t *cell_nodes,
+                     int64_t n_bfaces, const int64_t *bface_ptr, const int64_t *bface_nodes,
+                     const int32_t *bface_tag, cgks_mesh **out);
+
+int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out);
+
+/* Sweep order of the coloured point relaxation (the index order of
+ * Algorithm 1 replaced by colour classes): rcm[k] = caller cell at position
+ * k of the reverse Cuthill-McKee order, colour[c] = colour of caller cell c. */
+int cgks_mesh_ordering(const cgks_mesh *m, int64_t *rcm, int32_t *colour);
+
+int cgks_mesh_destroy(cgks_mesh *m);
+
+/* Create a solver on a mesh: uploads geometry and operators to the device
+ * and allocates the state.  The mesh may be destroyed afterwards. */
+int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **out);
+int cgks_solver_destroy(cgks_solver *s);
+
+/* Load cell averages W and cell-averaged gradients Wx (NULL = zero) from
+ * host memory (layouts above).  Clears the status word. */
+int cgks_set_state(cgks_solver *s, const double *W, const double *Wx);
+/* Same from device memory (same layouts, caller order). */
+int cgks_set_state_device(cgks_solver *s, const double *W_dev, const double *Wx_dev);
+/* Copy the state to host memory (either pointer may be NULL). */
+int cgks_get_state(cgks_solver *s, double *W, double *Wx);
+int cgks_get_state_device(cgks_solver *s, double *W_dev, double *Wx_dev);
+
+/* One explicit high-order step (Sections 2.2-2.4): compact reconstruction,
+ * gas-kinetic smooth flux and interface state at every Gauss point,
+ * S1O2 or S2O4 update of W and Gauss-Green update of Wx.
+ *   dt <= 0: global time step from cfl_hi.  *dt_used (may be NULL) gets it. */
+int cgks_highorder_step(cgks_solver *s, double dt, double *dt_used);
+
+/* n explicit high-order steps without host synchronisation in between;
+ * res_hist (host, may be NULL) receives the density residual of each. */
+int cgks_explicit_steps(cgks_solver *s, int n, double *res_hist);
+
+/* Low-order level alone (Section 3, steps 3-5) on the current state, with
+ * R_p0 of the last high-order evaluation: forcing, n_implicit backward-
+ * Euler steps by coloured point relaxation, prolongation of the correction. */
+int cgks_loworder_smooth(cgks_solver *s);
+
+/* n two-level V-cycles (Section 3, steps 1-5): high-order step, residual
+ * R_p0 re-evaluated at W^{n+1}, low-order implicit solve, correction.
+ * res_hist (host, may be NULL) receives Res of each cycle. */
+int cgks_pmg_cycle(cgks_solver *s, int n_cycles, double *res_hist);
+
+/* Density residual Res = sum|rho^{n+1} - rho^n| / sum rho^n of the last
+ * update (Section 4), and optionally the L2 norm of each component of the
+ * last high-order residual R_p0 (r_l2[4], may be NULL). */
+int cgks_residual(cgks_solver *s, double *res, double *r_l2);
+
+/* Test access to intermediate results of the last high-order evaluation in
+ * the caller's cell order: R_p0 [n_cells*4] (may be NULL). */
+int cgks_get_rp0(cgks_solver *s, double *Rp0);
+
+const char *cgks_strerror(int status);
+
+/* ---- instrumentation (no counterpart in the paper) ----
+ * Per-kernel timers: while on, every kernel launch of this solver is
+ * bracketed by CUDA events on the library's stream and CUDA graphs are
+ * bypassed.  cgks_get_timing fills up to max entries (kernel name, total
+ * milliseconds, launch count) and returns the number of entries. */
+int cgks_set_timing(cgks_solver *s, int on);
+int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_ms, int64_t *count);
+int cgks_reset_timing(cgks_solver *s);
+/* Kernels launched by this solver so far, and kernels per V-cycle (cycle=1)
+ * or per explicit step (cycle=0). */
+int64_t cgks_launch_count(const cgks_solver *s);
+int cgks_launches_per_call(const cgks_solver *s, int cycle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

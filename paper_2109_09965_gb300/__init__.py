@@ -4,14 +4,12 @@
 binding of the CUDA library ``libcgks.so`` (imported lazily so the mesh
 generators work without a GPU or a built library).
 """
+import importlib
+
 __all__ = ["meshgen", "cgks"]
 
 
 def __getattr__(name):
-    if name == "cgks":
-        from . import cgks
-        return cgks
-    if name == "meshgen":
-        from . import meshgen
-        return meshgen
+    if name in __all__:
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,312 @@
+"""Thin ctypes binding of libcgks (include/cgks.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  PyTorch supplies device memory (through the allocator callback)
+and the stream the library synchronises with.  There is no CPU fallback:
+if libcgks.so is missing or no CUDA device is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+TRI, QUAD = 0, 1
+BC_SLIP, BC_NOSLIP, BC_FARFIELD = 0, 1, 2
+S1O2, S2O4 = 0, 1
+FP64, MIXED = 0, 1
+MAX_BC = 16
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "mesh rejected", -4: "CUDA error",
+          -5: "diverged", -6: "timeout", -7: "memory budget exceeded"}
+
+
+class CgksError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {lib().cgks_strerror(status).decode()} ({status})")
+
+
+class CgksBC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("u_wall", C.c_double * 2),
+                ("rho", C.c_double), ("u", C.c_double * 2), ("p", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class CgksParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+                ("cfl_hi", C.c_double), ("cfl_lo", C.c_double),
+                ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32), ("time_scheme", C.c_int32),
+                ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
+                ("bc", CgksBC * MAX_BC), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class CgksMeshInfo(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_bfaces", C.c_int64),
+                ("n_colours", C.c_int32), ("dim", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+_dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+
+# every entry point of include/cgks.h with its ctypes signature
+SIGNATURES = {
+    "cgks_default_params": (None, [C.POINTER(CgksParams)]),
+    "cgks_strerror": (C.c_char_p, [C.c_int]),
+    "cgks_mesh_create": (C.c_int, [C.c_int, C.c_int64, _dp, C.c_int64, _u8p, _i64p, _i64p, C.c_int64,
+                                   _i64p, _i64p, _i32p, C.POINTER(C.c_void_p)]),
+    "cgks_mesh_info": (C.c_int, [C.c_void_p, C.POINTER(CgksMeshInfo)]),
+    "cgks_mesh_ordering": (C.c_int, [C.c_void_p, _i64p, _i32p]),
+    "cgks_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "cgks_solver_create": (C.c_int, [C.c_void_p, C.POINTER(CgksParams), C.POINTER(C.c_void_p)]),
+    "cgks_solver_destroy": (C.c_int, [C.c_void_p]),
+    "cgks_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cgks_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cgks_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cgks_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cgks_highorder_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "cgks_explicit_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "cgks_loworder_smooth": (C.c_int, [C.c_void_p]),
+    "cgks_pmg_cycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "cgks_residual": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "cgks_get_rp0": (C.c_int, [C.c_void_p, _dp]),
+    "cgks_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "cgks_get_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.c_void_p, C.c_void_p]),
+    "cgks_reset_timing": (C.c_int, [C.c_void_p]),
+    "cgks_launch_count": (C.c_int64, [C.c_void_p]),
+    "cgks_launches_per_call": (C.c_int, [C.c_void_p, C.c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libcgks.so (building it with nvcc if absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and _build.needs_build():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libcgks.so is not built; run paper_2109_09965_gb300/build.py")
+            L = C.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise CgksError(rc, what)
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Mesh:
+    """Mesh handle built from raw node / cell / boundary arrays (meshgen.Mesh)."""
+
+    def __init__(self, m):
+        L = lib()
+        h = C.c_void_p()
+        rc = L.cgks_mesh_create(int(m.dim), m.nodes.shape[0], np.ascontiguousarray(m.nodes, np.float64),
+                                m.cell_type.shape[0], np.ascontiguousarray(m.cell_type, np.uint8),
+                                np.ascontiguousarray(m.cell_ptr, np.int64),
+                                np.ascontiguousarray(m.cell_nodes, np.int64), m.bface_tag.shape[0],
+                                np.ascontiguousarray(m.bface_ptr, np.int64),
+                                np.ascontiguousarray(m.bface_nodes, np.int64),
+                                np.ascontiguousarray(m.bface_tag, np.int32), C.byref(h))
+        _check(rc, "cgks_mesh_create")
+        self._h = h
+        info = CgksMeshInfo()
+        _check(L.cgks_mesh_info(h, C.byref(info)), "cgks_mesh_info")
+        self.n_cells = info.n_cells
+        self.n_faces = info.n_faces
+        self.n_bfaces = info.n_bfaces
+        self.n_colours = info.n_colours
+        self.device_bytes = info.device_bytes
+
+    def ordering(self):
+        rcm = np.zeros(self.n_cells, np.int64)
+        col = np.zeros(self.n_cells, np.int32)
+        _check(lib().cgks_mesh_ordering(self._h, rcm, col), "cgks_mesh_ordering")
+        return rcm, col
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cgks_mesh_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
+    """Problem settings from a plain dict (same keys as the bench configs):
+    gamma, mu, alpha, cfl_hi, cfl_lo, n_implicit, n_sweeps, time_scheme,
+    precision, use_graph, bcs=[{kind, uw, rho, u, p}]."""
+    P = CgksParams()
+    lib().cgks_default_params(C.byref(P))
+    for key in ("gamma", "mu", "alpha", "cfl_hi", "cfl_lo"):
+        if key in spec:
+            setattr(P, key, float(spec[key]))
+    for key in ("n_implicit", "n_sweeps", "use_graph"):
+        if key in spec:
+            setattr(P, key, int(spec[key]))
+    P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
+    P.precision = {"fp64": FP64, "mixed": MIXED}[spec.get("precision", "fp64")]
+    bcs = spec.get("bcs", [])
+    P.n_bc = len(bcs)
+    kinds = {"slip": BC_SLIP, "noslip": BC_NOSLIP, "farfield": BC_FARFIELD}
+    for i, b in enumerate(bcs):
+        P.bc[i].kind = kinds[b["kind"]]
+        uw = b.get("uw", (0.0, 0.0))
+        P.bc[i].u_wall[0], P.bc[i].u_wall[1] = float(uw[0]), float(uw[1])
+        P.bc[i].rho = float(b.get("rho", 1.0))
+        u = b.get("u", (0.0, 0.0))
+        P.bc[i].u[0], P.bc[i].u[1] = float(u[0]), float(u[1])
+        P.bc[i].p = float(b.get("p", 1.0 / P.gamma))
+    if stream is not None:
+        P.stream = C.c_void_p(stream)
+    if allocator is not None:
+        P.alloc, P.free, P.alloc_ctx = allocator.alloc_fn, allocator.free_fn, None
+    return P
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.blocks = {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        self.blocks[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self.blocks.pop(ptr, None)
+
+
+class Solver:
+    """One steady solve on one mesh; state lives on the device."""
+
+    def __init__(self, mesh: Mesh, spec: dict, use_torch: bool = True):
+        L = lib()
+        self.mesh = mesh
+        self.n_cells = mesh.n_cells
+        stream, self._alloc = None, None
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("libcgks needs a CUDA device; none is available")
+            self._alloc = TorchAllocator()
+            stream = torch.cuda.current_stream().cuda_stream
+        self.params = make_params(spec, stream=stream, allocator=self._alloc)
+        h = C.c_void_p()
+        _check(L.cgks_solver_create(mesh._h, C.byref(self.params), C.byref(h)), "cgks_solver_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cgks_solver_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    # -- state --------------------------------------------------------
+    def set_state(self, W, Wx=None):
+        W = np.ascontiguousarray(W, np.float64).reshape(self.n_cells, 4)
+        Wx = None if Wx is None else np.ascontiguousarray(Wx, np.float64).reshape(self.n_cells, 2, 4)
+        _check(lib().cgks_set_state(self._h, _ptr(W), _ptr(Wx)), "cgks_set_state")
+
+    def set_state_device(self, W_ptr: int, Wx_ptr: int | None = None):
+        _check(lib().cgks_set_state_device(self._h, C.c_void_p(W_ptr), C.c_void_p(Wx_ptr) if Wx_ptr else None),
+               "cgks_set_state_device")
+
+    def get_state(self):
+        W = np.zeros((self.n_cells, 4))
+        Wx = np.zeros((self.n_cells, 2, 4))
+        _check(lib().cgks_get_state(self._h, _ptr(W), _ptr(Wx)), "cgks_get_state")
+        return W, Wx
+
+    def get_state_device(self, W_ptr: int, Wx_ptr: int | None = None):
+        _check(lib().cgks_get_state_device(self._h, C.c_void_p(W_ptr), C.c_void_p(Wx_ptr) if Wx_ptr else None),
+               "cgks_get_state_device")
+
+    # -- hot path -----------------------------------------------------
+    def highorder_step(self, dt: float = -1.0) -> float:
+        used = C.c_double()
+        _check(lib().cgks_highorder_step(self._h, float(dt), C.byref(used)), "cgks_highorder_step")
+        return used.value
+
+    def explicit_steps(self, n: int, record=True):
+        r = np.zeros(max(n, 1)) if record else None
+        _check(lib().cgks_explicit_steps(self._h, int(n), _ptr(r)), "cgks_explicit_steps")
+        return r[:n] if record else None
+
+    def pmg_cycle(self, n: int, record=True):
+        r = np.zeros(max(n, 1)) if record else None
+        _check(lib().cgks_pmg_cycle(self._h, int(n), _ptr(r)), "cgks_pmg_cycle")
+        return r[:n] if record else None
+
+    def loworder_smooth(self):
+        _check(lib().cgks_loworder_smooth(self._h), "cgks_loworder_smooth")
+
+    def residual(self):
+        res = C.c_double()
+        rl2 = np.zeros(4)
+        _check(lib().cgks_residual(self._h, C.byref(res), _ptr(rl2)), "cgks_residual")
+        return res.value, rl2
+
+    def rp0(self):
+        R = np.zeros((self.n_cells, 4))
+        _check(lib().cgks_get_rp0(self._h, R), "cgks_get_rp0")
+        return R
+
+    # -- instrumentation ----------------------------------------------
+    def set_timing(self, on: bool):
+        _check(lib().cgks_set_timing(self._h, int(bool(on))), "cgks_set_timing")
+
+    def timing(self):
+        names = (C.c_char_p * 32)()
+        ms = np.zeros(32)
+        cnt = np.zeros(32, np.int64)
+        k = lib().cgks_get_timing(self._h, 32, names, _ptr(ms), _ptr(cnt))
+        return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+
+    def reset_timing(self):
+        _check(lib().cgks_reset_timing(self._h), "cgks_reset_timing")
+
+    def launch_count(self) -> int:
+        return int(lib().cgks_launch_count(self._h))
+
+    def launches_per_call(self, cycle: bool) -> int:
+        return int(lib().cgks_launches_per_call(self._h, int(bool(cycle))))

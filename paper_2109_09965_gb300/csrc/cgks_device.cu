@@ -1,0 +1,1142 @@
+// libcgks device runtime: kernels of the high-order level (compact
+// reconstruction, gas-kinetic face flux, S1O2 / S2O4 update with
+// Gauss-Green gradients), of the low-order level (KFVS residual, L-F
+// diagonal, coloured point relaxation) and of the two-level V-cycle of
+// Ji, Shyy & Xu (arXiv:2109.09965), plus the C ABI declared in cgks.h.
+//
+// Layout: structure-of-arrays in the library's cell order (colour-major,
+// reverse Cuthill-McKee inside a colour).  One thread per cell or face.
+// The cell update gathers the face sums through each cell's face slots
+// (no atomics, deterministic); reductions use a fixed block tree.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cgks_internal.h"
+#include "cgks_physics.cuh"
+
+using namespace cgks;
+namespace D = cgks::dev;
+
+namespace {
+
+constexpr int kCellBlock = 256;
+constexpr int kFaceBlock = 128;
+constexpr int kMaxBlocksReduce = 4096;
+
+// status bits of the device status word
+constexpr int kBadState = 1;
+
+struct DevParams {
+  double gamma, K, mu, alpha, cfl_hi, cfl_lo;
+  int n_bc;
+  int bc_kind[CGKS_MAX_BC];
+  double bc_uw[CGKS_MAX_BC][2];
+  double bc_rho[CGKS_MAX_BC], bc_u[CGKS_MAX_BC][2], bc_p[CGKS_MAX_BC];
+};
+
+struct DevMesh {
+  int nc, nf;
+  const double *vol, *per, *h, *m2;          // m2: [3][nc]
+  const int *cface, *cnbr;                   // [4][nc]
+  const double *op;                          // [kNCol*kNM][nc]
+  const int *fc0, *fc1;
+  const double *fn, *fS, *fdelta, *fxi;      // fn [2][nf], fxi [8][nf]
+};
+
+struct Scalars {
+  unsigned long long dt_bits;   // min over cells of the local explicit step (bits of a positive double)
+  int status;
+  int res_ctr;                  // next slot of the residual history
+  double dt_fixed;              // > 0: prescribed step
+};
+
+__device__ __forceinline__ double dt_value(const Scalars *sc, double cfl) {
+  if (sc->dt_fixed > 0.0) return sc->dt_fixed;
+  return cfl * __longlong_as_double(static_cast<long long>(sc->dt_bits));
+}
+
+__device__ __forceinline__ bool state_ok(double gamma, const double w[4]) {
+  double p = (gamma - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+  return w[0] > 0.0 && p > 0.0 && isfinite(w[0]) && isfinite(p) && isfinite(w[1]) && isfinite(w[2]);
+}
+
+// Block reduction of two doubles in a fixed order; thread 0 writes them.
+__device__ __forceinline__ void block_sum2(double a, double b, double *out2) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { out2[0] = a; out2[1] = b; }
+  }
+}
+
+// ------------------------------------------------------------------
+// K0: reset per-step scalars
+__global__ void k_reset_dt(Scalars *sc, double dt_fixed) {
+  sc->dt_bits = 0x7ff0000000000000ull;  // +inf
+  sc->dt_fixed = dt_fixed;
+}
+
+// K4: local explicit step per cell, global min by atomicMin on the bits
+// (min is order independent).  h = 2|Omega|/perimeter, speed |U| + c + 2 nu / h.
+__global__ void k_dt(DevMesh m, DevParams P, const double *__restrict__ W, Scalars *sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = INFINITY;
+  if (i < m.nc) {
+    int n = m.nc;
+    double rho = W[i], mx = W[n + i], my = W[2 * n + i], E = W[3 * n + i];
+    double u = mx / rho, v = my / rho;
+    double p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+    double a = sqrt(P.gamma * p / rho);
+    double hh = 2.0 * m.vol[i] / m.per[i];
+    double speed = sqrt(u * u + v * v) + a + 2.0 * (P.mu / rho) / hh;
+    d = hh / speed;
+  }
+  for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_down_sync(0xffffffffu, d, o));
+  if ((threadIdx.x & 31) == 0 && d < INFINITY)
+    atomicMin(&sc->dt_bits, static_cast<unsigned long long>(__double_as_longlong(d)));
+}
+
+// Wall ghost of a cell mean / mean gradient or of a point state, global frame.
+__device__ __forceinline__ void wall_ghost_global(const DevParams &P, int tag, double nx, double ny,
+                                                  const double w[4], const double gx[4], const double gy[4],
+                                                  double wg[4], double ggx[4], double ggy[4]) {
+  double wl[4], dn[4], dt[4], tn[4], tt[4];
+  D::rot_in(nx, ny, w, wl);
+  for (int v = 0; v < 4; ++v) { tn[v] = nx * gx[v] + ny * gy[v]; tt[v] = -ny * gx[v] + nx * gy[v]; }
+  D::rot_in(nx, ny, tn, dn);
+  D::rot_in(nx, ny, tt, dt);
+  double wgl[4], dng[4], dtg[4];
+  if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+    D::ghost_slip(wl, dn, dt, wgl, dng, dtg);
+  } else {
+    double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+    double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+    D::ghost_noslip(P.gamma, wn, wt, wl, dn, dt, wgl, dng, dtg);
+  }
+  double gn[4], gt[4];
+  D::rot_out(nx, ny, wgl, wg);
+  D::rot_out(nx, ny, dng, gn);
+  D::rot_out(nx, ny, dtg, gt);
+  for (int v = 0; v < 4; ++v) { ggx[v] = nx * gn[v] - ny * gt[v]; ggy[v] = ny * gn[v] + nx * gt[v]; }
+}
+
+// K1: compact least-squares quadratic of every cell.
+//   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
+__global__ void __launch_bounds__(kCellBlock) k_recon(DevMesh m, DevParams P, const double *__restrict__ W,
+                                                      const double *__restrict__ Wx, double *__restrict__ coef) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc;
+  double wi[4], gxi[4], gyi[4];
+  for (int v = 0; v < 4; ++v) { wi[v] = W[v * n + i]; gxi[v] = Wx[v * n + i]; gyi[v] = Wx[(4 + v) * n + i]; }
+  double c[kNM][4];
+  for (int q = 0; q < kNM; ++q) {
+    double o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
+    for (int v = 0; v < 4; ++v) c[q][v] = o0 * gxi[v] + o1 * gyi[v];
+  }
+  for (int s = 0; s < kMaxFace; ++s) {
+    int fs = m.cface[s * n + i];
+    if (fs == kNoFace) continue;
+    int j = m.cnbr[s * n + i];
+    double b0[4], b1[4], b2[4];
+    if (j >= 0) {
+      for (int v = 0; v < 4; ++v) {
+        b0[v] = W[v * n + j] - wi[v];
+        b1[v] = Wx[v * n + j];
+        b2[v] = Wx[(4 + v) * n + j];
+      }
+    } else {
+      int f = fs >= 0 ? fs : ~fs;
+      int tag = -1 - m.fc1[f];
+      if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
+      double wg[4];
+      wall_ghost_global(P, tag, m.fn[f], m.fn[m.nf + f], wi, gxi, gyi, wg, b1, b2);
+      for (int v = 0; v < 4; ++v) b0[v] = wg[v] - wi[v];
+    }
+    for (int q = 0; q < kNM; ++q) {
+      double o0 = m.op[((3 * s) * kNM + q) * n + i];
+      double o1 = m.op[((3 * s + 1) * kNM + q) * n + i];
+      double o2 = m.op[((3 * s + 2) * kNM + q) * n + i];
+      for (int v = 0; v < 4; ++v) c[q][v] += o0 * b0[v] + o1 * b1[v] + o2 * b2[v];
+    }
+  }
+  for (int q = 0; q < kNM; ++q)
+    for (int v = 0; v < 4; ++v) coef[(q * 4 + v) * n + i] = c[q][v];
+}
+
+// value and gradient of the quadratic of cell i at scaled offset (x, y)
+__device__ __forceinline__ void recon_point(const DevMesh &m, const double *__restrict__ W,
+                                            const double *__restrict__ coef, int i, double x, double y,
+                                            double val[4], double gx[4], double gy[4]) {
+  const int n = m.nc;
+  double ih = 1.0 / m.h[i];
+  double p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
+  for (int v = 0; v < 4; ++v) {
+    double c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
+    double c3 = coef[(3 * 4 + v) * n + i], c4 = coef[(4 * 4 + v) * n + i];
+    val[v] = W[v * n + i] + c0 * x + c1 * y + c2 * p2 + c3 * p3 + c4 * p4;
+    gx[v] = (c0 + 2.0 * c2 * x + c3 * y) * ih;
+    gy[v] = (c1 + c3 * x + 2.0 * c4 * y) * ih;
+  }
+}
+
+// K2: gas-kinetic flux and interface state at the two Gauss points of every
+// face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
+//   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
+__global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, const double *__restrict__ W,
+                                                     const double *__restrict__ coef, double *__restrict__ out) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int nf = m.nf;
+  const int c0 = m.fc0[f], c1 = m.fc1[f];
+  const double nx = m.fn[f], ny = m.fn[nf + f], delta = m.fdelta[f];
+  double acc[4][4];
+  for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = 0.0;
+  double wff[4];
+  bool farfield = false;
+  int tag = 0;
+  if (c1 < 0) {
+    tag = -1 - c1;
+    farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
+    if (farfield) {
+      // Riemann-invariant state from the cell mean and the free stream
+      double wm[4], wl[4];
+      for (int v = 0; v < 4; ++v) wm[v] = W[v * m.nc + c0];
+      D::rot_in(nx, ny, wm, wl);
+      double une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
+      double ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
+      D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wff);
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    double wL[4], gxL[4], gyL[4];
+    recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
+    double wl[4], dnl[4], dtl[4], t0[4], t1[4];
+    D::rot_in(nx, ny, wL, wl);
+    for (int v = 0; v < 4; ++v) { t0[v] = nx * gxL[v] + ny * gyL[v]; t1[v] = -ny * gxL[v] + nx * gyL[v]; }
+    D::rot_in(nx, ny, t0, dnl);
+    D::rot_in(nx, ny, t1, dtl);
+    double wr[4], dnr[4], dtr[4];
+    if (c1 >= 0) {
+      double wR[4], gxR[4], gyR[4];
+      recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
+      D::rot_in(nx, ny, wR, wr);
+      for (int v = 0; v < 4; ++v) { t0[v] = nx * gxR[v] + ny * gyR[v]; t1[v] = -ny * gxR[v] + nx * gyR[v]; }
+      D::rot_in(nx, ny, t0, dnr);
+      D::rot_in(nx, ny, t1, dtr);
+    } else if (farfield) {
+      for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = 0.0; dtr[v] = 0.0; }
+    } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+      D::ghost_slip(wl, dnl, dtl, wr, dnr, dtr);
+    } else {
+      double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+      double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+      D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
+    }
+    double F0[4], F1[4], Wc[4], Wt[4];
+    D::gks_point_local(P.K, P.mu, P.alpha, delta, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
+    double g[4];
+    D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += 0.5 * g[v];
+    D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += 0.5 * g[v];
+    D::rot_out(nx, ny, Wc, g); for (int v = 0; v < 4; ++v) acc[2][v] += 0.5 * g[v];
+    D::rot_out(nx, ny, Wt, g); for (int v = 0; v < 4; ++v) acc[3][v] += 0.5 * g[v];
+  }
+  for (int k = 0; k < 4; ++k)
+    for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
+}
+
+// K3 modes
+enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
+
+// K3: gather the face sums of each cell.
+//   net flux   R  = -sum_p sgn S_p (a0 F0A + a1 F1A + a2 F1B)
+//   W_out = W_base + dt/|Omega| R    (or R itself in kResidual mode)
+//   Wx_out = 1/|Omega| sum_p sgn S_p n_p (WcA + b1 WtX)
+// plus the per-block density-residual partial sums and the state check.
+__global__ void __launch_bounds__(kCellBlock) k_update(DevMesh m, DevParams P, int mode, const double *__restrict__ Wbase,
+                                                       const double *__restrict__ FA, const double *__restrict__ FB,
+                                                       Scalars *sc, double *__restrict__ Wout, double *__restrict__ Wxout,
+                                                       double *__restrict__ partial, double *__restrict__ Rout) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc, nf = m.nf;
+  double num = 0.0, den = 0.0;
+  if (i < n) {
+    double dt = dt_value(sc, P.cfl_hi);
+    double a0, a1, a2, b1;
+    const double *FW = FA;   // where Wt is taken from
+    switch (mode) {
+      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; a2 = 0.0; b1 = dt; break;
+      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; a2 = 0.0; b1 = 0.5 * dt; break;
+      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; a2 = 2.0; b1 = dt; FW = FB; break;
+      default: a0 = 1.0; a1 = 0.5 * dt; a2 = 0.0; b1 = 0.0; break;
+    }
+    double R[4] = { 0, 0, 0, 0 }, gx[4] = { 0, 0, 0, 0 }, gy[4] = { 0, 0, 0, 0 };
+    for (int s = 0; s < kMaxFace; ++s) {
+      int fs = m.cface[s * n + i];
+      if (fs == kNoFace) continue;
+      int f = fs >= 0 ? fs : ~fs;
+      double sg = fs >= 0 ? 1.0 : -1.0;
+      double S = m.fS[f], nx = m.fn[f], ny = m.fn[nf + f];
+      for (int v = 0; v < 4; ++v) {
+        double f1 = FA[(4 + v) * nf + f];
+        if (mode == kS2O4Final) f1 += a2 * FB[(4 + v) * nf + f];
+        double fl = S * (a0 * FA[v * nf + f] + a1 * f1);
+        R[v] -= sg * fl;
+        if (mode != kResidual) {
+          double wp = FA[(8 + v) * nf + f] + b1 * FW[(12 + v) * nf + f];
+          gx[v] += sg * S * nx * wp;
+          gy[v] += sg * S * ny * wp;
+        }
+      }
+    }
+    if (Rout)
+      for (int v = 0; v < 4; ++v) Rout[v * n + i] = R[v];
+    if (mode != kResidual) {
+      double iv = 1.0 / m.vol[i];
+      double w[4];
+      for (int v = 0; v < 4; ++v) {
+        w[v] = Wbase[v * n + i] + dt / m.vol[i] * R[v];
+        Wout[v * n + i] = w[v];
+        Wxout[v * n + i] = gx[v] * iv;
+        Wxout[(4 + v) * n + i] = gy[v] * iv;
+      }
+      if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
+      num = fabs(w[0] - Wbase[i]);
+      den = Wbase[i];
+    }
+  }
+  if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+// Sum the block partials in a fixed order; Res = num / den into hist[ctr++].
+__global__ void k_res_final(const double *__restrict__ partial, int nblocks, Scalars *sc, double *hist, int cap,
+                            double *last) {
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) { a += partial[2 * k]; b += partial[2 * k + 1]; }
+  block_sum2(a, b, last + 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = last[1] / last[2];
+    last[0] = r;
+    int c = sc->res_ctr;
+    if (hist && c < cap) hist[c] = r;
+    sc->res_ctr = c + 1;
+  }
+}
+
+// ---------------------------- low-order level ----------------------------
+__device__ __forceinline__ double lambda_side(const DevParams &P, const double w[4], double nx, double ny,
+                                              double S, double vol) {
+  double rho = w[0], u = w[1] / rho, v = w[2] / rho;
+  double p = (P.gamma - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
+  double c = sqrt(P.gamma * p / rho);
+  return fabs(u * nx + v * ny) + c + 2.0 * (P.mu / rho) * S / vol;
+}
+
+// ghost of a cell-mean state (zero gradients)
+__device__ __forceinline__ void lo_ghost(const DevParams &P, int tag, double nx, double ny, const double w[4],
+                                         double wg[4]) {
+  double wl[4], z[4] = { 0, 0, 0, 0 }, wgl[4], a[4], b[4];
+  D::rot_in(nx, ny, w, wl);
+  int kind = P.bc_kind[tag];
+  if (kind == CGKS_BC_FARFIELD) {
+    double une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
+    double ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
+    D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wgl);
+  } else if (kind == CGKS_BC_SLIP) {
+    D::ghost_slip(wl, z, z, wgl, a, b);
+  } else {
+    double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+    double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+    D::ghost_noslip(P.gamma, wn, wt, wl, z, z, wgl, a, b);
+  }
+  D::rot_out(nx, ny, wgl, wg);
+}
+
+// K5: first-order KFVS flux and spectral radius per face.
+__global__ void __launch_bounds__(kCellBlock) k_lo_face(DevMesh m, DevParams P, const double *__restrict__ U,
+                                                        double *__restrict__ Flo, double *__restrict__ lam) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int n = m.nc, nf = m.nf;
+  int c0 = m.fc0[f], c1 = m.fc1[f];
+  double nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
+  double w0[4], w1[4];
+  for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
+  double vol1;
+  if (c1 >= 0) {
+    for (int v = 0; v < 4; ++v) w1[v] = U[v * n + c1];
+    vol1 = m.vol[c1];
+  } else {
+    lo_ghost(P, -1 - c1, nx, ny, w0, w1);
+    vol1 = m.vol[c0];
+  }
+  double l0[4], l1[4], F[4], g[4];
+  D::rot_in(nx, ny, w0, l0);
+  D::rot_in(nx, ny, w1, l1);
+  D::kfvs_local(P.K, l0, l1, F);
+  D::rot_out(nx, ny, F, g);
+  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = g[v];
+  double la = lambda_side(P, w0, nx, ny, S, m.vol[c0]);
+  double lb = lambda_side(P, w1, nx, ny, S, vol1);
+  lam[f] = la > lb ? la : lb;
+}
+
+// K6: low-order right-hand side R^k = R_lo(U^k) + S and diagonal D_i.
+// first: also forms the forcing S = R_p0 - R_lo(W_p0) (Section 3, step 3).
+__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, int first,
+                                                       const double *__restrict__ Flo, const double *__restrict__ lam,
+                                                       const double *__restrict__ Rp0, double *__restrict__ Src,
+                                                       double *__restrict__ Rk, double *__restrict__ Dg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc, nf = m.nf;
+  double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
+  for (int s = 0; s < kMaxFace; ++s) {
+    int fs = m.cface[s * n + i];
+    if (fs == kNoFace) continue;
+    int f = fs >= 0 ? fs : ~fs;
+    double sg = fs >= 0 ? 1.0 : -1.0;
+    double S = m.fS[f];
+    for (int v = 0; v < 4; ++v) R[v] -= sg * S * Flo[v * nf + f];
+    sum += lam[f] * S;
+  }
+  for (int v = 0; v < 4; ++v) {
+    double src;
+    if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
+    else src = Src[v * n + i];
+    Rk[v * n + i] = R[v] + src;
+  }
+  double dti = P.cfl_lo * m.vol[i] / sum;
+  Dg[i] = m.vol[i] / dti + 0.5 * sum;
+}
+
+// K7: point relaxation of the cells of one colour, Eq. (implicit-local):
+//   dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
+//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
+__global__ void __launch_bounds__(kCellBlock) k_sweep(DevMesh m, DevParams P, int begin, int end,
+                                                      const double *__restrict__ U, const double *__restrict__ Rk,
+                                                      const double *__restrict__ Dg, const double *__restrict__ lam,
+                                                      double *__restrict__ dU) {
+  int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= end) return;
+  const int n = m.nc, nf = m.nf;
+  double acc[4];
+  for (int v = 0; v < 4; ++v) acc[v] = Rk[v * n + i];
+  for (int s = 0; s < kMaxFace; ++s) {
+    int j = m.cnbr[s * n + i];
+    if (j < 0) continue;
+    int fs = m.cface[s * n + i];
+    int f = fs >= 0 ? fs : ~fs;
+    double sg = fs >= 0 ? 1.0 : -1.0;
+    double nx = sg * m.fn[f], ny = sg * m.fn[nf + f], S = m.fS[f], lp = lam[f];
+    double uj[4], up[4], fa[4], fb[4];
+    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; up[v] = uj[v] + dU[v * n + j]; }
+    D::euler_flux(P.gamma, up, nx, ny, fa);
+    D::euler_flux(P.gamma, uj, nx, ny, fb);
+    for (int v = 0; v < 4; ++v) {
+      double ma = 0.5 * (fa[v] - lp * up[v]);
+      double mb = 0.5 * (fb[v] - lp * uj[v]);
+      acc[v] -= S * (ma - mb);
+    }
+  }
+  double id = Dg[i];
+  for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] / id;
+}
+
+// K8: U += dU
+__global__ void k_axpy(int n4, double *__restrict__ U, const double *__restrict__ dU) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n4) U[i] += dU[i];
+}
+
+// K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
+// residual against the state at the start of the cycle, state check.
+__global__ void __launch_bounds__(kCellBlock) k_prolong(DevMesh m, DevParams P, double *__restrict__ W,
+                                                        const double *__restrict__ Wp0, const double *__restrict__ U,
+                                                        Scalars *sc, double *__restrict__ partial) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc;
+  double num = 0.0, den = 0.0;
+  if (i < n) {
+    double w[4];
+    double old_rho = W[i];
+    for (int v = 0; v < 4; ++v) {
+      double wp = Wp0[v * n + i];
+      w[v] = wp + (U[v * n + i] - wp);
+      W[v * n + i] = w[v];
+    }
+    if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
+    num = fabs(w[0] - old_rho);
+    den = old_rho;
+  }
+  block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+// AoS caller order <-> SoA internal order
+__global__ void k_gather_state(int n, const int *__restrict__ perm, const double *__restrict__ Wa,
+                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = perm[i];
+  for (int v = 0; v < 4; ++v) W[v * n + i] = Wa[4 * c + v];
+  for (int k = 0; k < 8; ++k) Wx[k * n + i] = Wxa ? Wxa[8 * c + k] : 0.0;
+}
+__global__ void k_scatter_state(int n, const int *__restrict__ perm, const double *__restrict__ W,
+                                const double *__restrict__ Wx, double *__restrict__ Wa, double *__restrict__ Wxa) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = perm[i];
+  if (Wa) for (int v = 0; v < 4; ++v) Wa[4 * c + v] = W[v * n + i];
+  if (Wxa) for (int k = 0; k < 8; ++k) Wxa[8 * c + k] = Wx[k * n + i];
+}
+
+// kernel ids for the per-kernel timers
+enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_AXPY,
+                KI_PROLONG, KI_COUNT };
+const char *kKernelNames[KI_COUNT] = { "k_dt", "k_recon", "k_face", "k_update", "k_res_final", "k_lo_face",
+                                       "k_lo_rhs", "k_sweep", "k_axpy", "k_prolong" };
+
+inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+struct cgks_solver {
+  HostMesh hm;                  // host copy (ordering and permutations)
+  cgks_params params{};
+  DevParams dp{};
+  DevMesh dm{};
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  int device = 0;
+  // state and work arrays (device)
+  double *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr;
+  double *coef = nullptr, *FA = nullptr, *FB = nullptr;
+  double *U = nullptr, *dU = nullptr, *Rp0 = nullptr, *Src = nullptr, *Rk = nullptr, *Dg = nullptr;
+  double *Flo = nullptr, *lam = nullptr, *partial = nullptr, *last = nullptr;
+  double *hist = nullptr;
+  int hist_cap = 0;
+  double *stage_aos = nullptr;  // [12 n] staging for set/get state
+  int *perm = nullptr;
+  Scalars *sc = nullptr;
+  int nblk_cell = 0;
+  // graphs
+  cudaGraphExec_t g_cycle = nullptr, g_step = nullptr;
+  // timers
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+  double t_ms[KI_COUNT] = { 0 };
+  long long t_cnt[KI_COUNT] = { 0 };
+  long long launches = 0;
+  int status_cache = 0;
+};
+
+namespace {
+
+void *dev_alloc(cgks_solver *s, size_t bytes) {
+  if (s->params.alloc) return s->params.alloc(bytes, s->params.alloc_ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+void dev_free(cgks_solver *s, void *p) {
+  if (!p) return;
+  if (s->params.alloc && s->params.free) s->params.free(p, s->params.alloc_ctx);
+  else if (!s->params.alloc) cudaFree(p);
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return CGKS_ECUDA;   \
+  } while (0)
+
+// launch helper with optional timing
+template <typename Kern, typename... Args>
+void launch(cgks_solver *s, int id, Kern kern, dim3 grid, dim3 block, Args... args) {
+  if (grid.x == 0) return;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (s->timing) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s->stream);
+  }
+  kern<<<grid, block, 0, s->stream>>>(args...);
+  if (s->timing) {
+    cudaEventRecord(b, s->stream);
+    s->tev.push_back({ id, { a, b } });
+  }
+  s->launches++;
+}
+
+// ---- building blocks of a step / cycle ----
+void enqueue_dt(cgks_solver *s, double dt_fixed) {
+  launch(s, KI_DT, k_reset_dt, dim3(1), dim3(1), s->sc, dt_fixed);
+  if (!(dt_fixed > 0.0)) launch(s, KI_DT, k_dt, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (const double *)s->W, s->sc);
+}
+
+void enqueue_hi_eval(cgks_solver *s, const double *W, const double *Wx, double *Fout) {
+  launch(s, KI_RECON, k_recon, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, W, Wx, s->coef);
+  launch(s, KI_FACE, k_face, dim3(nblk(s->dm.nf, kFaceBlock)), dim3(kFaceBlock), s->dm, s->dp, W,
+         (const double *)s->coef, Fout);
+}
+
+// high-order step from (W, Wx) into (Wout, Wx): Wx updated in place.
+void enqueue_hi_step(cgks_solver *s, double *Wout, bool want_res) {
+  double *part = want_res ? s->partial : nullptr;
+  enqueue_hi_eval(s, s->W, s->Wx, s->FA);
+  if (s->params.time_scheme == CGKS_S1O2) {
+    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS1O2,
+           (const double *)s->W, (const double *)s->FA, (const double *)s->FA, s->sc, Wout, s->Wx, part, s->Rp0);
+  } else {
+    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Stage,
+           (const double *)s->W, (const double *)s->FA, (const double *)s->FA, s->sc, s->Ws, s->Wxs,
+           (double *)nullptr, (double *)nullptr);
+    enqueue_hi_eval(s, s->Ws, s->Wxs, s->FB);
+    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Final,
+           (const double *)s->W, (const double *)s->FA, (const double *)s->FB, s->sc, Wout, s->Wx, part, s->Rp0);
+  }
+  if (want_res)
+    launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
+           s->hist_cap, s->last);
+}
+
+// low-order solve from U = W_p0 (= s->Wn), R_p0 in s->Rp0; result in s->U
+void enqueue_lo_solve(cgks_solver *s) {
+  const int n = s->dm.nc, nf = s->dm.nf;
+  cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream);
+  for (int k = 0; k < s->params.n_implicit; ++k) {
+    launch(s, KI_LOFACE, k_lo_face, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, (const double *)s->U,
+           s->Flo, s->lam);
+    launch(s, KI_LORHS, k_lo_rhs, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0,
+           (const double *)s->Flo, (const double *)s->lam, (const double *)s->Rp0, s->Src, s->Rk, s->Dg);
+    cudaMemsetAsync(s->dU, 0, sizeof(double) * 4 * n, s->stream);
+    for (int sw = 0; sw < s->params.n_sweeps; ++sw) {
+      for (int dir = 0; dir < 2; ++dir) {
+        for (int q = 0; q < s->hm.n_colours; ++q) {
+          int c = dir == 0 ? q : s->hm.n_colours - 1 - q;
+          int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
+          launch(s, KI_SWEEP, k_sweep, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, b, e,
+                 (const double *)s->U, (const double *)s->Rk, (const double *)s->Dg, (const double *)s->lam, s->dU);
+        }
+      }
+    }
+    launch(s, KI_AXPY, k_axpy, dim3(nblk(4 * n, kCellBlock)), dim3(kCellBlock), 4 * n, s->U, (const double *)s->dU);
+  }
+}
+
+void enqueue_cycle(cgks_solver *s) {
+  enqueue_dt(s, -1.0);
+  // 1: high-order step into W_p0 = Wn (W keeps W^n for the residual)
+  enqueue_hi_step(s, s->Wn, false);
+  // 2: R_p0 = time-averaged high-order net flux at W^{n+1}
+  enqueue_hi_eval(s, s->Wn, s->Wx, s->FB);
+  launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kResidual,
+         (const double *)s->Wn, (const double *)s->FB, (const double *)s->FB, s->sc, (double *)nullptr,
+         (double *)nullptr, (double *)nullptr, s->Rp0);
+  // 3-4: forcing and implicit low-order solve
+  enqueue_lo_solve(s);
+  // 5: correction and residual
+  launch(s, KI_PROLONG, k_prolong, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W, (const double *)s->Wn,
+         (const double *)s->U, s->sc, s->partial);
+  launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
+         s->hist_cap, s->last);
+}
+
+void enqueue_explicit_step(cgks_solver *s, double dt_fixed) {
+  enqueue_dt(s, dt_fixed);
+  enqueue_hi_step(s, s->W, true);
+}
+
+int ensure_hist(cgks_solver *s, int n) {
+  if (n <= s->hist_cap) return CGKS_OK;
+  // grow: graphs captured with the old pointer must be rebuilt
+  double *p = static_cast<double *>(dev_alloc(s, sizeof(double) * n));
+  if (!p) return CGKS_ENOMEM;
+  if (s->hist) { cudaStreamSynchronize(s->stream); dev_free(s, s->hist); }
+  s->hist = p;
+  s->hist_cap = n;
+  if (s->g_cycle) { cudaGraphExecDestroy(s->g_cycle); s->g_cycle = nullptr; }
+  if (s->g_step) { cudaGraphExecDestroy(s->g_step); s->g_step = nullptr; }
+  return CGKS_OK;
+}
+
+int begin_call(cgks_solver *s) {
+  CK(cudaSetDevice(s->device));
+  CK(cudaEventRecord(s->ev_user, s->user_stream));
+  CK(cudaStreamWaitEvent(s->stream, s->ev_user, 0));
+  return CGKS_OK;
+}
+int end_call(cgks_solver *s) {
+  CK(cudaEventRecord(s->ev_done, s->stream));
+  CK(cudaStreamWaitEvent(s->user_stream, s->ev_done, 0));
+  return CGKS_OK;
+}
+
+int capture(cgks_solver *s, bool cycle, cudaGraphExec_t *out) {
+  cudaGraph_t g = nullptr;
+  bool t = s->timing;
+  s->timing = false;
+  long long l0 = s->launches;
+  CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  if (cycle) enqueue_cycle(s);
+  else enqueue_explicit_step(s, -1.0);
+  cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+  s->launches = l0;
+  s->timing = t;
+  if (e != cudaSuccess) return CGKS_ECUDA;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? CGKS_OK : CGKS_ECUDA;
+}
+
+long long count_launches(cgks_solver *s, bool cycle) {
+  // number of kernels one cycle / step enqueues
+  long long per_eval = 2;
+  long long hi = 1 + per_eval + 1 + (s->params.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
+  long long dt = 2;
+  if (!cycle) return dt + hi + 1;
+  long long lo = s->params.n_implicit * (3 + 2LL * s->params.n_sweeps * s->hm.n_colours);
+  return dt + hi + per_eval + 1 + lo + 2;
+}
+
+int read_status(cgks_solver *s) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, &s->sc->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->status_cache = st;
+  return st ? CGKS_EDIVERGED : CGKS_OK;
+}
+
+void collect_timing(cgks_solver *s) {
+  for (auto &e : s->tev) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.second.second);
+    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+    s->t_ms[e.first] += ms;
+    s->t_cnt[e.first] += 1;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  s->tev.clear();
+}
+
+}  // namespace
+
+// =============================== C ABI ===================================
+extern "C" {
+
+void cgks_default_params(cgks_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->gamma = 1.4;
+  p->mu = 0.0;
+  p->alpha = 4.0 / 3.0;
+  p->cfl_hi = 0.4;
+  p->cfl_lo = 1000.0;
+  p->n_implicit = 6;
+  p->n_sweeps = 2;
+  p->time_scheme = CGKS_S1O2;
+  p->precision = CGKS_FP64;
+  p->use_graph = 1;
+}
+
+const char *cgks_strerror(int st) {
+  switch (st) {
+    case CGKS_OK: return "ok";
+    case CGKS_EINVAL: return "invalid argument";
+    case CGKS_ENOMEM: return "out of memory";
+    case CGKS_EMESH: return "mesh rejected";
+    case CGKS_ECUDA: return "CUDA error or no device";
+    case CGKS_EDIVERGED: return "solution diverged (non-positive or non-finite density / pressure)";
+    case CGKS_ETIMEOUT: return "timeout";
+    case CGKS_EBUDGET: return "memory budget exceeded";
+    default: return "unknown status";
+  }
+}
+
+int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cells, const uint8_t *cell_type,
+                     const int64_t *cell_ptr, const int64_t *cell_nodes, int64_t n_bfaces, const int64_t *bface_ptr,
+                     const int64_t *bface_nodes, const int32_t *bface_tag, cgks_mesh **out) {
+  if (!out) return CGKS_EINVAL;
+  *out = nullptr;
+  if (dim != 2) return CGKS_EINVAL;
+  cgks_mesh *m = new (std::nothrow) cgks_mesh();
+  if (!m) return CGKS_ENOMEM;
+  int rc;
+  try {
+    rc = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces, bface_ptr, bface_nodes,
+                         bface_tag, m->h);
+  } catch (const std::bad_alloc &) {
+    rc = CGKS_ENOMEM;
+  }
+  if (rc != CGKS_OK) { delete m; return rc; }
+  *out = m;
+  return CGKS_OK;
+}
+
+static size_t solver_bytes(int64_t nc, int64_t nf) {
+  size_t cells = 4 + 8 + 4 + 4 + 8 + 20 + 4 * 6 + 1;      // state + work
+  size_t geo_c = 3 + 3 + kNCol * kNM;                      // vol, per, h, m2, op
+  size_t faces = 16 * 2 + 4 + 1 + 2 + 1 + 1 + 8;           // FA, FB, Flo, lam, fn, fS, fdelta, fxi
+  size_t ints = 8 * nc + 2 * nf + nc;                      // cface, cnbr, fc0/fc1, perm
+  return sizeof(double) * ((cells + geo_c + 12) * nc + faces * nf + 2 * kMaxBlocksReduce + 16) + sizeof(int) * ints +
+         64 * 256 + sizeof(Scalars);
+}
+
+int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
+  if (!m || !out) return CGKS_EINVAL;
+  out->n_cells = m->h.n_cells;
+  out->n_faces = m->h.n_faces;
+  out->n_bfaces = m->h.n_bfaces;
+  out->n_colours = m->h.n_colours;
+  out->dim = m->h.dim;
+  out->device_bytes = static_cast<int64_t>(solver_bytes(m->h.n_cells, m->h.n_faces));
+  return CGKS_OK;
+}
+
+int cgks_mesh_ordering(const cgks_mesh *m, int64_t *rcm, int32_t *colour) {
+  if (!m) return CGKS_EINVAL;
+  if (rcm) std::copy(m->h.rcm.begin(), m->h.rcm.end(), rcm);
+  if (colour) std::copy(m->h.colour.begin(), m->h.colour.end(), colour);
+  return CGKS_OK;
+}
+
+int cgks_mesh_destroy(cgks_mesh *m) {
+  delete m;
+  return CGKS_OK;
+}
+
+int cgks_solver_destroy(cgks_solver *s) {
+  if (!s) return CGKS_OK;
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  collect_timing(s);
+  if (s->g_cycle) cudaGraphExecDestroy(s->g_cycle);
+  if (s->g_step) cudaGraphExecDestroy(s->g_step);
+  dev_free(s, s->hist);
+  dev_free(s, s->arena);
+  if (s->ev_user) cudaEventDestroy(s->ev_user);
+  if (s->ev_done) cudaEventDestroy(s->ev_done);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return CGKS_OK;
+}
+
+int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **out) {
+  if (!m || !p || !out) return CGKS_EINVAL;
+  *out = nullptr;
+  if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
+      p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
+      p->n_bc > CGKS_MAX_BC || p->precision != CGKS_FP64)
+    return CGKS_EINVAL;
+  for (int t : m->h.bface_tags_used)
+    if (t >= p->n_bc) return CGKS_EINVAL;
+  for (int b = 0; b < p->n_bc; ++b) {
+    int k = p->bc[b].kind;
+    if (k != CGKS_BC_SLIP && k != CGKS_BC_NOSLIP && k != CGKS_BC_FARFIELD) return CGKS_EINVAL;
+    if (k == CGKS_BC_FARFIELD && !(p->bc[b].rho > 0.0 && p->bc[b].p > 0.0)) return CGKS_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CGKS_ECUDA;
+  cgks_solver *s = new (std::nothrow) cgks_solver();
+  if (!s) return CGKS_ENOMEM;
+  s->hm = m->h;
+  s->params = *p;
+  cudaGetDevice(&s->device);
+  s->user_stream = static_cast<cudaStream_t>(p->stream);
+  auto fail = [&](int rc) { cgks_solver_destroy(s); return rc; };
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
+  // parameters
+  DevParams &dp = s->dp;
+  dp.gamma = p->gamma;
+  dp.K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
+  dp.mu = p->mu;
+  dp.alpha = p->alpha;
+  dp.cfl_hi = p->cfl_hi;
+  dp.cfl_lo = p->cfl_lo;
+  dp.n_bc = p->n_bc;
+  for (int b = 0; b < CGKS_MAX_BC; ++b) {
+    const cgks_bc &bc = p->bc[b];
+    dp.bc_kind[b] = b < p->n_bc ? bc.kind : CGKS_BC_SLIP;
+    dp.bc_uw[b][0] = bc.u_wall[0]; dp.bc_uw[b][1] = bc.u_wall[1];
+    dp.bc_rho[b] = bc.rho; dp.bc_u[b][0] = bc.u[0]; dp.bc_u[b][1] = bc.u[1]; dp.bc_p[b] = bc.p;
+  }
+  // operators depend on which tags are walls
+  std::vector<char> wall(CGKS_MAX_BC, 0);
+  for (int b = 0; b < p->n_bc; ++b) wall[b] = p->bc[b].kind != CGKS_BC_FARFIELD;
+  std::vector<double> op;
+  try {
+    build_operator(s->hm, wall, op);
+  } catch (const std::bad_alloc &) {
+    return fail(CGKS_ENOMEM);
+  }
+  const int64_t nc = s->hm.n_cells, nf = s->hm.n_faces;
+  s->nblk_cell = nblk(static_cast<int>(nc), kCellBlock);
+  if (s->nblk_cell > kMaxBlocksReduce * 64) return fail(CGKS_EINVAL);
+  // carve one arena
+  struct Piece { void **dst; size_t bytes; };
+  std::vector<Piece> pieces;
+  auto D8 = [&](double **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(double) * cnt }); };
+  auto I4 = [&](int **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(int) * cnt }); };
+  double *vol, *per, *h, *m2, *opd, *fn, *fS, *fdelta, *fxi;
+  int *cface, *cnbr, *fc0, *fc1;
+  D8(&s->W, 4 * nc); D8(&s->Wx, 8 * nc); D8(&s->Wn, 4 * nc); D8(&s->Ws, 4 * nc); D8(&s->Wxs, 8 * nc);
+  D8(&s->coef, 20 * nc); D8(&s->FA, 16 * nf); D8(&s->FB, 16 * nf);
+  D8(&s->U, 4 * nc); D8(&s->dU, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc); D8(&s->Rk, 4 * nc);
+  D8(&s->Dg, nc); D8(&s->Flo, 4 * nf); D8(&s->lam, nf);
+  D8(&s->partial, 2 * std::max(s->nblk_cell, 1)); D8(&s->last, 4); D8(&s->stage_aos, 12 * nc);
+  D8(&vol, nc); D8(&per, nc); D8(&h, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
+  D8(&fn, 2 * nf); D8(&fS, nf); D8(&fdelta, nf); D8(&fxi, 8 * nf);
+  I4(&cface, kMaxFace * nc); I4(&cnbr, kMaxFace * nc); I4(&fc0, nf); I4(&fc1, nf); I4(&s->perm, nc);
+  pieces.push_back({ reinterpret_cast<void **>(&s->sc), sizeof(Scalars) });
+  size_t total = 0;
+  for (auto &pc : pieces) total += (pc.bytes + 255) & ~size_t(255);
+  s->arena = dev_alloc(s, total);
+  if (!s->arena) return fail(CGKS_ENOMEM);
+  s->arena_bytes = total;
+  {
+    char *cur = static_cast<char *>(s->arena);
+    for (auto &pc : pieces) { *pc.dst = cur; cur += (pc.bytes + 255) & ~size_t(255); }
+  }
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
+  };
+  const HostMesh &hm = s->hm;
+  bool ok = up(vol, hm.vol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) && up(h, hm.h.data(), 8 * nc) &&
+            up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) && up(fn, hm.fn.data(), 8 * 2 * nf) &&
+            up(fS, hm.fS.data(), 8 * nf) && up(fdelta, hm.fdelta.data(), 8 * nf) && up(fxi, hm.fxi.data(), 8 * 8 * nf) &&
+            up(cface, hm.cface.data(), 4 * kMaxFace * nc) && up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) &&
+            up(fc0, hm.fc0.data(), 4 * nf) && up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc);
+  if (!ok) return fail(CGKS_ECUDA);
+  if (cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaMemsetAsync(s->W, 0, sizeof(double) * 12 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaMemsetAsync(s->Rp0, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  DevMesh &dm = s->dm;
+  dm.nc = static_cast<int>(nc); dm.nf = static_cast<int>(nf);
+  dm.vol = vol; dm.per = per; dm.h = h; dm.m2 = m2; dm.op = opd;
+  dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
+  dm.fn = fn; dm.fS = fS; dm.fdelta = fdelta; dm.fxi = fxi;
+  if (ensure_hist(s, 1024) != CGKS_OK) return fail(CGKS_ENOMEM);
+  *out = s;
+  return CGKS_OK;
+}
+
+static int set_state_impl(cgks_solver *s, const double *W, const double *Wx, bool device) {
+  if (!s || !W) return CGKS_EINVAL;
+  const int n = s->dm.nc;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  double *wa = s->stage_aos, *wxa = s->stage_aos + 4 * n;
+  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(wa, W, sizeof(double) * 4 * n, kind, s->stream));
+  if (Wx) CK(cudaMemcpyAsync(wxa, Wx, sizeof(double) * 8 * n, kind, s->stream));
+  k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, wa, Wx ? wxa : nullptr, s->W, s->Wx);
+  s->launches++;
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(&s->sc->status, 0, sizeof(int), s->stream));
+  s->status_cache = 0;
+  return end_call(s);
+}
+
+int cgks_set_state(cgks_solver *s, const double *W, const double *Wx) { return set_state_impl(s, W, Wx, false); }
+int cgks_set_state_device(cgks_solver *s, const double *W, const double *Wx) { return set_state_impl(s, W, Wx, true); }
+
+static int get_state_impl(cgks_solver *s, double *W, double *Wx, bool device) {
+  if (!s) return CGKS_EINVAL;
+  const int n = s->dm.nc;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  double *wa = s->stage_aos, *wxa = s->stage_aos + 4 * n;
+  k_scatter_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, s->W, s->Wx, wa, wxa);
+  s->launches++;
+  CK(cudaGetLastError());
+  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (W) CK(cudaMemcpyAsync(W, wa, sizeof(double) * 4 * n, kind, s->stream));
+  if (Wx) CK(cudaMemcpyAsync(Wx, wxa, sizeof(double) * 8 * n, kind, s->stream));
+  if (!device) CK(cudaStreamSynchronize(s->stream));
+  return end_call(s);
+}
+
+int cgks_get_state(cgks_solver *s, double *W, double *Wx) { return get_state_impl(s, W, Wx, false); }
+int cgks_get_state_device(cgks_solver *s, double *W, double *Wx) { return get_state_impl(s, W, Wx, true); }
+
+int cgks_highorder_step(cgks_solver *s, double dt, double *dt_used) {
+  if (!s) return CGKS_EINVAL;
+  if (s->status_cache) return CGKS_EDIVERGED;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
+  enqueue_explicit_step(s, dt);
+  CK(cudaGetLastError());
+  Scalars h;
+  CK(cudaMemcpyAsync(&h, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->timing) collect_timing(s);
+  if (dt_used) *dt_used = h.dt_fixed > 0.0 ? h.dt_fixed : s->params.cfl_hi * __builtin_bit_cast(double, h.dt_bits);
+  s->status_cache = h.status;
+  rc = end_call(s);
+  if (rc) return rc;
+  return h.status ? CGKS_EDIVERGED : CGKS_OK;
+}
+
+static int run_many(cgks_solver *s, int n, double *res_hist, bool cycle) {
+  if (!s || n < 0) return CGKS_EINVAL;
+  if (s->status_cache) return CGKS_EDIVERGED;
+  if (n == 0) return CGKS_OK;
+  int rc = ensure_hist(s, n);
+  if (rc) return rc;
+  rc = begin_call(s);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
+  bool graph = s->params.use_graph && !s->timing;
+  cudaGraphExec_t *ge = cycle ? &s->g_cycle : &s->g_step;
+  if (graph && !*ge) {
+    rc = capture(s, cycle, ge);
+    if (rc) return rc;
+  }
+  long long per = count_launches(s, cycle);
+  for (int k = 0; k < n; ++k) {
+    if (graph) {
+      CK(cudaGraphLaunch(*ge, s->stream));
+      s->launches += per;
+    } else if (cycle) {
+      enqueue_cycle(s);
+    } else {
+      enqueue_explicit_step(s, -1.0);
+    }
+  }
+  CK(cudaGetLastError());
+  if (res_hist) CK(cudaMemcpyAsync(res_hist, s->hist, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+  rc = read_status(s);
+  if (s->timing) collect_timing(s);
+  int rc2 = end_call(s);
+  return rc ? rc : rc2;
+}
+
+int cgks_explicit_steps(cgks_solver *s, int n, double *res_hist) { return run_many(s, n, res_hist, false); }
+int cgks_pmg_cycle(cgks_solver *s, int n_cycles, double *res_hist) { return run_many(s, n_cycles, res_hist, true); }
+
+int cgks_loworder_smooth(cgks_solver *s) {
+  if (!s) return CGKS_EINVAL;
+  if (s->status_cache) return CGKS_EDIVERGED;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  const int n = s->dm.nc;
+  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
+  CK(cudaMemcpyAsync(s->Wn, s->W, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream));
+  enqueue_lo_solve(s);
+  launch(s, KI_PROLONG, k_prolong, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W, (const double *)s->Wn,
+         (const double *)s->U, s->sc, s->partial);
+  launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
+         s->hist_cap, s->last);
+  CK(cudaGetLastError());
+  rc = read_status(s);
+  if (s->timing) collect_timing(s);
+  int rc2 = end_call(s);
+  return rc ? rc : rc2;
+}
+
+int cgks_residual(cgks_solver *s, double *res, double *r_l2) {
+  if (!s) return CGKS_EINVAL;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  double last[3];
+  CK(cudaMemcpyAsync(last, s->last, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<double> R;
+  if (r_l2) {
+    R.resize(4 * static_cast<size_t>(s->dm.nc));
+    CK(cudaMemcpyAsync(R.data(), s->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  if (res) *res = last[0];
+  if (r_l2) {
+    const int n = s->dm.nc;
+    for (int v = 0; v < 4; ++v) {
+      double a = 0.0;
+      for (int i = 0; i < n; ++i) a += R[v * n + i] * R[v * n + i];
+      r_l2[v] = std::sqrt(a);
+    }
+  }
+  return end_call(s);
+}
+
+int cgks_get_rp0(cgks_solver *s, double *Rp0) {
+  if (!s || !Rp0) return CGKS_EINVAL;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  const int n = s->dm.nc;
+  std::vector<double> R(4 * static_cast<size_t>(n));
+  CK(cudaMemcpyAsync(R.data(), s->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < n; ++i) {
+    int c = s->hm.perm[i];
+    for (int v = 0; v < 4; ++v) Rp0[4 * c + v] = R[v * n + i];
+  }
+  return end_call(s);
+}
+
+// ---- instrumentation (not in the paper): per-kernel CUDA-event timers and
+// the count of kernels this solver has launched ----
+int cgks_set_timing(cgks_solver *s, int on) {
+  if (!s) return CGKS_EINVAL;
+  cudaStreamSynchronize(s->stream);
+  collect_timing(s);
+  s->timing = on != 0;
+  return CGKS_OK;
+}
+
+int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_ms, int64_t *count) {
+  if (!s) return CGKS_EINVAL;
+  cudaStreamSynchronize(s->stream);
+  collect_timing(s);
+  int k = 0;
+  for (; k < KI_COUNT && k < max; ++k) {
+    if (names) names[k] = kKernelNames[k];
+    if (total_ms) total_ms[k] = s->t_ms[k];
+    if (count) count[k] = s->t_cnt[k];
+  }
+  return k;
+}
+
+int cgks_reset_timing(cgks_solver *s) {
+  if (!s) return CGKS_EINVAL;
+  cudaStreamSynchronize(s->stream);
+  collect_timing(s);
+  for (int k = 0; k < KI_COUNT; ++k) { s->t_ms[k] = 0.0; s->t_cnt[k] = 0; }
+  return CGKS_OK;
+}
+
+int64_t cgks_launch_count(const cgks_solver *s) { return s ? s->launches : -1; }
+
+int cgks_launches_per_call(const cgks_solver *s, int cycle) {
+  return s ? static_cast<int>(count_launches(const_cast<cgks_solver *>(s), cycle != 0)) : -1;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+// Device-side gas-kinetic physics of the compact GKS, 2-D (Sections 2.2-2.3
+// and 3 of Ji, Shyy & Xu, arXiv:2109.09965).
+//
+// All routines work in the local face frame (normal n, tangent t = (-ny, nx))
+// on conservative variables (rho, rho*u_n, rho*u_t, rho*E) and their
+// derivatives along n and t.  Moments of the Maxwellian are normalised by
+// rho: <u^a> by the standard recurrence, <xi^2> = K/(2 lambda),
+// <xi^4> = K(K+2)/(4 lambda^2).  The micro-slope solve <a psi> = b uses its
+// closed form.  Templated on the arithmetic type so the same code serves
+// the FP64 path and the FP32 flux of the mixed path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cgks {
+namespace dev {
+
+constexpr int NV = 4;
+
+template <typename T> __device__ __forceinline__ T d_erfc(T x);
+template <> __device__ __forceinline__ double d_erfc<double>(double x) { return erfc(x); }
+template <> __device__ __forceinline__ float d_erfc<float>(float x) { return erfcf(x); }
+template <typename T> __device__ __forceinline__ T d_exp(T x);
+template <> __device__ __forceinline__ double d_exp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float d_exp<float>(float x) { return expf(x); }
+template <typename T> __device__ __forceinline__ T d_sqrt(T x);
+template <> __device__ __forceinline__ double d_sqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float d_sqrt<float>(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ T d_pi();
+template <> __device__ __forceinline__ double d_pi<double>() { return 3.141592653589793238462643; }
+template <> __device__ __forceinline__ float d_pi<float>() { return 3.14159265358979f; }
+
+// Rotate a conservative vector between global and face frames.
+template <typename T>
+__device__ __forceinline__ void rot_in(T nx, T ny, const T g[NV], T l[NV]) {
+  l[0] = g[0];
+  l[1] = g[1] * nx + g[2] * ny;
+  l[2] = -g[1] * ny + g[2] * nx;
+  l[3] = g[3];
+}
+template <typename T>
+__device__ __forceinline__ void rot_out(T nx, T ny, const T l[NV], T g[NV]) {
+  g[0] = l[0];
+  g[1] = l[1] * nx - l[2] * ny;
+  g[2] = l[1] * ny + l[2] * nx;
+  g[3] = l[3];
+}
+
+// Maxwellian parameters (rho, U, V, lambda) of local-frame conservative W.
+template <typename T>
+struct Maxw {
+  T rho, U, V, lam;
+};
+template <typename T>
+__device__ __forceinline__ Maxw<T> maxw(const T W[NV], T K) {
+  Maxw<T> g;
+  g.rho = W[0];
+  T ir = T(1) / W[0];
+  g.U = W[1] * ir;
+  g.V = W[2] * ir;
+  g.lam = (K + T(2)) * g.rho / (T(4) * (W[3] - T(0.5) * g.rho * (g.U * g.U + g.V * g.V)));
+  return g;
+}
+
+// Half-range moments <u^k>, k = 0..KMAX, over u > 0 (sgn = +1) or u < 0 (-1).
+template <typename T, int KMAX>
+__device__ __forceinline__ void half_moments(const Maxw<T> &g, int sgn, T mu[KMAX + 1]) {
+  T sl = d_sqrt(g.lam);
+  T e = d_exp(-g.lam * g.U * g.U) / d_sqrt(d_pi<T>() * g.lam);
+  T i2l = T(0.5) / g.lam;
+  if (sgn > 0) {
+    mu[0] = T(0.5) * d_erfc(-sl * g.U);
+    mu[1] = g.U * mu[0] + T(0.5) * e;
+  } else {
+    mu[0] = T(0.5) * d_erfc(sl * g.U);
+    mu[1] = g.U * mu[0] - T(0.5) * e;
+  }
+#pragma unroll
+  for (int k = 2; k <= KMAX; ++k) mu[k] = g.U * mu[k - 1] + T(k - 1) * i2l * mu[k - 2];
+}
+
+// Full-range moment tables of the equilibrium used by the flux.
+template <typename T>
+struct Mom {
+  T mu[7], mv[7], x2, x4;   // <u^k>, <v^k>, <xi^2>, <xi^4>
+};
+template <typename T>
+__device__ __forceinline__ void full_moments(const Maxw<T> &g, T K, Mom<T> &m) {
+  T i2l = T(0.5) / g.lam;
+  m.mu[0] = T(1); m.mu[1] = g.U;
+  m.mv[0] = T(1); m.mv[1] = g.V;
+#pragma unroll
+  for (int k = 2; k < 7; ++k) {
+    m.mu[k] = g.U * m.mu[k - 1] + T(k - 1) * i2l * m.mu[k - 2];
+    m.mv[k] = g.V * m.mv[k - 1] + T(k - 1) * i2l * m.mv[k - 2];
+  }
+  m.x2 = K * i2l;
+  m.x4 = K * (K + T(2)) * i2l * i2l;
+}
+
+// <u^a v^b xi^(2d) * s>, slope s = s0 + s1 u + s2 v + s3 (u^2+v^2+xi^2)/2
+template <typename T>
+__device__ __forceinline__ T mslope(const Mom<T> &m, int a, int b, int d, const T s[NV]) {
+  const T xd = d == 0 ? T(1) : (d == 1 ? m.x2 : m.x4);
+  const T xd1 = d == 0 ? m.x2 : m.x4;
+  T r = s[0] * m.mu[a] * m.mv[b] * xd + s[1] * m.mu[a + 1] * m.mv[b] * xd + s[2] * m.mu[a] * m.mv[b + 1] * xd;
+  r += T(0.5) * s[3] * (m.mu[a + 2] * m.mv[b] * xd + m.mu[a] * m.mv[b + 2] * xd + m.mu[a] * m.mv[b] * xd1);
+  return r;
+}
+// vector <u^a v^b s psi>
+template <typename T>
+__device__ __forceinline__ void gpsi(const Mom<T> &m, int a, int b, const T s[NV], T out[NV]) {
+  out[0] = mslope(m, a, b, 0, s);
+  out[1] = mslope(m, a + 1, b, 0, s);
+  out[2] = mslope(m, a, b + 1, 0, s);
+  out[3] = T(0.5) * (mslope(m, a + 2, b, 0, s) + mslope(m, a, b + 2, 0, s) + mslope(m, a, b, 1, s));
+}
+
+// Closed-form solution of <s psi> = b (b already divided by rho), 2-D, K
+// internal degrees of freedom.
+template <typename T>
+__device__ __forceinline__ void micro_slope(const Maxw<T> &g, T K, const T b[NV], T s[NV]) {
+  T q = g.U * g.U + g.V * g.V + (K + T(2)) / (T(2) * g.lam);
+  T R4 = T(2) * b[3] - q * b[0];
+  T R3 = b[2] - g.V * b[0];
+  T R2 = b[1] - g.U * b[0];
+  s[3] = T(4) * g.lam * g.lam / (K + T(2)) * (R4 - T(2) * g.U * R2 - T(2) * g.V * R3);
+  s[2] = T(2) * g.lam * R3 - g.V * s[3];
+  s[1] = T(2) * g.lam * R2 - g.U * s[3];
+  s[0] = b[0] - g.U * s[1] - g.V * s[2] - T(0.5) * s[3] * q;
+}
+
+// Smooth gas-kinetic flux at one Gauss point, Eq. (2nd-smooth-flux):
+//   f = g^c - tau (a_n u + a_t v + A) g^c + A g^c t,   tau = mu / p^c
+// with W^c from the half-range moments of g^l (u>0) and g^r (u<0), the
+// equilibrium slopes from the mean of the side derivatives plus, along n,
+// alpha * (W^r - W^l) / delta.  Inputs and outputs in the local frame:
+//   F0 + t F1 = flux, Wc + t Wt = interface state.
+template <typename T>
+__device__ __forceinline__ void gks_point_local(T K, T mu_visc, T alpha, T delta,
+                                                const T Wl[NV], const T Wr[NV],
+                                                const T dnl[NV], const T dtl[NV],
+                                                const T dnr[NV], const T dtr[NV],
+                                                T F0[NV], T F1[NV], T Wc[NV], T Wt[NV]) {
+  Maxw<T> gl = maxw(Wl, K), gr = maxw(Wr, K);
+  T ml[3], mr[3];
+  half_moments<T, 2>(gl, +1, ml);
+  half_moments<T, 2>(gr, -1, mr);
+  T el = gl.V * gl.V + (K + T(1)) / (T(2) * gl.lam);
+  T er = gr.V * gr.V + (K + T(1)) / (T(2) * gr.lam);
+  Wc[0] = gl.rho * ml[0] + gr.rho * mr[0];
+  Wc[1] = gl.rho * ml[1] + gr.rho * mr[1];
+  Wc[2] = gl.rho * ml[0] * gl.V + gr.rho * mr[0] * gr.V;
+  Wc[3] = gl.rho * T(0.5) * (ml[2] + ml[0] * el) + gr.rho * T(0.5) * (mr[2] + mr[0] * er);
+  Maxw<T> gc = maxw(Wc, K);
+  Mom<T> m;
+  full_moments(gc, K, m);
+  T irc = T(1) / gc.rho;
+  T bn[NV], bt[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T dn = T(0.5) * (dnl[v] + dnr[v]);
+    if (delta > T(0)) dn += alpha * (Wr[v] - Wl[v]) / delta;
+    bn[v] = dn * irc;
+    bt[v] = T(0.5) * (dtl[v] + dtr[v]) * irc;
+  }
+  T an[NV], at[NV], A[NV], bA[NV], g1[NV], g2[NV];
+  micro_slope(gc, K, bn, an);
+  micro_slope(gc, K, bt, at);
+  gpsi(m, 1, 0, an, g1);
+  gpsi(m, 0, 1, at, g2);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) bA[v] = -(g1[v] + g2[v]);
+  micro_slope(gc, K, bA, A);
+  T pc = gc.rho / (T(2) * gc.lam);
+  T tau = mu_visc / pc;
+  T gAu[NV], gA[NV], gn2[NV], gtuv[NV];
+  gpsi(m, 1, 0, A, gAu);
+  gpsi(m, 0, 0, A, gA);
+  gpsi(m, 2, 0, an, gn2);
+  gpsi(m, 1, 1, at, gtuv);
+  T feq[NV] = { m.mu[1], m.mu[2], m.mu[1] * gc.V,
+                T(0.5) * (m.mu[3] + m.mu[1] * m.mv[2] + m.mu[1] * m.x2) };
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    F0[v] = gc.rho * (feq[v] - tau * (gn2[v] + gtuv[v] + gAu[v]));
+    F1[v] = gc.rho * gAu[v];
+    Wt[v] = gc.rho * gA[v];
+  }
+}
+
+// First-order KFVS flux of two cell-average states (local frame).
+template <typename T>
+__device__ __forceinline__ void kfvs_local(T K, const T Wl[NV], const T Wr[NV], T F[NV]) {
+  Maxw<T> gl = maxw(Wl, K), gr = maxw(Wr, K);
+  T ml[4], mr[4];
+  half_moments<T, 3>(gl, +1, ml);
+  half_moments<T, 3>(gr, -1, mr);
+  T el = gl.V * gl.V + (K + T(1)) / (T(2) * gl.lam);
+  T er = gr.V * gr.V + (K + T(1)) / (T(2) * gr.lam);
+  F[0] = gl.rho * ml[1] + gr.rho * mr[1];
+  F[1] = gl.rho * ml[2] + gr.rho * mr[2];
+  F[2] = gl.rho * ml[1] * gl.V + gr.rho * mr[1] * gr.V;
+  F[3] = gl.rho * T(0.5) * (ml[3] + ml[1] * el) + gr.rho * T(0.5) * (mr[3] + mr[1] * er);
+}
+
+// Euler normal flux F(U).n, global frame.
+template <typename T>
+__device__ __forceinline__ void euler_flux(T gamma, const T W[NV], T nx, T ny, T F[NV]) {
+  T ir = T(1) / W[0];
+  T u = W[1] * ir, v = W[2] * ir;
+  T p = (gamma - T(1)) * (W[3] - T(0.5) * W[0] * (u * u + v * v));
+  T un = u * nx + v * ny;
+  F[0] = W[0] * un;
+  F[1] = W[1] * un + p * nx;
+  F[2] = W[2] * un + p * ny;
+  F[3] = (W[3] + p) * un;
+}
+
+// ---------------- boundary ghost states (local frame) ----------------
+// Wall velocity (wn, wt) and free stream (rho, un, ut, p) are given in the
+// face frame of the boundary face.
+template <typename T>
+__device__ __forceinline__ void ghost_slip(const T W[NV], const T dn[NV], const T dt[NV],
+                                           T Wg[NV], T dng[NV], T dtg[NV]) {
+  // rho, rho u_t, rho E even across the wall, rho u_n odd
+  Wg[0] = W[0]; Wg[1] = -W[1]; Wg[2] = W[2]; Wg[3] = W[3];
+  dng[0] = -dn[0]; dng[1] = dn[1]; dng[2] = -dn[2]; dng[3] = -dn[3];
+  dtg[0] = dt[0]; dtg[1] = -dt[1]; dtg[2] = dt[2]; dtg[3] = dt[3];
+}
+
+template <typename T>
+__device__ __forceinline__ void ghost_noslip(T gamma, T wn, T wt, const T W[NV], const T dn[NV],
+                                             const T dt[NV], T Wg[NV], T dng[NV], T dtg[NV]) {
+  // rho, p even; u_g = 2 u_w - u  (derivatives: along n kept, along t flipped)
+  T rho = W[0], ir = T(1) / rho;
+  T u = W[1] * ir, v = W[2] * ir;
+  T ke = T(0.5) * (u * u + v * v);
+  T p = (gamma - T(1)) * (W[3] - rho * ke);
+  T ug = T(2) * wn - u, vg = T(2) * wt - v;
+  T keg = T(0.5) * (ug * ug + vg * vg);
+  Wg[0] = rho; Wg[1] = rho * ug; Wg[2] = rho * vg; Wg[3] = p / (gamma - T(1)) + rho * keg;
+  const T *D[2] = { dn, dt };
+  T *G[2] = { dng, dtg };
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    T dr = D[b][0];
+    T du = (D[b][1] - u * dr) * ir, dv = (D[b][2] - v * dr) * ir;
+    T dp = (gamma - T(1)) * (D[b][3] - ke * dr - rho * (u * du + v * dv));
+    T s = b == 0 ? T(-1) : T(1);   // scalars: normal derivative flips
+    T drg = s * dr, dpg = s * dp;
+    T dug = -s * du, dvg = -s * dv;  // velocity: tangential derivative flips
+    G[b][0] = drg;
+    G[b][1] = ug * drg + rho * dug;
+    G[b][2] = vg * drg + rho * dvg;
+    G[b][3] = dpg / (gamma - T(1)) + keg * drg + rho * (ug * dug + vg * dvg);
+  }
+}
+
+// 1-D Riemann invariants normal to the face between the interior state W
+// and the free stream (rho_e, une, ute, pe); local frame.
+template <typename T>
+__device__ __forceinline__ void ghost_farfield(T gamma, T re, T une, T ute, T pe, const T W[NV], T Wg[NV]) {
+  T ri = W[0], ir = T(1) / ri;
+  T uni = W[1] * ir, uti = W[2] * ir;
+  T pi = (gamma - T(1)) * (W[3] - T(0.5) * ri * (uni * uni + uti * uti));
+  T ci = d_sqrt(gamma * pi / ri), ce = d_sqrt(gamma * pe / re);
+  T rb, unb, utb, pb;
+  if (uni <= -ci) {
+    rb = re; unb = une; utb = ute; pb = pe;
+  } else if (uni >= ci) {
+    rb = ri; unb = uni; utb = uti; pb = pi;
+  } else {
+    T Rp = uni + T(2) * ci / (gamma - T(1));
+    T Rm = une - T(2) * ce / (gamma - T(1));
+    unb = T(0.5) * (Rp + Rm);
+    T cb = T(0.25) * (gamma - T(1)) * (Rp - Rm);
+    T s;
+    if (unb >= T(0)) { s = pi / pow(ri, gamma); utb = uti; }
+    else { s = pe / pow(re, gamma); utb = ute; }
+    rb = pow(cb * cb / (gamma * s), T(1) / (gamma - T(1)));
+    pb = rb * cb * cb / gamma;
+  }
+  Wg[0] = rb; Wg[1] = rb * unb; Wg[2] = rb * utb;
+  Wg[3] = pb / (gamma - T(1)) + T(0.5) * rb * (unb * unb + utb * utb);
+}
+
+}  // namespace dev
+}  // namespace cgks

@@ -1,0 +1,95 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point
+declared in include/cgks.h, builds meshes on the host, reproduces the
+oracle's sweep order bit for bit, rejects bad meshes, and refuses to run
+without a GPU instead of falling back to the CPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2109_09965_gb300 import meshgen as MG
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cg():
+    from paper_2109_09965_gb300 import cgks
+    cgks.lib()
+    return cgks
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cgks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cgks_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(cg):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = C.CDLL(cg.lib_path())
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(cg.SIGNATURES), set(names) ^ set(cg.SIGNATURES)
+
+
+@pytest.mark.parametrize("mesh", [MG.cavity(8), MG.cylinder(24, 3, 5),
+                                  MG.box(7, 5, jitter=0.2, seed=2, cells="mixed",
+                                         quad_mask=lambda i, j: (i + j) % 3 == 0)],
+                         ids=["cavity", "cylinder", "mixed"])
+def test_host_mesh_and_ordering_match_oracle(cg, oracle_lib, mesh):
+    gm = cg.Mesh(mesh)
+    om = oracle_lib.OracleMesh(mesh)
+    assert gm.n_faces == om.n_faces
+    assert gm.n_colours == om.n_colours
+    rcm, col = gm.ordering()
+    orcm, ocol = om.ordering()
+    np.testing.assert_array_equal(rcm, orcm)
+    np.testing.assert_array_equal(col, ocol)
+    assert gm.device_bytes > 0
+
+
+def test_bad_meshes_are_rejected(cg):
+    m = MG.box(3, 3)
+    # clockwise cell
+    bad = MG.box(3, 3)
+    nodes = bad.cell_nodes.copy()
+    a, b = bad.cell_ptr[0], bad.cell_ptr[1]
+    nodes[a:b] = nodes[a:b][::-1]
+    bad.cell_nodes = nodes
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(bad)
+    assert e.value.status == -3
+    # boundary edge without a tag
+    bad2 = MG.box(3, 3)
+    bad2.bface_ptr = bad2.bface_ptr[:-1]
+    bad2.bface_tag = bad2.bface_tag[:-1]
+    bad2.bface_nodes = bad2.bface_nodes[:-2]
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(bad2)
+    assert e.value.status == -3
+    # three-dimensional input is not implemented
+    m3 = MG.box(2, 2)
+    m3.dim = 3
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(m3)
+    assert e.value.status == -1
+
+
+def test_no_cpu_fallback_without_gpu(cg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    gm = cg.Mesh(MG.cavity(4))
+    with pytest.raises(cg.CgksError) as e:
+        cg.Solver(gm, dict(bcs=[dict(kind="noslip"), dict(kind="noslip")]), use_torch=False)
+    assert e.value.status == -4
+
+
+def test_default_params(cg):
+    P = cg.make_params({})
+    assert P.gamma == 1.4 and P.cfl_lo == 1000.0 and P.n_implicit == 6 and P.n_sweeps == 2
+    assert abs(P.alpha - 4.0 / 3.0) < 1e-15 and P.use_graph == 1
