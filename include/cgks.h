@@ -193,6 +193,31 @@ int cgks_reset_timing(cgks_solver *s);
 int64_t cgks_launch_count(const cgks_solver *s);
 int cgks_launches_per_call(const cgks_solver *s, int cycle);
 
+/* ---- allocation-free residual (the paper has no counterpart) ----
+ * Some callers cannot allocate device memory when they call into the
+ * library: serving processes that fix their device memory at start-up and
+ * keep cudaMalloc off the request path (it can block, synchronise the
+ * device or fail under the budget), and host frameworks that own all device
+ * memory and forbid libraries from allocating.  This entry point computes
+ * the density residual Res = sum|rho_new - rho_old| / sum rho_old (the
+ * monitor of Section 4) of two device states without allocating anything.
+ *   W_new_dev, W_old_dev  device arrays [n_cells*4], the ABI state layout
+ *                         (only component 0, rho, is read)
+ *   n_cells               1 .. 1,048,576; larger returns CGKS_EINVAL
+ *   res_dev               device pointer receiving one double
+ *   stream                cudaStream_t the two kernels run on (NULL = default)
+ * Its scratch is a fixed 64 KiB __device__ array inside libcgks that every
+ * GPU loading the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's partial sums; every call overwrites the slots it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU (different streams,
+ * or different host threads) race on it and must be serialised by the
+ * caller.  Returns CGKS_OK, CGKS_EINVAL or CGKS_ECUDA. */
+int cgks_density_residual_noalloc(const double *W_new_dev, const double *W_old_dev, int64_t n_cells,
+                                  double *res_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ SIGNATURES = {
     "cgks_reset_timing": (C.c_int, [C.c_void_p]),
     "cgks_launch_count": (C.c_int64, [C.c_void_p]),
     "cgks_launches_per_call": (C.c_int, [C.c_void_p, C.c_int]),
+    "cgks_density_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 
