@@ -35,6 +35,7 @@ constexpr int kBadState = 1;
 
 struct DevParams {
   double gamma, K, mu, alpha, cfl_hi, cfl_lo;
+  D::KC<double> kc;
   int n_bc;
   int bc_kind[CGKS_MAX_BC];
   double bc_uw[CGKS_MAX_BC][2];
@@ -43,11 +44,11 @@ struct DevParams {
 
 struct DevMesh {
   int nc, nf;
-  const double *vol, *per, *h, *m2;          // m2: [3][nc]
+  const double *vol, *ivol, *per, *ih, *m2;  // ih = 1/h; m2: [3][nc]
   const int *cface, *cnbr;                   // [4][nc]
   const double *op;                          // [kNCol*kNM][nc]
   const int *fc0, *fc1;
-  const double *fn, *fS, *fdelta, *fxi;      // fn [2][nf], fxi [8][nf]
+  const double *fn, *fS, *fjump, *fxi;       // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
 };
 
 struct Scalars {
@@ -189,7 +190,7 @@ __device__ __forceinline__ void recon_point(const DevMesh &m, const double *__re
                                             const double *__restrict__ coef, int i, double x, double y,
                                             double val[4], double gx[4], double gy[4]) {
   const int n = m.nc;
-  double ih = 1.0 / m.h[i];
+  double ih = m.ih[i];
   double p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
   for (int v = 0; v < 4; ++v) {
     double c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, con
   if (f >= m.nf) return;
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const double nx = m.fn[f], ny = m.fn[nf + f], delta = m.fdelta[f];
+  const double nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
   double acc[4][4];
   for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = 0.0;
   double wff[4];
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, con
       D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
     }
     double F0[4], F1[4], Wc[4], Wt[4];
-    D::gks_point_local(P.K, P.mu, P.alpha, delta, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
+    D::gks_point_local(P.kc, P.mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
     double g[4];
     D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += 0.5 * g[v];
     D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += 0.5 * g[v];
@@ -345,14 +346,6 @@ __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Sca
 }
 
 // ---------------------------- low-order level ----------------------------
-__device__ __forceinline__ double lambda_side(const DevParams &P, const double w[4], double nx, double ny,
-                                              double S, double vol) {
-  double rho = w[0], u = w[1] / rho, v = w[2] / rho;
-  double p = (P.gamma - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
-  double c = sqrt(P.gamma * p / rho);
-  return fabs(u * nx + v * ny) + c + 2.0 * (P.mu / rho) * S / vol;
-}
-
 // ghost of a cell-mean state (zero gradients)
 __device__ __forceinline__ void lo_ghost(const DevParams &P, int tag, double nx, double ny, const double w[4],
                                          double wg[4]) {
@@ -373,41 +366,87 @@ __device__ __forceinline__ void lo_ghost(const DevParams &P, int tag, double nx,
   D::rot_out(nx, ny, wgl, wg);
 }
 
-// K5: first-order KFVS flux and spectral radius per face.
+// K5a: per-cell start of an implicit step: U = W_p0 (first step) or
+// U += dU (Algorithm 1's update), then the primitives of U.
+__global__ void __launch_bounds__(kCellBlock) k_lo_cell(DevMesh m, DevParams P, int first,
+                                                        const double *__restrict__ Wp0, double *__restrict__ U,
+                                                        const double *__restrict__ dU, double *__restrict__ prim) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc;
+  double w[4];
+  for (int v = 0; v < 4; ++v) {
+    w[v] = first ? Wp0[v * n + i] : U[v * n + i] + dU[v * n + i];
+    U[v * n + i] = w[v];
+  }
+  D::Prim<double> q = D::prim_of(w, P.gamma, P.kc);
+  prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.p;
+  prim[4 * n + i] = q.i2l; prim[5 * n + i] = q.sl; prim[6 * n + i] = q.isp; prim[7 * n + i] = q.c;
+  prim[8 * n + i] = q.ir;
+}
+
+__device__ __forceinline__ D::Prim<double> load_prim(const double *__restrict__ prim, int n, int i) {
+  D::Prim<double> q;
+  q.rho = prim[0 * n + i]; q.u = prim[1 * n + i]; q.v = prim[2 * n + i]; q.p = prim[3 * n + i];
+  q.i2l = prim[4 * n + i]; q.sl = prim[5 * n + i]; q.isp = prim[6 * n + i]; q.c = prim[7 * n + i];
+  q.ir = prim[8 * n + i];
+  return q;
+}
+
+// K5b: first-order KFVS flux, spectral radius lambda_p = max of both sides,
+// and the Euler normal fluxes F_n(U_c0), F_n(U_c1) the relaxation reuses.
 __global__ void __launch_bounds__(kCellBlock) k_lo_face(DevMesh m, DevParams P, const double *__restrict__ U,
-                                                        double *__restrict__ Flo, double *__restrict__ lam) {
+                                                        const double *__restrict__ prim, double *__restrict__ Flo,
+                                                        double *__restrict__ lam, double *__restrict__ E0,
+                                                        double *__restrict__ E1) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
   const int n = m.nc, nf = m.nf;
-  int c0 = m.fc0[f], c1 = m.fc1[f];
-  double nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
-  double w0[4], w1[4];
-  for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
-  double vol1;
+  const int c0 = m.fc0[f], c1 = m.fc1[f];
+  const double nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
+  D::Prim<double> a = load_prim(prim, n, c0), b;
+  double ivb;
   if (c1 >= 0) {
-    for (int v = 0; v < 4; ++v) w1[v] = U[v * n + c1];
-    vol1 = m.vol[c1];
+    b = load_prim(prim, n, c1);
+    ivb = m.ivol[c1];
   } else {
-    lo_ghost(P, -1 - c1, nx, ny, w0, w1);
-    vol1 = m.vol[c0];
+    double w0[4], wg[4];
+    for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
+    lo_ghost(P, -1 - c1, nx, ny, w0, wg);
+    b = D::prim_of(wg, P.gamma, P.kc);
+    ivb = m.ivol[c0];
   }
-  double l0[4], l1[4], F[4], g[4];
-  D::rot_in(nx, ny, w0, l0);
-  D::rot_in(nx, ny, w1, l1);
-  D::kfvs_local(P.K, l0, l1, F);
-  D::rot_out(nx, ny, F, g);
-  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = g[v];
-  double la = lambda_side(P, w0, nx, ny, S, m.vol[c0]);
-  double lb = lambda_side(P, w1, nx, ny, S, vol1);
+  const double una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
+  const double unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
+  double Fl[4], F[4];
+  D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
+  D::rot_out(nx, ny, Fl, F);
+  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
+  const double la = fabs(una) + a.c + 2.0 * (P.mu * a.ir) * S * m.ivol[c0];
+  const double lb = fabs(unb) + b.c + 2.0 * (P.mu * b.ir) * S * ivb;
   lam[f] = la > lb ? la : lb;
+  // Euler normal flux of the cell means (interior faces: both sides)
+  E0[0 * nf + f] = a.rho * una;
+  E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
+  E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
+  E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
+  if (c1 >= 0) {
+    E1[0 * nf + f] = b.rho * unb;
+    E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
+    E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
+    E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
+  }
 }
 
-// K6: low-order right-hand side R^k = R_lo(U^k) + S and diagonal D_i.
+// K6: low-order right-hand side R^k = R_lo(U^k) + S, 1/D_i, and the first
+// colour pass of the relaxation: with dU = 0 everywhere the update of a
+// colour-0 cell reduces to dU_i = R_i / D_i; all other cells start at 0.
 // first: also forms the forcing S = R_p0 - R_lo(W_p0) (Section 3, step 3).
-__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, int first,
+__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, int first, int colour0_end,
                                                        const double *__restrict__ Flo, const double *__restrict__ lam,
                                                        const double *__restrict__ Rp0, double *__restrict__ Src,
-                                                       double *__restrict__ Rk, double *__restrict__ Dg) {
+                                                       double *__restrict__ Rk, double *__restrict__ invD,
+                                                       double *__restrict__ dU) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
   const int n = m.nc, nf = m.nf;
@@ -421,22 +460,27 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, i
     for (int v = 0; v < 4; ++v) R[v] -= sg * S * Flo[v * nf + f];
     sum += lam[f] * S;
   }
+  // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2
+  const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
+  invD[i] = id;
   for (int v = 0; v < 4; ++v) {
     double src;
     if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
     else src = Src[v * n + i];
-    Rk[v * n + i] = R[v] + src;
+    double r = R[v] + src;
+    Rk[v * n + i] = r;
+    dU[v * n + i] = i < colour0_end ? r * id : 0.0;
   }
-  double dti = P.cfl_lo * m.vol[i] / sum;
-  Dg[i] = m.vol[i] / dti + 0.5 * sum;
 }
 
 // K7: point relaxation of the cells of one colour, Eq. (implicit-local):
 //   dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
-//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
+//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero;
+// F_n(U_ip) comes from the face cache of this implicit step.
 __global__ void __launch_bounds__(kCellBlock) k_sweep(DevMesh m, DevParams P, int begin, int end,
                                                       const double *__restrict__ U, const double *__restrict__ Rk,
-                                                      const double *__restrict__ Dg, const double *__restrict__ lam,
+                                                      const double *__restrict__ invD, const double *__restrict__ lam,
+                                                      const double *__restrict__ E0, const double *__restrict__ E1,
                                                       double *__restrict__ dU) {
   int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
@@ -447,27 +491,21 @@ __global__ void __launch_bounds__(kCellBlock) k_sweep(DevMesh m, DevParams P, in
     int j = m.cnbr[s * n + i];
     if (j < 0) continue;
     int fs = m.cface[s * n + i];
-    int f = fs >= 0 ? fs : ~fs;
-    double sg = fs >= 0 ? 1.0 : -1.0;
-    double nx = sg * m.fn[f], ny = sg * m.fn[nf + f], S = m.fS[f], lp = lam[f];
+    bool is0 = fs >= 0;
+    int f = is0 ? fs : ~fs;
+    double sg = is0 ? 1.0 : -1.0;
+    double nx = sg * m.fn[f], ny = sg * m.fn[nf + f], hS = 0.5 * m.fS[f], lp = lam[f];
     double uj[4], up[4], fa[4], fb[4];
-    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; up[v] = uj[v] + dU[v * n + j]; }
-    D::euler_flux(P.gamma, up, nx, ny, fa);
-    D::euler_flux(P.gamma, uj, nx, ny, fb);
     for (int v = 0; v < 4; ++v) {
-      double ma = 0.5 * (fa[v] - lp * up[v]);
-      double mb = 0.5 * (fb[v] - lp * uj[v]);
-      acc[v] -= S * (ma - mb);
+      uj[v] = U[v * n + j];
+      up[v] = uj[v] + dU[v * n + j];
+      fb[v] = is0 ? E1[v * nf + f] : -E0[v * nf + f];
     }
+    D::euler_flux(P.gamma, up, nx, ny, fa);
+    for (int v = 0; v < 4; ++v) acc[v] -= hS * ((fa[v] - fb[v]) - lp * (up[v] - uj[v]));
   }
-  double id = Dg[i];
-  for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] / id;
-}
-
-// K8: U += dU
-__global__ void k_axpy(int n4, double *__restrict__ U, const double *__restrict__ dU) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n4) U[i] += dU[i];
+  const double id = invD[i];
+  for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] * id;
 }
 
 // K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
@@ -512,10 +550,10 @@ __global__ void k_scatter_state(int n, const int *__restrict__ perm, const doubl
 }
 
 // kernel ids for the per-kernel timers
-enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_AXPY,
+enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_LOCELL,
                 KI_PROLONG, KI_COUNT };
 const char *kKernelNames[KI_COUNT] = { "k_dt", "k_recon", "k_face", "k_update", "k_res_final", "k_lo_face",
-                                       "k_lo_rhs", "k_sweep", "k_axpy", "k_prolong" };
+                                       "k_lo_rhs", "k_sweep", "k_lo_cell", "k_prolong" };
 
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
@@ -535,8 +573,10 @@ struct cgks_solver {
   // state and work arrays (device)
   double *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr;
   double *coef = nullptr, *FA = nullptr, *FB = nullptr;
-  double *U = nullptr, *dU = nullptr, *Rp0 = nullptr, *Src = nullptr, *Rk = nullptr, *Dg = nullptr;
-  double *Flo = nullptr, *lam = nullptr, *partial = nullptr, *last = nullptr;
+  double *U = nullptr, *dU = nullptr, *Rp0 = nullptr, *Src = nullptr, *Rk = nullptr, *invD = nullptr;
+  double *Flo = nullptr, *lam = nullptr, *E0 = nullptr, *E1 = nullptr, *prim = nullptr;
+  double *partial = nullptr, *last = nullptr;
+  std::vector<int> sweep_colours;   // colour sequence of the relaxation after the first pass
   double *hist = nullptr;
   int hist_cap = 0;
   double *stage_aos = nullptr;  // [12 n] staging for set/get state
@@ -624,28 +664,32 @@ void enqueue_hi_step(cgks_solver *s, double *Wout, bool want_res) {
            s->hist_cap, s->last);
 }
 
-// low-order solve from U = W_p0 (= s->Wn), R_p0 in s->Rp0; result in s->U
+// low-order solve from U = W_p0 (= s->Wn), R_p0 in s->Rp0; result in s->U.
+// Per implicit step: cell primitives (and U += dU), KFVS faces, right-hand
+// side with the first colour pass, then the remaining colour passes.
 void enqueue_lo_solve(cgks_solver *s) {
   const int n = s->dm.nc, nf = s->dm.nf;
-  cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream);
+  const int c0_end = s->params.n_sweeps > 0 ? s->hm.colour_start[1] : 0;
   for (int k = 0; k < s->params.n_implicit; ++k) {
+    launch(s, KI_LOCELL, k_lo_cell, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0,
+           (const double *)s->Wn, s->U, (const double *)s->dU, s->prim);
     launch(s, KI_LOFACE, k_lo_face, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, (const double *)s->U,
-           s->Flo, s->lam);
-    launch(s, KI_LORHS, k_lo_rhs, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0,
-           (const double *)s->Flo, (const double *)s->lam, (const double *)s->Rp0, s->Src, s->Rk, s->Dg);
-    cudaMemsetAsync(s->dU, 0, sizeof(double) * 4 * n, s->stream);
-    for (int sw = 0; sw < s->params.n_sweeps; ++sw) {
-      for (int dir = 0; dir < 2; ++dir) {
-        for (int q = 0; q < s->hm.n_colours; ++q) {
-          int c = dir == 0 ? q : s->hm.n_colours - 1 - q;
-          int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
-          launch(s, KI_SWEEP, k_sweep, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, b, e,
-                 (const double *)s->U, (const double *)s->Rk, (const double *)s->Dg, (const double *)s->lam, s->dU);
-        }
-      }
+           (const double *)s->prim, s->Flo, s->lam, s->E0, s->E1);
+    launch(s, KI_LORHS, k_lo_rhs, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0, c0_end,
+           (const double *)s->Flo, (const double *)s->lam, (const double *)s->Rp0, s->Src, s->Rk, s->invD, s->dU);
+    for (int c : s->sweep_colours) {
+      int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
+      launch(s, KI_SWEEP, k_sweep, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, b, e,
+             (const double *)s->U, (const double *)s->Rk, (const double *)s->invD, (const double *)s->lam,
+             (const double *)s->E0, (const double *)s->E1, s->dU);
     }
-    launch(s, KI_AXPY, k_axpy, dim3(nblk(4 * n, kCellBlock)), dim3(kCellBlock), 4 * n, s->U, (const double *)s->dU);
   }
+  // U^{n_implicit} = U + dU of the last step
+  if (s->params.n_implicit > 0)
+    launch(s, KI_LOCELL, k_lo_cell, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, 0, (const double *)s->Wn,
+           s->U, (const double *)s->dU, s->prim);
+  else
+    cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream);
 }
 
 void enqueue_cycle(cgks_solver *s) {
@@ -719,7 +763,8 @@ long long count_launches(cgks_solver *s, bool cycle) {
   long long hi = 1 + per_eval + 1 + (s->params.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
   long long dt = 2;
   if (!cycle) return dt + hi + 1;
-  long long lo = s->params.n_implicit * (3 + 2LL * s->params.n_sweeps * s->hm.n_colours);
+  long long lo = s->params.n_implicit * (3 + static_cast<long long>(s->sweep_colours.size())) +
+                 (s->params.n_implicit > 0 ? 1 : 0);
   return dt + hi + per_eval + 1 + lo + 2;
 }
 
@@ -799,9 +844,9 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
 }
 
 static size_t solver_bytes(int64_t nc, int64_t nf) {
-  size_t cells = 4 + 8 + 4 + 4 + 8 + 20 + 4 * 6 + 1;      // state + work
-  size_t geo_c = 3 + 3 + kNCol * kNM;                      // vol, per, h, m2, op
-  size_t faces = 16 * 2 + 4 + 1 + 2 + 1 + 1 + 8;           // FA, FB, Flo, lam, fn, fS, fdelta, fxi
+  size_t cells = 4 + 8 + 4 + 4 + 8 + 20 + 4 * 6 + 1 + 9;  // state + work + primitives
+  size_t geo_c = 4 + 3 + kNCol * kNM;                      // vol, 1/vol, per, 1/h, m2, op
+  size_t faces = 16 * 2 + 4 + 1 + 8 + 2 + 1 + 1 + 8;       // FA, FB, Flo, lam, E0/E1, fn, fS, fjump, fxi
   size_t ints = 8 * nc + 2 * nf + nc;                      // cface, cnbr, fc0/fc1, perm
   return sizeof(double) * ((cells + geo_c + 12) * nc + faces * nf + 2 * kMaxBlocksReduce + 16) + sizeof(int) * ints +
          64 * 256 + sizeof(Scalars);
@@ -876,6 +921,9 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   DevParams &dp = s->dp;
   dp.gamma = p->gamma;
   dp.K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
+  dp.kc.K = dp.K;
+  dp.kc.c2K = 2.0 / (dp.K + 2.0);
+  dp.kc.c4K = 4.0 / (dp.K + 2.0);
   dp.mu = p->mu;
   dp.alpha = p->alpha;
   dp.cfl_hi = p->cfl_hi;
@@ -904,15 +952,16 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   std::vector<Piece> pieces;
   auto D8 = [&](double **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(double) * cnt }); };
   auto I4 = [&](int **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(int) * cnt }); };
-  double *vol, *per, *h, *m2, *opd, *fn, *fS, *fdelta, *fxi;
+  double *vol, *ivol, *per, *ih, *m2, *opd, *fn, *fS, *fjump, *fxi;
   int *cface, *cnbr, *fc0, *fc1;
   D8(&s->W, 4 * nc); D8(&s->Wx, 8 * nc); D8(&s->Wn, 4 * nc); D8(&s->Ws, 4 * nc); D8(&s->Wxs, 8 * nc);
   D8(&s->coef, 20 * nc); D8(&s->FA, 16 * nf); D8(&s->FB, 16 * nf);
   D8(&s->U, 4 * nc); D8(&s->dU, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc); D8(&s->Rk, 4 * nc);
-  D8(&s->Dg, nc); D8(&s->Flo, 4 * nf); D8(&s->lam, nf);
+  D8(&s->invD, nc); D8(&s->Flo, 4 * nf); D8(&s->lam, nf); D8(&s->E0, 4 * nf); D8(&s->E1, 4 * nf);
+  D8(&s->prim, D::NPRIM * nc);
   D8(&s->partial, 2 * std::max(s->nblk_cell, 1)); D8(&s->last, 4); D8(&s->stage_aos, 12 * nc);
-  D8(&vol, nc); D8(&per, nc); D8(&h, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
-  D8(&fn, 2 * nf); D8(&fS, nf); D8(&fdelta, nf); D8(&fxi, 8 * nf);
+  D8(&vol, nc); D8(&ivol, nc); D8(&per, nc); D8(&ih, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
+  D8(&fn, 2 * nf); D8(&fS, nf); D8(&fjump, nf); D8(&fxi, 8 * nf);
   I4(&cface, kMaxFace * nc); I4(&cnbr, kMaxFace * nc); I4(&fc0, nf); I4(&fc1, nf); I4(&s->perm, nc);
   pieces.push_back({ reinterpret_cast<void **>(&s->sc), sizeof(Scalars) });
   size_t total = 0;
@@ -928,21 +977,41 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
   };
   const HostMesh &hm = s->hm;
-  bool ok = up(vol, hm.vol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) && up(h, hm.h.data(), 8 * nc) &&
+  // derived per-solver arrays: reciprocals and the jump coefficient alpha/delta
+  std::vector<double> h_ivol(nc), h_ih(nc), h_jump(nf);
+  for (int64_t i = 0; i < nc; ++i) { h_ivol[i] = 1.0 / hm.vol[i]; h_ih[i] = 1.0 / hm.h[i]; }
+  for (int64_t f = 0; f < nf; ++f) h_jump[f] = hm.fdelta[f] > 0.0 ? p->alpha / hm.fdelta[f] : 0.0;
+  bool ok = up(vol, hm.vol.data(), 8 * nc) && up(ivol, h_ivol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) &&
+            up(ih, h_ih.data(), 8 * nc) &&
             up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) && up(fn, hm.fn.data(), 8 * 2 * nf) &&
-            up(fS, hm.fS.data(), 8 * nf) && up(fdelta, hm.fdelta.data(), 8 * nf) && up(fxi, hm.fxi.data(), 8 * 8 * nf) &&
+            up(fS, hm.fS.data(), 8 * nf) && up(fjump, h_jump.data(), 8 * nf) && up(fxi, hm.fxi.data(), 8 * 8 * nf) &&
             up(cface, hm.cface.data(), 4 * kMaxFace * nc) && up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) &&
             up(fc0, hm.fc0.data(), 4 * nf) && up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc);
   if (!ok) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->W, 0, sizeof(double) * 12 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->Rp0, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (cudaMemsetAsync(s->dU, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   DevMesh &dm = s->dm;
   dm.nc = static_cast<int>(nc); dm.nf = static_cast<int>(nf);
-  dm.vol = vol; dm.per = per; dm.h = h; dm.m2 = m2; dm.op = opd;
+  dm.vol = vol; dm.ivol = ivol; dm.per = per; dm.ih = ih; dm.m2 = m2; dm.op = opd;
   dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
-  dm.fn = fn; dm.fS = fS; dm.fdelta = fdelta; dm.fxi = fxi;
+  dm.fn = fn; dm.fS = fS; dm.fjump = fjump; dm.fxi = fxi;
+  // Colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
+  // C-1..0).  A colour repeated back to back recomputes identical values
+  // (its cells read only other colours), and the first pass is done by
+  // k_lo_rhs, so both are dropped.
+  {
+    std::vector<int> seq;
+    const int C = s->hm.n_colours;
+    for (int sw = 0; sw < p->n_sweeps; ++sw) {
+      for (int c = 0; c < C; ++c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+      for (int c = C - 1; c >= 0; --c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+    }
+    if (!seq.empty()) seq.erase(seq.begin());
+    s->sweep_colours = seq;
+  }
   if (ensure_hist(s, 1024) != CGKS_OK) return fail(CGKS_ENOMEM);
   *out = s;
   return CGKS_OK;

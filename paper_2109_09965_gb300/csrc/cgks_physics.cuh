@@ -46,37 +46,54 @@ __device__ __forceinline__ void rot_out(T nx, T ny, const T l[NV], T g[NV]) {
   g[3] = l[3];
 }
 
-// Maxwellian parameters (rho, U, V, lambda) of local-frame conservative W.
+// Constants of the kinetic model with K internal degrees of freedom,
+// computed once on the host: c2K = 2/(K+2), c4K = 4/(K+2).
+template <typename T>
+struct KC {
+  T K, c2K, c4K;
+};
+constexpr double kInvSqrtPi = 0.56418958354775628694807945156;
+
+// Maxwellian of local-frame conservative W: rho, 1/rho, U, V, lambda and
+// 1/(2 lambda).  Two divisions; everything downstream multiplies.
 template <typename T>
 struct Maxw {
-  T rho, U, V, lam;
+  T rho, ir, U, V, lam, i2l;
 };
 template <typename T>
-__device__ __forceinline__ Maxw<T> maxw(const T W[NV], T K) {
+__device__ __forceinline__ Maxw<T> maxw(const T W[NV], T c2K) {
+  // lambda = (K+2) rho / (4 (rho E - rho |U|^2 / 2)),  c2K = 2 / (K+2)
   Maxw<T> g;
   g.rho = W[0];
-  T ir = T(1) / W[0];
-  g.U = W[1] * ir;
-  g.V = W[2] * ir;
-  g.lam = (K + T(2)) * g.rho / (T(4) * (W[3] - T(0.5) * g.rho * (g.U * g.U + g.V * g.V)));
+  g.ir = T(1) / W[0];
+  g.U = W[1] * g.ir;
+  g.V = W[2] * g.ir;
+  T eps = W[3] - T(0.5) * g.rho * (g.U * g.U + g.V * g.V);
+  g.i2l = c2K * eps * g.ir;
+  g.lam = T(0.5) / g.i2l;
   return g;
 }
 
-// Half-range moments <u^k>, k = 0..KMAX, over u > 0 (sgn = +1) or u < 0 (-1).
+template <typename T> __device__ __forceinline__ T d_rsqrt(T x);
+template <> __device__ __forceinline__ double d_rsqrt<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float d_rsqrt<float>(float x) { return rsqrtf(x); }
+
+// Half-range moments <u^k>, k = 0..KMAX, over u > 0 (sgn = +1) or u < 0
+// (-1), of the Maxwellian with mean U, 1/(2 lambda) = i2l, sqrt(lambda) = sl
+// and 1/sqrt(pi lambda) = isp.
 template <typename T, int KMAX>
-__device__ __forceinline__ void half_moments(const Maxw<T> &g, int sgn, T mu[KMAX + 1]) {
-  T sl = d_sqrt(g.lam);
-  T e = d_exp(-g.lam * g.U * g.U) / d_sqrt(d_pi<T>() * g.lam);
-  T i2l = T(0.5) / g.lam;
+__device__ __forceinline__ void half_moments(T U, T i2l, T sl, T isp, int sgn, T mu[KMAX + 1]) {
+  T z = sl * U;
+  T e = d_exp(-z * z) * isp;
   if (sgn > 0) {
-    mu[0] = T(0.5) * d_erfc(-sl * g.U);
-    mu[1] = g.U * mu[0] + T(0.5) * e;
+    mu[0] = T(0.5) * d_erfc(-z);
+    mu[1] = U * mu[0] + T(0.5) * e;
   } else {
-    mu[0] = T(0.5) * d_erfc(sl * g.U);
-    mu[1] = g.U * mu[0] - T(0.5) * e;
+    mu[0] = T(0.5) * d_erfc(z);
+    mu[1] = U * mu[0] - T(0.5) * e;
   }
 #pragma unroll
-  for (int k = 2; k <= KMAX; ++k) mu[k] = g.U * mu[k - 1] + T(k - 1) * i2l * mu[k - 2];
+  for (int k = 2; k <= KMAX; ++k) mu[k] = U * mu[k - 1] + T(k - 1) * i2l * mu[k - 2];
 }
 
 // Full-range moment tables of the equilibrium used by the flux.
@@ -86,7 +103,7 @@ struct Mom {
 };
 template <typename T>
 __device__ __forceinline__ void full_moments(const Maxw<T> &g, T K, Mom<T> &m) {
-  T i2l = T(0.5) / g.lam;
+  const T i2l = g.i2l;
   m.mu[0] = T(1); m.mu[1] = g.U;
   m.mv[0] = T(1); m.mv[1] = g.V;
 #pragma unroll
@@ -116,64 +133,76 @@ __device__ __forceinline__ void gpsi(const Mom<T> &m, int a, int b, const T s[NV
   out[3] = T(0.5) * (mslope(m, a + 2, b, 0, s) + mslope(m, a, b + 2, 0, s) + mslope(m, a, b, 1, s));
 }
 
-// Closed-form solution of <s psi> = b (b already divided by rho), 2-D, K
-// internal degrees of freedom.
+// Closed-form solution of <s psi> = b (b already divided by rho), 2-D,
+// K internal degrees of freedom.  q = U^2 + V^2 + (K+2)/(2 lambda),
+// tl = 2 lambda, l2 = 4 lambda^2 / (K+2): shared by the three solves.
 template <typename T>
-__device__ __forceinline__ void micro_slope(const Maxw<T> &g, T K, const T b[NV], T s[NV]) {
-  T q = g.U * g.U + g.V * g.V + (K + T(2)) / (T(2) * g.lam);
-  T R4 = T(2) * b[3] - q * b[0];
-  T R3 = b[2] - g.V * b[0];
-  T R2 = b[1] - g.U * b[0];
-  s[3] = T(4) * g.lam * g.lam / (K + T(2)) * (R4 - T(2) * g.U * R2 - T(2) * g.V * R3);
-  s[2] = T(2) * g.lam * R3 - g.V * s[3];
-  s[1] = T(2) * g.lam * R2 - g.U * s[3];
-  s[0] = b[0] - g.U * s[1] - g.V * s[2] - T(0.5) * s[3] * q;
+struct SlopeSolver {
+  T U, V, q, tl, l2;
+};
+template <typename T>
+__device__ __forceinline__ SlopeSolver<T> slope_solver(const Maxw<T> &g, const KC<T> &kc) {
+  SlopeSolver<T> S;
+  S.U = g.U; S.V = g.V;
+  S.q = g.U * g.U + g.V * g.V + (kc.K + T(2)) * g.i2l;
+  S.tl = T(2) * g.lam;
+  S.l2 = kc.c4K * g.lam * g.lam;
+  return S;
+}
+template <typename T>
+__device__ __forceinline__ void micro_slope(const SlopeSolver<T> &S, const T b[NV], T s[NV]) {
+  T R4 = T(2) * b[3] - S.q * b[0];
+  T R3 = b[2] - S.V * b[0];
+  T R2 = b[1] - S.U * b[0];
+  s[3] = S.l2 * (R4 - T(2) * S.U * R2 - T(2) * S.V * R3);
+  s[2] = S.tl * R3 - S.V * s[3];
+  s[1] = S.tl * R2 - S.U * s[3];
+  s[0] = b[0] - S.U * s[1] - S.V * s[2] - T(0.5) * s[3] * S.q;
 }
 
 // Smooth gas-kinetic flux at one Gauss point, Eq. (2nd-smooth-flux):
 //   f = g^c - tau (a_n u + a_t v + A) g^c + A g^c t,   tau = mu / p^c
 // with W^c from the half-range moments of g^l (u>0) and g^r (u<0), the
 // equilibrium slopes from the mean of the side derivatives plus, along n,
-// alpha * (W^r - W^l) / delta.  Inputs and outputs in the local frame:
-//   F0 + t F1 = flux, Wc + t Wt = interface state.
+// ajump * (W^r - W^l) with ajump = alpha / delta.  Inputs and outputs in
+// the local frame: F0 + t F1 = flux, Wc + t Wt = interface state.
 template <typename T>
-__device__ __forceinline__ void gks_point_local(T K, T mu_visc, T alpha, T delta,
+__device__ __forceinline__ void gks_point_local(const KC<T> &kc, T mu_visc, T ajump,
                                                 const T Wl[NV], const T Wr[NV],
                                                 const T dnl[NV], const T dtl[NV],
                                                 const T dnr[NV], const T dtr[NV],
                                                 T F0[NV], T F1[NV], T Wc[NV], T Wt[NV]) {
-  Maxw<T> gl = maxw(Wl, K), gr = maxw(Wr, K);
+  const T K = kc.K, c2K = kc.c2K;
+  Maxw<T> gl = maxw(Wl, c2K), gr = maxw(Wr, c2K);
   T ml[3], mr[3];
-  half_moments<T, 2>(gl, +1, ml);
-  half_moments<T, 2>(gr, -1, mr);
-  T el = gl.V * gl.V + (K + T(1)) / (T(2) * gl.lam);
-  T er = gr.V * gr.V + (K + T(1)) / (T(2) * gr.lam);
+  half_moments<T, 2>(gl.U, gl.i2l, d_sqrt(gl.lam), d_rsqrt(gl.lam) * T(kInvSqrtPi), +1, ml);
+  half_moments<T, 2>(gr.U, gr.i2l, d_sqrt(gr.lam), d_rsqrt(gr.lam) * T(kInvSqrtPi), -1, mr);
+  T el = gl.V * gl.V + (K + T(1)) * gl.i2l;
+  T er = gr.V * gr.V + (K + T(1)) * gr.i2l;
   Wc[0] = gl.rho * ml[0] + gr.rho * mr[0];
   Wc[1] = gl.rho * ml[1] + gr.rho * mr[1];
   Wc[2] = gl.rho * ml[0] * gl.V + gr.rho * mr[0] * gr.V;
   Wc[3] = gl.rho * T(0.5) * (ml[2] + ml[0] * el) + gr.rho * T(0.5) * (mr[2] + mr[0] * er);
-  Maxw<T> gc = maxw(Wc, K);
+  Maxw<T> gc = maxw(Wc, c2K);
   Mom<T> m;
   full_moments(gc, K, m);
-  T irc = T(1) / gc.rho;
+  SlopeSolver<T> SS = slope_solver(gc, kc);
   T bn[NV], bt[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    T dn = T(0.5) * (dnl[v] + dnr[v]);
-    if (delta > T(0)) dn += alpha * (Wr[v] - Wl[v]) / delta;
-    bn[v] = dn * irc;
-    bt[v] = T(0.5) * (dtl[v] + dtr[v]) * irc;
+    T dn = T(0.5) * (dnl[v] + dnr[v]) + ajump * (Wr[v] - Wl[v]);
+    bn[v] = dn * gc.ir;
+    bt[v] = T(0.5) * (dtl[v] + dtr[v]) * gc.ir;
   }
   T an[NV], at[NV], A[NV], bA[NV], g1[NV], g2[NV];
-  micro_slope(gc, K, bn, an);
-  micro_slope(gc, K, bt, at);
+  micro_slope(SS, bn, an);
+  micro_slope(SS, bt, at);
   gpsi(m, 1, 0, an, g1);
   gpsi(m, 0, 1, at, g2);
 #pragma unroll
   for (int v = 0; v < NV; ++v) bA[v] = -(g1[v] + g2[v]);
-  micro_slope(gc, K, bA, A);
-  T pc = gc.rho / (T(2) * gc.lam);
-  T tau = mu_visc / pc;
+  micro_slope(SS, bA, A);
+  T tau = mu_visc * SS.tl * gc.ir;          // mu / p^c, p^c = rho / (2 lambda)
   T gAu[NV], gA[NV], gn2[NV], gtuv[NV];
   gpsi(m, 1, 0, A, gAu);
   gpsi(m, 0, 0, A, gA);
@@ -189,19 +218,45 @@ __device__ __forceinline__ void gks_point_local(T K, T mu_visc, T alpha, T delta
   }
 }
 
-// First-order KFVS flux of two cell-average states (local frame).
+// Cell-average primitives used by the low level (one set per cell and
+// implicit step): rho, u, v, p, 1/(2 lambda), sqrt(lambda), 1/sqrt(pi
+// lambda), sound speed c, 1/rho.
+constexpr int NPRIM = 9;
 template <typename T>
-__device__ __forceinline__ void kfvs_local(T K, const T Wl[NV], const T Wr[NV], T F[NV]) {
-  Maxw<T> gl = maxw(Wl, K), gr = maxw(Wr, K);
+struct Prim {
+  T rho, u, v, p, i2l, sl, isp, c, ir;
+};
+template <typename T>
+__device__ __forceinline__ Prim<T> prim_of(const T W[NV], T gamma, const KC<T> &kc) {
+  Prim<T> q;
+  q.rho = W[0];
+  q.ir = T(1) / W[0];
+  q.u = W[1] * q.ir;
+  q.v = W[2] * q.ir;
+  T eps = W[3] - T(0.5) * q.rho * (q.u * q.u + q.v * q.v);
+  q.p = (gamma - T(1)) * eps;
+  q.i2l = kc.c2K * eps * q.ir;
+  T lam = T(0.5) / q.i2l;
+  q.sl = d_sqrt(lam);
+  q.isp = d_rsqrt(lam) * T(kInvSqrtPi);
+  q.c = d_sqrt(gamma * q.p * q.ir);
+  return q;
+}
+
+// First-order KFVS flux of two cell-average states, local frame, from
+// their primitives (normal / tangential velocities already rotated).
+template <typename T>
+__device__ __forceinline__ void kfvs_prims(T K, T rl, T unl, T utl, T i2ll, T sll, T ispl,
+                                           T rr, T unr, T utr, T i2lr, T slr, T ispr, T F[NV]) {
   T ml[4], mr[4];
-  half_moments<T, 3>(gl, +1, ml);
-  half_moments<T, 3>(gr, -1, mr);
-  T el = gl.V * gl.V + (K + T(1)) / (T(2) * gl.lam);
-  T er = gr.V * gr.V + (K + T(1)) / (T(2) * gr.lam);
-  F[0] = gl.rho * ml[1] + gr.rho * mr[1];
-  F[1] = gl.rho * ml[2] + gr.rho * mr[2];
-  F[2] = gl.rho * ml[1] * gl.V + gr.rho * mr[1] * gr.V;
-  F[3] = gl.rho * T(0.5) * (ml[3] + ml[1] * el) + gr.rho * T(0.5) * (mr[3] + mr[1] * er);
+  half_moments<T, 3>(unl, i2ll, sll, ispl, +1, ml);
+  half_moments<T, 3>(unr, i2lr, slr, ispr, -1, mr);
+  T el = utl * utl + (K + T(1)) * i2ll;
+  T er = utr * utr + (K + T(1)) * i2lr;
+  F[0] = rl * ml[1] + rr * mr[1];
+  F[1] = rl * ml[2] + rr * mr[2];
+  F[2] = rl * ml[1] * utl + rr * mr[1] * utr;
+  F[3] = rl * T(0.5) * (ml[3] + ml[1] * el) + rr * T(0.5) * (mr[3] + mr[1] * er);
 }
 
 // Euler normal flux F(U).n, global frame.
