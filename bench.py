@@ -184,10 +184,12 @@ def run_reference(args):
 
 
 def config_block(mesh, args):
+    prec = getattr(args, "precision", "fp64")
     return {"workload": f"2-D inviscid cylinder Ma {MA}, AoA 0, hybrid O-mesh 256 x (32 quad + 96 split-triangle "
                         f"layers), {mesh.n_cells} cells, p-multigrid V-cycle ({args.scheme} high-order step + "
-                        f"6 implicit low-order steps x 2 coloured sweep pairs), FP64",
-            "n_cells": mesh.n_cells, "scheme": args.scheme, "precision": "fp64", "parallelism": "replicas",
+                        f"6 implicit low-order steps x 2 coloured sweep pairs), "
+                        f"{'FP64' if prec == 'fp64' else 'FP32 fluxes / FP64 accumulation'}",
+            "n_cells": mesh.n_cells, "scheme": args.scheme, "precision": prec, "parallelism": "replicas",
             "l2": "flushed between timed steps (256 MiB write, outside the per-step events)"}
 
 
@@ -198,6 +200,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scheme", default="S1O2", choices=["S1O2", "S2O4"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
     args = ap.parse_args()
@@ -211,7 +214,7 @@ def main():
     from paper_2109_09965_gb300 import cgks
     cgks.lib()
     mesh, spec, W0 = workload()
-    spec = dict(spec, time_scheme=args.scheme)
+    spec = dict(spec, time_scheme=args.scheme, precision=args.precision)
     gm = cgks.Mesh(mesh)
     solver = cgks.Solver(gm, spec)
     solver.set_state(W0)
@@ -277,7 +280,8 @@ def main():
     roof = roofline(top, kt, mesh, gm, hbm, hbm_src)
     line = {"metric": BASELINE_METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": config_block(mesh, args), "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]}

@@ -77,7 +77,7 @@ typedef void (*cgks_free_fn)(void *ptr, void *ctx);
 typedef struct {
   double gamma;          /* ratio of specific heats (1.4) */
   double mu;             /* constant dynamic viscosity; 0 = Euler */
-  double alpha;          /* jump coefficient of the equilibrium normal slope (4/3) */
+  double alpha;          /* jump coefficient of the equilibrium normal slope (1/2) */
   double cfl_hi;         /* explicit CFL of the high-order level (0.3-0.5, Section 4) */
   double cfl_lo;         /* local CFL of the low-order level (1000, Section 4) */
   int32_t n_implicit;    /* backward-Euler steps per V-cycle (6, Section 3) */

@@ -105,13 +105,13 @@ def lib():
 
 def make_params(spec: dict) -> OrParams:
     """spec keys: gamma, mu, cfl_hi, cfl_lo, n_implicit, n_sweeps,
-    time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 4/3),
+    time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
     bcs: list of dicts {kind: 'slip'|'noslip'|'farfield', uw=(u,v),
     rho, u=(u,v), p}."""
     P = OrParams()
     P.gamma = float(spec.get("gamma", 1.4))
     P.mu = float(spec.get("mu", 0.0))
-    P.alpha = float(spec.get("alpha", 4.0 / 3.0))
+    P.alpha = float(spec.get("alpha", 0.5))
     P.cfl_hi = float(spec.get("cfl_hi", 0.4))
     P.cfl_lo = float(spec.get("cfl_lo", 1000.0))
     P.n_implicit = int(spec.get("n_implicit", 6))

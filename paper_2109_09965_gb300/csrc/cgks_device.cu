@@ -8,6 +8,12 @@
 // reverse Cuthill-McKee inside a colour).  One thread per cell or face.
 // The cell update gathers the face sums through each cell's face slots
 // (no atomics, deterministic); reductions use a fixed block tree.
+//
+// Precision: kernels that evaluate fluxes are templated on the flux type
+// TF.  FP64 mode runs everything in double.  Mixed mode keeps the
+// conservative variables (W, W_x, U) and every accumulation into them, the
+// residuals and the diagonal inversion in double, and runs reconstruction,
+// face fluxes and relaxation sweeps in float on float mirrors of the state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +22,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "cgks_internal.h"
@@ -28,27 +35,37 @@ namespace {
 
 constexpr int kCellBlock = 256;
 constexpr int kFaceBlock = 128;
-constexpr int kMaxBlocksReduce = 4096;
 
 // status bits of the device status word
 constexpr int kBadState = 1;
 
-struct DevParams {
-  double gamma, K, mu, alpha, cfl_hi, cfl_lo;
-  D::KC<double> kc;
-  int n_bc;
+template <typename T>
+struct ParamsT {
+  T gamma, K, mu, cfl_hi, cfl_lo;
+  D::KC<T> kc;
   int bc_kind[CGKS_MAX_BC];
-  double bc_uw[CGKS_MAX_BC][2];
-  double bc_rho[CGKS_MAX_BC], bc_u[CGKS_MAX_BC][2], bc_p[CGKS_MAX_BC];
+  T bc_uw[CGKS_MAX_BC][2];
+  T bc_rho[CGKS_MAX_BC], bc_u[CGKS_MAX_BC][2], bc_p[CGKS_MAX_BC];
 };
 
-struct DevMesh {
+template <typename T>
+struct MeshT {
   int nc, nf;
-  const double *vol, *ivol, *per, *ih, *m2;  // ih = 1/h; m2: [3][nc]
+  const T *vol, *ivol, *per, *ih, *m2;       // ih = 1/h; m2: [3][nc]
+  const T *op;                               // [kNCol*kNM][nc]
+  const T *fn, *fS, *fjump, *fxi;            // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
   const int *cface, *cnbr;                   // [4][nc]
-  const double *op;                          // [kNCol*kNM][nc]
   const int *fc0, *fc1;
-  const double *fn, *fS, *fjump, *fxi;       // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
+};
+
+// arrays in the flux type TF (in FP64 mode the state entries alias the
+// double state, in mixed mode they are float mirrors)
+template <typename T>
+struct Bufs {
+  T *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr, *U = nullptr;
+  T *coef = nullptr, *FA = nullptr, *FB = nullptr;
+  T *prim = nullptr, *Flo = nullptr, *lam = nullptr, *E0 = nullptr, *E1 = nullptr;
+  T *Rk = nullptr, *invD = nullptr, *dU = nullptr;
 };
 
 struct Scalars {
@@ -57,6 +74,9 @@ struct Scalars {
   int res_ctr;                  // next slot of the residual history
   double dt_fixed;              // > 0: prescribed step
 };
+
+template <typename T>
+__host__ __device__ constexpr bool is_f32() { return std::is_same<T, float>::value; }
 
 __device__ __forceinline__ double dt_value(const Scalars *sc, double cfl) {
   if (sc->dt_fixed > 0.0) return sc->dt_fixed;
@@ -99,7 +119,7 @@ __global__ void k_reset_dt(Scalars *sc, double dt_fixed) {
 
 // K4: local explicit step per cell, global min by atomicMin on the bits
 // (min is order independent).  h = 2|Omega|/perimeter, speed |U| + c + 2 nu / h.
-__global__ void k_dt(DevMesh m, DevParams P, const double *__restrict__ W, Scalars *sc) {
+__global__ void k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W, Scalars *sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = INFINITY;
   if (i < m.nc) {
@@ -117,24 +137,24 @@ __global__ void k_dt(DevMesh m, DevParams P, const double *__restrict__ W, Scala
     atomicMin(&sc->dt_bits, static_cast<unsigned long long>(__double_as_longlong(d)));
 }
 
-// Wall ghost of a cell mean / mean gradient or of a point state, global frame.
-__device__ __forceinline__ void wall_ghost_global(const DevParams &P, int tag, double nx, double ny,
-                                                  const double w[4], const double gx[4], const double gy[4],
-                                                  double wg[4], double ggx[4], double ggy[4]) {
-  double wl[4], dn[4], dt[4], tn[4], tt[4];
+// Wall ghost of a state and its gradient (global frame), through the face frame.
+template <typename T>
+__device__ __forceinline__ void wall_ghost_global(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4],
+                                                  const T gx[4], const T gy[4], T wg[4], T ggx[4], T ggy[4]) {
+  T wl[4], dn[4], dt[4], tn[4], tt[4];
   D::rot_in(nx, ny, w, wl);
   for (int v = 0; v < 4; ++v) { tn[v] = nx * gx[v] + ny * gy[v]; tt[v] = -ny * gx[v] + nx * gy[v]; }
   D::rot_in(nx, ny, tn, dn);
   D::rot_in(nx, ny, tt, dt);
-  double wgl[4], dng[4], dtg[4];
+  T wgl[4], dng[4], dtg[4];
   if (P.bc_kind[tag] == CGKS_BC_SLIP) {
     D::ghost_slip(wl, dn, dt, wgl, dng, dtg);
   } else {
-    double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-    double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+    T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+    T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
     D::ghost_noslip(P.gamma, wn, wt, wl, dn, dt, wgl, dng, dtg);
   }
-  double gn[4], gt[4];
+  T gn[4], gt[4];
   D::rot_out(nx, ny, wgl, wg);
   D::rot_out(nx, ny, dng, gn);
   D::rot_out(nx, ny, dtg, gt);
@@ -143,23 +163,24 @@ __device__ __forceinline__ void wall_ghost_global(const DevParams &P, int tag, d
 
 // K1: compact least-squares quadratic of every cell.
 //   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
-__global__ void __launch_bounds__(kCellBlock) k_recon(DevMesh m, DevParams P, const double *__restrict__ W,
-                                                      const double *__restrict__ Wx, double *__restrict__ coef) {
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
   const int n = m.nc;
-  double wi[4], gxi[4], gyi[4];
+  T wi[4], gxi[4], gyi[4];
   for (int v = 0; v < 4; ++v) { wi[v] = W[v * n + i]; gxi[v] = Wx[v * n + i]; gyi[v] = Wx[(4 + v) * n + i]; }
-  double c[kNM][4];
+  T c[kNM][4];
   for (int q = 0; q < kNM; ++q) {
-    double o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
+    T o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
     for (int v = 0; v < 4; ++v) c[q][v] = o0 * gxi[v] + o1 * gyi[v];
   }
   for (int s = 0; s < kMaxFace; ++s) {
     int fs = m.cface[s * n + i];
     if (fs == kNoFace) continue;
     int j = m.cnbr[s * n + i];
-    double b0[4], b1[4], b2[4];
+    T b0[4], b1[4], b2[4];
     if (j >= 0) {
       for (int v = 0; v < 4; ++v) {
         b0[v] = W[v * n + j] - wi[v];
@@ -170,14 +191,14 @@ __global__ void __launch_bounds__(kCellBlock) k_recon(DevMesh m, DevParams P, co
       int f = fs >= 0 ? fs : ~fs;
       int tag = -1 - m.fc1[f];
       if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
-      double wg[4];
+      T wg[4];
       wall_ghost_global(P, tag, m.fn[f], m.fn[m.nf + f], wi, gxi, gyi, wg, b1, b2);
       for (int v = 0; v < 4; ++v) b0[v] = wg[v] - wi[v];
     }
     for (int q = 0; q < kNM; ++q) {
-      double o0 = m.op[((3 * s) * kNM + q) * n + i];
-      double o1 = m.op[((3 * s + 1) * kNM + q) * n + i];
-      double o2 = m.op[((3 * s + 2) * kNM + q) * n + i];
+      T o0 = m.op[((3 * s) * kNM + q) * n + i];
+      T o1 = m.op[((3 * s + 1) * kNM + q) * n + i];
+      T o2 = m.op[((3 * s + 2) * kNM + q) * n + i];
       for (int v = 0; v < 4; ++v) c[q][v] += o0 * b0[v] + o1 * b1[v] + o2 * b2[v];
     }
   }
@@ -186,34 +207,54 @@ __global__ void __launch_bounds__(kCellBlock) k_recon(DevMesh m, DevParams P, co
 }
 
 // value and gradient of the quadratic of cell i at scaled offset (x, y)
-__device__ __forceinline__ void recon_point(const DevMesh &m, const double *__restrict__ W,
-                                            const double *__restrict__ coef, int i, double x, double y,
-                                            double val[4], double gx[4], double gy[4]) {
+template <typename T>
+__device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restrict__ W, const T *__restrict__ coef,
+                                            int i, T x, T y, T val[4], T gx[4], T gy[4]) {
   const int n = m.nc;
-  double ih = m.ih[i];
-  double p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
+  T ih = m.ih[i];
+  T p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
   for (int v = 0; v < 4; ++v) {
-    double c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
-    double c3 = coef[(3 * 4 + v) * n + i], c4 = coef[(4 * 4 + v) * n + i];
+    T c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
+    T c3 = coef[(3 * 4 + v) * n + i], c4 = coef[(4 * 4 + v) * n + i];
     val[v] = W[v * n + i] + c0 * x + c1 * y + c2 * p2 + c3 * p3 + c4 * p4;
-    gx[v] = (c0 + 2.0 * c2 * x + c3 * y) * ih;
-    gy[v] = (c1 + c3 * x + 2.0 * c4 * y) * ih;
+    gx[v] = (c0 + T(2) * c2 * x + c3 * y) * ih;
+    gy[v] = (c1 + c3 * x + T(2) * c4 * y) * ih;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4], T wg[4]) {
+  T wl[4], z[4] = { T(0), T(0), T(0), T(0) }, wgl[4], a[4], b[4];
+  D::rot_in(nx, ny, w, wl);
+  int kind = P.bc_kind[tag];
+  if (kind == CGKS_BC_FARFIELD) {
+    T une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
+    T ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
+    D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wgl);
+  } else if (kind == CGKS_BC_SLIP) {
+    D::ghost_slip(wl, z, z, wgl, a, b);
+  } else {
+    T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+    T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+    D::ghost_noslip(P.gamma, wn, wt, wl, z, z, wgl, a, b);
+  }
+  D::rot_out(nx, ny, wgl, wg);
 }
 
 // K2: gas-kinetic flux and interface state at the two Gauss points of every
 // face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
 //   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
-__global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, const double *__restrict__ W,
-                                                     const double *__restrict__ coef, double *__restrict__ out) {
+template <typename T>
+__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                     const T *__restrict__ coef, T *__restrict__ out) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const double nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
-  double acc[4][4];
-  for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = 0.0;
-  double wff[4];
+  const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
+  T acc[4][4];
+  for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = T(0);
+  T wff[4];
   bool farfield = false;
   int tag = 0;
   if (c1 < 0) {
@@ -221,46 +262,46 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, con
     farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
     if (farfield) {
       // Riemann-invariant state from the cell mean and the free stream
-      double wm[4], wl[4];
+      T wm[4], wl[4];
       for (int v = 0; v < 4; ++v) wm[v] = W[v * m.nc + c0];
       D::rot_in(nx, ny, wm, wl);
-      double une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
-      double ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
+      T une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
+      T ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
       D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wff);
     }
   }
   for (int k = 0; k < 2; ++k) {
-    double wL[4], gxL[4], gyL[4];
+    T wL[4], gxL[4], gyL[4];
     recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
-    double wl[4], dnl[4], dtl[4], t0[4], t1[4];
+    T wl[4], dnl[4], dtl[4], t0[4], t1[4];
     D::rot_in(nx, ny, wL, wl);
     for (int v = 0; v < 4; ++v) { t0[v] = nx * gxL[v] + ny * gyL[v]; t1[v] = -ny * gxL[v] + nx * gyL[v]; }
     D::rot_in(nx, ny, t0, dnl);
     D::rot_in(nx, ny, t1, dtl);
-    double wr[4], dnr[4], dtr[4];
+    T wr[4], dnr[4], dtr[4];
     if (c1 >= 0) {
-      double wR[4], gxR[4], gyR[4];
+      T wR[4], gxR[4], gyR[4];
       recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
       D::rot_in(nx, ny, wR, wr);
       for (int v = 0; v < 4; ++v) { t0[v] = nx * gxR[v] + ny * gyR[v]; t1[v] = -ny * gxR[v] + nx * gyR[v]; }
       D::rot_in(nx, ny, t0, dnr);
       D::rot_in(nx, ny, t1, dtr);
     } else if (farfield) {
-      for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = 0.0; dtr[v] = 0.0; }
+      for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = T(0); dtr[v] = T(0); }
     } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
       D::ghost_slip(wl, dnl, dtl, wr, dnr, dtr);
     } else {
-      double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-      double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
+      T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
+      T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
       D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
     }
-    double F0[4], F1[4], Wc[4], Wt[4];
+    T F0[4], F1[4], Wc[4], Wt[4];
     D::gks_point_local(P.kc, P.mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
-    double g[4];
-    D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += 0.5 * g[v];
-    D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += 0.5 * g[v];
-    D::rot_out(nx, ny, Wc, g); for (int v = 0; v < 4; ++v) acc[2][v] += 0.5 * g[v];
-    D::rot_out(nx, ny, Wt, g); for (int v = 0; v < 4; ++v) acc[3][v] += 0.5 * g[v];
+    T g[4];
+    D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, Wc, g); for (int v = 0; v < 4; ++v) acc[2][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, Wt, g); for (int v = 0; v < 4; ++v) acc[3][v] += T(0.5) * g[v];
   }
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
@@ -269,27 +310,31 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(DevMesh m, DevParams P, con
 // K3 modes
 enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
 
-// K3: gather the face sums of each cell.
+// K3: gather the face sums of each cell (accumulated in FP64).
 //   net flux   R  = -sum_p sgn S_p (a0 F0A + a1 F1A + a2 F1B)
-//   W_out = W_base + dt/|Omega| R    (or R itself in kResidual mode)
+//   W_out = W_base + dt/|Omega| R   (not in kResidual mode)
 //   Wx_out = 1/|Omega| sum_p sgn S_p n_p (WcA + b1 WtX)
-// plus the per-block density-residual partial sums and the state check.
-__global__ void __launch_bounds__(kCellBlock) k_update(DevMesh m, DevParams P, int mode, const double *__restrict__ Wbase,
-                                                       const double *__restrict__ FA, const double *__restrict__ FB,
-                                                       Scalars *sc, double *__restrict__ Wout, double *__restrict__ Wxout,
-                                                       double *__restrict__ partial, double *__restrict__ Rout) {
+// optional outputs: R itself, float mirrors of W_out / Wx_out, the
+// per-block density-residual partial sums; plus the state check.
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P, int mode,
+                                                       const double *__restrict__ Wbase, const TF *__restrict__ FA,
+                                                       const TF *__restrict__ FB, Scalars *sc,
+                                                       double *__restrict__ Wout, double *__restrict__ Wxout,
+                                                       double *__restrict__ partial, double *__restrict__ Rout,
+                                                       TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc, nf = m.nf;
   double num = 0.0, den = 0.0;
   if (i < n) {
     double dt = dt_value(sc, P.cfl_hi);
-    double a0, a1, a2, b1;
-    const double *FW = FA;   // where Wt is taken from
+    double a0, a1, b1;
+    const TF *FW = FA;   // where Wt is taken from
     switch (mode) {
-      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; a2 = 0.0; b1 = dt; break;
-      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; a2 = 0.0; b1 = 0.5 * dt; break;
-      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; a2 = 2.0; b1 = dt; FW = FB; break;
-      default: a0 = 1.0; a1 = 0.5 * dt; a2 = 0.0; b1 = 0.0; break;
+      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; b1 = dt; break;
+      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; b1 = 0.5 * dt; break;
+      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; FW = FB; break;
+      default: a0 = 1.0; a1 = 0.5 * dt; b1 = 0.0; break;
     }
     double R[4] = { 0, 0, 0, 0 }, gx[4] = { 0, 0, 0, 0 }, gy[4] = { 0, 0, 0, 0 };
     for (int s = 0; s < kMaxFace; ++s) {
@@ -299,12 +344,12 @@ __global__ void __launch_bounds__(kCellBlock) k_update(DevMesh m, DevParams P, i
       double sg = fs >= 0 ? 1.0 : -1.0;
       double S = m.fS[f], nx = m.fn[f], ny = m.fn[nf + f];
       for (int v = 0; v < 4; ++v) {
-        double f1 = FA[(4 + v) * nf + f];
-        if (mode == kS2O4Final) f1 += a2 * FB[(4 + v) * nf + f];
-        double fl = S * (a0 * FA[v * nf + f] + a1 * f1);
+        double f1 = static_cast<double>(FA[(4 + v) * nf + f]);
+        if (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(FB[(4 + v) * nf + f]);
+        double fl = S * (a0 * static_cast<double>(FA[v * nf + f]) + a1 * f1);
         R[v] -= sg * fl;
         if (mode != kResidual) {
-          double wp = FA[(8 + v) * nf + f] + b1 * FW[(12 + v) * nf + f];
+          double wp = static_cast<double>(FA[(8 + v) * nf + f]) + b1 * static_cast<double>(FW[(12 + v) * nf + f]);
           gx[v] += sg * S * nx * wp;
           gy[v] += sg * S * ny * wp;
         }
@@ -313,13 +358,18 @@ __global__ void __launch_bounds__(kCellBlock) k_update(DevMesh m, DevParams P, i
     if (Rout)
       for (int v = 0; v < 4; ++v) Rout[v * n + i] = R[v];
     if (mode != kResidual) {
-      double iv = 1.0 / m.vol[i];
+      double iv = m.ivol[i];
       double w[4];
       for (int v = 0; v < 4; ++v) {
         w[v] = Wbase[v * n + i] + dt / m.vol[i] * R[v];
         Wout[v * n + i] = w[v];
         Wxout[v * n + i] = gx[v] * iv;
         Wxout[(4 + v) * n + i] = gy[v] * iv;
+        if (Wout_m) {
+          Wout_m[v * n + i] = static_cast<TF>(w[v]);
+          Wxout_m[v * n + i] = static_cast<TF>(gx[v] * iv);
+          Wxout_m[(4 + v) * n + i] = static_cast<TF>(gy[v] * iv);
+        }
       }
       if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
       num = fabs(w[0] - Wbase[i]);
@@ -346,47 +396,31 @@ __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Sca
 }
 
 // ---------------------------- low-order level ----------------------------
-// ghost of a cell-mean state (zero gradients)
-__device__ __forceinline__ void lo_ghost(const DevParams &P, int tag, double nx, double ny, const double w[4],
-                                         double wg[4]) {
-  double wl[4], z[4] = { 0, 0, 0, 0 }, wgl[4], a[4], b[4];
-  D::rot_in(nx, ny, w, wl);
-  int kind = P.bc_kind[tag];
-  if (kind == CGKS_BC_FARFIELD) {
-    double une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
-    double ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
-    D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wgl);
-  } else if (kind == CGKS_BC_SLIP) {
-    D::ghost_slip(wl, z, z, wgl, a, b);
-  } else {
-    double wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-    double wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
-    D::ghost_noslip(P.gamma, wn, wt, wl, z, z, wgl, a, b);
-  }
-  D::rot_out(nx, ny, wgl, wg);
-}
-
 // K5a: per-cell start of an implicit step: U = W_p0 (first step) or
-// U += dU (Algorithm 1's update), then the primitives of U.
-__global__ void __launch_bounds__(kCellBlock) k_lo_cell(DevMesh m, DevParams P, int first,
-                                                        const double *__restrict__ Wp0, double *__restrict__ U,
-                                                        const double *__restrict__ dU, double *__restrict__ prim) {
+// U += dU (Algorithm 1's update, in FP64), then the primitives of U (and
+// its float mirror in mixed mode).
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
+                                                        double *__restrict__ U, const TF *__restrict__ dU,
+                                                        TF *__restrict__ prim, TF *__restrict__ Um) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
-  const int n = m.nc;
-  double w[4];
+  if (i >= n) return;
+  TF w[4];
   for (int v = 0; v < 4; ++v) {
-    w[v] = first ? Wp0[v * n + i] : U[v * n + i] + dU[v * n + i];
-    U[v * n + i] = w[v];
+    double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(dU[v * n + i]);
+    U[v * n + i] = u;
+    w[v] = static_cast<TF>(u);
+    if (Um) Um[v * n + i] = w[v];
   }
-  D::Prim<double> q = D::prim_of(w, P.gamma, P.kc);
+  D::Prim<TF> q = D::prim_of(w, P.gamma, P.kc);
   prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.p;
   prim[4 * n + i] = q.i2l; prim[5 * n + i] = q.sl; prim[6 * n + i] = q.isp; prim[7 * n + i] = q.c;
   prim[8 * n + i] = q.ir;
 }
 
-__device__ __forceinline__ D::Prim<double> load_prim(const double *__restrict__ prim, int n, int i) {
-  D::Prim<double> q;
+template <typename T>
+__device__ __forceinline__ D::Prim<T> load_prim(const T *__restrict__ prim, int n, int i) {
+  D::Prim<T> q;
   q.rho = prim[0 * n + i]; q.u = prim[1 * n + i]; q.v = prim[2 * n + i]; q.p = prim[3 * n + i];
   q.i2l = prim[4 * n + i]; q.sl = prim[5 * n + i]; q.isp = prim[6 * n + i]; q.c = prim[7 * n + i];
   q.ir = prim[8 * n + i];
@@ -394,59 +428,63 @@ __device__ __forceinline__ D::Prim<double> load_prim(const double *__restrict__ 
 }
 
 // K5b: first-order KFVS flux, spectral radius lambda_p = max of both sides,
-// and the Euler normal fluxes F_n(U_c0), F_n(U_c1) the relaxation reuses.
-__global__ void __launch_bounds__(kCellBlock) k_lo_face(DevMesh m, DevParams P, const double *__restrict__ U,
-                                                        const double *__restrict__ prim, double *__restrict__ Flo,
-                                                        double *__restrict__ lam, double *__restrict__ E0,
-                                                        double *__restrict__ E1) {
+// and (FP64 mode) the Euler normal fluxes F_n(U_c0), F_n(U_c1) the
+// relaxation reuses.
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
+                                                        const T *__restrict__ prim, T *__restrict__ Flo,
+                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
   const int n = m.nc, nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const double nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
-  D::Prim<double> a = load_prim(prim, n, c0), b;
-  double ivb;
+  const T nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
+  D::Prim<T> a = load_prim(prim, n, c0), b;
+  T ivb;
   if (c1 >= 0) {
     b = load_prim(prim, n, c1);
     ivb = m.ivol[c1];
   } else {
-    double w0[4], wg[4];
+    T w0[4], wg[4];
     for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
     lo_ghost(P, -1 - c1, nx, ny, w0, wg);
     b = D::prim_of(wg, P.gamma, P.kc);
     ivb = m.ivol[c0];
   }
-  const double una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
-  const double unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
-  double Fl[4], F[4];
+  const T una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
+  const T unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
+  T Fl[4], F[4];
   D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
   D::rot_out(nx, ny, Fl, F);
   for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
-  const double la = fabs(una) + a.c + 2.0 * (P.mu * a.ir) * S * m.ivol[c0];
-  const double lb = fabs(unb) + b.c + 2.0 * (P.mu * b.ir) * S * ivb;
+  const T la = fabs(una) + a.c + T(2) * (P.mu * a.ir) * S * m.ivol[c0];
+  const T lb = fabs(unb) + b.c + T(2) * (P.mu * b.ir) * S * ivb;
   lam[f] = la > lb ? la : lb;
-  // Euler normal flux of the cell means (interior faces: both sides)
-  E0[0 * nf + f] = a.rho * una;
-  E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
-  E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
-  E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
-  if (c1 >= 0) {
-    E1[0 * nf + f] = b.rho * unb;
-    E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
-    E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
-    E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
+  if (E0) {
+    // Euler normal flux of the cell means (interior faces: both sides)
+    E0[0 * nf + f] = a.rho * una;
+    E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
+    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
+    E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
+    if (c1 >= 0) {
+      E1[0 * nf + f] = b.rho * unb;
+      E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
+      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
+      E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
+    }
   }
 }
 
-// K6: low-order right-hand side R^k = R_lo(U^k) + S, 1/D_i, and the first
-// colour pass of the relaxation: with dU = 0 everywhere the update of a
-// colour-0 cell reduces to dU_i = R_i / D_i; all other cells start at 0.
-// first: also forms the forcing S = R_p0 - R_lo(W_p0) (Section 3, step 3).
-__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, int first, int colour0_end,
-                                                       const double *__restrict__ Flo, const double *__restrict__ lam,
+// K6: low-order right-hand side R^k = R_lo(U^k) + S (FP64 sums), 1/D_i
+// (FP64 inversion), and the first colour pass of the relaxation: with
+// dU = 0 everywhere the update of a colour-0 cell reduces to R_i / D_i; all
+// other cells start at 0.  first: also forms the forcing S = R_p0 -
+// R_lo(W_p0) (Section 3, step 3).
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0_end,
+                                                       const TF *__restrict__ Flo, const TF *__restrict__ lam,
                                                        const double *__restrict__ Rp0, double *__restrict__ Src,
-                                                       double *__restrict__ Rk, double *__restrict__ invD,
-                                                       double *__restrict__ dU) {
+                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
   const int n = m.nc, nf = m.nf;
@@ -457,35 +495,37 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(DevMesh m, DevParams P, i
     int f = fs >= 0 ? fs : ~fs;
     double sg = fs >= 0 ? 1.0 : -1.0;
     double S = m.fS[f];
-    for (int v = 0; v < 4; ++v) R[v] -= sg * S * Flo[v * nf + f];
-    sum += lam[f] * S;
+    for (int v = 0; v < 4; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
+    sum += static_cast<double>(lam[f]) * S;
   }
   // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2
   const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
-  invD[i] = id;
+  invD[i] = static_cast<TF>(id);
   for (int v = 0; v < 4; ++v) {
     double src;
     if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
     else src = Src[v * n + i];
     double r = R[v] + src;
-    Rk[v * n + i] = r;
-    dU[v * n + i] = i < colour0_end ? r * id : 0.0;
+    Rk[v * n + i] = static_cast<TF>(r);
+    dU[v * n + i] = i < colour0_end ? static_cast<TF>(r * id) : TF(0);
   }
 }
 
 // K7: point relaxation of the cells of one colour, Eq. (implicit-local):
 //   dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
-//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero;
-// F_n(U_ip) comes from the face cache of this implicit step.
-__global__ void __launch_bounds__(kCellBlock) k_sweep(DevMesh m, DevParams P, int begin, int end,
-                                                      const double *__restrict__ U, const double *__restrict__ Rk,
-                                                      const double *__restrict__ invD, const double *__restrict__ lam,
-                                                      const double *__restrict__ E0, const double *__restrict__ E1,
-                                                      double *__restrict__ dU) {
+//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
+// FP64: F_n(U_ip) from the face cache of this implicit step.  Mixed: the
+// difference F_n(U_ip + dU_ip) - F_n(U_ip) in the exact increment form.
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int end,
+                                                      const T *__restrict__ U, const T *__restrict__ prim,
+                                                      const T *__restrict__ Rk, const T *__restrict__ invD,
+                                                      const T *__restrict__ lam, const T *__restrict__ E0,
+                                                      const T *__restrict__ E1, T *__restrict__ dU) {
   int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
   const int n = m.nc, nf = m.nf;
-  double acc[4];
+  T acc[4];
   for (int v = 0; v < 4; ++v) acc[v] = Rk[v * n + i];
   for (int s = 0; s < kMaxFace; ++s) {
     int j = m.cnbr[s * n + i];
@@ -493,26 +533,33 @@ __global__ void __launch_bounds__(kCellBlock) k_sweep(DevMesh m, DevParams P, in
     int fs = m.cface[s * n + i];
     bool is0 = fs >= 0;
     int f = is0 ? fs : ~fs;
-    double sg = is0 ? 1.0 : -1.0;
-    double nx = sg * m.fn[f], ny = sg * m.fn[nf + f], hS = 0.5 * m.fS[f], lp = lam[f];
-    double uj[4], up[4], fa[4], fb[4];
-    for (int v = 0; v < 4; ++v) {
-      uj[v] = U[v * n + j];
-      up[v] = uj[v] + dU[v * n + j];
-      fb[v] = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+    T sg = is0 ? T(1) : T(-1);
+    T nx = sg * m.fn[f], ny = sg * m.fn[nf + f], hS = T(0.5) * m.fS[f], lp = lam[f];
+    T uj[4], du[4], dF[4];
+    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
+    if constexpr (is_f32<T>()) {
+      D::euler_flux_delta(P.gamma, uj, prim[1 * n + j], prim[2 * n + j], prim[3 * n + j], du, nx, ny, dF);
+      for (int v = 0; v < 4; ++v) acc[v] -= hS * (dF[v] - lp * du[v]);
+    } else {
+      T up[4], fa[4], fb;
+      for (int v = 0; v < 4; ++v) up[v] = uj[v] + du[v];
+      D::euler_flux(P.gamma, up, nx, ny, fa);
+      for (int v = 0; v < 4; ++v) {
+        fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        acc[v] -= hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
+      }
     }
-    D::euler_flux(P.gamma, up, nx, ny, fa);
-    for (int v = 0; v < 4; ++v) acc[v] -= hS * ((fa[v] - fb[v]) - lp * (up[v] - uj[v]));
   }
-  const double id = invD[i];
+  const T id = invD[i];
   for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] * id;
 }
 
 // K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
 // residual against the state at the start of the cycle, state check.
-__global__ void __launch_bounds__(kCellBlock) k_prolong(DevMesh m, DevParams P, double *__restrict__ W,
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT<double> P, double *__restrict__ W,
                                                         const double *__restrict__ Wp0, const double *__restrict__ U,
-                                                        Scalars *sc, double *__restrict__ partial) {
+                                                        Scalars *sc, double *__restrict__ partial, TF *__restrict__ Wm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc;
   double num = 0.0, den = 0.0;
@@ -523,6 +570,7 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(DevMesh m, DevParams P, 
       double wp = Wp0[v * n + i];
       w[v] = wp + (U[v * n + i] - wp);
       W[v * n + i] = w[v];
+      if (Wm) Wm[v * n + i] = static_cast<TF>(w[v]);
     }
     if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
     num = fabs(w[0] - old_rho);
@@ -533,12 +581,21 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(DevMesh m, DevParams P, 
 
 // AoS caller order <-> SoA internal order
 __global__ void k_gather_state(int n, const int *__restrict__ perm, const double *__restrict__ Wa,
-                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx) {
+                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx,
+                               float *__restrict__ W32, float *__restrict__ Wx32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = perm[i];
-  for (int v = 0; v < 4; ++v) W[v * n + i] = Wa[4 * c + v];
-  for (int k = 0; k < 8; ++k) Wx[k * n + i] = Wxa ? Wxa[8 * c + k] : 0.0;
+  for (int v = 0; v < 4; ++v) {
+    double w = Wa[4 * c + v];
+    W[v * n + i] = w;
+    if (W32) W32[v * n + i] = static_cast<float>(w);
+  }
+  for (int k = 0; k < 8; ++k) {
+    double g = Wxa ? Wxa[8 * c + k] : 0.0;
+    Wx[k * n + i] = g;
+    if (Wx32) Wx32[k * n + i] = static_cast<float>(g);
+  }
 }
 __global__ void k_scatter_state(int n, const int *__restrict__ perm, const double *__restrict__ W,
                                 const double *__restrict__ Wx, double *__restrict__ Wa, double *__restrict__ Wxa) {
@@ -563,19 +620,23 @@ inline int nblk(int n, int b) { return (n + b - 1) / b; }
 struct cgks_solver {
   HostMesh hm;                  // host copy (ordering and permutations)
   cgks_params params{};
-  DevParams dp{};
-  DevMesh dm{};
+  bool mixed = false;
+  ParamsT<double> dp{};
+  ParamsT<float> fp{};
+  MeshT<double> dm{};
+  MeshT<float> fm{};
   cudaStream_t user_stream = nullptr, stream = nullptr;
   cudaEvent_t ev_user = nullptr, ev_done = nullptr;
   void *arena = nullptr;
   size_t arena_bytes = 0;
   int device = 0;
-  // state and work arrays (device)
+  // FP64 state and accumulation arrays (device)
   double *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr;
-  double *coef = nullptr, *FA = nullptr, *FB = nullptr;
-  double *U = nullptr, *dU = nullptr, *Rp0 = nullptr, *Src = nullptr, *Rk = nullptr, *invD = nullptr;
-  double *Flo = nullptr, *lam = nullptr, *E0 = nullptr, *E1 = nullptr, *prim = nullptr;
+  double *U = nullptr, *Rp0 = nullptr, *Src = nullptr;
   double *partial = nullptr, *last = nullptr;
+  // flux-type arrays
+  Bufs<double> bd;
+  Bufs<float> bf;
   std::vector<int> sweep_colours;   // colour sequence of the relaxation after the first pass
   double *hist = nullptr;
   int hist_cap = 0;
@@ -632,32 +693,51 @@ void launch(cgks_solver *s, int id, Kern kern, dim3 grid, dim3 block, Args... ar
   s->launches++;
 }
 
+template <typename TF> Bufs<TF> &bufs(cgks_solver *s);
+template <> Bufs<double> &bufs<double>(cgks_solver *s) { return s->bd; }
+template <> Bufs<float> &bufs<float>(cgks_solver *s) { return s->bf; }
+template <typename TF> const MeshT<TF> &fmesh(cgks_solver *s);
+template <> const MeshT<double> &fmesh<double>(cgks_solver *s) { return s->dm; }
+template <> const MeshT<float> &fmesh<float>(cgks_solver *s) { return s->fm; }
+template <typename TF> const ParamsT<TF> &fparams(cgks_solver *s);
+template <> const ParamsT<double> &fparams<double>(cgks_solver *s) { return s->dp; }
+template <> const ParamsT<float> &fparams<float>(cgks_solver *s) { return s->fp; }
+// float mirror of a flux-type array, or null when the flux type is double
+template <typename TF> TF *mirror(TF *p) { return is_f32<TF>() ? p : nullptr; }
+
 // ---- building blocks of a step / cycle ----
 void enqueue_dt(cgks_solver *s, double dt_fixed) {
   launch(s, KI_DT, k_reset_dt, dim3(1), dim3(1), s->sc, dt_fixed);
-  if (!(dt_fixed > 0.0)) launch(s, KI_DT, k_dt, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (const double *)s->W, s->sc);
+  if (!(dt_fixed > 0.0))
+    launch(s, KI_DT, k_dt, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (const double *)s->W, s->sc);
 }
 
-void enqueue_hi_eval(cgks_solver *s, const double *W, const double *Wx, double *Fout) {
-  launch(s, KI_RECON, k_recon, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, W, Wx, s->coef);
-  launch(s, KI_FACE, k_face, dim3(nblk(s->dm.nf, kFaceBlock)), dim3(kFaceBlock), s->dm, s->dp, W,
-         (const double *)s->coef, Fout);
+template <typename TF>
+void enqueue_hi_eval(cgks_solver *s, const TF *W, const TF *Wx, TF *Fout) {
+  Bufs<TF> &B = bufs<TF>(s);
+  launch(s, KI_RECON, k_recon<TF>, dim3(s->nblk_cell), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s), W, Wx, B.coef);
+  launch(s, KI_FACE, k_face<TF>, dim3(nblk(s->dm.nf, kFaceBlock)), dim3(kFaceBlock), fmesh<TF>(s), fparams<TF>(s), W,
+         (const TF *)B.coef, Fout);
 }
 
 // high-order step from (W, Wx) into (Wout, Wx): Wx updated in place.
-void enqueue_hi_step(cgks_solver *s, double *Wout, bool want_res) {
+template <typename TF>
+void enqueue_hi_step(cgks_solver *s, double *Wout, TF *Wout_m, bool want_res) {
+  Bufs<TF> &B = bufs<TF>(s);
   double *part = want_res ? s->partial : nullptr;
-  enqueue_hi_eval(s, s->W, s->Wx, s->FA);
+  enqueue_hi_eval<TF>(s, B.W, B.Wx, B.FA);
   if (s->params.time_scheme == CGKS_S1O2) {
-    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS1O2,
-           (const double *)s->W, (const double *)s->FA, (const double *)s->FA, s->sc, Wout, s->Wx, part, s->Rp0);
+    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS1O2,
+           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FA, s->sc, Wout, s->Wx, part, s->Rp0, Wout_m,
+           mirror<TF>(B.Wx));
   } else {
-    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Stage,
-           (const double *)s->W, (const double *)s->FA, (const double *)s->FA, s->sc, s->Ws, s->Wxs,
-           (double *)nullptr, (double *)nullptr);
-    enqueue_hi_eval(s, s->Ws, s->Wxs, s->FB);
-    launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Final,
-           (const double *)s->W, (const double *)s->FA, (const double *)s->FB, s->sc, Wout, s->Wx, part, s->Rp0);
+    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Stage,
+           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FA, s->sc, s->Ws, s->Wxs, (double *)nullptr,
+           (double *)nullptr, mirror<TF>(B.Ws), mirror<TF>(B.Wxs));
+    enqueue_hi_eval<TF>(s, B.Ws, B.Wxs, B.FB);
+    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Final,
+           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FB, s->sc, Wout, s->Wx, part, s->Rp0, Wout_m,
+           mirror<TF>(B.Wx));
   }
   if (want_res)
     launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
@@ -667,52 +747,73 @@ void enqueue_hi_step(cgks_solver *s, double *Wout, bool want_res) {
 // low-order solve from U = W_p0 (= s->Wn), R_p0 in s->Rp0; result in s->U.
 // Per implicit step: cell primitives (and U += dU), KFVS faces, right-hand
 // side with the first colour pass, then the remaining colour passes.
+template <typename TF>
 void enqueue_lo_solve(cgks_solver *s) {
+  Bufs<TF> &B = bufs<TF>(s);
   const int n = s->dm.nc, nf = s->dm.nf;
   const int c0_end = s->params.n_sweeps > 0 ? s->hm.colour_start[1] : 0;
   for (int k = 0; k < s->params.n_implicit; ++k) {
-    launch(s, KI_LOCELL, k_lo_cell, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0,
-           (const double *)s->Wn, s->U, (const double *)s->dU, s->prim);
-    launch(s, KI_LOFACE, k_lo_face, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, (const double *)s->U,
-           (const double *)s->prim, s->Flo, s->lam, s->E0, s->E1);
-    launch(s, KI_LORHS, k_lo_rhs, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0, c0_end,
-           (const double *)s->Flo, (const double *)s->lam, (const double *)s->Rp0, s->Src, s->Rk, s->invD, s->dU);
+    launch(s, KI_LOCELL, k_lo_cell<TF>, dim3(s->nblk_cell), dim3(kCellBlock), n, fparams<TF>(s), k == 0 ? 1 : 0,
+           (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
+    launch(s, KI_LOFACE, k_lo_face<TF>, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s),
+           (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
+    launch(s, KI_LORHS, k_lo_rhs<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0, c0_end,
+           (const TF *)B.Flo, (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU);
     for (int c : s->sweep_colours) {
       int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
-      launch(s, KI_SWEEP, k_sweep, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, b, e,
-             (const double *)s->U, (const double *)s->Rk, (const double *)s->invD, (const double *)s->lam,
-             (const double *)s->E0, (const double *)s->E1, s->dU);
+      launch(s, KI_SWEEP, k_sweep<TF>, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s),
+             b, e, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD, (const TF *)B.lam,
+             (const TF *)B.E0, (const TF *)B.E1, B.dU);
     }
   }
   // U^{n_implicit} = U + dU of the last step
   if (s->params.n_implicit > 0)
-    launch(s, KI_LOCELL, k_lo_cell, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, 0, (const double *)s->Wn,
-           s->U, (const double *)s->dU, s->prim);
+    launch(s, KI_LOCELL, k_lo_cell<TF>, dim3(s->nblk_cell), dim3(kCellBlock), n, fparams<TF>(s), 0,
+           (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
   else
     cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream);
 }
 
-void enqueue_cycle(cgks_solver *s) {
-  enqueue_dt(s, -1.0);
-  // 1: high-order step into W_p0 = Wn (W keeps W^n for the residual)
-  enqueue_hi_step(s, s->Wn, false);
-  // 2: R_p0 = time-averaged high-order net flux at W^{n+1}
-  enqueue_hi_eval(s, s->Wn, s->Wx, s->FB);
-  launch(s, KI_UPDATE, k_update, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kResidual,
-         (const double *)s->Wn, (const double *)s->FB, (const double *)s->FB, s->sc, (double *)nullptr,
-         (double *)nullptr, (double *)nullptr, s->Rp0);
-  // 3-4: forcing and implicit low-order solve
-  enqueue_lo_solve(s);
-  // 5: correction and residual
-  launch(s, KI_PROLONG, k_prolong, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W, (const double *)s->Wn,
-         (const double *)s->U, s->sc, s->partial);
+template <typename TF>
+void enqueue_prolong(cgks_solver *s) {
+  launch(s, KI_PROLONG, k_prolong<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W,
+         (const double *)s->Wn, (const double *)s->U, s->sc, s->partial, mirror<TF>(bufs<TF>(s).W));
   launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
          s->hist_cap, s->last);
 }
 
+template <typename TF>
+void enqueue_cycle_t(cgks_solver *s) {
+  Bufs<TF> &B = bufs<TF>(s);
+  enqueue_dt(s, -1.0);
+  // 1: high-order step into W_p0 = Wn (W keeps W^n for the residual)
+  enqueue_hi_step<TF>(s, s->Wn, mirror<TF>(B.Wn), false);
+  // 2: R_p0 = time-averaged high-order net flux at W^{n+1}
+  enqueue_hi_eval<TF>(s, B.Wn, B.Wx, B.FB);
+  launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kResidual,
+         (const double *)s->Wn, (const TF *)B.FB, (const TF *)B.FB, s->sc, (double *)nullptr, (double *)nullptr,
+         (double *)nullptr, s->Rp0, (TF *)nullptr, (TF *)nullptr);
+  // 3-4: forcing and implicit low-order solve
+  enqueue_lo_solve<TF>(s);
+  // 5: correction and residual
+  enqueue_prolong<TF>(s);
+}
+
+void enqueue_cycle(cgks_solver *s) {
+  if (s->mixed) enqueue_cycle_t<float>(s);
+  else enqueue_cycle_t<double>(s);
+}
+
 void enqueue_explicit_step(cgks_solver *s, double dt_fixed) {
   enqueue_dt(s, dt_fixed);
-  enqueue_hi_step(s, s->W, true);
+  if (s->mixed) enqueue_hi_step<float>(s, s->W, s->bf.W, true);
+  else enqueue_hi_step<double>(s, s->W, nullptr, true);
+}
+
+void enqueue_lo_smooth(cgks_solver *s) {
+  cudaMemcpyAsync(s->Wn, s->W, sizeof(double) * 4 * s->dm.nc, cudaMemcpyDeviceToDevice, s->stream);
+  if (s->mixed) { enqueue_lo_solve<float>(s); enqueue_prolong<float>(s); }
+  else { enqueue_lo_solve<double>(s); enqueue_prolong<double>(s); }
 }
 
 int ensure_hist(cgks_solver *s, int n) {
@@ -760,7 +861,7 @@ int capture(cgks_solver *s, bool cycle, cudaGraphExec_t *out) {
 long long count_launches(cgks_solver *s, bool cycle) {
   // number of kernels one cycle / step enqueues
   long long per_eval = 2;
-  long long hi = 1 + per_eval + 1 + (s->params.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
+  long long hi = per_eval + 1 + (s->params.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
   long long dt = 2;
   if (!cycle) return dt + hi + 1;
   long long lo = s->params.n_implicit * (3 + static_cast<long long>(s->sweep_colours.size())) +
@@ -789,6 +890,29 @@ void collect_timing(cgks_solver *s) {
   s->tev.clear();
 }
 
+template <typename T>
+void fill_params(const cgks_params *p, ParamsT<T> &P) {
+  double K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
+  P.gamma = static_cast<T>(p->gamma);
+  P.K = static_cast<T>(K);
+  P.mu = static_cast<T>(p->mu);
+  P.cfl_hi = static_cast<T>(p->cfl_hi);
+  P.cfl_lo = static_cast<T>(p->cfl_lo);
+  P.kc.K = static_cast<T>(K);
+  P.kc.c2K = static_cast<T>(2.0 / (K + 2.0));
+  P.kc.c4K = static_cast<T>(4.0 / (K + 2.0));
+  for (int b = 0; b < CGKS_MAX_BC; ++b) {
+    const cgks_bc &bc = p->bc[b];
+    P.bc_kind[b] = b < p->n_bc ? bc.kind : CGKS_BC_SLIP;
+    P.bc_uw[b][0] = static_cast<T>(bc.u_wall[0]);
+    P.bc_uw[b][1] = static_cast<T>(bc.u_wall[1]);
+    P.bc_rho[b] = static_cast<T>(bc.rho);
+    P.bc_u[b][0] = static_cast<T>(bc.u[0]);
+    P.bc_u[b][1] = static_cast<T>(bc.u[1]);
+    P.bc_p[b] = static_cast<T>(bc.p);
+  }
+}
+
 }  // namespace
 
 // =============================== C ABI ===================================
@@ -799,7 +923,7 @@ void cgks_default_params(cgks_params *p) {
   std::memset(p, 0, sizeof(*p));
   p->gamma = 1.4;
   p->mu = 0.0;
-  p->alpha = 4.0 / 3.0;
+  p->alpha = 0.5;
   p->cfl_hi = 0.4;
   p->cfl_lo = 1000.0;
   p->n_implicit = 6;
@@ -843,13 +967,20 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
   return CGKS_OK;
 }
 
-static size_t solver_bytes(int64_t nc, int64_t nf) {
-  size_t cells = 4 + 8 + 4 + 4 + 8 + 20 + 4 * 6 + 1 + 9;  // state + work + primitives
-  size_t geo_c = 4 + 3 + kNCol * kNM;                      // vol, 1/vol, per, 1/h, m2, op
-  size_t faces = 16 * 2 + 4 + 1 + 8 + 2 + 1 + 1 + 8;       // FA, FB, Flo, lam, E0/E1, fn, fS, fjump, fxi
-  size_t ints = 8 * nc + 2 * nf + nc;                      // cface, cnbr, fc0/fc1, perm
-  return sizeof(double) * ((cells + geo_c + 12) * nc + faces * nf + 2 * kMaxBlocksReduce + 16) + sizeof(int) * ints +
-         64 * 256 + sizeof(Scalars);
+// device bytes of a solver: FP64 state/accumulation + geometry + the flux
+// arrays in the flux type (doubles in FP64 mode, floats in mixed mode with
+// float mirrors of the state and of the geometry)
+static size_t solver_bytes(int64_t nc, int64_t nf, bool mixed) {
+  const size_t d_cells = 4 * 5 + 8 * 2 + 4 * 3 + 12 + 6 + 3 + kNCol * kNM;  // W..Wxs, U, Rp0, Src, stage, geometry, op
+  const size_t d_faces = 2 + 1 + 1 + 8;                                   // fn, fS, fjump, fxi
+  const size_t t_cells = 4 + 8 + 4 + 4 + 8 + 4 + 20 + D::NPRIM + 4 + 1 + 4;  // mirrors, coef, prim, Rk, invD, dU
+  const size_t t_faces = 16 * 2 + 4 + 1 + (mixed ? 0 : 8);               // FA, FB, Flo, lam, E0/E1
+  const size_t f_geo_c = mixed ? (1 + 1 + 3 + kNCol * kNM) : 0;          // float ivol, ih, m2, op
+  const size_t f_geo_f = mixed ? 12 : 0;
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  return sizeof(double) * (d_cells * nc + d_faces * nf) + tsz * (t_cells * nc + t_faces * nf) +
+         sizeof(float) * (f_geo_c * nc + f_geo_f * nf) + sizeof(int) * (8 * nc + 2 * nf + nc) +
+         sizeof(double) * (2 * ((nc + kCellBlock - 1) / kCellBlock) + 16) + 64 * 256 + sizeof(Scalars);
 }
 
 int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
@@ -859,7 +990,7 @@ int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
   out->n_bfaces = m->h.n_bfaces;
   out->n_colours = m->h.n_colours;
   out->dim = m->h.dim;
-  out->device_bytes = static_cast<int64_t>(solver_bytes(m->h.n_cells, m->h.n_faces));
+  out->device_bytes = static_cast<int64_t>(solver_bytes(m->h.n_cells, m->h.n_faces, false));
   return CGKS_OK;
 }
 
@@ -896,7 +1027,7 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   *out = nullptr;
   if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
       p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
-      p->n_bc > CGKS_MAX_BC || p->precision != CGKS_FP64)
+      p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED))
     return CGKS_EINVAL;
   for (int t : m->h.bface_tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
@@ -911,30 +1042,15 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   if (!s) return CGKS_ENOMEM;
   s->hm = m->h;
   s->params = *p;
+  s->mixed = p->precision == CGKS_MIXED;
   cudaGetDevice(&s->device);
   s->user_stream = static_cast<cudaStream_t>(p->stream);
   auto fail = [&](int rc) { cgks_solver_destroy(s); return rc; };
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
-  // parameters
-  DevParams &dp = s->dp;
-  dp.gamma = p->gamma;
-  dp.K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
-  dp.kc.K = dp.K;
-  dp.kc.c2K = 2.0 / (dp.K + 2.0);
-  dp.kc.c4K = 4.0 / (dp.K + 2.0);
-  dp.mu = p->mu;
-  dp.alpha = p->alpha;
-  dp.cfl_hi = p->cfl_hi;
-  dp.cfl_lo = p->cfl_lo;
-  dp.n_bc = p->n_bc;
-  for (int b = 0; b < CGKS_MAX_BC; ++b) {
-    const cgks_bc &bc = p->bc[b];
-    dp.bc_kind[b] = b < p->n_bc ? bc.kind : CGKS_BC_SLIP;
-    dp.bc_uw[b][0] = bc.u_wall[0]; dp.bc_uw[b][1] = bc.u_wall[1];
-    dp.bc_rho[b] = bc.rho; dp.bc_u[b][0] = bc.u[0]; dp.bc_u[b][1] = bc.u[1]; dp.bc_p[b] = bc.p;
-  }
+  fill_params(p, s->dp);
+  fill_params(p, s->fp);
   // operators depend on which tags are walls
   std::vector<char> wall(CGKS_MAX_BC, 0);
   for (int b = 0; b < p->n_bc; ++b) wall[b] = p->bc[b].kind != CGKS_BC_FARFIELD;
@@ -946,23 +1062,36 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   }
   const int64_t nc = s->hm.n_cells, nf = s->hm.n_faces;
   s->nblk_cell = nblk(static_cast<int>(nc), kCellBlock);
-  if (s->nblk_cell > kMaxBlocksReduce * 64) return fail(CGKS_EINVAL);
   // carve one arena
   struct Piece { void **dst; size_t bytes; };
   std::vector<Piece> pieces;
   auto D8 = [&](double **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(double) * cnt }); };
+  auto F4 = [&](float **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(float) * cnt }); };
   auto I4 = [&](int **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(int) * cnt }); };
   double *vol, *ivol, *per, *ih, *m2, *opd, *fn, *fS, *fjump, *fxi;
   int *cface, *cnbr, *fc0, *fc1;
   D8(&s->W, 4 * nc); D8(&s->Wx, 8 * nc); D8(&s->Wn, 4 * nc); D8(&s->Ws, 4 * nc); D8(&s->Wxs, 8 * nc);
-  D8(&s->coef, 20 * nc); D8(&s->FA, 16 * nf); D8(&s->FB, 16 * nf);
-  D8(&s->U, 4 * nc); D8(&s->dU, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc); D8(&s->Rk, 4 * nc);
-  D8(&s->invD, nc); D8(&s->Flo, 4 * nf); D8(&s->lam, nf); D8(&s->E0, 4 * nf); D8(&s->E1, 4 * nf);
-  D8(&s->prim, D::NPRIM * nc);
+  D8(&s->U, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc);
   D8(&s->partial, 2 * std::max(s->nblk_cell, 1)); D8(&s->last, 4); D8(&s->stage_aos, 12 * nc);
   D8(&vol, nc); D8(&ivol, nc); D8(&per, nc); D8(&ih, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
   D8(&fn, 2 * nf); D8(&fS, nf); D8(&fjump, nf); D8(&fxi, 8 * nf);
   I4(&cface, kMaxFace * nc); I4(&cnbr, kMaxFace * nc); I4(&fc0, nf); I4(&fc1, nf); I4(&s->perm, nc);
+  float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
+        *f_fjump = nullptr, *f_fxi = nullptr;
+  if (!s->mixed) {
+    Bufs<double> &B = s->bd;
+    D8(&B.coef, 20 * nc); D8(&B.FA, 16 * nf); D8(&B.FB, 16 * nf);
+    D8(&B.prim, D::NPRIM * nc); D8(&B.Flo, 4 * nf); D8(&B.lam, nf); D8(&B.E0, 4 * nf); D8(&B.E1, 4 * nf);
+    D8(&B.Rk, 4 * nc); D8(&B.invD, nc); D8(&B.dU, 4 * nc);
+  } else {
+    Bufs<float> &B = s->bf;
+    F4(&B.W, 4 * nc); F4(&B.Wx, 8 * nc); F4(&B.Wn, 4 * nc); F4(&B.Ws, 4 * nc); F4(&B.Wxs, 8 * nc); F4(&B.U, 4 * nc);
+    F4(&B.coef, 20 * nc); F4(&B.FA, 16 * nf); F4(&B.FB, 16 * nf);
+    F4(&B.prim, D::NPRIM * nc); F4(&B.Flo, 4 * nf); F4(&B.lam, nf);
+    F4(&B.Rk, 4 * nc); F4(&B.invD, nc); F4(&B.dU, 4 * nc);
+    F4(&f_ivol, nc); F4(&f_ih, nc); F4(&f_m2, 3 * nc); F4(&f_op, kNCol * kNM * nc);
+    F4(&f_fn, 2 * nf); F4(&f_fS, nf); F4(&f_fjump, nf); F4(&f_fxi, 8 * nf);
+  }
   pieces.push_back({ reinterpret_cast<void **>(&s->sc), sizeof(Scalars) });
   size_t total = 0;
   for (auto &pc : pieces) total += (pc.bytes + 255) & ~size_t(255);
@@ -973,6 +1102,10 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
     char *cur = static_cast<char *>(s->arena);
     for (auto &pc : pieces) { *pc.dst = cur; cur += (pc.bytes + 255) & ~size_t(255); }
   }
+  if (!s->mixed) {
+    Bufs<double> &B = s->bd;
+    B.W = s->W; B.Wx = s->Wx; B.Wn = s->Wn; B.Ws = s->Ws; B.Wxs = s->Wxs; B.U = s->U;
+  }
   auto up = [&](void *dst, const void *src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
   };
@@ -982,22 +1115,43 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   for (int64_t i = 0; i < nc; ++i) { h_ivol[i] = 1.0 / hm.vol[i]; h_ih[i] = 1.0 / hm.h[i]; }
   for (int64_t f = 0; f < nf; ++f) h_jump[f] = hm.fdelta[f] > 0.0 ? p->alpha / hm.fdelta[f] : 0.0;
   bool ok = up(vol, hm.vol.data(), 8 * nc) && up(ivol, h_ivol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) &&
-            up(ih, h_ih.data(), 8 * nc) &&
-            up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) && up(fn, hm.fn.data(), 8 * 2 * nf) &&
-            up(fS, hm.fS.data(), 8 * nf) && up(fjump, h_jump.data(), 8 * nf) && up(fxi, hm.fxi.data(), 8 * 8 * nf) &&
-            up(cface, hm.cface.data(), 4 * kMaxFace * nc) && up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) &&
-            up(fc0, hm.fc0.data(), 4 * nf) && up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc);
+            up(ih, h_ih.data(), 8 * nc) && up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) &&
+            up(fn, hm.fn.data(), 8 * 2 * nf) && up(fS, hm.fS.data(), 8 * nf) && up(fjump, h_jump.data(), 8 * nf) &&
+            up(fxi, hm.fxi.data(), 8 * 8 * nf) && up(cface, hm.cface.data(), 4 * kMaxFace * nc) &&
+            up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) && up(fc0, hm.fc0.data(), 4 * nf) &&
+            up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc);
+  std::vector<float> tmp;
+  auto upf = [&](float *dst, const double *src, size_t cnt) {
+    tmp.assign(src, src + cnt);
+    bool r = cudaMemcpyAsync(dst, tmp.data(), 4 * cnt, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
+    return r && cudaStreamSynchronize(s->stream) == cudaSuccess;   // tmp is reused
+  };
+  if (ok && s->mixed)
+    ok = upf(f_ivol, h_ivol.data(), nc) && upf(f_ih, h_ih.data(), nc) && upf(f_m2, hm.m2.data(), 3 * nc) &&
+         upf(f_op, op.data(), op.size()) && upf(f_fn, hm.fn.data(), 2 * nf) && upf(f_fS, hm.fS.data(), nf) &&
+         upf(f_fjump, h_jump.data(), nf) && upf(f_fxi, hm.fxi.data(), 8 * nf);
   if (!ok) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->W, 0, sizeof(double) * 12 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->Rp0, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  if (cudaMemsetAsync(s->dU, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (s->mixed) {
+    if (cudaMemsetAsync(s->bf.dU, 0, sizeof(float) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+    if (cudaMemsetAsync(s->bf.W, 0, sizeof(float) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+    if (cudaMemsetAsync(s->bf.Wx, 0, sizeof(float) * 8 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
+  } else if (cudaMemsetAsync(s->bd.dU, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) {
+    return fail(CGKS_ECUDA);
+  }
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  DevMesh &dm = s->dm;
+  MeshT<double> &dm = s->dm;
   dm.nc = static_cast<int>(nc); dm.nf = static_cast<int>(nf);
   dm.vol = vol; dm.ivol = ivol; dm.per = per; dm.ih = ih; dm.m2 = m2; dm.op = opd;
-  dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
   dm.fn = fn; dm.fS = fS; dm.fjump = fjump; dm.fxi = fxi;
+  dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
+  MeshT<float> &fm = s->fm;
+  fm.nc = dm.nc; fm.nf = dm.nf;
+  fm.vol = nullptr; fm.per = nullptr; fm.ivol = f_ivol; fm.ih = f_ih; fm.m2 = f_m2; fm.op = f_op;
+  fm.fn = f_fn; fm.fS = f_fS; fm.fjump = f_fjump; fm.fxi = f_fxi;
+  fm.cface = cface; fm.cnbr = cnbr; fm.fc0 = fc0; fm.fc1 = fc1;
   // Colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
   // C-1..0).  A colour repeated back to back recomputes identical values
   // (its cells read only other colours), and the first pass is done by
@@ -1026,7 +1180,9 @@ static int set_state_impl(cgks_solver *s, const double *W, const double *Wx, boo
   cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemcpyAsync(wa, W, sizeof(double) * 4 * n, kind, s->stream));
   if (Wx) CK(cudaMemcpyAsync(wxa, Wx, sizeof(double) * 8 * n, kind, s->stream));
-  k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, wa, Wx ? wxa : nullptr, s->W, s->Wx);
+  k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, wa, Wx ? wxa : nullptr, s->W, s->Wx,
+                                                                    s->mixed ? s->bf.W : nullptr,
+                                                                    s->mixed ? s->bf.Wx : nullptr);
   s->launches++;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(&s->sc->status, 0, sizeof(int), s->stream));
@@ -1117,14 +1273,8 @@ int cgks_loworder_smooth(cgks_solver *s) {
   if (s->status_cache) return CGKS_EDIVERGED;
   int rc = begin_call(s);
   if (rc) return rc;
-  const int n = s->dm.nc;
   CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
-  CK(cudaMemcpyAsync(s->Wn, s->W, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream));
-  enqueue_lo_solve(s);
-  launch(s, KI_PROLONG, k_prolong, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W, (const double *)s->Wn,
-         (const double *)s->U, s->sc, s->partial);
-  launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
-         s->hist_cap, s->last);
+  enqueue_lo_smooth(s);
   CK(cudaGetLastError());
   rc = read_status(s);
   if (s->timing) collect_timing(s);

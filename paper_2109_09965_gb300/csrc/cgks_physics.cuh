@@ -272,6 +272,30 @@ __device__ __forceinline__ void euler_flux(T gamma, const T W[NV], T nx, T ny, T
   F[3] = (W[3] + p) * un;
 }
 
+// F_n(U + dU) - F_n(U) of the Euler normal flux, written so that every
+// term is proportional to the increment (no cancellation between two
+// nearly equal fluxes): exact algebra, accurate to the working precision
+// relative to the difference itself.  Base state: conservative W, velocity
+// (u, v), pressure p; dW the increment; (nx, ny) the normal.
+template <typename T>
+__device__ __forceinline__ void euler_flux_delta(T gamma, const T W[NV], T u, T v, T p, const T dW[NV],
+                                                 T nx, T ny, T dF[NV]) {
+  const T rho = W[0], r1 = W[0] + dW[0];
+  const T inv = T(1) / (rho * r1);
+  const T mn = W[1] * nx + W[2] * ny, dmn = dW[1] * nx + dW[2] * ny;
+  const T un = u * nx + v * ny;
+  const T dun = (rho * dmn - mn * dW[0]) * inv;                       // (un)' - un
+  const T un1 = un + dun;
+  const T m2 = W[1] * W[1] + W[2] * W[2];
+  const T dm2 = T(2) * (W[1] * dW[1] + W[2] * dW[2]) + dW[1] * dW[1] + dW[2] * dW[2];
+  const T dke = T(0.5) * (rho * dm2 - m2 * dW[0]) * inv;              // d(|m|^2 / (2 rho))
+  const T dp = (gamma - T(1)) * (dW[3] - dke);
+  dF[0] = dmn;
+  dF[1] = dW[1] * un1 + W[1] * dun + dp * nx;
+  dF[2] = dW[2] * un1 + W[2] * dun + dp * ny;
+  dF[3] = (dW[3] + dp) * un1 + (W[3] + p) * dun;
+}
+
 // ---------------- boundary ghost states (local frame) ----------------
 // Wall velocity (wn, wt) and free stream (rho, un, ut, p) are given in the
 // face frame of the boundary face.

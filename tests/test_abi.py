@@ -92,4 +92,4 @@ def test_no_cpu_fallback_without_gpu(cg):
 def test_default_params(cg):
     P = cg.make_params({})
     assert P.gamma == 1.4 and P.cfl_lo == 1000.0 and P.n_implicit == 6 and P.n_sweeps == 2
-    assert abs(P.alpha - 4.0 / 3.0) < 1e-15 and P.use_graph == 1
+    assert P.alpha == 0.5 and P.use_graph == 1
