@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kCellBlock = 256;
 constexpr int kFaceBlock = 128;
+constexpr int kSweepBlock = 128;
 
 // status bits of the device status word
 constexpr int kBadState = 1;
@@ -54,6 +55,7 @@ struct MeshT {
   const T *vol, *ivol, *per, *ih, *m2;       // ih = 1/h; m2: [3][nc]
   const T *op;                               // [kNCol*kNM][nc]
   const T *fn, *fS, *fjump, *fxi;            // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
+  const T *snx, *sny, *shs;                  // [4][nc] per face slot: outward normal of the cell, S/2
   const int *cface, *cnbr;                   // [4][nc]
   const int *fc0, *fc1;
 };
@@ -65,7 +67,7 @@ struct Bufs {
   T *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr, *U = nullptr;
   T *coef = nullptr, *FA = nullptr, *FB = nullptr;
   T *prim = nullptr, *Flo = nullptr, *lam = nullptr, *E0 = nullptr, *E1 = nullptr;
-  T *Rk = nullptr, *invD = nullptr, *dU = nullptr;
+  T *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
 };
 
 struct Scalars {
@@ -484,19 +486,22 @@ template <typename TF>
 __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0_end,
                                                        const TF *__restrict__ Flo, const TF *__restrict__ lam,
                                                        const double *__restrict__ Rp0, double *__restrict__ Src,
-                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU) {
+                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
+                                                       TF *__restrict__ lamS) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
   const int n = m.nc, nf = m.nf;
   double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
   for (int s = 0; s < kMaxFace; ++s) {
     int fs = m.cface[s * n + i];
-    if (fs == kNoFace) continue;
+    if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
     int f = fs >= 0 ? fs : ~fs;
     double sg = fs >= 0 ? 1.0 : -1.0;
     double S = m.fS[f];
     for (int v = 0; v < 4; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
-    sum += static_cast<double>(lam[f]) * S;
+    TF l = lam[f];
+    lamS[s * n + i] = l;
+    sum += static_cast<double>(l) * S;
   }
   // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2
   const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
@@ -516,41 +521,53 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
 //   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
 // FP64: F_n(U_ip) from the face cache of this implicit step.  Mixed: the
 // difference F_n(U_ip + dU_ip) - F_n(U_ip) in the exact increment form.
+// All neighbour loads are issued up front (absent slots read the cell
+// itself and contribute nothing) so they overlap.
 template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int end,
-                                                      const T *__restrict__ U, const T *__restrict__ prim,
-                                                      const T *__restrict__ Rk, const T *__restrict__ invD,
-                                                      const T *__restrict__ lam, const T *__restrict__ E0,
-                                                      const T *__restrict__ E1, T *__restrict__ dU) {
+__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int end,
+                                                       const T *__restrict__ U, const T *__restrict__ prim,
+                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
+                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
+                                                       const T *__restrict__ E1, T *__restrict__ dU) {
   int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
   const int n = m.nc, nf = m.nf;
+  int jn[kMaxFace];
+#pragma unroll
+  for (int s = 0; s < kMaxFace; ++s) jn[s] = m.cnbr[s * n + i];
   T acc[4];
+#pragma unroll
   for (int v = 0; v < 4; ++v) acc[v] = Rk[v * n + i];
+#pragma unroll
   for (int s = 0; s < kMaxFace; ++s) {
-    int j = m.cnbr[s * n + i];
-    if (j < 0) continue;
-    int fs = m.cface[s * n + i];
-    bool is0 = fs >= 0;
-    int f = is0 ? fs : ~fs;
-    T sg = is0 ? T(1) : T(-1);
-    T nx = sg * m.fn[f], ny = sg * m.fn[nf + f], hS = T(0.5) * m.fS[f], lp = lam[f];
+    const bool ok = jn[s] >= 0;
+    const int j = ok ? jn[s] : i;
+    const T w = ok ? T(1) : T(0);
+    const T nx = m.snx[s * n + i], ny = m.sny[s * n + i], hS = w * m.shs[s * n + i], lp = lamS[s * n + i];
     T uj[4], du[4], dF[4];
+#pragma unroll
     for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
     if constexpr (is_f32<T>()) {
       D::euler_flux_delta(P.gamma, uj, prim[1 * n + j], prim[2 * n + j], prim[3 * n + j], du, nx, ny, dF);
+#pragma unroll
       for (int v = 0; v < 4; ++v) acc[v] -= hS * (dF[v] - lp * du[v]);
     } else {
-      T up[4], fa[4], fb;
+      const int fs = m.cface[s * n + i];
+      const bool is0 = fs >= 0;
+      const int f = ok ? (is0 ? fs : ~fs) : 0;
+      T up[4], fa[4];
+#pragma unroll
       for (int v = 0; v < 4; ++v) up[v] = uj[v] + du[v];
       D::euler_flux(P.gamma, up, nx, ny, fa);
+#pragma unroll
       for (int v = 0; v < 4; ++v) {
-        fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
         acc[v] -= hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
       }
     }
   }
   const T id = invD[i];
+#pragma unroll
   for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] * id;
 }
 
@@ -758,12 +775,12 @@ void enqueue_lo_solve(cgks_solver *s) {
     launch(s, KI_LOFACE, k_lo_face<TF>, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s),
            (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
     launch(s, KI_LORHS, k_lo_rhs<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0, c0_end,
-           (const TF *)B.Flo, (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU);
+           (const TF *)B.Flo, (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU, B.lamS);
     for (int c : s->sweep_colours) {
       int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
-      launch(s, KI_SWEEP, k_sweep<TF>, dim3(nblk(e - b, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s),
-             b, e, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD, (const TF *)B.lam,
-             (const TF *)B.E0, (const TF *)B.E1, B.dU);
+      launch(s, KI_SWEEP, k_sweep<TF>, dim3(nblk(e - b, kSweepBlock)), dim3(kSweepBlock), fmesh<TF>(s),
+             fparams<TF>(s), b, e, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
+             (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, B.dU);
     }
   }
   // U^{n_implicit} = U + dU of the last step
@@ -973,12 +990,13 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
 static size_t solver_bytes(int64_t nc, int64_t nf, bool mixed) {
   const size_t d_cells = 4 * 5 + 8 * 2 + 4 * 3 + 12 + 6 + 3 + kNCol * kNM;  // W..Wxs, U, Rp0, Src, stage, geometry, op
   const size_t d_faces = 2 + 1 + 1 + 8;                                   // fn, fS, fjump, fxi
+  const size_t d_slots = 3 * kMaxFace;                                    // slot normals, S/2
   const size_t t_cells = 4 + 8 + 4 + 4 + 8 + 4 + 20 + D::NPRIM + 4 + 1 + 4;  // mirrors, coef, prim, Rk, invD, dU
   const size_t t_faces = 16 * 2 + 4 + 1 + (mixed ? 0 : 8);               // FA, FB, Flo, lam, E0/E1
-  const size_t f_geo_c = mixed ? (1 + 1 + 3 + kNCol * kNM) : 0;          // float ivol, ih, m2, op
+  const size_t f_geo_c = mixed ? (1 + 1 + 3 + kNCol * kNM + 3 * kMaxFace) : 0;  // float ivol, ih, m2, op, slots
   const size_t f_geo_f = mixed ? 12 : 0;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
-  return sizeof(double) * (d_cells * nc + d_faces * nf) + tsz * (t_cells * nc + t_faces * nf) +
+  return sizeof(double) * ((d_cells + d_slots) * nc + d_faces * nf) + tsz * ((t_cells + kMaxFace) * nc + t_faces * nf) +
          sizeof(float) * (f_geo_c * nc + f_geo_f * nf) + sizeof(int) * (8 * nc + 2 * nf + nc) +
          sizeof(double) * (2 * ((nc + kCellBlock - 1) / kCellBlock) + 16) + 64 * 256 + sizeof(Scalars);
 }
@@ -1068,29 +1086,31 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   auto D8 = [&](double **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(double) * cnt }); };
   auto F4 = [&](float **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(float) * cnt }); };
   auto I4 = [&](int **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(int) * cnt }); };
-  double *vol, *ivol, *per, *ih, *m2, *opd, *fn, *fS, *fjump, *fxi;
+  double *vol, *ivol, *per, *ih, *m2, *opd, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs;
   int *cface, *cnbr, *fc0, *fc1;
   D8(&s->W, 4 * nc); D8(&s->Wx, 8 * nc); D8(&s->Wn, 4 * nc); D8(&s->Ws, 4 * nc); D8(&s->Wxs, 8 * nc);
   D8(&s->U, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc);
   D8(&s->partial, 2 * std::max(s->nblk_cell, 1)); D8(&s->last, 4); D8(&s->stage_aos, 12 * nc);
   D8(&vol, nc); D8(&ivol, nc); D8(&per, nc); D8(&ih, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
   D8(&fn, 2 * nf); D8(&fS, nf); D8(&fjump, nf); D8(&fxi, 8 * nf);
+  D8(&snx, kMaxFace * nc); D8(&sny, kMaxFace * nc); D8(&shs, kMaxFace * nc);
   I4(&cface, kMaxFace * nc); I4(&cnbr, kMaxFace * nc); I4(&fc0, nf); I4(&fc1, nf); I4(&s->perm, nc);
   float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
-        *f_fjump = nullptr, *f_fxi = nullptr;
+        *f_fjump = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr;
   if (!s->mixed) {
     Bufs<double> &B = s->bd;
     D8(&B.coef, 20 * nc); D8(&B.FA, 16 * nf); D8(&B.FB, 16 * nf);
     D8(&B.prim, D::NPRIM * nc); D8(&B.Flo, 4 * nf); D8(&B.lam, nf); D8(&B.E0, 4 * nf); D8(&B.E1, 4 * nf);
-    D8(&B.Rk, 4 * nc); D8(&B.invD, nc); D8(&B.dU, 4 * nc);
+    D8(&B.Rk, 4 * nc); D8(&B.invD, nc); D8(&B.dU, 4 * nc); D8(&B.lamS, kMaxFace * nc);
   } else {
     Bufs<float> &B = s->bf;
     F4(&B.W, 4 * nc); F4(&B.Wx, 8 * nc); F4(&B.Wn, 4 * nc); F4(&B.Ws, 4 * nc); F4(&B.Wxs, 8 * nc); F4(&B.U, 4 * nc);
     F4(&B.coef, 20 * nc); F4(&B.FA, 16 * nf); F4(&B.FB, 16 * nf);
     F4(&B.prim, D::NPRIM * nc); F4(&B.Flo, 4 * nf); F4(&B.lam, nf);
-    F4(&B.Rk, 4 * nc); F4(&B.invD, nc); F4(&B.dU, 4 * nc);
+    F4(&B.Rk, 4 * nc); F4(&B.invD, nc); F4(&B.dU, 4 * nc); F4(&B.lamS, kMaxFace * nc);
     F4(&f_ivol, nc); F4(&f_ih, nc); F4(&f_m2, 3 * nc); F4(&f_op, kNCol * kNM * nc);
     F4(&f_fn, 2 * nf); F4(&f_fS, nf); F4(&f_fjump, nf); F4(&f_fxi, 8 * nf);
+    F4(&f_snx, kMaxFace * nc); F4(&f_sny, kMaxFace * nc); F4(&f_shs, kMaxFace * nc);
   }
   pieces.push_back({ reinterpret_cast<void **>(&s->sc), sizeof(Scalars) });
   size_t total = 0;
@@ -1114,12 +1134,26 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   std::vector<double> h_ivol(nc), h_ih(nc), h_jump(nf);
   for (int64_t i = 0; i < nc; ++i) { h_ivol[i] = 1.0 / hm.vol[i]; h_ih[i] = 1.0 / hm.h[i]; }
   for (int64_t f = 0; f < nf; ++f) h_jump[f] = hm.fdelta[f] > 0.0 ? p->alpha / hm.fdelta[f] : 0.0;
+  // per face slot: the cell's outward unit normal and half the face length
+  std::vector<double> h_snx(kMaxFace * nc, 0.0), h_sny(kMaxFace * nc, 0.0), h_shs(kMaxFace * nc, 0.0);
+  for (int64_t i = 0; i < nc; ++i)
+    for (int sl = 0; sl < kMaxFace; ++sl) {
+      int32_t fs = hm.cface[sl * nc + i];
+      if (fs == kNoFace) continue;
+      int32_t f = fs >= 0 ? fs : ~fs;
+      double sg = fs >= 0 ? 1.0 : -1.0;
+      h_snx[sl * nc + i] = sg * hm.fn[f];
+      h_sny[sl * nc + i] = sg * hm.fn[nf + f];
+      h_shs[sl * nc + i] = 0.5 * hm.fS[f];
+    }
   bool ok = up(vol, hm.vol.data(), 8 * nc) && up(ivol, h_ivol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) &&
             up(ih, h_ih.data(), 8 * nc) && up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) &&
             up(fn, hm.fn.data(), 8 * 2 * nf) && up(fS, hm.fS.data(), 8 * nf) && up(fjump, h_jump.data(), 8 * nf) &&
             up(fxi, hm.fxi.data(), 8 * 8 * nf) && up(cface, hm.cface.data(), 4 * kMaxFace * nc) &&
             up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) && up(fc0, hm.fc0.data(), 4 * nf) &&
-            up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc);
+            up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc) &&
+            up(snx, h_snx.data(), 8 * kMaxFace * nc) && up(sny, h_sny.data(), 8 * kMaxFace * nc) &&
+            up(shs, h_shs.data(), 8 * kMaxFace * nc);
   std::vector<float> tmp;
   auto upf = [&](float *dst, const double *src, size_t cnt) {
     tmp.assign(src, src + cnt);
@@ -1129,7 +1163,9 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   if (ok && s->mixed)
     ok = upf(f_ivol, h_ivol.data(), nc) && upf(f_ih, h_ih.data(), nc) && upf(f_m2, hm.m2.data(), 3 * nc) &&
          upf(f_op, op.data(), op.size()) && upf(f_fn, hm.fn.data(), 2 * nf) && upf(f_fS, hm.fS.data(), nf) &&
-         upf(f_fjump, h_jump.data(), nf) && upf(f_fxi, hm.fxi.data(), 8 * nf);
+         upf(f_fjump, h_jump.data(), nf) && upf(f_fxi, hm.fxi.data(), 8 * nf) &&
+         upf(f_snx, h_snx.data(), kMaxFace * nc) && upf(f_sny, h_sny.data(), kMaxFace * nc) &&
+         upf(f_shs, h_shs.data(), kMaxFace * nc);
   if (!ok) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaMemsetAsync(s->W, 0, sizeof(double) * 12 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
@@ -1145,12 +1181,12 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   MeshT<double> &dm = s->dm;
   dm.nc = static_cast<int>(nc); dm.nf = static_cast<int>(nf);
   dm.vol = vol; dm.ivol = ivol; dm.per = per; dm.ih = ih; dm.m2 = m2; dm.op = opd;
-  dm.fn = fn; dm.fS = fS; dm.fjump = fjump; dm.fxi = fxi;
+  dm.fn = fn; dm.fS = fS; dm.fjump = fjump; dm.fxi = fxi; dm.snx = snx; dm.sny = sny; dm.shs = shs;
   dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
   MeshT<float> &fm = s->fm;
   fm.nc = dm.nc; fm.nf = dm.nf;
   fm.vol = nullptr; fm.per = nullptr; fm.ivol = f_ivol; fm.ih = f_ih; fm.m2 = f_m2; fm.op = f_op;
-  fm.fn = f_fn; fm.fS = f_fS; fm.fjump = f_fjump; fm.fxi = f_fxi;
+  fm.fn = f_fn; fm.fS = f_fS; fm.fjump = f_fjump; fm.fxi = f_fxi; fm.snx = f_snx; fm.sny = f_sny; fm.shs = f_shs;
   fm.cface = cface; fm.cnbr = cnbr; fm.fc0 = fc0; fm.fc1 = fc1;
   // Colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
   // C-1..0).  A colour repeated back to back recomputes identical values
