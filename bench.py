@@ -193,35 +193,14 @@ def config_block(mesh, args):
             "l2": "flushed between timed steps (256 MiB write, outside the per-step events)"}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--scheme", default="S1O2", choices=["S1O2", "S2O4"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-
+def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm, hbm_src, with_e2e):
+    """Device-timed K V-cycles (per-step events, L2 flushed between steps),
+    a per-kernel timing pass, and optionally the end-to-end C-ABI run."""
     import torch
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    from paper_2109_09965_gb300 import cgks
-    cgks.lib()
-    mesh, spec, W0 = workload()
-    spec = dict(spec, time_scheme=args.scheme, precision=args.precision)
-    gm = cgks.Mesh(mesh)
-    solver = cgks.Solver(gm, spec)
+    sp = dict(spec, precision=precision)
+    solver = cgks.Solver(gm, sp)
     solver.set_state(W0)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
-
-    # ---- device-resident timing: K V-cycles, per-step events, L2 flushed between
     for _ in range(args.warmup):
         solver.pmg_cycle(1, record=False)
     torch.cuda.synchronize()
@@ -243,7 +222,7 @@ def main():
     value = world * mesh.n_cells * args.steps / (ms / 1000.0)
     res, _ = solver.residual()
 
-    # ---- per-kernel timing pass (events around every launch, same K cycles)
+    # per-kernel timing pass (events around every launch, same K cycles)
     solver.set_timing(True)
     solver.reset_timing()
     for k in range(args.steps):
@@ -253,40 +232,83 @@ def main():
     kt = solver.timing()
     solver.set_timing(False)
     total_k = sum(v[0] for v in kt.values())
-    top = max(kt, key=lambda k: kt[k][0])
+    wm = work_model(mesh, gm, sp, precision)
+    roof, per_gbs = roofline(kt, wm, precision, hbm, hbm_src, args.steps)
+    kernels = {k: dict({"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]},
+                       **per_gbs.get(k, {}))
+               for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0}
+    out = {"value": value, "ms": ms, "launches": int(launches), "clocks": clk.summary(), "roof": roof,
+           "kernels": kernels, "res": res}
+    if with_e2e:
+        # end to end through the C ABI with pinned host buffers
+        Wh = torch.from_numpy(W0.copy()).pin_memory()
+        Xh = torch.zeros((mesh.n_cells, 2, 4), dtype=torch.float64).pin_memory()
+        Wout = torch.zeros((mesh.n_cells, 4), dtype=torch.float64).pin_memory()
+        resh = np.zeros(1)
+        Wn, Xn = Wh.numpy(), Xh.numpy()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            cgks.lib().cgks_set_state(solver._h, Wn.ctypes.data, Xn.ctypes.data)
+            cgks.lib().cgks_pmg_cycle(solver._h, 1, resh.ctypes.data)
+            cgks.lib().cgks_get_state(solver._h, Wout.numpy().ctypes.data, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = dist_max(e0.elapsed_time(e1), world)
+        out["e2e"] = {"value": world * mesh.n_cells * args.steps / (e2e_ms / 1000.0), "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": 12 * 8 * mesh.n_cells, "d2h_bytes_per_step": 4 * 8 * mesh.n_cells + 8}
+    solver.close()
+    return out
 
-    # ---- end to end through the C ABI with pinned host buffers
-    Wh = torch.from_numpy(W0.copy()).pin_memory()
-    Xh = torch.zeros((mesh.n_cells, 2, 4), dtype=torch.float64).pin_memory()
-    Wout = torch.zeros((mesh.n_cells, 4), dtype=torch.float64).pin_memory()
-    resh = np.zeros(1)
-    Wn, Xn = Wh.numpy(), Xh.numpy()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
-        cgks.lib().cgks_set_state(solver._h, Wn.ctypes.data, Xn.ctypes.data)
-        cgks.lib().cgks_pmg_cycle(solver._h, 1, resh.ctypes.data)
-        cgks.lib().cgks_get_state(solver._h, Wout.numpy().ctypes.data, None)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = dist_max(e0.elapsed_time(e1), world)
-    e2e = {"value": world * mesh.n_cells * args.steps / (e2e_ms / 1000.0), "unit": "cell-updates/s",
-           "h2d_bytes_per_step": 12 * 8 * mesh.n_cells, "d2h_bytes_per_step": 4 * 8 * mesh.n_cells + 8}
 
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scheme", default="S1O2", choices=["S1O2", "S2O4"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant of the line")
+    ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2109_09965_gb300 import cgks
+    cgks.lib()
+    mesh, spec, W0 = workload()
+    spec = dict(spec, time_scheme=args.scheme)
+    gm = cgks.Mesh(mesh)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    hbm, hbm_src = peaks()
+    m = measure(cgks, gm, mesh, spec, W0, args, args.precision, world, local, flush, hbm, hbm_src,
+                with_e2e=True)
+    variants = {}
+    if args.precision == "fp64" and not args.no_variants:
+        mv = measure(cgks, gm, mesh, spec, W0, args, "mixed", world, local, flush, hbm, hbm_src, with_e2e=False)
+        variants["mixed"] = {"value": mv["value"], "ms_per_step": mv["ms"] / args.steps, "dtype": "f32+f64",
+                             "gpu_launches": mv["launches"], "roofline": mv["roof"], "kernels": mv["kernels"],
+                             "clocks": mv["clocks"],
+                             "note": "FP32 reconstruction, fluxes and sweeps; FP64 accumulation, diagonal "
+                                     "inversion and residual norms; same workload and step"}
     if rank != 0:
         return
-    hbm, hbm_src = peaks()
-    roof = roofline(top, kt, mesh, gm, hbm, hbm_src)
-    line = {"metric": BASELINE_METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    line = {"metric": BASELINE_METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic", "config": config_block(mesh, args), "e2e": e2e,
-            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
-            "kernels": {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]}
-                        for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0},
-            "residual_last": res}
+            "data": "synthetic", "config": config_block(mesh, args), "e2e": m["e2e"],
+            "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roof"],
+            "kernels": m["kernels"], "residual_last": m["res"]}
+    if variants:
+        line["variants"] = variants
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, spec, W0)
     if args.converge:
@@ -294,25 +316,104 @@ def main():
     print(json.dumps(line), flush=True)
 
 
-# Algorithmic work per launch of each kernel (FP64 operation counts and
-# compulsory bytes; see the design doc for the derivation).
-FLOPS_PER_GAUSS_POINT = 1169          # smooth GKS flux incl. reconstruction evaluation, one side pair
-FP64_PEAK_TFLOPS = 1.25               # nominal FP64 of GB300 (2 FMA / clk / SM x 152 SM x ~2.06 GHz)
 
 
-def roofline(top, kt, mesh, gm, hbm, hbm_src):
-    ms, n = kt[top]
-    per_launch_s = ms / max(n, 1) / 1000.0
-    if top == "k_face":
-        flops = FLOPS_PER_GAUSS_POINT * 2 * gm.n_faces
-        ach = flops / per_launch_s / 1e12
-        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+def topology(mesh, gm):
+    """Interior-neighbour count per cell and colour per cell (caller order)."""
+    edges = {}
+    for c in range(mesh.n_cells):
+        nodes = mesh.cell_nodes[mesh.cell_ptr[c]:mesh.cell_ptr[c + 1]]
+        for k in range(len(nodes)):
+            e = (min(nodes[k], nodes[(k + 1) % len(nodes)]), max(nodes[k], nodes[(k + 1) % len(nodes)]))
+            edges.setdefault(e, []).append(c)
+    nb = np.zeros(mesh.n_cells, np.int64)
+    nbrs = [[] for _ in range(mesh.n_cells)]
+    for cs in edges.values():
+        if len(cs) == 2:
+            nb[cs[0]] += 1
+            nb[cs[1]] += 1
+            nbrs[cs[0]].append(cs[1])
+            nbrs[cs[1]].append(cs[0])
+    _, colour = gm.ordering()
+    n_int = sum(1 for cs in edges.values() if len(cs) == 2)
+    return nb, nbrs, np.asarray(colour), n_int, len(edges)
+
+
+# FP64 operations (add, mul, div each 1) of the relaxation term of one
+# interior neighbour: U + dU (4), Euler normal flux (23), the bracket
+# ((F - F_cache) - lambda (U + dU - U)) scaled by S/2 and accumulated (24),
+# S/2 weight (1); plus 4 multiplications by 1/D per cell.
+SWEEP_FLOPS_PER_NEIGHBOUR = 52
+SWEEP_FLOPS_PER_CELL = 4
+FP64_PEAK_TFLOPS = 1.25    # GB300: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 flops (recipe table)
+
+
+def work_model(mesh, gm, spec, precision):
+    """Algorithmic work per V-cycle of each kernel: FP64 flops of the
+    sweep, compulsory bytes of every kernel (each array element read or
+    written once per launch; words of 8 B in FP64, 4 B for the float
+    arrays of the mixed path)."""
+    nb, nbrs, colour, n_int, n_faces = topology(mesh, gm)
+    n, F = mesh.n_cells, n_faces
+    C = int(colour.max()) + 1
+    seq = []
+    for _ in range(spec["n_sweeps"]):
+        for c in list(range(C)) + list(range(C - 1, -1, -1)):
+            if not seq or seq[-1] != c:
+                seq.append(c)
+    seq = seq[1:]
+    ni = spec["n_implicit"]
+    w = 8 if precision == "fp64" else 4
+    by_c = {}
+    for c in range(C):
+        cells = np.nonzero(colour == c)[0]
+        slots = int(nb[cells].sum())
+        uniq = len({j for i in cells for j in nbrs[i]})
+        flops = SWEEP_FLOPS_PER_NEIGHBOUR * slots + SWEEP_FLOPS_PER_CELL * len(cells)
+        own = len(cells) * 9 * w
+        per_slot = slots * (4 + 4 * w + (4 + 4 * w if precision == "fp64" else 0))
+        nbr = uniq * (8 * w + (3 * w if precision == "mixed" else 0))
+        by_c[c] = (flops, own + per_slot + nbr)
+    sweep_flops = ni * sum(by_c[c][0] for c in seq)
+    sweep_bytes = ni * sum(by_c[c][1] for c in seq)
+    d = 8
+    bytes_ = {
+        "k_sweep": sweep_bytes,
+        # W, Wx of every cell, operator (14 x 5), coef written (20), connectivity
+        "k_recon": n * ((12 + 70 + 20) * w + 32),
+        # per cell coef + W + 1/h + second moments; per face geometry, flux sums written
+        "k_face": n * 28 * w + F * (27 * w + 12),
+        # face sums read once (16 in S1O2, 4 in the residual mode), geometry, W in, W/Wx out
+        "k_update": F * (16 + 4) * w + F * 3 * d + n * (16 + 2 * 4 * d + 2 * 8 * d),
+        "k_lo_face": ni * (n * 13 * w + F * (5 * w + 3 * w + 12 + (8 * w if precision == "fp64" else 0))),
+        "k_lo_rhs": ni * (F * 6 * w + n * (16 + 4 * d + 13 * w + 4 * w)),
+        "k_lo_cell": (ni + 1) * n * (8 * d + 4 * w + 9 * w),
+        "k_prolong": n * (4 * 3 + 4) * d,
+    }
+    return {"sweep_flops": sweep_flops, "bytes": bytes_, "colours": C, "sweep_launches": ni * len(seq)}
+
+
+def roofline(kt, wm, precision, hbm, hbm_src, steps):
+    """Roofline entry of the dominant kernel and achieved GB/s of all."""
+    per = {}
+    for k, (ms, cnt) in kt.items():
+        if cnt == 0 or k not in wm["bytes"]:
+            continue
+        s = ms / 1000.0 / steps
+        per[k] = {"gbs": wm["bytes"][k] / s / 1e9, "frac_hbm": wm["bytes"][k] / s / 1e9 / hbm}
+    top = max(kt, key=lambda k: kt[k][0])
+    s_top = kt[top][0] / 1000.0 / steps
+    if top == "k_sweep" and precision == "fp64":
+        ach = wm["sweep_flops"] / s_top / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300 (recipe table); see DESIGN.md"}
-    bytes_per_launch = {"k_sweep": 8 * (4 * 4 + 4 + 1) * mesh.n_cells / 4}.get(top, 0.0)
-    ach = bytes_per_launch / per_launch_s / 1e9
-    return {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "peak_source": hbm_src}
+                "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
+                               "1.197 TFLOP/s)"}
+    else:
+        ach = wm["bytes"].get(top, 0.0) / s_top / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    return roof, per
 
 
 def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=100000):

@@ -180,6 +180,73 @@ int cgks_get_rp0(cgks_solver *s, double *Rp0);
 
 const char *cgks_strerror(int status);
 
+/* ---- serving: many steady solves advanced together (no counterpart in
+ * the paper; the per-solve arithmetic is the V-cycle above) ----
+ * A server keeps every admitted solve's state on the device and advances
+ * all of them with one batched V-cycle per cgks_server_step: their cells
+ * and faces are concatenated into one index space (each solve's cells
+ * padded to a multiple of 256), so every kernel of the cycle runs once for
+ * the whole batch.  Requests are admitted first-come-first-served while the
+ * sum of their device footprints stays within hbm_budget and fewer than
+ * max_active are running; a solve retires when its density residual Res
+ * (Section 4) has dropped by res_drop relative to its first cycle, when it
+ * reaches max_cycles, or when it diverges.  Each solve's arithmetic is
+ * identical to running it alone with cgks_pmg_cycle. */
+typedef struct cgks_server cgks_server;
+
+typedef struct {
+  int32_t precision;     /* CGKS_FP64 or CGKS_MIXED for every solve */
+  int32_t time_scheme;   /* CGKS_S1O2 or CGKS_S2O4 */
+  double cfl_hi, cfl_lo; /* shared by all solves */
+  int32_t n_implicit, n_sweeps;
+  int32_t max_active;    /* solves per batch */
+  int32_t max_cycles;    /* retire unconverged solves after this many cycles */
+  int32_t use_graph;
+  int32_t pad_;
+  void *stream;          /* cudaStream_t (NULL = default) */
+  cgks_alloc_fn alloc;
+  cgks_free_fn free;
+  void *alloc_ctx;
+} cgks_server_opts;
+
+enum { CGKS_REQ_QUEUED = 0, CGKS_REQ_ACTIVE = 1, CGKS_REQ_CONVERGED = 2, CGKS_REQ_STOPPED = 3,
+       CGKS_REQ_DIVERGED = 4, CGKS_REQ_REJECTED = 5 };
+
+typedef struct {
+  int32_t state;         /* CGKS_REQ_* */
+  int32_t cycles;        /* V-cycles run */
+  double res_first, res_last;
+  double t_submit, t_admit, t_done;  /* seconds on the server's steady clock */
+  int64_t n_cells;
+} cgks_req_status;
+
+/* Fill opts with defaults (FP64, S1O2, CFL 0.4 / 1000, 6 x 2, 64 active,
+ * 20000 cycles, graphs on). */
+void cgks_server_default_opts(cgks_server_opts *o);
+int cgks_server_create(size_t hbm_budget, const cgks_server_opts *opts, cgks_server **out);
+/* Queue a request.  The mesh and W0 ([n_cells*4], caller order, host) are
+ * copied; p supplies gamma, mu, alpha and the boundary conditions (the
+ * batch-wide fields come from the server options).  A request whose
+ * footprint alone exceeds the budget is rejected (CGKS_EBUDGET); so are
+ * the requests of a batch the server fails to allocate (the step that
+ * tried returns the error). */
+int cgks_server_submit(cgks_server *srv, const cgks_mesh *m, const cgks_params *p, const double *W0,
+                       double res_drop, int64_t *req_id);
+/* Retire finished solves, admit queued ones, run one batched V-cycle.
+ * *n_active (may be NULL) receives the number of solves that ran. */
+int cgks_server_step(cgks_server *srv, int32_t *n_active);
+/* Status of a request; W_out (host [n_cells*4], may be NULL) receives the
+ * final state once the request is done.  timeout_ms > 0: keep stepping the
+ * server until the request is done or the time is up (CGKS_ETIMEOUT). */
+int cgks_server_poll(cgks_server *srv, int64_t req_id, cgks_req_status *st, double *W_out, int timeout_ms);
+/* Device bytes a request on mesh m counts against the budget: its share of
+ * a batch's arena, its residual history and the stash that carries its
+ * state across batch rebuilds. */
+int cgks_server_footprint(const cgks_server *srv, const cgks_mesh *m, int64_t *bytes);
+/* Bytes of device memory the active batch holds, and queued / active counts. */
+int cgks_server_info(cgks_server *srv, int64_t *device_bytes, int32_t *n_queued, int32_t *n_active);
+int cgks_server_destroy(cgks_server *srv);
+
 /* ---- instrumentation (no counterpart in the paper) ----
  * Per-kernel timers: while on, every kernel launch of this solver is
  * bracketed by CUDA events on the library's stream and CUDA graphs are

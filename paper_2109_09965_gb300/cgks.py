@@ -311,3 +311,112 @@ class Solver:
 
     def launches_per_call(self, cycle: bool) -> int:
         return int(lib().cgks_launches_per_call(self._h, int(bool(cycle))))
+
+
+# ---------------------------------------------------------------- serving
+class CgksServerOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("time_scheme", C.c_int32), ("cfl_hi", C.c_double),
+                ("cfl_lo", C.c_double), ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32),
+                ("max_active", C.c_int32), ("max_cycles", C.c_int32), ("use_graph", C.c_int32),
+                ("pad_", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class CgksReqStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("cycles", C.c_int32), ("res_first", C.c_double),
+                ("res_last", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("n_cells", C.c_int64)]
+
+
+REQ_STATES = {0: "queued", 1: "active", 2: "converged", 3: "stopped", 4: "diverged", 5: "rejected"}
+
+SIGNATURES.update({
+    "cgks_server_default_opts": (None, [C.POINTER(CgksServerOpts)]),
+    "cgks_server_create": (C.c_int, [C.c_size_t, C.POINTER(CgksServerOpts), C.POINTER(C.c_void_p)]),
+    "cgks_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(CgksParams), _dp, C.c_double,
+                                     C.POINTER(C.c_int64)]),
+    "cgks_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "cgks_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(CgksReqStatus), C.c_void_p, C.c_int]),
+    "cgks_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
+    "cgks_server_footprint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "cgks_server_destroy": (C.c_int, [C.c_void_p]),
+})
+
+
+class Server:
+    """Continuous batching of steady solves: submit requests, step the
+    server (one batched V-cycle per step), poll for finished states."""
+
+    def __init__(self, hbm_budget: int, precision="fp64", time_scheme="S1O2", max_active=64,
+                 max_cycles=20000, use_torch: bool = True, **kw):
+        L = lib()
+        o = CgksServerOpts()
+        L.cgks_server_default_opts(C.byref(o))
+        o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+        o.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[time_scheme]
+        o.max_active, o.max_cycles = int(max_active), int(max_cycles)
+        for key in ("cfl_hi", "cfl_lo"):
+            if key in kw:
+                setattr(o, key, float(kw[key]))
+        for key in ("n_implicit", "n_sweeps", "use_graph"):
+            if key in kw:
+                setattr(o, key, int(kw[key]))
+        self._alloc = None
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("libcgks needs a CUDA device; none is available")
+            self._alloc = TorchAllocator()
+            o.stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+            o.alloc, o.free, o.alloc_ctx = self._alloc.alloc_fn, self._alloc.free_fn, None
+        self.opts = o
+        self.n_cells = {}
+        h = C.c_void_p()
+        _check(L.cgks_server_create(int(hbm_budget), C.byref(o), C.byref(h)), "cgks_server_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cgks_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def submit(self, mesh: Mesh, spec: dict, W0, res_drop: float) -> int:
+        """Queue a solve; returns its id.  Raises CgksError(-7) when the
+        request alone exceeds the budget (the id is then still pollable)."""
+        P = make_params(spec)
+        W0 = np.ascontiguousarray(W0, np.float64).reshape(-1)
+        rid = C.c_int64(0)
+        rc = lib().cgks_server_submit(self._h, mesh._h, C.byref(P), W0, float(res_drop), C.byref(rid))
+        self.n_cells[rid.value] = mesh.n_cells
+        _check(rc, "cgks_server_submit")
+        return rid.value
+
+    def step(self) -> int:
+        n = C.c_int32(0)
+        _check(lib().cgks_server_step(self._h, C.byref(n)), "cgks_server_step")
+        return n.value
+
+    def poll(self, rid: int, timeout_ms: int = 0, want_state=True):
+        """(status dict, W or None).  With timeout_ms > 0 the server is
+        stepped until the request is done (CgksError -6 on timeout)."""
+        st = CgksReqStatus()
+        W = np.zeros((self.n_cells[rid], 4)) if want_state else None
+        _check(lib().cgks_server_poll(self._h, int(rid), C.byref(st), _ptr(W), int(timeout_ms)),
+               "cgks_server_poll")
+        d = {k: getattr(st, k) for k, _ in CgksReqStatus._fields_}
+        d["state"] = REQ_STATES[st.state]
+        done = d["state"] in ("converged", "stopped", "diverged", "rejected")
+        return d, (W if done and d["state"] != "rejected" else None)
+
+    def footprint(self, mesh: Mesh) -> int:
+        b = C.c_int64(0)
+        _check(lib().cgks_server_footprint(self._h, mesh._h, C.byref(b)), "cgks_server_footprint")
+        return b.value
+
+    def info(self):
+        b, q, a = C.c_int64(0), C.c_int32(0), C.c_int32(0)
+        _check(lib().cgks_server_info(self._h, C.byref(b), C.byref(q), C.byref(a)), "cgks_server_info")
+        return dict(device_bytes=b.value, n_queued=q.value, n_active=a.value)

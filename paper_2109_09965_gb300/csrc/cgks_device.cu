@@ -1,64 +1,35 @@
-// libcgks device runtime: kernels of the high-order level (compact
-// reconstruction, gas-kinetic face flux, S1O2 / S2O4 update with
-// Gauss-Green gradients), of the low-order level (KFVS residual, L-F
-// diagonal, coloured point relaxation) and of the two-level V-cycle of
-// Ji, Shyy & Xu (arXiv:2109.09965), plus the C ABI declared in cgks.h.
+// libcgks device runtime and C ABI.
 //
-// Layout: structure-of-arrays in the library's cell order (colour-major,
-// reverse Cuthill-McKee inside a colour).  One thread per cell or face.
-// The cell update gathers the face sums through each cell's face slots
-// (no atomics, deterministic); reductions use a fixed block tree.
-//
-// Precision: kernels that evaluate fluxes are templated on the flux type
-// TF.  FP64 mode runs everything in double.  Mixed mode keeps the
-// conservative variables (W, W_x, U) and every accumulation into them, the
-// residuals and the diagonal inversion in double, and runs reconstruction,
-// face fluxes and relaxation sweeps in float on float mirrors of the state.
+// A Batch holds one or more steady solves in one concatenated index space
+// (see cgks_kernels.cuh) and runs the two-level V-cycle of Ji, Shyy & Xu
+// (arXiv:2109.09965, Section 3) or the explicit high-order step (Section
+// 2.4) for all of them with one launch per kernel, captured in a CUDA
+// graph.  cgks_solver is a batch of one solve; cgks_server admits and
+// retires solves and rebuilds its batch when the active set changes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
 #include <new>
 #include <string>
-#include <type_traits>
 #include <vector>
 
 #include "cgks_internal.h"
-#include "cgks_physics.cuh"
+#include "cgks_kernels.cuh"
 
 using namespace cgks;
+using namespace cgks::kern;
 namespace D = cgks::dev;
 
 namespace {
 
-constexpr int kCellBlock = 256;
-constexpr int kFaceBlock = 128;
-constexpr int kSweepBlock = 128;
-
-// status bits of the device status word
-constexpr int kBadState = 1;
-
-template <typename T>
-struct ParamsT {
-  T gamma, K, mu, cfl_hi, cfl_lo;
-  D::KC<T> kc;
-  int bc_kind[CGKS_MAX_BC];
-  T bc_uw[CGKS_MAX_BC][2];
-  T bc_rho[CGKS_MAX_BC], bc_u[CGKS_MAX_BC][2], bc_p[CGKS_MAX_BC];
-};
-
-template <typename T>
-struct MeshT {
-  int nc, nf;
-  const T *vol, *ivol, *per, *ih, *m2;       // ih = 1/h; m2: [3][nc]
-  const T *op;                               // [kNCol*kNM][nc]
-  const T *fn, *fS, *fjump, *fxi;            // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
-  const T *snx, *sny, *shs;                  // [4][nc] per face slot: outward normal of the cell, S/2
-  const int *cface, *cnbr;                   // [4][nc]
-  const int *fc0, *fc1;
-};
+inline int nblk(int64_t n, int b) { return static_cast<int>((n + b - 1) / b); }
 
 // arrays in the flux type TF (in FP64 mode the state entries alias the
 // double state, in mixed mode they are float mirrors)
@@ -70,620 +41,91 @@ struct Bufs {
   T *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
 };
 
-struct Scalars {
-  unsigned long long dt_bits;   // min over cells of the local explicit step (bits of a positive double)
-  int status;
-  int res_ctr;                  // next slot of the residual history
-  double dt_fixed;              // > 0: prescribed step
-};
-
-template <typename T>
-__host__ __device__ constexpr bool is_f32() { return std::is_same<T, float>::value; }
-
-__device__ __forceinline__ double dt_value(const Scalars *sc, double cfl) {
-  if (sc->dt_fixed > 0.0) return sc->dt_fixed;
-  return cfl * __longlong_as_double(static_cast<long long>(sc->dt_bits));
-}
-
-__device__ __forceinline__ bool state_ok(double gamma, const double w[4]) {
-  double p = (gamma - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
-  return w[0] > 0.0 && p > 0.0 && isfinite(w[0]) && isfinite(p) && isfinite(w[1]) && isfinite(w[2]);
-}
-
-// Block reduction of two doubles in a fixed order; thread 0 writes them.
-__device__ __forceinline__ void block_sum2(double a, double b, double *out2) {
-  __shared__ double sa[32], sb[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
-  __syncthreads();
-  if (warp == 0) {
-    int nw = blockDim.x >> 5;
-    a = lane < nw ? sa[lane] : 0.0;
-    b = lane < nw ? sb[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) { out2[0] = a; out2[1] = b; }
-  }
-}
-
-// ------------------------------------------------------------------
-// K0: reset per-step scalars
-__global__ void k_reset_dt(Scalars *sc, double dt_fixed) {
-  sc->dt_bits = 0x7ff0000000000000ull;  // +inf
-  sc->dt_fixed = dt_fixed;
-}
-
-// K4: local explicit step per cell, global min by atomicMin on the bits
-// (min is order independent).  h = 2|Omega|/perimeter, speed |U| + c + 2 nu / h.
-__global__ void k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W, Scalars *sc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double d = INFINITY;
-  if (i < m.nc) {
-    int n = m.nc;
-    double rho = W[i], mx = W[n + i], my = W[2 * n + i], E = W[3 * n + i];
-    double u = mx / rho, v = my / rho;
-    double p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
-    double a = sqrt(P.gamma * p / rho);
-    double hh = 2.0 * m.vol[i] / m.per[i];
-    double speed = sqrt(u * u + v * v) + a + 2.0 * (P.mu / rho) / hh;
-    d = hh / speed;
-  }
-  for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_down_sync(0xffffffffu, d, o));
-  if ((threadIdx.x & 31) == 0 && d < INFINITY)
-    atomicMin(&sc->dt_bits, static_cast<unsigned long long>(__double_as_longlong(d)));
-}
-
-// Wall ghost of a state and its gradient (global frame), through the face frame.
-template <typename T>
-__device__ __forceinline__ void wall_ghost_global(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4],
-                                                  const T gx[4], const T gy[4], T wg[4], T ggx[4], T ggy[4]) {
-  T wl[4], dn[4], dt[4], tn[4], tt[4];
-  D::rot_in(nx, ny, w, wl);
-  for (int v = 0; v < 4; ++v) { tn[v] = nx * gx[v] + ny * gy[v]; tt[v] = -ny * gx[v] + nx * gy[v]; }
-  D::rot_in(nx, ny, tn, dn);
-  D::rot_in(nx, ny, tt, dt);
-  T wgl[4], dng[4], dtg[4];
-  if (P.bc_kind[tag] == CGKS_BC_SLIP) {
-    D::ghost_slip(wl, dn, dt, wgl, dng, dtg);
-  } else {
-    T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-    T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
-    D::ghost_noslip(P.gamma, wn, wt, wl, dn, dt, wgl, dng, dtg);
-  }
-  T gn[4], gt[4];
-  D::rot_out(nx, ny, wgl, wg);
-  D::rot_out(nx, ny, dng, gn);
-  D::rot_out(nx, ny, dtg, gt);
-  for (int v = 0; v < 4; ++v) { ggx[v] = nx * gn[v] - ny * gt[v]; ggy[v] = ny * gn[v] + nx * gt[v]; }
-}
-
-// K1: compact least-squares quadratic of every cell.
-//   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
-template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
-  const int n = m.nc;
-  T wi[4], gxi[4], gyi[4];
-  for (int v = 0; v < 4; ++v) { wi[v] = W[v * n + i]; gxi[v] = Wx[v * n + i]; gyi[v] = Wx[(4 + v) * n + i]; }
-  T c[kNM][4];
-  for (int q = 0; q < kNM; ++q) {
-    T o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
-    for (int v = 0; v < 4; ++v) c[q][v] = o0 * gxi[v] + o1 * gyi[v];
-  }
-  for (int s = 0; s < kMaxFace; ++s) {
-    int fs = m.cface[s * n + i];
-    if (fs == kNoFace) continue;
-    int j = m.cnbr[s * n + i];
-    T b0[4], b1[4], b2[4];
-    if (j >= 0) {
-      for (int v = 0; v < 4; ++v) {
-        b0[v] = W[v * n + j] - wi[v];
-        b1[v] = Wx[v * n + j];
-        b2[v] = Wx[(4 + v) * n + j];
-      }
-    } else {
-      int f = fs >= 0 ? fs : ~fs;
-      int tag = -1 - m.fc1[f];
-      if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
-      T wg[4];
-      wall_ghost_global(P, tag, m.fn[f], m.fn[m.nf + f], wi, gxi, gyi, wg, b1, b2);
-      for (int v = 0; v < 4; ++v) b0[v] = wg[v] - wi[v];
-    }
-    for (int q = 0; q < kNM; ++q) {
-      T o0 = m.op[((3 * s) * kNM + q) * n + i];
-      T o1 = m.op[((3 * s + 1) * kNM + q) * n + i];
-      T o2 = m.op[((3 * s + 2) * kNM + q) * n + i];
-      for (int v = 0; v < 4; ++v) c[q][v] += o0 * b0[v] + o1 * b1[v] + o2 * b2[v];
-    }
-  }
-  for (int q = 0; q < kNM; ++q)
-    for (int v = 0; v < 4; ++v) coef[(q * 4 + v) * n + i] = c[q][v];
-}
-
-// value and gradient of the quadratic of cell i at scaled offset (x, y)
-template <typename T>
-__device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restrict__ W, const T *__restrict__ coef,
-                                            int i, T x, T y, T val[4], T gx[4], T gy[4]) {
-  const int n = m.nc;
-  T ih = m.ih[i];
-  T p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
-  for (int v = 0; v < 4; ++v) {
-    T c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
-    T c3 = coef[(3 * 4 + v) * n + i], c4 = coef[(4 * 4 + v) * n + i];
-    val[v] = W[v * n + i] + c0 * x + c1 * y + c2 * p2 + c3 * p3 + c4 * p4;
-    gx[v] = (c0 + T(2) * c2 * x + c3 * y) * ih;
-    gy[v] = (c1 + c3 * x + T(2) * c4 * y) * ih;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4], T wg[4]) {
-  T wl[4], z[4] = { T(0), T(0), T(0), T(0) }, wgl[4], a[4], b[4];
-  D::rot_in(nx, ny, w, wl);
-  int kind = P.bc_kind[tag];
-  if (kind == CGKS_BC_FARFIELD) {
-    T une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
-    T ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
-    D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wgl);
-  } else if (kind == CGKS_BC_SLIP) {
-    D::ghost_slip(wl, z, z, wgl, a, b);
-  } else {
-    T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-    T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
-    D::ghost_noslip(P.gamma, wn, wt, wl, z, z, wgl, a, b);
-  }
-  D::rot_out(nx, ny, wgl, wg);
-}
-
-// K2: gas-kinetic flux and interface state at the two Gauss points of every
-// face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
-//   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
-template <typename T>
-__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                     const T *__restrict__ coef, T *__restrict__ out) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
-  const int nf = m.nf;
-  const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
-  T acc[4][4];
-  for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = T(0);
-  T wff[4];
-  bool farfield = false;
-  int tag = 0;
-  if (c1 < 0) {
-    tag = -1 - c1;
-    farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
-    if (farfield) {
-      // Riemann-invariant state from the cell mean and the free stream
-      T wm[4], wl[4];
-      for (int v = 0; v < 4; ++v) wm[v] = W[v * m.nc + c0];
-      D::rot_in(nx, ny, wm, wl);
-      T une = P.bc_u[tag][0] * nx + P.bc_u[tag][1] * ny;
-      T ute = -P.bc_u[tag][0] * ny + P.bc_u[tag][1] * nx;
-      D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wff);
-    }
-  }
-  for (int k = 0; k < 2; ++k) {
-    T wL[4], gxL[4], gyL[4];
-    recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
-    T wl[4], dnl[4], dtl[4], t0[4], t1[4];
-    D::rot_in(nx, ny, wL, wl);
-    for (int v = 0; v < 4; ++v) { t0[v] = nx * gxL[v] + ny * gyL[v]; t1[v] = -ny * gxL[v] + nx * gyL[v]; }
-    D::rot_in(nx, ny, t0, dnl);
-    D::rot_in(nx, ny, t1, dtl);
-    T wr[4], dnr[4], dtr[4];
-    if (c1 >= 0) {
-      T wR[4], gxR[4], gyR[4];
-      recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
-      D::rot_in(nx, ny, wR, wr);
-      for (int v = 0; v < 4; ++v) { t0[v] = nx * gxR[v] + ny * gyR[v]; t1[v] = -ny * gxR[v] + nx * gyR[v]; }
-      D::rot_in(nx, ny, t0, dnr);
-      D::rot_in(nx, ny, t1, dtr);
-    } else if (farfield) {
-      for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = T(0); dtr[v] = T(0); }
-    } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
-      D::ghost_slip(wl, dnl, dtl, wr, dnr, dtr);
-    } else {
-      T wn = P.bc_uw[tag][0] * nx + P.bc_uw[tag][1] * ny;
-      T wt = -P.bc_uw[tag][0] * ny + P.bc_uw[tag][1] * nx;
-      D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
-    }
-    T F0[4], F1[4], Wc[4], Wt[4];
-    D::gks_point_local(P.kc, P.mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
-    T g[4];
-    D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += T(0.5) * g[v];
-    D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += T(0.5) * g[v];
-    D::rot_out(nx, ny, Wc, g); for (int v = 0; v < 4; ++v) acc[2][v] += T(0.5) * g[v];
-    D::rot_out(nx, ny, Wt, g); for (int v = 0; v < 4; ++v) acc[3][v] += T(0.5) * g[v];
-  }
-  for (int k = 0; k < 4; ++k)
-    for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
-}
-
-// K3 modes
-enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
-
-// K3: gather the face sums of each cell (accumulated in FP64).
-//   net flux   R  = -sum_p sgn S_p (a0 F0A + a1 F1A + a2 F1B)
-//   W_out = W_base + dt/|Omega| R   (not in kResidual mode)
-//   Wx_out = 1/|Omega| sum_p sgn S_p n_p (WcA + b1 WtX)
-// optional outputs: R itself, float mirrors of W_out / Wx_out, the
-// per-block density-residual partial sums; plus the state check.
-template <typename TF>
-__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P, int mode,
-                                                       const double *__restrict__ Wbase, const TF *__restrict__ FA,
-                                                       const TF *__restrict__ FB, Scalars *sc,
-                                                       double *__restrict__ Wout, double *__restrict__ Wxout,
-                                                       double *__restrict__ partial, double *__restrict__ Rout,
-                                                       TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = m.nc, nf = m.nf;
-  double num = 0.0, den = 0.0;
-  if (i < n) {
-    double dt = dt_value(sc, P.cfl_hi);
-    double a0, a1, b1;
-    const TF *FW = FA;   // where Wt is taken from
-    switch (mode) {
-      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; b1 = dt; break;
-      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; b1 = 0.5 * dt; break;
-      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; FW = FB; break;
-      default: a0 = 1.0; a1 = 0.5 * dt; b1 = 0.0; break;
-    }
-    double R[4] = { 0, 0, 0, 0 }, gx[4] = { 0, 0, 0, 0 }, gy[4] = { 0, 0, 0, 0 };
-    for (int s = 0; s < kMaxFace; ++s) {
-      int fs = m.cface[s * n + i];
-      if (fs == kNoFace) continue;
-      int f = fs >= 0 ? fs : ~fs;
-      double sg = fs >= 0 ? 1.0 : -1.0;
-      double S = m.fS[f], nx = m.fn[f], ny = m.fn[nf + f];
-      for (int v = 0; v < 4; ++v) {
-        double f1 = static_cast<double>(FA[(4 + v) * nf + f]);
-        if (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(FB[(4 + v) * nf + f]);
-        double fl = S * (a0 * static_cast<double>(FA[v * nf + f]) + a1 * f1);
-        R[v] -= sg * fl;
-        if (mode != kResidual) {
-          double wp = static_cast<double>(FA[(8 + v) * nf + f]) + b1 * static_cast<double>(FW[(12 + v) * nf + f]);
-          gx[v] += sg * S * nx * wp;
-          gy[v] += sg * S * ny * wp;
-        }
-      }
-    }
-    if (Rout)
-      for (int v = 0; v < 4; ++v) Rout[v * n + i] = R[v];
-    if (mode != kResidual) {
-      double iv = m.ivol[i];
-      double w[4];
-      for (int v = 0; v < 4; ++v) {
-        w[v] = Wbase[v * n + i] + dt / m.vol[i] * R[v];
-        Wout[v * n + i] = w[v];
-        Wxout[v * n + i] = gx[v] * iv;
-        Wxout[(4 + v) * n + i] = gy[v] * iv;
-        if (Wout_m) {
-          Wout_m[v * n + i] = static_cast<TF>(w[v]);
-          Wxout_m[v * n + i] = static_cast<TF>(gx[v] * iv);
-          Wxout_m[(4 + v) * n + i] = static_cast<TF>(gy[v] * iv);
-        }
-      }
-      if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
-      num = fabs(w[0] - Wbase[i]);
-      den = Wbase[i];
-    }
-  }
-  if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
-}
-
-// Sum the block partials in a fixed order; Res = num / den into hist[ctr++].
-__global__ void k_res_final(const double *__restrict__ partial, int nblocks, Scalars *sc, double *hist, int cap,
-                            double *last) {
-  double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) { a += partial[2 * k]; b += partial[2 * k + 1]; }
-  block_sum2(a, b, last + 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = last[1] / last[2];
-    last[0] = r;
-    int c = sc->res_ctr;
-    if (hist && c < cap) hist[c] = r;
-    sc->res_ctr = c + 1;
-  }
-}
-
-// ---------------------------- low-order level ----------------------------
-// K5a: per-cell start of an implicit step: U = W_p0 (first step) or
-// U += dU (Algorithm 1's update, in FP64), then the primitives of U (and
-// its float mirror in mixed mode).
-template <typename TF>
-__global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
-                                                        double *__restrict__ U, const TF *__restrict__ dU,
-                                                        TF *__restrict__ prim, TF *__restrict__ Um) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  TF w[4];
-  for (int v = 0; v < 4; ++v) {
-    double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(dU[v * n + i]);
-    U[v * n + i] = u;
-    w[v] = static_cast<TF>(u);
-    if (Um) Um[v * n + i] = w[v];
-  }
-  D::Prim<TF> q = D::prim_of(w, P.gamma, P.kc);
-  prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.p;
-  prim[4 * n + i] = q.i2l; prim[5 * n + i] = q.sl; prim[6 * n + i] = q.isp; prim[7 * n + i] = q.c;
-  prim[8 * n + i] = q.ir;
-}
-
-template <typename T>
-__device__ __forceinline__ D::Prim<T> load_prim(const T *__restrict__ prim, int n, int i) {
-  D::Prim<T> q;
-  q.rho = prim[0 * n + i]; q.u = prim[1 * n + i]; q.v = prim[2 * n + i]; q.p = prim[3 * n + i];
-  q.i2l = prim[4 * n + i]; q.sl = prim[5 * n + i]; q.isp = prim[6 * n + i]; q.c = prim[7 * n + i];
-  q.ir = prim[8 * n + i];
-  return q;
-}
-
-// K5b: first-order KFVS flux, spectral radius lambda_p = max of both sides,
-// and (FP64 mode) the Euler normal fluxes F_n(U_c0), F_n(U_c1) the
-// relaxation reuses.
-template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
-                                                        const T *__restrict__ prim, T *__restrict__ Flo,
-                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
-  const int n = m.nc, nf = m.nf;
-  const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const T nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
-  D::Prim<T> a = load_prim(prim, n, c0), b;
-  T ivb;
-  if (c1 >= 0) {
-    b = load_prim(prim, n, c1);
-    ivb = m.ivol[c1];
-  } else {
-    T w0[4], wg[4];
-    for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
-    lo_ghost(P, -1 - c1, nx, ny, w0, wg);
-    b = D::prim_of(wg, P.gamma, P.kc);
-    ivb = m.ivol[c0];
-  }
-  const T una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
-  const T unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
-  T Fl[4], F[4];
-  D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
-  D::rot_out(nx, ny, Fl, F);
-  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
-  const T la = fabs(una) + a.c + T(2) * (P.mu * a.ir) * S * m.ivol[c0];
-  const T lb = fabs(unb) + b.c + T(2) * (P.mu * b.ir) * S * ivb;
-  lam[f] = la > lb ? la : lb;
-  if (E0) {
-    // Euler normal flux of the cell means (interior faces: both sides)
-    E0[0 * nf + f] = a.rho * una;
-    E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
-    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
-    E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
-    if (c1 >= 0) {
-      E1[0 * nf + f] = b.rho * unb;
-      E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
-      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
-      E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
-    }
-  }
-}
-
-// K6: low-order right-hand side R^k = R_lo(U^k) + S (FP64 sums), 1/D_i
-// (FP64 inversion), and the first colour pass of the relaxation: with
-// dU = 0 everywhere the update of a colour-0 cell reduces to R_i / D_i; all
-// other cells start at 0.  first: also forms the forcing S = R_p0 -
-// R_lo(W_p0) (Section 3, step 3).
-template <typename TF>
-__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0_end,
-                                                       const TF *__restrict__ Flo, const TF *__restrict__ lam,
-                                                       const double *__restrict__ Rp0, double *__restrict__ Src,
-                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
-                                                       TF *__restrict__ lamS) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
-  const int n = m.nc, nf = m.nf;
-  double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
-  for (int s = 0; s < kMaxFace; ++s) {
-    int fs = m.cface[s * n + i];
-    if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
-    int f = fs >= 0 ? fs : ~fs;
-    double sg = fs >= 0 ? 1.0 : -1.0;
-    double S = m.fS[f];
-    for (int v = 0; v < 4; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
-    TF l = lam[f];
-    lamS[s * n + i] = l;
-    sum += static_cast<double>(l) * S;
-  }
-  // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2
-  const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
-  invD[i] = static_cast<TF>(id);
-  for (int v = 0; v < 4; ++v) {
-    double src;
-    if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
-    else src = Src[v * n + i];
-    double r = R[v] + src;
-    Rk[v * n + i] = static_cast<TF>(r);
-    dU[v * n + i] = i < colour0_end ? static_cast<TF>(r * id) : TF(0);
-  }
-}
-
-// K7: point relaxation of the cells of one colour, Eq. (implicit-local):
-//   dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
-//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
-// FP64: F_n(U_ip) from the face cache of this implicit step.  Mixed: the
-// difference F_n(U_ip + dU_ip) - F_n(U_ip) in the exact increment form.
-// All neighbour loads are issued up front (absent slots read the cell
-// itself and contribute nothing) so they overlap.
-template <typename T>
-__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int end,
-                                                       const T *__restrict__ U, const T *__restrict__ prim,
-                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
-                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
-                                                       const T *__restrict__ E1, T *__restrict__ dU) {
-  int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= end) return;
-  const int n = m.nc, nf = m.nf;
-  int jn[kMaxFace];
-#pragma unroll
-  for (int s = 0; s < kMaxFace; ++s) jn[s] = m.cnbr[s * n + i];
-  T acc[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) acc[v] = Rk[v * n + i];
-#pragma unroll
-  for (int s = 0; s < kMaxFace; ++s) {
-    const bool ok = jn[s] >= 0;
-    const int j = ok ? jn[s] : i;
-    const T w = ok ? T(1) : T(0);
-    const T nx = m.snx[s * n + i], ny = m.sny[s * n + i], hS = w * m.shs[s * n + i], lp = lamS[s * n + i];
-    T uj[4], du[4], dF[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
-    if constexpr (is_f32<T>()) {
-      D::euler_flux_delta(P.gamma, uj, prim[1 * n + j], prim[2 * n + j], prim[3 * n + j], du, nx, ny, dF);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] -= hS * (dF[v] - lp * du[v]);
-    } else {
-      const int fs = m.cface[s * n + i];
-      const bool is0 = fs >= 0;
-      const int f = ok ? (is0 ? fs : ~fs) : 0;
-      T up[4], fa[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) up[v] = uj[v] + du[v];
-      D::euler_flux(P.gamma, up, nx, ny, fa);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
-        acc[v] -= hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
-      }
-    }
-  }
-  const T id = invD[i];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) dU[v * n + i] = acc[v] * id;
-}
-
-// K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
-// residual against the state at the start of the cycle, state check.
-template <typename TF>
-__global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT<double> P, double *__restrict__ W,
-                                                        const double *__restrict__ Wp0, const double *__restrict__ U,
-                                                        Scalars *sc, double *__restrict__ partial, TF *__restrict__ Wm) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = m.nc;
-  double num = 0.0, den = 0.0;
-  if (i < n) {
-    double w[4];
-    double old_rho = W[i];
-    for (int v = 0; v < 4; ++v) {
-      double wp = Wp0[v * n + i];
-      w[v] = wp + (U[v * n + i] - wp);
-      W[v * n + i] = w[v];
-      if (Wm) Wm[v * n + i] = static_cast<TF>(w[v]);
-    }
-    if (!state_ok(P.gamma, w)) atomicOr(&sc->status, kBadState);
-    num = fabs(w[0] - old_rho);
-    den = old_rho;
-  }
-  block_sum2(num, den, &partial[2 * blockIdx.x]);
-}
-
-// AoS caller order <-> SoA internal order
-__global__ void k_gather_state(int n, const int *__restrict__ perm, const double *__restrict__ Wa,
-                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx,
-                               float *__restrict__ W32, float *__restrict__ Wx32) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int c = perm[i];
-  for (int v = 0; v < 4; ++v) {
-    double w = Wa[4 * c + v];
-    W[v * n + i] = w;
-    if (W32) W32[v * n + i] = static_cast<float>(w);
-  }
-  for (int k = 0; k < 8; ++k) {
-    double g = Wxa ? Wxa[8 * c + k] : 0.0;
-    Wx[k * n + i] = g;
-    if (Wx32) Wx32[k * n + i] = static_cast<float>(g);
-  }
-}
-__global__ void k_scatter_state(int n, const int *__restrict__ perm, const double *__restrict__ W,
-                                const double *__restrict__ Wx, double *__restrict__ Wa, double *__restrict__ Wxa) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int c = perm[i];
-  if (Wa) for (int v = 0; v < 4; ++v) Wa[4 * c + v] = W[v * n + i];
-  if (Wxa) for (int k = 0; k < 8; ++k) Wxa[8 * c + k] = Wx[k * n + i];
-}
-
 // kernel ids for the per-kernel timers
 enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_LOCELL,
                 KI_PROLONG, KI_COUNT };
 const char *kKernelNames[KI_COUNT] = { "k_dt", "k_recon", "k_face", "k_update", "k_res_final", "k_lo_face",
                                        "k_lo_rhs", "k_sweep", "k_lo_cell", "k_prolong" };
 
-inline int nblk(int n, int b) { return (n + b - 1) / b; }
+// batch-wide settings (every solve of a batch shares them)
+struct Shared {
+  double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
+  int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1;
+  cgks_alloc_fn alloc = nullptr;
+  cgks_free_fn free = nullptr;
+  void *alloc_ctx = nullptr;
+};
 
-}  // namespace
+// One solve of a batch: its mesh, its parameters and where it sits.
+struct Member {
+  std::shared_ptr<const HostMesh> mesh;
+  cgks_params params;
+  int64_t cell_off = 0, n_pad = 0, face_off = 0;
+};
 
-// ------------------------------------------------------------------------
-struct cgks_solver {
-  HostMesh hm;                  // host copy (ordering and permutations)
-  cgks_params params{};
+struct Timer {
+  bool on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  double ms[KI_COUNT] = { 0 };
+  long long cnt[KI_COUNT] = { 0 };
+};
+
+// device tables of a batch (views into its arena)
+struct DevArrays {
+  double *vol, *ivol, *per, *ih, *m2, *op, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs;
+  double *mu, *bcuw, *bcrho, *bcu, *bcp;
+  int *cface, *cnbr, *fc0, *fc1, *csid, *fsid, *bckind;
+  unsigned char *ccol;
+  float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
+        *f_fjump = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr, *f_mu = nullptr,
+        *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
+};
+
+struct Batch {
+  Shared sh;
+  DevArrays d{};
+  std::vector<Member> mem;
+  int S = 0;
+  int64_t N = 0, F = 0;        // padded cells, faces
   bool mixed = false;
+  int n_colours = 0;
+  std::vector<int> sweep_seq;        // colour order after the first pass
+  std::vector<int> list_off;         // [n_colours + 1] offsets into the sweep cell list
+  std::vector<Ranges> ranges;        // per colour: per-solve cell ranges (n = 0: use the list)
   ParamsT<double> dp{};
   ParamsT<float> fp{};
   MeshT<double> dm{};
   MeshT<float> fm{};
-  cudaStream_t user_stream = nullptr, stream = nullptr;
-  cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+  cudaStream_t stream = nullptr;
   void *arena = nullptr;
   size_t arena_bytes = 0;
-  int device = 0;
-  // FP64 state and accumulation arrays (device)
+  // FP64 state and accumulation arrays
   double *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr;
-  double *U = nullptr, *Rp0 = nullptr, *Src = nullptr;
-  double *partial = nullptr, *last = nullptr;
-  // flux-type arrays
+  double *U = nullptr, *Rp0 = nullptr, *Src = nullptr, *partial = nullptr, *last = nullptr, *stage = nullptr;
   Bufs<double> bd;
   Bufs<float> bf;
-  std::vector<int> sweep_colours;   // colour sequence of the relaxation after the first pass
-  double *hist = nullptr;
+  int *list = nullptr, *perm = nullptr, *blk_begin = nullptr;
+  Ctl *ctl = nullptr;
+  unsigned long long *dt_bits = nullptr;
+  int *status = nullptr;
+  double *res = nullptr;               // [S] residual of the last update
+  double *hist = nullptr;              // solve 0's residual history
   int hist_cap = 0;
-  double *stage_aos = nullptr;  // [12 n] staging for set/get state
-  int *perm = nullptr;
-  Scalars *sc = nullptr;
-  int nblk_cell = 0;
-  // graphs
   cudaGraphExec_t g_cycle = nullptr, g_step = nullptr;
-  // timers
-  bool timing = false;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
-  double t_ms[KI_COUNT] = { 0 };
-  long long t_cnt[KI_COUNT] = { 0 };
+  Timer *timer = nullptr;              // owned by the caller
   long long launches = 0;
-  int status_cache = 0;
 };
 
-namespace {
-
-void *dev_alloc(cgks_solver *s, size_t bytes) {
-  if (s->params.alloc) return s->params.alloc(bytes, s->params.alloc_ctx);
+void *dev_alloc(const Shared &sh, size_t bytes) {
+  if (sh.alloc) return sh.alloc(bytes, sh.alloc_ctx);
   void *p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
   return p;
 }
-void dev_free(cgks_solver *s, void *p) {
+void dev_free(const Shared &sh, void *p) {
   if (!p) return;
-  if (s->params.alloc && s->params.free) s->params.free(p, s->params.alloc_ctx);
-  else if (!s->params.alloc) cudaFree(p);
+  if (sh.alloc) { if (sh.free) sh.free(p, sh.alloc_ctx); }
+  else cudaFree(p);
 }
 
 #define CK(x)                                   \
@@ -692,242 +134,675 @@ void dev_free(cgks_solver *s, void *p) {
     if (e_ != cudaSuccess) return CGKS_ECUDA;   \
   } while (0)
 
-// launch helper with optional timing
+// ------------------------------------------------------------------------
+// launch helper with optional per-kernel timing
 template <typename Kern, typename... Args>
-void launch(cgks_solver *s, int id, Kern kern, dim3 grid, dim3 block, Args... args) {
+void launch(Batch *b, int id, Kern kern, dim3 grid, dim3 block, Args... args) {
   if (grid.x == 0) return;
-  cudaEvent_t a = nullptr, b = nullptr;
-  if (s->timing) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool t = b->timer && b->timer->on;
+  if (t) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->stream);
   }
-  kern<<<grid, block, 0, s->stream>>>(args...);
-  if (s->timing) {
-    cudaEventRecord(b, s->stream);
-    s->tev.push_back({ id, { a, b } });
+  kern<<<grid, block, 0, b->stream>>>(args...);
+  if (t) {
+    cudaEventRecord(e1, b->stream);
+    b->timer->ev.push_back({ id, { e0, e1 } });
   }
-  s->launches++;
+  b->launches++;
 }
 
-template <typename TF> Bufs<TF> &bufs(cgks_solver *s);
-template <> Bufs<double> &bufs<double>(cgks_solver *s) { return s->bd; }
-template <> Bufs<float> &bufs<float>(cgks_solver *s) { return s->bf; }
-template <typename TF> const MeshT<TF> &fmesh(cgks_solver *s);
-template <> const MeshT<double> &fmesh<double>(cgks_solver *s) { return s->dm; }
-template <> const MeshT<float> &fmesh<float>(cgks_solver *s) { return s->fm; }
-template <typename TF> const ParamsT<TF> &fparams(cgks_solver *s);
-template <> const ParamsT<double> &fparams<double>(cgks_solver *s) { return s->dp; }
-template <> const ParamsT<float> &fparams<float>(cgks_solver *s) { return s->fp; }
+template <typename TF> Bufs<TF> &bufs(Batch *b);
+template <> Bufs<double> &bufs<double>(Batch *b) { return b->bd; }
+template <> Bufs<float> &bufs<float>(Batch *b) { return b->bf; }
+template <typename TF> const MeshT<TF> &fmesh(Batch *b);
+template <> const MeshT<double> &fmesh<double>(Batch *b) { return b->dm; }
+template <> const MeshT<float> &fmesh<float>(Batch *b) { return b->fm; }
+template <typename TF> const ParamsT<TF> &fparams(Batch *b);
+template <> const ParamsT<double> &fparams<double>(Batch *b) { return b->dp; }
+template <> const ParamsT<float> &fparams<float>(Batch *b) { return b->fp; }
 // float mirror of a flux-type array, or null when the flux type is double
 template <typename TF> TF *mirror(TF *p) { return is_f32<TF>() ? p : nullptr; }
 
-// ---- building blocks of a step / cycle ----
-void enqueue_dt(cgks_solver *s, double dt_fixed) {
-  launch(s, KI_DT, k_reset_dt, dim3(1), dim3(1), s->sc, dt_fixed);
+void enqueue_dt(Batch *b, double dt_fixed) {
+  launch(b, KI_DT, k_reset_dt, dim3(1), dim3(256), b->ctl, b->dt_bits, b->S, dt_fixed);
   if (!(dt_fixed > 0.0))
-    launch(s, KI_DT, k_dt, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (const double *)s->W, s->sc);
+    launch(b, KI_DT, k_dt, dim3(nblk(b->N, kCellBlock)), dim3(kCellBlock), b->dm, b->dp, (const double *)b->W, b->dt_bits);
+}
+
+void enqueue_res(Batch *b) {
+  launch(b, KI_RESFIN, k_res_final, dim3(b->S), dim3(256), (const double *)b->partial, (const int *)b->blk_begin,
+         b->ctl, b->res, b->hist, b->hist_cap, b->last);
 }
 
 template <typename TF>
-void enqueue_hi_eval(cgks_solver *s, const TF *W, const TF *Wx, TF *Fout) {
-  Bufs<TF> &B = bufs<TF>(s);
-  launch(s, KI_RECON, k_recon<TF>, dim3(s->nblk_cell), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s), W, Wx, B.coef);
-  launch(s, KI_FACE, k_face<TF>, dim3(nblk(s->dm.nf, kFaceBlock)), dim3(kFaceBlock), fmesh<TF>(s), fparams<TF>(s), W,
+void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
+  Bufs<TF> &B = bufs<TF>(b);
+  launch(b, KI_RECON, k_recon<TF>, dim3(nblk(b->N, kCellBlock)), dim3(kCellBlock), fmesh<TF>(b), fparams<TF>(b), W, Wx,
+         B.coef);
+  launch(b, KI_FACE, k_face<TF>, dim3(nblk(b->F, kFaceBlock)), dim3(kFaceBlock), fmesh<TF>(b), fparams<TF>(b), W,
          (const TF *)B.coef, Fout);
 }
 
 // high-order step from (W, Wx) into (Wout, Wx): Wx updated in place.
 template <typename TF>
-void enqueue_hi_step(cgks_solver *s, double *Wout, TF *Wout_m, bool want_res) {
-  Bufs<TF> &B = bufs<TF>(s);
-  double *part = want_res ? s->partial : nullptr;
-  enqueue_hi_eval<TF>(s, B.W, B.Wx, B.FA);
-  if (s->params.time_scheme == CGKS_S1O2) {
-    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS1O2,
-           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FA, s->sc, Wout, s->Wx, part, s->Rp0, Wout_m,
-           mirror<TF>(B.Wx));
+void enqueue_hi_step(Batch *b, double *Wout, TF *Wout_m, bool want_res) {
+  Bufs<TF> &B = bufs<TF>(b);
+  double *part = want_res ? b->partial : nullptr;
+  const dim3 g(nblk(b->N, kCellBlock)), blk(kCellBlock);
+  enqueue_hi_eval<TF>(b, B.W, B.Wx, B.FA);
+  if (b->sh.time_scheme == CGKS_S1O2) {
+    launch(b, KI_UPDATE, k_update<TF>, g, blk, b->dm, b->dp, (int)kS1O2, (const double *)b->W, (const TF *)B.FA,
+           (const TF *)B.FA, (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits, b->status, Wout, b->Wx,
+           part, b->Rp0, Wout_m, mirror<TF>(B.Wx));
   } else {
-    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Stage,
-           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FA, s->sc, s->Ws, s->Wxs, (double *)nullptr,
-           (double *)nullptr, mirror<TF>(B.Ws), mirror<TF>(B.Wxs));
-    enqueue_hi_eval<TF>(s, B.Ws, B.Wxs, B.FB);
-    launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kS2O4Final,
-           (const double *)s->W, (const TF *)B.FA, (const TF *)B.FB, s->sc, Wout, s->Wx, part, s->Rp0, Wout_m,
-           mirror<TF>(B.Wx));
+    launch(b, KI_UPDATE, k_update<TF>, g, blk, b->dm, b->dp, (int)kS2O4Stage, (const double *)b->W, (const TF *)B.FA,
+           (const TF *)B.FA, (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits, b->status, b->Ws, b->Wxs,
+           (double *)nullptr, (double *)nullptr, mirror<TF>(B.Ws), mirror<TF>(B.Wxs));
+    enqueue_hi_eval<TF>(b, B.Ws, B.Wxs, B.FB);
+    launch(b, KI_UPDATE, k_update<TF>, g, blk, b->dm, b->dp, (int)kS2O4Final, (const double *)b->W, (const TF *)B.FA,
+           (const TF *)B.FB, (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits, b->status, Wout, b->Wx,
+           part, b->Rp0, Wout_m, mirror<TF>(B.Wx));
   }
-  if (want_res)
-    launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
-           s->hist_cap, s->last);
+  if (want_res) enqueue_res(b);
 }
 
-// low-order solve from U = W_p0 (= s->Wn), R_p0 in s->Rp0; result in s->U.
-// Per implicit step: cell primitives (and U += dU), KFVS faces, right-hand
-// side with the first colour pass, then the remaining colour passes.
+// low-order solve from U = W_p0 (= Wn), R_p0 in Rp0; result in U.  Per
+// implicit step: cell primitives (and U += dU), KFVS faces, right-hand side
+// with the first colour pass, then the remaining colour passes.
 template <typename TF>
-void enqueue_lo_solve(cgks_solver *s) {
-  Bufs<TF> &B = bufs<TF>(s);
-  const int n = s->dm.nc, nf = s->dm.nf;
-  const int c0_end = s->params.n_sweeps > 0 ? s->hm.colour_start[1] : 0;
-  for (int k = 0; k < s->params.n_implicit; ++k) {
-    launch(s, KI_LOCELL, k_lo_cell<TF>, dim3(s->nblk_cell), dim3(kCellBlock), n, fparams<TF>(s), k == 0 ? 1 : 0,
-           (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
-    launch(s, KI_LOFACE, k_lo_face<TF>, dim3(nblk(nf, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fparams<TF>(s),
-           (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
-    launch(s, KI_LORHS, k_lo_rhs<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, k == 0 ? 1 : 0, c0_end,
-           (const TF *)B.Flo, (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU, B.lamS);
-    for (int c : s->sweep_colours) {
-      int b = s->hm.colour_start[c], e = s->hm.colour_start[c + 1];
-      launch(s, KI_SWEEP, k_sweep<TF>, dim3(nblk(e - b, kSweepBlock)), dim3(kSweepBlock), fmesh<TF>(s),
-             fparams<TF>(s), b, e, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
-             (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, B.dU);
+void enqueue_lo_solve(Batch *b) {
+  Bufs<TF> &B = bufs<TF>(b);
+  const dim3 gc(nblk(b->N, kCellBlock)), gf(nblk(b->F, kCellBlock)), blk(kCellBlock);
+  const int colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
+  for (int k = 0; k < b->sh.n_implicit; ++k) {
+    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->N), fparams<TF>(b), k == 0 ? 1 : 0,
+           (const double *)b->Wn, b->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
+    launch(b, KI_LOFACE, k_lo_face<TF>, gf, blk, fmesh<TF>(b), fparams<TF>(b), (const TF *)B.U, (const TF *)B.prim,
+           B.Flo, B.lam, B.E0, B.E1);
+    launch(b, KI_LORHS, k_lo_rhs<TF>, gc, blk, b->dm, b->dp, k == 0 ? 1 : 0, colour0, (const TF *)B.Flo,
+           (const TF *)B.lam, (const double *)b->Rp0, b->Src, B.Rk, B.invD, B.dU, B.lamS);
+    for (int c : b->sweep_seq) {
+      const int cnt = b->list_off[c + 1] - b->list_off[c];
+      const Ranges &R = b->ranges[c];
+      const bool use_list = R.n == 0;
+      const int grid = use_list ? nblk(cnt, kSweepCells) : R.blk[R.n];
+      launch(b, KI_SWEEP, k_sweep<TF>, dim3(grid), dim3(kSweepBlock), fmesh<TF>(b), fparams<TF>(b), R,
+             use_list ? (const int *)b->list + b->list_off[c] : (const int *)nullptr, cnt, (const TF *)B.U,
+             (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD, (const TF *)B.lamS, (const TF *)B.E0,
+             (const TF *)B.E1, B.dU);
     }
   }
   // U^{n_implicit} = U + dU of the last step
-  if (s->params.n_implicit > 0)
-    launch(s, KI_LOCELL, k_lo_cell<TF>, dim3(s->nblk_cell), dim3(kCellBlock), n, fparams<TF>(s), 0,
-           (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
+  if (b->sh.n_implicit > 0)
+    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->N), fparams<TF>(b), 0, (const double *)b->Wn, b->U,
+           (const TF *)B.dU, B.prim, mirror<TF>(B.U));
   else
-    cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(b->U, b->Wn, sizeof(double) * 4 * b->N, cudaMemcpyDeviceToDevice, b->stream);
 }
 
 template <typename TF>
-void enqueue_prolong(cgks_solver *s) {
-  launch(s, KI_PROLONG, k_prolong<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, s->W,
-         (const double *)s->Wn, (const double *)s->U, s->sc, s->partial, mirror<TF>(bufs<TF>(s).W));
-  launch(s, KI_RESFIN, k_res_final, dim3(1), dim3(256), (const double *)s->partial, s->nblk_cell, s->sc, s->hist,
-         s->hist_cap, s->last);
+void enqueue_prolong(Batch *b) {
+  launch(b, KI_PROLONG, k_prolong<TF>, dim3(nblk(b->N, kCellBlock)), dim3(kCellBlock), b->dm, b->dp, b->W,
+         (const double *)b->Wn, (const double *)b->U, b->status, b->partial, mirror<TF>(bufs<TF>(b).W));
+  enqueue_res(b);
 }
 
 template <typename TF>
-void enqueue_cycle_t(cgks_solver *s) {
-  Bufs<TF> &B = bufs<TF>(s);
-  enqueue_dt(s, -1.0);
+void enqueue_cycle_t(Batch *b) {
+  Bufs<TF> &B = bufs<TF>(b);
+  enqueue_dt(b, -1.0);
   // 1: high-order step into W_p0 = Wn (W keeps W^n for the residual)
-  enqueue_hi_step<TF>(s, s->Wn, mirror<TF>(B.Wn), false);
+  enqueue_hi_step<TF>(b, b->Wn, mirror<TF>(B.Wn), false);
   // 2: R_p0 = time-averaged high-order net flux at W^{n+1}
-  enqueue_hi_eval<TF>(s, B.Wn, B.Wx, B.FB);
-  launch(s, KI_UPDATE, k_update<TF>, dim3(s->nblk_cell), dim3(kCellBlock), s->dm, s->dp, (int)kResidual,
-         (const double *)s->Wn, (const TF *)B.FB, (const TF *)B.FB, s->sc, (double *)nullptr, (double *)nullptr,
-         (double *)nullptr, s->Rp0, (TF *)nullptr, (TF *)nullptr);
+  enqueue_hi_eval<TF>(b, B.Wn, B.Wx, B.FB);
+  launch(b, KI_UPDATE, k_update<TF>, dim3(nblk(b->N, kCellBlock)), dim3(kCellBlock), b->dm, b->dp, (int)kResidual,
+         (const double *)b->Wn, (const TF *)B.FB, (const TF *)B.FB, (const Ctl *)b->ctl,
+         (const unsigned long long *)b->dt_bits, b->status, (double *)nullptr, (double *)nullptr, (double *)nullptr,
+         b->Rp0, (TF *)nullptr, (TF *)nullptr);
   // 3-4: forcing and implicit low-order solve
-  enqueue_lo_solve<TF>(s);
+  enqueue_lo_solve<TF>(b);
   // 5: correction and residual
-  enqueue_prolong<TF>(s);
+  enqueue_prolong<TF>(b);
 }
 
-void enqueue_cycle(cgks_solver *s) {
-  if (s->mixed) enqueue_cycle_t<float>(s);
-  else enqueue_cycle_t<double>(s);
+void enqueue_cycle(Batch *b) {
+  if (b->mixed) enqueue_cycle_t<float>(b);
+  else enqueue_cycle_t<double>(b);
 }
 
-void enqueue_explicit_step(cgks_solver *s, double dt_fixed) {
-  enqueue_dt(s, dt_fixed);
-  if (s->mixed) enqueue_hi_step<float>(s, s->W, s->bf.W, true);
-  else enqueue_hi_step<double>(s, s->W, nullptr, true);
+void enqueue_explicit_step(Batch *b, double dt_fixed) {
+  enqueue_dt(b, dt_fixed);
+  if (b->mixed) enqueue_hi_step<float>(b, b->W, b->bf.W, true);
+  else enqueue_hi_step<double>(b, b->W, nullptr, true);
 }
 
-void enqueue_lo_smooth(cgks_solver *s) {
-  cudaMemcpyAsync(s->Wn, s->W, sizeof(double) * 4 * s->dm.nc, cudaMemcpyDeviceToDevice, s->stream);
-  if (s->mixed) { enqueue_lo_solve<float>(s); enqueue_prolong<float>(s); }
-  else { enqueue_lo_solve<double>(s); enqueue_prolong<double>(s); }
+void enqueue_lo_smooth(Batch *b) {
+  cudaMemcpyAsync(b->Wn, b->W, sizeof(double) * 4 * b->N, cudaMemcpyDeviceToDevice, b->stream);
+  if (b->mixed) { enqueue_lo_solve<float>(b); enqueue_prolong<float>(b); }
+  else { enqueue_lo_solve<double>(b); enqueue_prolong<double>(b); }
 }
 
-int ensure_hist(cgks_solver *s, int n) {
-  if (n <= s->hist_cap) return CGKS_OK;
-  // grow: graphs captured with the old pointer must be rebuilt
-  double *p = static_cast<double *>(dev_alloc(s, sizeof(double) * n));
+long long count_launches(const Batch *b, bool cycle) {
+  long long per_eval = 2;
+  long long hi = per_eval + 1 + (b->sh.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
+  long long dt = 2;
+  if (!cycle) return dt + hi + 1;
+  long long lo = b->sh.n_implicit * (3 + static_cast<long long>(b->sweep_seq.size())) + (b->sh.n_implicit > 0 ? 1 : 0);
+  return dt + hi + per_eval + 1 + lo + 2;
+}
+
+void drop_graphs(Batch *b) {
+  if (b->g_cycle) { cudaGraphExecDestroy(b->g_cycle); b->g_cycle = nullptr; }
+  if (b->g_step) { cudaGraphExecDestroy(b->g_step); b->g_step = nullptr; }
+}
+
+int ensure_hist(Batch *b, int n) {
+  if (n <= b->hist_cap) return CGKS_OK;
+  double *p = static_cast<double *>(dev_alloc(b->sh, sizeof(double) * n));
   if (!p) return CGKS_ENOMEM;
-  if (s->hist) { cudaStreamSynchronize(s->stream); dev_free(s, s->hist); }
-  s->hist = p;
-  s->hist_cap = n;
-  if (s->g_cycle) { cudaGraphExecDestroy(s->g_cycle); s->g_cycle = nullptr; }
-  if (s->g_step) { cudaGraphExecDestroy(s->g_step); s->g_step = nullptr; }
+  if (b->hist) { cudaStreamSynchronize(b->stream); dev_free(b->sh, b->hist); }
+  b->hist = p;
+  b->hist_cap = n;
+  drop_graphs(b);   // graphs hold the old pointer
   return CGKS_OK;
 }
 
-int begin_call(cgks_solver *s) {
-  CK(cudaSetDevice(s->device));
-  CK(cudaEventRecord(s->ev_user, s->user_stream));
-  CK(cudaStreamWaitEvent(s->stream, s->ev_user, 0));
-  return CGKS_OK;
-}
-int end_call(cgks_solver *s) {
-  CK(cudaEventRecord(s->ev_done, s->stream));
-  CK(cudaStreamWaitEvent(s->user_stream, s->ev_done, 0));
-  return CGKS_OK;
-}
-
-int capture(cgks_solver *s, bool cycle, cudaGraphExec_t *out) {
+int capture(Batch *b, bool cycle, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
-  bool t = s->timing;
-  s->timing = false;
-  long long l0 = s->launches;
-  CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  if (cycle) enqueue_cycle(s);
-  else enqueue_explicit_step(s, -1.0);
-  cudaError_t e = cudaStreamEndCapture(s->stream, &g);
-  s->launches = l0;
-  s->timing = t;
+  Timer *t = b->timer;
+  b->timer = nullptr;
+  long long l0 = b->launches;
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  if (cycle) enqueue_cycle(b);
+  else enqueue_explicit_step(b, -1.0);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->launches = l0;
+  b->timer = t;
   if (e != cudaSuccess) return CGKS_ECUDA;
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   return e == cudaSuccess ? CGKS_OK : CGKS_ECUDA;
 }
 
-long long count_launches(cgks_solver *s, bool cycle) {
-  // number of kernels one cycle / step enqueues
-  long long per_eval = 2;
-  long long hi = per_eval + 1 + (s->params.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
-  long long dt = 2;
-  if (!cycle) return dt + hi + 1;
-  long long lo = s->params.n_implicit * (3 + static_cast<long long>(s->sweep_colours.size())) +
-                 (s->params.n_implicit > 0 ? 1 : 0);
-  return dt + hi + per_eval + 1 + lo + 2;
+// n cycles (or explicit steps) without host synchronisation
+int run_many(Batch *b, int n, bool cycle) {
+  if (n <= 0) return CGKS_OK;
+  CK(cudaMemsetAsync(&b->ctl->res_ctr, 0, sizeof(int), b->stream));
+  const bool graph = b->sh.use_graph && !(b->timer && b->timer->on);
+  cudaGraphExec_t *ge = cycle ? &b->g_cycle : &b->g_step;
+  if (graph && !*ge) {
+    int rc = capture(b, cycle, ge);
+    if (rc) return rc;
+  }
+  const long long per = count_launches(b, cycle);
+  for (int k = 0; k < n; ++k) {
+    if (graph) {
+      CK(cudaGraphLaunch(*ge, b->stream));
+      b->launches += per;
+    } else if (cycle) {
+      enqueue_cycle(b);
+    } else {
+      enqueue_explicit_step(b, -1.0);
+    }
+  }
+  CK(cudaGetLastError());
+  return CGKS_OK;
 }
 
-int read_status(cgks_solver *s) {
+void collect_timing(Timer *t) {
+  if (!t) return;
+  for (auto &e : t->ev) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.second.second);
+    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+    t->ms[e.first] += ms;
+    t->cnt[e.first] += 1;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  t->ev.clear();
+}
+
+template <typename T>
+void fill_shared_params(const Shared &sh, ParamsT<T> &P) {
+  double K = (4.0 - 2.0 * sh.gamma) / (sh.gamma - 1.0);
+  P.gamma = static_cast<T>(sh.gamma);
+  P.K = static_cast<T>(K);
+  P.cfl_hi = static_cast<T>(sh.cfl_hi);
+  P.cfl_lo = static_cast<T>(sh.cfl_lo);
+  P.kc.K = static_cast<T>(K);
+  P.kc.c2K = static_cast<T>(2.0 / (K + 2.0));
+  P.kc.c4K = static_cast<T>(4.0 / (K + 2.0));
+}
+
+// The device arena of a batch: one allocation carved into 256-byte aligned
+// pieces.  plan_arena lists the pieces for N padded cells, F faces, S
+// solves and L cells in the sweep lists; arena_total is the exact size.
+struct Piece { void **dst; size_t bytes; };
+
+size_t arena_total(const std::vector<Piece> &pieces) {
+  size_t total = 0;
+  for (auto &pc : pieces) total += (pc.bytes + 255) & ~size_t(255);
+  return total;
+}
+
+void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, std::vector<Piece> &pieces) {
+  DevArrays &d = b->d;
+  auto P8 = [&](double **x, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(x), sizeof(double) * cnt }); };
+  auto P4 = [&](float **x, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(x), sizeof(float) * cnt }); };
+  auto PI = [&](int **x, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(x), sizeof(int) * cnt }); };
+  auto PV = [&](void **x, size_t bytes) { pieces.push_back({ x, bytes }); };
+  const int64_t T = kTagsPerSolve * static_cast<int64_t>(S);
+  P8(&b->W, 4 * N); P8(&b->Wx, 8 * N); P8(&b->Wn, 4 * N); P8(&b->Ws, 4 * N); P8(&b->Wxs, 8 * N);
+  P8(&b->U, 4 * N); P8(&b->Rp0, 4 * N); P8(&b->Src, 4 * N); P8(&b->stage, 12 * N);
+  P8(&b->partial, 2 * std::max<int64_t>(N / kCellBlock, 1)); P8(&b->last, 4); P8(&b->res, S);
+  P8(&d.vol, N); P8(&d.ivol, N); P8(&d.per, N); P8(&d.ih, N); P8(&d.m2, 3 * N); P8(&d.op, kNCol * kNM * N);
+  P8(&d.snx, kMaxFace * N); P8(&d.sny, kMaxFace * N); P8(&d.shs, kMaxFace * N);
+  P8(&d.fn, 2 * F); P8(&d.fS, F); P8(&d.fjump, F); P8(&d.fxi, 8 * F);
+  P8(&d.mu, S); P8(&d.bcuw, 2 * T); P8(&d.bcrho, T); P8(&d.bcu, 2 * T); P8(&d.bcp, T);
+  PI(&d.cface, kMaxFace * N); PI(&d.cnbr, kMaxFace * N); PI(&d.fc0, F); PI(&d.fc1, F); PI(&d.csid, N); PI(&d.fsid, F);
+  PI(&d.bckind, T); PI(&b->list, std::max<int64_t>(L, 1)); PI(&b->perm, N); PI(&b->blk_begin, S + 1);
+  PV(reinterpret_cast<void **>(&d.ccol), N);
+  PV(reinterpret_cast<void **>(&b->ctl), sizeof(Ctl));
+  PV(reinterpret_cast<void **>(&b->dt_bits), sizeof(unsigned long long) * S);
+  PI(&b->status, S);
+  if (!mixed) {
+    Bufs<double> &X = b->bd;
+    P8(&X.coef, 20 * N); P8(&X.FA, 16 * F); P8(&X.FB, 16 * F);
+    P8(&X.prim, D::NPRIM * N); P8(&X.Flo, 4 * F); P8(&X.lam, F); P8(&X.E0, 4 * F); P8(&X.E1, 4 * F);
+    P8(&X.Rk, 4 * N); P8(&X.invD, N); P8(&X.dU, 4 * N); P8(&X.lamS, kMaxFace * N);
+  } else {
+    Bufs<float> &X = b->bf;
+    P4(&X.W, 4 * N); P4(&X.Wx, 8 * N); P4(&X.Wn, 4 * N); P4(&X.Ws, 4 * N); P4(&X.Wxs, 8 * N); P4(&X.U, 4 * N);
+    P4(&X.coef, 20 * N); P4(&X.FA, 16 * F); P4(&X.FB, 16 * F);
+    P4(&X.prim, D::NPRIM * N); P4(&X.Flo, 4 * F); P4(&X.lam, F);
+    P4(&X.Rk, 4 * N); P4(&X.invD, N); P4(&X.dU, 4 * N); P4(&X.lamS, kMaxFace * N);
+    P4(&d.f_ivol, N); P4(&d.f_ih, N); P4(&d.f_m2, 3 * N); P4(&d.f_op, kNCol * kNM * N);
+    P4(&d.f_snx, kMaxFace * N); P4(&d.f_sny, kMaxFace * N); P4(&d.f_shs, kMaxFace * N);
+    P4(&d.f_fn, 2 * F); P4(&d.f_fS, F); P4(&d.f_fjump, F); P4(&d.f_fxi, 8 * F);
+    P4(&d.f_mu, S); P4(&d.f_bcuw, 2 * T); P4(&d.f_bcrho, T); P4(&d.f_bcu, 2 * T); P4(&d.f_bcp, T);
+  }
+}
+
+constexpr int kHistDefault = 1024;
+
+// Device bytes one solve of n cells and nf faces adds to a batch: its
+// share of the arena, the residual history and, for the serving rebuild,
+// the stash of its state (12 doubles) and two move maps per cell.  The
+// arena size is sub-additive over solves, so the footprints of a set of
+// solves bound the batch they form.
+size_t solve_footprint(int64_t n, int64_t nf, bool mixed) {
+  const int64_t np = (n + kCellBlock - 1) / kCellBlock * kCellBlock;
+  Batch tmp;
+  std::vector<Piece> pieces;
+  plan_arena(&tmp, np, nf, 1, n, mixed, pieces);
+  return arena_total(pieces) + sizeof(double) * kHistDefault + (12 * sizeof(double) + 2 * sizeof(int)) * np + 3 * 256;
+}
+
+int64_t pad_cells(int64_t n) { return (n + kCellBlock - 1) / kCellBlock * kCellBlock; }
+
+void destroy_batch(Batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  dev_free(b->sh, b->hist);
+  dev_free(b->sh, b->arena);
+  delete b;
+}
+
+// Build a batch on stream st from members (mesh + per-solve parameters).
+int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batch **out) {
+  *out = nullptr;
+  std::unique_ptr<Batch> B(new (std::nothrow) Batch());
+  if (!B) return CGKS_ENOMEM;
+  Batch *b = B.get();
+  b->sh = sh;
+  b->mem = std::move(mem);
+  b->S = static_cast<int>(b->mem.size());
+  b->mixed = sh.precision == CGKS_MIXED;
+  b->stream = st;
+  if (b->S == 0) return CGKS_EINVAL;
+  int64_t N = 0, F = 0;
+  int C = 0;
+  for (auto &m : b->mem) {
+    m.cell_off = N;
+    m.n_pad = pad_cells(m.mesh->n_cells);
+    m.face_off = F;
+    N += m.n_pad;
+    F += m.mesh->n_faces;
+    C = std::max(C, m.mesh->n_colours);
+  }
+  if (N > INT32_MAX / 32 || F > INT32_MAX / 32) return CGKS_EINVAL;
+  b->N = N; b->F = F; b->n_colours = C;
+  const int S = b->S;
+  // ---- host arrays of the concatenated index space
+  std::vector<double> vol(N, 1.0), ivol(N, 1.0), per(N, 4.0), ih(N, 1.0), m2(3 * N, 0.0), op(kNCol * kNM * N, 0.0);
+  std::vector<double> snx(kMaxFace * N, 0.0), sny(kMaxFace * N, 0.0), shs(kMaxFace * N, 0.0);
+  std::vector<double> fn(2 * F), fS(F), fjump(F), fxi(8 * F);
+  std::vector<int> cface(kMaxFace * N, kNoFace), cnbr(kMaxFace * N, -1), fc0(F), fc1(F), csid(N, -1), fsid(F),
+      perm(N, 0), blk(S + 1);
+  std::vector<unsigned char> ccol(N, 255);
+  std::vector<double> mu(S), bc_uw(2 * kTagsPerSolve * S, 0.0), bc_rho(kTagsPerSolve * S, 1.0),
+      bc_u(2 * kTagsPerSolve * S, 0.0), bc_p(kTagsPerSolve * S, 1.0);
+  std::vector<int> bc_kind(kTagsPerSolve * S, CGKS_BC_SLIP);
+  std::vector<std::vector<int>> lists(C);
+  for (int s = 0; s < S; ++s) {
+    const Member &M = b->mem[s];
+    const HostMesh &hm = *M.mesh;
+    const cgks_params &p = M.params;
+    const int64_t nc = hm.n_cells, nf = hm.n_faces, co = M.cell_off, fo = M.face_off;
+    blk[s] = static_cast<int>(co / kCellBlock);
+    mu[s] = p.mu;
+    for (int t = 0; t < kTagsPerSolve; ++t) {
+      const int g = s * kTagsPerSolve + t;
+      const cgks_bc &bc = p.bc[t];
+      bc_kind[g] = t < p.n_bc ? bc.kind : CGKS_BC_SLIP;
+      bc_uw[2 * g] = bc.u_wall[0]; bc_uw[2 * g + 1] = bc.u_wall[1];
+      bc_rho[g] = bc.rho; bc_u[2 * g] = bc.u[0]; bc_u[2 * g + 1] = bc.u[1]; bc_p[g] = bc.p;
+    }
+    std::vector<char> wall(kTagsPerSolve, 0);
+    for (int t = 0; t < p.n_bc; ++t) wall[t] = p.bc[t].kind != CGKS_BC_FARFIELD;
+    std::vector<double> ops;
+    build_operator(hm, wall, ops);
+    for (int64_t i = 0; i < nc; ++i) {
+      const int64_t I = co + i;
+      vol[I] = hm.vol[i]; ivol[I] = 1.0 / hm.vol[i]; per[I] = hm.per[i]; ih[I] = 1.0 / hm.h[i];
+      for (int q = 0; q < 3; ++q) m2[q * N + I] = hm.m2[q * nc + i];
+      for (int q = 0; q < kNCol * kNM; ++q) op[q * N + I] = ops[q * nc + i];
+      csid[I] = s;
+      perm[I] = hm.perm[i];
+      for (int sl = 0; sl < kMaxFace; ++sl) {
+        const int32_t fs = hm.cface[sl * nc + i];
+        if (fs == kNoFace) continue;
+        const int32_t f = fs >= 0 ? fs : ~fs;
+        const double sg = fs >= 0 ? 1.0 : -1.0;
+        cface[sl * N + I] = fs >= 0 ? static_cast<int>(f + fo) : ~static_cast<int>(f + fo);
+        const int32_t j = hm.cnbr[sl * nc + i];
+        cnbr[sl * N + I] = j >= 0 ? static_cast<int>(j + co) : -1;
+        snx[sl * N + I] = sg * hm.fn[f];
+        sny[sl * N + I] = sg * hm.fn[nf + f];
+        shs[sl * N + I] = 0.5 * hm.fS[f];
+      }
+    }
+    for (int c = 0; c < hm.n_colours; ++c)
+      for (int32_t i = hm.colour_start[c]; i < hm.colour_start[c + 1]; ++i) {
+        ccol[co + i] = static_cast<unsigned char>(c);
+        lists[c].push_back(static_cast<int>(co + i));
+      }
+    for (int64_t f = 0; f < nf; ++f) {
+      const int64_t G = fo + f;
+      fc0[G] = static_cast<int>(hm.fc0[f] + co);
+      const int32_t c1 = hm.fc1[f];
+      fc1[G] = c1 >= 0 ? static_cast<int>(c1 + co) : -1 - (s * kTagsPerSolve + (-1 - c1));
+      fsid[G] = s;
+      fn[G] = hm.fn[f]; fn[F + G] = hm.fn[nf + f];
+      fS[G] = hm.fS[f];
+      fjump[G] = hm.fdelta[f] > 0.0 ? p.alpha / hm.fdelta[f] : 0.0;
+      for (int q = 0; q < 8; ++q) fxi[q * F + G] = hm.fxi[q * nf + f];
+    }
+  }
+  blk[S] = static_cast<int>(N / kCellBlock);
+  std::vector<int> list;
+  b->list_off.assign(C + 1, 0);
+  for (int c = 0; c < C; ++c) {
+    list.insert(list.end(), lists[c].begin(), lists[c].end());
+    b->list_off[c + 1] = static_cast<int>(list.size());
+  }
+  if (list.empty()) list.push_back(0);
+  // per-colour ranges for the sweeps (the list is used beyond kMaxRanges solves)
+  b->ranges.assign(C, Ranges{});
+  for (int c = 0; c < C; ++c) {
+    Ranges &R = b->ranges[c];
+    std::memset(&R, 0, sizeof(R));
+    int nr = 0, blocks = 0;
+    bool fits = true;
+    for (int s = 0; s < S && fits; ++s) {
+      const HostMesh &hm = *b->mem[s].mesh;
+      if (c >= hm.n_colours) continue;
+      const int beg = static_cast<int>(b->mem[s].cell_off) + hm.colour_start[c];
+      const int end = static_cast<int>(b->mem[s].cell_off) + hm.colour_start[c + 1];
+      if (end == beg) continue;
+      if (nr == kMaxRanges) { fits = false; break; }
+      R.blk[nr] = blocks;
+      R.begin[nr] = beg;
+      R.end[nr] = end;
+      blocks += nblk(end - beg, kSweepCells);
+      ++nr;
+    }
+    if (fits) { R.n = nr; R.blk[nr] = blocks; }
+    else std::memset(&R, 0, sizeof(R));
+  }
+  // colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
+  // C-1..0).  A colour repeated back to back recomputes identical values
+  // (its cells read only other colours), and the first pass is done by
+  // k_lo_rhs, so both are dropped.
+  {
+    std::vector<int> seq;
+    for (int sw = 0; sw < sh.n_sweeps; ++sw) {
+      for (int c = 0; c < C; ++c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+      for (int c = C - 1; c >= 0; --c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+    }
+    if (!seq.empty()) seq.erase(seq.begin());
+    b->sweep_seq = seq;
+  }
+  // ---- device arena
+  DevArrays &d = b->d;
+  std::vector<Piece> pieces;
+  plan_arena(b, N, F, S, static_cast<int64_t>(list.size()), b->mixed, pieces);
+  const size_t total = arena_total(pieces);
+  b->arena = dev_alloc(sh, total);
+  if (!b->arena) return CGKS_ENOMEM;
+  b->arena_bytes = total;
+  {
+    char *cur = static_cast<char *>(b->arena);
+    for (auto &pc : pieces) { *pc.dst = cur; cur += (pc.bytes + 255) & ~size_t(255); }
+  }
+  if (!b->mixed) {
+    Bufs<double> &X = b->bd;
+    X.W = b->W; X.Wx = b->Wx; X.Wn = b->Wn; X.Ws = b->Ws; X.Wxs = b->Wxs; X.U = b->U;
+  }
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = up(d.vol, vol.data(), 8 * N) && up(d.ivol, ivol.data(), 8 * N) && up(d.per, per.data(), 8 * N) &&
+            up(d.ih, ih.data(), 8 * N) && up(d.m2, m2.data(), 8 * m2.size()) && up(d.op, op.data(), 8 * op.size()) &&
+            up(d.snx, snx.data(), 8 * snx.size()) && up(d.sny, sny.data(), 8 * sny.size()) &&
+            up(d.shs, shs.data(), 8 * shs.size()) && up(d.fn, fn.data(), 8 * fn.size()) && up(d.fS, fS.data(), 8 * F) &&
+            up(d.fjump, fjump.data(), 8 * F) && up(d.fxi, fxi.data(), 8 * fxi.size()) && up(d.mu, mu.data(), 8 * S) &&
+            up(d.bcuw, bc_uw.data(), 8 * bc_uw.size()) && up(d.bcrho, bc_rho.data(), 8 * bc_rho.size()) &&
+            up(d.bcu, bc_u.data(), 8 * bc_u.size()) && up(d.bcp, bc_p.data(), 8 * bc_p.size()) &&
+            up(d.cface, cface.data(), 4 * cface.size()) && up(d.cnbr, cnbr.data(), 4 * cnbr.size()) &&
+            up(d.fc0, fc0.data(), 4 * F) && up(d.fc1, fc1.data(), 4 * F) && up(d.csid, csid.data(), 4 * N) &&
+            up(d.fsid, fsid.data(), 4 * F) && up(d.bckind, bc_kind.data(), 4 * bc_kind.size()) &&
+            up(b->list, list.data(), 4 * list.size()) && up(b->perm, perm.data(), 4 * N) &&
+            up(b->blk_begin, blk.data(), 4 * (S + 1)) && up(d.ccol, ccol.data(), N);
+  std::vector<float> tmp;
+  auto upf = [&](float *dst, const std::vector<double> &src) {
+    tmp.assign(src.begin(), src.end());
+    bool r = cudaMemcpyAsync(dst, tmp.data(), 4 * tmp.size(), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    return r && cudaStreamSynchronize(st) == cudaSuccess;   // tmp is reused
+  };
+  if (ok && b->mixed)
+    ok = upf(d.f_ivol, ivol) && upf(d.f_ih, ih) && upf(d.f_m2, m2) && upf(d.f_op, op) && upf(d.f_snx, snx) && upf(d.f_sny, sny) &&
+         upf(d.f_shs, shs) && upf(d.f_fn, fn) && upf(d.f_fS, fS) && upf(d.f_fjump, fjump) && upf(d.f_fxi, fxi) &&
+         upf(d.f_mu, mu) && upf(d.f_bcuw, bc_uw) && upf(d.f_bcrho, bc_rho) && upf(d.f_bcu, bc_u) && upf(d.f_bcp, bc_p);
+  if (ok) ok = cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
+               cudaMemsetAsync(b->status, 0, sizeof(int) * S, st) == cudaSuccess &&
+               cudaMemsetAsync(b->Rp0, 0, sizeof(double) * 4 * N, st) == cudaSuccess &&
+               cudaMemsetAsync(b->res, 0, sizeof(double) * S, st) == cudaSuccess &&
+               cudaMemsetAsync(b->last, 0, sizeof(double) * 4, st) == cudaSuccess;
+  if (ok) {
+    if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * N, st) == cudaSuccess;
+    else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * N, st) == cudaSuccess;
+  }
+  if (ok) {
+    k_fill_padding<<<nblk(N, kCellBlock), kCellBlock, 0, st>>>(static_cast<int>(N), d.csid, b->W, b->Wx,
+                                                               b->mixed ? b->bf.W : nullptr,
+                                                               b->mixed ? b->bf.Wx : nullptr);
+    ok = cudaGetLastError() == cudaSuccess;
+    // the stage and predictor states keep the same inert padding: the
+    // update kernels never write padding cells
+    ok = ok && cudaMemcpyAsync(b->Wn, b->W, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(b->Ws, b->W, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(b->Wxs, b->Wx, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    if (ok && b->mixed)
+      ok = cudaMemcpyAsync(b->bf.Wn, b->bf.W, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(b->bf.Ws, b->bf.W, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(b->bf.Wxs, b->bf.Wx, sizeof(float) * 8 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  if (!ok) { destroy_batch(B.release()); return CGKS_ECUDA; }
+  // kernel-side views
+  fill_shared_params(sh, b->dp);
+  fill_shared_params(sh, b->fp);
+  b->dp.mu = d.mu; b->dp.bc_kind = d.bckind; b->dp.bc_uw = d.bcuw; b->dp.bc_rho = d.bcrho; b->dp.bc_u = d.bcu;
+  b->dp.bc_p = d.bcp;
+  b->fp.mu = d.f_mu; b->fp.bc_kind = d.bckind; b->fp.bc_uw = d.f_bcuw; b->fp.bc_rho = d.f_bcrho; b->fp.bc_u = d.f_bcu;
+  b->fp.bc_p = d.f_bcp;
+  MeshT<double> &dm = b->dm;
+  dm.nc = static_cast<int>(N); dm.nf = static_cast<int>(F);
+  dm.vol = d.vol; dm.ivol = d.ivol; dm.per = d.per; dm.ih = d.ih; dm.m2 = d.m2; dm.op = d.op;
+  dm.fn = d.fn; dm.fS = d.fS; dm.fjump = d.fjump; dm.fxi = d.fxi; dm.snx = d.snx; dm.sny = d.sny; dm.shs = d.shs;
+  dm.cface = d.cface; dm.cnbr = d.cnbr; dm.fc0 = d.fc0; dm.fc1 = d.fc1; dm.csid = d.csid; dm.fsid = d.fsid;
+  dm.ccol = d.ccol;
+  MeshT<float> &fm = b->fm;
+  fm.nc = dm.nc; fm.nf = dm.nf;
+  fm.vol = nullptr; fm.per = nullptr; fm.ivol = d.f_ivol; fm.ih = d.f_ih; fm.m2 = d.f_m2; fm.op = d.f_op;
+  fm.fn = d.f_fn; fm.fS = d.f_fS; fm.fjump = d.f_fjump; fm.fxi = d.f_fxi; fm.snx = d.f_snx; fm.sny = d.f_sny; fm.shs = d.f_shs;
+  fm.cface = d.cface; fm.cnbr = d.cnbr; fm.fc0 = d.fc0; fm.fc1 = d.fc1; fm.csid = d.csid; fm.fsid = d.fsid;
+  fm.ccol = d.ccol;
+  int rc = ensure_hist(b, kHistDefault);
+  if (rc) { destroy_batch(B.release()); return rc; }
+  *out = B.release();
+  return CGKS_OK;
+}
+
+// state of member s from caller-order AoS (host or device staging)
+int load_state(Batch *b, int s, const double *W, const double *Wx, bool device) {
+  const Member &M = b->mem[s];
+  const int64_t n = M.mesh->n_cells;
+  double *wa = b->stage, *wxa = b->stage + 4 * n;
+  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(wa, W, sizeof(double) * 4 * n, kind, b->stream));
+  if (Wx) CK(cudaMemcpyAsync(wxa, Wx, sizeof(double) * 8 * n, kind, b->stream));
+  k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, b->stream>>>(
+      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->N), b->perm + M.cell_off, wa,
+      Wx ? wxa : nullptr, b->W, b->Wx, b->mixed ? b->bf.W : nullptr, b->mixed ? b->bf.Wx : nullptr);
+  b->launches++;
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(b->status + s, 0, sizeof(int), b->stream));
+  return CGKS_OK;
+}
+
+int store_state(Batch *b, int s, double *W, double *Wx, bool device) {
+  const Member &M = b->mem[s];
+  const int64_t n = M.mesh->n_cells;
+  double *wa = b->stage, *wxa = b->stage + 4 * n;
+  k_scatter_state<<<nblk(n, kCellBlock), kCellBlock, 0, b->stream>>>(
+      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->N), b->perm + M.cell_off, b->W, b->Wx, wa,
+      wxa);
+  b->launches++;
+  CK(cudaGetLastError());
+  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (W) CK(cudaMemcpyAsync(W, wa, sizeof(double) * 4 * n, kind, b->stream));
+  if (Wx) CK(cudaMemcpyAsync(Wx, wxa, sizeof(double) * 8 * n, kind, b->stream));
+  if (!device) CK(cudaStreamSynchronize(b->stream));
+  return CGKS_OK;
+}
+
+Shared shared_from(const cgks_params *p) {
+  Shared sh;
+  sh.gamma = p->gamma; sh.cfl_hi = p->cfl_hi; sh.cfl_lo = p->cfl_lo;
+  sh.n_implicit = p->n_implicit; sh.n_sweeps = p->n_sweeps; sh.time_scheme = p->time_scheme;
+  sh.precision = p->precision; sh.use_graph = p->use_graph;
+  sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
+  return sh;
+}
+
+int validate_params(const cgks_params *p, const HostMesh &hm) {
+  if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
+      p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
+      p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0))
+    return CGKS_EINVAL;
+  for (int t : hm.bface_tags_used)
+    if (t >= p->n_bc) return CGKS_EINVAL;
+  for (int b = 0; b < p->n_bc; ++b) {
+    int k = p->bc[b].kind;
+    if (k != CGKS_BC_SLIP && k != CGKS_BC_NOSLIP && k != CGKS_BC_FARFIELD) return CGKS_EINVAL;
+    if (k == CGKS_BC_FARFIELD && !(p->bc[b].rho > 0.0 && p->bc[b].p > 0.0)) return CGKS_EINVAL;
+  }
+  return CGKS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+struct cgks_solver {
+  Batch *b = nullptr;
+  cgks_params params{};
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+  int device = 0;
+  Timer timer;
+  int status_cache = 0;
+};
+
+struct cgks_server {
+  struct Req {
+    int64_t id;
+    std::shared_ptr<const HostMesh> mesh;
+    cgks_params params;
+    std::vector<double> W0;
+    double drop;
+    cgks_req_status st;
+    std::vector<double> result;      // final state, caller order
+    size_t footprint;
+  };
+  Shared sh;
+  int max_active = 64, max_cycles = 20000;
+  size_t budget = 0;
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+  int device = 0;
+  int64_t next_id = 1;
+  std::map<int64_t, std::unique_ptr<Req>> reqs;
+  std::deque<int64_t> queue;
+  std::vector<int64_t> active;     // member s of the batch runs request active[s]
+  Batch *b = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  std::vector<double> res_host;
+  std::vector<int> status_host;
+};
+
+namespace {
+
+int begin_call(cudaStream_t user, cudaStream_t own, cudaEvent_t ev, int device) {
+  CK(cudaSetDevice(device));
+  CK(cudaEventRecord(ev, user));
+  CK(cudaStreamWaitEvent(own, ev, 0));
+  return CGKS_OK;
+}
+int end_call(cudaStream_t user, cudaStream_t own, cudaEvent_t ev) {
+  CK(cudaEventRecord(ev, own));
+  CK(cudaStreamWaitEvent(user, ev, 0));
+  return CGKS_OK;
+}
+int begin_call(cgks_solver *s) { return begin_call(s->user_stream, s->stream, s->ev_user, s->device); }
+int end_call(cgks_solver *s) { return end_call(s->user_stream, s->stream, s->ev_done); }
+
+int solver_status(cgks_solver *s) {
   int st = 0;
-  CK(cudaMemcpyAsync(&st, &s->sc->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&st, s->b->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   s->status_cache = st;
   return st ? CGKS_EDIVERGED : CGKS_OK;
 }
 
-void collect_timing(cgks_solver *s) {
-  for (auto &e : s->tev) {
-    float ms = 0.f;
-    cudaEventSynchronize(e.second.second);
-    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
-    s->t_ms[e.first] += ms;
-    s->t_cnt[e.first] += 1;
-    cudaEventDestroy(e.second.first);
-    cudaEventDestroy(e.second.second);
-  }
-  s->tev.clear();
-}
-
-template <typename T>
-void fill_params(const cgks_params *p, ParamsT<T> &P) {
-  double K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
-  P.gamma = static_cast<T>(p->gamma);
-  P.K = static_cast<T>(K);
-  P.mu = static_cast<T>(p->mu);
-  P.cfl_hi = static_cast<T>(p->cfl_hi);
-  P.cfl_lo = static_cast<T>(p->cfl_lo);
-  P.kc.K = static_cast<T>(K);
-  P.kc.c2K = static_cast<T>(2.0 / (K + 2.0));
-  P.kc.c4K = static_cast<T>(4.0 / (K + 2.0));
-  for (int b = 0; b < CGKS_MAX_BC; ++b) {
-    const cgks_bc &bc = p->bc[b];
-    P.bc_kind[b] = b < p->n_bc ? bc.kind : CGKS_BC_SLIP;
-    P.bc_uw[b][0] = static_cast<T>(bc.u_wall[0]);
-    P.bc_uw[b][1] = static_cast<T>(bc.u_wall[1]);
-    P.bc_rho[b] = static_cast<T>(bc.rho);
-    P.bc_u[b][0] = static_cast<T>(bc.u[0]);
-    P.bc_u[b][1] = static_cast<T>(bc.u[1]);
-    P.bc_p[b] = static_cast<T>(bc.p);
-  }
+double now_s(const cgks_server *v) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - v->t0).count();
 }
 
 }  // namespace
@@ -984,23 +859,6 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
   return CGKS_OK;
 }
 
-// device bytes of a solver: FP64 state/accumulation + geometry + the flux
-// arrays in the flux type (doubles in FP64 mode, floats in mixed mode with
-// float mirrors of the state and of the geometry)
-static size_t solver_bytes(int64_t nc, int64_t nf, bool mixed) {
-  const size_t d_cells = 4 * 5 + 8 * 2 + 4 * 3 + 12 + 6 + 3 + kNCol * kNM;  // W..Wxs, U, Rp0, Src, stage, geometry, op
-  const size_t d_faces = 2 + 1 + 1 + 8;                                   // fn, fS, fjump, fxi
-  const size_t d_slots = 3 * kMaxFace;                                    // slot normals, S/2
-  const size_t t_cells = 4 + 8 + 4 + 4 + 8 + 4 + 20 + D::NPRIM + 4 + 1 + 4;  // mirrors, coef, prim, Rk, invD, dU
-  const size_t t_faces = 16 * 2 + 4 + 1 + (mixed ? 0 : 8);               // FA, FB, Flo, lam, E0/E1
-  const size_t f_geo_c = mixed ? (1 + 1 + 3 + kNCol * kNM + 3 * kMaxFace) : 0;  // float ivol, ih, m2, op, slots
-  const size_t f_geo_f = mixed ? 12 : 0;
-  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
-  return sizeof(double) * ((d_cells + d_slots) * nc + d_faces * nf) + tsz * ((t_cells + kMaxFace) * nc + t_faces * nf) +
-         sizeof(float) * (f_geo_c * nc + f_geo_f * nf) + sizeof(int) * (8 * nc + 2 * nf + nc) +
-         sizeof(double) * (2 * ((nc + kCellBlock - 1) / kCellBlock) + 16) + 64 * 256 + sizeof(Scalars);
-}
-
 int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
   if (!m || !out) return CGKS_EINVAL;
   out->n_cells = m->h.n_cells;
@@ -1008,7 +866,7 @@ int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
   out->n_bfaces = m->h.n_bfaces;
   out->n_colours = m->h.n_colours;
   out->dim = m->h.dim;
-  out->device_bytes = static_cast<int64_t>(solver_bytes(m->h.n_cells, m->h.n_faces, false));
+  out->device_bytes = static_cast<int64_t>(solve_footprint(m->h.n_cells, m->h.n_faces, false));
   return CGKS_OK;
 }
 
@@ -1028,11 +886,8 @@ int cgks_solver_destroy(cgks_solver *s) {
   if (!s) return CGKS_OK;
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
-  collect_timing(s);
-  if (s->g_cycle) cudaGraphExecDestroy(s->g_cycle);
-  if (s->g_step) cudaGraphExecDestroy(s->g_step);
-  dev_free(s, s->hist);
-  dev_free(s, s->arena);
+  collect_timing(&s->timer);
+  destroy_batch(s->b);
   if (s->ev_user) cudaEventDestroy(s->ev_user);
   if (s->ev_done) cudaEventDestroy(s->ev_done);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -1043,185 +898,39 @@ int cgks_solver_destroy(cgks_solver *s) {
 int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **out) {
   if (!m || !p || !out) return CGKS_EINVAL;
   *out = nullptr;
-  if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
-      p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
-      p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED))
-    return CGKS_EINVAL;
-  for (int t : m->h.bface_tags_used)
-    if (t >= p->n_bc) return CGKS_EINVAL;
-  for (int b = 0; b < p->n_bc; ++b) {
-    int k = p->bc[b].kind;
-    if (k != CGKS_BC_SLIP && k != CGKS_BC_NOSLIP && k != CGKS_BC_FARFIELD) return CGKS_EINVAL;
-    if (k == CGKS_BC_FARFIELD && !(p->bc[b].rho > 0.0 && p->bc[b].p > 0.0)) return CGKS_EINVAL;
-  }
+  int rc = validate_params(p, m->h);
+  if (rc) return rc;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CGKS_ECUDA;
   cgks_solver *s = new (std::nothrow) cgks_solver();
   if (!s) return CGKS_ENOMEM;
-  s->hm = m->h;
   s->params = *p;
-  s->mixed = p->precision == CGKS_MIXED;
   cudaGetDevice(&s->device);
   s->user_stream = static_cast<cudaStream_t>(p->stream);
-  auto fail = [&](int rc) { cgks_solver_destroy(s); return rc; };
+  auto fail = [&](int r) { cgks_solver_destroy(s); return r; };
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
-  fill_params(p, s->dp);
-  fill_params(p, s->fp);
-  // operators depend on which tags are walls
-  std::vector<char> wall(CGKS_MAX_BC, 0);
-  for (int b = 0; b < p->n_bc; ++b) wall[b] = p->bc[b].kind != CGKS_BC_FARFIELD;
-  std::vector<double> op;
+  std::vector<Member> mem(1);
   try {
-    build_operator(s->hm, wall, op);
+    mem[0].mesh = std::make_shared<HostMesh>(m->h);
   } catch (const std::bad_alloc &) {
     return fail(CGKS_ENOMEM);
   }
-  const int64_t nc = s->hm.n_cells, nf = s->hm.n_faces;
-  s->nblk_cell = nblk(static_cast<int>(nc), kCellBlock);
-  // carve one arena
-  struct Piece { void **dst; size_t bytes; };
-  std::vector<Piece> pieces;
-  auto D8 = [&](double **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(double) * cnt }); };
-  auto F4 = [&](float **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(float) * cnt }); };
-  auto I4 = [&](int **d, int64_t cnt) { pieces.push_back({ reinterpret_cast<void **>(d), sizeof(int) * cnt }); };
-  double *vol, *ivol, *per, *ih, *m2, *opd, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs;
-  int *cface, *cnbr, *fc0, *fc1;
-  D8(&s->W, 4 * nc); D8(&s->Wx, 8 * nc); D8(&s->Wn, 4 * nc); D8(&s->Ws, 4 * nc); D8(&s->Wxs, 8 * nc);
-  D8(&s->U, 4 * nc); D8(&s->Rp0, 4 * nc); D8(&s->Src, 4 * nc);
-  D8(&s->partial, 2 * std::max(s->nblk_cell, 1)); D8(&s->last, 4); D8(&s->stage_aos, 12 * nc);
-  D8(&vol, nc); D8(&ivol, nc); D8(&per, nc); D8(&ih, nc); D8(&m2, 3 * nc); D8(&opd, kNCol * kNM * nc);
-  D8(&fn, 2 * nf); D8(&fS, nf); D8(&fjump, nf); D8(&fxi, 8 * nf);
-  D8(&snx, kMaxFace * nc); D8(&sny, kMaxFace * nc); D8(&shs, kMaxFace * nc);
-  I4(&cface, kMaxFace * nc); I4(&cnbr, kMaxFace * nc); I4(&fc0, nf); I4(&fc1, nf); I4(&s->perm, nc);
-  float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
-        *f_fjump = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr;
-  if (!s->mixed) {
-    Bufs<double> &B = s->bd;
-    D8(&B.coef, 20 * nc); D8(&B.FA, 16 * nf); D8(&B.FB, 16 * nf);
-    D8(&B.prim, D::NPRIM * nc); D8(&B.Flo, 4 * nf); D8(&B.lam, nf); D8(&B.E0, 4 * nf); D8(&B.E1, 4 * nf);
-    D8(&B.Rk, 4 * nc); D8(&B.invD, nc); D8(&B.dU, 4 * nc); D8(&B.lamS, kMaxFace * nc);
-  } else {
-    Bufs<float> &B = s->bf;
-    F4(&B.W, 4 * nc); F4(&B.Wx, 8 * nc); F4(&B.Wn, 4 * nc); F4(&B.Ws, 4 * nc); F4(&B.Wxs, 8 * nc); F4(&B.U, 4 * nc);
-    F4(&B.coef, 20 * nc); F4(&B.FA, 16 * nf); F4(&B.FB, 16 * nf);
-    F4(&B.prim, D::NPRIM * nc); F4(&B.Flo, 4 * nf); F4(&B.lam, nf);
-    F4(&B.Rk, 4 * nc); F4(&B.invD, nc); F4(&B.dU, 4 * nc); F4(&B.lamS, kMaxFace * nc);
-    F4(&f_ivol, nc); F4(&f_ih, nc); F4(&f_m2, 3 * nc); F4(&f_op, kNCol * kNM * nc);
-    F4(&f_fn, 2 * nf); F4(&f_fS, nf); F4(&f_fjump, nf); F4(&f_fxi, 8 * nf);
-    F4(&f_snx, kMaxFace * nc); F4(&f_sny, kMaxFace * nc); F4(&f_shs, kMaxFace * nc);
-  }
-  pieces.push_back({ reinterpret_cast<void **>(&s->sc), sizeof(Scalars) });
-  size_t total = 0;
-  for (auto &pc : pieces) total += (pc.bytes + 255) & ~size_t(255);
-  s->arena = dev_alloc(s, total);
-  if (!s->arena) return fail(CGKS_ENOMEM);
-  s->arena_bytes = total;
-  {
-    char *cur = static_cast<char *>(s->arena);
-    for (auto &pc : pieces) { *pc.dst = cur; cur += (pc.bytes + 255) & ~size_t(255); }
-  }
-  if (!s->mixed) {
-    Bufs<double> &B = s->bd;
-    B.W = s->W; B.Wx = s->Wx; B.Wn = s->Wn; B.Ws = s->Ws; B.Wxs = s->Wxs; B.U = s->U;
-  }
-  auto up = [&](void *dst, const void *src, size_t bytes) {
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
-  };
-  const HostMesh &hm = s->hm;
-  // derived per-solver arrays: reciprocals and the jump coefficient alpha/delta
-  std::vector<double> h_ivol(nc), h_ih(nc), h_jump(nf);
-  for (int64_t i = 0; i < nc; ++i) { h_ivol[i] = 1.0 / hm.vol[i]; h_ih[i] = 1.0 / hm.h[i]; }
-  for (int64_t f = 0; f < nf; ++f) h_jump[f] = hm.fdelta[f] > 0.0 ? p->alpha / hm.fdelta[f] : 0.0;
-  // per face slot: the cell's outward unit normal and half the face length
-  std::vector<double> h_snx(kMaxFace * nc, 0.0), h_sny(kMaxFace * nc, 0.0), h_shs(kMaxFace * nc, 0.0);
-  for (int64_t i = 0; i < nc; ++i)
-    for (int sl = 0; sl < kMaxFace; ++sl) {
-      int32_t fs = hm.cface[sl * nc + i];
-      if (fs == kNoFace) continue;
-      int32_t f = fs >= 0 ? fs : ~fs;
-      double sg = fs >= 0 ? 1.0 : -1.0;
-      h_snx[sl * nc + i] = sg * hm.fn[f];
-      h_sny[sl * nc + i] = sg * hm.fn[nf + f];
-      h_shs[sl * nc + i] = 0.5 * hm.fS[f];
-    }
-  bool ok = up(vol, hm.vol.data(), 8 * nc) && up(ivol, h_ivol.data(), 8 * nc) && up(per, hm.per.data(), 8 * nc) &&
-            up(ih, h_ih.data(), 8 * nc) && up(m2, hm.m2.data(), 8 * 3 * nc) && up(opd, op.data(), 8 * op.size()) &&
-            up(fn, hm.fn.data(), 8 * 2 * nf) && up(fS, hm.fS.data(), 8 * nf) && up(fjump, h_jump.data(), 8 * nf) &&
-            up(fxi, hm.fxi.data(), 8 * 8 * nf) && up(cface, hm.cface.data(), 4 * kMaxFace * nc) &&
-            up(cnbr, hm.cnbr.data(), 4 * kMaxFace * nc) && up(fc0, hm.fc0.data(), 4 * nf) &&
-            up(fc1, hm.fc1.data(), 4 * nf) && up(s->perm, hm.perm.data(), 4 * nc) &&
-            up(snx, h_snx.data(), 8 * kMaxFace * nc) && up(sny, h_sny.data(), 8 * kMaxFace * nc) &&
-            up(shs, h_shs.data(), 8 * kMaxFace * nc);
-  std::vector<float> tmp;
-  auto upf = [&](float *dst, const double *src, size_t cnt) {
-    tmp.assign(src, src + cnt);
-    bool r = cudaMemcpyAsync(dst, tmp.data(), 4 * cnt, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
-    return r && cudaStreamSynchronize(s->stream) == cudaSuccess;   // tmp is reused
-  };
-  if (ok && s->mixed)
-    ok = upf(f_ivol, h_ivol.data(), nc) && upf(f_ih, h_ih.data(), nc) && upf(f_m2, hm.m2.data(), 3 * nc) &&
-         upf(f_op, op.data(), op.size()) && upf(f_fn, hm.fn.data(), 2 * nf) && upf(f_fS, hm.fS.data(), nf) &&
-         upf(f_fjump, h_jump.data(), nf) && upf(f_fxi, hm.fxi.data(), 8 * nf) &&
-         upf(f_snx, h_snx.data(), kMaxFace * nc) && upf(f_sny, h_sny.data(), kMaxFace * nc) &&
-         upf(f_shs, h_shs.data(), kMaxFace * nc);
-  if (!ok) return fail(CGKS_ECUDA);
-  if (cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  if (cudaMemsetAsync(s->W, 0, sizeof(double) * 12 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  if (cudaMemsetAsync(s->Rp0, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  if (s->mixed) {
-    if (cudaMemsetAsync(s->bf.dU, 0, sizeof(float) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-    if (cudaMemsetAsync(s->bf.W, 0, sizeof(float) * 4 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-    if (cudaMemsetAsync(s->bf.Wx, 0, sizeof(float) * 8 * nc, s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  } else if (cudaMemsetAsync(s->bd.dU, 0, sizeof(double) * 4 * nc, s->stream) != cudaSuccess) {
-    return fail(CGKS_ECUDA);
-  }
-  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(CGKS_ECUDA);
-  MeshT<double> &dm = s->dm;
-  dm.nc = static_cast<int>(nc); dm.nf = static_cast<int>(nf);
-  dm.vol = vol; dm.ivol = ivol; dm.per = per; dm.ih = ih; dm.m2 = m2; dm.op = opd;
-  dm.fn = fn; dm.fS = fS; dm.fjump = fjump; dm.fxi = fxi; dm.snx = snx; dm.sny = sny; dm.shs = shs;
-  dm.cface = cface; dm.cnbr = cnbr; dm.fc0 = fc0; dm.fc1 = fc1;
-  MeshT<float> &fm = s->fm;
-  fm.nc = dm.nc; fm.nf = dm.nf;
-  fm.vol = nullptr; fm.per = nullptr; fm.ivol = f_ivol; fm.ih = f_ih; fm.m2 = f_m2; fm.op = f_op;
-  fm.fn = f_fn; fm.fS = f_fS; fm.fjump = f_fjump; fm.fxi = f_fxi; fm.snx = f_snx; fm.sny = f_sny; fm.shs = f_shs;
-  fm.cface = cface; fm.cnbr = cnbr; fm.fc0 = fc0; fm.fc1 = fc1;
-  // Colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
-  // C-1..0).  A colour repeated back to back recomputes identical values
-  // (its cells read only other colours), and the first pass is done by
-  // k_lo_rhs, so both are dropped.
-  {
-    std::vector<int> seq;
-    const int C = s->hm.n_colours;
-    for (int sw = 0; sw < p->n_sweeps; ++sw) {
-      for (int c = 0; c < C; ++c) if (seq.empty() || seq.back() != c) seq.push_back(c);
-      for (int c = C - 1; c >= 0; --c) if (seq.empty() || seq.back() != c) seq.push_back(c);
-    }
-    if (!seq.empty()) seq.erase(seq.begin());
-    s->sweep_colours = seq;
-  }
-  if (ensure_hist(s, 1024) != CGKS_OK) return fail(CGKS_ENOMEM);
+  mem[0].params = *p;
+  rc = build_batch(shared_from(p), std::move(mem), s->stream, &s->b);
+  if (rc) return fail(rc);
+  s->b->timer = &s->timer;
   *out = s;
   return CGKS_OK;
 }
 
 static int set_state_impl(cgks_solver *s, const double *W, const double *Wx, bool device) {
   if (!s || !W) return CGKS_EINVAL;
-  const int n = s->dm.nc;
   int rc = begin_call(s);
   if (rc) return rc;
-  double *wa = s->stage_aos, *wxa = s->stage_aos + 4 * n;
-  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(wa, W, sizeof(double) * 4 * n, kind, s->stream));
-  if (Wx) CK(cudaMemcpyAsync(wxa, Wx, sizeof(double) * 8 * n, kind, s->stream));
-  k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, wa, Wx ? wxa : nullptr, s->W, s->Wx,
-                                                                    s->mixed ? s->bf.W : nullptr,
-                                                                    s->mixed ? s->bf.Wx : nullptr);
-  s->launches++;
-  CK(cudaGetLastError());
-  CK(cudaMemsetAsync(&s->sc->status, 0, sizeof(int), s->stream));
+  rc = load_state(s->b, 0, W, Wx, device);
+  if (rc) return rc;
   s->status_cache = 0;
   return end_call(s);
 }
@@ -1231,17 +940,10 @@ int cgks_set_state_device(cgks_solver *s, const double *W, const double *Wx) { r
 
 static int get_state_impl(cgks_solver *s, double *W, double *Wx, bool device) {
   if (!s) return CGKS_EINVAL;
-  const int n = s->dm.nc;
   int rc = begin_call(s);
   if (rc) return rc;
-  double *wa = s->stage_aos, *wxa = s->stage_aos + 4 * n;
-  k_scatter_state<<<nblk(n, kCellBlock), kCellBlock, 0, s->stream>>>(n, s->perm, s->W, s->Wx, wa, wxa);
-  s->launches++;
-  CK(cudaGetLastError());
-  cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (W) CK(cudaMemcpyAsync(W, wa, sizeof(double) * 4 * n, kind, s->stream));
-  if (Wx) CK(cudaMemcpyAsync(Wx, wxa, sizeof(double) * 8 * n, kind, s->stream));
-  if (!device) CK(cudaStreamSynchronize(s->stream));
+  rc = store_state(s->b, 0, W, Wx, device);
+  if (rc) return rc;
   return end_call(s);
 }
 
@@ -1253,67 +955,56 @@ int cgks_highorder_step(cgks_solver *s, double dt, double *dt_used) {
   if (s->status_cache) return CGKS_EDIVERGED;
   int rc = begin_call(s);
   if (rc) return rc;
-  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
-  enqueue_explicit_step(s, dt);
+  Batch *b = s->b;
+  CK(cudaMemsetAsync(&b->ctl->res_ctr, 0, sizeof(int), s->stream));
+  enqueue_explicit_step(b, dt);
   CK(cudaGetLastError());
-  Scalars h;
-  CK(cudaMemcpyAsync(&h, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s->stream));
+  Ctl c;
+  unsigned long long bits = 0;
+  int st = 0;
+  CK(cudaMemcpyAsync(&c, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&bits, b->dt_bits, sizeof(bits), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  if (s->timing) collect_timing(s);
-  if (dt_used) *dt_used = h.dt_fixed > 0.0 ? h.dt_fixed : s->params.cfl_hi * __builtin_bit_cast(double, h.dt_bits);
-  s->status_cache = h.status;
+  collect_timing(&s->timer);
+  if (dt_used) *dt_used = c.dt_fixed > 0.0 ? c.dt_fixed : s->params.cfl_hi * __builtin_bit_cast(double, bits);
+  s->status_cache = st;
   rc = end_call(s);
   if (rc) return rc;
-  return h.status ? CGKS_EDIVERGED : CGKS_OK;
+  return st ? CGKS_EDIVERGED : CGKS_OK;
 }
 
-static int run_many(cgks_solver *s, int n, double *res_hist, bool cycle) {
+static int solver_run(cgks_solver *s, int n, double *res_hist, bool cycle) {
   if (!s || n < 0) return CGKS_EINVAL;
   if (s->status_cache) return CGKS_EDIVERGED;
   if (n == 0) return CGKS_OK;
-  int rc = ensure_hist(s, n);
+  Batch *b = s->b;
+  int rc = ensure_hist(b, n);
   if (rc) return rc;
   rc = begin_call(s);
   if (rc) return rc;
-  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
-  bool graph = s->params.use_graph && !s->timing;
-  cudaGraphExec_t *ge = cycle ? &s->g_cycle : &s->g_step;
-  if (graph && !*ge) {
-    rc = capture(s, cycle, ge);
-    if (rc) return rc;
-  }
-  long long per = count_launches(s, cycle);
-  for (int k = 0; k < n; ++k) {
-    if (graph) {
-      CK(cudaGraphLaunch(*ge, s->stream));
-      s->launches += per;
-    } else if (cycle) {
-      enqueue_cycle(s);
-    } else {
-      enqueue_explicit_step(s, -1.0);
-    }
-  }
-  CK(cudaGetLastError());
-  if (res_hist) CK(cudaMemcpyAsync(res_hist, s->hist, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
-  rc = read_status(s);
-  if (s->timing) collect_timing(s);
+  rc = run_many(b, n, cycle);
+  if (rc) return rc;
+  if (res_hist) CK(cudaMemcpyAsync(res_hist, b->hist, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+  rc = solver_status(s);
+  collect_timing(&s->timer);
   int rc2 = end_call(s);
   return rc ? rc : rc2;
 }
 
-int cgks_explicit_steps(cgks_solver *s, int n, double *res_hist) { return run_many(s, n, res_hist, false); }
-int cgks_pmg_cycle(cgks_solver *s, int n_cycles, double *res_hist) { return run_many(s, n_cycles, res_hist, true); }
+int cgks_explicit_steps(cgks_solver *s, int n, double *res_hist) { return solver_run(s, n, res_hist, false); }
+int cgks_pmg_cycle(cgks_solver *s, int n_cycles, double *res_hist) { return solver_run(s, n_cycles, res_hist, true); }
 
 int cgks_loworder_smooth(cgks_solver *s) {
   if (!s) return CGKS_EINVAL;
   if (s->status_cache) return CGKS_EDIVERGED;
   int rc = begin_call(s);
   if (rc) return rc;
-  CK(cudaMemsetAsync(&s->sc->res_ctr, 0, sizeof(int), s->stream));
-  enqueue_lo_smooth(s);
+  CK(cudaMemsetAsync(&s->b->ctl->res_ctr, 0, sizeof(int), s->stream));
+  enqueue_lo_smooth(s->b);
   CK(cudaGetLastError());
-  rc = read_status(s);
-  if (s->timing) collect_timing(s);
+  rc = solver_status(s);
+  collect_timing(&s->timer);
   int rc2 = end_call(s);
   return rc ? rc : rc2;
 }
@@ -1322,20 +1013,21 @@ int cgks_residual(cgks_solver *s, double *res, double *r_l2) {
   if (!s) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
+  Batch *b = s->b;
   double last[3];
-  CK(cudaMemcpyAsync(last, s->last, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(last, b->last, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
   std::vector<double> R;
   if (r_l2) {
-    R.resize(4 * static_cast<size_t>(s->dm.nc));
-    CK(cudaMemcpyAsync(R.data(), s->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
+    R.resize(4 * static_cast<size_t>(b->N));
+    CK(cudaMemcpyAsync(R.data(), b->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
   }
   CK(cudaStreamSynchronize(s->stream));
   if (res) *res = last[0];
   if (r_l2) {
-    const int n = s->dm.nc;
+    const int64_t n = b->mem[0].mesh->n_cells, N = b->N;
     for (int v = 0; v < 4; ++v) {
       double a = 0.0;
-      for (int i = 0; i < n; ++i) a += R[v * n + i] * R[v * n + i];
+      for (int64_t i = 0; i < n; ++i) a += R[v * N + i] * R[v * N + i];
       r_l2[v] = std::sqrt(a);
     }
   }
@@ -1346,13 +1038,15 @@ int cgks_get_rp0(cgks_solver *s, double *Rp0) {
   if (!s || !Rp0) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
-  const int n = s->dm.nc;
-  std::vector<double> R(4 * static_cast<size_t>(n));
-  CK(cudaMemcpyAsync(R.data(), s->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
+  Batch *b = s->b;
+  const int64_t N = b->N, n = b->mem[0].mesh->n_cells;
+  std::vector<double> R(4 * static_cast<size_t>(N));
+  CK(cudaMemcpyAsync(R.data(), b->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  for (int i = 0; i < n; ++i) {
-    int c = s->hm.perm[i];
-    for (int v = 0; v < 4; ++v) Rp0[4 * c + v] = R[v * n + i];
+  const HostMesh &hm = *b->mem[0].mesh;
+  for (int64_t i = 0; i < n; ++i) {
+    int c = hm.perm[i];
+    for (int v = 0; v < 4; ++v) Rp0[4 * c + v] = R[v * N + i];
   }
   return end_call(s);
 }
@@ -1362,20 +1056,20 @@ int cgks_get_rp0(cgks_solver *s, double *Rp0) {
 int cgks_set_timing(cgks_solver *s, int on) {
   if (!s) return CGKS_EINVAL;
   cudaStreamSynchronize(s->stream);
-  collect_timing(s);
-  s->timing = on != 0;
+  collect_timing(&s->timer);
+  s->timer.on = on != 0;
   return CGKS_OK;
 }
 
 int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_ms, int64_t *count) {
   if (!s) return CGKS_EINVAL;
   cudaStreamSynchronize(s->stream);
-  collect_timing(s);
+  collect_timing(&s->timer);
   int k = 0;
   for (; k < KI_COUNT && k < max; ++k) {
     if (names) names[k] = kKernelNames[k];
-    if (total_ms) total_ms[k] = s->t_ms[k];
-    if (count) count[k] = s->t_cnt[k];
+    if (total_ms) total_ms[k] = s->timer.ms[k];
+    if (count) count[k] = s->timer.cnt[k];
   }
   return k;
 }
@@ -1383,15 +1077,304 @@ int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_m
 int cgks_reset_timing(cgks_solver *s) {
   if (!s) return CGKS_EINVAL;
   cudaStreamSynchronize(s->stream);
-  collect_timing(s);
-  for (int k = 0; k < KI_COUNT; ++k) { s->t_ms[k] = 0.0; s->t_cnt[k] = 0; }
+  collect_timing(&s->timer);
+  for (int k = 0; k < KI_COUNT; ++k) { s->timer.ms[k] = 0.0; s->timer.cnt[k] = 0; }
   return CGKS_OK;
 }
 
-int64_t cgks_launch_count(const cgks_solver *s) { return s ? s->launches : -1; }
+int64_t cgks_launch_count(const cgks_solver *s) { return s ? s->b->launches : -1; }
 
 int cgks_launches_per_call(const cgks_solver *s, int cycle) {
-  return s ? static_cast<int>(count_launches(const_cast<cgks_solver *>(s), cycle != 0)) : -1;
+  return s ? static_cast<int>(count_launches(s->b, cycle != 0)) : -1;
+}
+
+// ================================ serving ================================
+void cgks_server_default_opts(cgks_server_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = CGKS_FP64;
+  o->time_scheme = CGKS_S1O2;
+  o->cfl_hi = 0.4;
+  o->cfl_lo = 1000.0;
+  o->n_implicit = 6;
+  o->n_sweeps = 2;
+  o->max_active = 64;
+  o->max_cycles = 20000;
+  o->use_graph = 1;
+}
+
+int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server **out) {
+  if (!o || !out || hbm_budget == 0 || o->max_active < 1 || o->max_cycles < 1 || !(o->cfl_hi > 0.0) ||
+      !(o->cfl_lo > 0.0) || o->n_implicit < 0 || o->n_sweeps < 0 ||
+      (o->precision != CGKS_FP64 && o->precision != CGKS_MIXED) ||
+      (o->time_scheme != CGKS_S1O2 && o->time_scheme != CGKS_S2O4))
+    return CGKS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CGKS_ECUDA;
+  cgks_server *v = new (std::nothrow) cgks_server();
+  if (!v) return CGKS_ENOMEM;
+  v->sh.cfl_hi = o->cfl_hi; v->sh.cfl_lo = o->cfl_lo; v->sh.n_implicit = o->n_implicit; v->sh.n_sweeps = o->n_sweeps;
+  v->sh.time_scheme = o->time_scheme; v->sh.precision = o->precision; v->sh.use_graph = o->use_graph;
+  v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
+  v->max_active = o->max_active;
+  v->max_cycles = o->max_cycles;
+  v->budget = hbm_budget;
+  v->user_stream = static_cast<cudaStream_t>(o->stream);
+  cudaGetDevice(&v->device);
+  v->t0 = std::chrono::steady_clock::now();
+  if (cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&v->ev_user, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&v->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+    cgks_server_destroy(v);
+    return CGKS_ECUDA;
+  }
+  *out = v;
+  return CGKS_OK;
+}
+
+int cgks_server_destroy(cgks_server *v) {
+  if (!v) return CGKS_OK;
+  cudaSetDevice(v->device);
+  destroy_batch(v->b);
+  if (v->ev_user) cudaEventDestroy(v->ev_user);
+  if (v->ev_done) cudaEventDestroy(v->ev_done);
+  if (v->stream) cudaStreamDestroy(v->stream);
+  delete v;
+  return CGKS_OK;
+}
+
+int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p, const double *W0, double res_drop,
+                       int64_t *req_id) {
+  if (!v || !m || !p || !W0 || !(res_drop > 0.0)) return CGKS_EINVAL;
+  cgks_params q = *p;   // batch-wide fields come from the server
+  q.cfl_hi = v->sh.cfl_hi; q.cfl_lo = v->sh.cfl_lo; q.n_implicit = v->sh.n_implicit; q.n_sweeps = v->sh.n_sweeps;
+  q.time_scheme = v->sh.time_scheme; q.precision = v->sh.precision;
+  int rc = validate_params(&q, m->h);
+  if (rc) return rc;
+  if (std::fabs(q.gamma - v->sh.gamma) > 1e-15) {
+    if (v->reqs.empty()) v->sh.gamma = q.gamma;
+    else return CGKS_EINVAL;   // every solve of a server shares gamma
+  }
+  std::unique_ptr<cgks_server::Req> r(new (std::nothrow) cgks_server::Req());
+  if (!r) return CGKS_ENOMEM;
+  try {
+    r->mesh = std::make_shared<HostMesh>(m->h);
+    r->W0.assign(W0, W0 + 4 * m->h.n_cells);
+  } catch (const std::bad_alloc &) {
+    return CGKS_ENOMEM;
+  }
+  r->id = v->next_id++;
+  r->params = q;
+  r->drop = res_drop;
+  std::memset(&r->st, 0, sizeof(r->st));
+  r->st.n_cells = m->h.n_cells;
+  r->st.t_submit = now_s(v);
+  r->footprint = solve_footprint(m->h.n_cells, m->h.n_faces, v->sh.precision == CGKS_MIXED);
+  const int64_t id = r->id;
+  if (req_id) *req_id = id;
+  if (r->footprint > v->budget) {
+    r->st.state = CGKS_REQ_REJECTED;
+    r->st.t_done = r->st.t_submit;
+    v->reqs[id] = std::move(r);
+    return CGKS_EBUDGET;
+  }
+  r->st.state = CGKS_REQ_QUEUED;
+  v->reqs[id] = std::move(r);
+  v->queue.push_back(id);
+  return CGKS_OK;
+}
+
+// Replace the active batch by one running `next`.  Continuing solves keep
+// their device state: it is stashed compactly, the old batch is freed, the
+// new batch is built and the stash is moved in, so device memory never
+// holds two batches at once.
+static int server_rebuild(cgks_server *v, const std::vector<int64_t> &next) {
+  Batch *old = v->b;
+  v->b = nullptr;
+  // continuing solves: (index in next, index in old)
+  std::vector<std::pair<int, int>> cont;
+  for (size_t s = 0; s < next.size(); ++s)
+    for (size_t k = 0; k < v->active.size(); ++k)
+      if (v->active[k] == next[s]) cont.push_back({ static_cast<int>(s), static_cast<int>(k) });
+  int64_t n_st = 0;
+  for (auto &c : cont) n_st += old->mem[c.second].mesh->n_cells;
+  std::vector<int64_t> st_off(cont.size());
+  char *stash = nullptr;
+  double *sW = nullptr, *sWx = nullptr;
+  int *smap = nullptr;
+  int64_t N_new = 0;
+  for (int64_t id : next) N_new += pad_cells(v->reqs[id]->mesh->n_cells);
+  v->active.clear();
+  if (n_st > 0) {
+    const size_t bytes = sizeof(double) * 12 * n_st + sizeof(int) * std::max(n_st, N_new) + 512;
+    stash = static_cast<char *>(dev_alloc(v->sh, bytes));
+    if (!stash) { destroy_batch(old); return CGKS_ENOMEM; }
+    sW = reinterpret_cast<double *>(stash);
+    sWx = sW + 4 * n_st;
+    smap = reinterpret_cast<int *>(sWx + 8 * n_st);
+    std::vector<int> map(n_st);
+    int64_t o = 0;
+    for (size_t c = 0; c < cont.size(); ++c) {
+      const Member &O = old->mem[cont[c].second];
+      st_off[c] = o;
+      for (int64_t i = 0; i < O.mesh->n_cells; ++i) map[o + i] = static_cast<int>(O.cell_off + i);
+      o += O.mesh->n_cells;
+    }
+    CK(cudaMemcpyAsync(smap, map.data(), sizeof(int) * n_st, cudaMemcpyHostToDevice, v->stream));
+    k_move_state<<<nblk(n_st, kCellBlock), kCellBlock, 0, v->stream>>>(
+        static_cast<int>(n_st), static_cast<int>(old->N), smap, old->W, old->Wx, sW, sWx, nullptr, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(v->stream));
+  }
+  destroy_batch(old);
+  auto fail = [&](int rc) { dev_free(v->sh, stash); return rc; };
+  if (next.empty()) return fail(CGKS_OK);
+  std::vector<Member> mem(next.size());
+  for (size_t s = 0; s < next.size(); ++s) {
+    mem[s].mesh = v->reqs[next[s]]->mesh;
+    mem[s].params = v->reqs[next[s]]->params;
+  }
+  Batch *nb = nullptr;
+  int rc = build_batch(v->sh, std::move(mem), v->stream, &nb);
+  if (rc) return fail(rc);
+  if (n_st > 0) {
+    std::vector<int> map(nb->N, -1);
+    for (size_t c = 0; c < cont.size(); ++c) {
+      const Member &M = nb->mem[cont[c].first];
+      for (int64_t i = 0; i < M.mesh->n_cells; ++i) map[M.cell_off + i] = static_cast<int>(st_off[c] + i);
+    }
+    if (cudaMemcpyAsync(smap, map.data(), sizeof(int) * nb->N, cudaMemcpyHostToDevice, v->stream) != cudaSuccess) {
+      destroy_batch(nb);
+      return fail(CGKS_ECUDA);
+    }
+    k_move_state<<<nblk(nb->N, kCellBlock), kCellBlock, 0, v->stream>>>(
+        static_cast<int>(nb->N), static_cast<int>(n_st), smap, sW, sWx, nb->W, nb->Wx,
+        nb->mixed ? nb->bf.W : nullptr, nb->mixed ? nb->bf.Wx : nullptr);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(v->stream) != cudaSuccess) {
+      destroy_batch(nb);
+      return fail(CGKS_ECUDA);
+    }
+  }
+  dev_free(v->sh, stash);
+  for (size_t s = 0; s < next.size(); ++s) {
+    bool is_cont = false;
+    for (auto &c : cont) is_cont |= c.first == static_cast<int>(s);
+    if (!is_cont) {
+      rc = load_state(nb, static_cast<int>(s), v->reqs[next[s]]->W0.data(), nullptr, false);
+      if (rc) { destroy_batch(nb); return rc; }
+    }
+  }
+  CK(cudaStreamSynchronize(v->stream));
+  v->b = nb;
+  v->active = next;
+  return CGKS_OK;
+}
+
+int cgks_server_step(cgks_server *v, int32_t *n_active) {
+  if (!v) return CGKS_EINVAL;
+  int rc = begin_call(v->user_stream, v->stream, v->ev_user, v->device);
+  if (rc) return rc;
+  const double t = now_s(v);
+  // 1. drop finished solves (their states were copied out when they finished)
+  std::vector<int64_t> next;
+  for (int64_t id : v->active)
+    if (v->reqs[id]->st.state == CGKS_REQ_ACTIVE) next.push_back(id);
+  // 2. admit queued requests while the footprint fits
+  size_t used = 0;
+  for (int64_t id : next) used += v->reqs[id]->footprint;
+  bool changed = next.size() != v->active.size();
+  while (!v->queue.empty() && static_cast<int>(next.size()) < v->max_active) {
+    cgks_server::Req &r = *v->reqs[v->queue.front()];
+    if (used + r.footprint > v->budget) break;
+    used += r.footprint;
+    r.st.state = CGKS_REQ_ACTIVE;
+    r.st.t_admit = t;
+    next.push_back(r.id);
+    v->queue.pop_front();
+    changed = true;
+  }
+  if (changed) {
+    rc = server_rebuild(v, next);
+    if (rc) {
+      // the batch could not be formed: its requests are rejected
+      for (int64_t id : next) {
+        cgks_server::Req &r = *v->reqs[id];
+        r.st.state = CGKS_REQ_REJECTED;
+        r.st.t_done = now_s(v);
+      }
+      return rc;
+    }
+  }
+  if (n_active) *n_active = static_cast<int32_t>(v->active.size());
+  if (v->active.empty()) return end_call(v->user_stream, v->stream, v->ev_done);
+  // 3. one batched V-cycle
+  Batch *b = v->b;
+  rc = run_many(b, 1, true);
+  if (rc) return rc;
+  v->res_host.resize(b->S);
+  v->status_host.resize(b->S);
+  CK(cudaMemcpyAsync(v->res_host.data(), b->res, sizeof(double) * b->S, cudaMemcpyDeviceToHost, v->stream));
+  CK(cudaMemcpyAsync(v->status_host.data(), b->status, sizeof(int) * b->S, cudaMemcpyDeviceToHost, v->stream));
+  CK(cudaStreamSynchronize(v->stream));
+  const double t1 = now_s(v);
+  // 4. convergence bookkeeping
+  for (int s = 0; s < b->S; ++s) {
+    cgks_server::Req &r = *v->reqs[v->active[s]];
+    const double res = v->res_host[s];
+    r.st.cycles += 1;
+    if (r.st.cycles == 1) r.st.res_first = res;
+    r.st.res_last = res;
+    int state = CGKS_REQ_ACTIVE;
+    if (v->status_host[s] || !std::isfinite(res)) state = CGKS_REQ_DIVERGED;
+    else if (r.st.cycles > 1 && res <= r.drop * r.st.res_first) state = CGKS_REQ_CONVERGED;
+    else if (r.st.cycles >= v->max_cycles) state = CGKS_REQ_STOPPED;
+    if (state != CGKS_REQ_ACTIVE) {
+      try {
+        r.result.resize(4 * r.mesh->n_cells);
+      } catch (const std::bad_alloc &) {
+        return CGKS_ENOMEM;
+      }
+      rc = store_state(b, s, r.result.data(), nullptr, false);
+      if (rc) return rc;
+      r.st.state = state;
+      r.st.t_done = t1;
+    }
+  }
+  return end_call(v->user_stream, v->stream, v->ev_done);
+}
+
+int cgks_server_poll(cgks_server *v, int64_t req_id, cgks_req_status *st, double *W_out, int timeout_ms) {
+  if (!v) return CGKS_EINVAL;
+  auto it = v->reqs.find(req_id);
+  if (it == v->reqs.end()) return CGKS_EINVAL;
+  cgks_server::Req &r = *it->second;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms > 0 ? timeout_ms : 0);
+  auto done = [&] { return r.st.state >= CGKS_REQ_CONVERGED; };
+  while (timeout_ms > 0 && !done() && std::chrono::steady_clock::now() < deadline) {
+    int rc = cgks_server_step(v, nullptr);
+    if (rc) return rc;
+  }
+  if (st) *st = r.st;
+  if (done()) {
+    if (W_out && !r.result.empty()) std::copy(r.result.begin(), r.result.end(), W_out);
+    return CGKS_OK;
+  }
+  return timeout_ms > 0 ? CGKS_ETIMEOUT : CGKS_OK;
+}
+
+int cgks_server_footprint(const cgks_server *v, const cgks_mesh *m, int64_t *bytes) {
+  if (!v || !m || !bytes) return CGKS_EINVAL;
+  *bytes = static_cast<int64_t>(solve_footprint(m->h.n_cells, m->h.n_faces, v->sh.precision == CGKS_MIXED));
+  return CGKS_OK;
+}
+
+int cgks_server_info(cgks_server *v, int64_t *device_bytes, int32_t *n_queued, int32_t *n_active) {
+  if (!v) return CGKS_EINVAL;
+  if (device_bytes) *device_bytes = v->b ? static_cast<int64_t>(v->b->arena_bytes + sizeof(double) * v->b->hist_cap) : 0;
+  if (n_queued) *n_queued = static_cast<int32_t>(v->queue.size());
+  if (n_active) *n_active = static_cast<int32_t>(v->active.size());
+  return CGKS_OK;
 }
 
 }  // extern "C"

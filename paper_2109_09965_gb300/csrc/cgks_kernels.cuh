@@ -1,0 +1,709 @@
+// Kernels of the batched hot path (included by cgks_device.cu only).
+//
+// Index space: a batch concatenates one or more solves.  Each solve owns a
+// contiguous range of cells (padded to a multiple of kCellBlock with inert
+// padding cells, csid = -1) and a contiguous range of faces; within a
+// solve, cells are colour-major with reverse Cuthill-McKee order inside a
+// colour.  Boundary faces store -1 - (16 * solve + tag) in fc1, so one
+// global table holds every solve's boundary conditions.  Per-solve values
+// (viscosity, time step, status, residual) are indexed by the solve id.
+//
+// Precision: kernels that evaluate fluxes are templated on the flux type
+// TF.  FP64 mode runs everything in double.  Mixed mode keeps the
+// conservative variables (W, W_x, U) and every accumulation into them, the
+// residuals and the diagonal inversion in double, and runs reconstruction,
+// face fluxes and relaxation sweeps in float on float mirrors of the state.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "cgks_internal.h"
+#include "cgks_physics.cuh"
+
+namespace cgks {
+namespace kern {
+
+namespace D = cgks::dev;
+
+constexpr int kCellBlock = 256;
+constexpr int kFaceBlock = 128;
+constexpr int kSweepBlock = 128;
+constexpr int kTagsPerSolve = CGKS_MAX_BC;
+constexpr int kBadState = 1;   // bit of a solve's status word
+
+template <typename T>
+__host__ __device__ constexpr bool is_f32() { return std::is_same<T, float>::value; }
+
+// Shared model constants and pointers to per-solve / per-tag tables.
+template <typename T>
+struct ParamsT {
+  T gamma, K, cfl_hi, cfl_lo;
+  D::KC<T> kc;
+  const T *mu;                   // [S] dynamic viscosity per solve
+  const int *bc_kind;            // [16 S] boundary kind per global tag
+  const T *bc_uw;                // [16 S][2] wall velocity
+  const T *bc_rho, *bc_u, *bc_p; // [16 S], [16 S][2], [16 S] far-field free stream
+};
+
+template <typename T>
+struct MeshT {
+  int nc, nf;                                // padded cells, faces
+  const T *vol, *ivol, *per, *ih, *m2;       // ih = 1/h; m2: [3][nc]
+  const T *op;                               // [kNCol*kNM][nc]
+  const T *fn, *fS, *fjump, *fxi;            // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
+  const T *snx, *sny, *shs;                  // [4][nc] per face slot: outward normal of the cell, S/2
+  const int *cface, *cnbr;                   // [4][nc]
+  const int *fc0, *fc1;
+  const int *csid, *fsid;                    // solve of each cell (-1: padding) and face
+  const unsigned char *ccol;                 // colour of each cell (255: padding)
+};
+
+// per-batch control words on the device
+struct Ctl {
+  double dt_fixed;   // > 0: prescribed step for every solve
+  int res_ctr;       // next slot of solve 0's residual history
+  int pad_;
+};
+
+__device__ __forceinline__ double dt_of(const Ctl *ctl, const unsigned long long *dt_bits, int sid, double cfl) {
+  if (ctl->dt_fixed > 0.0) return ctl->dt_fixed;
+  return cfl * __longlong_as_double(static_cast<long long>(dt_bits[sid]));
+}
+
+__device__ __forceinline__ bool state_ok(double gamma, const double w[4]) {
+  double p = (gamma - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+  return w[0] > 0.0 && p > 0.0 && isfinite(w[0]) && isfinite(p) && isfinite(w[1]) && isfinite(w[2]);
+}
+
+// Block reduction of two doubles in a fixed order; thread 0 writes them.
+__device__ __forceinline__ void block_sum2(double a, double b, double *out2) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { out2[0] = a; out2[1] = b; }
+  }
+}
+
+// ------------------------------------------------------------------
+// K0: reset the per-solve time steps
+__global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, int S, double dt_fixed) {
+  for (int s = threadIdx.x; s < S; s += blockDim.x) dt_bits[s] = 0x7ff0000000000000ull;  // +inf
+  if (threadIdx.x == 0) ctl->dt_fixed = dt_fixed;
+}
+
+// K4: local explicit step per cell, per-solve min by atomicMin on the bits
+// (min is order independent).  h = 2|Omega|/perimeter, speed |U| + c + 2 nu / h.
+// Solves are padded to whole blocks, so a warp never spans two solves.
+__global__ void k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
+                     unsigned long long *dt_bits) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = INFINITY;
+  int sid = i < m.nc ? m.csid[i] : -1;
+  if (sid >= 0) {
+    int n = m.nc;
+    double rho = W[i], mx = W[n + i], my = W[2 * n + i], E = W[3 * n + i];
+    double u = mx / rho, v = my / rho;
+    double p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+    double a = sqrt(P.gamma * p / rho);
+    double hh = 2.0 * m.vol[i] / m.per[i];
+    double speed = sqrt(u * u + v * v) + a + 2.0 * (P.mu[sid] / rho) / hh;
+    d = hh / speed;
+  }
+  for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_down_sync(0xffffffffu, d, o));
+  int s0 = __shfl_sync(0xffffffffu, sid, 0);
+  if ((threadIdx.x & 31) == 0 && s0 >= 0 && d < INFINITY)
+    atomicMin(&dt_bits[s0], static_cast<unsigned long long>(__double_as_longlong(d)));
+}
+
+// Wall ghost of a state and its gradient (global frame), through the face frame.
+template <typename T>
+__device__ __forceinline__ void wall_ghost_global(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4],
+                                                  const T gx[4], const T gy[4], T wg[4], T ggx[4], T ggy[4]) {
+  T wl[4], dn[4], dt[4], tn[4], tt[4];
+  D::rot_in(nx, ny, w, wl);
+  for (int v = 0; v < 4; ++v) { tn[v] = nx * gx[v] + ny * gy[v]; tt[v] = -ny * gx[v] + nx * gy[v]; }
+  D::rot_in(nx, ny, tn, dn);
+  D::rot_in(nx, ny, tt, dt);
+  T wgl[4], dng[4], dtg[4];
+  if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+    D::ghost_slip(wl, dn, dt, wgl, dng, dtg);
+  } else {
+    T wn = P.bc_uw[2 * tag] * nx + P.bc_uw[2 * tag + 1] * ny;
+    T wt = -P.bc_uw[2 * tag] * ny + P.bc_uw[2 * tag + 1] * nx;
+    D::ghost_noslip(P.gamma, wn, wt, wl, dn, dt, wgl, dng, dtg);
+  }
+  T gn[4], gt[4];
+  D::rot_out(nx, ny, wgl, wg);
+  D::rot_out(nx, ny, dng, gn);
+  D::rot_out(nx, ny, dtg, gt);
+  for (int v = 0; v < 4; ++v) { ggx[v] = nx * gn[v] - ny * gt[v]; ggy[v] = ny * gn[v] + nx * gt[v]; }
+}
+
+template <typename T>
+__device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, T nx, T ny, const T wl[4], T wg[4]) {
+  T une = P.bc_u[2 * tag] * nx + P.bc_u[2 * tag + 1] * ny;
+  T ute = -P.bc_u[2 * tag] * ny + P.bc_u[2 * tag + 1] * nx;
+  D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wg);
+}
+
+// K1: compact least-squares quadratic of every cell.
+//   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc;
+  T wi[4], gxi[4], gyi[4];
+  for (int v = 0; v < 4; ++v) { wi[v] = W[v * n + i]; gxi[v] = Wx[v * n + i]; gyi[v] = Wx[(4 + v) * n + i]; }
+  T c[kNM][4];
+  for (int q = 0; q < kNM; ++q) {
+    T o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
+    for (int v = 0; v < 4; ++v) c[q][v] = o0 * gxi[v] + o1 * gyi[v];
+  }
+  for (int s = 0; s < kMaxFace; ++s) {
+    int fs = m.cface[s * n + i];
+    if (fs == kNoFace) continue;
+    int j = m.cnbr[s * n + i];
+    T b0[4], b1[4], b2[4];
+    if (j >= 0) {
+      for (int v = 0; v < 4; ++v) {
+        b0[v] = W[v * n + j] - wi[v];
+        b1[v] = Wx[v * n + j];
+        b2[v] = Wx[(4 + v) * n + j];
+      }
+    } else {
+      int f = fs >= 0 ? fs : ~fs;
+      int tag = -1 - m.fc1[f];
+      if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
+      T wg[4];
+      wall_ghost_global(P, tag, m.fn[f], m.fn[m.nf + f], wi, gxi, gyi, wg, b1, b2);
+      for (int v = 0; v < 4; ++v) b0[v] = wg[v] - wi[v];
+    }
+    for (int q = 0; q < kNM; ++q) {
+      T o0 = m.op[((3 * s) * kNM + q) * n + i];
+      T o1 = m.op[((3 * s + 1) * kNM + q) * n + i];
+      T o2 = m.op[((3 * s + 2) * kNM + q) * n + i];
+      for (int v = 0; v < 4; ++v) c[q][v] += o0 * b0[v] + o1 * b1[v] + o2 * b2[v];
+    }
+  }
+  for (int q = 0; q < kNM; ++q)
+    for (int v = 0; v < 4; ++v) coef[(q * 4 + v) * n + i] = c[q][v];
+}
+
+// value and gradient of the quadratic of cell i at scaled offset (x, y)
+template <typename T>
+__device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restrict__ W, const T *__restrict__ coef,
+                                            int i, T x, T y, T val[4], T gx[4], T gy[4]) {
+  const int n = m.nc;
+  T ih = m.ih[i];
+  T p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
+  for (int v = 0; v < 4; ++v) {
+    T c0 = coef[(0 * 4 + v) * n + i], c1 = coef[(1 * 4 + v) * n + i], c2 = coef[(2 * 4 + v) * n + i];
+    T c3 = coef[(3 * 4 + v) * n + i], c4 = coef[(4 * 4 + v) * n + i];
+    val[v] = W[v * n + i] + c0 * x + c1 * y + c2 * p2 + c3 * p3 + c4 * p4;
+    gx[v] = (c0 + T(2) * c2 * x + c3 * y) * ih;
+    gy[v] = (c1 + c3 * x + T(2) * c4 * y) * ih;
+  }
+}
+
+// ghost of a cell-mean state (zero gradients)
+template <typename T>
+__device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4], T wg[4]) {
+  T wl[4], z[4] = { T(0), T(0), T(0), T(0) }, wgl[4], a[4], b[4];
+  D::rot_in(nx, ny, w, wl);
+  int kind = P.bc_kind[tag];
+  if (kind == CGKS_BC_FARFIELD) {
+    farfield_ghost(P, tag, nx, ny, wl, wgl);
+  } else if (kind == CGKS_BC_SLIP) {
+    D::ghost_slip(wl, z, z, wgl, a, b);
+  } else {
+    T wn = P.bc_uw[2 * tag] * nx + P.bc_uw[2 * tag + 1] * ny;
+    T wt = -P.bc_uw[2 * tag] * ny + P.bc_uw[2 * tag + 1] * nx;
+    D::ghost_noslip(P.gamma, wn, wt, wl, z, z, wgl, a, b);
+  }
+  D::rot_out(nx, ny, wgl, wg);
+}
+
+// K2: gas-kinetic flux and interface state at the two Gauss points of every
+// face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
+//   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
+template <typename T>
+__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                     const T *__restrict__ coef, T *__restrict__ out) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int nf = m.nf;
+  const int c0 = m.fc0[f], c1 = m.fc1[f];
+  const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
+  const T mu = P.mu[m.fsid[f]];
+  T acc[4][4];
+  for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = T(0);
+  T wff[4];
+  bool farfield = false;
+  int tag = 0;
+  if (c1 < 0) {
+    tag = -1 - c1;
+    farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
+    if (farfield) {
+      // Riemann-invariant state from the cell mean and the free stream
+      T wm[4], wl[4];
+      for (int v = 0; v < 4; ++v) wm[v] = W[v * m.nc + c0];
+      D::rot_in(nx, ny, wm, wl);
+      farfield_ghost(P, tag, nx, ny, wl, wff);
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    T wL[4], gxL[4], gyL[4];
+    recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
+    T wl[4], dnl[4], dtl[4], t0[4], t1[4];
+    D::rot_in(nx, ny, wL, wl);
+    for (int v = 0; v < 4; ++v) { t0[v] = nx * gxL[v] + ny * gyL[v]; t1[v] = -ny * gxL[v] + nx * gyL[v]; }
+    D::rot_in(nx, ny, t0, dnl);
+    D::rot_in(nx, ny, t1, dtl);
+    T wr[4], dnr[4], dtr[4];
+    if (c1 >= 0) {
+      T wR[4], gxR[4], gyR[4];
+      recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
+      D::rot_in(nx, ny, wR, wr);
+      for (int v = 0; v < 4; ++v) { t0[v] = nx * gxR[v] + ny * gyR[v]; t1[v] = -ny * gxR[v] + nx * gyR[v]; }
+      D::rot_in(nx, ny, t0, dnr);
+      D::rot_in(nx, ny, t1, dtr);
+    } else if (farfield) {
+      for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = T(0); dtr[v] = T(0); }
+    } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+      D::ghost_slip(wl, dnl, dtl, wr, dnr, dtr);
+    } else {
+      T wn = P.bc_uw[2 * tag] * nx + P.bc_uw[2 * tag + 1] * ny;
+      T wt = -P.bc_uw[2 * tag] * ny + P.bc_uw[2 * tag + 1] * nx;
+      D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
+    }
+    T F0[4], F1[4], Wc[4], Wt[4];
+    D::gks_point_local(P.kc, mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
+    T g[4];
+    D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, Wc, g); for (int v = 0; v < 4; ++v) acc[2][v] += T(0.5) * g[v];
+    D::rot_out(nx, ny, Wt, g); for (int v = 0; v < 4; ++v) acc[3][v] += T(0.5) * g[v];
+  }
+  for (int k = 0; k < 4; ++k)
+    for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
+}
+
+// K3 modes
+enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
+
+// K3: gather the face sums of each cell (accumulated in FP64).
+//   net flux   R  = -sum_p sgn S_p (a0 F0A + a1 F1A + a2 F1B)
+//   W_out = W_base + dt/|Omega| R   (not in kResidual mode)
+//   Wx_out = 1/|Omega| sum_p sgn S_p n_p (WcA + b1 WtX)
+// optional outputs: R itself, float mirrors of W_out / Wx_out, the
+// per-block density-residual partial sums; plus the state check.
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P, int mode,
+                                                       const double *__restrict__ Wbase, const TF *__restrict__ FA,
+                                                       const TF *__restrict__ FB, const Ctl *ctl,
+                                                       const unsigned long long *dt_bits, int *status,
+                                                       double *__restrict__ Wout, double *__restrict__ Wxout,
+                                                       double *__restrict__ partial, double *__restrict__ Rout,
+                                                       TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc, nf = m.nf;
+  double num = 0.0, den = 0.0;
+  const int sid = i < n ? m.csid[i] : -1;
+  if (sid >= 0) {
+    double dt = dt_of(ctl, dt_bits, sid, P.cfl_hi);
+    double a0, a1, b1;
+    const TF *FW = FA;   // where Wt is taken from
+    switch (mode) {
+      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; b1 = dt; break;
+      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; b1 = 0.5 * dt; break;
+      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; FW = FB; break;
+      default: a0 = 1.0; a1 = 0.5 * dt; b1 = 0.0; break;
+    }
+    double R[4] = { 0, 0, 0, 0 }, gx[4] = { 0, 0, 0, 0 }, gy[4] = { 0, 0, 0, 0 };
+    for (int s = 0; s < kMaxFace; ++s) {
+      int fs = m.cface[s * n + i];
+      if (fs == kNoFace) continue;
+      int f = fs >= 0 ? fs : ~fs;
+      double sg = fs >= 0 ? 1.0 : -1.0;
+      double S = m.fS[f], nx = m.fn[f], ny = m.fn[nf + f];
+      for (int v = 0; v < 4; ++v) {
+        double f1 = static_cast<double>(FA[(4 + v) * nf + f]);
+        if (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(FB[(4 + v) * nf + f]);
+        double fl = S * (a0 * static_cast<double>(FA[v * nf + f]) + a1 * f1);
+        R[v] -= sg * fl;
+        if (mode != kResidual) {
+          double wp = static_cast<double>(FA[(8 + v) * nf + f]) + b1 * static_cast<double>(FW[(12 + v) * nf + f]);
+          gx[v] += sg * S * nx * wp;
+          gy[v] += sg * S * ny * wp;
+        }
+      }
+    }
+    if (Rout)
+      for (int v = 0; v < 4; ++v) Rout[v * n + i] = R[v];
+    if (mode != kResidual) {
+      double iv = m.ivol[i];
+      double w[4];
+      for (int v = 0; v < 4; ++v) {
+        w[v] = Wbase[v * n + i] + dt / m.vol[i] * R[v];
+        Wout[v * n + i] = w[v];
+        Wxout[v * n + i] = gx[v] * iv;
+        Wxout[(4 + v) * n + i] = gy[v] * iv;
+        if (Wout_m) {
+          Wout_m[v * n + i] = static_cast<TF>(w[v]);
+          Wxout_m[v * n + i] = static_cast<TF>(gx[v] * iv);
+          Wxout_m[(4 + v) * n + i] = static_cast<TF>(gy[v] * iv);
+        }
+      }
+      if (!state_ok(P.gamma, w)) atomicOr(&status[sid], kBadState);
+      num = fabs(w[0] - Wbase[i]);
+      den = Wbase[i];
+    }
+  }
+  if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+// Sum each solve's block partials in a fixed order (one block per solve):
+// Res_s = num / den.  Solve 0 also appends to the residual history.
+__global__ void k_res_final(const double *__restrict__ partial, const int *__restrict__ blk_begin, Ctl *ctl,
+                            double *__restrict__ res, double *hist, int cap, double *last) {
+  const int s = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int k = blk_begin[s] + threadIdx.x; k < blk_begin[s + 1]; k += blockDim.x) {
+    a += partial[2 * k];
+    b += partial[2 * k + 1];
+  }
+  __shared__ double tot[2];
+  block_sum2(a, b, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = tot[0] / tot[1];
+    res[s] = r;
+    if (s == 0) {
+      last[0] = r; last[1] = tot[0]; last[2] = tot[1];
+      int c = ctl->res_ctr;
+      if (hist && c < cap) hist[c] = r;
+      ctl->res_ctr = c + 1;
+    }
+  }
+}
+
+// ---------------------------- low-order level ----------------------------
+// K5a: per-cell start of an implicit step: U = W_p0 (first step) or
+// U += dU (Algorithm 1's update, in FP64), then the primitives of U (and
+// its float mirror in mixed mode).
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
+                                                        double *__restrict__ U, const TF *__restrict__ dU,
+                                                        TF *__restrict__ prim, TF *__restrict__ Um) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  TF w[4];
+  for (int v = 0; v < 4; ++v) {
+    double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(dU[v * n + i]);
+    U[v * n + i] = u;
+    w[v] = static_cast<TF>(u);
+    if (Um) Um[v * n + i] = w[v];
+  }
+  D::Prim<TF> q = D::prim_of(w, P.gamma, P.kc);
+  prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.p;
+  prim[4 * n + i] = q.i2l; prim[5 * n + i] = q.sl; prim[6 * n + i] = q.isp; prim[7 * n + i] = q.c;
+  prim[8 * n + i] = q.ir;
+}
+
+template <typename T>
+__device__ __forceinline__ D::Prim<T> load_prim(const T *__restrict__ prim, int n, int i) {
+  D::Prim<T> q;
+  q.rho = prim[0 * n + i]; q.u = prim[1 * n + i]; q.v = prim[2 * n + i]; q.p = prim[3 * n + i];
+  q.i2l = prim[4 * n + i]; q.sl = prim[5 * n + i]; q.isp = prim[6 * n + i]; q.c = prim[7 * n + i];
+  q.ir = prim[8 * n + i];
+  return q;
+}
+
+// K5b: first-order KFVS flux, spectral radius lambda_p = max of both sides,
+// and (FP64 mode) the Euler normal fluxes F_n(U_c0), F_n(U_c1) the
+// relaxation reuses.
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
+                                                        const T *__restrict__ prim, T *__restrict__ Flo,
+                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int n = m.nc, nf = m.nf;
+  const int c0 = m.fc0[f], c1 = m.fc1[f];
+  const T nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
+  const T mu = P.mu[m.fsid[f]];
+  D::Prim<T> a = load_prim(prim, n, c0), b;
+  T ivb;
+  if (c1 >= 0) {
+    b = load_prim(prim, n, c1);
+    ivb = m.ivol[c1];
+  } else {
+    T w0[4], wg[4];
+    for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
+    lo_ghost(P, -1 - c1, nx, ny, w0, wg);
+    b = D::prim_of(wg, P.gamma, P.kc);
+    ivb = m.ivol[c0];
+  }
+  const T una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
+  const T unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
+  T Fl[4], F[4];
+  D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
+  D::rot_out(nx, ny, Fl, F);
+  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
+  const T la = fabs(una) + a.c + T(2) * (mu * a.ir) * S * m.ivol[c0];
+  const T lb = fabs(unb) + b.c + T(2) * (mu * b.ir) * S * ivb;
+  lam[f] = la > lb ? la : lb;
+  if (E0) {
+    // Euler normal flux of the cell means (interior faces: both sides)
+    E0[0 * nf + f] = a.rho * una;
+    E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
+    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
+    E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
+    if (c1 >= 0) {
+      E1[0 * nf + f] = b.rho * unb;
+      E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
+      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
+      E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
+    }
+  }
+}
+
+// K6: low-order right-hand side R^k = R_lo(U^k) + S (FP64 sums), 1/D_i
+// (FP64 inversion), each slot's lambda for the sweeps, and the first colour
+// pass of the relaxation: with dU = 0 everywhere the update of a colour-0
+// cell reduces to R_i / D_i; all other cells start at 0.  first: also
+// forms the forcing S = R_p0 - R_lo(W_p0) (Section 3, step 3).
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0,
+                                                       const TF *__restrict__ Flo, const TF *__restrict__ lam,
+                                                       const double *__restrict__ Rp0, double *__restrict__ Src,
+                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
+                                                       TF *__restrict__ lamS) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc, nf = m.nf;
+  double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
+  for (int s = 0; s < kMaxFace; ++s) {
+    int fs = m.cface[s * n + i];
+    if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
+    int f = fs >= 0 ? fs : ~fs;
+    double sg = fs >= 0 ? 1.0 : -1.0;
+    double S = m.fS[f];
+    for (int v = 0; v < 4; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
+    TF l = lam[f];
+    lamS[s * n + i] = l;
+    sum += static_cast<double>(l) * S;
+  }
+  // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2 (padding cells: 0)
+  const double id = sum > 0.0 ? 1.0 / (sum / P.cfl_lo + 0.5 * sum) : 0.0;
+  invD[i] = static_cast<TF>(id);
+  const bool c0 = colour0 && m.ccol[i] == 0;
+  for (int v = 0; v < 4; ++v) {
+    double src;
+    if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
+    else src = Src[v * n + i];
+    double r = R[v] + src;
+    Rk[v * n + i] = static_cast<TF>(r);
+    dU[v * n + i] = c0 ? static_cast<TF>(r * id) : TF(0);
+  }
+}
+
+// The cells of one colour form one contiguous range per solve.  A sweep
+// launch covers up to kMaxRanges ranges, carried in the kernel parameters
+// (constant bank) so no dependent global load precedes the cell's own
+// loads: block b works on range r with blk[r] <= b < blk[r+1].
+constexpr int kMaxRanges = 64;
+struct Ranges {
+  int n;
+  int blk[kMaxRanges + 1];
+  int begin[kMaxRanges], end[kMaxRanges];
+};
+
+// cell of local index cl (cells per block: cpb) in the block's range, or -1
+__device__ __forceinline__ int range_cell(const Ranges &R, int cl, int cpb) {
+  int r = 0;
+  if (R.n > 1) {
+    int lo = 0, hi = R.n - 1;   // largest r with blk[r] <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (R.blk[mid] <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+    }
+    r = lo;
+  }
+  const int i = R.begin[r] + (static_cast<int>(blockIdx.x) - R.blk[r]) * cpb + cl;
+  return i < R.end[r] ? i : -1;
+}
+
+// K7: point relaxation of the cells of one colour (ranges or a list
+// spanning every solve of the batch), Eq. (implicit-local):
+//   dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
+//   F^-(U) = (F_n(U) - lambda_p U) / 2, ghost increments zero.
+// FP64: F_n(U_ip) from the face cache of this implicit step.  Mixed: the
+// difference F_n(U_ip + dU_ip) - F_n(U_ip) in the exact increment form.
+// Four lanes per cell, one per face slot: each lane evaluates its
+// neighbour's term, the four terms are summed by shuffles within the lane
+// group, and lane v writes component v.  Cells of one colour never
+// neighbour each other, so the dU_ip read here are not written by this
+// launch.
+constexpr int kSweepCells = kSweepBlock / kMaxFace;
+template <typename T>
+__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, const __grid_constant__ Ranges R,
+                                                       const int *__restrict__ list, int count,
+                                                       const T *__restrict__ U, const T *__restrict__ prim,
+                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
+                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
+                                                       const T *__restrict__ E1, T *__restrict__ dU) {
+  const int s = threadIdx.x & (kMaxFace - 1);
+  const int cl = threadIdx.x / kMaxFace;
+  int i;
+  if (list) {
+    const int g = blockIdx.x * kSweepCells + cl;
+    i = g < count ? list[g] : -1;
+  } else {
+    i = range_cell(R, cl, kSweepCells);
+  }
+  const int n = m.nc, nf = m.nf;
+  // every lane stays to the shuffles; lanes of absent cells or slots add 0
+  const int j = i >= 0 ? m.cnbr[s * n + i] : -1;
+  T c[4] = { T(0), T(0), T(0), T(0) };
+  if (j >= 0) {
+    const T nx = m.snx[s * n + i], ny = m.sny[s * n + i], hS = m.shs[s * n + i], lp = lamS[s * n + i];
+    T uj[4], du[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
+    if constexpr (is_f32<T>()) {
+      T dF[4];
+      D::euler_flux_delta(P.gamma, uj, prim[1 * n + j], prim[2 * n + j], prim[3 * n + j], du, nx, ny, dF);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) c[v] = hS * (dF[v] - lp * du[v]);
+    } else {
+      const int fs = m.cface[s * n + i];
+      const bool is0 = fs >= 0;
+      const int f = is0 ? fs : ~fs;
+      T up[4], fa[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) up[v] = uj[v] + du[v];
+      D::euler_flux(P.gamma, up, nx, ny, fa);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 1);
+    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 2);
+  }
+  if (i >= 0) {
+    const T mine = s == 0 ? c[0] : s == 1 ? c[1] : s == 2 ? c[2] : c[3];
+    dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+  }
+}
+
+// K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
+// residual against the state at the start of the cycle, state check.
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT<double> P, double *__restrict__ W,
+                                                        const double *__restrict__ Wp0, const double *__restrict__ U,
+                                                        int *status, double *__restrict__ partial,
+                                                        TF *__restrict__ Wm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc;
+  double num = 0.0, den = 0.0;
+  const int sid = i < n ? m.csid[i] : -1;
+  if (i < n) {
+    double w[4];
+    double old_rho = W[i];
+    for (int v = 0; v < 4; ++v) {
+      double wp = Wp0[v * n + i];
+      w[v] = wp + (U[v * n + i] - wp);
+      W[v * n + i] = w[v];
+      if (Wm) Wm[v * n + i] = static_cast<TF>(w[v]);
+    }
+    if (sid >= 0) {
+      if (!state_ok(P.gamma, w)) atomicOr(&status[sid], kBadState);
+      num = fabs(w[0] - old_rho);
+      den = old_rho;
+    }
+  }
+  block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+// Caller AoS order <-> internal SoA order for the n cells of one solve
+// starting at internal offset off (perm: internal within solve -> caller).
+__global__ void k_gather_state(int ns, int off, int N, const int *__restrict__ perm, const double *__restrict__ Wa,
+                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx,
+                               float *__restrict__ W32, float *__restrict__ Wx32) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  int c = perm[k], i = off + k;
+  for (int v = 0; v < 4; ++v) {
+    double w = Wa[4 * c + v];
+    W[v * N + i] = w;
+    if (W32) W32[v * N + i] = static_cast<float>(w);
+  }
+  for (int q = 0; q < 8; ++q) {
+    double g = Wxa ? Wxa[8 * c + q] : 0.0;
+    Wx[q * N + i] = g;
+    if (Wx32) Wx32[q * N + i] = static_cast<float>(g);
+  }
+}
+__global__ void k_scatter_state(int ns, int off, int N, const int *__restrict__ perm, const double *__restrict__ W,
+                                const double *__restrict__ Wx, double *__restrict__ Wa, double *__restrict__ Wxa) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  int c = perm[k], i = off + k;
+  if (Wa) for (int v = 0; v < 4; ++v) Wa[4 * c + v] = W[v * N + i];
+  if (Wxa) for (int q = 0; q < 8; ++q) Wxa[8 * c + q] = Wx[q * N + i];
+}
+// Padding cells: a valid uniform state so their (unused) arithmetic stays finite.
+__global__ void k_fill_padding(int N, const int *__restrict__ csid, double *__restrict__ W, double *__restrict__ Wx,
+                               float *__restrict__ W32, float *__restrict__ Wx32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || csid[i] >= 0) return;
+  const double w[4] = { 1.0, 0.0, 0.0, 2.5 };
+  for (int v = 0; v < 4; ++v) { W[v * N + i] = w[v]; if (W32) W32[v * N + i] = static_cast<float>(w[v]); }
+  for (int q = 0; q < 8; ++q) { Wx[q * N + i] = 0.0; if (Wx32) Wx32[q * N + i] = 0.0f; }
+}
+// Move the states of continuing solves between two batches: dst cell i
+// takes src cell map[i] (map[i] < 0: untouched).
+__global__ void k_move_state(int N, int Nsrc, const int *__restrict__ map, const double *__restrict__ Ws,
+                             const double *__restrict__ Wxs, double *__restrict__ W, double *__restrict__ Wx,
+                             float *__restrict__ W32, float *__restrict__ Wx32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int j = map[i];
+  if (j < 0) return;
+  for (int v = 0; v < 4; ++v) {
+    double w = Ws[v * Nsrc + j];
+    W[v * N + i] = w;
+    if (W32) W32[v * N + i] = static_cast<float>(w);
+  }
+  for (int q = 0; q < 8; ++q) {
+    double g = Wxs[q * Nsrc + j];
+    Wx[q * N + i] = g;
+    if (Wx32) Wx32[q * N + i] = static_cast<float>(g);
+  }
+}
+
+}  // namespace kern
+}  // namespace cgks
