@@ -262,6 +262,100 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     return out
 
 
+def serving_requests(n_req, n_lo, n_hi, seed=5):
+    """Request mix of the serving workload: half lid-driven cavities (n x n
+    quads split into triangles, n chosen for the cell count, Re
+    log-uniform in [100, 3200], Ma 0.15), half inviscid cylinders (hybrid
+    O-mesh with N_theta for the cell count, Ma U[0.2, 0.4], AoA U[0, 10]
+    deg).  Cell counts log-uniform in [n_lo, n_hi]; mesh seed 1000 + id."""
+    from paper_2109_09965_gb300 import meshgen
+    rng = np.random.default_rng(seed)
+    out = []
+    for rid in range(n_req):
+        cells = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        if rng.uniform() < 0.5:
+            n = max(8, int(round(math.sqrt(cells / 2.0))))
+            re = math.exp(rng.uniform(math.log(100.0), math.log(3200.0)))
+            mesh = meshgen.cavity(n, seed=1000 + rid)
+            U = 0.15
+            spec = dict(gamma=GAMMA, mu=U / re, bcs=[dict(kind="noslip"), dict(kind="noslip", uw=(U, 0.0))])
+            W = np.tile([1.0, 0.0, 0.0, 1.0 / GAMMA / (GAMMA - 1.0)], (mesh.n_cells, 1))
+            out.append(dict(kind="cavity", Re=re, mesh=mesh, spec=spec, W=W))
+        else:
+            nt = max(16, 8 * int(round(math.sqrt(cells * 8.0 / 7.0) / 8.0)))
+            ma = rng.uniform(0.2, 0.4)
+            aoa = math.radians(rng.uniform(0.0, 10.0))
+            mesh = meshgen.cylinder(nt, nt // 8, 3 * nt // 8)
+            u, v = ma * math.cos(aoa), ma * math.sin(aoa)
+            spec = dict(gamma=GAMMA, mu=0.0, bcs=[dict(kind="slip"),
+                                                  dict(kind="farfield", rho=1.0, u=(u, v), p=1.0 / GAMMA)])
+            W = np.tile([1.0, u, v, 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * ma * ma], (mesh.n_cells, 1))
+            out.append(dict(kind="cylinder", Ma=ma, mesh=mesh, spec=spec, W=W))
+    return out
+
+
+def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles, max_active, precision,
+            load=0.8, seed=5):
+    """Continuous-batching serving run: requests arrive by a Poisson process
+    on the server's clock and are submitted when due; the server admits by
+    device footprint within the budget, runs one batched V-cycle per step
+    and retires each solve on its own criterion.  Time to converge is
+    measured from arrival to retirement."""
+    import torch
+    t_prep = time.perf_counter()
+    reqs = serving_requests(n_req, n_lo, n_hi, seed)
+    meshes = [cgks.Mesh(r["mesh"]) for r in reqs]
+    t_prep = time.perf_counter() - t_prep
+    srv = cgks.Server(int(budget_gb * 2**30), precision=precision, max_active=max_active, max_cycles=max_cycles)
+    # mean inter-arrival: load x (mean cells x cycles) / a nominal 2e8 cell-updates/s
+    mean_cells = float(np.mean([r["mesh"].n_cells for r in reqs]))
+    mean_service = mean_cells * 0.5 * (cavity_cycles + 1500) / 2e8
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(load * mean_service / max(max_active, 1), n_req))
+    arrivals -= arrivals[0]
+    ids = [None] * n_req
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nxt, steps, peak_bytes, peak_active = 0, 0, 0, 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            r = reqs[nxt]
+            is_cav = r["kind"] == "cavity"
+            ids[nxt] = srv.submit(meshes[nxt], r["spec"], r["W"], 1e-300 if is_cav else drop,
+                                  cavity_cycles if is_cav else 0)
+            nxt += 1
+        n = srv.step()
+        steps += 1
+        info = srv.info()
+        peak_bytes = max(peak_bytes, info["device_bytes"])
+        peak_active = max(peak_active, n)
+        if n == 0 and info["n_queued"] == 0:
+            if nxt == n_req:
+                break
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    lat, states, cells_done = [], {}, 0
+    t_server0 = None
+    for k, rid in enumerate(ids):
+        st, _ = srv.poll(rid, want_state=False)
+        states[st["state"]] = states.get(st["state"], 0) + 1
+        cells_done += st["n_cells"] * st["cycles"]
+        lat.append(st["t_done"] - st["t_submit"])
+    lat = np.asarray(lat)
+    srv.close()
+    return {"requests": n_req, "cells_range": [int(min(r["mesh"].n_cells for r in reqs)),
+                                               int(max(r["mesh"].n_cells for r in reqs))],
+            "wall_s": wall, "solves_per_hour": n_req / wall * 3600.0,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "states": states, "steps": steps,
+            "cell_updates_per_s": cells_done / wall, "peak_device_bytes": int(peak_bytes),
+            "peak_active": int(peak_active), "budget_bytes": int(budget_gb * 2**30), "precision": precision,
+            "criterion": f"cylinders: Res drop {drop:g} relative to the first cycle (cap {max_cycles}); "
+                         f"cavities: {cavity_cycles} cycles",
+            "mesh_prep_s": t_prep}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +367,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant of the line")
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
+    ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
+                    help="serving run: a small sample in the line (default), or the full 256-request mix")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -309,6 +405,10 @@ def main():
             "kernels": m["kernels"], "residual_last": m["res"]}
     if variants:
         line["variants"] = variants
+    if args.serving == "sample":
+        line["serving"] = serving(cgks, 24, 2000, 20000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
+    elif args.serving == "full":
+        line["serving"] = serving(cgks, 256, 2000, 260000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, spec, W0)
     if args.converge:

@@ -226,12 +226,13 @@ void cgks_server_default_opts(cgks_server_opts *o);
 int cgks_server_create(size_t hbm_budget, const cgks_server_opts *opts, cgks_server **out);
 /* Queue a request.  The mesh and W0 ([n_cells*4], caller order, host) are
  * copied; p supplies gamma, mu, alpha and the boundary conditions (the
- * batch-wide fields come from the server options).  A request whose
+ * batch-wide fields come from the server options).  max_cycles > 0 caps
+ * this request's cycles below the server's max_cycles.  A request whose
  * footprint alone exceeds the budget is rejected (CGKS_EBUDGET); so are
  * the requests of a batch the server fails to allocate (the step that
  * tried returns the error). */
 int cgks_server_submit(cgks_server *srv, const cgks_mesh *m, const cgks_params *p, const double *W0,
-                       double res_drop, int64_t *req_id);
+                       double res_drop, int32_t max_cycles, int64_t *req_id);
 /* Retire finished solves, admit queued ones, run one batched V-cycle.
  * *n_active (may be NULL) receives the number of solves that ran. */
 int cgks_server_step(cgks_server *srv, int32_t *n_active);

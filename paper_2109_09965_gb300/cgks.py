@@ -334,7 +334,7 @@ SIGNATURES.update({
     "cgks_server_default_opts": (None, [C.POINTER(CgksServerOpts)]),
     "cgks_server_create": (C.c_int, [C.c_size_t, C.POINTER(CgksServerOpts), C.POINTER(C.c_void_p)]),
     "cgks_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(CgksParams), _dp, C.c_double,
-                                     C.POINTER(C.c_int64)]),
+                                     C.c_int32, C.POINTER(C.c_int64)]),
     "cgks_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "cgks_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(CgksReqStatus), C.c_void_p, C.c_int]),
     "cgks_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -383,13 +383,14 @@ class Server:
 
     __del__ = close
 
-    def submit(self, mesh: Mesh, spec: dict, W0, res_drop: float) -> int:
+    def submit(self, mesh: Mesh, spec: dict, W0, res_drop: float, max_cycles: int = 0) -> int:
         """Queue a solve; returns its id.  Raises CgksError(-7) when the
         request alone exceeds the budget (the id is then still pollable)."""
         P = make_params(spec)
         W0 = np.ascontiguousarray(W0, np.float64).reshape(-1)
         rid = C.c_int64(0)
-        rc = lib().cgks_server_submit(self._h, mesh._h, C.byref(P), W0, float(res_drop), C.byref(rid))
+        rc = lib().cgks_server_submit(self._h, mesh._h, C.byref(P), W0, float(res_drop), int(max_cycles),
+                                      C.byref(rid))
         self.n_cells[rid.value] = mesh.n_cells
         _check(rc, "cgks_server_submit")
         return rid.value

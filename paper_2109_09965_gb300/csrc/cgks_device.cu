@@ -59,8 +59,9 @@ struct Shared {
 // One solve of a batch: its mesh, its parameters and where it sits.
 struct Member {
   std::shared_ptr<const HostMesh> mesh;
-  cgks_params params;
+  cgks_params params{};
   int64_t cell_off = 0, n_pad = 0, face_off = 0;
+  bool active = false;
 };
 
 struct Timer {
@@ -81,12 +82,19 @@ struct DevArrays {
         *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
 };
 
+// A batch is a slot table over one device arena: capacity for Ncap cells,
+// Fcap faces and S solve slots.  A solve occupies a contiguous cell range
+// (a multiple of kCellBlock) and a contiguous face range; cells and faces
+// outside every solve are inert (csid / fsid = -1, no faces, a valid
+// uniform state).  Kernels run over [0, N) cells and [0, F) faces, the
+// extents of the solves present; arrays are strided by the capacity.
 struct Batch {
   Shared sh;
   DevArrays d{};
-  std::vector<Member> mem;
+  std::vector<Member> mem;     // [S] slots
   int S = 0;
-  int64_t N = 0, F = 0;        // padded cells, faces
+  int64_t Ncap = 0, Fcap = 0;  // capacity (array strides)
+  int64_t N = 0, F = 0;        // launch extents
   bool mixed = false;
   int n_colours = 0;
   std::vector<int> sweep_seq;        // colour order after the first pass
@@ -104,7 +112,7 @@ struct Batch {
   double *U = nullptr, *Rp0 = nullptr, *Src = nullptr, *partial = nullptr, *last = nullptr, *stage = nullptr;
   Bufs<double> bd;
   Bufs<float> bf;
-  int *list = nullptr, *perm = nullptr, *blk_begin = nullptr;
+  int *list = nullptr, *perm = nullptr, *blk = nullptr;   // blk: [S][2] residual block range per slot
   Ctl *ctl = nullptr;
   unsigned long long *dt_bits = nullptr;
   int *status = nullptr;
@@ -173,7 +181,7 @@ void enqueue_dt(Batch *b, double dt_fixed) {
 }
 
 void enqueue_res(Batch *b) {
-  launch(b, KI_RESFIN, k_res_final, dim3(b->S), dim3(256), (const double *)b->partial, (const int *)b->blk_begin,
+  launch(b, KI_RESFIN, k_res_final, dim3(b->S), dim3(256), (const double *)b->partial, (const int *)b->blk,
          b->ctl, b->res, b->hist, b->hist_cap, b->last);
 }
 
@@ -218,7 +226,7 @@ void enqueue_lo_solve(Batch *b) {
   const dim3 gc(nblk(b->N, kCellBlock)), gf(nblk(b->F, kCellBlock)), blk(kCellBlock);
   const int colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
   for (int k = 0; k < b->sh.n_implicit; ++k) {
-    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->N), fparams<TF>(b), k == 0 ? 1 : 0,
+    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->Ncap), fparams<TF>(b), k == 0 ? 1 : 0,
            (const double *)b->Wn, b->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
     launch(b, KI_LOFACE, k_lo_face<TF>, gf, blk, fmesh<TF>(b), fparams<TF>(b), (const TF *)B.U, (const TF *)B.prim,
            B.Flo, B.lam, B.E0, B.E1);
@@ -237,10 +245,10 @@ void enqueue_lo_solve(Batch *b) {
   }
   // U^{n_implicit} = U + dU of the last step
   if (b->sh.n_implicit > 0)
-    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->N), fparams<TF>(b), 0, (const double *)b->Wn, b->U,
+    launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->Ncap), fparams<TF>(b), 0, (const double *)b->Wn, b->U,
            (const TF *)B.dU, B.prim, mirror<TF>(B.U));
   else
-    cudaMemcpyAsync(b->U, b->Wn, sizeof(double) * 4 * b->N, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(b->U, b->Wn, sizeof(double) * 4 * b->Ncap, cudaMemcpyDeviceToDevice, b->stream);
 }
 
 template <typename TF>
@@ -280,7 +288,7 @@ void enqueue_explicit_step(Batch *b, double dt_fixed) {
 }
 
 void enqueue_lo_smooth(Batch *b) {
-  cudaMemcpyAsync(b->Wn, b->W, sizeof(double) * 4 * b->N, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(b->Wn, b->W, sizeof(double) * 4 * b->Ncap, cudaMemcpyDeviceToDevice, b->stream);
   if (b->mixed) { enqueue_lo_solve<float>(b); enqueue_prolong<float>(b); }
   else { enqueue_lo_solve<double>(b); enqueue_prolong<double>(b); }
 }
@@ -404,7 +412,7 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   P8(&d.fn, 2 * F); P8(&d.fS, F); P8(&d.fjump, F); P8(&d.fxi, 8 * F);
   P8(&d.mu, S); P8(&d.bcuw, 2 * T); P8(&d.bcrho, T); P8(&d.bcu, 2 * T); P8(&d.bcp, T);
   PI(&d.cface, kMaxFace * N); PI(&d.cnbr, kMaxFace * N); PI(&d.fc0, F); PI(&d.fc1, F); PI(&d.csid, N); PI(&d.fsid, F);
-  PI(&d.bckind, T); PI(&b->list, std::max<int64_t>(L, 1)); PI(&b->perm, N); PI(&b->blk_begin, S + 1);
+  PI(&d.bckind, T); PI(&b->list, std::max<int64_t>(L, 1)); PI(&b->perm, N); PI(&b->blk, 2 * S);
   PV(reinterpret_cast<void **>(&d.ccol), N);
   PV(reinterpret_cast<void **>(&b->ctl), sizeof(Ctl));
   PV(reinterpret_cast<void **>(&b->dt_bits), sizeof(unsigned long long) * S);
@@ -429,17 +437,15 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
 
 constexpr int kHistDefault = 1024;
 
-// Device bytes one solve of n cells and nf faces adds to a batch: its
-// share of the arena, the residual history and, for the serving rebuild,
-// the stash of its state (12 doubles) and two move maps per cell.  The
-// arena size is sub-additive over solves, so the footprints of a set of
-// solves bound the batch they form.
+// Device bytes one solve of n cells and nf faces takes in a batch: the
+// arena pieces for its padded cells and faces and one solve slot, plus a
+// residual history.
 size_t solve_footprint(int64_t n, int64_t nf, bool mixed) {
   const int64_t np = (n + kCellBlock - 1) / kCellBlock * kCellBlock;
   Batch tmp;
   std::vector<Piece> pieces;
   plan_arena(&tmp, np, nf, 1, n, mixed, pieces);
-  return arena_total(pieces) + sizeof(double) * kHistDefault + (12 * sizeof(double) + 2 * sizeof(int)) * np + 3 * 256;
+  return arena_total(pieces) + sizeof(double) * kHistDefault;
 }
 
 int64_t pad_cells(int64_t n) { return (n + kCellBlock - 1) / kCellBlock * kCellBlock; }
@@ -453,145 +459,33 @@ void destroy_batch(Batch *b) {
   delete b;
 }
 
-// Build a batch on stream st from members (mesh + per-solve parameters).
-int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batch **out) {
+// Make cells [c0, c1) inert: no faces, no solve, no colour, uniform state.
+void clear_cells(Batch *b, int64_t c0, int64_t c1) {
+  if (c1 <= c0) return;
+  k_clear_cells<<<nblk(c1 - c0, kCellBlock), kCellBlock, 0, b->stream>>>(
+      static_cast<int>(c0), static_cast<int>(c1), static_cast<int>(b->Ncap), b->d.csid, b->d.ccol, b->d.cface,
+      b->d.cnbr, b->W, b->Wx, b->Wn, b->Ws, b->Wxs, b->mixed ? b->bf.W : nullptr, b->mixed ? b->bf.Wx : nullptr,
+      b->mixed ? b->bf.Wn : nullptr, b->mixed ? b->bf.Ws : nullptr, b->mixed ? b->bf.Wxs : nullptr);
+}
+
+// Allocate a batch with capacity for Ncap cells, Fcap faces and S slots;
+// every cell and face starts inert.
+int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream_t st, Batch **out) {
   *out = nullptr;
+  if (S < 1 || Ncap < kCellBlock || Ncap % kCellBlock || Fcap < 1) return CGKS_EINVAL;
+  if (Ncap * kNCol * kNM > INT32_MAX || Fcap * 16 > INT32_MAX) return CGKS_EINVAL;
   std::unique_ptr<Batch> B(new (std::nothrow) Batch());
   if (!B) return CGKS_ENOMEM;
   Batch *b = B.get();
   b->sh = sh;
-  b->mem = std::move(mem);
-  b->S = static_cast<int>(b->mem.size());
+  b->S = S;
+  b->mem.assign(S, Member{});
+  b->Ncap = Ncap; b->Fcap = Fcap;
   b->mixed = sh.precision == CGKS_MIXED;
   b->stream = st;
-  if (b->S == 0) return CGKS_EINVAL;
-  int64_t N = 0, F = 0;
-  int C = 0;
-  for (auto &m : b->mem) {
-    m.cell_off = N;
-    m.n_pad = pad_cells(m.mesh->n_cells);
-    m.face_off = F;
-    N += m.n_pad;
-    F += m.mesh->n_faces;
-    C = std::max(C, m.mesh->n_colours);
-  }
-  if (N > INT32_MAX / 32 || F > INT32_MAX / 32) return CGKS_EINVAL;
-  b->N = N; b->F = F; b->n_colours = C;
-  const int S = b->S;
-  // ---- host arrays of the concatenated index space
-  std::vector<double> vol(N, 1.0), ivol(N, 1.0), per(N, 4.0), ih(N, 1.0), m2(3 * N, 0.0), op(kNCol * kNM * N, 0.0);
-  std::vector<double> snx(kMaxFace * N, 0.0), sny(kMaxFace * N, 0.0), shs(kMaxFace * N, 0.0);
-  std::vector<double> fn(2 * F), fS(F), fjump(F), fxi(8 * F);
-  std::vector<int> cface(kMaxFace * N, kNoFace), cnbr(kMaxFace * N, -1), fc0(F), fc1(F), csid(N, -1), fsid(F),
-      perm(N, 0), blk(S + 1);
-  std::vector<unsigned char> ccol(N, 255);
-  std::vector<double> mu(S), bc_uw(2 * kTagsPerSolve * S, 0.0), bc_rho(kTagsPerSolve * S, 1.0),
-      bc_u(2 * kTagsPerSolve * S, 0.0), bc_p(kTagsPerSolve * S, 1.0);
-  std::vector<int> bc_kind(kTagsPerSolve * S, CGKS_BC_SLIP);
-  std::vector<std::vector<int>> lists(C);
-  for (int s = 0; s < S; ++s) {
-    const Member &M = b->mem[s];
-    const HostMesh &hm = *M.mesh;
-    const cgks_params &p = M.params;
-    const int64_t nc = hm.n_cells, nf = hm.n_faces, co = M.cell_off, fo = M.face_off;
-    blk[s] = static_cast<int>(co / kCellBlock);
-    mu[s] = p.mu;
-    for (int t = 0; t < kTagsPerSolve; ++t) {
-      const int g = s * kTagsPerSolve + t;
-      const cgks_bc &bc = p.bc[t];
-      bc_kind[g] = t < p.n_bc ? bc.kind : CGKS_BC_SLIP;
-      bc_uw[2 * g] = bc.u_wall[0]; bc_uw[2 * g + 1] = bc.u_wall[1];
-      bc_rho[g] = bc.rho; bc_u[2 * g] = bc.u[0]; bc_u[2 * g + 1] = bc.u[1]; bc_p[g] = bc.p;
-    }
-    std::vector<char> wall(kTagsPerSolve, 0);
-    for (int t = 0; t < p.n_bc; ++t) wall[t] = p.bc[t].kind != CGKS_BC_FARFIELD;
-    std::vector<double> ops;
-    build_operator(hm, wall, ops);
-    for (int64_t i = 0; i < nc; ++i) {
-      const int64_t I = co + i;
-      vol[I] = hm.vol[i]; ivol[I] = 1.0 / hm.vol[i]; per[I] = hm.per[i]; ih[I] = 1.0 / hm.h[i];
-      for (int q = 0; q < 3; ++q) m2[q * N + I] = hm.m2[q * nc + i];
-      for (int q = 0; q < kNCol * kNM; ++q) op[q * N + I] = ops[q * nc + i];
-      csid[I] = s;
-      perm[I] = hm.perm[i];
-      for (int sl = 0; sl < kMaxFace; ++sl) {
-        const int32_t fs = hm.cface[sl * nc + i];
-        if (fs == kNoFace) continue;
-        const int32_t f = fs >= 0 ? fs : ~fs;
-        const double sg = fs >= 0 ? 1.0 : -1.0;
-        cface[sl * N + I] = fs >= 0 ? static_cast<int>(f + fo) : ~static_cast<int>(f + fo);
-        const int32_t j = hm.cnbr[sl * nc + i];
-        cnbr[sl * N + I] = j >= 0 ? static_cast<int>(j + co) : -1;
-        snx[sl * N + I] = sg * hm.fn[f];
-        sny[sl * N + I] = sg * hm.fn[nf + f];
-        shs[sl * N + I] = 0.5 * hm.fS[f];
-      }
-    }
-    for (int c = 0; c < hm.n_colours; ++c)
-      for (int32_t i = hm.colour_start[c]; i < hm.colour_start[c + 1]; ++i) {
-        ccol[co + i] = static_cast<unsigned char>(c);
-        lists[c].push_back(static_cast<int>(co + i));
-      }
-    for (int64_t f = 0; f < nf; ++f) {
-      const int64_t G = fo + f;
-      fc0[G] = static_cast<int>(hm.fc0[f] + co);
-      const int32_t c1 = hm.fc1[f];
-      fc1[G] = c1 >= 0 ? static_cast<int>(c1 + co) : -1 - (s * kTagsPerSolve + (-1 - c1));
-      fsid[G] = s;
-      fn[G] = hm.fn[f]; fn[F + G] = hm.fn[nf + f];
-      fS[G] = hm.fS[f];
-      fjump[G] = hm.fdelta[f] > 0.0 ? p.alpha / hm.fdelta[f] : 0.0;
-      for (int q = 0; q < 8; ++q) fxi[q * F + G] = hm.fxi[q * nf + f];
-    }
-  }
-  blk[S] = static_cast<int>(N / kCellBlock);
-  std::vector<int> list;
-  b->list_off.assign(C + 1, 0);
-  for (int c = 0; c < C; ++c) {
-    list.insert(list.end(), lists[c].begin(), lists[c].end());
-    b->list_off[c + 1] = static_cast<int>(list.size());
-  }
-  if (list.empty()) list.push_back(0);
-  // per-colour ranges for the sweeps (the list is used beyond kMaxRanges solves)
-  b->ranges.assign(C, Ranges{});
-  for (int c = 0; c < C; ++c) {
-    Ranges &R = b->ranges[c];
-    std::memset(&R, 0, sizeof(R));
-    int nr = 0, blocks = 0;
-    bool fits = true;
-    for (int s = 0; s < S && fits; ++s) {
-      const HostMesh &hm = *b->mem[s].mesh;
-      if (c >= hm.n_colours) continue;
-      const int beg = static_cast<int>(b->mem[s].cell_off) + hm.colour_start[c];
-      const int end = static_cast<int>(b->mem[s].cell_off) + hm.colour_start[c + 1];
-      if (end == beg) continue;
-      if (nr == kMaxRanges) { fits = false; break; }
-      R.blk[nr] = blocks;
-      R.begin[nr] = beg;
-      R.end[nr] = end;
-      blocks += nblk(end - beg, kSweepCells);
-      ++nr;
-    }
-    if (fits) { R.n = nr; R.blk[nr] = blocks; }
-    else std::memset(&R, 0, sizeof(R));
-  }
-  // colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
-  // C-1..0).  A colour repeated back to back recomputes identical values
-  // (its cells read only other colours), and the first pass is done by
-  // k_lo_rhs, so both are dropped.
-  {
-    std::vector<int> seq;
-    for (int sw = 0; sw < sh.n_sweeps; ++sw) {
-      for (int c = 0; c < C; ++c) if (seq.empty() || seq.back() != c) seq.push_back(c);
-      for (int c = C - 1; c >= 0; --c) if (seq.empty() || seq.back() != c) seq.push_back(c);
-    }
-    if (!seq.empty()) seq.erase(seq.begin());
-    b->sweep_seq = seq;
-  }
-  // ---- device arena
   DevArrays &d = b->d;
   std::vector<Piece> pieces;
-  plan_arena(b, N, F, S, static_cast<int64_t>(list.size()), b->mixed, pieces);
+  plan_arena(b, Ncap, Fcap, S, Ncap, b->mixed, pieces);
   const size_t total = arena_total(pieces);
   b->arena = dev_alloc(sh, total);
   if (!b->arena) return CGKS_ENOMEM;
@@ -604,57 +498,6 @@ int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batc
     Bufs<double> &X = b->bd;
     X.W = b->W; X.Wx = b->Wx; X.Wn = b->Wn; X.Ws = b->Ws; X.Wxs = b->Wxs; X.U = b->U;
   }
-  auto up = [&](void *dst, const void *src, size_t bytes) {
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
-  };
-  bool ok = up(d.vol, vol.data(), 8 * N) && up(d.ivol, ivol.data(), 8 * N) && up(d.per, per.data(), 8 * N) &&
-            up(d.ih, ih.data(), 8 * N) && up(d.m2, m2.data(), 8 * m2.size()) && up(d.op, op.data(), 8 * op.size()) &&
-            up(d.snx, snx.data(), 8 * snx.size()) && up(d.sny, sny.data(), 8 * sny.size()) &&
-            up(d.shs, shs.data(), 8 * shs.size()) && up(d.fn, fn.data(), 8 * fn.size()) && up(d.fS, fS.data(), 8 * F) &&
-            up(d.fjump, fjump.data(), 8 * F) && up(d.fxi, fxi.data(), 8 * fxi.size()) && up(d.mu, mu.data(), 8 * S) &&
-            up(d.bcuw, bc_uw.data(), 8 * bc_uw.size()) && up(d.bcrho, bc_rho.data(), 8 * bc_rho.size()) &&
-            up(d.bcu, bc_u.data(), 8 * bc_u.size()) && up(d.bcp, bc_p.data(), 8 * bc_p.size()) &&
-            up(d.cface, cface.data(), 4 * cface.size()) && up(d.cnbr, cnbr.data(), 4 * cnbr.size()) &&
-            up(d.fc0, fc0.data(), 4 * F) && up(d.fc1, fc1.data(), 4 * F) && up(d.csid, csid.data(), 4 * N) &&
-            up(d.fsid, fsid.data(), 4 * F) && up(d.bckind, bc_kind.data(), 4 * bc_kind.size()) &&
-            up(b->list, list.data(), 4 * list.size()) && up(b->perm, perm.data(), 4 * N) &&
-            up(b->blk_begin, blk.data(), 4 * (S + 1)) && up(d.ccol, ccol.data(), N);
-  std::vector<float> tmp;
-  auto upf = [&](float *dst, const std::vector<double> &src) {
-    tmp.assign(src.begin(), src.end());
-    bool r = cudaMemcpyAsync(dst, tmp.data(), 4 * tmp.size(), cudaMemcpyHostToDevice, st) == cudaSuccess;
-    return r && cudaStreamSynchronize(st) == cudaSuccess;   // tmp is reused
-  };
-  if (ok && b->mixed)
-    ok = upf(d.f_ivol, ivol) && upf(d.f_ih, ih) && upf(d.f_m2, m2) && upf(d.f_op, op) && upf(d.f_snx, snx) && upf(d.f_sny, sny) &&
-         upf(d.f_shs, shs) && upf(d.f_fn, fn) && upf(d.f_fS, fS) && upf(d.f_fjump, fjump) && upf(d.f_fxi, fxi) &&
-         upf(d.f_mu, mu) && upf(d.f_bcuw, bc_uw) && upf(d.f_bcrho, bc_rho) && upf(d.f_bcu, bc_u) && upf(d.f_bcp, bc_p);
-  if (ok) ok = cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
-               cudaMemsetAsync(b->status, 0, sizeof(int) * S, st) == cudaSuccess &&
-               cudaMemsetAsync(b->Rp0, 0, sizeof(double) * 4 * N, st) == cudaSuccess &&
-               cudaMemsetAsync(b->res, 0, sizeof(double) * S, st) == cudaSuccess &&
-               cudaMemsetAsync(b->last, 0, sizeof(double) * 4, st) == cudaSuccess;
-  if (ok) {
-    if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * N, st) == cudaSuccess;
-    else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * N, st) == cudaSuccess;
-  }
-  if (ok) {
-    k_fill_padding<<<nblk(N, kCellBlock), kCellBlock, 0, st>>>(static_cast<int>(N), d.csid, b->W, b->Wx,
-                                                               b->mixed ? b->bf.W : nullptr,
-                                                               b->mixed ? b->bf.Wx : nullptr);
-    ok = cudaGetLastError() == cudaSuccess;
-    // the stage and predictor states keep the same inert padding: the
-    // update kernels never write padding cells
-    ok = ok && cudaMemcpyAsync(b->Wn, b->W, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
-         cudaMemcpyAsync(b->Ws, b->W, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
-         cudaMemcpyAsync(b->Wxs, b->Wx, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
-    if (ok && b->mixed)
-      ok = cudaMemcpyAsync(b->bf.Wn, b->bf.W, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
-           cudaMemcpyAsync(b->bf.Ws, b->bf.W, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
-           cudaMemcpyAsync(b->bf.Wxs, b->bf.Wx, sizeof(float) * 8 * N, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
-    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
-  }
-  if (!ok) { destroy_batch(B.release()); return CGKS_ECUDA; }
   // kernel-side views
   fill_shared_params(sh, b->dp);
   fill_shared_params(sh, b->fp);
@@ -663,7 +506,7 @@ int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batc
   b->fp.mu = d.f_mu; b->fp.bc_kind = d.bckind; b->fp.bc_uw = d.f_bcuw; b->fp.bc_rho = d.f_bcrho; b->fp.bc_u = d.f_bcu;
   b->fp.bc_p = d.f_bcp;
   MeshT<double> &dm = b->dm;
-  dm.nc = static_cast<int>(N); dm.nf = static_cast<int>(F);
+  dm.nc = static_cast<int>(Ncap); dm.nf = static_cast<int>(Fcap);
   dm.vol = d.vol; dm.ivol = d.ivol; dm.per = d.per; dm.ih = d.ih; dm.m2 = d.m2; dm.op = d.op;
   dm.fn = d.fn; dm.fS = d.fS; dm.fjump = d.fjump; dm.fxi = d.fxi; dm.snx = d.snx; dm.sny = d.sny; dm.shs = d.shs;
   dm.cface = d.cface; dm.cnbr = d.cnbr; dm.fc0 = d.fc0; dm.fc1 = d.fc1; dm.csid = d.csid; dm.fsid = d.fsid;
@@ -671,12 +514,236 @@ int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batc
   MeshT<float> &fm = b->fm;
   fm.nc = dm.nc; fm.nf = dm.nf;
   fm.vol = nullptr; fm.per = nullptr; fm.ivol = d.f_ivol; fm.ih = d.f_ih; fm.m2 = d.f_m2; fm.op = d.f_op;
-  fm.fn = d.f_fn; fm.fS = d.f_fS; fm.fjump = d.f_fjump; fm.fxi = d.f_fxi; fm.snx = d.f_snx; fm.sny = d.f_sny; fm.shs = d.f_shs;
+  fm.fn = d.f_fn; fm.fS = d.f_fS; fm.fjump = d.f_fjump; fm.fxi = d.f_fxi; fm.snx = d.f_snx; fm.sny = d.f_sny;
+  fm.shs = d.f_shs;
   fm.cface = d.cface; fm.cnbr = d.cnbr; fm.fc0 = d.fc0; fm.fc1 = d.fc1; fm.csid = d.csid; fm.fsid = d.fsid;
   fm.ccol = d.ccol;
+  bool ok = cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
+            cudaMemsetAsync(b->status, 0, sizeof(int) * S, st) == cudaSuccess &&
+            cudaMemsetAsync(b->res, 0, sizeof(double) * S, st) == cudaSuccess &&
+            cudaMemsetAsync(b->blk, 0, sizeof(int) * 2 * S, st) == cudaSuccess &&
+            cudaMemsetAsync(b->last, 0, sizeof(double) * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(b->Rp0, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess &&
+            cudaMemsetAsync(d.fsid, 0xff, sizeof(int) * Fcap, st) == cudaSuccess &&
+            cudaMemsetAsync(d.bckind, 0, sizeof(int) * kTagsPerSolve * S, st) == cudaSuccess;
+  if (ok) {
+    if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * Ncap, st) == cudaSuccess;
+    else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess;
+  }
+  if (ok) {
+    clear_cells(b, 0, Ncap);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  if (!ok) { destroy_batch(B.release()); return CGKS_ECUDA; }
   int rc = ensure_hist(b, kHistDefault);
   if (rc) { destroy_batch(B.release()); return rc; }
   *out = B.release();
+  return CGKS_OK;
+}
+
+// Upload solve m into slot s at cells [cell_off, cell_off + n_pad) and
+// faces [face_off, face_off + n_faces).  Its state is set separately.
+int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t face_off) {
+  const HostMesh &hm = *m.mesh;
+  const cgks_params &p = m.params;
+  const int64_t nc = hm.n_cells, nf = hm.n_faces, np = pad_cells(nc), co = cell_off, fo = face_off;
+  const int64_t N = b->Ncap, F = b->Fcap;
+  if (s < 0 || s >= b->S || b->mem[s].active || co % kCellBlock || co + np > N || fo + nf > F) return CGKS_EINVAL;
+  cudaStream_t st = b->stream;
+  clear_cells(b, co, co + np);
+  if (cudaGetLastError() != cudaSuccess) return CGKS_ECUDA;
+  // local tables (np cells, nf faces) with global indices
+  std::vector<double> vol(np, 1.0), ivol(np, 1.0), per(np, 4.0), ih(np, 1.0), m2(3 * np, 0.0),
+      op(kNCol * kNM * np, 0.0), snx(kMaxFace * np, 0.0), sny(kMaxFace * np, 0.0), shs(kMaxFace * np, 0.0);
+  std::vector<double> fn(2 * nf), fS(nf), fjump(nf), fxi(8 * nf);
+  std::vector<int> cface(kMaxFace * np, kNoFace), cnbr(kMaxFace * np, -1), csid(np, -1), perm(np, 0), fc0(nf),
+      fc1(nf), fsid(nf, s);
+  std::vector<unsigned char> ccol(np, 255);
+  std::vector<char> wall(kTagsPerSolve, 0);
+  for (int t = 0; t < p.n_bc; ++t) wall[t] = p.bc[t].kind != CGKS_BC_FARFIELD;
+  std::vector<double> ops;
+  build_operator(hm, wall, ops);
+  for (int64_t i = 0; i < nc; ++i) {
+    vol[i] = hm.vol[i]; ivol[i] = 1.0 / hm.vol[i]; per[i] = hm.per[i]; ih[i] = 1.0 / hm.h[i];
+    for (int q = 0; q < 3; ++q) m2[q * np + i] = hm.m2[q * nc + i];
+    for (int q = 0; q < kNCol * kNM; ++q) op[q * np + i] = ops[q * nc + i];
+    csid[i] = s;
+    perm[i] = hm.perm[i];
+    for (int sl = 0; sl < kMaxFace; ++sl) {
+      const int32_t fs = hm.cface[sl * nc + i];
+      if (fs == kNoFace) continue;
+      const int32_t f = fs >= 0 ? fs : ~fs;
+      const double sg = fs >= 0 ? 1.0 : -1.0;
+      cface[sl * np + i] = fs >= 0 ? static_cast<int>(f + fo) : ~static_cast<int>(f + fo);
+      const int32_t j = hm.cnbr[sl * nc + i];
+      cnbr[sl * np + i] = j >= 0 ? static_cast<int>(j + co) : -1;
+      snx[sl * np + i] = sg * hm.fn[f];
+      sny[sl * np + i] = sg * hm.fn[nf + f];
+      shs[sl * np + i] = 0.5 * hm.fS[f];
+    }
+  }
+  for (int c = 0; c < hm.n_colours; ++c)
+    for (int32_t i = hm.colour_start[c]; i < hm.colour_start[c + 1]; ++i) ccol[i] = static_cast<unsigned char>(c);
+  for (int64_t f = 0; f < nf; ++f) {
+    fc0[f] = static_cast<int>(hm.fc0[f] + co);
+    const int32_t c1 = hm.fc1[f];
+    fc1[f] = c1 >= 0 ? static_cast<int>(c1 + co) : -1 - (s * kTagsPerSolve + (-1 - c1));
+    fn[f] = hm.fn[f]; fn[nf + f] = hm.fn[nf + f];
+    fS[f] = hm.fS[f];
+    fjump[f] = hm.fdelta[f] > 0.0 ? p.alpha / hm.fdelta[f] : 0.0;
+    for (int q = 0; q < 8; ++q) fxi[q * nf + f] = hm.fxi[q * nf + f];
+  }
+  std::vector<double> mu(1, p.mu), bc_uw(2 * kTagsPerSolve, 0.0), bc_rho(kTagsPerSolve, 1.0),
+      bc_u(2 * kTagsPerSolve, 0.0), bc_p(kTagsPerSolve, 1.0);
+  std::vector<int> bc_kind(kTagsPerSolve, CGKS_BC_SLIP);
+  for (int t = 0; t < kTagsPerSolve; ++t) {
+    const cgks_bc &bc = p.bc[t];
+    bc_kind[t] = t < p.n_bc ? bc.kind : CGKS_BC_SLIP;
+    bc_uw[2 * t] = bc.u_wall[0]; bc_uw[2 * t + 1] = bc.u_wall[1];
+    bc_rho[t] = bc.rho; bc_u[2 * t] = bc.u[0]; bc_u[2 * t + 1] = bc.u[1]; bc_p[t] = bc.p;
+  }
+  // component-sliced uploads: host [comps][len] -> device [comps][stride] at off
+  bool ok = true;
+  auto up = [&](auto *dst, const auto &src, int64_t len, int64_t stride, int64_t off) {
+    using E = typename std::decay_t<decltype(src)>::value_type;
+    const int64_t comps = static_cast<int64_t>(src.size()) / std::max<int64_t>(len, 1);
+    for (int64_t q = 0; q < comps && ok && len > 0; ++q)
+      ok = cudaMemcpyAsync(dst + q * stride + off, src.data() + q * len, sizeof(E) * len, cudaMemcpyHostToDevice,
+                           st) == cudaSuccess;
+  };
+  DevArrays &d = b->d;
+  const int64_t T = kTagsPerSolve;
+  up(d.vol, vol, np, N, co); up(d.ivol, ivol, np, N, co); up(d.per, per, np, N, co); up(d.ih, ih, np, N, co);
+  up(d.m2, m2, np, N, co); up(d.op, op, np, N, co); up(d.snx, snx, np, N, co); up(d.sny, sny, np, N, co);
+  up(d.shs, shs, np, N, co); up(d.cface, cface, np, N, co); up(d.cnbr, cnbr, np, N, co);
+  up(d.csid, csid, np, N, co); up(b->perm, perm, np, N, co); up(d.ccol, ccol, np, N, co);
+  up(d.fn, fn, nf, F, fo); up(d.fS, fS, nf, F, fo); up(d.fjump, fjump, nf, F, fo); up(d.fxi, fxi, nf, F, fo);
+  up(d.fc0, fc0, nf, F, fo); up(d.fc1, fc1, nf, F, fo); up(d.fsid, fsid, nf, F, fo);
+  up(d.mu, mu, 1, 1, s); up(d.bcuw, bc_uw, 2 * T, 0, 2 * T * s); up(d.bcrho, bc_rho, T, 0, T * s);
+  up(d.bcu, bc_u, 2 * T, 0, 2 * T * s); up(d.bcp, bc_p, T, 0, T * s); up(d.bckind, bc_kind, T, 0, T * s);
+  if (ok && b->mixed) {
+    auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+    std::vector<std::vector<float>> keep;   // alive until the stream syncs
+    auto upf = [&](float *dst, const std::vector<double> &src, int64_t len, int64_t stride, int64_t off) {
+      keep.push_back(f32(src));
+      up(dst, keep.back(), len, stride, off);
+    };
+    upf(d.f_ivol, ivol, np, N, co); upf(d.f_ih, ih, np, N, co); upf(d.f_m2, m2, np, N, co);
+    upf(d.f_op, op, np, N, co); upf(d.f_snx, snx, np, N, co); upf(d.f_sny, sny, np, N, co);
+    upf(d.f_shs, shs, np, N, co);
+    upf(d.f_fn, fn, nf, F, fo); upf(d.f_fS, fS, nf, F, fo); upf(d.f_fjump, fjump, nf, F, fo);
+    upf(d.f_fxi, fxi, nf, F, fo);
+    upf(d.f_mu, mu, 1, 1, s); upf(d.f_bcuw, bc_uw, 2 * T, 0, 2 * T * s); upf(d.f_bcrho, bc_rho, T, 0, T * s);
+    upf(d.f_bcu, bc_u, 2 * T, 0, 2 * T * s); upf(d.f_bcp, bc_p, T, 0, T * s);
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  ok = ok && cudaMemsetAsync(b->status + s, 0, sizeof(int), st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;   // host tables go out of scope
+  if (!ok) return CGKS_ECUDA;
+  Member &M = b->mem[s];
+  M = m;
+  M.cell_off = co; M.n_pad = np; M.face_off = fo; M.active = true;
+  return CGKS_OK;
+}
+
+// Take solve s out: its cells and faces become inert.
+int remove_solve(Batch *b, int s) {
+  Member &M = b->mem[s];
+  if (!M.active) return CGKS_EINVAL;
+  clear_cells(b, M.cell_off, M.cell_off + M.n_pad);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(b->d.fsid + M.face_off, 0xff, sizeof(int) * M.mesh->n_faces, b->stream));
+  M.active = false;
+  M.mesh.reset();
+  return CGKS_OK;
+}
+
+// After inserts and removals: launch extents, colour sequence, sweep
+// ranges (or cell lists beyond kMaxRanges solves), residual block ranges.
+int finalize_batch(Batch *b) {
+  int64_t N = 0, F = 0;
+  int C = 0;
+  std::vector<int> order;   // active slots by cell offset
+  for (int s = 0; s < b->S; ++s) {
+    const Member &M = b->mem[s];
+    if (!M.active) continue;
+    order.push_back(s);
+    N = std::max(N, M.cell_off + M.n_pad);
+    F = std::max(F, M.face_off + M.mesh->n_faces);
+    C = std::max(C, M.mesh->n_colours);
+  }
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return b->mem[x].cell_off < b->mem[y].cell_off; });
+  b->N = N; b->F = F; b->n_colours = C;
+  std::vector<int> blk(2 * b->S, 0);
+  for (int s : order) {
+    blk[2 * s] = static_cast<int>(b->mem[s].cell_off / kCellBlock);
+    blk[2 * s + 1] = static_cast<int>((b->mem[s].cell_off + b->mem[s].n_pad) / kCellBlock);
+  }
+  CK(cudaMemcpyAsync(b->blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice, b->stream));
+  // colour sequence of Algorithm 1 with colour classes: n_sweeps x (0..C-1,
+  // C-1..0).  A colour repeated back to back recomputes identical values
+  // (its cells read only other colours), and the first pass is done by
+  // k_lo_rhs, so both are dropped.
+  std::vector<int> seq;
+  for (int sw = 0; sw < b->sh.n_sweeps; ++sw) {
+    for (int c = 0; c < C; ++c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+    for (int c = C - 1; c >= 0; --c) if (seq.empty() || seq.back() != c) seq.push_back(c);
+  }
+  if (!seq.empty()) seq.erase(seq.begin());
+  b->sweep_seq = seq;
+  b->ranges.assign(C, Ranges{});
+  b->list_off.assign(C + 1, 0);
+  std::vector<int> list;
+  bool need_list = false;
+  for (int c = 0; c < C; ++c) {
+    Ranges &R = b->ranges[c];
+    std::memset(&R, 0, sizeof(R));
+    int nr = 0, blocks = 0;
+    for (int s : order) {
+      const Member &M = b->mem[s];
+      const HostMesh &hm = *M.mesh;
+      if (c >= hm.n_colours) continue;
+      const int beg = static_cast<int>(M.cell_off) + hm.colour_start[c];
+      const int end = static_cast<int>(M.cell_off) + hm.colour_start[c + 1];
+      if (end == beg) continue;
+      for (int i = beg; i < end; ++i) list.push_back(i);
+      if (nr == kMaxRanges) { nr = -1; continue; }
+      if (nr < 0) continue;
+      R.blk[nr] = blocks;
+      R.begin[nr] = beg;
+      R.end[nr] = end;
+      blocks += nblk(end - beg, kSweepCells);
+      ++nr;
+    }
+    if (nr >= 0) { R.n = nr; R.blk[nr] = blocks; }
+    else { std::memset(&R, 0, sizeof(R)); need_list = true; }
+    b->list_off[c + 1] = static_cast<int>(list.size());
+  }
+  if (need_list && !list.empty())
+    CK(cudaMemcpyAsync(b->list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  drop_graphs(b);
+  return CGKS_OK;
+}
+
+// A batch holding exactly the given solves, packed from offset 0.
+int build_batch(const Shared &sh, std::vector<Member> mem, cudaStream_t st, Batch **out) {
+  *out = nullptr;
+  if (mem.empty()) return CGKS_EINVAL;
+  int64_t N = 0, F = 0;
+  for (auto &m : mem) { N += pad_cells(m.mesh->n_cells); F += m.mesh->n_faces; }
+  Batch *b = nullptr;
+  int rc = create_batch(sh, N, std::max<int64_t>(F, 1), static_cast<int>(mem.size()), st, &b);
+  if (rc) return rc;
+  int64_t co = 0, fo = 0;
+  for (size_t s = 0; s < mem.size() && !rc; ++s) {
+    rc = insert_solve(b, static_cast<int>(s), mem[s], co, fo);
+    co += pad_cells(mem[s].mesh->n_cells);
+    fo += mem[s].mesh->n_faces;
+  }
+  if (!rc) rc = finalize_batch(b);
+  if (rc) { destroy_batch(b); return rc; }
+  *out = b;
   return CGKS_OK;
 }
 
@@ -689,7 +756,7 @@ int load_state(Batch *b, int s, const double *W, const double *Wx, bool device) 
   CK(cudaMemcpyAsync(wa, W, sizeof(double) * 4 * n, kind, b->stream));
   if (Wx) CK(cudaMemcpyAsync(wxa, Wx, sizeof(double) * 8 * n, kind, b->stream));
   k_gather_state<<<nblk(n, kCellBlock), kCellBlock, 0, b->stream>>>(
-      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->N), b->perm + M.cell_off, wa,
+      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->Ncap), b->perm + M.cell_off, wa,
       Wx ? wxa : nullptr, b->W, b->Wx, b->mixed ? b->bf.W : nullptr, b->mixed ? b->bf.Wx : nullptr);
   b->launches++;
   CK(cudaGetLastError());
@@ -702,7 +769,7 @@ int store_state(Batch *b, int s, double *W, double *Wx, bool device) {
   const int64_t n = M.mesh->n_cells;
   double *wa = b->stage, *wxa = b->stage + 4 * n;
   k_scatter_state<<<nblk(n, kCellBlock), kCellBlock, 0, b->stream>>>(
-      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->N), b->perm + M.cell_off, b->W, b->Wx, wa,
+      static_cast<int>(n), static_cast<int>(M.cell_off), static_cast<int>(b->Ncap), b->perm + M.cell_off, b->W, b->Wx, wa,
       wxa);
   b->launches++;
   CK(cudaGetLastError());
@@ -750,6 +817,32 @@ struct cgks_solver {
   int status_cache = 0;
 };
 
+// First-fit allocator of ranges [0, cap) in units of `align`.
+struct RangeAlloc {
+  std::map<int64_t, int64_t> free_;   // offset -> length
+  void reset(int64_t cap) { free_.clear(); if (cap > 0) free_[0] = cap; }
+  int64_t alloc(int64_t len) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < len) continue;
+      const int64_t off = it->first, rest = it->second - len;
+      free_.erase(it);
+      if (rest > 0) free_[off + len] = rest;
+      return off;
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t len) {
+    if (len <= 0) return;
+    auto it = free_.emplace(off, len).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && off + len == nx->first) { it->second += nx->second; free_.erase(nx); }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+    }
+  }
+};
+
 struct cgks_server {
   struct Req {
     int64_t id;
@@ -757,21 +850,24 @@ struct cgks_server {
     cgks_params params;
     std::vector<double> W0;
     double drop;
+    int max_cycles;
     cgks_req_status st;
     std::vector<double> result;      // final state, caller order
     size_t footprint;
   };
   Shared sh;
   int max_active = 64, max_cycles = 20000;
-  size_t budget = 0;
+  size_t budget = 0, used = 0;
+  int64_t Ncap = 0, Fcap = 0;      // batch capacity the budget allows
   cudaStream_t user_stream = nullptr, stream = nullptr;
   cudaEvent_t ev_user = nullptr, ev_done = nullptr;
   int device = 0;
   int64_t next_id = 1;
   std::map<int64_t, std::unique_ptr<Req>> reqs;
   std::deque<int64_t> queue;
-  std::vector<int64_t> active;     // member s of the batch runs request active[s]
-  Batch *b = nullptr;
+  std::vector<int64_t> slot_req;   // request in each slot of the batch, -1 free
+  RangeAlloc cells, faces;
+  Batch *b = nullptr;              // created at the first admission
   std::chrono::steady_clock::time_point t0;
   std::vector<double> res_host;
   std::vector<int> status_host;
@@ -1018,13 +1114,13 @@ int cgks_residual(cgks_solver *s, double *res, double *r_l2) {
   CK(cudaMemcpyAsync(last, b->last, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
   std::vector<double> R;
   if (r_l2) {
-    R.resize(4 * static_cast<size_t>(b->N));
+    R.resize(4 * static_cast<size_t>(b->Ncap));
     CK(cudaMemcpyAsync(R.data(), b->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
   }
   CK(cudaStreamSynchronize(s->stream));
   if (res) *res = last[0];
   if (r_l2) {
-    const int64_t n = b->mem[0].mesh->n_cells, N = b->N;
+    const int64_t n = b->mem[0].mesh->n_cells, N = b->Ncap;
     for (int v = 0; v < 4; ++v) {
       double a = 0.0;
       for (int64_t i = 0; i < n; ++i) a += R[v * N + i] * R[v * N + i];
@@ -1039,7 +1135,7 @@ int cgks_get_rp0(cgks_solver *s, double *Rp0) {
   int rc = begin_call(s);
   if (rc) return rc;
   Batch *b = s->b;
-  const int64_t N = b->N, n = b->mem[0].mesh->n_cells;
+  const int64_t N = b->Ncap, n = b->mem[0].mesh->n_cells;
   std::vector<double> R(4 * static_cast<size_t>(N));
   CK(cudaMemcpyAsync(R.data(), b->Rp0, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -1103,6 +1199,10 @@ void cgks_server_default_opts(cgks_server_opts *o) {
   o->use_graph = 1;
 }
 
+// Faces per cell the batch capacity provides for (2-D: triangles 1.5,
+// quads 2, plus boundary faces of small meshes).
+constexpr double kFacesPerCell = 2.5;
+
 int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server **out) {
   if (!o || !out || hbm_budget == 0 || o->max_active < 1 || o->max_cycles < 1 || !(o->cfl_hi > 0.0) ||
       !(o->cfl_lo > 0.0) || o->n_implicit < 0 || o->n_sweeps < 0 ||
@@ -1120,6 +1220,28 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;
   v->budget = hbm_budget;
+  v->slot_req.assign(o->max_active, -1);
+  // capacity: the arena of Ncap cells and kFacesPerCell * Ncap faces within the budget
+  {
+    const bool mixed = o->precision == CGKS_MIXED;
+    const int64_t U = 1 << 20;
+    auto total = [&](int64_t N, int64_t F) {
+      Batch tmp;
+      std::vector<Piece> pc;
+      plan_arena(&tmp, N, F, o->max_active, N, mixed, pc);
+      return static_cast<double>(arena_total(pc));
+    };
+    const double c0 = total(kCellBlock, 1);
+    const double cc = (total(kCellBlock + U, 1) - c0) / U, cf = (total(kCellBlock, 1 + U) - c0) / U;
+    const double room = static_cast<double>(hbm_budget) - c0 - sizeof(double) * kHistDefault - 64.0 * 256;
+    int64_t N = room > 0 ? static_cast<int64_t>(room / (cc + kFacesPerCell * cf)) : 0;
+    N = std::min<int64_t>(N, (INT32_MAX / (kNCol * kNM)) & ~int64_t(kCellBlock - 1));
+    N = N / kCellBlock * kCellBlock;
+    v->Ncap = N;
+    v->Fcap = static_cast<int64_t>(kFacesPerCell * N);
+    v->cells.reset(v->Ncap);
+    v->faces.reset(v->Fcap);
+  }
   v->user_stream = static_cast<cudaStream_t>(o->stream);
   cudaGetDevice(&v->device);
   v->t0 = std::chrono::steady_clock::now();
@@ -1145,7 +1267,7 @@ int cgks_server_destroy(cgks_server *v) {
 }
 
 int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p, const double *W0, double res_drop,
-                       int64_t *req_id) {
+                       int32_t max_cycles, int64_t *req_id) {
   if (!v || !m || !p || !W0 || !(res_drop > 0.0)) return CGKS_EINVAL;
   cgks_params q = *p;   // batch-wide fields come from the server
   q.cfl_hi = v->sh.cfl_hi; q.cfl_lo = v->sh.cfl_lo; q.n_implicit = v->sh.n_implicit; q.n_sweeps = v->sh.n_sweeps;
@@ -1167,13 +1289,14 @@ int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p,
   r->id = v->next_id++;
   r->params = q;
   r->drop = res_drop;
+  r->max_cycles = max_cycles > 0 ? std::min(max_cycles, v->max_cycles) : v->max_cycles;
   std::memset(&r->st, 0, sizeof(r->st));
   r->st.n_cells = m->h.n_cells;
   r->st.t_submit = now_s(v);
   r->footprint = solve_footprint(m->h.n_cells, m->h.n_faces, v->sh.precision == CGKS_MIXED);
   const int64_t id = r->id;
   if (req_id) *req_id = id;
-  if (r->footprint > v->budget) {
+  if (r->footprint > v->budget || pad_cells(m->h.n_cells) > v->Ncap || m->h.n_faces > v->Fcap) {
     r->st.state = CGKS_REQ_REJECTED;
     r->st.t_done = r->st.t_submit;
     v->reqs[id] = std::move(r);
@@ -1185,89 +1308,67 @@ int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p,
   return CGKS_OK;
 }
 
-// Replace the active batch by one running `next`.  Continuing solves keep
-// their device state: it is stashed compactly, the old batch is freed, the
-// new batch is built and the stash is moved in, so device memory never
-// holds two batches at once.
-static int server_rebuild(cgks_server *v, const std::vector<int64_t> &next) {
-  Batch *old = v->b;
-  v->b = nullptr;
-  // continuing solves: (index in next, index in old)
-  std::vector<std::pair<int, int>> cont;
-  for (size_t s = 0; s < next.size(); ++s)
-    for (size_t k = 0; k < v->active.size(); ++k)
-      if (v->active[k] == next[s]) cont.push_back({ static_cast<int>(s), static_cast<int>(k) });
-  int64_t n_st = 0;
-  for (auto &c : cont) n_st += old->mem[c.second].mesh->n_cells;
-  std::vector<int64_t> st_off(cont.size());
-  char *stash = nullptr;
-  double *sW = nullptr, *sWx = nullptr;
-  int *smap = nullptr;
-  int64_t N_new = 0;
-  for (int64_t id : next) N_new += pad_cells(v->reqs[id]->mesh->n_cells);
-  v->active.clear();
-  if (n_st > 0) {
-    const size_t bytes = sizeof(double) * 12 * n_st + sizeof(int) * std::max(n_st, N_new) + 512;
-    stash = static_cast<char *>(dev_alloc(v->sh, bytes));
-    if (!stash) { destroy_batch(old); return CGKS_ENOMEM; }
-    sW = reinterpret_cast<double *>(stash);
-    sWx = sW + 4 * n_st;
-    smap = reinterpret_cast<int *>(sWx + 8 * n_st);
-    std::vector<int> map(n_st);
-    int64_t o = 0;
-    for (size_t c = 0; c < cont.size(); ++c) {
-      const Member &O = old->mem[cont[c].second];
-      st_off[c] = o;
-      for (int64_t i = 0; i < O.mesh->n_cells; ++i) map[o + i] = static_cast<int>(O.cell_off + i);
-      o += O.mesh->n_cells;
-    }
-    CK(cudaMemcpyAsync(smap, map.data(), sizeof(int) * n_st, cudaMemcpyHostToDevice, v->stream));
-    k_move_state<<<nblk(n_st, kCellBlock), kCellBlock, 0, v->stream>>>(
-        static_cast<int>(n_st), static_cast<int>(old->N), smap, old->W, old->Wx, sW, sWx, nullptr, nullptr);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(v->stream));
+// Retire finished solves, admit queued ones into free slots and free cell /
+// face space, and refresh the batch's launch plan when the set changed.
+static int server_update(cgks_server *v, double t, bool *changed) {
+  *changed = false;
+  Batch *b = v->b;
+  for (int s = 0; s < v->max_active; ++s) {
+    const int64_t id = v->slot_req[s];
+    if (id < 0) continue;
+    cgks_server::Req &r = *v->reqs[id];
+    if (r.st.state == CGKS_REQ_ACTIVE) continue;
+    const Member &M = b->mem[s];
+    const int64_t co = M.cell_off, np = M.n_pad, fo = M.face_off, nf = M.mesh->n_faces;
+    int rc = remove_solve(b, s);
+    if (rc) return rc;
+    v->cells.release(co, np);
+    v->faces.release(fo, nf);
+    v->used -= r.footprint;
+    v->slot_req[s] = -1;
+    *changed = true;
   }
-  destroy_batch(old);
-  auto fail = [&](int rc) { dev_free(v->sh, stash); return rc; };
-  if (next.empty()) return fail(CGKS_OK);
-  std::vector<Member> mem(next.size());
-  for (size_t s = 0; s < next.size(); ++s) {
-    mem[s].mesh = v->reqs[next[s]]->mesh;
-    mem[s].params = v->reqs[next[s]]->params;
+  while (!v->queue.empty()) {
+    cgks_server::Req &r = *v->reqs[v->queue.front()];
+    int s = 0;
+    while (s < v->max_active && v->slot_req[s] >= 0) ++s;
+    if (s == v->max_active || v->used + r.footprint > v->budget) break;
+    const int64_t np = pad_cells(r.mesh->n_cells), nf = r.mesh->n_faces;
+    const int64_t co = v->cells.alloc(np);
+    if (co < 0) break;
+    const int64_t fo = v->faces.alloc(nf);
+    if (fo < 0) { v->cells.release(co, np); break; }
+    if (!v->b) {
+      int rc = create_batch(v->sh, v->Ncap, v->Fcap, v->max_active, v->stream, &v->b);
+      if (rc) { v->cells.release(co, np); v->faces.release(fo, nf); return rc; }
+      b = v->b;
+    }
+    Member m;
+    m.mesh = r.mesh;
+    m.params = r.params;
+    int rc = insert_solve(b, s, m, co, fo);
+    if (!rc) rc = load_state(b, s, r.W0.data(), nullptr, false);
+    if (rc) {
+      // this request cannot be placed: reject it and leave the rest queued
+      if (b->mem[s].active) remove_solve(b, s);
+      v->cells.release(co, np);
+      v->faces.release(fo, nf);
+      r.st.state = CGKS_REQ_REJECTED;
+      r.st.t_done = t;
+      v->queue.pop_front();
+      *changed = true;
+      return rc;
+    }
+    v->slot_req[s] = r.id;
+    v->used += r.footprint;
+    r.st.state = CGKS_REQ_ACTIVE;
+    r.st.t_admit = t;
+    r.W0.clear();
+    r.W0.shrink_to_fit();
+    v->queue.pop_front();
+    *changed = true;
   }
-  Batch *nb = nullptr;
-  int rc = build_batch(v->sh, std::move(mem), v->stream, &nb);
-  if (rc) return fail(rc);
-  if (n_st > 0) {
-    std::vector<int> map(nb->N, -1);
-    for (size_t c = 0; c < cont.size(); ++c) {
-      const Member &M = nb->mem[cont[c].first];
-      for (int64_t i = 0; i < M.mesh->n_cells; ++i) map[M.cell_off + i] = static_cast<int>(st_off[c] + i);
-    }
-    if (cudaMemcpyAsync(smap, map.data(), sizeof(int) * nb->N, cudaMemcpyHostToDevice, v->stream) != cudaSuccess) {
-      destroy_batch(nb);
-      return fail(CGKS_ECUDA);
-    }
-    k_move_state<<<nblk(nb->N, kCellBlock), kCellBlock, 0, v->stream>>>(
-        static_cast<int>(nb->N), static_cast<int>(n_st), smap, sW, sWx, nb->W, nb->Wx,
-        nb->mixed ? nb->bf.W : nullptr, nb->mixed ? nb->bf.Wx : nullptr);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(v->stream) != cudaSuccess) {
-      destroy_batch(nb);
-      return fail(CGKS_ECUDA);
-    }
-  }
-  dev_free(v->sh, stash);
-  for (size_t s = 0; s < next.size(); ++s) {
-    bool is_cont = false;
-    for (auto &c : cont) is_cont |= c.first == static_cast<int>(s);
-    if (!is_cont) {
-      rc = load_state(nb, static_cast<int>(s), v->reqs[next[s]]->W0.data(), nullptr, false);
-      if (rc) { destroy_batch(nb); return rc; }
-    }
-  }
-  CK(cudaStreamSynchronize(v->stream));
-  v->b = nb;
-  v->active = next;
+  if (*changed && b) return finalize_batch(b);
   return CGKS_OK;
 }
 
@@ -1275,40 +1376,14 @@ int cgks_server_step(cgks_server *v, int32_t *n_active) {
   if (!v) return CGKS_EINVAL;
   int rc = begin_call(v->user_stream, v->stream, v->ev_user, v->device);
   if (rc) return rc;
-  const double t = now_s(v);
-  // 1. drop finished solves (their states were copied out when they finished)
-  std::vector<int64_t> next;
-  for (int64_t id : v->active)
-    if (v->reqs[id]->st.state == CGKS_REQ_ACTIVE) next.push_back(id);
-  // 2. admit queued requests while the footprint fits
-  size_t used = 0;
-  for (int64_t id : next) used += v->reqs[id]->footprint;
-  bool changed = next.size() != v->active.size();
-  while (!v->queue.empty() && static_cast<int>(next.size()) < v->max_active) {
-    cgks_server::Req &r = *v->reqs[v->queue.front()];
-    if (used + r.footprint > v->budget) break;
-    used += r.footprint;
-    r.st.state = CGKS_REQ_ACTIVE;
-    r.st.t_admit = t;
-    next.push_back(r.id);
-    v->queue.pop_front();
-    changed = true;
-  }
-  if (changed) {
-    rc = server_rebuild(v, next);
-    if (rc) {
-      // the batch could not be formed: its requests are rejected
-      for (int64_t id : next) {
-        cgks_server::Req &r = *v->reqs[id];
-        r.st.state = CGKS_REQ_REJECTED;
-        r.st.t_done = now_s(v);
-      }
-      return rc;
-    }
-  }
-  if (n_active) *n_active = static_cast<int32_t>(v->active.size());
-  if (v->active.empty()) return end_call(v->user_stream, v->stream, v->ev_done);
-  // 3. one batched V-cycle
+  bool changed = false;
+  rc = server_update(v, now_s(v), &changed);
+  if (rc) { end_call(v->user_stream, v->stream, v->ev_done); return rc; }
+  int na = 0;
+  for (int64_t id : v->slot_req) na += id >= 0;
+  if (n_active) *n_active = na;
+  if (na == 0) return end_call(v->user_stream, v->stream, v->ev_done);
+  // one batched V-cycle
   Batch *b = v->b;
   rc = run_many(b, 1, true);
   if (rc) return rc;
@@ -1318,9 +1393,11 @@ int cgks_server_step(cgks_server *v, int32_t *n_active) {
   CK(cudaMemcpyAsync(v->status_host.data(), b->status, sizeof(int) * b->S, cudaMemcpyDeviceToHost, v->stream));
   CK(cudaStreamSynchronize(v->stream));
   const double t1 = now_s(v);
-  // 4. convergence bookkeeping
+  // convergence bookkeeping; finished states are copied out now and their
+  // slots freed at the next step
   for (int s = 0; s < b->S; ++s) {
-    cgks_server::Req &r = *v->reqs[v->active[s]];
+    if (v->slot_req[s] < 0) continue;
+    cgks_server::Req &r = *v->reqs[v->slot_req[s]];
     const double res = v->res_host[s];
     r.st.cycles += 1;
     if (r.st.cycles == 1) r.st.res_first = res;
@@ -1328,7 +1405,7 @@ int cgks_server_step(cgks_server *v, int32_t *n_active) {
     int state = CGKS_REQ_ACTIVE;
     if (v->status_host[s] || !std::isfinite(res)) state = CGKS_REQ_DIVERGED;
     else if (r.st.cycles > 1 && res <= r.drop * r.st.res_first) state = CGKS_REQ_CONVERGED;
-    else if (r.st.cycles >= v->max_cycles) state = CGKS_REQ_STOPPED;
+    else if (r.st.cycles >= r.max_cycles) state = CGKS_REQ_STOPPED;
     if (state != CGKS_REQ_ACTIVE) {
       try {
         r.result.resize(4 * r.mesh->n_cells);
@@ -1373,7 +1450,9 @@ int cgks_server_info(cgks_server *v, int64_t *device_bytes, int32_t *n_queued, i
   if (!v) return CGKS_EINVAL;
   if (device_bytes) *device_bytes = v->b ? static_cast<int64_t>(v->b->arena_bytes + sizeof(double) * v->b->hist_cap) : 0;
   if (n_queued) *n_queued = static_cast<int32_t>(v->queue.size());
-  if (n_active) *n_active = static_cast<int32_t>(v->active.size());
+  int na = 0;
+  for (int64_t id : v->slot_req) na += id >= 0;
+  if (n_active) *n_active = na;
   return CGKS_OK;
 }
 

@@ -1,12 +1,14 @@
 // Kernels of the batched hot path (included by cgks_device.cu only).
 //
-// Index space: a batch concatenates one or more solves.  Each solve owns a
-// contiguous range of cells (padded to a multiple of kCellBlock with inert
-// padding cells, csid = -1) and a contiguous range of faces; within a
-// solve, cells are colour-major with reverse Cuthill-McKee order inside a
-// colour.  Boundary faces store -1 - (16 * solve + tag) in fc1, so one
-// global table holds every solve's boundary conditions.  Per-solve values
-// (viscosity, time step, status, residual) are indexed by the solve id.
+// Index space: a batch holds one or more solves in slots.  Each solve owns
+// a contiguous range of cells (padded to a multiple of kCellBlock with
+// inert cells, csid = -1) and a contiguous range of faces; space no solve
+// holds is inert too (csid / fsid = -1).  Within a solve, cells are
+// colour-major with reverse Cuthill-McKee order inside a colour.  Boundary
+// faces store -1 - (16 * slot + tag) in fc1, so one table holds every
+// solve's boundary conditions.  Per-solve values (viscosity, time step,
+// status, residual) are indexed by the slot.  Arrays are strided by the
+// batch capacity (m.nc cells, m.nf faces).
 //
 // Precision: kernels that evaluate fluxes are templated on the flux type
 // TF.  FP64 mode runs everything in double.  Mixed mode keeps the
@@ -108,9 +110,11 @@ __global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, int S, double 
 
 // K4: local explicit step per cell, per-solve min by atomicMin on the bits
 // (min is order independent).  h = 2|Omega|/perimeter, speed |U| + c + 2 nu / h.
-// Solves are padded to whole blocks, so a warp never spans two solves.
-__global__ void k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
-                     unsigned long long *dt_bits) {
+// Solves are padded to whole blocks, so a block never spans two solves and
+// its first cell is a real one: one atomic per block.
+__global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
+                                                   unsigned long long *dt_bits) {
+  __shared__ double wmin[kCellBlock / 32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = INFINITY;
   int sid = i < m.nc ? m.csid[i] : -1;
@@ -125,9 +129,13 @@ __global__ void k_dt(MeshT<double> m, ParamsT<double> P, const double *__restric
     d = hh / speed;
   }
   for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_down_sync(0xffffffffu, d, o));
-  int s0 = __shfl_sync(0xffffffffu, sid, 0);
-  if ((threadIdx.x & 31) == 0 && s0 >= 0 && d < INFINITY)
-    atomicMin(&dt_bits[s0], static_cast<unsigned long long>(__double_as_longlong(d)));
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kCellBlock / 32; ++w) d = fmin(d, wmin[w]);
+    const int s0 = blockIdx.x * blockDim.x < m.nc ? m.csid[blockIdx.x * blockDim.x] : -1;
+    if (s0 >= 0 && d < INFINITY) atomicMin(&dt_bits[s0], static_cast<unsigned long long>(__double_as_longlong(d)));
+  }
 }
 
 // Wall ghost of a state and its gradient (global frame), through the face frame.
@@ -248,10 +256,12 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, c
                                                      const T *__restrict__ coef, T *__restrict__ out) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
+  const int sid = m.fsid[f];
+  if (sid < 0) return;   // free face space of a batch
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
-  const T mu = P.mu[m.fsid[f]];
+  const T mu = P.mu[sid];
   T acc[4][4];
   for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = T(0);
   T wff[4];
@@ -379,13 +389,14 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
   if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
 }
 
-// Sum each solve's block partials in a fixed order (one block per solve):
-// Res_s = num / den.  Solve 0 also appends to the residual history.
-__global__ void k_res_final(const double *__restrict__ partial, const int *__restrict__ blk_begin, Ctl *ctl,
+// Sum each solve's block partials in a fixed order (one block per solve
+// slot; blk[2s], blk[2s+1] its cell blocks): Res_s = num / den.  Slot 0
+// also appends to the residual history.
+__global__ void k_res_final(const double *__restrict__ partial, const int *__restrict__ blk, Ctl *ctl,
                             double *__restrict__ res, double *hist, int cap, double *last) {
   const int s = blockIdx.x;
   double a = 0.0, b = 0.0;
-  for (int k = blk_begin[s] + threadIdx.x; k < blk_begin[s + 1]; k += blockDim.x) {
+  for (int k = blk[2 * s] + threadIdx.x; k < blk[2 * s + 1]; k += blockDim.x) {
     a += partial[2 * k];
     b += partial[2 * k + 1];
   }
@@ -445,10 +456,12 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P
                                                         T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
+  const int sid = m.fsid[f];
+  if (sid < 0) return;   // free face space of a batch
   const int n = m.nc, nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
-  const T mu = P.mu[m.fsid[f]];
+  const T mu = P.mu[sid];
   D::Prim<T> a = load_prim(prim, n, c0), b;
   T ivb;
   if (c1 >= 0) {
@@ -608,15 +621,13 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P,
       }
     }
   }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 1);
-    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 2);
-  }
-  if (i >= 0) {
-    const T mine = s == 0 ? c[0] : s == 1 ? c[1] : s == 2 ? c[2] : c[3];
-    dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
-  }
+  // lane s needs component s summed over the group: a transposing
+  // reduction (3 additions per lane instead of an all-reduce of 4 values)
+  const bool b0 = s & 1, b1 = s & 2;
+  const T k0 = (b0 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);   // component b0
+  const T k1 = (b0 ? c[3] : c[2]) + __shfl_xor_sync(0xffffffffu, b0 ? c[2] : c[3], 1);   // component b0 + 2
+  const T mine = (b1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
+  if (i >= 0) dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
 }
 
 // K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
@@ -675,33 +686,28 @@ __global__ void k_scatter_state(int ns, int off, int N, const int *__restrict__ 
   if (Wa) for (int v = 0; v < 4; ++v) Wa[4 * c + v] = W[v * N + i];
   if (Wxa) for (int q = 0; q < 8; ++q) Wxa[8 * c + q] = Wx[q * N + i];
 }
-// Padding cells: a valid uniform state so their (unused) arithmetic stays finite.
-__global__ void k_fill_padding(int N, const int *__restrict__ csid, double *__restrict__ W, double *__restrict__ Wx,
-                               float *__restrict__ W32, float *__restrict__ Wx32) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N || csid[i] >= 0) return;
+// Inert cells (padding, free space of a batch): no faces, no neighbours,
+// no solve, no colour, and a valid uniform state so that the arithmetic the
+// cell kernels still do for them stays finite.
+__global__ void k_clear_cells(int c0, int c1, int N, int *__restrict__ csid, unsigned char *__restrict__ ccol,
+                              int *__restrict__ cface, int *__restrict__ cnbr, double *__restrict__ W,
+                              double *__restrict__ Wx, double *__restrict__ Wn, double *__restrict__ Ws,
+                              double *__restrict__ Wxs, float *__restrict__ W32, float *__restrict__ Wx32,
+                              float *__restrict__ Wn32, float *__restrict__ Ws32, float *__restrict__ Wxs32) {
+  const int i = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c1) return;
+  csid[i] = -1;
+  ccol[i] = 255;
+  for (int s = 0; s < kMaxFace; ++s) { cface[s * N + i] = kNoFace; cnbr[s * N + i] = -1; }
   const double w[4] = { 1.0, 0.0, 0.0, 2.5 };
-  for (int v = 0; v < 4; ++v) { W[v * N + i] = w[v]; if (W32) W32[v * N + i] = static_cast<float>(w[v]); }
-  for (int q = 0; q < 8; ++q) { Wx[q * N + i] = 0.0; if (Wx32) Wx32[q * N + i] = 0.0f; }
-}
-// Move the states of continuing solves between two batches: dst cell i
-// takes src cell map[i] (map[i] < 0: untouched).
-__global__ void k_move_state(int N, int Nsrc, const int *__restrict__ map, const double *__restrict__ Ws,
-                             const double *__restrict__ Wxs, double *__restrict__ W, double *__restrict__ Wx,
-                             float *__restrict__ W32, float *__restrict__ Wx32) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int j = map[i];
-  if (j < 0) return;
   for (int v = 0; v < 4; ++v) {
-    double w = Ws[v * Nsrc + j];
-    W[v * N + i] = w;
-    if (W32) W32[v * N + i] = static_cast<float>(w);
+    W[v * N + i] = w[v]; Wn[v * N + i] = w[v]; Ws[v * N + i] = w[v];
+    if (W32) { W32[v * N + i] = static_cast<float>(w[v]); Wn32[v * N + i] = static_cast<float>(w[v]);
+               Ws32[v * N + i] = static_cast<float>(w[v]); }
   }
   for (int q = 0; q < 8; ++q) {
-    double g = Wxs[q * Nsrc + j];
-    Wx[q * N + i] = g;
-    if (Wx32) Wx32[q * N + i] = static_cast<float>(g);
+    Wx[q * N + i] = 0.0; Wxs[q * N + i] = 0.0;
+    if (Wx32) { Wx32[q * N + i] = 0.0f; Wxs32[q * N + i] = 0.0f; }
   }
 }
 

@@ -65,36 +65,47 @@ def test_batch_equals_standalone_bitwise(cg, precision):
         assert np.array_equal(Wb, Ws), (name, np.abs(Wb - Ws).max())
         assert st["res_last"] == hist[-1] and st["res_first"] == hist[0], name
     assert srv.step() == 0
-    assert srv.info()["device_bytes"] == 0
+    info = srv.info()
+    assert info["n_active"] == 0 and info["n_queued"] == 0
+    assert 0 < info["device_bytes"] <= 8 << 30
 
 
 def test_staggered_admission_and_budget(cg):
-    """Budget for two solves at a time, a late submission mid-run: batches
-    are rebuilt as solves retire and arrive, continuing solves carry their
-    state across rebuilds, and every result is bitwise the standalone one."""
+    """A budget for about three of four equal solves and a late submission
+    mid-run: solves are admitted as space frees up, retired ones leave
+    holes that later ones reuse, continuing solves keep running in place,
+    the device bytes stay within the budget, and every result is bitwise
+    the standalone one."""
     K = 5
-    reqs = requests()
+    reqs = []
+    for k in range(5):
+        mesh = MG.cavity(24, jitter=0.1, seed=10 + k)
+        lid = 0.1 + 0.02 * k
+        spec = dict(gamma=GAM, mu=lid / 400.0, bcs=[dict(kind="noslip"), dict(kind="noslip", uw=(lid, 0.0))])
+        W = np.tile(exact.cons_from_prim(GAM, 1.0, 0.0, 0.0, 1 / GAM), (mesh.n_cells, 1))
+        reqs.append((f"cavity24_{k}", mesh, spec, W))
     meshes = [cg.Mesh(m) for _, m, _, _ in reqs]
     probe = cg.Server(1 << 30, max_cycles=K)
-    fp = [probe.footprint(gm) for gm in meshes]
+    fp = probe.footprint(meshes[0])
     probe.close()
-    budget = sum(sorted(fp)[-2:])
+    budget = int(3.2 * fp)
     srv = cg.Server(budget, max_active=8, max_cycles=K)
-    ids = [srv.submit(gm, spec, W, NEVER) for gm, (_, _, spec, W) in zip(meshes[:3], reqs[:3])]
+    ids = [srv.submit(gm, spec, W, NEVER) for gm, (_, _, spec, W) in zip(meshes[:4], reqs[:4])]
     late = None
-    steps = 0
+    steps, counts = 0, []
     while True:
         n = srv.step()
         info = srv.info()
         assert info["device_bytes"] <= budget
-        assert n <= 2
+        counts.append(n)
         steps += 1
         if steps == 3:
-            _, _, spec, W = reqs[3]
-            late = srv.submit(meshes[3], spec, W, NEVER)
+            _, _, spec, W = reqs[4]
+            late = srv.submit(meshes[4], spec, W, NEVER)
         if n == 0 and info["n_queued"] == 0 and late is not None:
             break
         assert steps < 100
+    assert 1 <= max(counts) <= 3
     for rid, (name, mesh, spec, W) in zip(ids + [late], reqs):
         st, Wb = srv.poll(rid)
         assert st["state"] == "stopped" and st["cycles"] == K, (name, st)
@@ -173,3 +184,17 @@ def test_many_solves_use_cell_lists(cg):
         assert st["state"] == "stopped"
         Ws, _ = standalone(cg, mesh, spec, W, K, "fp64")
         assert np.array_equal(Wb, Ws)
+
+
+def test_per_request_cycle_cap(cg):
+    """A request's own cycle cap stops it early; the others keep running."""
+    reqs = requests()[:2]
+    meshes = [cg.Mesh(m) for _, m, _, _ in reqs]
+    srv = cg.Server(8 << 30, max_cycles=6)
+    a = srv.submit(meshes[0], reqs[0][2], reqs[0][3], NEVER, max_cycles=2)
+    b = srv.submit(meshes[1], reqs[1][2], reqs[1][3], NEVER)
+    counts = [srv.step() for _ in range(7)]
+    assert counts == [2, 2, 1, 1, 1, 1, 0]
+    assert srv.poll(a)[0]["cycles"] == 2 and srv.poll(b)[0]["cycles"] == 6
+    Ws, _ = standalone(cg, reqs[0][1], reqs[0][2], reqs[0][3], 2, "fp64")
+    assert np.array_equal(srv.poll(a)[1], Ws)
