@@ -493,6 +493,12 @@ def work_model(mesh, gm, spec, precision):
     return {"sweep_flops": sweep_flops, "bytes": bytes_, "colours": C, "sweep_launches": ni * len(seq)}
 
 
+# DRAM bytes per k_sweep launch (read + write) from one ncu capture of this
+# workload, averaged over the colours of a V-cycle (6 big + 2 small colour
+# launches per implicit step); profiles/k_sweep_cylinder57k.md.
+SWEEP_TRAFFIC_PER_LAUNCH = {"fp64": 7.44e6, "mixed": 3.03e6}
+
+
 def roofline(kt, wm, precision, hbm, hbm_src, steps):
     """Roofline entry of the dominant kernel and achieved GB/s of all."""
     per = {}
@@ -506,13 +512,14 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
     if top == "k_sweep" and precision == "fp64":
         ach = wm["sweep_flops"] / s_top / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_PER_LAUNCH.get(precision),
                 "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
                                "1.197 TFLOP/s)"}
     else:
         ach = wm["bytes"].get(top, 0.0) / s_top / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+                "traffic": SWEEP_TRAFFIC_PER_LAUNCH.get(precision) if top == "k_sweep" else None,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     return roof, per
 
 
