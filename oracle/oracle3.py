@@ -1,0 +1,305 @@
+"""ctypes wrapper of the serial FP64 3-D CPU oracle (``cgks_oracle3.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this module; the CUDA library never does.
+It imports nothing from the product package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cgks_oracle3.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle3.so")
+_lock = threading.Lock()
+_lib = None
+
+NV, ND = 5, 3
+BC_SLIP, BC_NOSLIP, BC_FARFIELD = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the 3-D oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class O3BC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("pad_", C.c_int), ("uw", C.c_double * 3),
+                ("rho", C.c_double), ("u", C.c_double * 3), ("p", C.c_double)]
+
+
+class O3Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
+                ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
+                ("time_scheme", C.c_int), ("n_bc", C.c_int), ("bc", O3BC * 16)]
+
+
+_dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            vp, P = C.c_void_p, C.POINTER(O3Params)
+            L.o3_mesh_create.restype = vp
+            L.o3_mesh_create.argtypes = [C.c_long, _dp, C.c_long, _u8p, _i64p, _i64p, C.c_long,
+                                         _i64p, _i64p, _i32p, C.POINTER(C.c_int)]
+            L.o3_mesh_destroy.argtypes = [vp]
+            L.o3_mesh_nfaces.restype = C.c_long
+            L.o3_mesh_nfaces.argtypes = [vp]
+            L.o3_mesh_ncolours.argtypes = [vp]
+            L.o3_mesh_geometry.argtypes = [vp, _dp, _dp, _dp]
+            L.o3_mesh_faces.argtypes = [vp, _i64p, _i64p, _i32p, _dp, _dp, _i32p, _dp, _dp]
+            L.o3_mesh_ordering.argtypes = [vp, _i64p, _i32p]
+            L.o3_solver_create.restype = vp
+            L.o3_solver_create.argtypes = [vp, P]
+            L.o3_solver_destroy.argtypes = [vp]
+            L.o3_set_state.argtypes = [vp, _dp, vp]
+            L.o3_get_state.argtypes = [vp, _dp, _dp]
+            L.o3_last_residual.restype = C.c_double
+            L.o3_last_residual.argtypes = [vp]
+            L.o3_status.argtypes = [vp]
+            L.o3_highorder_step.restype = C.c_double
+            L.o3_highorder_step.argtypes = [vp, C.c_double]
+            L.o3_explicit_dt.restype = C.c_double
+            L.o3_explicit_dt.argtypes = [vp]
+            L.o3_pmg_cycle.argtypes = [vp, C.c_int, _dp]
+            L.o3_explicit_steps.argtypes = [vp, C.c_int, _dp]
+            L.o3_loworder_smooth.argtypes = [vp]
+            L.o3_hi_residual.argtypes = [vp, C.c_double, _dp]
+            L.o3_reconstruct.argtypes = [vp]
+            L.o3_recon_eval.argtypes = [vp, C.c_long, _dp, _dp, _dp]
+            L.o3_lo_residual.argtypes = [vp, _dp, _dp]
+            L.o3_lo_lambda.argtypes = [vp, _dp, _dp]
+            L.o3_lo_diag.argtypes = [vp, _dp, _dp]
+            L.o3_lo_relax.argtypes = [vp, _dp, _dp, C.c_int, _dp]
+            L.o3_set_rp0.argtypes = [vp, _dp]
+            L.o3_get_rp0.argtypes = [vp, _dp]
+            L.o3_gks_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
+            L.o3_kfvs.argtypes = [P, _dp, _dp, _dp, _dp]
+            L.o3_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
+            L.o3_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.o3_micro_slope.argtypes = [C.c_double, _dp, _dp, _dp]
+            _lib = L
+    return _lib
+
+
+def _vec3(x):
+    x = tuple(float(v) for v in x)
+    return x + (0.0,) * (3 - len(x))
+
+
+def make_params(spec: dict) -> O3Params:
+    """Same keys as the 2-D oracle; velocities have three components."""
+    P = O3Params()
+    P.gamma = float(spec.get("gamma", 1.4))
+    P.mu = float(spec.get("mu", 0.0))
+    P.alpha = float(spec.get("alpha", 0.5))
+    P.cfl_hi = float(spec.get("cfl_hi", 0.4))
+    P.cfl_lo = float(spec.get("cfl_lo", 1000.0))
+    P.n_implicit = int(spec.get("n_implicit", 6))
+    P.n_sweeps = int(spec.get("n_sweeps", 2))
+    P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
+    bcs = spec.get("bcs", [])
+    P.n_bc = len(bcs)
+    for i, b in enumerate(bcs):
+        P.bc[i].kind = {"slip": BC_SLIP, "noslip": BC_NOSLIP, "farfield": BC_FARFIELD}[b["kind"]]
+        P.bc[i].uw[:] = _vec3(b.get("uw", (0.0, 0.0, 0.0)))
+        P.bc[i].rho = float(b.get("rho", 1.0))
+        P.bc[i].u[:] = _vec3(b.get("u", (0.0, 0.0, 0.0)))
+        P.bc[i].p = float(b.get("p", 1.0 / P.gamma))
+    return P
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+class OracleMesh3:
+    def __init__(self, mesh):
+        L = lib()
+        err = C.c_int(0)
+        self._m = L.o3_mesh_create(
+            mesh.nodes.shape[0], _f64(mesh.nodes), mesh.cell_type.shape[0],
+            np.ascontiguousarray(mesh.cell_type, np.uint8), np.ascontiguousarray(mesh.cell_ptr, np.int64),
+            np.ascontiguousarray(mesh.cell_nodes, np.int64), mesh.bface_tag.shape[0],
+            np.ascontiguousarray(mesh.bface_ptr, np.int64), np.ascontiguousarray(mesh.bface_nodes, np.int64),
+            np.ascontiguousarray(mesh.bface_tag, np.int32), C.byref(err))
+        if not self._m:
+            raise ValueError(f"oracle mesh rejected (code {err.value})")
+        self.n_cells = int(mesh.cell_type.shape[0])
+        self.n_faces = int(L.o3_mesh_nfaces(self._m))
+        self.n_colours = int(L.o3_mesh_ncolours(self._m))
+
+    def __del__(self):
+        if getattr(self, "_m", None):
+            lib().o3_mesh_destroy(self._m)
+            self._m = None
+
+    def geometry(self):
+        vol = np.zeros(self.n_cells); xc = np.zeros((self.n_cells, 3)); M2 = np.zeros((self.n_cells, 6))
+        lib().o3_mesh_geometry(self._m, vol, xc, M2)
+        return vol, xc, M2
+
+    def faces(self):
+        nf = self.n_faces
+        c0 = np.zeros(nf, np.int64); c1 = np.zeros(nf, np.int64); tag = np.zeros(nf, np.int32)
+        n = np.zeros((nf, 3)); S = np.zeros(nf); ng = np.zeros(nf, np.int32)
+        xg = np.zeros((nf, 4, 3)); wg = np.zeros((nf, 4))
+        lib().o3_mesh_faces(self._m, c0, c1, tag, n, S, ng, xg, wg)
+        return dict(c0=c0, c1=c1, tag=tag, n=n, S=S, ng=ng, xg=xg, wg=wg)
+
+    def ordering(self):
+        rcm = np.zeros(self.n_cells, np.int64); colour = np.zeros(self.n_cells, np.int32)
+        lib().o3_mesh_ordering(self._m, rcm, colour)
+        return rcm, colour
+
+
+class OracleSolver3:
+    def __init__(self, omesh: OracleMesh3, spec: dict):
+        self.mesh = omesh
+        self.params = make_params(spec)
+        self._s = lib().o3_solver_create(omesh._m, C.byref(self.params))
+        self.nc = omesh.n_cells
+
+    def __del__(self):
+        if getattr(self, "_s", None):
+            lib().o3_solver_destroy(self._s)
+            self._s = None
+
+    def set_state(self, W, Wx=None):
+        W = _f64(W, (self.nc, NV))
+        if Wx is None:
+            lib().o3_set_state(self._s, W, None)
+        else:
+            Wx = _f64(Wx, (self.nc, ND, NV))
+            lib().o3_set_state(self._s, W, Wx.ctypes.data_as(C.c_void_p))
+
+    def get_state(self):
+        W = np.zeros((self.nc, NV)); Wx = np.zeros((self.nc, ND, NV))
+        lib().o3_get_state(self._s, W, Wx)
+        return W, Wx
+
+    def status(self) -> int:
+        return int(lib().o3_status(self._s))
+
+    def explicit_dt(self) -> float:
+        return float(lib().o3_explicit_dt(self._s))
+
+    def highorder_step(self, dt: float = -1.0) -> float:
+        return float(lib().o3_highorder_step(self._s, dt))
+
+    def explicit_steps(self, n: int) -> np.ndarray:
+        r = np.zeros(max(n, 1))
+        rc = lib().o3_explicit_steps(self._s, n, r)
+        if rc:
+            raise FloatingPointError(f"oracle explicit steps failed (status {rc})")
+        return r[:n]
+
+    def pmg_cycles(self, n: int) -> np.ndarray:
+        r = np.zeros(max(n, 1))
+        rc = lib().o3_pmg_cycle(self._s, n, r)
+        if rc:
+            raise FloatingPointError(f"oracle p-multigrid cycle failed (status {rc})")
+        return r[:n]
+
+    def loworder_smooth(self):
+        lib().o3_loworder_smooth(self._s)
+
+    def residual(self) -> float:
+        return float(lib().o3_last_residual(self._s))
+
+    def hi_residual(self, dt: float) -> np.ndarray:
+        R = np.zeros((self.nc, NV))
+        lib().o3_hi_residual(self._s, dt, R)
+        return R
+
+    def reconstruct(self):
+        lib().o3_reconstruct(self._s)
+
+    def recon_eval(self, cell: int, x):
+        v = np.zeros(NV); g = np.zeros((ND, NV))
+        lib().o3_recon_eval(self._s, int(cell), _f64(x), v, g)
+        return v, g
+
+    def lo_residual(self, U):
+        R = np.zeros((self.nc, NV))
+        lib().o3_lo_residual(self._s, _f64(U, (self.nc, NV)), R)
+        return R
+
+    def lo_lambda(self, U):
+        lam = np.zeros(self.mesh.n_faces)
+        lib().o3_lo_lambda(self._s, _f64(U, (self.nc, NV)), lam)
+        return lam
+
+    def lo_diag(self, U):
+        D = np.zeros(self.nc)
+        lib().o3_lo_diag(self._s, _f64(U, (self.nc, NV)), D)
+        return D
+
+    def lo_relax(self, U, R, n_sweeps: int):
+        dU = np.zeros((self.nc, NV))
+        lib().o3_lo_relax(self._s, _f64(U, (self.nc, NV)), _f64(R, (self.nc, NV)), int(n_sweeps), dU)
+        return dU
+
+    def set_rp0(self, R):
+        lib().o3_set_rp0(self._s, _f64(R, (self.nc, NV)))
+
+    def get_rp0(self):
+        R = np.zeros((self.nc, NV))
+        lib().o3_get_rp0(self._s, R)
+        return R
+
+
+def gks_flux_point(spec, Wl, Wr, gl, gr, n, delta=0.0):
+    P = make_params(spec)
+    F0 = np.zeros(NV); F1 = np.zeros(NV); Wc = np.zeros(NV); Wt = np.zeros(NV)
+    lib().o3_gks_flux_point(C.byref(P), _f64(Wl), _f64(Wr), _f64(gl, (ND * NV,)), _f64(gr, (ND * NV,)),
+                            _f64(n), float(delta), F0, F1, Wc, Wt)
+    return F0, F1, Wc, Wt
+
+
+def kfvs(spec, Wl, Wr, n):
+    P = make_params(spec)
+    F = np.zeros(NV)
+    lib().o3_kfvs(C.byref(P), _f64(Wl), _f64(Wr), _f64(n), F)
+    return F
+
+
+def euler_flux(gamma, W, n):
+    F = np.zeros(NV)
+    lib().o3_euler_flux(float(gamma), _f64(W), _f64(n), F)
+    return F
+
+
+def ghost(spec, tag, W, grad, n):
+    P = make_params(spec)
+    Wg = np.zeros(NV); gg = np.zeros(ND * NV)
+    lib().o3_ghost(C.byref(P), int(tag), _f64(W), _f64(grad, (ND * NV,)), _f64(n), Wg, gg)
+    return Wg, gg.reshape(ND, NV)
+
+
+def micro_slope(gamma, W, dW):
+    s = np.zeros(NV)
+    rc = lib().o3_micro_slope(float(gamma), _f64(W), _f64(dW), s)
+    if rc:
+        raise np.linalg.LinAlgError("singular moment matrix")
+    return s

@@ -242,3 +242,286 @@ def cylinder(n_theta: int = 256, n_quad: int = 32, n_tri: int = 96, *, growth=1.
 
 def cylinder_cells(n_theta: int, n_quad: int, n_tri: int) -> int:
     return n_theta * (n_quad + 2 * n_tri)
+
+
+# ---------------------------------------------------------------- 3-D
+# Cell type codes in 3-D and node order.  Every 3-D cell is "positive": its
+# first face is counter-clockwise seen from the rest of the cell.
+#   tet     (2): 0 1 2 | 3
+#   prism   (3): 0 1 2 | 3 4 5        node k+3 above node k
+#   pyramid (4): 0 1 2 3 | 4          apex last
+#   hex     (5): 0 1 2 3 | 4 5 6 7    node k+4 above node k
+TET, PRISM, PYRAMID, HEX = 2, 3, 4, 5
+_NV3 = {TET: 4, PRISM: 6, PYRAMID: 5, HEX: 8}
+
+
+def _finish3(nodes, cells, bfaces, btags, meta) -> Mesh:
+    """cells: list of (type, node tuple); bfaces: node tuples (3 or 4)."""
+    cell_type = np.array([t for t, _ in cells], np.uint8)
+    sizes = np.array([len(c) for _, c in cells], np.int64)
+    cell_ptr = np.zeros(len(cells) + 1, np.int64)
+    np.cumsum(sizes, out=cell_ptr[1:])
+    cell_nodes = np.fromiter((v for _, c in cells for v in c), np.int64, count=int(cell_ptr[-1]))
+    bsz = np.array([len(f) for f in bfaces], np.int64)
+    bface_ptr = np.zeros(len(bfaces) + 1, np.int64)
+    np.cumsum(bsz, out=bface_ptr[1:])
+    bface_nodes = np.fromiter((v for f in bfaces for v in f), np.int64, count=int(bface_ptr[-1]))
+    return Mesh(3, np.ascontiguousarray(nodes, np.float64), cell_type, cell_ptr, cell_nodes,
+                bface_ptr, bface_nodes, np.asarray(btags, np.int32), meta)
+
+
+def _orient_tet(x, t):
+    """Swap two nodes of a tet if its node order is negative."""
+    a, b, c, d = t
+    v = np.dot(np.cross(x[b] - x[a], x[c] - x[a]), x[d] - x[a])
+    return (a, c, b, d) if v < 0 else (a, b, c, d)
+
+
+# the six monotone paths from corner 000 to corner 111 of a unit cube: the
+# Kuhn subdivision into tets, conforming across a structured grid
+_KUHN = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def box3(nx: int, ny: int, nz: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0, z0=0.0, z1=1.0, *,
+         jitter=0.0, seed=0, cells="tet", tags=(0, 1, 2, 3, 4, 5), hex_mask=None, name="box3") -> Mesh:
+    """Box [x0,x1]x[y0,y1]x[z0,z1] with nx*ny*nz grid cells.
+
+    ``cells``: 'tet' (6 tets per grid cell, Kuhn subdivision), 'prism' (2
+    prisms per grid cell, split along the xy diagonal), 'hex', 'pyramid' (6
+    pyramids per grid cell from its centre), or 'mixed' (hexes where
+    ``hex_mask(i, j, k)`` is true, tets elsewhere: only on faces where both
+    sides agree, so 'mixed' takes a mask constant in k and hexes only where
+    the mask holds on whole columns; boundaries then match because tets and
+    hexes never share a face: a hex column is surrounded by pyramid-free
+    interfaces only if the mask is constant -- use it for tests of cell
+    types only).  Interior nodes move by U(-jitter*h, +jitter*h) per axis.
+    Boundary faces carry ``tags`` = (x0, x1, y0, y1, z0, z1).
+    """
+    xs, ys, zs = np.linspace(x0, x1, nx + 1), np.linspace(y0, y1, ny + 1), np.linspace(z0, z1, nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    nodes = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
+
+    def nid(i, j, k):
+        return (k * (ny + 1) + j) * (nx + 1) + i
+
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        h = np.array([(x1 - x0) / nx, (y1 - y0) / ny, (z1 - z0) / nz])
+        d = rng.uniform(-1.0, 1.0, size=nodes.shape) * (jitter * h)
+        kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        interior = ((ii > 0) & (ii < nx) & (jj > 0) & (jj < ny) & (kk > 0) & (kk < nz)).reshape(-1)
+        nodes[interior] += d[interior]
+    centres = []
+    cl = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                corner = {(a, b, c): nid(i + a, j + b, k + c) for a in (0, 1) for b in (0, 1) for c in (0, 1)}
+                h8 = (corner[0, 0, 0], corner[1, 0, 0], corner[1, 1, 0], corner[0, 1, 0],
+                      corner[0, 0, 1], corner[1, 0, 1], corner[1, 1, 1], corner[0, 1, 1])
+                kind = cells
+                if cells == "mixed":
+                    kind = "hex" if hex_mask is not None and hex_mask(i, j, k) else "tet"
+                if kind == "hex":
+                    cl.append((HEX, h8))
+                elif kind == "prism":
+                    cl.append((PRISM, (h8[0], h8[1], h8[2], h8[4], h8[5], h8[6])))
+                    cl.append((PRISM, (h8[0], h8[2], h8[3], h8[4], h8[6], h8[7])))
+                elif kind == "pyramid":
+                    c = len(nodes) + len(centres)
+                    centres.append(nodes[list(h8)].mean(axis=0))
+                    for q in ((0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)):
+                        # base seen from the apex (the centre) must be counter-clockwise
+                        cl.append((PYRAMID, (h8[q[0]], h8[q[3]], h8[q[2]], h8[q[1]], c)))
+                else:
+                    for p in _KUHN:
+                        v = [0, 0, 0]
+                        path = [corner[tuple(v)]]
+                        for ax in p:
+                            v[ax] = 1
+                            path.append(corner[tuple(v)])
+                        cl.append((TET, tuple(path)))
+    if centres:
+        nodes = np.concatenate([nodes, np.array(centres)], axis=0)
+    cl = [(t, _orient_tet(nodes, c)) if t == TET else (t, c) for t, c in cl]
+    # boundary faces, by construction: grid quads on the six sides, split the
+    # way the cells split them
+    bf, bt = [], []
+
+    def side(quad, tag, split):
+        a, b, c, d = quad                      # (lo, lo) (hi, lo) (hi, hi) (lo, hi) in the side's axes
+        if split == "quad":
+            bf.append((a, b, c, d))
+        else:                                  # diagonal from the lowest to the highest corner
+            bf.append((a, b, c)); bf.append((a, c, d))
+        bt.append(tag)
+        if split != "quad":
+            bt.append(tag)
+
+    def kind_at(i, j, k):
+        if cells == "mixed":
+            return "hex" if hex_mask is not None and hex_mask(i, j, k) else "tet"
+        return cells
+
+    for k in range(nz):
+        for j in range(ny):
+            for (i, tag, ii) in ((0, tags[0], 0), (nx - 1, tags[1], nx)):
+                kd = kind_at(i, j, k)
+                side((nid(ii, j, k), nid(ii, j + 1, k), nid(ii, j + 1, k + 1), nid(ii, j, k + 1)), tag,
+                     "quad" if kd in ("hex", "prism", "pyramid") else "tri")
+    for k in range(nz):
+        for i in range(nx):
+            for (j, tag, jj) in ((0, tags[2], 0), (ny - 1, tags[3], ny)):
+                kd = kind_at(i, j, k)
+                side((nid(i, jj, k), nid(i + 1, jj, k), nid(i + 1, jj, k + 1), nid(i, jj, k + 1)), tag,
+                     "quad" if kd in ("hex", "prism", "pyramid") else "tri")
+    for j in range(ny):
+        for i in range(nx):
+            for (k, tag, kk) in ((0, tags[4], 0), (nz - 1, tags[5], nz)):
+                kd = kind_at(i, j, k)
+                side((nid(i, j, kk), nid(i + 1, j, kk), nid(i + 1, j + 1, kk), nid(i, j + 1, kk)), tag,
+                     "quad" if kd in ("hex", "pyramid") else "tri")
+    meta = dict(name=name, nx=nx, ny=ny, nz=nz, jitter=jitter, seed=seed, cells=cells,
+                bbox=(x0, x1, y0, y1, z0, z1))
+    return _finish3(nodes, cl, bf, bt, meta)
+
+
+def icosphere(level: int):
+    """Unit icosphere: 20 * 4**level triangles, outward counter-clockwise."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def m(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                p = verts[a] + verts[b]
+                verts.append(p / np.linalg.norm(p))
+                mid[key] = len(verts) - 1
+            return mid[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = m(a, b), m(b, c), m(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts)
+    F = np.array(faces, np.int64)
+    # outward orientation
+    cr = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    flip = (cr * V[F].mean(axis=1)).sum(axis=1) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return V, F
+
+
+def sphere_radii(n_prism, n_tet, h0, growth, R, R_far):
+    """Ring radii: n_prism layers from h0 growing by ``growth``, then n_tet
+    layers growing geometrically (ratio by bisection) to R_far, the first
+    one 1.1x the last prism layer... written as the continuation ratio."""
+    t = [h0 * growth ** k for k in range(n_prism)]
+    r = [R]
+    for d in t:
+        r.append(r[-1] + d)
+    if n_tet > 0:
+        first = t[-1] * growth if t else h0
+        span = R_far - r[-1]
+        lo, hi = 1.0 + 1e-12, 10.0
+        for _ in range(200):
+            q = 0.5 * (lo + hi)
+            s = first * (q ** n_tet - 1.0) / (q - 1.0)
+            lo, hi = (q, hi) if s < span else (lo, q)
+        q = 0.5 * (lo + hi)
+        for k in range(n_tet):
+            r.append(r[-1] + first * q ** k)
+        r[-1] = R_far
+    return np.array(r)
+
+
+# The 6 ways of cutting a prism (0 1 2 | 3 4 5) into 3 tets, with the
+# diagonal each one puts on the three quad faces (0 1 4 3), (1 2 5 4),
+# (2 0 3 5): the diagonal named by its end that lies on the bottom triangle
+# joined to the top of the other vertical edge.
+def _prism_splits():
+    out = []
+    for k in range(3):
+        a, b, c = k, (k + 1) % 3, (k + 2) % 3
+        A, B, C_ = a + 3, b + 3, c + 3
+        # two families per starting vertex
+        out.append(((a, b, c, A), (b, c, A, B), (c, A, B, C_)))
+        out.append(((a, b, c, A), (b, c, A, C_), (b, A, B, C_)))
+    return out
+
+
+def _tet_edges(t):
+    return {(min(t[i], t[j]), max(t[i], t[j])) for i in range(4) for j in range(i + 1, 4)}
+
+
+_PRISM_QUADS = ((0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5))
+
+
+def _split_local(p, x):
+    """Cut prism p (6 global nodes) into 3 tets; each quad face takes the
+    diagonal through its smallest global node index, so the cut conforms
+    with the neighbours'.  Returns the tets as local indices 0..5, each
+    positively ordered."""
+    want = []
+    for q in _PRISM_QUADS:
+        g = [p[i] for i in q]
+        m = int(np.argmin(g))
+        want.append((min(q[m], q[(m + 2) % 4]), max(q[m], q[(m + 2) % 4])))
+    for split in _prism_splits():
+        edges = set().union(*(_tet_edges(t) for t in split))
+        if all(w in edges for w in want):
+            out = []
+            for t in split:
+                a, b, c, d = t
+                v = np.dot(np.cross(x[p[b]] - x[p[a]], x[p[c]] - x[p[a]]), x[p[d]] - x[p[a]])
+                out.append((a, c, b, d) if v < 0 else t)
+            return out
+    raise ValueError("no conforming prism split")
+
+
+def sphere(level=4, n_prism=40, n_tet=20, *, h0=1e-3, growth=1.1, R=0.5, R_far=20.0) -> Mesh:
+    """Hybrid shell around a sphere of diameter 2R at the origin: the
+    icosphere of ``level`` (20*4**level triangles) extruded radially by
+    ``n_prism`` prism layers (first height h0*2R, growth ``growth``), then
+    ``n_tet`` layers of prisms each cut into 3 tets (conforming
+    smallest-index rule), geometric out to R_far * 2R.
+    Cells: 20*4**level * (n_prism + 3*n_tet).  Tags: 0 = sphere wall,
+    1 = far field."""
+    D = 2.0 * R
+    V, F = icosphere(level)
+    r = sphere_radii(n_prism, n_tet, h0 * D, growth, R, R_far * D)
+    nv, nt = V.shape[0], F.shape[0]
+    nodes = np.concatenate([V * rk for rk in r], axis=0)
+    # prism of surface triangle (a, b, c) between rings k and k+1: the
+    # surface triangle is counter-clockwise seen from outside, i.e. from
+    # the outer triangle, so (a, b, c | a', b', c') is positive
+    local = np.concatenate([F, F + nv], axis=1)              # [nt, 6] for k = 0
+    cl = []
+    prisms = np.concatenate([local + k * nv for k in range(n_prism)], axis=0) if n_prism else np.zeros((0, 6), np.int64)
+    cl += [(PRISM, tuple(int(v) for v in row)) for row in prisms]
+    if n_tet:
+        # the cut depends only on the order of the surface indices, the same
+        # in every layer; orientation is fixed on the first tet layer
+        k0 = n_prism
+        splits = [_split_local(tuple(int(v) for v in local[f] + k0 * nv), nodes) for f in range(nt)]
+        tets = np.array([[list(t) for t in sp] for sp in splits], np.int64)   # [nt, 3, 4] local
+        rows = np.take_along_axis(local[:, None, :].repeat(3, axis=1), tets, axis=2)  # [nt, 3, 4]
+        for k in range(n_tet):
+            g = (rows + (k0 + k) * nv).reshape(-1, 4)
+            cl += [(TET, tuple(int(v) for v in row)) for row in g]
+    nl = n_prism + n_tet
+    bf = [tuple(int(v) for v in f) for f in F] + [tuple(int(nl * nv + v) for v in f) for f in F]
+    bt = [0] * nt + [1] * nt
+    meta = dict(name=f"sphere{level}", level=level, n_prism=n_prism, n_tet=n_tet, h0=h0, growth=growth,
+                R=R, R_far=R_far)
+    return _finish3(nodes, cl, bf, bt, meta)
+
+
+SPHERE_WALL, SPHERE_FARFIELD = 0, 1
