@@ -48,7 +48,12 @@ enum {
 };
 
 /* cell types (node order counter-clockwise, as VTK) */
-enum { CGKS_TRI = 0, CGKS_QUAD = 1 };
+/* cell types: 2-D triangle / quadrilateral; 3-D tetrahedron, prism,
+ * pyramid, hexahedron.  Node order: 2-D counter-clockwise; 3-D "positive"
+ * (the first face counter-clockwise seen from the rest of the cell):
+ *   tet 0 1 2 | 3;  prism 0 1 2 | 3 4 5 (node k+3 above node k);
+ *   pyramid 0 1 2 3 | 4;  hex 0 1 2 3 | 4 5 6 7 (node k+4 above node k). */
+enum { CGKS_TRI = 0, CGKS_QUAD = 1, CGKS_TET = 2, CGKS_PRISM = 3, CGKS_PYRAMID = 4, CGKS_HEX = 5 };
 
 /* boundary conditions, Section 4 of the paper: reflective (slip) wall,
  * non-slip adiabatic wall (optionally moving tangentially), far field with
@@ -67,8 +72,8 @@ enum { CGKS_FP64 = 0, CGKS_MIXED = 1 };
 typedef struct {
   int32_t kind;          /* CGKS_BC_* */
   int32_t pad_;
-  double u_wall[2];      /* no-slip wall velocity (tangential) */
-  double rho, u[2], p;   /* far-field free stream (primitive variables) */
+  double u_wall[3];      /* no-slip wall velocity (tangential; 2-D uses x, y) */
+  double rho, u[3], p;   /* far-field free stream (primitive variables; 2-D uses x, y) */
 } cgks_bc;
 
 typedef void *(*cgks_alloc_fn)(size_t bytes, void *ctx);
@@ -107,20 +112,24 @@ typedef struct cgks_solver cgks_solver;
  * 6 implicit steps, 2 sweeps, S1O2, FP64, graphs on, no boundaries). */
 void cgks_default_params(cgks_params *p);
 
-/* Build a mesh from nodes, cells and tagged boundary edges (the finite-
+/* Build a mesh from nodes, cells and tagged boundary faces (the finite-
  * volume setting of Section 2.1).
- *   dim           2 (only 2-D is implemented; 3 returns CGKS_EINVAL)
+ *   dim           2 or 3
  *   xyz           [n_nodes*dim] node coordinates
- *   cell_type     [n_cells] CGKS_TRI / CGKS_QUAD
+ *   cell_type     [n_cells] CGKS_TRI / CGKS_QUAD (2-D), CGKS_TET /
+ *                 CGKS_PRISM / CGKS_PYRAMID / CGKS_HEX (3-D)
  *   cell_ptr      [n_cells+1] offsets into cell_nodes
- *   cell_nodes    node indices, counter-clockwise per cell
- *   bface_ptr     [n_bfaces+1] offsets into bface_nodes (2 nodes per edge)
+ *   cell_nodes    node indices in the order given with the cell types
+ *   bface_ptr     [n_bfaces+1] offsets into bface_nodes (2 nodes per edge
+ *                 in 2-D; 3 or 4 per face in 3-D, any order)
  *   bface_tag     [n_bfaces] index into cgks_params.bc[]
- * Builds faces, areas, centroids, 2-point Gauss-Legendre quadrature per
- * edge, the compact reconstruction operators, the reverse Cuthill-McKee
- * order and the greedy colouring.  Returns CGKS_EMESH for clockwise or
- * degenerate cells, edges shared by more than two cells, or boundary edges
- * without a tag.  Host only; no device memory is touched. */
+ * Builds faces, areas / volumes, centroids, Gauss quadrature per face (2
+ * points per edge; 3 per triangle, 4 per quadrilateral in 3-D), the reverse
+ * Cuthill-McKee order and the greedy colouring.  Returns CGKS_EMESH for
+ * negatively ordered or degenerate cells, faces shared by more than two
+ * cells, or boundary faces without a tag.  Host only.
+ * State layouts at the ABI, caller cell order: W [n_cells][dim+2],
+ * Wx [n_cells][dim][dim+2]. */
 int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cells,
                      const uint8_t *cell_type, const int64_t *cell_ptr, const int64_t *cell_nodes,
                      int64_t n_bfaces, const int64_t *bface_ptr, const int64_t *bface_nodes,
@@ -171,11 +180,11 @@ int cgks_pmg_cycle(cgks_solver *s, int n_cycles, double *res_hist);
 
 /* Density residual Res = sum|rho^{n+1} - rho^n| / sum rho^n of the last
  * update (Section 4), and optionally the L2 norm of each component of the
- * last high-order residual R_p0 (r_l2[4], may be NULL). */
+ * last high-order residual R_p0 (r_l2[dim+2], may be NULL). */
 int cgks_residual(cgks_solver *s, double *res, double *r_l2);
 
 /* Test access to intermediate results of the last high-order evaluation in
- * the caller's cell order: R_p0 [n_cells*4] (may be NULL). */
+ * the caller's cell order: R_p0 [n_cells*(dim+2)] (may be NULL). */
 int cgks_get_rp0(cgks_solver *s, double *Rp0);
 
 const char *cgks_strerror(int status);

@@ -524,13 +524,17 @@ static void tet_moments(const double p[3], const double a[3], const double b[3],
     }
 }
 
-/* volume, centroid and central second moments of a cell with nodes X */
-static void polyhedron(int type, const double X[8][3], double *vol, double xc[3], double M2[6]) {
+/* volume, centroid and central second moments of a cell with nodes X0;
+ * the moments are taken about the mean of the nodes (no cancellation for
+ * small cells far from the origin) */
+static void polyhedron(int type, const double X0[8][3], double *vol, double xc[3], double M2[6]) {
   const int (*tab)[4];
   int nf = cell_faces(type, &tab);
   int nv = type_nodes(type);
+  double o[3] = { 0, 0, 0 }, X[8][3];
+  for (int k = 0; k < nv; ++k) for (int d = 0; d < 3; ++d) o[d] += X0[k][d] / nv;
+  for (int k = 0; k < nv; ++k) for (int d = 0; d < 3; ++d) X[k][d] = X0[k][d] - o[d];
   double p[3] = { 0, 0, 0 };
-  for (int k = 0; k < nv; ++k) for (int d = 0; d < 3; ++d) p[d] += X[k][d] / nv;
   double V = 0.0, S1[3] = { 0, 0, 0 }, S2[6] = { 0, 0, 0, 0, 0, 0 };
   for (int f = 0; f < nf; ++f) {
     int m = tab[f][3] < 0 ? 3 : 4;
@@ -542,10 +546,12 @@ static void polyhedron(int type, const double X[8][3], double *vol, double xc[3]
     }
   }
   *vol = V;
-  for (int d = 0; d < 3; ++d) xc[d] = S1[d] / V;
+  double c[3];
+  for (int d = 0; d < 3; ++d) c[d] = S1[d] / V;
   int q = 0;
   for (int i = 0; i < 3; ++i)
-    for (int j = i; j < 3; ++j, ++q) M2[q] = S2[q] / V - xc[i] * xc[j];
+    for (int j = i; j < 3; ++j, ++q) M2[q] = S2[q] / V - c[i] * c[j];
+  for (int d = 0; d < 3; ++d) xc[d] = o[d] + c[d];
 }
 
 /* face of nodes X[0..m-1] (counter-clockwise seen from outside) */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcgks.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cgks_host.cpp", "cgks_device.cu", "cgks_noalloc.cu"]
+SOURCES = ["cgks_host.cpp", "cgks_host3.cpp", "cgks_device.cu", "cgks_device3.cu", "cgks_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -18,7 +18,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-TRI, QUAD = 0, 1
+TRI, QUAD, TET, PRISM, PYRAMID, HEX = 0, 1, 2, 3, 4, 5
 BC_SLIP, BC_NOSLIP, BC_FARFIELD = 0, 1, 2
 S1O2, S2O4 = 0, 1
 FP64, MIXED = 0, 1
@@ -35,8 +35,8 @@ class CgksError(RuntimeError):
 
 
 class CgksBC(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("u_wall", C.c_double * 2),
-                ("rho", C.c_double), ("u", C.c_double * 2), ("p", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("u_wall", C.c_double * 3),
+                ("rho", C.c_double), ("u", C.c_double * 3), ("p", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -144,6 +144,8 @@ class Mesh:
         self.n_faces = info.n_faces
         self.n_bfaces = info.n_bfaces
         self.n_colours = info.n_colours
+        self.dim = info.dim
+        self.nv = info.dim + 2
         self.device_bytes = info.device_bytes
 
     def ordering(self):
@@ -177,13 +179,14 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     kinds = {"slip": BC_SLIP, "noslip": BC_NOSLIP, "farfield": BC_FARFIELD}
+    def vec3(x):
+        x = [float(v) for v in x]
+        return x + [0.0] * (3 - len(x))
     for i, b in enumerate(bcs):
         P.bc[i].kind = kinds[b["kind"]]
-        uw = b.get("uw", (0.0, 0.0))
-        P.bc[i].u_wall[0], P.bc[i].u_wall[1] = float(uw[0]), float(uw[1])
+        P.bc[i].u_wall[:] = vec3(b.get("uw", (0.0, 0.0)))
         P.bc[i].rho = float(b.get("rho", 1.0))
-        u = b.get("u", (0.0, 0.0))
-        P.bc[i].u[0], P.bc[i].u[1] = float(u[0]), float(u[1])
+        P.bc[i].u[:] = vec3(b.get("u", (0.0, 0.0)))
         P.bc[i].p = float(b.get("p", 1.0 / P.gamma))
     if stream is not None:
         P.stream = C.c_void_p(stream)
@@ -223,6 +226,7 @@ class Solver:
         L = lib()
         self.mesh = mesh
         self.n_cells = mesh.n_cells
+        self.dim, self.nv = mesh.dim, mesh.nv
         stream, self._alloc = None, None
         if use_torch:
             import torch
@@ -244,8 +248,8 @@ class Solver:
 
     # -- state --------------------------------------------------------
     def set_state(self, W, Wx=None):
-        W = np.ascontiguousarray(W, np.float64).reshape(self.n_cells, 4)
-        Wx = None if Wx is None else np.ascontiguousarray(Wx, np.float64).reshape(self.n_cells, 2, 4)
+        W = np.ascontiguousarray(W, np.float64).reshape(self.n_cells, self.nv)
+        Wx = None if Wx is None else np.ascontiguousarray(Wx, np.float64).reshape(self.n_cells, self.dim, self.nv)
         _check(lib().cgks_set_state(self._h, _ptr(W), _ptr(Wx)), "cgks_set_state")
 
     def set_state_device(self, W_ptr: int, Wx_ptr: int | None = None):
@@ -253,8 +257,8 @@ class Solver:
                "cgks_set_state_device")
 
     def get_state(self):
-        W = np.zeros((self.n_cells, 4))
-        Wx = np.zeros((self.n_cells, 2, 4))
+        W = np.zeros((self.n_cells, self.nv))
+        Wx = np.zeros((self.n_cells, self.dim, self.nv))
         _check(lib().cgks_get_state(self._h, _ptr(W), _ptr(Wx)), "cgks_get_state")
         return W, Wx
 
@@ -283,13 +287,13 @@ class Solver:
 
     def residual(self):
         res = C.c_double()
-        rl2 = np.zeros(4)
+        rl2 = np.zeros(self.nv)
         _check(lib().cgks_residual(self._h, C.byref(res), _ptr(rl2)), "cgks_residual")
         return res.value, rl2
 
     def rp0(self):
-        R = np.zeros((self.n_cells, 4))
-        _check(lib().cgks_get_rp0(self._h, R), "cgks_get_rp0")
+        R = np.zeros((self.n_cells, self.nv))
+        _check(lib().cgks_get_rp0(self._h, R.reshape(-1)), "cgks_get_rp0")
         return R
 
     # -- instrumentation ----------------------------------------------

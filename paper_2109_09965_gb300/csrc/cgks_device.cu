@@ -22,6 +22,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_kernels.cuh"
+#include "cgks_runtime.h"
 
 using namespace cgks;
 using namespace cgks::kern;
@@ -41,12 +42,6 @@ struct Bufs {
   T *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
 };
 
-// kernel ids for the per-kernel timers
-enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_LOCELL,
-                KI_PROLONG, KI_COUNT };
-const char *kKernelNames[KI_COUNT] = { "k_dt", "k_recon", "k_face", "k_update", "k_res_final", "k_lo_face",
-                                       "k_lo_rhs", "k_sweep", "k_lo_cell", "k_prolong" };
-
 // batch-wide settings (every solve of a batch shares them)
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
@@ -62,13 +57,6 @@ struct Member {
   cgks_params params{};
   int64_t cell_off = 0, n_pad = 0, face_off = 0;
   bool active = false;
-};
-
-struct Timer {
-  bool on = false;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
-  double ms[KI_COUNT] = { 0 };
-  long long cnt[KI_COUNT] = { 0 };
 };
 
 // device tables of a batch (views into its arena)
@@ -358,20 +346,6 @@ int run_many(Batch *b, int n, bool cycle) {
   }
   CK(cudaGetLastError());
   return CGKS_OK;
-}
-
-void collect_timing(Timer *t) {
-  if (!t) return;
-  for (auto &e : t->ev) {
-    float ms = 0.f;
-    cudaEventSynchronize(e.second.second);
-    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
-    t->ms[e.first] += ms;
-    t->cnt[e.first] += 1;
-    cudaEventDestroy(e.second.first);
-    cudaEventDestroy(e.second.second);
-  }
-  t->ev.clear();
 }
 
 template <typename T>
@@ -789,12 +763,12 @@ Shared shared_from(const cgks_params *p) {
   return sh;
 }
 
-int validate_params(const cgks_params *p, const HostMesh &hm) {
+int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_used) {
   if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
       p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
       p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0))
     return CGKS_EINVAL;
-  for (int t : hm.bface_tags_used)
+  for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
   for (int b = 0; b < p->n_bc; ++b) {
     int k = p->bc[b].kind;
@@ -804,11 +778,14 @@ int validate_params(const cgks_params *p, const HostMesh &hm) {
   return CGKS_OK;
 }
 
+int validate_params(const cgks_params *p, const HostMesh &hm) { return validate_params_tags(p, hm.bface_tags_used); }
+
 }  // namespace
 
 // ------------------------------------------------------------------------
 struct cgks_solver {
   Batch *b = nullptr;
+  Solver3 *s3 = nullptr;       // 3-D meshes
   cgks_params params{};
   cudaStream_t user_stream = nullptr, stream = nullptr;
   cudaEvent_t ev_user = nullptr, ev_done = nullptr;
@@ -891,8 +868,13 @@ int end_call(cgks_solver *s) { return end_call(s->user_stream, s->stream, s->ev_
 
 int solver_status(cgks_solver *s) {
   int st = 0;
-  CK(cudaMemcpyAsync(&st, s->b->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  if (s->s3) {
+    int rc = s3_status(s->s3, &st);
+    if (rc) return rc;
+  } else {
+    CK(cudaMemcpyAsync(&st, s->b->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
   s->status_cache = st;
   return st ? CGKS_EDIVERGED : CGKS_OK;
 }
@@ -940,13 +922,18 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
                      const int64_t *bface_nodes, const int32_t *bface_tag, cgks_mesh **out) {
   if (!out) return CGKS_EINVAL;
   *out = nullptr;
-  if (dim != 2) return CGKS_EINVAL;
+  if (dim != 2 && dim != 3) return CGKS_EINVAL;
   cgks_mesh *m = new (std::nothrow) cgks_mesh();
   if (!m) return CGKS_ENOMEM;
+  m->dim = dim;
   int rc;
   try {
-    rc = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces, bface_ptr, bface_nodes,
-                         bface_tag, m->h);
+    if (dim == 2)
+      rc = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces, bface_ptr, bface_nodes,
+                           bface_tag, m->h);
+    else
+      rc = build_host_mesh3(n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces, bface_ptr,
+                            bface_nodes, bface_tag, m->h3);
   } catch (const std::bad_alloc &) {
     rc = CGKS_ENOMEM;
   }
@@ -957,6 +944,15 @@ int cgks_mesh_create(int dim, int64_t n_nodes, const double *xyz, int64_t n_cell
 
 int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
   if (!m || !out) return CGKS_EINVAL;
+  if (m->dim == 3) {
+    out->n_cells = m->h3.n_cells;
+    out->n_faces = m->h3.n_faces;
+    out->n_bfaces = m->h3.n_bfaces;
+    out->n_colours = m->h3.n_colours;
+    out->dim = 3;
+    out->device_bytes = static_cast<int64_t>(s3_footprint(m->h3.n_cells, m->h3.n_faces, false));
+    return CGKS_OK;
+  }
   out->n_cells = m->h.n_cells;
   out->n_faces = m->h.n_faces;
   out->n_bfaces = m->h.n_bfaces;
@@ -968,8 +964,10 @@ int cgks_mesh_info(const cgks_mesh *m, cgks_mesh_info_t *out) {
 
 int cgks_mesh_ordering(const cgks_mesh *m, int64_t *rcm, int32_t *colour) {
   if (!m) return CGKS_EINVAL;
-  if (rcm) std::copy(m->h.rcm.begin(), m->h.rcm.end(), rcm);
-  if (colour) std::copy(m->h.colour.begin(), m->h.colour.end(), colour);
+  const std::vector<int64_t> &r = m->dim == 3 ? m->h3.rcm : m->h.rcm;
+  const std::vector<int32_t> &c = m->dim == 3 ? m->h3.colour : m->h.colour;
+  if (rcm) std::copy(r.begin(), r.end(), rcm);
+  if (colour) std::copy(c.begin(), c.end(), colour);
   return CGKS_OK;
 }
 
@@ -984,6 +982,7 @@ int cgks_solver_destroy(cgks_solver *s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   collect_timing(&s->timer);
   destroy_batch(s->b);
+  s3_destroy(s->s3);
   if (s->ev_user) cudaEventDestroy(s->ev_user);
   if (s->ev_done) cudaEventDestroy(s->ev_done);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -994,7 +993,7 @@ int cgks_solver_destroy(cgks_solver *s) {
 int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **out) {
   if (!m || !p || !out) return CGKS_EINVAL;
   *out = nullptr;
-  int rc = validate_params(p, m->h);
+  int rc = validate_params_tags(p, m->dim == 3 ? m->h3.bface_tags_used : m->h.bface_tags_used);
   if (rc) return rc;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CGKS_ECUDA;
@@ -1007,6 +1006,16 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
   if (cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming) != cudaSuccess) return fail(CGKS_ECUDA);
+  if (m->dim == 3) {
+    try {
+      rc = s3_create(m->h3, p, s->stream, &s->timer, &s->s3);
+    } catch (const std::bad_alloc &) {
+      rc = CGKS_ENOMEM;
+    }
+    if (rc) return fail(rc);
+    *out = s;
+    return CGKS_OK;
+  }
   std::vector<Member> mem(1);
   try {
     mem[0].mesh = std::make_shared<HostMesh>(m->h);
@@ -1025,7 +1034,7 @@ static int set_state_impl(cgks_solver *s, const double *W, const double *Wx, boo
   if (!s || !W) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
-  rc = load_state(s->b, 0, W, Wx, device);
+  rc = s->s3 ? s3_set_state(s->s3, W, Wx, device) : load_state(s->b, 0, W, Wx, device);
   if (rc) return rc;
   s->status_cache = 0;
   return end_call(s);
@@ -1038,7 +1047,7 @@ static int get_state_impl(cgks_solver *s, double *W, double *Wx, bool device) {
   if (!s) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
-  rc = store_state(s->b, 0, W, Wx, device);
+  rc = s->s3 ? s3_get_state(s->s3, W, Wx, device) : store_state(s->b, 0, W, Wx, device);
   if (rc) return rc;
   return end_call(s);
 }
@@ -1051,6 +1060,16 @@ int cgks_highorder_step(cgks_solver *s, double dt, double *dt_used) {
   if (s->status_cache) return CGKS_EDIVERGED;
   int rc = begin_call(s);
   if (rc) return rc;
+  if (s->s3) {
+    int st = 0;
+    rc = s3_highorder_step(s->s3, dt, dt_used, &st);
+    if (rc) return rc;
+    collect_timing(&s->timer);
+    s->status_cache = st;
+    rc = end_call(s);
+    if (rc) return rc;
+    return st ? CGKS_EDIVERGED : CGKS_OK;
+  }
   Batch *b = s->b;
   CK(cudaMemsetAsync(&b->ctl->res_ctr, 0, sizeof(int), s->stream));
   enqueue_explicit_step(b, dt);
@@ -1074,6 +1093,17 @@ static int solver_run(cgks_solver *s, int n, double *res_hist, bool cycle) {
   if (!s || n < 0) return CGKS_EINVAL;
   if (s->status_cache) return CGKS_EDIVERGED;
   if (n == 0) return CGKS_OK;
+  if (s->s3) {
+    int rc = begin_call(s);
+    if (rc) return rc;
+    rc = s3_run(s->s3, n, cycle);
+    if (rc) return rc;
+    if (res_hist) { rc = s3_history(s->s3, res_hist, n); if (rc) return rc; }
+    rc = solver_status(s);
+    collect_timing(&s->timer);
+    int rc2 = end_call(s);
+    return rc ? rc : rc2;
+  }
   Batch *b = s->b;
   int rc = ensure_hist(b, n);
   if (rc) return rc;
@@ -1096,9 +1126,14 @@ int cgks_loworder_smooth(cgks_solver *s) {
   if (s->status_cache) return CGKS_EDIVERGED;
   int rc = begin_call(s);
   if (rc) return rc;
-  CK(cudaMemsetAsync(&s->b->ctl->res_ctr, 0, sizeof(int), s->stream));
-  enqueue_lo_smooth(s->b);
-  CK(cudaGetLastError());
+  if (s->s3) {
+    rc = s3_loworder_smooth(s->s3);
+    if (rc) return rc;
+  } else {
+    CK(cudaMemsetAsync(&s->b->ctl->res_ctr, 0, sizeof(int), s->stream));
+    enqueue_lo_smooth(s->b);
+    CK(cudaGetLastError());
+  }
   rc = solver_status(s);
   collect_timing(&s->timer);
   int rc2 = end_call(s);
@@ -1109,6 +1144,11 @@ int cgks_residual(cgks_solver *s, double *res, double *r_l2) {
   if (!s) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
+  if (s->s3) {
+    rc = s3_residual(s->s3, res, r_l2);
+    if (rc) return rc;
+    return end_call(s);
+  }
   Batch *b = s->b;
   double last[3];
   CK(cudaMemcpyAsync(last, b->last, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
@@ -1134,6 +1174,11 @@ int cgks_get_rp0(cgks_solver *s, double *Rp0) {
   if (!s || !Rp0) return CGKS_EINVAL;
   int rc = begin_call(s);
   if (rc) return rc;
+  if (s->s3) {
+    rc = s3_get_rp0(s->s3, Rp0);
+    if (rc) return rc;
+    return end_call(s);
+  }
   Batch *b = s->b;
   const int64_t N = b->Ncap, n = b->mem[0].mesh->n_cells;
   std::vector<double> R(4 * static_cast<size_t>(N));
@@ -1163,7 +1208,7 @@ int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_m
   collect_timing(&s->timer);
   int k = 0;
   for (; k < KI_COUNT && k < max; ++k) {
-    if (names) names[k] = kKernelNames[k];
+    if (names) names[k] = kernel_name(k);
     if (total_ms) total_ms[k] = s->timer.ms[k];
     if (count) count[k] = s->timer.cnt[k];
   }
@@ -1178,10 +1223,14 @@ int cgks_reset_timing(cgks_solver *s) {
   return CGKS_OK;
 }
 
-int64_t cgks_launch_count(const cgks_solver *s) { return s ? s->b->launches : -1; }
+int64_t cgks_launch_count(const cgks_solver *s) {
+  if (!s) return -1;
+  return s->s3 ? s3_launches(s->s3) : s->b->launches;
+}
 
 int cgks_launches_per_call(const cgks_solver *s, int cycle) {
-  return s ? static_cast<int>(count_launches(s->b, cycle != 0)) : -1;
+  if (!s) return -1;
+  return s->s3 ? s3_launches_per_call(s->s3, cycle != 0) : static_cast<int>(count_launches(s->b, cycle != 0));
 }
 
 // ================================ serving ================================
@@ -1269,6 +1318,7 @@ int cgks_server_destroy(cgks_server *v) {
 int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p, const double *W0, double res_drop,
                        int32_t max_cycles, int64_t *req_id) {
   if (!v || !m || !p || !W0 || !(res_drop > 0.0)) return CGKS_EINVAL;
+  if (m->dim != 2) return CGKS_EINVAL;   // the serving path batches 2-D solves
   cgks_params q = *p;   // batch-wide fields come from the server
   q.cfl_hi = v->sh.cfl_hi; q.cfl_lo = v->sh.cfl_lo; q.n_implicit = v->sh.n_implicit; q.n_sweeps = v->sh.n_sweeps;
   q.time_scheme = v->sh.time_scheme; q.precision = v->sh.precision;
@@ -1441,7 +1491,7 @@ int cgks_server_poll(cgks_server *v, int64_t req_id, cgks_req_status *st, double
 }
 
 int cgks_server_footprint(const cgks_server *v, const cgks_mesh *m, int64_t *bytes) {
-  if (!v || !m || !bytes) return CGKS_EINVAL;
+  if (!v || !m || !bytes || m->dim != 2) return CGKS_EINVAL;
   *bytes = static_cast<int64_t>(solve_footprint(m->h.n_cells, m->h.n_faces, v->sh.precision == CGKS_MIXED));
   return CGKS_OK;
 }

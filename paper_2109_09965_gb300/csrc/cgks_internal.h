@@ -55,8 +55,47 @@ int build_host_mesh(int64_t n_nodes, const double *xy, int64_t n_cells, const ui
                     const int64_t *bptr, const int64_t *bnodes, const int32_t *btag,
                     HostMesh &out);
 
+// ---------------------------------------------------------------- 3-D
+constexpr int kNV3 = 5;        // rho, rho u, rho v, rho w, rho E
+constexpr int kNM3 = 9;        // xi eta zeta xi^2 xi*eta xi*zeta eta^2 eta*zeta zeta^2
+constexpr int kMaxFace3 = 6;   // faces per cell (hexahedron)
+constexpr int kNCol3 = 4 * kMaxFace3 + 3;  // 4 per face slot (mean, 3 gradients) + own gradient
+constexpr int kMaxGP3 = 4;     // Gauss points per face (quadrilateral)
+
+// 3-D mesh in the library's internal orders (as HostMesh).
+struct HostMesh3 {
+  int64_t n_cells = 0, n_faces = 0, n_bfaces = 0;
+  int n_colours = 0;
+  std::vector<int64_t> rcm;
+  std::vector<int32_t> colour, perm, iperm, colour_start;
+  // cells, internal order
+  std::vector<double> vol, h, asum;  // volume, |Omega|^(1/3), sum of face areas
+  std::vector<double> xc;            // [3][n] centroid
+  std::vector<double> c2;            // [6][n] central second moments / volume: xx xy xz yy yz zz
+  std::vector<double> m2;            // [6][n] c2 / h^2: own means of the quadratic monomials
+  std::vector<int32_t> nfc;
+  std::vector<int32_t> cface;        // [6][n] f or ~f, kNoFace
+  std::vector<int32_t> cnbr;         // [6][n]
+  // faces, internal order
+  std::vector<int32_t> fc0, fc1, fng;
+  std::vector<double> fn;            // [3][nf]
+  std::vector<double> fS, fdelta;
+  std::vector<double> fw;            // [4][nf] Gauss weights (sum 1)
+  std::vector<double> fxf;           // [3][nf] face centre
+  std::vector<double> fxi;           // [24][nf] scaled Gauss offsets: side 0 (k: x y z), side 1
+  std::vector<int32_t> bface_tags_used;
+};
+
+int build_host_mesh3(int64_t n_nodes, const double *xyz, int64_t n_cells, const uint8_t *ctype,
+                     const int64_t *cptr, const int64_t *cnodes, int64_t n_bfaces, const int64_t *bptr,
+                     const int64_t *bnodes, const int32_t *btag, HostMesh3 &out);
+// [kNCol3 * kNM3][n], h_i folded into the gradient columns
+void build_operator3(const HostMesh3 &m, const std::vector<char> &tag_is_wall, std::vector<double> &op);
+
 }  // namespace cgks
 
 struct cgks_mesh {
+  int dim = 2;
   cgks::HostMesh h;
+  cgks::HostMesh3 h3;
 };

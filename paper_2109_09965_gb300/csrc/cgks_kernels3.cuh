@@ -1,0 +1,696 @@
+// Kernels of the 3-D hot path (included by cgks_device3.cu only).
+//
+// One solve; cells colour-major with reverse Cuthill-McKee order inside a
+// colour, faces sorted by their lower cell; structure-of-arrays
+// [component][n].  Flux kernels are templated on the flux type TF (double,
+// or float in the mixed path, where W, W_x, U and every accumulation into
+// them stay double).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "cgks_internal.h"
+#include "cgks_physics3.cuh"
+
+namespace cgks {
+namespace kern3 {
+
+namespace D3 = cgks::dev3;
+constexpr int NV = 5;
+constexpr int kCellBlock = 256;
+constexpr int kFaceBlock = 128;
+constexpr int kSweepLanes = 8;                     // lanes per cell (6 face slots)
+constexpr int kSweepBlock = 128;
+constexpr int kSweepCells = kSweepBlock / kSweepLanes;
+constexpr int kBadState = 1;
+
+template <typename T>
+__host__ __device__ constexpr bool is_f32() { return std::is_same<T, float>::value; }
+
+template <typename T>
+struct ParamsT {
+  T gamma, K, cfl_hi, cfl_lo, mu;
+  D3::KC<T> kc;
+  const int *bc_kind;          // [16]
+  const T *bc_uw;              // [16][3] wall velocity (global)
+  const T *bc_rho, *bc_u, *bc_p;  // [16], [16][3], [16] free stream (global)
+};
+
+template <typename T>
+struct MeshT {
+  int nc, nf;
+  const T *vol, *ivol, *ih, *hdt, *m2, *op;       // m2 [6][nc], op [27*9][nc]
+  const T *fe, *fS, *fjump, *fw, *fxi;            // fe [9][nf] (n, t1, t2), fw [4][nf], fxi [24][nf]
+  const T *sn, *shs;                              // [6*3][nc] outward normal per slot, [6][nc] S/2
+  const int *fng, *cface, *cnbr, *fc0, *fc1;
+};
+
+struct Ctl {
+  double dt_fixed;
+  int res_ctr, pad_;
+};
+
+__device__ __forceinline__ bool state_ok(double gamma, const double w[NV]) {
+  const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
+  return w[0] > 0.0 && p > 0.0 && isfinite(w[0]) && isfinite(p) && isfinite(w[1]) && isfinite(w[2]) &&
+         isfinite(w[3]);
+}
+
+__device__ __forceinline__ void block_sum2(double a, double b, double *out2) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { out2[0] = a; out2[1] = b; }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ D3::Frame<T> frame_of(const MeshT<T> &m, int f) {
+  D3::Frame<T> F;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) F.e[a][d] = m.fe[(3 * a + d) * m.nf + f];
+  return F;
+}
+
+// ------------------------------------------------------------------
+__global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, double dt_fixed) {
+  if (threadIdx.x == 0) { *dt_bits = 0x7ff0000000000000ull; ctl->dt_fixed = dt_fixed; }
+}
+
+// explicit step: min over cells of h / (|U| + c + 2 nu / h), h = 3|Omega| / sum S
+__global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
+                                                   unsigned long long *dt_bits) {
+  __shared__ double wmin[kCellBlock / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = INFINITY;
+  if (i < m.nc) {
+    const int n = m.nc;
+    const double rho = W[i], ir = 1.0 / rho;
+    const double u = W[n + i] * ir, v = W[2 * n + i] * ir, w = W[3 * n + i] * ir;
+    const double p = (P.gamma - 1.0) * (W[4 * n + i] - 0.5 * rho * (u * u + v * v + w * w));
+    const double hh = m.hdt[i];
+    const double speed = sqrt(u * u + v * v + w * w) + sqrt(P.gamma * p * ir) + 2.0 * (P.mu * ir) / hh;
+    d = hh / speed;
+  }
+  for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_down_sync(0xffffffffu, d, o));
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kCellBlock / 32; ++k) d = fmin(d, wmin[k]);
+    if (d < INFINITY) atomicMin(dt_bits, static_cast<unsigned long long>(__double_as_longlong(d)));
+  }
+}
+
+// wall ghost of a state and its gradient (global), through the face frame
+template <typename T>
+__device__ __forceinline__ void wall_ghost(const ParamsT<T> &P, int tag, const D3::Frame<T> &F, const T w[NV],
+                                           const T g[3][NV], T wg[NV], T gg[3][NV]) {
+  T wl[NV], dl[3][NV], wgl[NV], dgl[3][NV];
+  D3::rot_in(F, w, wl);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T t[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) t[v] = F.e[k][0] * g[0][v] + F.e[k][1] * g[1][v] + F.e[k][2] * g[2][v];
+    D3::rot_in(F, t, dl[k]);
+  }
+  if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+    D3::ghost_slip(wl, dl, wgl, dgl);
+  } else {
+    T uw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      uw[a] = F.e[a][0] * P.bc_uw[3 * tag] + F.e[a][1] * P.bc_uw[3 * tag + 1] + F.e[a][2] * P.bc_uw[3 * tag + 2];
+    D3::ghost_noslip(P.gamma, uw, wl, dl, wgl, dgl);
+  }
+  D3::rot_out(F, wgl, wg);
+  T gk[3][NV];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) D3::rot_out(F, dgl[k], gk[k]);
+  // global gradient: grad_d = sum_k e_k[d] (derivative along e_k)
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) gg[d][v] = F.e[0][d] * gk[0][v] + F.e[1][d] * gk[1][v] + F.e[2][d] * gk[2][v];
+}
+
+template <typename T>
+__device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, const D3::Frame<T> &F, const T wl[NV],
+                                               T wg[NV]) {
+  T ue[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    ue[a] = F.e[a][0] * P.bc_u[3 * tag] + F.e[a][1] * P.bc_u[3 * tag + 1] + F.e[a][2] * P.bc_u[3 * tag + 2];
+  D3::ghost_farfield(P.gamma, P.bc_rho[tag], ue, P.bc_p[tag], wl, wg);
+}
+
+// K1: compact quadratic per cell: coef[(q*5 + v)][n], 9 monomials
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc;
+  T wi[NV], gi[3][NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    wi[v] = W[v * n + i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gi[d][v] = Wx[(d * NV + v) * n + i];
+  }
+  T c[kNM3][NV];
+#pragma unroll
+  for (int q = 0; q < kNM3; ++q) {
+    const T o0 = m.op[((4 * kMaxFace3) * kNM3 + q) * n + i];
+    const T o1 = m.op[((4 * kMaxFace3 + 1) * kNM3 + q) * n + i];
+    const T o2 = m.op[((4 * kMaxFace3 + 2) * kNM3 + q) * n + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[q][v] = o0 * gi[0][v] + o1 * gi[1][v] + o2 * gi[2][v];
+  }
+  for (int s = 0; s < kMaxFace3; ++s) {
+    const int fs = m.cface[s * n + i];
+    if (fs == kNoFace) continue;
+    const int j = m.cnbr[s * n + i];
+    T b0[NV], b[3][NV];
+    if (j >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        b0[v] = W[v * n + j] - wi[v];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) b[d][v] = Wx[(d * NV + v) * n + j];
+      }
+    } else {
+      const int f = fs >= 0 ? fs : ~fs;
+      const int tag = -1 - m.fc1[f];
+      if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
+      const D3::Frame<T> F = frame_of(m, f);
+      T wg[NV];
+      wall_ghost(P, tag, F, wi, gi, wg, b);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) b0[v] = wg[v] - wi[v];
+    }
+#pragma unroll
+    for (int q = 0; q < kNM3; ++q) {
+      const T o0 = m.op[((4 * s) * kNM3 + q) * n + i], o1 = m.op[((4 * s + 1) * kNM3 + q) * n + i];
+      const T o2 = m.op[((4 * s + 2) * kNM3 + q) * n + i], o3 = m.op[((4 * s + 3) * kNM3 + q) * n + i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) c[q][v] += o0 * b0[v] + o1 * b[0][v] + o2 * b[1][v] + o3 * b[2][v];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kNM3; ++q)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) coef[(q * NV + v) * n + i] = c[q][v];
+}
+
+// value and gradient of cell i's quadratic at scaled offset x
+template <typename T>
+__device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restrict__ W, const T *__restrict__ coef,
+                                            int i, const T x[3], T val[NV], T g[3][NV]) {
+  const int n = m.nc;
+  const T ih = m.ih[i];
+  const T a = x[0], b = x[1], e = x[2];
+  const T p[6] = { a * a - m.m2[i], a * b - m.m2[n + i], a * e - m.m2[2 * n + i], b * b - m.m2[3 * n + i],
+                   b * e - m.m2[4 * n + i], e * e - m.m2[5 * n + i] };
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T c[kNM3];
+#pragma unroll
+    for (int q = 0; q < kNM3; ++q) c[q] = coef[(q * NV + v) * n + i];
+    val[v] = W[v * n + i] + c[0] * a + c[1] * b + c[2] * e + c[3] * p[0] + c[4] * p[1] + c[5] * p[2] + c[6] * p[3] +
+             c[7] * p[4] + c[8] * p[5];
+    g[0][v] = (c[0] + T(2) * c[3] * a + c[4] * b + c[5] * e) * ih;
+    g[1][v] = (c[1] + c[4] * a + T(2) * c[6] * b + c[7] * e) * ih;
+    g[2][v] = (c[2] + c[5] * a + c[7] * b + T(2) * c[8] * e) * ih;
+  }
+}
+
+// K2: smooth GKS flux and interface state at the Gauss points of every face:
+// out[(k*5 + v)][nf], k = 0 F0, 1 F1, 2 Wc, 3 Wt, weighted sums, global frame
+template <typename T>
+__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
+                                                     const T *__restrict__ coef, T *__restrict__ out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int nf = m.nf;
+  const int c0 = m.fc0[f], c1 = m.fc1[f], ng = m.fng[f];
+  const T ajump = m.fjump[f];
+  const D3::Frame<T> F = frame_of(m, f);
+  T acc[4][NV];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[k][v] = T(0);
+  int tag = 0;
+  bool farfield = false;
+  T wff[NV];
+  if (c1 < 0) {
+    tag = -1 - c1;
+    farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
+    if (farfield) {
+      T wm[NV], wl[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wm[v] = W[v * m.nc + c0];
+      D3::rot_in(F, wm, wl);
+      farfield_ghost(P, tag, F, wl, wff);
+    }
+  }
+  for (int k = 0; k < ng; ++k) {
+    T x0[3], wL[NV], gL[3][NV];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x0[d] = m.fxi[(3 * k + d) * nf + f];
+    recon_point(m, W, coef, c0, x0, wL, gL);
+    T wl[NV], dl[3][NV];
+    D3::rot_in(F, wL, wl);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T t[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) t[v] = F.e[a][0] * gL[0][v] + F.e[a][1] * gL[1][v] + F.e[a][2] * gL[2][v];
+      D3::rot_in(F, t, dl[a]);
+    }
+    T wr[NV], dr[3][NV];
+    if (c1 >= 0) {
+      T x1[3], wR[NV], gR[3][NV];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) x1[d] = m.fxi[(12 + 3 * k + d) * nf + f];
+      recon_point(m, W, coef, c1, x1, wR, gR);
+      D3::rot_in(F, wR, wr);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T t[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) t[v] = F.e[a][0] * gR[0][v] + F.e[a][1] * gR[1][v] + F.e[a][2] * gR[2][v];
+        D3::rot_in(F, t, dr[a]);
+      }
+    } else if (farfield) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wr[v] = wff[v];
+        dr[0][v] = dr[1][v] = dr[2][v] = T(0);
+      }
+    } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+      D3::ghost_slip(wl, dl, wr, dr);
+    } else {
+      T uw[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        uw[a] = F.e[a][0] * P.bc_uw[3 * tag] + F.e[a][1] * P.bc_uw[3 * tag + 1] + F.e[a][2] * P.bc_uw[3 * tag + 2];
+      D3::ghost_noslip(P.gamma, uw, wl, dl, wr, dr);
+    }
+    T F0[NV], F1[NV], Wc[NV], Wt[NV];
+    D3::gks_point_local(P.kc, P.mu, ajump, wl, wr, dl, dr, F0, F1, Wc, Wt);
+    const T wk = m.fw[k * nf + f];
+    T gq[NV];
+    D3::rot_out(F, F0, gq);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[0][v] += wk * gq[v];
+    D3::rot_out(F, F1, gq);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[1][v] += wk * gq[v];
+    D3::rot_out(F, Wc, gq);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[2][v] += wk * gq[v];
+    D3::rot_out(F, Wt, gq);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[3][v] += wk * gq[v];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[(k * NV + v) * nf + f] = acc[k][v];
+}
+
+enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
+
+__device__ __forceinline__ double dt_of(const Ctl *ctl, const unsigned long long *dt_bits, double cfl) {
+  if (ctl->dt_fixed > 0.0) return ctl->dt_fixed;
+  return cfl * __longlong_as_double(static_cast<long long>(*dt_bits));
+}
+
+// K3: per cell gather of the face sums in FP64 (see the 2-D k_update):
+//   R = -sum sgn S (a0 F0A + a1 F1(A, B));  W_out = W_base + dt/|Omega| R;
+//   Wx_out = 1/|Omega| sum sgn S n (WcA + b1 Wt)
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P, int mode,
+                                                       const double *__restrict__ Wbase, const TF *__restrict__ FA,
+                                                       const TF *__restrict__ FB, const Ctl *ctl,
+                                                       const unsigned long long *dt_bits, int *status,
+                                                       double *__restrict__ Wout, double *__restrict__ Wxout,
+                                                       double *__restrict__ partial, double *__restrict__ Rout,
+                                                       TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc, nf = m.nf;
+  double num = 0.0, den = 0.0;
+  if (i < n) {
+    const double dt = dt_of(ctl, dt_bits, P.cfl_hi);
+    double a0, a1, b1;
+    const TF *FW = FA;
+    switch (mode) {
+      case kS1O2: a0 = 1.0; a1 = 0.5 * dt; b1 = dt; break;
+      case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; b1 = 0.5 * dt; break;
+      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; FW = FB; break;
+      default: a0 = 1.0; a1 = 0.5 * dt; b1 = 0.0; break;
+    }
+    double R[NV] = { 0, 0, 0, 0, 0 }, g[3][NV] = { { 0 } };
+    for (int s = 0; s < kMaxFace3; ++s) {
+      const int fs = m.cface[s * n + i];
+      if (fs == kNoFace) continue;
+      const int f = fs >= 0 ? fs : ~fs;
+      const double sg = fs >= 0 ? 1.0 : -1.0;
+      const double S = m.fS[f];
+      const double nx = m.fe[f], ny = m.fe[nf + f], nz = m.fe[2 * nf + f];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double f1 = static_cast<double>(FA[(NV + v) * nf + f]);
+        if (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(FB[(NV + v) * nf + f]);
+        R[v] -= sg * S * (a0 * static_cast<double>(FA[v * nf + f]) + a1 * f1);
+        if (mode != kResidual) {
+          const double wp = static_cast<double>(FA[(2 * NV + v) * nf + f]) + b1 * static_cast<double>(FW[(3 * NV + v) * nf + f]);
+          g[0][v] += sg * S * nx * wp;
+          g[1][v] += sg * S * ny * wp;
+          g[2][v] += sg * S * nz * wp;
+        }
+      }
+    }
+    if (Rout)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Rout[v * n + i] = R[v];
+    if (mode != kResidual) {
+      const double iv = m.ivol[i];
+      double w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        w[v] = Wbase[v * n + i] + dt / m.vol[i] * R[v];
+        Wout[v * n + i] = w[v];
+        if (Wout_m) Wout_m[v * n + i] = static_cast<TF>(w[v]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          Wxout[(d * NV + v) * n + i] = g[d][v] * iv;
+          if (Wxout_m) Wxout_m[(d * NV + v) * n + i] = static_cast<TF>(g[d][v] * iv);
+        }
+      }
+      if (!state_ok(P.gamma, w)) atomicOr(status, kBadState);
+      num = fabs(w[0] - Wbase[i]);
+      den = Wbase[i];
+    }
+  }
+  if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+__global__ void k_res_final(const double *__restrict__ partial, int nblocks, Ctl *ctl, double *hist, int cap,
+                            double *last) {
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) { a += partial[2 * k]; b += partial[2 * k + 1]; }
+  __shared__ double tot[2];
+  block_sum2(a, b, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double r = tot[0] / tot[1];
+    last[0] = r; last[1] = tot[0]; last[2] = tot[1];
+    const int c = ctl->res_ctr;
+    if (hist && c < cap) hist[c] = r;
+    ctl->res_ctr = c + 1;
+  }
+}
+
+// ---------------------------- low-order level ----------------------------
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
+                                                        double *__restrict__ U, const TF *__restrict__ dU,
+                                                        TF *__restrict__ prim, TF *__restrict__ Um) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  TF w[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(dU[v * n + i]);
+    U[v * n + i] = u;
+    w[v] = static_cast<TF>(u);
+    if (Um) Um[v * n + i] = w[v];
+  }
+  const D3::Prim<TF> q = D3::prim_of(w, P.gamma, P.kc);
+  prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.w;
+  prim[4 * n + i] = q.p; prim[5 * n + i] = q.i2l; prim[6 * n + i] = q.sl; prim[7 * n + i] = q.isp;
+  prim[8 * n + i] = q.c; prim[9 * n + i] = q.ir;
+}
+
+template <typename T>
+__device__ __forceinline__ D3::Prim<T> load_prim(const T *__restrict__ prim, int n, int i) {
+  D3::Prim<T> q;
+  q.rho = prim[i]; q.u = prim[n + i]; q.v = prim[2 * n + i]; q.w = prim[3 * n + i]; q.p = prim[4 * n + i];
+  q.i2l = prim[5 * n + i]; q.sl = prim[6 * n + i]; q.isp = prim[7 * n + i]; q.c = prim[8 * n + i];
+  q.ir = prim[9 * n + i];
+  return q;
+}
+
+// ghost of a cell-mean state (zero gradients), global
+template <typename T>
+__device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, const D3::Frame<T> &F, const T w[NV],
+                                         T wg[NV]) {
+  T wl[NV], wgl[NV];
+  D3::rot_in(F, w, wl);
+  const int kind = P.bc_kind[tag];
+  if (kind == CGKS_BC_FARFIELD) {
+    farfield_ghost(P, tag, F, wl, wgl);
+  } else {
+    T z[3][NV], dz[3][NV];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) z[k][v] = T(0);
+    if (kind == CGKS_BC_SLIP) {
+      D3::ghost_slip(wl, z, wgl, dz);
+    } else {
+      T uw[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        uw[a] = F.e[a][0] * P.bc_uw[3 * tag] + F.e[a][1] * P.bc_uw[3 * tag + 1] + F.e[a][2] * P.bc_uw[3 * tag + 2];
+      D3::ghost_noslip(P.gamma, uw, wl, z, wgl, dz);
+    }
+  }
+  D3::rot_out(F, wgl, wg);
+}
+
+// KFVS flux, lambda_p = max of both sides, Euler flux cache (FP64 mode)
+template <typename T>
+__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
+                                                        const T *__restrict__ prim, T *__restrict__ Flo,
+                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int n = m.nc, nf = m.nf;
+  const int c0 = m.fc0[f], c1 = m.fc1[f];
+  const T S = m.fS[f];
+  const D3::Frame<T> F = frame_of(m, f);
+  D3::Prim<T> a = load_prim(prim, n, c0), b;
+  T ivb;
+  if (c1 >= 0) {
+    b = load_prim(prim, n, c1);
+    ivb = m.ivol[c1];
+  } else {
+    T w0[NV], wg[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w0[v] = U[v * n + c0];
+    lo_ghost(P, -1 - c1, F, w0, wg);
+    b = D3::prim_of(wg, P.gamma, P.kc);
+    ivb = m.ivol[c0];
+  }
+  T la3[3], lb3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    la3[k] = a.u * F.e[k][0] + a.v * F.e[k][1] + a.w * F.e[k][2];
+    lb3[k] = b.u * F.e[k][0] + b.v * F.e[k][1] + b.w * F.e[k][2];
+  }
+  T Fl[NV], Fg[NV];
+  D3::kfvs(P.K, a.rho, la3[0], la3[1], la3[2], a.i2l, a.sl, a.isp, b.rho, lb3[0], lb3[1], lb3[2], b.i2l, b.sl, b.isp,
+           Fl);
+  D3::rot_out(F, Fl, Fg);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Flo[v * nf + f] = Fg[v];
+  const T la = fabs(la3[0]) + a.c + T(2) * (P.mu * a.ir) * S * m.ivol[c0];
+  const T lb = fabs(lb3[0]) + b.c + T(2) * (P.mu * b.ir) * S * ivb;
+  lam[f] = la > lb ? la : lb;
+  if (E0) {
+    const T nx = F.e[0][0], ny = F.e[0][1], nz = F.e[0][2];
+    const T una = la3[0], unb = lb3[0];
+    E0[f] = a.rho * una;
+    E0[nf + f] = U[n + c0] * una + a.p * nx;
+    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
+    E0[3 * nf + f] = U[3 * n + c0] * una + a.p * nz;
+    E0[4 * nf + f] = (U[4 * n + c0] + a.p) * una;
+    if (c1 >= 0) {
+      E1[f] = b.rho * unb;
+      E1[nf + f] = U[n + c1] * unb + b.p * nx;
+      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
+      E1[3 * nf + f] = U[3 * n + c1] * unb + b.p * nz;
+      E1[4 * nf + f] = (U[4 * n + c1] + b.p) * unb;
+    }
+  }
+}
+
+// right-hand side R^k = R_lo + S (FP64 sums), 1/D_i (FP64), lambda per slot,
+// first colour pass (dU = R / D on colour 0, zero elsewhere)
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0_end,
+                                                       const TF *__restrict__ Flo, const TF *__restrict__ lam,
+                                                       const double *__restrict__ Rp0, double *__restrict__ Src,
+                                                       TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
+                                                       TF *__restrict__ lamS) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.nc) return;
+  const int n = m.nc, nf = m.nf;
+  double R[NV] = { 0, 0, 0, 0, 0 }, sum = 0.0;
+  for (int s = 0; s < kMaxFace3; ++s) {
+    const int fs = m.cface[s * n + i];
+    if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
+    const int f = fs >= 0 ? fs : ~fs;
+    const double sg = fs >= 0 ? 1.0 : -1.0;
+    const double S = m.fS[f];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
+    const TF l = lam[f];
+    lamS[s * n + i] = l;
+    sum += static_cast<double>(l) * S;
+  }
+  const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
+  invD[i] = static_cast<TF>(id);
+  const bool c0 = i < colour0_end;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double src;
+    if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
+    else src = Src[v * n + i];
+    const double r = R[v] + src;
+    Rk[v * n + i] = static_cast<TF>(r);
+    dU[v * n + i] = c0 ? static_cast<TF>(r * id) : TF(0);
+  }
+}
+
+// point relaxation of the cells [begin, begin + count) of one colour, Eq.
+// (implicit-local): 8 lanes per cell, one per face slot (6 used); the five
+// terms are summed over the lane group by shuffles, lane v writes
+// component v.
+template <typename T>
+__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count,
+                                                       const T *__restrict__ U, const T *__restrict__ prim,
+                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
+                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
+                                                       const T *__restrict__ E1, T *__restrict__ dU) {
+  const int s = threadIdx.x & (kSweepLanes - 1);
+  const int cl = threadIdx.x / kSweepLanes;
+  const int g = blockIdx.x * kSweepCells + cl;
+  const int i = g < count ? begin + g : -1;
+  const int n = m.nc, nf = m.nf;
+  const int j = (i >= 0 && s < kMaxFace3) ? m.cnbr[s * n + i] : -1;
+  T c[NV] = { T(0), T(0), T(0), T(0), T(0) };
+  if (j >= 0) {
+    const T nn[3] = { m.sn[(3 * s) * n + i], m.sn[(3 * s + 1) * n + i], m.sn[(3 * s + 2) * n + i] };
+    const T hS = m.shs[s * n + i], lp = lamS[s * n + i];
+    T uj[NV], du[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
+    if constexpr (is_f32<T>()) {
+      T dF[NV];
+      D3::euler_flux_delta(P.gamma, uj, prim[n + j], prim[2 * n + j], prim[3 * n + j], prim[4 * n + j], du, nn, dF);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) c[v] = hS * (dF[v] - lp * du[v]);
+    } else {
+      const int fs = m.cface[s * n + i];
+      const bool is0 = fs >= 0;
+      const int f = is0 ? fs : ~fs;
+      T up[NV], fa[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) up[v] = uj[v] + du[v];
+      D3::euler_flux(P.gamma, up, nn, fa);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 1);
+    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 2);
+    c[v] += __shfl_xor_sync(0xffffffffu, c[v], 4);
+  }
+  if (i >= 0 && s < NV) {
+    const T mine = s == 0 ? c[0] : s == 1 ? c[1] : s == 2 ? c[2] : s == 3 ? c[3] : c[4];
+    dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+  }
+}
+
+// W = W_p0 + (U - W_p0), density residual partials, state check
+template <typename TF>
+__global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT<double> P, double *__restrict__ W,
+                                                        const double *__restrict__ Wp0, const double *__restrict__ U,
+                                                        int *status, double *__restrict__ partial,
+                                                        TF *__restrict__ Wm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = m.nc;
+  double num = 0.0, den = 0.0;
+  if (i < n) {
+    double w[NV];
+    const double old = W[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double wp = Wp0[v * n + i];
+      w[v] = wp + (U[v * n + i] - wp);
+      W[v * n + i] = w[v];
+      if (Wm) Wm[v * n + i] = static_cast<TF>(w[v]);
+    }
+    if (!state_ok(P.gamma, w)) atomicOr(status, kBadState);
+    num = fabs(w[0] - old);
+    den = old;
+  }
+  block_sum2(num, den, &partial[2 * blockIdx.x]);
+}
+
+// caller AoS <-> internal SoA
+__global__ void k_gather_state(int n, const int *__restrict__ perm, const double *__restrict__ Wa,
+                               const double *__restrict__ Wxa, double *__restrict__ W, double *__restrict__ Wx,
+                               float *__restrict__ W32, float *__restrict__ Wx32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = perm[i];
+  for (int v = 0; v < NV; ++v) {
+    const double w = Wa[NV * c + v];
+    W[v * n + i] = w;
+    if (W32) W32[v * n + i] = static_cast<float>(w);
+  }
+  for (int q = 0; q < 3 * NV; ++q) {
+    const double g = Wxa ? Wxa[3 * NV * c + q] : 0.0;
+    Wx[q * n + i] = g;
+    if (Wx32) Wx32[q * n + i] = static_cast<float>(g);
+  }
+}
+__global__ void k_scatter_state(int n, const int *__restrict__ perm, const double *__restrict__ W,
+                                const double *__restrict__ Wx, double *__restrict__ Wa, double *__restrict__ Wxa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = perm[i];
+  if (Wa) for (int v = 0; v < NV; ++v) Wa[NV * c + v] = W[v * n + i];
+  if (Wxa) for (int q = 0; q < 3 * NV; ++q) Wxa[3 * NV * c + q] = Wx[q * n + i];
+}
+
+}  // namespace kern3
+}  // namespace cgks

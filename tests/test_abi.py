@@ -71,12 +71,51 @@ def test_bad_meshes_are_rejected(cg):
     with pytest.raises(cg.CgksError) as e:
         cg.Mesh(bad2)
     assert e.value.status == -3
-    # three-dimensional input is not implemented
+    # 2-D cell types handed in as a 3-D mesh are rejected; dim 4 is invalid
     m3 = MG.box(2, 2)
     m3.dim = 3
     with pytest.raises(cg.CgksError) as e:
         cg.Mesh(m3)
+    assert e.value.status == -3
+    m3.dim = 4
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(m3)
     assert e.value.status == -1
+    # 3-D: a negatively ordered tet, and a boundary face without a tag
+    b3 = MG.box3(2, 2, 2, cells="tet")
+    nodes = b3.cell_nodes.copy()
+    a = b3.cell_ptr[0]
+    nodes[a], nodes[a + 1] = nodes[a + 1], nodes[a]
+    b3.cell_nodes = nodes
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(b3)
+    assert e.value.status == -3
+    c3 = MG.box3(2, 2, 2, cells="hex")
+    c3.bface_ptr = c3.bface_ptr[:-1]
+    c3.bface_tag = c3.bface_tag[:-1]
+    c3.bface_nodes = c3.bface_nodes[:-4]
+    with pytest.raises(cg.CgksError) as e:
+        cg.Mesh(c3)
+    assert e.value.status == -3
+
+
+@pytest.mark.parametrize("mesh", [MG.box3(3, 2, 2, jitter=0.2, seed=1, cells="tet"),
+                                  MG.box3(2, 3, 2, jitter=0.2, seed=2, cells="prism"),
+                                  MG.box3(2, 2, 2, jitter=0.1, seed=3, cells="pyramid"),
+                                  MG.sphere(1, 3, 2, R_far=4.0)],
+                         ids=["tet", "prism", "pyramid", "sphere"])
+def test_host_mesh3_and_ordering_match_oracle(cg, mesh):
+    from oracle import oracle3 as O3
+    gm = cg.Mesh(mesh)
+    om = O3.OracleMesh3(mesh)
+    assert gm.dim == 3 and gm.nv == 5
+    assert gm.n_faces == om.n_faces
+    assert gm.n_colours == om.n_colours
+    rcm, col = gm.ordering()
+    orcm, ocol = om.ordering()
+    np.testing.assert_array_equal(rcm, orcm)
+    np.testing.assert_array_equal(col, ocol)
+    assert gm.device_bytes > 0
 
 
 def test_no_cpu_fallback_without_gpu(cg):
