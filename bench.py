@@ -193,10 +193,13 @@ def config_block(mesh, args):
             "l2": "flushed between timed steps (256 MiB write, outside the per-step events)"}
 
 
-def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm, hbm_src, with_e2e):
+def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm, hbm_src, with_e2e,
+            steps=None, work_model=None):
     """Device-timed K V-cycles (per-step events, L2 flushed between steps),
     a per-kernel timing pass, and optionally the end-to-end C-ABI run."""
     import torch
+    if steps is not None:
+        args = argparse.Namespace(**dict(vars(args), steps=steps))
     sp = dict(spec, precision=precision)
     solver = cgks.Solver(gm, sp)
     solver.set_state(W0)
@@ -232,7 +235,7 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     kt = solver.timing()
     solver.set_timing(False)
     total_k = sum(v[0] for v in kt.values())
-    wm = work_model(mesh, gm, sp, precision)
+    wm = (work_model or globals()["work_model"])(mesh, gm, sp, precision)
     roof, per_gbs = roofline(kt, wm, precision, hbm, hbm_src, args.steps)
     kernels = {k: dict({"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]},
                        **per_gbs.get(k, {}))
@@ -242,8 +245,8 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     if with_e2e:
         # end to end through the C ABI with pinned host buffers
         Wh = torch.from_numpy(W0.copy()).pin_memory()
-        Xh = torch.zeros((mesh.n_cells, 2, 4), dtype=torch.float64).pin_memory()
-        Wout = torch.zeros((mesh.n_cells, 4), dtype=torch.float64).pin_memory()
+        Xh = torch.zeros((mesh.n_cells, gm.dim, gm.nv), dtype=torch.float64).pin_memory()
+        Wout = torch.zeros((mesh.n_cells, gm.nv), dtype=torch.float64).pin_memory()
         resh = np.zeros(1)
         Wn, Xn = Wh.numpy(), Xh.numpy()
         torch.cuda.synchronize()
@@ -257,7 +260,8 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
         torch.cuda.synchronize()
         e2e_ms = dist_max(e0.elapsed_time(e1), world)
         out["e2e"] = {"value": world * mesh.n_cells * args.steps / (e2e_ms / 1000.0), "unit": "cell-updates/s",
-                      "h2d_bytes_per_step": 12 * 8 * mesh.n_cells, "d2h_bytes_per_step": 4 * 8 * mesh.n_cells + 8}
+                      "h2d_bytes_per_step": (gm.dim + 1) * gm.nv * 8 * mesh.n_cells,
+                      "d2h_bytes_per_step": gm.nv * 8 * mesh.n_cells + 8}
     solver.close()
     return out
 
@@ -356,6 +360,122 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
             "mesh_prep_s": t_prep}
 
 
+# ------------------------------------------------------------------ 3-D
+FACES3 = {2: [(0, 2, 1), (0, 1, 3), (1, 2, 3), (2, 0, 3)],
+          3: [(0, 2, 1), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5)],
+          4: [(0, 3, 2, 1), (0, 1, 4), (1, 2, 4), (2, 3, 4), (3, 0, 4)],
+          5: [(0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)]}
+# FP64 operations per Gauss point of the 3-D smooth flux: 2395 for the
+# kinetic flux (630 add, 1749 mul, 8 div, 4 sqrt, 2 exp, 2 erfc; counted by
+# instantiating the kernels' templated physics on a counting number type)
+# + ~825 for the two quadratic evaluations, frame rotations and sums.
+FLOPS_PER_GP3 = 3220
+# per interior neighbour of a relaxed cell: U + dU 5, Euler flux 31, bracket
+# and accumulation 30, weight 1; 5 multiplications by 1/D per cell
+SWEEP3_FLOPS_PER_NEIGHBOUR, SWEEP3_FLOPS_PER_CELL = 67, 5
+
+
+def topology3(mesh, gm):
+    """Interior faces per cell, tri / quad face counts and the neighbours
+    of every cell, by matching sorted face node sets (vectorised)."""
+    ct = mesh.cell_type
+    rows, owner, sizes = [], [], []
+    for t, faces in FACES3.items():
+        cells = np.nonzero(ct == t)[0]
+        if cells.size == 0:
+            continue
+        nodes = np.stack([mesh.cell_nodes[mesh.cell_ptr[cells] + k] for k in range(len(faces[0]) and max(max(f) for f in faces) + 1)], 1)
+        for f in faces:
+            k = np.full((cells.size, 4), -1, np.int64)
+            k[:, :len(f)] = np.sort(nodes[:, list(f)], axis=1)
+            rows.append(k); owner.append(cells); sizes.append(np.full(cells.size, len(f)))
+    K = np.concatenate(rows); own = np.concatenate(owner); sz = np.concatenate(sizes)
+    order = np.lexsort(K.T[::-1])
+    Ks = K[order]
+    same = np.all(Ks[1:] == Ks[:-1], axis=1)
+    pair = np.nonzero(same)[0]
+    a, b = own[order][pair], own[order][pair + 1]
+    nb = np.bincount(np.concatenate([a, b]), minlength=mesh.n_cells)
+    n_tri_uses, n_quad_uses = int((sz == 3).sum()), int((sz == 4).sum())
+    bsz = np.diff(mesh.bface_ptr)
+    T = (n_tri_uses + int((bsz == 3).sum())) // 2
+    Q = (n_quad_uses + int((bsz == 4).sum())) // 2
+    return nb, a, b, T, Q
+
+
+def work_model3(mesh, gm, spec, precision, _cache={}):
+    key = id(mesh)
+    if key not in _cache:
+        _cache.clear()
+        _cache[key] = topology3(mesh, gm)
+    nb, a, b, T, Q = _cache[key]
+    _, colour = gm.ordering()
+    colour = np.asarray(colour)
+    C = int(colour.max()) + 1
+    seq = []
+    for _ in range(spec["n_sweeps"]):
+        for c in list(range(C)) + list(range(C - 1, -1, -1)):
+            if not seq or seq[-1] != c:
+                seq.append(c)
+    seq = seq[1:]
+    ni = spec["n_implicit"]
+    w = 8 if precision == "fp64" else 4
+    by_c = {}
+    for c in range(C):
+        incol = colour == c
+        slots = int(nb[incol].sum())
+        # distinct neighbours of the colour's cells
+        na = b[incol[a]]
+        nbb = a[incol[b]]
+        uniq = np.unique(np.concatenate([na, nbb])).size
+        flops = SWEEP3_FLOPS_PER_NEIGHBOUR * slots + SWEEP3_FLOPS_PER_CELL * int(incol.sum())
+        own = int(incol.sum()) * 11 * w
+        per_slot = slots * (4 + 5 * w + (4 + 5 * w if precision == "fp64" else 0))
+        nbr = uniq * (10 * w + (4 * w if precision == "mixed" else 0))
+        by_c[c] = (flops, own + per_slot + nbr)
+    n, F = mesh.n_cells, gm.n_faces
+    gps = 3 * T + 4 * Q
+    return {"sweep_flops": ni * sum(by_c[c][0] for c in seq),
+            "face_flops": 2 * gps * FLOPS_PER_GP3,     # two evaluations per V-cycle
+            "bytes": {"k_sweep": ni * sum(by_c[c][1] for c in seq),
+                      "k_recon": 2 * n * ((20 + 243 + 45) * w + 48),
+                      "k_face": 2 * (n * 56 * w + F * (47 * w + 12)),
+                      "k_lo_face": ni * (n * 15 * w + F * (6 * w + 9 * w + 12 + (10 * w if precision == "fp64" else 0))),
+                      "k_lo_rhs": ni * (F * 7 * w + n * (24 + 5 * 8 + 16 * w + 6 * w)),
+                      "k_lo_cell": (ni + 1) * n * (10 * 8 + 5 * w + 10 * w),
+                      "k_prolong": n * 20 * 8},
+            "gauss_points": gps, "colours": C, "sweep_launches": ni * len(seq)}
+
+
+def sphere_case(level, n_prism, n_tet, h0, ma, re):
+    from paper_2109_09965_gb300 import meshgen
+    mesh = meshgen.sphere(level, n_prism, n_tet, h0=h0)
+    spec = dict(gamma=GAMMA, mu=ma * 1.0 / re, cfl_hi=0.4, cfl_lo=1000.0, n_implicit=6, n_sweeps=2,
+                time_scheme="S1O2", bcs=[dict(kind="noslip"),
+                                         dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0), p=1.0 / GAMMA)])
+    W = np.zeros((mesh.n_cells, 5))
+    W[:, 0] = 1.0
+    W[:, 1] = ma
+    W[:, 4] = 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * ma * ma
+    return mesh, spec, W
+
+
+def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_prism, n_tet, h0, ma, re, steps,
+                 note):
+    t0 = time.perf_counter()
+    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, ma, re)
+    gm = cgks.Mesh(mesh)
+    prep = time.perf_counter() - t0
+    out = {"workload": note, "n_cells": mesh.n_cells, "n_faces": gm.n_faces, "mesh_prep_s": prep}
+    for prec in ("fp64", "mixed"):
+        m = measure(cgks, gm, mesh, spec, W0, args, prec, world, local, flush, hbm, hbm_src, with_e2e=False,
+                    steps=steps, work_model=work_model3)
+        out[prec] = {"value": m["value"], "unit": "cell-updates/s", "ms_per_step": m["ms"] / steps, "steps": steps,
+                     "roofline": m["roof"], "kernels": m["kernels"], "gpu_launches": m["launches"],
+                     "residual_last": m["res"], "clocks": m["clocks"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,6 +487,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant of the line")
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D sphere workloads")
+    ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-1e-8 comparison")
     ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
                     help="serving run: a small sample in the line (default), or the full 256-request mix")
     args = ap.parse_args()
@@ -405,6 +527,19 @@ def main():
             "kernels": m["kernels"], "residual_last": m["res"]}
     if variants:
         line["variants"] = variants
+    if not args.no_3d:
+        line["workloads_3d"] = {
+            "sphere512k": sphere_bench(
+                cgks, args, world, local, flush, hbm, hbm_src, "sphere512k", 4, 40, 20, 5e-3, 0.2, 118, 30,
+                "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism layers "
+                "(growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: 512,000 cells; first "
+                "layer 5e-3 D instead of 1e-3 D (the V-cycle diverges on the thinner layer)"),
+            "sphere3M": sphere_bench(
+                cgks, args, world, local, flush, hbm, hbm_src, "sphere3M", 5, 60, 30, 1e-3, 0.2, 1000, 10,
+                "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
+                "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
+                "(throughput only: the Ma 1.5 case needs the limiter, not built)"),
+        }
     if args.serving == "sample":
         line["serving"] = serving(cgks, 24, 2000, 20000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
     elif args.serving == "full":
@@ -412,7 +547,21 @@ def main():
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, spec, W0)
     if args.converge:
-        line["convergence"] = converge(cgks, mesh, spec, W0)
+        line["convergence_57k"] = converge(cgks, mesh, spec, W0)
+    if not args.no_convergence:
+        # time to a 1e-8 drop on a cylinder small enough for both methods to
+        # get there within the bench: 64 x (8 quad + 24 triangle layers)
+        from paper_2109_09965_gb300 import meshgen
+        cm = meshgen.cylinder(64, 8, 24)
+        cW = np.zeros((cm.n_cells, 4))
+        cW[:, 0] = 1.0
+        cW[:, 1] = MA
+        cW[:, 3] = 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * MA * MA
+        conv = converge(cgks, cm, spec, cW, max_cycles=12000, max_steps=300000)
+        conv["workload"] = (f"inviscid cylinder Ma {MA}, AoA 0, hybrid O-mesh 64 x (8 quad + 24 split-triangle "
+                            f"layers) to 20 radii: {cm.n_cells} cells, FP64; Res drop 1e-8 relative to the first "
+                            "iteration; p-multigrid V-cycles vs explicit S2O4 steps, same GPU")
+        line["convergence"] = conv
     print(json.dumps(line), flush=True)
 
 
@@ -509,6 +658,12 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
         per[k] = {"gbs": wm["bytes"][k] / s / 1e9, "frac_hbm": wm["bytes"][k] / s / 1e9 / hbm}
     top = max(kt, key=lambda k: kt[k][0])
     s_top = kt[top][0] / 1000.0 / steps
+    if top == "k_face" and precision == "fp64" and "face_flops" in wm:
+        ach = wm["face_flops"] / s_top / 1e12
+        return ({"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                 "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
+                                "1.197 TFLOP/s)"}, per)
     if top == "k_sweep" and precision == "fp64":
         ach = wm["sweep_flops"] / s_top / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -518,7 +673,7 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
     else:
         ach = wm["bytes"].get(top, 0.0) / s_top / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": SWEEP_TRAFFIC_PER_LAUNCH.get(precision) if top == "k_sweep" else None,
+                "traffic": wm.get("sweep_traffic", SWEEP_TRAFFIC_PER_LAUNCH.get(precision)) if top == "k_sweep" else None,
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     return roof, per
 
@@ -535,7 +690,7 @@ def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=100000
         torch.cuda.synchronize()
         t = time.perf_counter()
         done, first, its, hist = False, None, 0, []
-        chunk = 100 if label == "pmg" else 1000
+        chunk = 100 if label == "pmg" else 2000
         while its < cap and not done:
             r = getattr(s, fn)(chunk)
             if first is None:
