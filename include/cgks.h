@@ -91,6 +91,9 @@ typedef struct {
   int32_t precision;     /* CGKS_FP64 or CGKS_MIXED */
   int32_t n_bc;          /* entries used in bc[] (boundary tags index it) */
   int32_t use_graph;     /* 1: capture each V-cycle in a CUDA graph */
+  int32_t low_order_fused; /* 1: the low-order level as one persistent cooperative launch (2-D);
+                            0 (default): one graph-replayed kernel per phase, faster on GB300 */
+  int32_t pad_;
   cgks_bc bc[CGKS_MAX_BC];
   void *stream;          /* cudaStream_t for all device work (NULL = default) */
   cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */
@@ -211,7 +214,7 @@ typedef struct {
   int32_t max_active;    /* solves per batch */
   int32_t max_cycles;    /* retire unconverged solves after this many cycles */
   int32_t use_graph;
-  int32_t pad_;
+  int32_t low_order_fused; /* 1: persistent cooperative low-order level */
   void *stream;          /* cudaStream_t (NULL = default) */
   cgks_alloc_fn alloc;
   cgks_free_fn free;

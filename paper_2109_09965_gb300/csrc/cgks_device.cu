@@ -22,6 +22,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_kernels.cuh"
+#include "cgks_persistent.cuh"
 #include "cgks_runtime.h"
 
 using namespace cgks;
@@ -45,7 +46,7 @@ struct Bufs {
 // batch-wide settings (every solve of a batch shares them)
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
-  int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1;
+  int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 1;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -110,7 +111,14 @@ struct Batch {
   cudaGraphExec_t g_cycle = nullptr, g_step = nullptr;
   Timer *timer = nullptr;              // owned by the caller
   long long launches = 0;
+  // persistent low-order level: barrier, per-colour ranges, grid size
+  GridBarrier *gb = nullptr;
+  int *r_start = nullptr, *r_begin = nullptr, *r_pre = nullptr;
+  int lo_grid = 0;
+  bool lo_fused_ok = false;
 };
+
+constexpr int kMaxColFused = 16;     // colours the fused path handles
 
 void *dev_alloc(const Shared &sh, size_t bytes) {
   if (sh.alloc) return sh.alloc(bytes, sh.alloc_ctx);
@@ -209,7 +217,45 @@ void enqueue_hi_step(Batch *b, double *Wout, TF *Wout_m, bool want_res) {
 // implicit step: cell primitives (and U += dU), KFVS faces, right-hand side
 // with the first colour pass, then the remaining colour passes.
 template <typename TF>
+void enqueue_lo_fused(Batch *b) {
+  Bufs<TF> &B = bufs<TF>(b);
+  LoArgs<TF> a;
+  std::memset(&a, 0, sizeof(a));
+  a.dm = b->dm; a.fm = fmesh<TF>(b); a.dp = b->dp; a.fp = fparams<TF>(b);
+  a.n_implicit = b->sh.n_implicit;
+  a.colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
+  a.n_seq = static_cast<int>(b->sweep_seq.size());
+  a.n_cells = static_cast<int>(b->N);
+  a.n_faces = static_cast<int>(b->F);
+  for (int q = 0; q < a.n_seq; ++q) a.seq[q] = b->sweep_seq[q];
+  a.cr.rstart = b->r_start; a.cr.rbegin = b->r_begin; a.cr.rpre = b->r_pre;
+  a.Wp0 = b->Wn; a.Rp0 = b->Rp0; a.U = b->U; a.Src = b->Src;
+  a.dU = B.dU; a.prim = B.prim; a.Um = mirror<TF>(B.U); a.Flo = B.Flo; a.lam = B.lam; a.E0 = B.E0; a.E1 = B.E1;
+  a.Rk = B.Rk; a.invD = B.invD; a.lamS = B.lamS;
+  a.gb = b->gb; a.err = b->status;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->lo_grid);
+  cfg.blockDim = dim3(kPersistBlock);
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool t = b->timer && b->timer->on;
+  if (t) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, b->stream); }
+  cudaLaunchKernelEx(&cfg, k_lo_solve<TF>, a);
+  if (t) { cudaEventRecord(e1, b->stream); b->timer->ev.push_back({ KI_LOSOLVE, { e0, e1 } }); }
+  b->launches++;
+}
+
+template <typename TF>
 void enqueue_lo_solve(Batch *b) {
+  if (b->lo_fused_ok) {
+    enqueue_lo_fused<TF>(b);
+    return;
+  }
   Bufs<TF> &B = bufs<TF>(b);
   const dim3 gc(nblk(b->N, kCellBlock)), gf(nblk(b->F, kCellBlock)), blk(kCellBlock);
   const int colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
@@ -286,7 +332,9 @@ long long count_launches(const Batch *b, bool cycle) {
   long long hi = per_eval + 1 + (b->sh.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
   long long dt = 2;
   if (!cycle) return dt + hi + 1;
-  long long lo = b->sh.n_implicit * (3 + static_cast<long long>(b->sweep_seq.size())) + (b->sh.n_implicit > 0 ? 1 : 0);
+  long long lo = b->lo_fused_ok ? 1
+                               : b->sh.n_implicit * (3 + static_cast<long long>(b->sweep_seq.size())) +
+                                     (b->sh.n_implicit > 0 ? 1 : 0);
   return dt + hi + per_eval + 1 + lo + 2;
 }
 
@@ -391,6 +439,9 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   PV(reinterpret_cast<void **>(&b->ctl), sizeof(Ctl));
   PV(reinterpret_cast<void **>(&b->dt_bits), sizeof(unsigned long long) * S);
   PI(&b->status, S);
+  PV(reinterpret_cast<void **>(&b->gb), sizeof(GridBarrier));
+  PI(&b->r_start, kMaxColFused + 1); PI(&b->r_begin, kMaxColFused * static_cast<int64_t>(S));
+  PI(&b->r_pre, kMaxColFused * static_cast<int64_t>(S) + kMaxColFused);
   if (!mixed) {
     Bufs<double> &X = b->bd;
     P8(&X.coef, 20 * N); P8(&X.FA, 16 * F); P8(&X.FB, 16 * F);
@@ -499,7 +550,8 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
             cudaMemsetAsync(b->last, 0, sizeof(double) * 4, st) == cudaSuccess &&
             cudaMemsetAsync(b->Rp0, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess &&
             cudaMemsetAsync(d.fsid, 0xff, sizeof(int) * Fcap, st) == cudaSuccess &&
-            cudaMemsetAsync(d.bckind, 0, sizeof(int) * kTagsPerSolve * S, st) == cudaSuccess;
+            cudaMemsetAsync(d.bckind, 0, sizeof(int) * kTagsPerSolve * S, st) == cudaSuccess &&
+            cudaMemsetAsync(b->gb, 0, sizeof(GridBarrier), st) == cudaSuccess;
   if (ok) {
     if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * Ncap, st) == cudaSuccess;
     else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess;
@@ -511,6 +563,17 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   if (!ok) { destroy_batch(B.release()); return CGKS_ECUDA; }
   int rc = ensure_hist(b, kHistDefault);
   if (rc) { destroy_batch(B.release()); return rc; }
+  // grid of the persistent low-order launch: every block resident at once
+  {
+    int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (b->mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lo_solve<float>, kPersistBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lo_solve<double>, kPersistBlock, 0);
+    b->lo_grid = coop ? per_sm * nsm : 0;
+    cudaGetLastError();
+  }
   *out = B.release();
   return CGKS_OK;
 }
@@ -695,6 +758,33 @@ int finalize_batch(Batch *b) {
   }
   if (need_list && !list.empty())
     CK(cudaMemcpyAsync(b->list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream));
+  // the fused low-order launch: per-colour ranges of every active solve
+  b->lo_fused_ok = false;
+  if (b->sh.lo_fused && b->lo_grid > 0 && C <= kMaxColFused && b->sweep_seq.size() <= 48 && N > 0) {
+    std::vector<int> rstart(kMaxColFused + 1, 0), rbegin, rpre;
+    for (int c = 0; c < C; ++c) {
+      rstart[c] = static_cast<int>(rbegin.size());
+      int acc = 0;
+      for (int s : order) {
+        const Member &M = b->mem[s];
+        const HostMesh &hm = *M.mesh;
+        if (c >= hm.n_colours) continue;
+        const int beg = static_cast<int>(M.cell_off) + hm.colour_start[c];
+        const int cnt = hm.colour_start[c + 1] - hm.colour_start[c];
+        if (cnt == 0) continue;
+        rbegin.push_back(beg);
+        rpre.push_back(acc);
+        acc += cnt;
+      }
+      rpre.push_back(acc);
+    }
+    for (int c = C; c <= kMaxColFused; ++c) rstart[c] = static_cast<int>(rbegin.size());
+    if (rbegin.empty()) rbegin.push_back(0);
+    CK(cudaMemcpyAsync(b->r_start, rstart.data(), sizeof(int) * rstart.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->r_begin, rbegin.data(), sizeof(int) * rbegin.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->r_pre, rpre.data(), sizeof(int) * rpre.size(), cudaMemcpyHostToDevice, b->stream));
+    b->lo_fused_ok = true;
+  }
   CK(cudaStreamSynchronize(b->stream));
   drop_graphs(b);
   return CGKS_OK;
@@ -758,7 +848,7 @@ Shared shared_from(const cgks_params *p) {
   Shared sh;
   sh.gamma = p->gamma; sh.cfl_hi = p->cfl_hi; sh.cfl_lo = p->cfl_lo;
   sh.n_implicit = p->n_implicit; sh.n_sweeps = p->n_sweeps; sh.time_scheme = p->time_scheme;
-  sh.precision = p->precision; sh.use_graph = p->use_graph;
+  sh.precision = p->precision; sh.use_graph = p->use_graph; sh.lo_fused = p->low_order_fused;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -876,6 +966,7 @@ int solver_status(cgks_solver *s) {
     CK(cudaStreamSynchronize(s->stream));
   }
   s->status_cache = st;
+  if (st & kBarrierTimeout) return CGKS_ETIMEOUT;
   return st ? CGKS_EDIVERGED : CGKS_OK;
 }
 
@@ -901,6 +992,7 @@ void cgks_default_params(cgks_params *p) {
   p->time_scheme = CGKS_S1O2;
   p->precision = CGKS_FP64;
   p->use_graph = 1;
+  p->low_order_fused = 0;
 }
 
 const char *cgks_strerror(int st) {
@@ -1246,6 +1338,7 @@ void cgks_server_default_opts(cgks_server_opts *o) {
   o->max_active = 64;
   o->max_cycles = 20000;
   o->use_graph = 1;
+  o->low_order_fused = 0;
 }
 
 // Faces per cell the batch capacity provides for (2-D: triangles 1.5,
@@ -1265,6 +1358,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   if (!v) return CGKS_ENOMEM;
   v->sh.cfl_hi = o->cfl_hi; v->sh.cfl_lo = o->cfl_lo; v->sh.n_implicit = o->n_implicit; v->sh.n_sweeps = o->n_sweeps;
   v->sh.time_scheme = o->time_scheme; v->sh.precision = o->precision; v->sh.use_graph = o->use_graph;
+  v->sh.lo_fused = o->low_order_fused;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;

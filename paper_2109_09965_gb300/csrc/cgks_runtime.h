@@ -12,10 +12,11 @@ namespace cgks {
 
 // kernel ids for the per-kernel timers
 enum KernelId { KI_DT = 0, KI_RECON, KI_FACE, KI_UPDATE, KI_RESFIN, KI_LOFACE, KI_LORHS, KI_SWEEP, KI_LOCELL,
-                KI_PROLONG, KI_COUNT };
+                KI_PROLONG, KI_LOSOLVE, KI_COUNT };
 inline const char *kernel_name(int k) {
   static const char *names[KI_COUNT] = { "k_dt", "k_recon", "k_face", "k_update", "k_res_final", "k_lo_face",
-                                         "k_lo_rhs", "k_sweep", "k_lo_cell", "k_prolong" };
+                                         "k_lo_rhs", "k_sweep", "k_lo_cell", "k_prolong",
+                                         "k_lo_solve" };
   return names[k];
 }
 
