@@ -200,10 +200,19 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     import torch
     if steps is not None:
         args = argparse.Namespace(**dict(vars(args), steps=steps))
-    sp = dict(spec, precision=precision)
+    sp = dict(spec, precision=precision, autotune=0 if args.no_autotune else 1)
     solver = cgks.Solver(gm, sp)
     solver.set_state(W0)
     stream = torch.cuda.current_stream()
+    # the autotuner's cycles (ordinary V-cycles, each kernel trying its
+    # launch shapes in turn) run before the warm-up, outside the timed region
+    tune_cycles = 0
+    while not all(v["done"] for v in solver.tuning().values()) and tune_cycles < 64:
+        solver.pmg_cycle(1, record=False)
+        tune_cycles += 1
+    tuning = {k: {"shape": dict(zip(("block", "per_thread", "min_blocks"), cgks.tune_shape(v["shape"]))),
+                  "ms_by_shape": [round(x, 5) for x in v["ms"]]}
+              for k, v in solver.tuning().items()}
     for _ in range(args.warmup):
         solver.pmg_cycle(1, record=False)
     torch.cuda.synchronize()
@@ -241,7 +250,7 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
                        **per_gbs.get(k, {}))
                for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0}
     out = {"value": value, "ms": ms, "launches": int(launches), "clocks": clk.summary(), "roof": roof,
-           "kernels": kernels, "res": res}
+           "kernels": kernels, "res": res, "tuning": dict(tuning, cycles=tune_cycles)}
     if with_e2e:
         # end to end through the C ABI with pinned host buffers
         Wh = torch.from_numpy(W0.copy()).pin_memory()
@@ -347,6 +356,7 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
         cells_done += st["n_cells"] * st["cycles"]
         lat.append(st["t_done"] - st["t_submit"])
     lat = np.asarray(lat)
+    tuned = {k: v["shape"] for k, v in srv.tuning().items()}
     srv.close()
     return {"requests": n_req, "cells_range": [int(min(r["mesh"].n_cells for r in reqs)),
                                                int(max(r["mesh"].n_cells for r in reqs))],
@@ -357,7 +367,7 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
             "peak_active": int(peak_active), "budget_bytes": int(budget_gb * 2**30), "precision": precision,
             "criterion": f"cylinders: Res drop {drop:g} relative to the first cycle (cap {max_cycles}); "
                          f"cavities: {cavity_cycles} cycles",
-            "mesh_prep_s": t_prep}
+            "mesh_prep_s": t_prep, "tuned_shapes": tuned}
 
 
 # ------------------------------------------------------------------ 3-D
@@ -472,7 +482,7 @@ def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_p
                     steps=steps, work_model=work_model3)
         out[prec] = {"value": m["value"], "unit": "cell-updates/s", "ms_per_step": m["ms"] / steps, "steps": steps,
                      "roofline": m["roof"], "kernels": m["kernels"], "gpu_launches": m["launches"],
-                     "residual_last": m["res"], "clocks": m["clocks"]}
+                     "residual_last": m["res"], "clocks": m["clocks"], "tuning": m["tuning"]}
     return out
 
 
@@ -488,6 +498,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant of the line")
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D sphere workloads")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed default launch shapes")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-1e-8 comparison")
     ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
                     help="serving run: a small sample in the line (default), or the full 256-request mix")
@@ -513,7 +524,7 @@ def main():
         mv = measure(cgks, gm, mesh, spec, W0, args, "mixed", world, local, flush, hbm, hbm_src, with_e2e=False)
         variants["mixed"] = {"value": mv["value"], "ms_per_step": mv["ms"] / args.steps, "dtype": "f32+f64",
                              "gpu_launches": mv["launches"], "roofline": mv["roof"], "kernels": mv["kernels"],
-                             "clocks": mv["clocks"],
+                             "clocks": mv["clocks"], "tuning": mv["tuning"],
                              "note": "FP32 reconstruction, fluxes and sweeps; FP64 accumulation, diagonal "
                                      "inversion and residual norms; same workload and step"}
     if rank != 0:
@@ -524,7 +535,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": config_block(mesh, args), "e2e": m["e2e"],
             "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roof"],
-            "kernels": m["kernels"], "residual_last": m["res"]}
+            "kernels": m["kernels"], "residual_last": m["res"], "tuning": m["tuning"]}
     if variants:
         line["variants"] = variants
     if not args.no_3d:

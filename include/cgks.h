@@ -93,7 +93,8 @@ typedef struct {
   int32_t use_graph;     /* 1: capture each V-cycle in a CUDA graph */
   int32_t low_order_fused; /* 1: the low-order level as one persistent cooperative launch (2-D);
                             0 (default): one graph-replayed kernel per phase, faster on GB300 */
-  int32_t pad_;
+  int32_t autotune;      /* 1 (default): the block-size autotuner picks the launch shapes (see
+                            cgks_get_tuning); 0: the fixed default shapes */
   cgks_bc bc[CGKS_MAX_BC];
   void *stream;          /* cudaStream_t for all device work (NULL = default) */
   cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */
@@ -112,7 +113,8 @@ typedef struct cgks_mesh cgks_mesh;
 typedef struct cgks_solver cgks_solver;
 
 /* Fill p with the defaults above (gamma 1.4, Euler, CFL 0.4 / 1000,
- * 6 implicit steps, 2 sweeps, S1O2, FP64, graphs on, no boundaries). */
+ * 6 implicit steps, 2 sweeps, S1O2, FP64, graphs on, autotune on,
+ * per-phase low-order launches, no boundaries). */
 void cgks_default_params(cgks_params *p);
 
 /* Build a mesh from nodes, cells and tagged boundary faces (the finite-
@@ -215,6 +217,8 @@ typedef struct {
   int32_t max_cycles;    /* retire unconverged solves after this many cycles */
   int32_t use_graph;
   int32_t low_order_fused; /* 1: persistent cooperative low-order level */
+  int32_t autotune;      /* 1 (default): autotuned launch shapes for the batch */
+  int32_t pad_;
   void *stream;          /* cudaStream_t (NULL = default) */
   cgks_alloc_fn alloc;
   cgks_free_fn free;
@@ -233,7 +237,7 @@ typedef struct {
 } cgks_req_status;
 
 /* Fill opts with defaults (FP64, S1O2, CFL 0.4 / 1000, 6 x 2, 64 active,
- * 20000 cycles, graphs on). */
+ * 20000 cycles, graphs on, autotune on). */
 void cgks_server_default_opts(cgks_server_opts *o);
 int cgks_server_create(size_t hbm_budget, const cgks_server_opts *opts, cgks_server **out);
 /* Queue a request.  The mesh and W0 ([n_cells*4], caller order, host) are
@@ -272,6 +276,37 @@ int cgks_reset_timing(cgks_solver *s);
  * or per explicit step (cycle=0). */
 int64_t cgks_launch_count(const cgks_solver *s);
 int cgks_launches_per_call(const cgks_solver *s, int cycle);
+
+/* ---- launch-shape autotuner (no counterpart in the paper) ----
+ * Four kernels take a launch shape: the compact reconstruction, the
+ * gas-kinetic face flux, the low-order (KFVS) face flux and the colour
+ * sweep, in that order (CGKS_TUNE_KERNELS).  A shape (CGKS_TUNE_SHAPES of
+ * them, index 0..4) is a block size, a number of items (cells or faces;
+ * cells per lane group for the sweep) per thread and a minimum number of
+ * resident blocks per SM (a register cap); cgks_tune_shape describes one.
+ * Each item is computed by the same arithmetic under every shape, so the
+ * shape never changes a result, only the time.
+ * With autotune on, the first 3 x CGKS_TUNE_SHAPES V-cycles (or explicit
+ * steps) that launch a kernel run without CUDA graphs, each with the next
+ * shape in turn for that kernel; the first round only warms up (module
+ * loading), the other rounds time every launch with CUDA events.  Then
+ * each kernel keeps the shape of least mean launch time and the graphs are
+ * captured with it.  The tuning cycles are ordinary cycles: the state
+ * advances exactly as with fixed shapes. */
+#define CGKS_TUNE_KERNELS 4
+#define CGKS_TUNE_SHAPES 5
+typedef struct {
+  int32_t shape[CGKS_TUNE_KERNELS];  /* the shape in use (while tuning: the next one to try) */
+  int32_t done[CGKS_TUNE_KERNELS];   /* 1 once the kernel's shape is final */
+  double ms[CGKS_TUNE_KERNELS][CGKS_TUNE_SHAPES];  /* mean timed launch per shape (ms); 0 = not timed */
+} cgks_tuning;
+/* block size, items per thread, minimum resident blocks per SM of shape
+ * index 0 .. CGKS_TUNE_SHAPES-1 (CGKS_EINVAL otherwise) */
+int cgks_tune_shape(int32_t shape, int32_t *block, int32_t *per_thread, int32_t *min_blocks);
+int cgks_get_tuning(cgks_solver *s, cgks_tuning *t);
+/* Fix the shapes (each 0 .. CGKS_TUNE_SHAPES-1) and end any tuning. */
+int cgks_set_tuning(cgks_solver *s, const int32_t shape[CGKS_TUNE_KERNELS]);
+int cgks_server_get_tuning(cgks_server *srv, cgks_tuning *t);
 
 /* ---- allocation-free residual (the paper has no counterpart) ----
  * Some callers cannot allocate device memory when they call into the

@@ -48,8 +48,23 @@ class CgksParams(C.Structure):
                 ("cfl_hi", C.c_double), ("cfl_lo", C.c_double),
                 ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32), ("time_scheme", C.c_int32),
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
-                ("low_order_fused", C.c_int32), ("pad_", C.c_int32), ("bc", CgksBC * MAX_BC), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("bc", CgksBC * MAX_BC),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+TUNE_KERNELS = 4
+TUNE_SHAPES = 5
+TUNE_NAMES = ("k_recon", "k_face", "k_lo_face", "k_sweep")
+
+
+class CgksTuning(C.Structure):
+    _fields_ = [("shape", C.c_int32 * TUNE_KERNELS), ("done", C.c_int32 * TUNE_KERNELS),
+                ("ms", (C.c_double * TUNE_SHAPES) * TUNE_KERNELS)]
+
+
+def _tuning_dict(t: CgksTuning) -> dict:
+    return {name: dict(shape=int(t.shape[k]), done=bool(t.done[k]), ms=[float(x) for x in t.ms[k]])
+            for k, name in enumerate(TUNE_NAMES)}
 
 
 class CgksMeshInfo(C.Structure):
@@ -88,6 +103,9 @@ SIGNATURES = {
     "cgks_reset_timing": (C.c_int, [C.c_void_p]),
     "cgks_launch_count": (C.c_int64, [C.c_void_p]),
     "cgks_launches_per_call": (C.c_int, [C.c_void_p, C.c_int]),
+    "cgks_tune_shape": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "cgks_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(CgksTuning)]),
+    "cgks_set_tuning": (C.c_int, [C.c_void_p, _i32p]),
     "cgks_density_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
@@ -171,7 +189,7 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     for key in ("gamma", "mu", "alpha", "cfl_hi", "cfl_lo"):
         if key in spec:
             setattr(P, key, float(spec[key]))
-    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused"):
+    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune"):
         if key in spec:
             setattr(P, key, int(spec[key]))
     P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
@@ -316,14 +334,35 @@ class Solver:
     def launches_per_call(self, cycle: bool) -> int:
         return int(lib().cgks_launches_per_call(self._h, int(bool(cycle))))
 
+    def tuning(self) -> dict:
+        """Per tunable kernel: shape index in use, whether it is final, and
+        the mean timed launch (ms) of every shape tried."""
+        t = CgksTuning()
+        _check(lib().cgks_get_tuning(self._h, C.byref(t)), "cgks_get_tuning")
+        return _tuning_dict(t)
+
+    def set_tuning(self, shapes):
+        """Fix the four launch shapes (indices 0 .. TUNE_SHAPES-1)."""
+        a = np.ascontiguousarray(shapes, np.int32)
+        if a.shape != (TUNE_KERNELS,):
+            raise ValueError("one shape per tunable kernel")
+        _check(lib().cgks_set_tuning(self._h, a), "cgks_set_tuning")
+
+
+def tune_shape(shape: int):
+    """(block size, items per thread, minimum resident blocks per SM)."""
+    b, i, m = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    _check(lib().cgks_tune_shape(int(shape), C.byref(b), C.byref(i), C.byref(m)), "cgks_tune_shape")
+    return b.value, i.value, m.value
+
 
 # ---------------------------------------------------------------- serving
 class CgksServerOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("time_scheme", C.c_int32), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32),
                 ("max_active", C.c_int32), ("max_cycles", C.c_int32), ("use_graph", C.c_int32),
-                ("low_order_fused", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("pad_", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class CgksReqStatus(C.Structure):
@@ -345,6 +384,7 @@ SIGNATURES.update({
                                    C.POINTER(C.c_int32)]),
     "cgks_server_footprint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "cgks_server_destroy": (C.c_int, [C.c_void_p]),
+    "cgks_server_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(CgksTuning)]),
 })
 
 
@@ -363,7 +403,7 @@ class Server:
         for key in ("cfl_hi", "cfl_lo"):
             if key in kw:
                 setattr(o, key, float(kw[key]))
-        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused"):
+        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune"):
             if key in kw:
                 setattr(o, key, int(kw[key]))
         self._alloc = None
@@ -425,3 +465,8 @@ class Server:
         b, q, a = C.c_int64(0), C.c_int32(0), C.c_int32(0)
         _check(lib().cgks_server_info(self._h, C.byref(b), C.byref(q), C.byref(a)), "cgks_server_info")
         return dict(device_bytes=b.value, n_queued=q.value, n_active=a.value)
+
+    def tuning(self) -> dict:
+        t = CgksTuning()
+        _check(lib().cgks_server_get_tuning(self._h, C.byref(t)), "cgks_server_get_tuning")
+        return _tuning_dict(t)

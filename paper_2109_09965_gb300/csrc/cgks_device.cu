@@ -46,7 +46,8 @@ struct Bufs {
 // batch-wide settings (every solve of a batch shares them)
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
-  int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 1;
+  int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 0;
+  int autotune = 1;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -88,7 +89,7 @@ struct Batch {
   int n_colours = 0;
   std::vector<int> sweep_seq;        // colour order after the first pass
   std::vector<int> list_off;         // [n_colours + 1] offsets into the sweep cell list
-  std::vector<Ranges> ranges;        // per colour: per-solve cell ranges (n = 0: use the list)
+  std::vector<Ranges> ranges[kNShape];  // per sweep shape, per colour: per-solve cell ranges (n = 0: the list)
   ParamsT<double> dp{};
   ParamsT<float> fp{};
   MeshT<double> dm{};
@@ -116,6 +117,7 @@ struct Batch {
   int *r_start = nullptr, *r_begin = nullptr, *r_pre = nullptr;
   int lo_grid = 0;
   bool lo_fused_ok = false;
+  Tuner tune;                          // launch shapes of the tunable kernels
 };
 
 constexpr int kMaxColFused = 16;     // colours the fused path handles
@@ -184,10 +186,20 @@ void enqueue_res(Batch *b) {
 template <typename TF>
 void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
   Bufs<TF> &B = bufs<TF>(b);
-  launch(b, KI_RECON, k_recon<TF>, dim3(nblk(b->N, kCellBlock)), dim3(kCellBlock), fmesh<TF>(b), fparams<TF>(b), W, Wx,
-         B.coef);
-  launch(b, KI_FACE, k_face<TF>, dim3(nblk(b->F, kFaceBlock)), dim3(kFaceBlock), fmesh<TF>(b), fparams<TF>(b), W,
-         (const TF *)B.coef, Fout);
+  tuned_launch(b->tune, TK_RECON, b->stream, [&] {
+    with_shape(b->tune.shape(TK_RECON), [&](auto sh) {
+      constexpr int S = decltype(sh)::value;
+      launch(b, KI_RECON, k_recon<TF, S>, dim3(nblk(b->N, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+             fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
+    });
+  });
+  tuned_launch(b->tune, TK_FACE, b->stream, [&] {
+    with_shape(b->tune.shape(TK_FACE), [&](auto sh) {
+      constexpr int S = decltype(sh)::value;
+      launch(b, KI_FACE, k_face<TF, S>, dim3(nblk(b->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+             fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout);
+    });
+  });
 }
 
 // high-order step from (W, Wx) into (Wout, Wx): Wx updated in place.
@@ -257,24 +269,35 @@ void enqueue_lo_solve(Batch *b) {
     return;
   }
   Bufs<TF> &B = bufs<TF>(b);
-  const dim3 gc(nblk(b->N, kCellBlock)), gf(nblk(b->F, kCellBlock)), blk(kCellBlock);
+  const dim3 gc(nblk(b->N, kCellBlock)), blk(kCellBlock);
   const int colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
   for (int k = 0; k < b->sh.n_implicit; ++k) {
     launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->Ncap), fparams<TF>(b), k == 0 ? 1 : 0,
            (const double *)b->Wn, b->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
-    launch(b, KI_LOFACE, k_lo_face<TF>, gf, blk, fmesh<TF>(b), fparams<TF>(b), (const TF *)B.U, (const TF *)B.prim,
-           B.Flo, B.lam, B.E0, B.E1);
+    tuned_launch(b->tune, TK_LOFACE, b->stream, [&] {
+      with_shape(b->tune.shape(TK_LOFACE), [&](auto sh) {
+        constexpr int S = decltype(sh)::value;
+        launch(b, KI_LOFACE, k_lo_face<TF, S>, dim3(nblk(b->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+               fmesh<TF>(b), fparams<TF>(b), (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
+      });
+    });
     launch(b, KI_LORHS, k_lo_rhs<TF>, gc, blk, b->dm, b->dp, k == 0 ? 1 : 0, colour0, (const TF *)B.Flo,
            (const TF *)B.lam, (const double *)b->Rp0, b->Src, B.Rk, B.invD, B.dU, B.lamS);
+    const int ssh = b->tune.shape(TK_SWEEP);
     for (int c : b->sweep_seq) {
       const int cnt = b->list_off[c + 1] - b->list_off[c];
-      const Ranges &R = b->ranges[c];
+      const Ranges &R = b->ranges[ssh][c];
       const bool use_list = R.n == 0;
-      const int grid = use_list ? nblk(cnt, kSweepCells) : R.blk[R.n];
-      launch(b, KI_SWEEP, k_sweep<TF>, dim3(grid), dim3(kSweepBlock), fmesh<TF>(b), fparams<TF>(b), R,
-             use_list ? (const int *)b->list + b->list_off[c] : (const int *)nullptr, cnt, (const TF *)B.U,
-             (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD, (const TF *)B.lamS, (const TF *)B.E0,
-             (const TF *)B.E1, B.dU);
+      const int grid = use_list ? nblk(cnt, sweep_cpb(ssh)) : R.blk[R.n];
+      tuned_launch(b->tune, TK_SWEEP, b->stream, [&] {
+        with_shape(ssh, [&](auto sh) {
+          constexpr int S = decltype(sh)::value;
+          launch(b, KI_SWEEP, k_sweep<TF, S>, dim3(grid), dim3(shape_bs(S)), fmesh<TF>(b), fparams<TF>(b), R,
+                 use_list ? (const int *)b->list + b->list_off[c] : (const int *)nullptr, cnt, (const TF *)B.U,
+                 (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD, (const TF *)B.lamS,
+                 (const TF *)B.E0, (const TF *)B.E1, B.dU);
+        });
+      });
     }
   }
   // U^{n_implicit} = U + dU of the last step
@@ -371,18 +394,29 @@ int capture(Batch *b, bool cycle, cudaGraphExec_t *out) {
   return e == cudaSuccess ? CGKS_OK : CGKS_ECUDA;
 }
 
-// n cycles (or explicit steps) without host synchronisation
+// n cycles (or explicit steps) without host synchronisation, except that
+// the autotuner's units read their events back (once per call)
 int run_many(Batch *b, int n, bool cycle) {
   if (n <= 0) return CGKS_OK;
   CK(cudaMemsetAsync(&b->ctl->res_ctr, 0, sizeof(int), b->stream));
   const bool graph = b->sh.use_graph && !(b->timer && b->timer->on);
   cudaGraphExec_t *ge = cycle ? &b->g_cycle : &b->g_step;
-  if (graph && !*ge) {
+  const long long per = count_launches(b, cycle);
+  int k = 0;
+  if (b->tune.eager(cycle)) {
+    for (; k < n && b->tune.eager(cycle); ++k) {
+      b->tune.begin_unit();
+      if (cycle) enqueue_cycle(b);
+      else enqueue_explicit_step(b, -1.0);
+      b->tune.end_unit(cycle);
+    }
+    if (b->tune.collect()) drop_graphs(b);
+  }
+  if (graph && k < n && !*ge) {
     int rc = capture(b, cycle, ge);
     if (rc) return rc;
   }
-  const long long per = count_launches(b, cycle);
-  for (int k = 0; k < n; ++k) {
+  for (; k < n; ++k) {
     if (graph) {
       CK(cudaGraphLaunch(*ge, b->stream));
       b->launches += per;
@@ -503,6 +537,7 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   if (!B) return CGKS_ENOMEM;
   Batch *b = B.get();
   b->sh = sh;
+  b->tune.on = sh.autotune != 0;
   b->S = S;
   b->mem.assign(S, Member{});
   b->Ncap = Ncap; b->Fcap = Fcap;
@@ -728,32 +763,35 @@ int finalize_batch(Batch *b) {
   }
   if (!seq.empty()) seq.erase(seq.begin());
   b->sweep_seq = seq;
-  b->ranges.assign(C, Ranges{});
+  for (auto &rs : b->ranges) rs.assign(C, Ranges{});
   b->list_off.assign(C + 1, 0);
   std::vector<int> list;
   bool need_list = false;
   for (int c = 0; c < C; ++c) {
-    Ranges &R = b->ranges[c];
-    std::memset(&R, 0, sizeof(R));
-    int nr = 0, blocks = 0;
-    for (int s : order) {
-      const Member &M = b->mem[s];
-      const HostMesh &hm = *M.mesh;
-      if (c >= hm.n_colours) continue;
-      const int beg = static_cast<int>(M.cell_off) + hm.colour_start[c];
-      const int end = static_cast<int>(M.cell_off) + hm.colour_start[c + 1];
-      if (end == beg) continue;
-      for (int i = beg; i < end; ++i) list.push_back(i);
-      if (nr == kMaxRanges) { nr = -1; continue; }
-      if (nr < 0) continue;
-      R.blk[nr] = blocks;
-      R.begin[nr] = beg;
-      R.end[nr] = end;
-      blocks += nblk(end - beg, kSweepCells);
-      ++nr;
+    for (int sh = 0; sh < kNShape; ++sh) {
+      Ranges &R = b->ranges[sh][c];
+      std::memset(&R, 0, sizeof(R));
+      int nr = 0, blocks = 0;
+      for (int s : order) {
+        const Member &M = b->mem[s];
+        const HostMesh &hm = *M.mesh;
+        if (c >= hm.n_colours) continue;
+        const int beg = static_cast<int>(M.cell_off) + hm.colour_start[c];
+        const int end = static_cast<int>(M.cell_off) + hm.colour_start[c + 1];
+        if (end == beg) continue;
+        if (sh == 0)
+          for (int i = beg; i < end; ++i) list.push_back(i);
+        if (nr == kMaxRanges) { nr = -1; continue; }
+        if (nr < 0) continue;
+        R.blk[nr] = blocks;
+        R.begin[nr] = beg;
+        R.end[nr] = end;
+        blocks += nblk(end - beg, sweep_cpb(sh));
+        ++nr;
+      }
+      if (nr >= 0) { R.n = nr; R.blk[nr] = blocks; }
+      else { std::memset(&R, 0, sizeof(R)); need_list = true; }
     }
-    if (nr >= 0) { R.n = nr; R.blk[nr] = blocks; }
-    else { std::memset(&R, 0, sizeof(R)); need_list = true; }
     b->list_off[c + 1] = static_cast<int>(list.size());
   }
   if (need_list && !list.empty())
@@ -849,6 +887,7 @@ Shared shared_from(const cgks_params *p) {
   sh.gamma = p->gamma; sh.cfl_hi = p->cfl_hi; sh.cfl_lo = p->cfl_lo;
   sh.n_implicit = p->n_implicit; sh.n_sweeps = p->n_sweeps; sh.time_scheme = p->time_scheme;
   sh.precision = p->precision; sh.use_graph = p->use_graph; sh.lo_fused = p->low_order_fused;
+  sh.autotune = p->autotune;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -993,6 +1032,7 @@ void cgks_default_params(cgks_params *p) {
   p->precision = CGKS_FP64;
   p->use_graph = 1;
   p->low_order_fused = 0;
+  p->autotune = 1;
 }
 
 const char *cgks_strerror(int st) {
@@ -1325,6 +1365,34 @@ int cgks_launches_per_call(const cgks_solver *s, int cycle) {
   return s->s3 ? s3_launches_per_call(s->s3, cycle != 0) : static_cast<int>(count_launches(s->b, cycle != 0));
 }
 
+int cgks_tune_shape(int32_t shape, int32_t *block, int32_t *per_thread, int32_t *min_blocks) {
+  if (shape < 0 || shape >= kNShape) return CGKS_EINVAL;
+  if (block) *block = shape_bs(shape);
+  if (per_thread) *per_thread = shape_ipt(shape);
+  if (min_blocks) *min_blocks = shape_minb(shape);
+  return CGKS_OK;
+}
+
+int cgks_get_tuning(cgks_solver *s, cgks_tuning *t) {
+  if (!s || !t) return CGKS_EINVAL;
+  if (s->s3) return s3_tuner(s->s3)->report(t), CGKS_OK;
+  s->b->tune.report(t);
+  return CGKS_OK;
+}
+
+int cgks_set_tuning(cgks_solver *s, const int32_t shape[CGKS_TUNE_KERNELS]) {
+  if (!s || !shape) return CGKS_EINVAL;
+  int shp[TK_COUNT];
+  for (int k = 0; k < TK_COUNT; ++k) {
+    if (shape[k] < 0 || shape[k] >= kNShape) return CGKS_EINVAL;
+    shp[k] = shape[k];
+  }
+  if (s->s3) return s3_set_tuning(s->s3, shp);
+  s->b->tune.set(shp);
+  drop_graphs(s->b);
+  return CGKS_OK;
+}
+
 // ================================ serving ================================
 void cgks_server_default_opts(cgks_server_opts *o) {
   if (!o) return;
@@ -1339,6 +1407,7 @@ void cgks_server_default_opts(cgks_server_opts *o) {
   o->max_cycles = 20000;
   o->use_graph = 1;
   o->low_order_fused = 0;
+  o->autotune = 1;
 }
 
 // Faces per cell the batch capacity provides for (2-D: triangles 1.5,
@@ -1359,6 +1428,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->sh.cfl_hi = o->cfl_hi; v->sh.cfl_lo = o->cfl_lo; v->sh.n_implicit = o->n_implicit; v->sh.n_sweeps = o->n_sweeps;
   v->sh.time_scheme = o->time_scheme; v->sh.precision = o->precision; v->sh.use_graph = o->use_graph;
   v->sh.lo_fused = o->low_order_fused;
+  v->sh.autotune = o->autotune;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;
@@ -1597,6 +1667,18 @@ int cgks_server_info(cgks_server *v, int64_t *device_bytes, int32_t *n_queued, i
   int na = 0;
   for (int64_t id : v->slot_req) na += id >= 0;
   if (n_active) *n_active = na;
+  return CGKS_OK;
+}
+
+int cgks_server_get_tuning(cgks_server *v, cgks_tuning *t) {
+  if (!v || !t) return CGKS_EINVAL;
+  if (v->b) {
+    v->b->tune.report(t);
+  } else {
+    Tuner fresh;   // no batch yet: nothing tuned
+    fresh.on = v->sh.autotune != 0;
+    fresh.report(t);
+  }
   return CGKS_OK;
 }
 

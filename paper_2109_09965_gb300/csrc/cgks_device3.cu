@@ -67,6 +67,7 @@ struct Solver3 {
   cudaGraphExec_t g_cycle = nullptr, g_step = nullptr;
   Timer *timer = nullptr;
   long long launches = 0;
+  Tuner tune;                     // launch shapes of the tunable kernels
 };
 
 namespace {
@@ -125,10 +126,20 @@ void enqueue_res(Solver3 *s) {
 template <typename TF>
 void hi_eval(Solver3 *s, const TF *W, const TF *Wx, TF *Fout) {
   Bufs3<TF> &B = bufs<TF>(s);
-  launch(s, KI_RECON, k_recon<TF>, dim3(nblk(s->N, kCellBlock)), dim3(kCellBlock), fmesh<TF>(s), fpar<TF>(s), W, Wx,
-         B.coef);
-  launch(s, KI_FACE, k_face<TF>, dim3(nblk(s->F, kFaceBlock)), dim3(kFaceBlock), fmesh<TF>(s), fpar<TF>(s), W,
-         (const TF *)B.coef, Fout);
+  tuned_launch(s->tune, TK_RECON, s->stream, [&] {
+    with_shape(s->tune.shape(TK_RECON), [&](auto sh) {
+      constexpr int S = decltype(sh)::value;
+      launch(s, KI_RECON, k_recon<TF, S>, dim3(nblk(s->N, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+             fmesh<TF>(s), fpar<TF>(s), W, Wx, B.coef);
+    });
+  });
+  tuned_launch(s->tune, TK_FACE, s->stream, [&] {
+    with_shape(s->tune.shape(TK_FACE), [&](auto sh) {
+      constexpr int S = decltype(sh)::value;
+      launch(s, KI_FACE, k_face<TF, S>, dim3(nblk(s->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+             fmesh<TF>(s), fpar<TF>(s), W, (const TF *)B.coef, Fout);
+    });
+  });
 }
 
 template <typename TF>
@@ -156,20 +167,30 @@ void hi_step(Solver3 *s, double *Wout, TF *Wout_m, bool want_res) {
 template <typename TF>
 void lo_solve(Solver3 *s) {
   Bufs3<TF> &B = bufs<TF>(s);
-  const dim3 gc(nblk(s->N, kCellBlock)), gf(nblk(s->F, kCellBlock)), blk(kCellBlock);
+  const dim3 gc(nblk(s->N, kCellBlock)), blk(kCellBlock);
   const int colour0_end = s->P.n_sweeps > 0 ? s->colour_start[1] : 0;
   for (int k = 0; k < s->P.n_implicit; ++k) {
     launch(s, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(s->N), fpar<TF>(s), k == 0 ? 1 : 0,
            (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
-    launch(s, KI_LOFACE, k_lo_face<TF>, gf, blk, fmesh<TF>(s), fpar<TF>(s), (const TF *)B.U, (const TF *)B.prim,
-           B.Flo, B.lam, B.E0, B.E1);
+    tuned_launch(s->tune, TK_LOFACE, s->stream, [&] {
+      with_shape(s->tune.shape(TK_LOFACE), [&](auto sh) {
+        constexpr int S = decltype(sh)::value;
+        launch(s, KI_LOFACE, k_lo_face<TF, S>, dim3(nblk(s->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
+               fmesh<TF>(s), fpar<TF>(s), (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
+      });
+    });
     launch(s, KI_LORHS, k_lo_rhs<TF>, gc, blk, s->dm, s->dp, k == 0 ? 1 : 0, colour0_end, (const TF *)B.Flo,
            (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU, B.lamS);
     for (int c : s->sweep_seq) {
       const int beg = s->colour_start[c], cnt = s->colour_start[c + 1] - beg;
-      launch(s, KI_SWEEP, k_sweep<TF>, dim3(nblk(cnt, kSweepCells)), dim3(kSweepBlock), fmesh<TF>(s), fpar<TF>(s),
-             beg, cnt, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
-             (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, B.dU);
+      tuned_launch(s->tune, TK_SWEEP, s->stream, [&] {
+        with_shape(s->tune.shape(TK_SWEEP), [&](auto sh) {
+          constexpr int S = decltype(sh)::value;
+          launch(s, KI_SWEEP, k_sweep<TF, S>, dim3(nblk(cnt, sweep_cpb(S))), dim3(shape_bs(S)), fmesh<TF>(s),
+                 fpar<TF>(s), beg, cnt, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
+                 (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, B.dU);
+        });
+      });
     }
   }
   if (s->P.n_implicit > 0)
@@ -296,6 +317,14 @@ void fill_params(const cgks_params &p, ParamsT<T> &P) {
 
 }  // namespace
 
+Tuner *s3_tuner(Solver3 *s) { return &s->tune; }
+
+int s3_set_tuning(Solver3 *s, const int *shape) {
+  s->tune.set(shape);
+  drop_graphs(s);
+  return CGKS_OK;
+}
+
 size_t s3_footprint(int64_t n_cells, int64_t n_faces, bool mixed) {
   Solver3 tmp;
   tmp.N = n_cells;
@@ -328,6 +357,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   s->colour_start = m.colour_start;
   s->stream = stream;
   s->timer = timer;
+  s->tune.on = p->autotune != 0;
   if (s->N * kNCol3 * kNM3 > INT32_MAX || s->F * 24 > INT32_MAX) return CGKS_EINVAL;
   {
     std::vector<int> seq;
@@ -511,12 +541,22 @@ int s3_run(Solver3 *s, int n, bool cycle) {
   CK3(cudaMemsetAsync(&s->ctl->res_ctr, 0, sizeof(int), s->stream));
   const bool graph = s->P.use_graph && !(s->timer && s->timer->on);
   cudaGraphExec_t *ge = cycle ? &s->g_cycle : &s->g_step;
-  if (graph && !*ge) {
+  int k = 0;
+  if (s->tune.eager(cycle)) {
+    for (; k < n && s->tune.eager(cycle); ++k) {
+      s->tune.begin_unit();
+      if (cycle) enqueue_cycle(s);
+      else enqueue_step(s, -1.0);
+      s->tune.end_unit(cycle);
+    }
+    if (s->tune.collect()) drop_graphs(s);
+  }
+  if (graph && k < n && !*ge) {
     const int rc = capture(s, cycle, ge);
     if (rc) return rc;
   }
   const long long per = count_launches(s, cycle);
-  for (int k = 0; k < n; ++k) {
+  for (; k < n; ++k) {
     if (graph) { CK3(cudaGraphLaunch(*ge, s->stream)); s->launches += per; }
     else if (cycle) enqueue_cycle(s);
     else enqueue_step(s, -1.0);

@@ -23,6 +23,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_physics.cuh"
+#include "cgks_shapes.h"
 
 namespace cgks {
 namespace kern {
@@ -30,8 +31,6 @@ namespace kern {
 namespace D = cgks::dev;
 
 constexpr int kCellBlock = 256;
-constexpr int kFaceBlock = 128;
-constexpr int kSweepBlock = 128;
 constexpr int kTagsPerSolve = CGKS_MAX_BC;
 constexpr int kBadState = 1;   // bit of a solve's status word
 
@@ -172,10 +171,8 @@ __device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, T n
 // K1: compact least-squares quadratic of every cell.
 //   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
 template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
+__device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
+                                         const T *__restrict__ Wx, T *__restrict__ coef, const int i) {
   const int n = m.nc;
   T wi[4], gxi[4], gyi[4];
   for (int v = 0; v < 4; ++v) { wi[v] = W[v * n + i]; gxi[v] = Wx[v * n + i]; gyi[v] = Wx[(4 + v) * n + i]; }
@@ -212,6 +209,13 @@ __global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, 
   }
   for (int q = 0; q < kNM; ++q)
     for (int v = 0; v < 4; ++v) coef[(q * 4 + v) * n + i] = c[q][v];
+}
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_recon(MeshT<T> m, ParamsT<T> P,
+                                                                        const T *__restrict__ W,
+                                                                        const T *__restrict__ Wx,
+                                                                        T *__restrict__ coef) {
+  for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
 }
 
 // value and gradient of the quadratic of cell i at scaled offset (x, y)
@@ -252,10 +256,8 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T n
 // face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
 //   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
 template <typename T>
-__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                     const T *__restrict__ coef, T *__restrict__ out) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
+__device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
+                                        const T *__restrict__ coef, T *__restrict__ out, const int f) {
   const int sid = m.fsid[f];
   if (sid < 0) return;   // free face space of a batch
   const int nf = m.nf;
@@ -313,6 +315,13 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, c
   }
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
+}
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_face(MeshT<T> m, ParamsT<T> P,
+                                                                       const T *__restrict__ W,
+                                                                       const T *__restrict__ coef,
+                                                                       T *__restrict__ out) {
+  for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
 }
 
 // K3 modes
@@ -451,11 +460,9 @@ __device__ __forceinline__ D::Prim<T> load_prim(const T *__restrict__ prim, int 
 // and (FP64 mode) the Euler normal fluxes F_n(U_c0), F_n(U_c1) the
 // relaxation reuses.
 template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
-                                                        const T *__restrict__ prim, T *__restrict__ Flo,
-                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
+__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ U,
+                                           const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam,
+                                           T *__restrict__ E0, T *__restrict__ E1, const int f) {
   const int sid = m.fsid[f];
   if (sid < 0) return;   // free face space of a batch
   const int n = m.nc, nf = m.nf;
@@ -496,6 +503,14 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P
       E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
     }
   }
+}
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_lo_face(MeshT<T> m, ParamsT<T> P,
+                                                                          const T *__restrict__ U,
+                                                                          const T *__restrict__ prim,
+                                                                          T *__restrict__ Flo, T *__restrict__ lam,
+                                                                          T *__restrict__ E0, T *__restrict__ E1) {
+  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, U, prim, Flo, lam, E0, E1, f); });
 }
 
 // K6: low-order right-hand side R^k = R_lo(U^k) + S (FP64 sums), 1/D_i
@@ -575,23 +590,12 @@ __device__ __forceinline__ int range_cell(const Ranges &R, int cl, int cpb) {
 // group, and lane v writes component v.  Cells of one colour never
 // neighbour each other, so the dU_ip read here are not written by this
 // launch.
-constexpr int kSweepCells = kSweepBlock / kMaxFace;
 template <typename T>
-__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, const __grid_constant__ Ranges R,
-                                                       const int *__restrict__ list, int count,
-                                                       const T *__restrict__ U, const T *__restrict__ prim,
-                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
-                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
-                                                       const T *__restrict__ E1, T *__restrict__ dU) {
-  const int s = threadIdx.x & (kMaxFace - 1);
-  const int cl = threadIdx.x / kMaxFace;
-  int i;
-  if (list) {
-    const int g = blockIdx.x * kSweepCells + cl;
-    i = g < count ? list[g] : -1;
-  } else {
-    i = range_cell(R, cl, kSweepCells);
-  }
+__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const int i, const int s,
+                                           const T *__restrict__ U, const T *__restrict__ prim,
+                                           const T *__restrict__ Rk, const T *__restrict__ invD,
+                                           const T *__restrict__ lamS, const T *__restrict__ E0,
+                                           const T *__restrict__ E1, T *__restrict__ dU) {
   const int n = m.nc, nf = m.nf;
   // every lane stays to the shuffles; lanes of absent cells or slots add 0
   const int j = i >= 0 ? m.cnbr[s * n + i] : -1;
@@ -628,6 +632,34 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P,
   const T k1 = (b0 ? c[3] : c[2]) + __shfl_xor_sync(0xffffffffu, b0 ? c[2] : c[3], 1);   // component b0 + 2
   const T mine = (b1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
   if (i >= 0) dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+}
+// cells per block of a sweep launch of shape SH
+__host__ __device__ constexpr int sweep_cpb(int sh) { return shape_bs(sh) / kMaxFace * shape_ipt(sh); }
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_sweep(MeshT<T> m, ParamsT<T> P,
+                                                                        const __grid_constant__ Ranges R,
+                                                                        const int *__restrict__ list, int count,
+                                                                        const T *__restrict__ U,
+                                                                        const T *__restrict__ prim,
+                                                                        const T *__restrict__ Rk,
+                                                                        const T *__restrict__ invD,
+                                                                        const T *__restrict__ lamS,
+                                                                        const T *__restrict__ E0,
+                                                                        const T *__restrict__ E1, T *__restrict__ dU) {
+  constexpr int kGroups = shape_bs(SH) / kMaxFace, kCpb = sweep_cpb(SH);
+  const int s = threadIdx.x & (kMaxFace - 1);
+#pragma unroll 1
+  for (int k = 0; k < shape_ipt(SH); ++k) {
+    const int cl = k * kGroups + static_cast<int>(threadIdx.x) / kMaxFace;
+    int i;
+    if (list) {
+      const int g = static_cast<int>(blockIdx.x) * kCpb + cl;
+      i = g < count ? list[g] : -1;
+    } else {
+      i = range_cell(R, cl, kCpb);
+    }
+    sweep_cell(m, P, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
+  }
 }
 
 // K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density

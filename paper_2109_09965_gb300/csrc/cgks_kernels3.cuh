@@ -13,6 +13,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_physics3.cuh"
+#include "cgks_shapes.h"
 
 namespace cgks {
 namespace kern3 {
@@ -20,10 +21,7 @@ namespace kern3 {
 namespace D3 = cgks::dev3;
 constexpr int NV = 5;
 constexpr int kCellBlock = 256;
-constexpr int kFaceBlock = 128;
 constexpr int kSweepLanes = 8;                     // lanes per cell (6 face slots)
-constexpr int kSweepBlock = 128;
-constexpr int kSweepCells = kSweepBlock / kSweepLanes;
 constexpr int kBadState = 1;
 
 template <typename T>
@@ -163,10 +161,7 @@ __device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, con
 
 // K1: compact quadratic per cell: coef[(q*5 + v)][n], 9 monomials
 template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                      const T *__restrict__ Wx, T *__restrict__ coef) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
+__device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef, const int i) {
   const int n = m.nc;
   T wi[NV], gi[3][NV];
 #pragma unroll
@@ -219,6 +214,11 @@ __global__ void __launch_bounds__(kCellBlock) k_recon(MeshT<T> m, ParamsT<T> P, 
 #pragma unroll
     for (int v = 0; v < NV; ++v) coef[(q * NV + v) * n + i] = c[q][v];
 }
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef) {
+  for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
+}
 
 // value and gradient of cell i's quadratic at scaled offset x
 template <typename T>
@@ -245,10 +245,7 @@ __device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restri
 // K2: smooth GKS flux and interface state at the Gauss points of every face:
 // out[(k*5 + v)][nf], k = 0 F0, 1 F1, 2 Wc, 3 Wt, weighted sums, global frame
 template <typename T>
-__global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W,
-                                                     const T *__restrict__ coef, T *__restrict__ out) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
+__device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out, const int f) {
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f], ng = m.fng[f];
   const T ajump = m.fjump[f];
@@ -336,6 +333,11 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(MeshT<T> m, ParamsT<T> P, c
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[(k * NV + v) * nf + f] = acc[k][v];
+}
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out) {
+  for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
 }
 
 enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
@@ -491,11 +493,7 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, const D3:
 
 // KFVS flux, lambda_p = max of both sides, Euler flux cache (FP64 mode)
 template <typename T>
-__global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U,
-                                                        const T *__restrict__ prim, T *__restrict__ Flo,
-                                                        T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
+__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ U, const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1, const int f) {
   const int n = m.nc, nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T S = m.fS[f];
@@ -545,6 +543,11 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_face(MeshT<T> m, ParamsT<T> P
     }
   }
 }
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U, const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
+  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, U, prim, Flo, lam, E0, E1, f); });
+}
 
 // right-hand side R^k = R_lo + S (FP64 sums), 1/D_i (FP64), lambda per slot,
 // first colour pass (dU = R / D on colour 0, zero elsewhere)
@@ -589,15 +592,11 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
 // terms are summed over the lane group by shuffles, lane v writes
 // component v.
 template <typename T>
-__global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count,
-                                                       const T *__restrict__ U, const T *__restrict__ prim,
-                                                       const T *__restrict__ Rk, const T *__restrict__ invD,
-                                                       const T *__restrict__ lamS, const T *__restrict__ E0,
-                                                       const T *__restrict__ E1, T *__restrict__ dU) {
-  const int s = threadIdx.x & (kSweepLanes - 1);
-  const int cl = threadIdx.x / kSweepLanes;
-  const int g = blockIdx.x * kSweepCells + cl;
-  const int i = g < count ? begin + g : -1;
+__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const int i, const int s,
+                                           const T *__restrict__ U, const T *__restrict__ prim,
+                                           const T *__restrict__ Rk, const T *__restrict__ invD,
+                                           const T *__restrict__ lamS, const T *__restrict__ E0,
+                                           const T *__restrict__ E1, T *__restrict__ dU) {
   const int n = m.nc, nf = m.nf;
   const int j = (i >= 0 && s < kMaxFace3) ? m.cnbr[s * n + i] : -1;
   T c[NV] = { T(0), T(0), T(0), T(0), T(0) };
@@ -636,6 +635,21 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep(MeshT<T> m, ParamsT<T> P,
   if (i >= 0 && s < NV) {
     const T mine = s == 0 ? c[0] : s == 1 ? c[1] : s == 2 ? c[2] : s == 3 ? c[3] : c[4];
     dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+  }
+}
+// cells per block of a sweep launch of shape SH
+__host__ __device__ constexpr int sweep_cpb(int sh) { return shape_bs(sh) / kSweepLanes * shape_ipt(sh); }
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count, const T *__restrict__ U, const T *__restrict__ prim,
+            const T *__restrict__ Rk, const T *__restrict__ invD, const T *__restrict__ lamS,
+            const T *__restrict__ E0, const T *__restrict__ E1, T *__restrict__ dU) {
+  constexpr int kGroups = shape_bs(SH) / kSweepLanes;
+  const int s = threadIdx.x & (kSweepLanes - 1);
+#pragma unroll 1
+  for (int k = 0; k < shape_ipt(SH); ++k) {
+    const int g = (static_cast<int>(blockIdx.x) * shape_ipt(SH) + k) * kGroups + static_cast<int>(threadIdx.x) / kSweepLanes;
+    sweep_cell(m, P, g < count ? begin + g : -1, s, U, prim, Rk, invD, lamS, E0, E1, dU);
   }
 }
 

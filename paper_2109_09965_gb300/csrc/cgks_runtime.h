@@ -3,10 +3,12 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
 #include <utility>
 #include <vector>
 
 #include "cgks_internal.h"
+#include "cgks_shapes.h"
 
 namespace cgks {
 
@@ -42,6 +44,122 @@ inline void collect_timing(Timer *t) {
   t->ev.clear();
 }
 
+// ---- launch-shape autotuner ----
+// Each tunable kernel's first kRounds x kNShape tuning units (eager cycles
+// or explicit steps that launch it) use shape unit % kNShape; the first
+// round only warms up (lazy module loading), the others are timed with CUDA
+// events around each launch.  When a kernel's units are spent it keeps the
+// shape of least mean launch time.  A unit runs eagerly (no graph) while a
+// kernel that this kind of unit launched last time is still being tuned.
+struct Tuner {
+  static constexpr int kRounds = 3;
+  bool on = false;
+  int pick[TK_COUNT] = { kDefaultShape[0], kDefaultShape[1], kDefaultShape[2], kDefaultShape[3] };
+  int unit[TK_COUNT] = { 0, 0, 0, 0 };
+  bool used[TK_COUNT] = { false, false, false, false };
+  bool seen[2][TK_COUNT] = { { true, true, true, true }, { true, true, true, true } };  // [cycle]
+  bool in_unit = false;
+  double ms[TK_COUNT][kNShape] = {};
+  int cnt[TK_COUNT][kNShape] = {};
+  struct Ev { int k, shape; cudaEvent_t e0, e1; };
+  std::vector<Ev> ev;
+
+  bool tuning(int k) const { return on && unit[k] < kRounds * kNShape; }
+  int shape(int k) const { return tuning(k) ? unit[k] % kNShape : pick[k]; }
+  bool timed(int k) const { return in_unit && tuning(k) && unit[k] >= kNShape; }
+  // the next unit of this kind runs eagerly
+  bool eager(bool cycle) const {
+    for (int k = 0; k < TK_COUNT; ++k)
+      if (seen[cycle][k] && tuning(k)) return true;
+    return false;
+  }
+  void begin_unit() {
+    in_unit = true;
+    for (bool &u : used) u = false;
+  }
+  void end_unit(bool cycle) {
+    in_unit = false;
+    for (int k = 0; k < TK_COUNT; ++k) {
+      seen[cycle][k] = used[k];
+      if (used[k] && tuning(k)) ++unit[k];
+    }
+  }
+  // read the pending events (synchronises on the last); kernels whose
+  // units are spent take the fastest shape.  Returns true if a pick changed.
+  bool collect() {
+    for (auto &e : ev) {
+      float t = 0.f;
+      cudaEventSynchronize(e.e1);
+      if (cudaEventElapsedTime(&t, e.e0, e.e1) == cudaSuccess) {
+        ms[e.k][e.shape] += t;
+        cnt[e.k][e.shape] += 1;
+      }
+      cudaEventDestroy(e.e0);
+      cudaEventDestroy(e.e1);
+    }
+    ev.clear();
+    bool changed = false;
+    for (int k = 0; k < TK_COUNT; ++k) {
+      if (!on || unit[k] != kRounds * kNShape || decided[k]) continue;
+      decided[k] = true;
+      int best = -1;
+      double tb = 0.0;
+      for (int s = 0; s < kNShape; ++s) {
+        if (!cnt[k][s]) continue;
+        const double t = ms[k][s] / cnt[k][s];
+        if (best < 0 || t < tb) { best = s; tb = t; }
+      }
+      if (best < 0) continue;   // never timed: keep the default
+      changed |= best != pick[k];
+      pick[k] = best;
+    }
+    return changed;
+  }
+  // fix the shapes and end tuning
+  void set(const int *shp) {
+    for (int k = 0; k < TK_COUNT; ++k) { pick[k] = shp[k]; unit[k] = kRounds * kNShape; decided[k] = true; }
+  }
+  void report(cgks_tuning *t) const {
+    for (int k = 0; k < TK_COUNT; ++k) {
+      t->shape[k] = shape(k);
+      t->done[k] = !tuning(k);
+      for (int s = 0; s < kNShape; ++s) t->ms[k][s] = cnt[k][s] ? ms[k][s] / cnt[k][s] : 0.0;
+    }
+  }
+  bool decided[TK_COUNT] = { false, false, false, false };
+};
+
+// launch kernel tk with a tuner's event pair around it while timed
+template <typename Launch>
+void tuned_launch(Tuner &tu, int tk, cudaStream_t st, Launch &&go) {
+  const bool t = tu.timed(tk);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (t) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  go();
+  if (t) {
+    cudaEventRecord(e1, st);
+    tu.ev.push_back({ tk, tu.shape(tk), e0, e1 });
+  }
+  tu.used[tk] = true;
+}
+
+// call f(std::integral_constant<int, s>) for the runtime shape index s
+template <typename F>
+void with_shape(int s, F &&f) {
+  switch (s) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    default: f(std::integral_constant<int, 0>{}); break;
+  }
+}
+static_assert(kNShape == 5, "with_shape covers every shape");
+
 // ---- the 3-D solver (cgks_device3.cu) ----
 struct Solver3;
 int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Timer *timer, Solver3 **out);
@@ -60,5 +178,7 @@ int s3_get_rp0(Solver3 *s, double *Rp0);
 long long s3_launches(const Solver3 *s);
 int s3_launches_per_call(const Solver3 *s, bool cycle);
 size_t s3_footprint(int64_t n_cells, int64_t n_faces, bool mixed);
+Tuner *s3_tuner(Solver3 *s);
+int s3_set_tuning(Solver3 *s, const int *shape);
 
 }  // namespace cgks

@@ -36,6 +36,25 @@ def test_library_exports_every_declared_symbol(cg):
     assert set(names) == set(cg.SIGNATURES), set(names) ^ set(cg.SIGNATURES)
 
 
+def test_tune_shapes_and_defaults(cg):
+    """The autotuner's launch shapes are distinct, legal block sizes, and
+    the defaults turn the tuner on (host-only calls, no GPU needed)."""
+    shapes = [cg.tune_shape(k) for k in range(cg.TUNE_SHAPES)]
+    assert len(set(shapes)) == cg.TUNE_SHAPES
+    for bs, ipt, minb in shapes:
+        assert bs % 32 == 0 and 64 <= bs <= 256 and 1 <= ipt <= 2 and 1 <= minb
+        assert bs * minb <= 2048          # resident threads per SM
+    for bad in (-1, cg.TUNE_SHAPES):
+        with pytest.raises(cg.CgksError):
+            cg.tune_shape(bad)
+    P = cg.CgksParams()
+    cg.lib().cgks_default_params(C.byref(P))
+    assert P.autotune == 1 and P.low_order_fused == 0 and P.use_graph == 1
+    O = cg.CgksServerOpts()
+    cg.lib().cgks_server_default_opts(C.byref(O))
+    assert O.autotune == 1 and O.max_active == 64
+
+
 @pytest.mark.parametrize("mesh", [MG.cavity(8), MG.cylinder(24, 3, 5),
                                   MG.box(7, 5, jitter=0.2, seed=2, cells="mixed",
                                          quad_mask=lambda i, j: (i + j) % 3 == 0)],

@@ -141,7 +141,7 @@ def test_graph_replay_is_bitwise_equal_to_launches(libs):
     mesh, spec, (W, Wx) = case("prism_walls")
     out = []
     for g in (1, 0):
-        s = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=g))
+        s = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=g, autotune=0))
         s.set_state(W, Wx)
         s.pmg_cycle(3)
         out.append(s.get_state())

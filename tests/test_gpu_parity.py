@@ -157,8 +157,8 @@ def test_many_cycles_and_history(libs):
 def test_graph_and_plain_launches_agree_bitwise(libs):
     cgks, _ = libs
     mesh, spec, state = case("cavity8")
-    a = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=1))
-    b = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=0))
+    a = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=1, autotune=0))
+    b = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=0, autotune=0))
     a.set_state(*state)
     b.set_state(*state)
     ra, rb = a.pmg_cycle(4), b.pmg_cycle(4)
