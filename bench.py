@@ -202,6 +202,8 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
         args = argparse.Namespace(**dict(vars(args), steps=steps))
     sp = dict(spec, precision=precision, autotune=0 if args.no_autotune else 1)
     solver = cgks.Solver(gm, sp)
+    if args.tune_shapes:
+        solver.set_tuning([int(x) for x in args.tune_shapes.split(",")])
     solver.set_state(W0)
     stream = torch.cuda.current_stream()
     # the autotuner's cycles (ordinary V-cycles, each kernel trying its
@@ -249,7 +251,18 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     kernels = {k: dict({"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]},
                        **per_gbs.get(k, {}))
                for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0}
-    out = {"value": value, "ms": ms, "launches": int(launches), "clocks": clk.summary(), "roof": roof,
+    # high level (explicit step, R_p0) and low level (implicit smoother) apart,
+    # by their shares of the timed cycle: cell-steps/s of the high-order step
+    # and cell-sweeps/s of the point relaxation (n_implicit x 2 n_sweeps
+    # passes over every cell per cycle)
+    hi_k = ("k_dt", "k_recon", "k_face", "k_update", "k_res_final")
+    hi_ms = sum(v[0] for k, v in kt.items() if k in hi_k) / total_k * ms / args.steps
+    lo_ms = ms / args.steps - hi_ms
+    n_imp, n_sw = sp.get("n_implicit", 6), sp.get("n_sweeps", 2)
+    split = {"high_level_ms_per_cycle": hi_ms, "low_level_ms_per_cycle": lo_ms,
+             "high_cell_steps_per_s": world * mesh.n_cells / (hi_ms / 1000.0),
+             "low_cell_sweeps_per_s": world * mesh.n_cells * n_imp * 2 * n_sw / (lo_ms / 1000.0)}
+    out = {"value": value, "ms": ms, "launches": int(launches), "clocks": clk.summary(), "roof": roof, "split": split,
            "kernels": kernels, "res": res, "tuning": dict(tuning, cycles=tune_cycles)}
     if with_e2e:
         # end to end through the C ABI with pinned host buffers
@@ -482,7 +495,7 @@ def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_p
                     steps=steps, work_model=work_model3)
         out[prec] = {"value": m["value"], "unit": "cell-updates/s", "ms_per_step": m["ms"] / steps, "steps": steps,
                      "roofline": m["roof"], "kernels": m["kernels"], "gpu_launches": m["launches"],
-                     "residual_last": m["res"], "clocks": m["clocks"], "tuning": m["tuning"]}
+                     "residual_last": m["res"], "clocks": m["clocks"], "tuning": m["tuning"], "split": m["split"]}
     return out
 
 
@@ -499,7 +512,11 @@ def main():
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D sphere workloads")
     ap.add_argument("--no-autotune", action="store_true", help="fixed default launch shapes")
+    ap.add_argument("--tune-shapes", default="",
+                    help="fix the launch shapes of k_recon,k_face,k_lo_face,k_sweep (e.g. 1,4,1,1; for profiling)")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-1e-8 comparison")
+    ap.add_argument("--converge3d-full", action="store_true",
+                    help="3-D convergence on the 512,000-cell sphere instead of the 128,000-cell one")
     ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
                     help="serving run: a small sample in the line (default), or the full 256-request mix")
     args = ap.parse_args()
@@ -524,7 +541,7 @@ def main():
         mv = measure(cgks, gm, mesh, spec, W0, args, "mixed", world, local, flush, hbm, hbm_src, with_e2e=False)
         variants["mixed"] = {"value": mv["value"], "ms_per_step": mv["ms"] / args.steps, "dtype": "f32+f64",
                              "gpu_launches": mv["launches"], "roofline": mv["roof"], "kernels": mv["kernels"],
-                             "clocks": mv["clocks"], "tuning": mv["tuning"],
+                             "clocks": mv["clocks"], "tuning": mv["tuning"], "split": mv["split"],
                              "note": "FP32 reconstruction, fluxes and sweeps; FP64 accumulation, diagonal "
                                      "inversion and residual norms; same workload and step"}
     if rank != 0:
@@ -535,7 +552,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": config_block(mesh, args), "e2e": m["e2e"],
             "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roof"],
-            "kernels": m["kernels"], "residual_last": m["res"], "tuning": m["tuning"]}
+            "kernels": m["kernels"], "residual_last": m["res"], "tuning": m["tuning"], "split": m["split"]}
     if variants:
         line["variants"] = variants
     if not args.no_3d:
@@ -573,6 +590,14 @@ def main():
                             f"layers) to 20 radii: {cm.n_cells} cells, FP64; Res drop 1e-8 relative to the first "
                             "iteration; p-multigrid V-cycles vs explicit S2O4 steps, same GPU")
         line["convergence"] = conv
+        if not args.no_3d:
+            lvl = 4 if args.converge3d_full else 3
+            c3 = converge3d(cgks, lvl, 40, 20, 5e-3)
+            c3["workload"] = (f"3-D laminar sphere, Re 118, Ma 0.2, icosphere level {lvl} extruded by 40 prism "
+                              f"layers (first 5e-3 D, growth 1.1) and 20 split-tet layers to 20 D: {c3['n_cells']} "
+                              "cells; p-multigrid to a 1e-8 drop of Res relative to the first cycle (FP64), then "
+                              "the mixed path over the same cycles")
+            line["convergence_3d"] = c3
     print(json.dumps(line), flush=True)
 
 
@@ -702,6 +727,48 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
     return roof, per
 
 
+def converge3d(cgks, level, n_prism, n_tet, h0, drop=1e-8, max_cycles=6000):
+    """3-D sphere (Re 118, Ma 0.2) to a 1e-8 drop of Res: FP64 p-multigrid,
+    then the mixed path over the same cycles (its Res floor and its field
+    against the FP64 field)."""
+    import torch
+    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, 0.2, 118)
+    gm = cgks.Mesh(mesh)
+    out = {"n_cells": mesh.n_cells}
+    s = cgks.Solver(gm, dict(spec, precision="fp64"))
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hist, done = [], False
+    while len(hist) < max_cycles and not done:
+        r = s.pmg_cycle(100)
+        hist.extend(r.tolist())
+        done = min(hist) <= drop * hist[0] or not np.all(np.isfinite(r))
+    el = time.perf_counter() - t
+    h = np.asarray(hist)
+    hit = np.nonzero(h <= drop * h[0])[0]
+    W64 = s.get_state()[0]
+    s.close()
+    out["fp64"] = {"converged": bool(hit.size), "iterations": int(hit[0]) + 1 if hit.size else len(h),
+                   "cycles_run": len(h), "wall_s": el, "res_first": float(h[0]),
+                   "res_min_drop": float(h.min() / h[0]),
+                   "history": [float(x / h[0]) for x in h[::max(1, len(h) // 30)]]}
+    s = cgks.Solver(gm, dict(spec, precision="mixed"))
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hm = s.pmg_cycle(len(h))
+    el = time.perf_counter() - t
+    Wm = s.get_state()[0]
+    s.close()
+    hit = np.nonzero(hm <= drop * hm[0])[0]
+    out["mixed"] = {"cycles": len(h), "wall_s": el, "res_floor": float(hm.min() / hm[0]),
+                    "iterations_to_drop": int(hit[0]) + 1 if hit.size else None,
+                    "field_rel_l2_vs_fp64": float(np.linalg.norm(Wm - W64) / np.linalg.norm(W64)),
+                    "history": [float(x / hm[0]) for x in hm[::max(1, len(hm) // 30)]]}
+    return out
+
+
 def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=100000):
     """Wall time to a 1e-8 drop of Res relative to its first value:
     p-multigrid (S1O2 high-order step) vs explicit S2O4."""
@@ -730,7 +797,25 @@ def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=100000
                       "wall_s_to_drop": el * (n_hit / its) if done else None,
                       "res_first": first, "res_last": hist[-1], "res_min": float(h.min()),
                       "history": [float(x) for x in h[::max(1, len(h) // 40)]]}
+        if label == "pmg":
+            W64, pmg_its = s.get_state()[0], its
         s.close()
+    # mixed precision on the same cycles: its residual floor and its field
+    # against the FP64 field (which tracks the FP64 oracle per cycle)
+    s = cgks.Solver(cgks.Mesh(mesh), dict(spec, precision="mixed"))
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hm = s.pmg_cycle(pmg_its)
+    el = time.perf_counter() - t
+    Wm = s.get_state()[0]
+    s.close()
+    hit = np.nonzero(hm <= drop * hm[0])[0]
+    out["pmg_mixed"] = {"cycles": pmg_its, "wall_s": el, "res_first": float(hm[0]),
+                        "res_floor": float(hm.min() / hm[0]),
+                        "iterations_to_drop": int(hit[0]) + 1 if hit.size else None,
+                        "field_rel_l2_vs_fp64": float(np.linalg.norm(Wm - W64) / np.linalg.norm(W64)),
+                        "history": [float(x) for x in hm[::max(1, len(hm) // 40)]]}
     if out["pmg"]["converged"] and out["explicit_S2O4"]["converged"]:
         out["speedup"] = out["explicit_S2O4"]["wall_s_to_drop"] / out["pmg"]["wall_s_to_drop"]
     elif out["pmg"]["converged"]:
