@@ -200,7 +200,8 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     import torch
     if steps is not None:
         args = argparse.Namespace(**dict(vars(args), steps=steps))
-    sp = dict(spec, precision=precision, autotune=0 if args.no_autotune else 1)
+    sp = dict(spec, precision=precision, autotune=0 if args.no_autotune else 1,
+              programmatic_launch=0 if args.no_programmatic_launch else 1)
     solver = cgks.Solver(gm, sp)
     if args.tune_shapes:
         solver.set_tuning([int(x) for x in args.tune_shapes.split(",")])
@@ -512,6 +513,8 @@ def main():
     ap.add_argument("--converge", action="store_true", help="also time p-MG vs explicit S2O4 to a 1e-8 drop")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D sphere workloads")
     ap.add_argument("--no-autotune", action="store_true", help="fixed default launch shapes")
+    ap.add_argument("--no-programmatic-launch", action="store_true",
+                    help="plain stream-ordered launches instead of programmatic dependent launch")
     ap.add_argument("--tune-shapes", default="",
                     help="fix the launch shapes of k_recon,k_face,k_lo_face,k_sweep (e.g. 1,4,1,1; for profiling)")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-1e-8 comparison")

@@ -95,6 +95,10 @@ typedef struct {
                             0 (default): one graph-replayed kernel per phase, faster on GB300 */
   int32_t autotune;      /* 1 (default): the block-size autotuner picks the launch shapes (see
                             cgks_get_tuning); 0: the fixed default shapes */
+  int32_t programmatic_launch; /* 1 (default): each kernel of a cycle may be scheduled while its
+                            predecessor runs and waits on the device for it (programmatic
+                            dependent launch, sm_90+); 0: plain stream order.  Same results. */
+  int32_t pad_;
   cgks_bc bc[CGKS_MAX_BC];
   void *stream;          /* cudaStream_t for all device work (NULL = default) */
   cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */
@@ -114,7 +118,7 @@ typedef struct cgks_solver cgks_solver;
 
 /* Fill p with the defaults above (gamma 1.4, Euler, CFL 0.4 / 1000,
  * 6 implicit steps, 2 sweeps, S1O2, FP64, graphs on, autotune on,
- * per-phase low-order launches, no boundaries). */
+ * programmatic launch on, per-phase low-order launches, no boundaries). */
 void cgks_default_params(cgks_params *p);
 
 /* Build a mesh from nodes, cells and tagged boundary faces (the finite-
@@ -218,7 +222,7 @@ typedef struct {
   int32_t use_graph;
   int32_t low_order_fused; /* 1: persistent cooperative low-order level */
   int32_t autotune;      /* 1 (default): autotuned launch shapes for the batch */
-  int32_t pad_;
+  int32_t programmatic_launch; /* 1 (default): programmatic dependent launch (see cgks_params) */
   void *stream;          /* cudaStream_t (NULL = default) */
   cgks_alloc_fn alloc;
   cgks_free_fn free;
@@ -237,7 +241,7 @@ typedef struct {
 } cgks_req_status;
 
 /* Fill opts with defaults (FP64, S1O2, CFL 0.4 / 1000, 6 x 2, 64 active,
- * 20000 cycles, graphs on, autotune on). */
+ * 20000 cycles, graphs on, autotune on, programmatic launch on). */
 void cgks_server_default_opts(cgks_server_opts *o);
 int cgks_server_create(size_t hbm_budget, const cgks_server_opts *opts, cgks_server **out);
 /* Queue a request.  The mesh and W0 ([n_cells*4], caller order, host) are

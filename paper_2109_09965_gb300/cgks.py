@@ -48,7 +48,8 @@ class CgksParams(C.Structure):
                 ("cfl_hi", C.c_double), ("cfl_lo", C.c_double),
                 ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32), ("time_scheme", C.c_int32),
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
-                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("bc", CgksBC * MAX_BC),
+                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
+                ("pad_", C.c_int32), ("bc", CgksBC * MAX_BC),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -189,7 +190,7 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     for key in ("gamma", "mu", "alpha", "cfl_hi", "cfl_lo"):
         if key in spec:
             setattr(P, key, float(spec[key]))
-    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune"):
+    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch"):
         if key in spec:
             setattr(P, key, int(spec[key]))
     P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
@@ -361,7 +362,7 @@ class CgksServerOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("time_scheme", C.c_int32), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32),
                 ("max_active", C.c_int32), ("max_cycles", C.c_int32), ("use_graph", C.c_int32),
-                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("pad_", C.c_int32),
+                ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -403,7 +404,7 @@ class Server:
         for key in ("cfl_hi", "cfl_lo"):
             if key in kw:
                 setattr(o, key, float(kw[key]))
-        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune"):
+        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch"):
             if key in kw:
                 setattr(o, key, int(kw[key]))
         self._alloc = None

@@ -47,7 +47,7 @@ struct Bufs {
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
   int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 0;
-  int autotune = 1;
+  int autotune = 1, pdl = 1;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -152,7 +152,7 @@ void launch(Batch *b, int id, Kern kern, dim3 grid, dim3 block, Args... args) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, b->stream);
   }
-  kern<<<grid, block, 0, b->stream>>>(args...);
+  launch_on(b->stream, b->sh.pdl != 0, kern, grid, block, args...);
   if (t) {
     cudaEventRecord(e1, b->stream);
     b->timer->ev.push_back({ id, { e0, e1 } });
@@ -888,6 +888,7 @@ Shared shared_from(const cgks_params *p) {
   sh.n_implicit = p->n_implicit; sh.n_sweeps = p->n_sweeps; sh.time_scheme = p->time_scheme;
   sh.precision = p->precision; sh.use_graph = p->use_graph; sh.lo_fused = p->low_order_fused;
   sh.autotune = p->autotune;
+  sh.pdl = p->programmatic_launch;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -1033,6 +1034,7 @@ void cgks_default_params(cgks_params *p) {
   p->use_graph = 1;
   p->low_order_fused = 0;
   p->autotune = 1;
+  p->programmatic_launch = 1;
 }
 
 const char *cgks_strerror(int st) {
@@ -1408,6 +1410,7 @@ void cgks_server_default_opts(cgks_server_opts *o) {
   o->use_graph = 1;
   o->low_order_fused = 0;
   o->autotune = 1;
+  o->programmatic_launch = 1;
 }
 
 // Faces per cell the batch capacity provides for (2-D: triangles 1.5,
@@ -1429,6 +1432,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->sh.time_scheme = o->time_scheme; v->sh.precision = o->precision; v->sh.use_graph = o->use_graph;
   v->sh.lo_fused = o->low_order_fused;
   v->sh.autotune = o->autotune;
+  v->sh.pdl = o->programmatic_launch;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;

@@ -93,7 +93,7 @@ void launch(Solver3 *s, int id, Kern kern, dim3 grid, dim3 block, Args... args) 
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s->stream);
   }
-  kern<<<grid, block, 0, s->stream>>>(args...);
+  launch_on(s->stream, s->P.programmatic_launch != 0, kern, grid, block, args...);
   if (t) {
     cudaEventRecord(e1, s->stream);
     s->timer->ev.push_back({ id, { e0, e1 } });

@@ -23,6 +23,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_physics.cuh"
+#include "cgks_pdl.cuh"
 #include "cgks_shapes.h"
 
 namespace cgks {
@@ -103,8 +104,10 @@ __device__ __forceinline__ void block_sum2(double a, double b, double *out2) {
 // ------------------------------------------------------------------
 // K0: reset the per-solve time steps
 __global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, int S, double dt_fixed) {
+  pdl_enter();
   for (int s = threadIdx.x; s < S; s += blockDim.x) dt_bits[s] = 0x7ff0000000000000ull;  // +inf
   if (threadIdx.x == 0) ctl->dt_fixed = dt_fixed;
+  pdl_exit();
 }
 
 // K4: local explicit step per cell, per-solve min by atomicMin on the bits
@@ -113,6 +116,7 @@ __global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, int S, double 
 // its first cell is a real one: one atomic per block.
 __global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
                                                    unsigned long long *dt_bits) {
+  pdl_enter();
   __shared__ double wmin[kCellBlock / 32];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = INFINITY;
@@ -135,6 +139,7 @@ __global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<doub
     const int s0 = blockIdx.x * blockDim.x < m.nc ? m.csid[blockIdx.x * blockDim.x] : -1;
     if (s0 >= 0 && d < INFINITY) atomicMin(&dt_bits[s0], static_cast<unsigned long long>(__double_as_longlong(d)));
   }
+  pdl_exit();
 }
 
 // Wall ghost of a state and its gradient (global frame), through the face frame.
@@ -215,7 +220,9 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_recon(MeshT<T>
                                                                         const T *__restrict__ W,
                                                                         const T *__restrict__ Wx,
                                                                         T *__restrict__ coef) {
+  pdl_enter();
   for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
+  pdl_exit();
 }
 
 // value and gradient of the quadratic of cell i at scaled offset (x, y)
@@ -321,7 +328,9 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_face(MeshT<T> 
                                                                        const T *__restrict__ W,
                                                                        const T *__restrict__ coef,
                                                                        T *__restrict__ out) {
+  pdl_enter();
   for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
+  pdl_exit();
 }
 
 // K3 modes
@@ -341,6 +350,7 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
                                                        double *__restrict__ Wout, double *__restrict__ Wxout,
                                                        double *__restrict__ partial, double *__restrict__ Rout,
                                                        TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc, nf = m.nf;
   double num = 0.0, den = 0.0;
@@ -396,6 +406,7 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
     }
   }
   if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
+  pdl_exit();
 }
 
 // Sum each solve's block partials in a fixed order (one block per solve
@@ -403,6 +414,7 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
 // also appends to the residual history.
 __global__ void k_res_final(const double *__restrict__ partial, const int *__restrict__ blk, Ctl *ctl,
                             double *__restrict__ res, double *hist, int cap, double *last) {
+  pdl_enter();
   const int s = blockIdx.x;
   double a = 0.0, b = 0.0;
   for (int k = blk[2 * s] + threadIdx.x; k < blk[2 * s + 1]; k += blockDim.x) {
@@ -422,6 +434,7 @@ __global__ void k_res_final(const double *__restrict__ partial, const int *__res
       ctl->res_ctr = c + 1;
     }
   }
+  pdl_exit();
 }
 
 // ---------------------------- low-order level ----------------------------
@@ -432,6 +445,7 @@ template <typename TF>
 __global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
                                                         double *__restrict__ U, const TF *__restrict__ dU,
                                                         TF *__restrict__ prim, TF *__restrict__ Um) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   TF w[4];
@@ -445,6 +459,7 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, in
   prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.p;
   prim[4 * n + i] = q.i2l; prim[5 * n + i] = q.sl; prim[6 * n + i] = q.isp; prim[7 * n + i] = q.c;
   prim[8 * n + i] = q.ir;
+  pdl_exit();
 }
 
 template <typename T>
@@ -460,26 +475,48 @@ __device__ __forceinline__ D::Prim<T> load_prim(const T *__restrict__ prim, int 
 // and (FP64 mode) the Euler normal fluxes F_n(U_c0), F_n(U_c1) the
 // relaxation reuses.
 template <typename T>
-__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ U,
-                                           const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam,
-                                           T *__restrict__ E0, T *__restrict__ E1, const int f) {
-  const int sid = m.fsid[f];
-  if (sid < 0) return;   // free face space of a batch
+struct LoFaceGeo {
+  int sid, c0, c1;
+  T nx, ny, S, mu, iva, ivb;
+};
+// mesh and per-solve data of face f (nothing in a cycle writes them)
+template <typename T>
+__device__ __forceinline__ LoFaceGeo<T> lo_face_geo(const MeshT<T> &m, const ParamsT<T> &P, const int f) {
+  LoFaceGeo<T> g;
+  g.sid = m.fsid[f];
+  g.c0 = g.c1 = 0;
+  g.nx = g.ny = g.S = g.mu = g.iva = g.ivb = T(0);
+  if (g.sid < 0) return g;
+  const int nf = m.nf;
+  g.c0 = m.fc0[f];
+  g.c1 = m.fc1[f];
+  g.nx = m.fn[f];
+  g.ny = m.fn[nf + f];
+  g.S = m.fS[f];
+  g.mu = P.mu[g.sid];
+  g.iva = m.ivol[g.c0];
+  g.ivb = g.c1 >= 0 ? m.ivol[g.c1] : g.iva;
+  return g;
+}
+template <typename T>
+__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const LoFaceGeo<T> &g,
+                                           const T *__restrict__ U, const T *__restrict__ prim,
+                                           T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0,
+                                           T *__restrict__ E1, const int f) {
+  if (g.sid < 0) return;   // free face space of a batch
   const int n = m.nc, nf = m.nf;
-  const int c0 = m.fc0[f], c1 = m.fc1[f];
-  const T nx = m.fn[f], ny = m.fn[nf + f], S = m.fS[f];
-  const T mu = P.mu[sid];
+  const int c0 = g.c0, c1 = g.c1;
+  const T nx = g.nx, ny = g.ny, S = g.S;
+  const T mu = g.mu;
   D::Prim<T> a = load_prim(prim, n, c0), b;
-  T ivb;
+  const T ivb = g.ivb;
   if (c1 >= 0) {
     b = load_prim(prim, n, c1);
-    ivb = m.ivol[c1];
   } else {
     T w0[4], wg[4];
     for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
     lo_ghost(P, -1 - c1, nx, ny, w0, wg);
     b = D::prim_of(wg, P.gamma, P.kc);
-    ivb = m.ivol[c0];
   }
   const T una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
   const T unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
@@ -487,7 +524,7 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
   D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
   D::rot_out(nx, ny, Fl, F);
   for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
-  const T la = fabs(una) + a.c + T(2) * (mu * a.ir) * S * m.ivol[c0];
+  const T la = fabs(una) + a.c + T(2) * (mu * a.ir) * S * g.iva;
   const T lb = fabs(unb) + b.c + T(2) * (mu * b.ir) * S * ivb;
   lam[f] = la > lb ? la : lb;
   if (E0) {
@@ -510,7 +547,9 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_lo_face(MeshT<
                                                                           const T *__restrict__ prim,
                                                                           T *__restrict__ Flo, T *__restrict__ lam,
                                                                           T *__restrict__ E0, T *__restrict__ E1) {
-  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, U, prim, Flo, lam, E0, E1, f); });
+  for_items_pdl<SH>(m.nf, [&](int f) { return lo_face_geo(m, P, f); },
+                    [&](int f, const LoFaceGeo<T> &g) { lo_face_at(m, P, g, U, prim, Flo, lam, E0, E1, f); });
+  pdl_exit();
 }
 
 // K6: low-order right-hand side R^k = R_lo(U^k) + S (FP64 sums), 1/D_i
@@ -525,15 +564,26 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
                                                        TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
                                                        TF *__restrict__ lamS) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.nc) return;
+  if (i >= m.nc) { pdl_enter(); return; }
   const int n = m.nc, nf = m.nf;
-  double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
+  // mesh data first (nothing in a cycle writes it), then wait for the predecessor
+  int fsl[kMaxFace];
+  double Sl[kMaxFace];
+#pragma unroll
   for (int s = 0; s < kMaxFace; ++s) {
-    int fs = m.cface[s * n + i];
+    fsl[s] = m.cface[s * n + i];
+    Sl[s] = fsl[s] == kNoFace ? 0.0 : m.fS[fsl[s] >= 0 ? fsl[s] : ~fsl[s]];
+  }
+  const bool c0 = colour0 && m.ccol[i] == 0;
+  pdl_enter();
+  double R[4] = { 0, 0, 0, 0 }, sum = 0.0;
+#pragma unroll
+  for (int s = 0; s < kMaxFace; ++s) {
+    int fs = fsl[s];
     if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
     int f = fs >= 0 ? fs : ~fs;
     double sg = fs >= 0 ? 1.0 : -1.0;
-    double S = m.fS[f];
+    double S = Sl[s];
     for (int v = 0; v < 4; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
     TF l = lam[f];
     lamS[s * n + i] = l;
@@ -542,7 +592,6 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
   // dt_i = CFL_lo |Omega| / sum;  D_i = |Omega| / dt_i + sum / 2 (padding cells: 0)
   const double id = sum > 0.0 ? 1.0 / (sum / P.cfl_lo + 0.5 * sum) : 0.0;
   invD[i] = static_cast<TF>(id);
-  const bool c0 = colour0 && m.ccol[i] == 0;
   for (int v = 0; v < 4; ++v) {
     double src;
     if (first) { src = Rp0[v * n + i] - R[v]; Src[v * n + i] = src; }
@@ -551,6 +600,7 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
     Rk[v * n + i] = static_cast<TF>(r);
     dU[v * n + i] = c0 ? static_cast<TF>(r * id) : TF(0);
   }
+  pdl_exit();
 }
 
 // The cells of one colour form one contiguous range per solve.  A sweep
@@ -590,18 +640,48 @@ __device__ __forceinline__ int range_cell(const Ranges &R, int cl, int cpb) {
 // group, and lane v writes component v.  Cells of one colour never
 // neighbour each other, so the dU_ip read here are not written by this
 // launch.
+// static (mesh) data of one lane of a sweep: the neighbour across face
+// slot s of cell i and the slot geometry; read before the kernel waits on
+// its predecessor, since no kernel of a cycle writes it
 template <typename T>
-__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const int i, const int s,
-                                           const T *__restrict__ U, const T *__restrict__ prim,
-                                           const T *__restrict__ Rk, const T *__restrict__ invD,
-                                           const T *__restrict__ lamS, const T *__restrict__ E0,
-                                           const T *__restrict__ E1, T *__restrict__ dU) {
+struct SweepGeo {
+  int j, f;
+  bool is0;
+  T nx, ny, hS;
+};
+template <typename T>
+__device__ __forceinline__ SweepGeo<T> sweep_geo(const MeshT<T> &m, const int i, const int s) {
+  const int n = m.nc;
+  SweepGeo<T> g;
+  g.j = i >= 0 ? m.cnbr[s * n + i] : -1;
+  g.f = 0;
+  g.is0 = true;
+  g.nx = g.ny = g.hS = T(0);
+  if (g.j >= 0) {
+    g.nx = m.snx[s * n + i];
+    g.ny = m.sny[s * n + i];
+    g.hS = m.shs[s * n + i];
+    if constexpr (!is_f32<T>()) {
+      const int fs = m.cface[s * n + i];
+      g.is0 = fs >= 0;
+      g.f = g.is0 ? fs : ~fs;
+    }
+  }
+  return g;
+}
+template <typename T>
+__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
+                                           const int i, const int s, const T *__restrict__ U,
+                                           const T *__restrict__ prim, const T *__restrict__ Rk,
+                                           const T *__restrict__ invD, const T *__restrict__ lamS,
+                                           const T *__restrict__ E0, const T *__restrict__ E1,
+                                           T *__restrict__ dU) {
   const int n = m.nc, nf = m.nf;
+  const int j = g.j;
   // every lane stays to the shuffles; lanes of absent cells or slots add 0
-  const int j = i >= 0 ? m.cnbr[s * n + i] : -1;
   T c[4] = { T(0), T(0), T(0), T(0) };
   if (j >= 0) {
-    const T nx = m.snx[s * n + i], ny = m.sny[s * n + i], hS = m.shs[s * n + i], lp = lamS[s * n + i];
+    const T nx = g.nx, ny = g.ny, hS = g.hS, lp = lamS[s * n + i];
     T uj[4], du[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
@@ -611,16 +691,14 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
 #pragma unroll
       for (int v = 0; v < 4; ++v) c[v] = hS * (dF[v] - lp * du[v]);
     } else {
-      const int fs = m.cface[s * n + i];
-      const bool is0 = fs >= 0;
-      const int f = is0 ? fs : ~fs;
+      const int f = g.f;
       T up[4], fa[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) up[v] = uj[v] + du[v];
       D::euler_flux(P.gamma, up, nx, ny, fa);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        const T fb = g.is0 ? E1[v * nf + f] : -E0[v * nf + f];
         c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
       }
     }
@@ -646,10 +724,12 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_sweep(MeshT<T>
                                                                         const T *__restrict__ lamS,
                                                                         const T *__restrict__ E0,
                                                                         const T *__restrict__ E1, T *__restrict__ dU) {
-  constexpr int kGroups = shape_bs(SH) / kMaxFace, kCpb = sweep_cpb(SH);
+  constexpr int kGroups = shape_bs(SH) / kMaxFace, kCpb = sweep_cpb(SH), kIpt = shape_ipt(SH);
   const int s = threadIdx.x & (kMaxFace - 1);
+  // one copy of the per-cell code for every shape (the same arithmetic);
+  // the first item's mesh data is read before the wait, later items' after
 #pragma unroll 1
-  for (int k = 0; k < shape_ipt(SH); ++k) {
+  for (int k = 0; k < kIpt; ++k) {
     const int cl = k * kGroups + static_cast<int>(threadIdx.x) / kMaxFace;
     int i;
     if (list) {
@@ -658,8 +738,11 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_sweep(MeshT<T>
     } else {
       i = range_cell(R, cl, kCpb);
     }
-    sweep_cell(m, P, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
+    const SweepGeo<T> geo = sweep_geo(m, i, s);
+    pdl_enter();
+    sweep_cell(m, P, geo, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
   }
+  pdl_exit();
 }
 
 // K9: prolongation W = W_p0 + (U - W_p0) (Section 3, step 5), density
@@ -669,6 +752,7 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT
                                                         const double *__restrict__ Wp0, const double *__restrict__ U,
                                                         int *status, double *__restrict__ partial,
                                                         TF *__restrict__ Wm) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc;
   double num = 0.0, den = 0.0;
@@ -689,6 +773,7 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT
     }
   }
   block_sum2(num, den, &partial[2 * blockIdx.x]);
+  pdl_exit();
 }
 
 // Caller AoS order <-> internal SoA order for the n cells of one solve

@@ -13,6 +13,7 @@
 
 #include "cgks_internal.h"
 #include "cgks_physics3.cuh"
+#include "cgks_pdl.cuh"
 #include "cgks_shapes.h"
 
 namespace cgks {
@@ -89,12 +90,15 @@ __device__ __forceinline__ D3::Frame<T> frame_of(const MeshT<T> &m, int f) {
 
 // ------------------------------------------------------------------
 __global__ void k_reset_dt(Ctl *ctl, unsigned long long *dt_bits, double dt_fixed) {
+  pdl_enter();
   if (threadIdx.x == 0) { *dt_bits = 0x7ff0000000000000ull; ctl->dt_fixed = dt_fixed; }
+  pdl_exit();
 }
 
 // explicit step: min over cells of h / (|U| + c + 2 nu / h), h = 3|Omega| / sum S
 __global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<double> P, const double *__restrict__ W,
                                                    unsigned long long *dt_bits) {
+  pdl_enter();
   __shared__ double wmin[kCellBlock / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = INFINITY;
@@ -114,6 +118,7 @@ __global__ void __launch_bounds__(kCellBlock) k_dt(MeshT<double> m, ParamsT<doub
     for (int k = 1; k < kCellBlock / 32; ++k) d = fmin(d, wmin[k]);
     if (d < INFINITY) atomicMin(dt_bits, static_cast<unsigned long long>(__double_as_longlong(d)));
   }
+  pdl_exit();
 }
 
 // wall ghost of a state and its gradient (global), through the face frame
@@ -217,7 +222,9 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef) {
+  pdl_enter();
   for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
+  pdl_exit();
 }
 
 // value and gradient of cell i's quadratic at scaled offset x
@@ -337,7 +344,9 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out) {
+  pdl_enter();
   for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
+  pdl_exit();
 }
 
 enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
@@ -358,6 +367,7 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
                                                        double *__restrict__ Wout, double *__restrict__ Wxout,
                                                        double *__restrict__ partial, double *__restrict__ Rout,
                                                        TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc, nf = m.nf;
   double num = 0.0, den = 0.0;
@@ -415,10 +425,12 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
     }
   }
   if (partial) block_sum2(num, den, &partial[2 * blockIdx.x]);
+  pdl_exit();
 }
 
 __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Ctl *ctl, double *hist, int cap,
                             double *last) {
+  pdl_enter();
   double a = 0.0, b = 0.0;
   for (int k = threadIdx.x; k < nblocks; k += blockDim.x) { a += partial[2 * k]; b += partial[2 * k + 1]; }
   __shared__ double tot[2];
@@ -431,6 +443,7 @@ __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Ctl
     if (hist && c < cap) hist[c] = r;
     ctl->res_ctr = c + 1;
   }
+  pdl_exit();
 }
 
 // ---------------------------- low-order level ----------------------------
@@ -438,6 +451,7 @@ template <typename TF>
 __global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
                                                         double *__restrict__ U, const TF *__restrict__ dU,
                                                         TF *__restrict__ prim, TF *__restrict__ Um) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   TF w[NV];
@@ -452,6 +466,7 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, in
   prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.w;
   prim[4 * n + i] = q.p; prim[5 * n + i] = q.i2l; prim[6 * n + i] = q.sl; prim[7 * n + i] = q.isp;
   prim[8 * n + i] = q.c; prim[9 * n + i] = q.ir;
+  pdl_exit();
 }
 
 template <typename T>
@@ -546,7 +561,9 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U, const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
+  pdl_enter();
   for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, U, prim, Flo, lam, E0, E1, f); });
+  pdl_exit();
 }
 
 // right-hand side R^k = R_lo + S (FP64 sums), 1/D_i (FP64), lambda per slot,
@@ -557,6 +574,7 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
                                                        const double *__restrict__ Rp0, double *__restrict__ Src,
                                                        TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
                                                        TF *__restrict__ lamS) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
   const int n = m.nc, nf = m.nf;
@@ -585,43 +603,73 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
     Rk[v * n + i] = static_cast<TF>(r);
     dU[v * n + i] = c0 ? static_cast<TF>(r * id) : TF(0);
   }
+  pdl_exit();
 }
 
 // point relaxation of the cells [begin, begin + count) of one colour, Eq.
 // (implicit-local): 8 lanes per cell, one per face slot (6 used); the five
 // terms are summed over the lane group by shuffles, lane v writes
 // component v.
+// static (mesh) data of one lane of a sweep: neighbour across face slot s
+// of cell i and the slot geometry; read before the kernel waits on its
+// predecessor, since no kernel of a cycle writes it
 template <typename T>
-__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const int i, const int s,
-                                           const T *__restrict__ U, const T *__restrict__ prim,
-                                           const T *__restrict__ Rk, const T *__restrict__ invD,
-                                           const T *__restrict__ lamS, const T *__restrict__ E0,
-                                           const T *__restrict__ E1, T *__restrict__ dU) {
+struct SweepGeo {
+  int j, f;
+  bool is0;
+  T nn[3], hS;
+};
+template <typename T>
+__device__ __forceinline__ SweepGeo<T> sweep_geo(const MeshT<T> &m, const int i, const int s) {
+  const int n = m.nc;
+  SweepGeo<T> g;
+  g.j = (i >= 0 && s < kMaxFace3) ? m.cnbr[s * n + i] : -1;
+  g.f = 0;
+  g.is0 = true;
+  g.nn[0] = g.nn[1] = g.nn[2] = g.hS = T(0);
+  if (g.j >= 0) {
+    g.nn[0] = m.sn[(3 * s) * n + i];
+    g.nn[1] = m.sn[(3 * s + 1) * n + i];
+    g.nn[2] = m.sn[(3 * s + 2) * n + i];
+    g.hS = m.shs[s * n + i];
+    if constexpr (!is_f32<T>()) {
+      const int fs = m.cface[s * n + i];
+      g.is0 = fs >= 0;
+      g.f = g.is0 ? fs : ~fs;
+    }
+  }
+  return g;
+}
+template <typename T>
+__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
+                                           const int i, const int s, const T *__restrict__ U,
+                                           const T *__restrict__ prim, const T *__restrict__ Rk,
+                                           const T *__restrict__ invD, const T *__restrict__ lamS,
+                                           const T *__restrict__ E0, const T *__restrict__ E1,
+                                           T *__restrict__ dU) {
   const int n = m.nc, nf = m.nf;
-  const int j = (i >= 0 && s < kMaxFace3) ? m.cnbr[s * n + i] : -1;
+  const int j = g.j;
   T c[NV] = { T(0), T(0), T(0), T(0), T(0) };
   if (j >= 0) {
-    const T nn[3] = { m.sn[(3 * s) * n + i], m.sn[(3 * s + 1) * n + i], m.sn[(3 * s + 2) * n + i] };
-    const T hS = m.shs[s * n + i], lp = lamS[s * n + i];
+    const T hS = g.hS, lp = lamS[s * n + i];
     T uj[NV], du[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
     if constexpr (is_f32<T>()) {
       T dF[NV];
-      D3::euler_flux_delta(P.gamma, uj, prim[n + j], prim[2 * n + j], prim[3 * n + j], prim[4 * n + j], du, nn, dF);
+      D3::euler_flux_delta(P.gamma, uj, prim[n + j], prim[2 * n + j], prim[3 * n + j], prim[4 * n + j], du, g.nn,
+                           dF);
 #pragma unroll
       for (int v = 0; v < NV; ++v) c[v] = hS * (dF[v] - lp * du[v]);
     } else {
-      const int fs = m.cface[s * n + i];
-      const bool is0 = fs >= 0;
-      const int f = is0 ? fs : ~fs;
+      const int f = g.f;
       T up[NV], fa[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) up[v] = uj[v] + du[v];
-      D3::euler_flux(P.gamma, up, nn, fa);
+      D3::euler_flux(P.gamma, up, g.nn, fa);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T fb = is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        const T fb = g.is0 ? E1[v * nf + f] : -E0[v * nf + f];
         c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
       }
     }
@@ -644,13 +692,19 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count, const T *__restrict__ U, const T *__restrict__ prim,
             const T *__restrict__ Rk, const T *__restrict__ invD, const T *__restrict__ lamS,
             const T *__restrict__ E0, const T *__restrict__ E1, T *__restrict__ dU) {
-  constexpr int kGroups = shape_bs(SH) / kSweepLanes;
+  constexpr int kGroups = shape_bs(SH) / kSweepLanes, kIpt = shape_ipt(SH);
   const int s = threadIdx.x & (kSweepLanes - 1);
+  // one copy of the per-cell code for every shape (the same arithmetic);
+  // the first item's mesh data is read before the wait, later items' after
 #pragma unroll 1
-  for (int k = 0; k < shape_ipt(SH); ++k) {
-    const int g = (static_cast<int>(blockIdx.x) * shape_ipt(SH) + k) * kGroups + static_cast<int>(threadIdx.x) / kSweepLanes;
-    sweep_cell(m, P, g < count ? begin + g : -1, s, U, prim, Rk, invD, lamS, E0, E1, dU);
+  for (int k = 0; k < kIpt; ++k) {
+    const int g = (static_cast<int>(blockIdx.x) * kIpt + k) * kGroups + static_cast<int>(threadIdx.x) / kSweepLanes;
+    const int i = g < count ? begin + g : -1;
+    const SweepGeo<T> geo = sweep_geo(m, i, s);
+    pdl_enter();
+    sweep_cell(m, P, geo, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
   }
+  pdl_exit();
 }
 
 // W = W_p0 + (U - W_p0), density residual partials, state check
@@ -659,6 +713,7 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT
                                                         const double *__restrict__ Wp0, const double *__restrict__ U,
                                                         int *status, double *__restrict__ partial,
                                                         TF *__restrict__ Wm) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = m.nc;
   double num = 0.0, den = 0.0;
@@ -677,6 +732,7 @@ __global__ void __launch_bounds__(kCellBlock) k_prolong(MeshT<double> m, ParamsT
     den = old;
   }
   block_sum2(num, den, &partial[2 * blockIdx.x]);
+  pdl_exit();
 }
 
 // caller AoS <-> internal SoA

@@ -44,6 +44,25 @@ inline void collect_timing(Timer *t) {
   t->ev.clear();
 }
 
+// Launch a kernel on st; with pdl, as a programmatic dependent launch: the
+// kernel may be scheduled while its predecessor on st still runs and orders
+// itself after it on the device (every kernel launched this way calls
+// pdl_enter() before touching global memory).
+template <typename... Exp, typename... Act>
+void launch_on(cudaStream_t st, bool pdl, void (*kern)(Exp...), dim3 grid, dim3 block, Act... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- launch-shape autotuner ----
 // Each tunable kernel's first kRounds x kNShape tuning units (eager cycles
 // or explicit steps that launch it) use shape unit % kNShape; the first

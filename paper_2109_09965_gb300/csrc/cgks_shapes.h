@@ -28,6 +28,10 @@ static_assert(TK_COUNT == CGKS_TUNE_KERNELS, "tunable kernel count");
 constexpr int kDefaultShape[TK_COUNT] = { 2, 0, 2, 0 };
 
 #ifdef __CUDACC__
+}  // namespace cgks
+#include "cgks_pdl.cuh"
+namespace cgks {
+
 // the items of this thread in a launch of shape SH over n items
 template <int SH, typename F>
 __device__ __forceinline__ void for_items(const int n, F &&f) {
@@ -36,6 +40,25 @@ __device__ __forceinline__ void for_items(const int n, F &&f) {
     const int i = (static_cast<int>(blockIdx.x) * shape_ipt(SH) + k) * shape_bs(SH) + static_cast<int>(threadIdx.x);
     if (i < n) f(i);
   }
+}
+
+// The same, for a kernel launched as a programmatic dependent launch: geo(i)
+// reads the item's mesh data (which no kernel of a cycle writes), then the
+// thread waits for the predecessor kernel before f(i, g) touches anything
+// else.  Every thread waits, so the grid completes only after its
+// predecessor has.  One copy of the per-item code serves every shape.
+template <int SH, typename G, typename F>
+__device__ __forceinline__ void for_items_pdl(const int n, G &&geo, F &&f) {
+#pragma unroll 1
+  for (int k = 0; k < shape_ipt(SH); ++k) {
+    const int i = (static_cast<int>(blockIdx.x) * shape_ipt(SH) + k) * shape_bs(SH) + static_cast<int>(threadIdx.x);
+    if (i < n) {
+      const auto g = geo(i);
+      pdl_enter();
+      f(i, g);
+    }
+  }
+  pdl_enter();   // threads without items wait too: this grid ends after its predecessor
 }
 #endif
 

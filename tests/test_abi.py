@@ -49,10 +49,10 @@ def test_tune_shapes_and_defaults(cg):
             cg.tune_shape(bad)
     P = cg.CgksParams()
     cg.lib().cgks_default_params(C.byref(P))
-    assert P.autotune == 1 and P.low_order_fused == 0 and P.use_graph == 1
+    assert P.autotune == 1 and P.low_order_fused == 0 and P.use_graph == 1 and P.programmatic_launch == 1
     O = cg.CgksServerOpts()
     cg.lib().cgks_server_default_opts(C.byref(O))
-    assert O.autotune == 1 and O.max_active == 64
+    assert O.autotune == 1 and O.programmatic_launch == 1 and O.max_active == 64
 
 
 @pytest.mark.parametrize("mesh", [MG.cavity(8), MG.cylinder(24, 3, 5),

@@ -166,3 +166,26 @@ def test_server_batch_is_tuned(cg):
         s.set_state(W)
         s.pmg_cycle(K)
         assert np.array_equal(Wb, s.get_state()[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_programmatic_launch_is_bitwise_equal(cg, dim, precision):
+    """Programmatic dependent launch only moves when a kernel is scheduled;
+    each kernel still waits on the device for its predecessor, so cycles,
+    explicit steps and the server give identical results with it on or off,
+    replayed from a graph or launched one by one."""
+    if dim == 2:
+        mesh, spec, state = case("cylinder_viscous")
+    else:
+        mesh, spec, state = case3()
+    out = []
+    for pdl, graph in ((1, 1), (0, 1), (1, 0)):
+        s = cg.Solver(cg.Mesh(mesh), dict(spec, precision=precision, programmatic_launch=pdl, use_graph=graph))
+        s.set_state(*state)
+        h = s.pmg_cycle(UNITS + 4)
+        s.explicit_steps(3)
+        out.append((s.get_state(), h))
+    for (W, X), h in out[1:]:
+        assert np.array_equal(W, out[0][0][0]) and np.array_equal(X, out[0][0][1])
+        assert np.array_equal(h, out[0][1])
