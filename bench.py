@@ -637,6 +637,11 @@ SWEEP_FLOPS_PER_CELL = 4
 # spectral radii and Euler cache ~120; right-hand side of a cell ~50 (face
 # sums, 1/D); cell primitives ~25 (1 division, 2 square roots)
 LO_FACE_FLOPS, LO_RHS_FLOPS, LO_CELL_FLOPS = 120, 50, 25
+# FP64 operations per Gauss point of the 2-D smooth flux: 1163 for the
+# kinetic flux (302 add, 827 mul, 26 div, 4 sqrt, 2 exp, 2 erfc; counted on
+# an operation-counting number type) + ~330 for the two quadratic
+# evaluations, rotations and sums (2 Gauss points per face)
+FLOPS_PER_GP2 = 1490
 FP64_PEAK_TFLOPS = 1.25    # GB300: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 flops (recipe table)
 
 
@@ -669,14 +674,17 @@ def work_model(mesh, gm, spec, precision):
     sweep_flops = ni * sum(by_c[c][0] for c in seq)
     sweep_bytes = ni * sum(by_c[c][1] for c in seq)
     d = 8
+    # high-order evaluations per cycle: the step (1 in S1O2, 2 in S2O4) and R_p0
+    ev = 2 if spec.get("time_scheme", "S1O2") == "S1O2" else 3
     bytes_ = {
         "k_sweep": sweep_bytes,
         # W, Wx of every cell, operator (14 x 5), coef written (20), connectivity
-        "k_recon": n * ((12 + 70 + 20) * w + 32),
+        "k_recon": ev * n * ((12 + 70 + 20) * w + 32),
         # per cell coef + W + 1/h + second moments; per face geometry, flux sums written
-        "k_face": n * 28 * w + F * (27 * w + 12),
-        # face sums read once (16 in S1O2, 4 in the residual mode), geometry, W in, W/Wx out
-        "k_update": F * (16 + 4) * w + F * 3 * d + n * (16 + 2 * 4 * d + 2 * 8 * d),
+        "k_face": ev * (n * 28 * w + F * (27 * w + 12)),
+        # face sums (16 per face in a stage update, 4 in the residual mode),
+        # geometry, W in, W/Wx out; ev launches per cycle
+        "k_update": F * (16 * (ev - 1) + 4) * w + ev * (F * 3 * d + n * (16 + 2 * 4 * d + 2 * 8 * d)),
         "k_lo_face": ni * (n * 13 * w + F * (5 * w + 3 * w + 12 + (8 * w if precision == "fp64" else 0))),
         "k_lo_rhs": ni * (F * 6 * w + n * (16 + 4 * d + 13 * w + 4 * w)),
         "k_lo_cell": (ni + 1) * n * (8 * d + 4 * w + 9 * w),
@@ -685,7 +693,7 @@ def work_model(mesh, gm, spec, precision):
     lo_flops = sweep_flops + ni * (LO_FACE_FLOPS * F + LO_RHS_FLOPS * n) + (ni + 1) * LO_CELL_FLOPS * n
     bytes_["k_lo_solve"] = sum(bytes_[k] for k in ("k_sweep", "k_lo_face", "k_lo_rhs", "k_lo_cell"))
     return {"sweep_flops": sweep_flops, "lo_flops": lo_flops, "bytes": bytes_, "colours": C,
-            "sweep_launches": ni * len(seq)}
+            "sweep_launches": ni * len(seq), "face_flops": ev * F * 2 * FLOPS_PER_GP2}
 
 
 # DRAM bytes per k_sweep launch (read + write) from one ncu capture of this
@@ -702,6 +710,10 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
             continue
         s = ms / 1000.0 / steps
         per[k] = {"gbs": wm["bytes"][k] / s / 1e9, "frac_hbm": wm["bytes"][k] / s / 1e9 / hbm}
+        if precision == "fp64" and k in ("k_face", "k_sweep"):
+            fl = wm["face_flops"] if k == "k_face" else wm["sweep_flops"]
+            per[k]["fp64_tflops"] = fl / s / 1e12
+            per[k]["frac_fp64"] = fl / s / 1e12 / FP64_PEAK_TFLOPS
     top = max(kt, key=lambda k: kt[k][0])
     s_top = kt[top][0] / 1000.0 / steps
     if top == "k_face" and precision == "fp64" and "face_flops" in wm:
