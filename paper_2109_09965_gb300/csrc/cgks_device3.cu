@@ -26,7 +26,7 @@ inline int nblk(int64_t n, int b) { return static_cast<int>((n + b - 1) / b); }
 template <typename T>
 struct Bufs3 {
   T *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr, *U = nullptr;
-  T *coef = nullptr, *FA = nullptr, *FB = nullptr, *prim = nullptr, *Flo = nullptr, *lam = nullptr;
+  T *coef = nullptr, *FA = nullptr, *FB = nullptr, *rec = nullptr, *Flo = nullptr, *lam = nullptr;
   T *E0 = nullptr, *E1 = nullptr, *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
 };
 
@@ -171,12 +171,12 @@ void lo_solve(Solver3 *s) {
   const int colour0_end = s->P.n_sweeps > 0 ? s->colour_start[1] : 0;
   for (int k = 0; k < s->P.n_implicit; ++k) {
     launch(s, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(s->N), fpar<TF>(s), k == 0 ? 1 : 0,
-           (const double *)s->Wn, s->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
+           (const double *)s->Wn, s->U, (const TF *)B.dU, B.rec);
     tuned_launch(s->tune, TK_LOFACE, s->stream, [&] {
       with_shape(s->tune.shape(TK_LOFACE), [&](auto sh) {
         constexpr int S = decltype(sh)::value;
         launch(s, KI_LOFACE, k_lo_face<TF, S>, dim3(nblk(s->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-               fmesh<TF>(s), fpar<TF>(s), (const TF *)B.U, (const TF *)B.prim, B.Flo, B.lam, B.E0, B.E1);
+               fmesh<TF>(s), fpar<TF>(s), (const TF *)B.rec, B.Flo, B.lam, B.E0, B.E1);
       });
     });
     launch(s, KI_LORHS, k_lo_rhs<TF>, gc, blk, s->dm, s->dp, k == 0 ? 1 : 0, colour0_end, (const TF *)B.Flo,
@@ -187,7 +187,7 @@ void lo_solve(Solver3 *s) {
         with_shape(s->tune.shape(TK_SWEEP), [&](auto sh) {
           constexpr int S = decltype(sh)::value;
           launch(s, KI_SWEEP, k_sweep<TF, S>, dim3(nblk(cnt, sweep_cpb(S))), dim3(shape_bs(S)), fmesh<TF>(s),
-                 fpar<TF>(s), beg, cnt, (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
+                 fpar<TF>(s), beg, cnt, (const TF *)B.rec, (const TF *)B.Rk, (const TF *)B.invD,
                  (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, B.dU);
         });
       });
@@ -195,7 +195,7 @@ void lo_solve(Solver3 *s) {
   }
   if (s->P.n_implicit > 0)
     launch(s, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(s->N), fpar<TF>(s), 0, (const double *)s->Wn, s->U,
-           (const TF *)B.dU, B.prim, mirror<TF>(B.U));
+           (const TF *)B.dU, B.rec);
   else
     cudaMemcpyAsync(s->U, s->Wn, sizeof(double) * NV * s->N, cudaMemcpyDeviceToDevice, s->stream);
 }
@@ -275,15 +275,15 @@ void plan(Solver3 *s, std::vector<Piece3> &pc) {
   pc.push_back({ reinterpret_cast<void **>(&s->dt_bits), sizeof(unsigned long long) });
   if (!s->mixed) {
     Bufs3<double> &X = s->bd;
-    P8(&X.coef, kNM3 * NV * N); P8(&X.FA, 4 * NV * F); P8(&X.FB, 4 * NV * F); P8(&X.prim, D3::NPRIM * N);
+    P8(&X.coef, kNM3 * NV * N); P8(&X.FA, 4 * NV * F); P8(&X.FB, 4 * NV * F); P8(&X.rec, kRec * N);
     P8(&X.Flo, NV * F); P8(&X.lam, F); P8(&X.E0, NV * F); P8(&X.E1, NV * F); P8(&X.Rk, NV * N); P8(&X.invD, N);
-    P8(&X.dU, NV * N); P8(&X.lamS, kMaxFace3 * N);
+    P8(&X.dU, kDU * N); P8(&X.lamS, kMaxFace3 * N);
   } else {
     Bufs3<float> &X = s->bf;
     P4(&X.W, NV * N); P4(&X.Wx, 3 * NV * N); P4(&X.Wn, NV * N); P4(&X.Ws, NV * N); P4(&X.Wxs, 3 * NV * N);
-    P4(&X.U, NV * N); P4(&X.coef, kNM3 * NV * N); P4(&X.FA, 4 * NV * F); P4(&X.FB, 4 * NV * F);
-    P4(&X.prim, D3::NPRIM * N); P4(&X.Flo, NV * F); P4(&X.lam, F); P4(&X.Rk, NV * N); P4(&X.invD, N);
-    P4(&X.dU, NV * N); P4(&X.lamS, kMaxFace3 * N);
+    P4(&X.coef, kNM3 * NV * N); P4(&X.FA, 4 * NV * F); P4(&X.FB, 4 * NV * F);
+    P4(&X.rec, kRec * N); P4(&X.Flo, NV * F); P4(&X.lam, F); P4(&X.Rk, NV * N); P4(&X.invD, N);
+    P4(&X.dU, kDU * N); P4(&X.lamS, kMaxFace3 * N);
     P4(&g.f_ivol, N); P4(&g.f_ih, N); P4(&g.f_m2, 6 * N); P4(&g.f_op, kNCol3 * kNM3 * N); P4(&g.f_fe, 9 * F);
     P4(&g.f_fS, F); P4(&g.f_fjump, F); P4(&g.f_fw, 4 * F); P4(&g.f_fxi, 24 * F); P4(&g.f_sn, 3 * kMaxFace3 * N);
     P4(&g.f_shs, kMaxFace3 * N); P4(&g.f_bcuw, 3 * CGKS_MAX_BC); P4(&g.f_bcrho, CGKS_MAX_BC);
@@ -456,8 +456,8 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
                cudaMemsetAsync(s->status, 0, sizeof(int), stream) == cudaSuccess &&
                cudaMemsetAsync(s->Rp0, 0, sizeof(double) * NV * N, stream) == cudaSuccess &&
                cudaMemsetAsync(s->last, 0, sizeof(double) * 4, stream) == cudaSuccess &&
-               (s->mixed ? cudaMemsetAsync(s->bf.dU, 0, sizeof(float) * NV * N, stream)
-                         : cudaMemsetAsync(s->bd.dU, 0, sizeof(double) * NV * N, stream)) == cudaSuccess;
+               (s->mixed ? cudaMemsetAsync(s->bf.dU, 0, sizeof(float) * kDU * N, stream)
+                         : cudaMemsetAsync(s->bd.dU, 0, sizeof(double) * kDU * N, stream)) == cudaSuccess;
   ok = ok && cudaStreamSynchronize(stream) == cudaSuccess;
   if (!ok) { s3_destroy(S.release()); return CGKS_ECUDA; }
   fill_params(*p, s->dp);

@@ -447,35 +447,76 @@ __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Ctl
 }
 
 // ---------------------------- low-order level ----------------------------
+// Cell record of the low level, one per cell and implicit step: the
+// conservative state U in the flux precision and its primitives, 16 values
+// in one aligned run, so a neighbour's data costs one or two cache sectors
+// instead of one sector per value:
+//   [0..4] U, [5] u, [6] v, [7] w, [8] p, [9] rho, [10] 1/(2 lambda),
+//   [11] sqrt(lambda), [12] 1/sqrt(pi lambda), [13] c, [14] 1/rho, [15] 0.
+// A sweep reads only the first 8 (U and the velocity: 32 bytes in FP32).
+// The increments dU are stored the same way, 8 values per cell ([0..4],
+// then zeros).
+constexpr int kRec = 16, kDU = 8;
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; static constexpr int W = 4; };
+template <> struct VecOf<double> { using V = double2; static constexpr int W = 2; };
+// N values from a 16-byte aligned address (N a multiple of the vector width)
+template <typename T, int N>
+__device__ __forceinline__ void vload(const T *__restrict__ p, T out[N]) {
+  using V = typename VecOf<T>::V;
+  constexpr int W = VecOf<T>::W;
+  static_assert(N % W == 0, "whole vectors");
+#pragma unroll
+  for (int k = 0; k < N / W; ++k) {
+    const V x = reinterpret_cast<const V *>(p)[k];
+    const T *e = reinterpret_cast<const T *>(&x);
+#pragma unroll
+    for (int c = 0; c < W; ++c) out[k * W + c] = e[c];
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void vstore(T *__restrict__ p, const T in[N]) {
+  using V = typename VecOf<T>::V;
+  constexpr int W = VecOf<T>::W;
+  static_assert(N % W == 0, "whole vectors");
+#pragma unroll
+  for (int k = 0; k < N / W; ++k) {
+    V x;
+    T *e = reinterpret_cast<T *>(&x);
+#pragma unroll
+    for (int c = 0; c < W; ++c) e[c] = in[k * W + c];
+    reinterpret_cast<V *>(p)[k] = x;
+  }
+}
+template <typename T>
+__device__ __forceinline__ D3::Prim<T> rec_prim(const T r[kRec]) {
+  D3::Prim<T> q;
+  q.u = r[5]; q.v = r[6]; q.w = r[7]; q.p = r[8]; q.rho = r[9];
+  q.i2l = r[10]; q.sl = r[11]; q.isp = r[12]; q.c = r[13]; q.ir = r[14];
+  return q;
+}
+
+// U^{k+1} = U^k + dU (FP64), cell record of U^{k+1}; first: U = W_p0
 template <typename TF>
 __global__ void __launch_bounds__(kCellBlock) k_lo_cell(int n, ParamsT<TF> P, int first, const double *__restrict__ Wp0,
                                                         double *__restrict__ U, const TF *__restrict__ dU,
-                                                        TF *__restrict__ prim, TF *__restrict__ Um) {
+                                                        TF *__restrict__ rec) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  TF d[kDU];
+  if (!first) vload<TF, kDU>(dU + static_cast<size_t>(i) * kDU, d);
   TF w[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(dU[v * n + i]);
+    const double u = first ? Wp0[v * n + i] : U[v * n + i] + static_cast<double>(d[v]);
     U[v * n + i] = u;
     w[v] = static_cast<TF>(u);
-    if (Um) Um[v * n + i] = w[v];
   }
   const D3::Prim<TF> q = D3::prim_of(w, P.gamma, P.kc);
-  prim[0 * n + i] = q.rho; prim[1 * n + i] = q.u; prim[2 * n + i] = q.v; prim[3 * n + i] = q.w;
-  prim[4 * n + i] = q.p; prim[5 * n + i] = q.i2l; prim[6 * n + i] = q.sl; prim[7 * n + i] = q.isp;
-  prim[8 * n + i] = q.c; prim[9 * n + i] = q.ir;
+  const TF r[kRec] = { w[0], w[1], w[2], w[3], w[4], q.u, q.v, q.w, q.p, q.rho, q.i2l, q.sl, q.isp, q.c, q.ir, TF(0) };
+  vstore<TF, kRec>(rec + static_cast<size_t>(i) * kRec, r);
   pdl_exit();
-}
-
-template <typename T>
-__device__ __forceinline__ D3::Prim<T> load_prim(const T *__restrict__ prim, int n, int i) {
-  D3::Prim<T> q;
-  q.rho = prim[i]; q.u = prim[n + i]; q.v = prim[2 * n + i]; q.w = prim[3 * n + i]; q.p = prim[4 * n + i];
-  q.i2l = prim[5 * n + i]; q.sl = prim[6 * n + i]; q.isp = prim[7 * n + i]; q.c = prim[8 * n + i];
-  q.ir = prim[9 * n + i];
-  return q;
 }
 
 // ghost of a cell-mean state (zero gradients), global
@@ -508,21 +549,26 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, const D3:
 
 // KFVS flux, lambda_p = max of both sides, Euler flux cache (FP64 mode)
 template <typename T>
-__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ U, const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1, const int f) {
-  const int n = m.nc, nf = m.nf;
+__device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ rec,
+                                           T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0,
+                                           T *__restrict__ E1, const int f) {
+  const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T S = m.fS[f];
   const D3::Frame<T> F = frame_of(m, f);
-  D3::Prim<T> a = load_prim(prim, n, c0), b;
+  T ra[kRec], rb[kRec];
+  vload<T, kRec>(rec + static_cast<size_t>(c0) * kRec, ra);
+  D3::Prim<T> a = rec_prim(ra), b;
   T ivb;
   if (c1 >= 0) {
-    b = load_prim(prim, n, c1);
+    vload<T, kRec>(rec + static_cast<size_t>(c1) * kRec, rb);
+    b = rec_prim(rb);
     ivb = m.ivol[c1];
   } else {
-    T w0[NV], wg[NV];
+    T wg[NV];
+    lo_ghost(P, -1 - c1, F, ra, wg);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w0[v] = U[v * n + c0];
-    lo_ghost(P, -1 - c1, F, w0, wg);
+    for (int v = 0; v < NV; ++v) rb[v] = wg[v];
     b = D3::prim_of(wg, P.gamma, P.kc);
     ivb = m.ivol[c0];
   }
@@ -545,24 +591,25 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
     const T nx = F.e[0][0], ny = F.e[0][1], nz = F.e[0][2];
     const T una = la3[0], unb = lb3[0];
     E0[f] = a.rho * una;
-    E0[nf + f] = U[n + c0] * una + a.p * nx;
-    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
-    E0[3 * nf + f] = U[3 * n + c0] * una + a.p * nz;
-    E0[4 * nf + f] = (U[4 * n + c0] + a.p) * una;
+    E0[nf + f] = ra[1] * una + a.p * nx;
+    E0[2 * nf + f] = ra[2] * una + a.p * ny;
+    E0[3 * nf + f] = ra[3] * una + a.p * nz;
+    E0[4 * nf + f] = (ra[4] + a.p) * una;
     if (c1 >= 0) {
       E1[f] = b.rho * unb;
-      E1[nf + f] = U[n + c1] * unb + b.p * nx;
-      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
-      E1[3 * nf + f] = U[3 * n + c1] * unb + b.p * nz;
-      E1[4 * nf + f] = (U[4 * n + c1] + b.p) * unb;
+      E1[nf + f] = rb[1] * unb + b.p * nx;
+      E1[2 * nf + f] = rb[2] * unb + b.p * ny;
+      E1[3 * nf + f] = rb[3] * unb + b.p * nz;
+      E1[4 * nf + f] = (rb[4] + b.p) * unb;
     }
   }
 }
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
-    k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ U, const T *__restrict__ prim, T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0, T *__restrict__ E1) {
+    k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ rec, T *__restrict__ Flo, T *__restrict__ lam,
+              T *__restrict__ E0, T *__restrict__ E1) {
   pdl_enter();
-  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, U, prim, Flo, lam, E0, E1, f); });
+  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, rec, Flo, lam, E0, E1, f); });
   pdl_exit();
 }
 
@@ -594,6 +641,7 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
   const double id = 1.0 / (sum / P.cfl_lo + 0.5 * sum);
   invD[i] = static_cast<TF>(id);
   const bool c0 = i < colour0_end;
+  TF d[kDU];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     double src;
@@ -601,8 +649,11 @@ __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<
     else src = Src[v * n + i];
     const double r = R[v] + src;
     Rk[v * n + i] = static_cast<TF>(r);
-    dU[v * n + i] = c0 ? static_cast<TF>(r * id) : TF(0);
+    d[v] = c0 ? static_cast<TF>(r * id) : TF(0);
   }
+#pragma unroll
+  for (int v = NV; v < kDU; ++v) d[v] = TF(0);
+  vstore<TF, kDU>(dU + static_cast<size_t>(i) * kDU, d);
   pdl_exit();
 }
 
@@ -642,23 +693,29 @@ __device__ __forceinline__ SweepGeo<T> sweep_geo(const MeshT<T> &m, const int i,
 }
 template <typename T>
 __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
-                                           const int i, const int s, const T *__restrict__ U,
-                                           const T *__restrict__ prim, const T *__restrict__ Rk,
-                                           const T *__restrict__ invD, const T *__restrict__ lamS,
-                                           const T *__restrict__ E0, const T *__restrict__ E1,
-                                           T *__restrict__ dU) {
+                                           const int i, const int s, const T *__restrict__ rec,
+                                           const T *__restrict__ Rk, const T *__restrict__ invD,
+                                           const T *__restrict__ lamS, const T *__restrict__ E0,
+                                           const T *__restrict__ E1, T *__restrict__ dU) {
   const int n = m.nc, nf = m.nf;
   const int j = g.j;
   T c[NV] = { T(0), T(0), T(0), T(0), T(0) };
   if (j >= 0) {
     const T hS = g.hS, lp = lamS[s * n + i];
+    // the neighbour's U and velocity (the first 8 values of its record; 6
+    // in FP64, which needs U only) and its increment
+    constexpr int kUsed = is_f32<T>() ? 8 : 6;
+    T rj[kUsed], dj[kDU];
+    vload<T, kUsed>(rec + static_cast<size_t>(j) * kRec, rj);
+    vload<T, kDU>(dU + static_cast<size_t>(j) * kDU, dj);
     T uj[NV], du[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
+    for (int v = 0; v < NV; ++v) { uj[v] = rj[v]; du[v] = dj[v]; }
     if constexpr (is_f32<T>()) {
       T dF[NV];
-      D3::euler_flux_delta(P.gamma, uj, prim[n + j], prim[2 * n + j], prim[3 * n + j], prim[4 * n + j], du, g.nn,
-                           dF);
+      // pressure of U_j, the expression of its primitives
+      const T pj = (P.gamma - T(1)) * (uj[4] - T(0.5) * uj[0] * (rj[5] * rj[5] + rj[6] * rj[6] + rj[7] * rj[7]));
+      D3::euler_flux_delta(P.gamma, uj, rj[5], rj[6], rj[7], pj, du, g.nn, dF);
 #pragma unroll
       for (int v = 0; v < NV; ++v) c[v] = hS * (dF[v] - lp * du[v]);
     } else {
@@ -682,14 +739,14 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
   }
   if (i >= 0 && s < NV) {
     const T mine = s == 0 ? c[0] : s == 1 ? c[1] : s == 2 ? c[2] : s == 3 ? c[3] : c[4];
-    dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+    dU[static_cast<size_t>(i) * kDU + s] = (Rk[s * n + i] - mine) * invD[i];
   }
 }
 // cells per block of a sweep launch of shape SH
 __host__ __device__ constexpr int sweep_cpb(int sh) { return shape_bs(sh) / kSweepLanes * shape_ipt(sh); }
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
-    k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count, const T *__restrict__ U, const T *__restrict__ prim,
+    k_sweep(MeshT<T> m, ParamsT<T> P, int begin, int count, const T *__restrict__ rec,
             const T *__restrict__ Rk, const T *__restrict__ invD, const T *__restrict__ lamS,
             const T *__restrict__ E0, const T *__restrict__ E1, T *__restrict__ dU) {
   constexpr int kGroups = shape_bs(SH) / kSweepLanes, kIpt = shape_ipt(SH);
@@ -702,7 +759,7 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     const int i = g < count ? begin + g : -1;
     const SweepGeo<T> geo = sweep_geo(m, i, s);
     pdl_enter();
-    sweep_cell(m, P, geo, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
+    sweep_cell(m, P, geo, i, s, rec, Rk, invD, lamS, E0, E1, dU);
   }
   pdl_exit();
 }
