@@ -15,6 +15,7 @@
 #include "cgks_physics3.cuh"
 #include "cgks_pdl.cuh"
 #include "cgks_shapes.h"
+#include "cgks_vec.cuh"
 
 namespace cgks {
 namespace kern3 {
@@ -457,37 +458,6 @@ __global__ void k_res_final(const double *__restrict__ partial, int nblocks, Ctl
 // The increments dU are stored the same way, 8 values per cell ([0..4],
 // then zeros).
 constexpr int kRec = 16, kDU = 8;
-template <typename T> struct VecOf;
-template <> struct VecOf<float> { using V = float4; static constexpr int W = 4; };
-template <> struct VecOf<double> { using V = double2; static constexpr int W = 2; };
-// N values from a 16-byte aligned address (N a multiple of the vector width)
-template <typename T, int N>
-__device__ __forceinline__ void vload(const T *__restrict__ p, T out[N]) {
-  using V = typename VecOf<T>::V;
-  constexpr int W = VecOf<T>::W;
-  static_assert(N % W == 0, "whole vectors");
-#pragma unroll
-  for (int k = 0; k < N / W; ++k) {
-    const V x = reinterpret_cast<const V *>(p)[k];
-    const T *e = reinterpret_cast<const T *>(&x);
-#pragma unroll
-    for (int c = 0; c < W; ++c) out[k * W + c] = e[c];
-  }
-}
-template <typename T, int N>
-__device__ __forceinline__ void vstore(T *__restrict__ p, const T in[N]) {
-  using V = typename VecOf<T>::V;
-  constexpr int W = VecOf<T>::W;
-  static_assert(N % W == 0, "whole vectors");
-#pragma unroll
-  for (int k = 0; k < N / W; ++k) {
-    V x;
-    T *e = reinterpret_cast<T *>(&x);
-#pragma unroll
-    for (int c = 0; c < W; ++c) e[c] = in[k * W + c];
-    reinterpret_cast<V *>(p)[k] = x;
-  }
-}
 template <typename T>
 __device__ __forceinline__ D3::Prim<T> rec_prim(const T r[kRec]) {
   D3::Prim<T> q;
