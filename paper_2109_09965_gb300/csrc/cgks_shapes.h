@@ -8,6 +8,9 @@
 #pragma once
 
 #include "../../include/cgks.h"
+#ifdef __CUDACC__
+#include "cgks_pdl.cuh"
+#endif
 
 namespace cgks {
 
@@ -28,10 +31,6 @@ static_assert(TK_COUNT == CGKS_TUNE_KERNELS, "tunable kernel count");
 constexpr int kDefaultShape[TK_COUNT] = { 2, 0, 2, 0 };
 
 #ifdef __CUDACC__
-}  // namespace cgks
-#include "cgks_pdl.cuh"
-namespace cgks {
-
 // the items of this thread in a launch of shape SH over n items
 template <int SH, typename F>
 __device__ __forceinline__ void for_items(const int n, F &&f) {
