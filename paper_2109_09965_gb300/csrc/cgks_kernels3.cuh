@@ -697,7 +697,7 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T fb = g.is0 ? E1[v * nf + f] : -E0[v * nf + f];
-        c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
+        c[v] = hS * ((fa[v] - fb) - lp * du[v]);   // (U + dU) - U = dU
       }
     }
   }

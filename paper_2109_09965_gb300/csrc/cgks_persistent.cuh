@@ -229,7 +229,7 @@ __device__ __forceinline__ void sweep_at(const LoArgs<TF> &a, int i, int s) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const TF fb = is0 ? ldcg(&a.E1[v * nf + f]) : -ldcg(&a.E0[v * nf + f]);
-        c[v] = hS * ((fa[v] - fb) - lp * (up[v] - uj[v]));
+        c[v] = hS * ((fa[v] - fb) - lp * du[v]);   // (U + dU) - U = dU
       }
     }
   }
