@@ -26,22 +26,6 @@ template <> __device__ __forceinline__ float d_exp<float>(float x) { return expf
 template <typename T> __device__ __forceinline__ T d_sqrt(T x);
 template <> __device__ __forceinline__ double d_sqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float d_sqrt<float>(float x) { return sqrtf(x); }
-// 1/x.  FP32: the IEEE quotient (cheap).  FP64: the hardware reciprocal
-// estimate refined by two Newton-Raphson steps r <- r + r (1 - x r), which
-// square the relative error each time (estimate ~2^-20, then ~2^-40, then
-// below the double precision rounding): within about an ulp of the
-// correctly rounded quotient for four FMAs, where an IEEE FP64 division
-// costs several times that on GB300's narrow FP64 pipe.
-template <typename T> __device__ __forceinline__ T d_rcp(T x);
-template <> __device__ __forceinline__ float d_rcp<float>(float x) { return 1.0f / x; }
-template <> __device__ __forceinline__ double d_rcp<double>(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
 template <typename T> __device__ __forceinline__ T d_pi();
 template <> __device__ __forceinline__ double d_pi<double>() { return 3.141592653589793238462643; }
 template <> __device__ __forceinline__ float d_pi<float>() { return 3.14159265358979f; }
@@ -81,12 +65,12 @@ __device__ __forceinline__ Maxw<T> maxw(const T W[NV], T c2K) {
   // lambda = (K+2) rho / (4 (rho E - rho |U|^2 / 2)),  c2K = 2 / (K+2)
   Maxw<T> g;
   g.rho = W[0];
-  g.ir = d_rcp(W[0]);
+  g.ir = T(1) / W[0];
   g.U = W[1] * g.ir;
   g.V = W[2] * g.ir;
   T eps = W[3] - T(0.5) * g.rho * (g.U * g.U + g.V * g.V);
   g.i2l = c2K * eps * g.ir;
-  g.lam = T(0.5) * d_rcp(g.i2l);
+  g.lam = T(0.5) / g.i2l;
   return g;
 }
 

@@ -50,13 +50,13 @@ __device__ __forceinline__ Maxw<T> maxw(const T Wc[NV], T c2K) {
   // lambda = (K+3) rho / (4 (rho E - rho |U|^2 / 2)), c2K = 2 / (K+3)
   Maxw<T> g;
   g.rho = Wc[0];
-  g.ir = dev::d_rcp(Wc[0]);
+  g.ir = T(1) / Wc[0];
   g.U = Wc[1] * g.ir;
   g.V = Wc[2] * g.ir;
   g.W = Wc[3] * g.ir;
   T eps = Wc[4] - T(0.5) * g.rho * (g.U * g.U + g.V * g.V + g.W * g.W);
   g.i2l = c2K * eps * g.ir;
-  g.lam = T(0.5) * dev::d_rcp(g.i2l);
+  g.lam = T(0.5) / g.i2l;
   return g;
 }
 

@@ -17,11 +17,13 @@ namespace cgks {
 constexpr int kNShape = CGKS_TUNE_SHAPES;
 
 __host__ __device__ constexpr int shape_bs(int s) {
-  return s == 1 ? 64 : s == 2 ? 256 : 128;
+  return (s == 1 || s == 4) ? 64 : s == 2 ? 256 : 128;
 }
-__host__ __device__ constexpr int shape_ipt(int s) { return s == 3 ? 2 : 1; }
-// minimum resident blocks per SM (a register cap for the compiler); 1 = none
-__host__ __device__ constexpr int shape_minb(int s) { return s == 4 ? 3 : 1; }
+__host__ __device__ constexpr int shape_ipt(int s) { return (s == 3 || s == 4) ? 2 : 1; }
+// minimum resident blocks per SM (a register cap for the compiler); 1 = none.
+// No shape caps registers: under a cap the compiler may fuse multiplies and
+// adds differently, and a shape must never change a result.
+__host__ __device__ constexpr int shape_minb(int) { return 1; }
 
 // tunable kernels
 enum TuneKernel { TK_RECON = 0, TK_FACE, TK_LOFACE, TK_SWEEP, TK_COUNT };
