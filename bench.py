@@ -107,26 +107,39 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend="nccl"):
+    """Replicas: one process per GPU from torchrun's environment.  NCCL on
+    the GPUs; the host logic runs the same over gloo on CPU (tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
 def dist_max(x, world):
+    """Maximum of x over the ranks (the slowest replica's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(n_cells, steps, ms_max, world):
+    """Whole-job cell-updates/s of `world` replicas, each advancing n_cells
+    by `steps` cycles, over the slowest replica's time."""
+    return world * n_cells * steps / (ms_max / 1000.0)
 
 
 def dist_barrier(world):
@@ -234,7 +247,7 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     ms = sum(a.elapsed_time(b) for a, b in evs)
     dist_barrier(world)
     ms = dist_max(ms, world)
-    value = world * mesh.n_cells * args.steps / (ms / 1000.0)
+    value = aggregate_value(mesh.n_cells, args.steps, ms, world)
     res, _ = solver.residual()
 
     # per-kernel timing pass (events around every launch, same K cycles)
