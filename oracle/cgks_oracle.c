@@ -35,7 +35,9 @@
  *   of g^l, g^r; W^c_x = mean of the two side gradients; tau = mu/p^c with
  *   constant mu; S2O4 after Li & Du (2016) with gradient stages at t/2 and
  *   midpoint; global dt from CFL_hi; residual re-evaluated at W^{n+1};
- *   first-order inviscid KFVS on the low level; lambda with nu = mu/rho;
+ *   first-order inviscid KFVS on the low level (or, as the alternative the
+ *   paper names, Lax-Friedrichs with the implicit operator's lambda_p as
+ *   its dissipation coefficient); lambda with nu = mu/rho;
  *   dt_i = CFL_lo |Omega_i| / sum(lambda S); coloured sweep order (colours
  *   ascending = forward, descending = backward); ghost-state boundaries:
  *   walls mirror the reconstructed point state (and enter the wall cell's
@@ -74,7 +76,7 @@ typedef struct {
   int time_scheme;            /* 0 = S1O2, 1 = S2O4 */
   int restrict_mode;          /* reserved, must be 0: R_p0 is re-evaluated at W^{n+1} */
   int n_bc;
-  int pad_;
+  int flux_lo;                /* low-level flux: 0 = KFVS, 1 = Lax-Friedrichs */
   or_bc bc[MAXBC];
 } or_params;
 
@@ -1134,7 +1136,27 @@ static void lo_ghost(const or_solver *s, int tag, const double U[NV], const doub
   or_ghost(&s->P, tag, U, g0, n, Ug, gg);
 }
 
-/* R_lo,i(U) = -sum_p S_p F_KFVS(U_i, U_ip; n_p) */
+/* modified spectral radius |U_n| + c + 2 nu S / |Omega| of one side */
+static double lo_lambda_side(const or_solver *s, const double U[NV], const double n[2], double S, double vol) {
+  double rho, u[2], p;
+  prim(s->P.gamma, U, &rho, u, &p);
+  double c = sqrt(s->P.gamma * p / rho);
+  return fabs(u[0] * n[0] + u[1] * n[1]) + c + 2.0 * (s->P.mu / rho) * S / vol;
+}
+
+/* The Lax-Friedrichs alternative of the low-level flux (Section 3 names the
+ * solver; its dissipation coefficient is read as the implicit operator's
+ * lambda_p = max of the two sides):
+ *   F = (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2. */
+static void lo_lf(const or_solver *s, const double Ul[NV], const double Ur[NV], const double n[2], double lam,
+                  double F[NV]) {
+  double Fl[NV], Fr[NV];
+  or_euler_flux(s->P.gamma, Ul, n, Fl);
+  or_euler_flux(s->P.gamma, Ur, n, Fr);
+  for (int v = 0; v < NV; ++v) F[v] = 0.5 * (Fl[v] + Fr[v]) - 0.5 * lam * (Ur[v] - Ul[v]);
+}
+
+/* R_lo,i(U) = -sum_p S_p F_lo(U_i, U_ip; n_p), F_lo = KFVS or L-F */
 static void lo_residual(const or_solver *s, const double *U, double *R) {
   const or_mesh *m = s->m;
   memset(R, 0, sizeof(double) * m->nc * NV);
@@ -1143,20 +1165,19 @@ static void lo_residual(const or_solver *s, const double *U, double *R) {
     double Ur[NV], Fl[NV];
     if (F->c1 >= 0) memcpy(Ur, &U[F->c1 * NV], sizeof Ur);
     else lo_ghost(s, F->tag, &U[F->c0 * NV], F->n, Ur);
-    or_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
+    if (s->P.flux_lo == 1) {
+      const double v0 = m->cell[F->c0].vol, v1 = F->c1 >= 0 ? m->cell[F->c1].vol : v0;
+      const double l0 = lo_lambda_side(s, &U[F->c0 * NV], F->n, F->S, v0);
+      const double l1 = lo_lambda_side(s, Ur, F->n, F->S, v1);
+      lo_lf(s, &U[F->c0 * NV], Ur, F->n, l0 > l1 ? l0 : l1, Fl);
+    } else {
+      or_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
+    }
     for (int v = 0; v < NV; ++v) {
       R[F->c0 * NV + v] -= F->S * Fl[v];
       if (F->c1 >= 0) R[F->c1 * NV + v] += F->S * Fl[v];
     }
   }
-}
-
-/* modified spectral radius |U_n| + c + 2 nu S / |Omega| of one side */
-static double lo_lambda_side(const or_solver *s, const double U[NV], const double n[2], double S, double vol) {
-  double rho, u[2], p;
-  prim(s->P.gamma, U, &rho, u, &p);
-  double c = sqrt(s->P.gamma * p / rho);
-  return fabs(u[0] * n[0] + u[1] * n[1]) + c + 2.0 * (s->P.mu / rho) * S / vol;
 }
 
 /* lambda_p = max(lambda_i, lambda_ip) per face */

@@ -67,6 +67,8 @@ typedef struct {
 typedef struct {
   double gamma, mu, alpha, cfl_hi, cfl_lo;
   int n_implicit, n_sweeps, time_scheme, n_bc;
+  int flux_lo;                /* low-level flux: 0 = KFVS, 1 = Lax-Friedrichs */
+  int pad_;
   o3_bc bc[MAXBC];
 } o3_params;
 
@@ -1164,6 +1166,14 @@ static void lo_ghost(const o3_solver *s, int tag, const double U[NV], const doub
   double g0[ND * NV] = { 0 }, gg[ND * NV];
   o3_ghost(&s->P, tag, U, g0, n, Ug, gg);
 }
+static double lo_lambda_side(const o3_solver *s, const double U[NV], const double n[3], double S, double vol) {
+  double rho, u[3], p;
+  prim3(s->P.gamma, U, &rho, u, &p);
+  return fabs(dot3(u, n)) + sqrt(s->P.gamma * p / rho) + 2.0 * (s->P.mu / rho) * S / vol;
+}
+/* R_lo,i(U) = -sum_p S_p F_lo(U_i, U_ip; n_p): KFVS, or the Lax-Friedrichs
+ * alternative of Section 3 with the implicit operator's lambda_p,
+ * (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2 */
 static void lo_residual(const o3_solver *s, const double *U, double *R) {
   const o3_mesh *m = s->m;
   memset(R, 0, sizeof(double) * m->nc * NV);
@@ -1172,17 +1182,23 @@ static void lo_residual(const o3_solver *s, const double *U, double *R) {
     double Ur[NV], Fl[NV];
     if (F->c1 >= 0) memcpy(Ur, &U[F->c1 * NV], sizeof Ur);
     else lo_ghost(s, F->tag, &U[F->c0 * NV], F->n, Ur);
-    o3_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
+    if (s->P.flux_lo == 1) {
+      const double v0 = m->cell[F->c0].vol, v1 = F->c1 >= 0 ? m->cell[F->c1].vol : v0;
+      const double l0 = lo_lambda_side(s, &U[F->c0 * NV], F->n, F->S, v0);
+      const double l1 = lo_lambda_side(s, Ur, F->n, F->S, v1);
+      const double lam = l0 > l1 ? l0 : l1;
+      double Fa[NV], Fb[NV];
+      o3_euler_flux(s->P.gamma, &U[F->c0 * NV], F->n, Fa);
+      o3_euler_flux(s->P.gamma, Ur, F->n, Fb);
+      for (int v = 0; v < NV; ++v) Fl[v] = 0.5 * (Fa[v] + Fb[v]) - 0.5 * lam * (Ur[v] - U[F->c0 * NV + v]);
+    } else {
+      o3_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
+    }
     for (int v = 0; v < NV; ++v) {
       R[F->c0 * NV + v] -= F->S * Fl[v];
       if (F->c1 >= 0) R[F->c1 * NV + v] += F->S * Fl[v];
     }
   }
-}
-static double lo_lambda_side(const o3_solver *s, const double U[NV], const double n[3], double S, double vol) {
-  double rho, u[3], p;
-  prim3(s->P.gamma, U, &rho, u, &p);
-  return fabs(dot3(u, n)) + sqrt(s->P.gamma * p / rho) + 2.0 * (s->P.mu / rho) * S / vol;
 }
 static void lo_lambda(const o3_solver *s, const double *U, double *lam) {
   const o3_mesh *m = s->m;

@@ -44,7 +44,7 @@ class OrParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
                 ("time_scheme", C.c_int), ("restrict_mode", C.c_int), ("n_bc", C.c_int),
-                ("pad_", C.c_int), ("bc", OrBC * 16)]
+                ("flux_lo", C.c_int), ("bc", OrBC * 16)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -106,6 +106,7 @@ def lib():
 def make_params(spec: dict) -> OrParams:
     """spec keys: gamma, mu, cfl_hi, cfl_lo, n_implicit, n_sweeps,
     time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
+    flux_lo ('kfvs' default | 'lf': low-level flux),
     bcs: list of dicts {kind: 'slip'|'noslip'|'farfield', uw=(u,v),
     rho, u=(u,v), p}."""
     P = OrParams()
@@ -118,6 +119,7 @@ def make_params(spec: dict) -> OrParams:
     P.n_sweeps = int(spec.get("n_sweeps", 2))
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.restrict_mode = 0
+    P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):

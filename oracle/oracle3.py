@@ -42,7 +42,8 @@ class O3BC(C.Structure):
 class O3Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
-                ("time_scheme", C.c_int), ("n_bc", C.c_int), ("bc", O3BC * 16)]
+                ("time_scheme", C.c_int), ("n_bc", C.c_int), ("flux_lo", C.c_int), ("pad_", C.c_int),
+                ("bc", O3BC * 16)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -117,6 +118,7 @@ def make_params(spec: dict) -> O3Params:
     P.n_implicit = int(spec.get("n_implicit", 6))
     P.n_sweeps = int(spec.get("n_sweeps", 2))
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
+    P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):

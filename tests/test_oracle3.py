@@ -580,3 +580,35 @@ def test_high_order_on_advected_density_wave(O3):
         errs.append(np.abs(W[inner, 0] - ref[:, 0]).mean())
     order = math.log(errs[0] / errs[1], 2)
     assert order > 2.4, (errs, order)
+
+
+def test_lf_low_level_free_stream_conservation_and_fixed_point(O3):
+    """3-D Lax-Friedrichs low level: zero residual for a free stream with
+    far-field ghosts, pairwise cancellation on a closed slip box, and the
+    V-cycle's fixed point unchanged (the explicit step leaves the converged
+    state as it is)."""
+    mesh = MG.box3(2, 2, 2, jitter=0.15, seed=31, cells="prism", tags=(0, 0, 0, 0, 0, 0))
+    om = O3.OracleMesh3(mesh)
+    vel = (0.3, 0.1, -0.1)
+    s = O3.OracleSolver3(om, dict(gamma=GAM, flux_lo="lf", bcs=[dict(kind="farfield", rho=1.0, u=vel, p=1 / GAM)]))
+    U = np.tile(cons3(1.0, *vel, 1 / GAM), (mesh.n_cells, 1))
+    assert np.abs(s.lo_residual(U)).max() < 1e-14
+    sb = O3.OracleSolver3(om, dict(gamma=GAM, mu=0.01, flux_lo="lf", bcs=[dict(kind="slip")]))
+    rng = np.random.default_rng(32)
+    n = mesh.n_cells
+    U = np.array([cons3(rng.uniform(0.8, 1.2), *rng.uniform(-0.3, 0.3, 3), rng.uniform(0.6, 0.8)) for _ in range(n)])
+    R = sb.lo_residual(U)
+    for v in (0, 4):
+        assert abs(R[:, v].sum()) < 1e-14 * np.abs(R[:, v]).sum()
+    # fixed point on a small far-field box with a wall
+    mesh = MG.box3(2, 2, 2, jitter=0.1, seed=33, cells="prism", tags=(1, 1, 1, 1, 0, 1))
+    om = O3.OracleMesh3(mesh)
+    spec = dict(gamma=GAM, mu=0.02, flux_lo="lf",
+                bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(0.2, 0.0, 0.0), p=1 / GAM)])
+    s = O3.OracleSolver3(om, spec)
+    s.set_state(np.tile(cons3(1.0, 0.2, 0.0, 0.0, 1 / GAM), (mesh.n_cells, 1)))
+    res = s.pmg_cycles(400)
+    assert res[-1] < 1e-13, res[-5:]
+    W, _ = s.get_state()
+    s.highorder_step()
+    assert np.abs(s.get_state()[0] - W).max() < 1e-12

@@ -161,3 +161,97 @@ def test_fas_fixed_point(oracle_lib):
     W2, _ = s.get_state()
     assert np.abs(W2 - W).max() < 1e-12
     assert np.abs(W - W0).max() > 1e-2
+
+
+# ---------------------------------------------------------------- L-F variant
+def test_lf_residual_linearises_to_the_implicit_operator(oracle_lib):
+    """The Lax-Friedrichs low-level flux with the implicit operator's
+    lambda_p (Section 3, the alternative solver) is the flux whose split the
+    point relaxation linearises: at a uniform state, where the lambda_p
+    derivatives drop out (they multiply U_r - U_l = 0), the finite-difference
+    Jacobian of R_lo couples neighbours by -S_p (A(U; n_p) - lambda_p I) / 2
+    and each interior cell to itself by -1/2 sum_p lambda_p S_p (closed cells,
+    sum_p n_p S_p = 0)."""
+    O = oracle_lib
+    mesh = MG.box(3, 3, jitter=0.2, seed=4, cells="mixed", quad_mask=lambda i, j: (i + j) % 2 == 0,
+                  tags=(0, 0, 0, 0))
+    om = O.OracleMesh(mesh)
+    s = O.OracleSolver(om, dict(gamma=GAM, mu=0.01, flux_lo="lf",
+                                bcs=[dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)]))
+    nc = mesh.n_cells
+    U = np.tile(exact.cons_from_prim(GAM, 1.1, 0.25, -0.15, 0.9 / GAM), (nc, 1))
+    lam = s.lo_lambda(U)
+    F = om.faces()
+    J = np.zeros((nc, 4, nc, 4))
+    h = 1e-6
+    for j in range(nc):
+        for k in range(4):
+            Up, Um = U.copy(), U.copy()
+            Up[j, k] += h
+            Um[j, k] -= h
+            J[:, :, j, k] = (s.lo_residual(Up) - s.lo_residual(Um)) / (2 * h)
+    expect = np.zeros_like(J)
+    boundary = set()
+    for f in range(om.n_faces):
+        c0, c1, n, S = F["c0"][f], F["c1"][f], F["n"][f], F["S"][f]
+        if c1 < 0:
+            boundary.add(c0)
+            continue
+        expect[c0, :, c1, :] -= S * 0.5 * (cjac(U[c1], n) - lam[f] * np.eye(4))
+        expect[c1, :, c0, :] -= S * 0.5 * (cjac(U[c0], -n) - lam[f] * np.eye(4))
+        expect[c0, :, c0, :] -= 0.5 * lam[f] * S * np.eye(4)
+        expect[c1, :, c1, :] -= 0.5 * lam[f] * S * np.eye(4)
+    interior = [i for i in range(nc) if i not in boundary]
+    assert interior, "the mesh needs interior cells"
+    scale = np.abs(expect).max()
+    for i in range(nc):
+        for j in range(nc):
+            if i == j and i in boundary:
+                continue             # boundary ghosts depend on the cell's own state
+            np.testing.assert_allclose(J[i, :, j, :], expect[i, :, j, :], rtol=0, atol=1e-7 * scale)
+
+
+def test_lf_residual_vanishes_for_free_stream_and_conserves(oracle_lib):
+    O = oracle_lib
+    mesh = MG.box(4, 4, jitter=0.2, seed=3, cells="tri", tags=(0, 0, 0, 0))
+    om = O.OracleMesh(mesh)
+    s = O.OracleSolver(om, dict(gamma=GAM, flux_lo="lf",
+                                bcs=[dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)]))
+    U = np.tile(exact.cons_from_prim(GAM, 1.0, 0.3, 0.1, 1 / GAM), (mesh.n_cells, 1))
+    assert np.abs(s.lo_residual(U)).max() < 1e-14
+    # closed slip box: interior fluxes cancel pairwise, walls pass no mass or energy
+    sb = O.OracleSolver(om, dict(gamma=GAM, mu=0.01, flux_lo="lf", bcs=[dict(kind="slip")]))
+    rng = np.random.default_rng(9)
+    n = mesh.n_cells
+    rho = rng.uniform(0.8, 1.2, n)
+    U = exact.cons_from_prim(GAM, rho, rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n),
+                             rho / GAM * rng.uniform(0.9, 1.1, n))
+    R = sb.lo_residual(U)
+    assert abs(R[:, 0].sum()) < 1e-14 * np.abs(R[:, 0]).sum()
+    assert abs(R[:, 3].sum()) < 1e-14 * np.abs(R[:, 3]).sum()
+
+
+def test_lf_cycle_keeps_the_fas_fixed_point(oracle_lib):
+    """With the L-F low level the V-cycle converges to the same high-order
+    fixed point (the correction vanishes where R_hi = 0 whatever the low
+    flux): the explicit step leaves the converged state unchanged, and the
+    field equals the one the KFVS low level converges to."""
+    O = oracle_lib
+    mesh = MG.cylinder(24, 4, 6, growth=1.2, R_far=5.0)
+    om = O.OracleMesh(mesh)
+    ma = 0.38
+    base = dict(gamma=GAM, mu=0.01, cfl_hi=0.4,
+                bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(ma, 0.0), p=1 / GAM)])
+    W0 = np.tile(exact.cons_from_prim(GAM, 1.0, ma, 0.0, 1 / GAM), (mesh.n_cells, 1))
+    out = {}
+    for flux in ("lf", "kfvs"):
+        s = O.OracleSolver(om, dict(base, flux_lo=flux))
+        s.set_state(W0)
+        res = s.pmg_cycles(600)
+        assert res[-1] < 1e-13, (flux, res[-5:])
+        W, _ = s.get_state()
+        s.highorder_step()
+        W2, _ = s.get_state()
+        assert np.abs(W2 - W).max() < 1e-12
+        out[flux] = W
+    assert np.abs(out["lf"] - out["kfvs"]).max() < 1e-10 * np.abs(out["kfvs"]).max()
