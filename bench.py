@@ -844,6 +844,23 @@ def converge(cgks, mesh, spec, W0, drop=1e-8, max_cycles=20000, max_steps=100000
                         "iterations_to_drop": int(hit[0]) + 1 if hit.size else None,
                         "field_rel_l2_vs_fp64": float(np.linalg.norm(Wm - W64) / np.linalg.norm(W64)),
                         "history": [float(x) for x in hm[::max(1, len(hm) // 40)]]}
+    # the Lax-Friedrichs low level the paper compares with KFVS (Section 3):
+    # cycles and wall time to the same drop
+    s = cgks.Solver(cgks.Mesh(mesh), dict(spec, flux_lo="lf"))
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hl = []
+    while len(hl) < max_cycles and not (hl and min(hl) <= drop * hl[0]):
+        hl.extend(s.pmg_cycle(500).tolist())
+    el = time.perf_counter() - t
+    s.close()
+    hl = np.asarray(hl)
+    hit = np.nonzero(hl <= drop * hl[0])[0]
+    out["pmg_lf_low_level"] = {"cycles_run": int(hl.size), "wall_s": el,
+                               "iterations_to_drop": int(hit[0]) + 1 if hit.size else None,
+                               "res_min_drop": float(hl.min() / hl[0]),
+                               "history": [float(x) for x in hl[::max(1, len(hl) // 40)]]}
     if out["pmg"]["converged"] and out["explicit_S2O4"]["converged"]:
         out["speedup"] = out["explicit_S2O4"]["wall_s_to_drop"] / out["pmg"]["wall_s_to_drop"]
     elif out["pmg"]["converged"]:

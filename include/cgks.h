@@ -67,6 +67,13 @@ enum { CGKS_S1O2 = 0, CGKS_S2O4 = 1 };
 /* arithmetic of the hot path */
 enum { CGKS_FP64 = 0, CGKS_MIXED = 1 };
 
+/* First-order flux of the low-order level (Section 3: KFVS by default; the
+ * paper also runs a Lax-Friedrichs solver there and finds the convergence
+ * nearly unchanged).  L-F: (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2
+ * with lambda_p the spectral radius of the implicit operator, max of the
+ * two sides. */
+enum { CGKS_FLUX_KFVS = 0, CGKS_FLUX_LF = 1 };
+
 #define CGKS_MAX_BC 16
 
 typedef struct {
@@ -98,7 +105,7 @@ typedef struct {
   int32_t programmatic_launch; /* 1 (default): each kernel of a cycle may be scheduled while its
                             predecessor runs and waits on the device for it (programmatic
                             dependent launch, sm_90+); 0: plain stream order.  Same results. */
-  int32_t pad_;
+  int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF */
   cgks_bc bc[CGKS_MAX_BC];
   void *stream;          /* cudaStream_t for all device work (NULL = default) */
   cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */
@@ -223,6 +230,8 @@ typedef struct {
   int32_t low_order_fused; /* 1: persistent cooperative low-order level */
   int32_t autotune;      /* 1 (default): autotuned launch shapes for the batch */
   int32_t programmatic_launch; /* 1 (default): programmatic dependent launch (see cgks_params) */
+  int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF for every solve */
+  int32_t pad_;
   void *stream;          /* cudaStream_t (NULL = default) */
   cgks_alloc_fn alloc;
   cgks_free_fn free;

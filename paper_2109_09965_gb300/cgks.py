@@ -22,6 +22,7 @@ TRI, QUAD, TET, PRISM, PYRAMID, HEX = 0, 1, 2, 3, 4, 5
 BC_SLIP, BC_NOSLIP, BC_FARFIELD = 0, 1, 2
 S1O2, S2O4 = 0, 1
 FP64, MIXED = 0, 1
+FLUX_KFVS, FLUX_LF = 0, 1
 MAX_BC = 16
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "mesh rejected", -4: "CUDA error",
@@ -49,7 +50,7 @@ class CgksParams(C.Structure):
                 ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32), ("time_scheme", C.c_int32),
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
-                ("pad_", C.c_int32), ("bc", CgksBC * MAX_BC),
+                ("flux_lo", C.c_int32), ("bc", CgksBC * MAX_BC),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -194,6 +195,7 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
         if key in spec:
             setattr(P, key, int(spec[key]))
     P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
+    P.flux_lo = {"kfvs": FLUX_KFVS, "lf": FLUX_LF}[spec.get("flux_lo", "kfvs")]
     P.precision = {"fp64": FP64, "mixed": MIXED}[spec.get("precision", "fp64")]
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
@@ -363,7 +365,7 @@ class CgksServerOpts(C.Structure):
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32),
                 ("max_active", C.c_int32), ("max_cycles", C.c_int32), ("use_graph", C.c_int32),
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
-                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("flux_lo", C.c_int32), ("pad_", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class CgksReqStatus(C.Structure):
@@ -400,6 +402,7 @@ class Server:
         L.cgks_server_default_opts(C.byref(o))
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         o.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[time_scheme]
+        o.flux_lo = {"kfvs": FLUX_KFVS, "lf": FLUX_LF}[kw.get("flux_lo", "kfvs")]
         o.max_active, o.max_cycles = int(max_active), int(max_cycles)
         for key in ("cfl_hi", "cfl_lo"):
             if key in kw:

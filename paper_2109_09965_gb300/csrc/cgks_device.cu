@@ -47,7 +47,7 @@ struct Bufs {
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
   int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 0;
-  int autotune = 1, pdl = 1;
+  int autotune = 1, pdl = 1, flux_lo = CGKS_FLUX_KFVS;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -440,6 +440,7 @@ void fill_shared_params(const Shared &sh, ParamsT<T> &P) {
   P.kc.K = static_cast<T>(K);
   P.kc.c2K = static_cast<T>(2.0 / (K + 2.0));
   P.kc.c4K = static_cast<T>(4.0 / (K + 2.0));
+  P.flux_lo = sh.flux_lo;
 }
 
 // The device arena of a batch: one allocation carved into 256-byte aligned
@@ -798,7 +799,9 @@ int finalize_batch(Batch *b) {
     CK(cudaMemcpyAsync(b->list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream));
   // the fused low-order launch: per-colour ranges of every active solve
   b->lo_fused_ok = false;
-  if (b->sh.lo_fused && b->lo_grid > 0 && C <= kMaxColFused && b->sweep_seq.size() <= 48 && N > 0) {
+  // (the fused launch implements the KFVS low level only)
+  if (b->sh.lo_fused && b->sh.flux_lo == CGKS_FLUX_KFVS && b->lo_grid > 0 && C <= kMaxColFused &&
+      b->sweep_seq.size() <= 48 && N > 0) {
     std::vector<int> rstart(kMaxColFused + 1, 0), rbegin, rpre;
     for (int c = 0; c < C; ++c) {
       rstart[c] = static_cast<int>(rbegin.size());
@@ -889,6 +892,7 @@ Shared shared_from(const cgks_params *p) {
   sh.precision = p->precision; sh.use_graph = p->use_graph; sh.lo_fused = p->low_order_fused;
   sh.autotune = p->autotune;
   sh.pdl = p->programmatic_launch;
+  sh.flux_lo = p->flux_lo;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -896,7 +900,8 @@ Shared shared_from(const cgks_params *p) {
 int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_used) {
   if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
       p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
-      p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0))
+      p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0) ||
+      (p->flux_lo != CGKS_FLUX_KFVS && p->flux_lo != CGKS_FLUX_LF))
     return CGKS_EINVAL;
   for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
@@ -1421,7 +1426,8 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   if (!o || !out || hbm_budget == 0 || o->max_active < 1 || o->max_cycles < 1 || !(o->cfl_hi > 0.0) ||
       !(o->cfl_lo > 0.0) || o->n_implicit < 0 || o->n_sweeps < 0 ||
       (o->precision != CGKS_FP64 && o->precision != CGKS_MIXED) ||
-      (o->time_scheme != CGKS_S1O2 && o->time_scheme != CGKS_S2O4))
+      (o->time_scheme != CGKS_S1O2 && o->time_scheme != CGKS_S2O4) ||
+      (o->flux_lo != CGKS_FLUX_KFVS && o->flux_lo != CGKS_FLUX_LF))
     return CGKS_EINVAL;
   *out = nullptr;
   int ndev = 0;
@@ -1433,6 +1439,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->sh.lo_fused = o->low_order_fused;
   v->sh.autotune = o->autotune;
   v->sh.pdl = o->programmatic_launch;
+  v->sh.flux_lo = o->flux_lo;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;

@@ -308,6 +308,7 @@ void fill_params(const cgks_params &p, ParamsT<T> &P) {
   P.kc.K = static_cast<T>(K);
   P.kc.c2K = static_cast<T>(2.0 / (K + 3.0));
   P.kc.c4K = static_cast<T>(4.0 / (K + 3.0));
+  P.flux_lo = p.flux_lo;
 }
 
 #define CK3(x)                                  \

@@ -47,6 +47,7 @@ struct ParamsT {
   const int *bc_kind;            // [16 S] boundary kind per global tag
   const T *bc_uw;                // [16 S][2] wall velocity
   const T *bc_rho, *bc_u, *bc_p; // [16 S], [16 S][2], [16 S] far-field free stream
+  int flux_lo;                   // low-level flux: CGKS_FLUX_KFVS or CGKS_FLUX_LF
 };
 
 template <typename T>
@@ -510,35 +511,45 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
   const T mu = g.mu;
   D::Prim<T> a = load_prim(prim, n, c0), b;
   const T ivb = g.ivb;
+  T wa[4], wb[4];   // states of the two sides (global frame); wb is the ghost on a boundary
+  const bool need_w = P.flux_lo == CGKS_FLUX_LF || E0 != nullptr;
   if (c1 >= 0) {
     b = load_prim(prim, n, c1);
+    if (need_w)
+      for (int v = 0; v < 4; ++v) { wa[v] = U[v * n + c0]; wb[v] = U[v * n + c1]; }
   } else {
-    T w0[4], wg[4];
-    for (int v = 0; v < 4; ++v) w0[v] = U[v * n + c0];
-    lo_ghost(P, -1 - c1, nx, ny, w0, wg);
-    b = D::prim_of(wg, P.gamma, P.kc);
+    for (int v = 0; v < 4; ++v) wa[v] = U[v * n + c0];
+    lo_ghost(P, -1 - c1, nx, ny, wa, wb);
+    b = D::prim_of(wb, P.gamma, P.kc);
   }
   const T una = a.u * nx + a.v * ny, uta = -a.u * ny + a.v * nx;
   const T unb = b.u * nx + b.v * ny, utb = -b.u * ny + b.v * nx;
-  T Fl[4], F[4];
-  D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
-  D::rot_out(nx, ny, Fl, F);
-  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
   const T la = fabs(una) + a.c + T(2) * (mu * a.ir) * S * g.iva;
   const T lb = fabs(unb) + b.c + T(2) * (mu * b.ir) * S * ivb;
-  lam[f] = la > lb ? la : lb;
+  const T lmax = la > lb ? la : lb;
+  lam[f] = lmax;
+  // Euler normal fluxes of the two sides (the L-F flux, the FP64 cache)
+  T Fa[4], Fb[4];
+  if (need_w) {
+    Fa[0] = a.rho * una; Fa[1] = wa[1] * una + a.p * nx; Fa[2] = wa[2] * una + a.p * ny; Fa[3] = (wa[3] + a.p) * una;
+    Fb[0] = b.rho * unb; Fb[1] = wb[1] * unb + b.p * nx; Fb[2] = wb[2] * unb + b.p * ny; Fb[3] = (wb[3] + b.p) * unb;
+  }
+  T F[4];
+  if (P.flux_lo == CGKS_FLUX_LF) {
+    // Lax-Friedrichs alternative of Section 3 with the implicit operator's
+    // lambda_p: (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2
+    for (int v = 0; v < 4; ++v) F[v] = T(0.5) * (Fa[v] + Fb[v]) - T(0.5) * lmax * (wb[v] - wa[v]);
+  } else {
+    T Fl[4];
+    D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
+    D::rot_out(nx, ny, Fl, F);
+  }
+  for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
   if (E0) {
     // Euler normal flux of the cell means (interior faces: both sides)
-    E0[0 * nf + f] = a.rho * una;
-    E0[1 * nf + f] = U[1 * n + c0] * una + a.p * nx;
-    E0[2 * nf + f] = U[2 * n + c0] * una + a.p * ny;
-    E0[3 * nf + f] = (U[3 * n + c0] + a.p) * una;
-    if (c1 >= 0) {
-      E1[0 * nf + f] = b.rho * unb;
-      E1[1 * nf + f] = U[1 * n + c1] * unb + b.p * nx;
-      E1[2 * nf + f] = U[2 * n + c1] * unb + b.p * ny;
-      E1[3 * nf + f] = (U[3 * n + c1] + b.p) * unb;
-    }
+    for (int v = 0; v < 4; ++v) E0[v * nf + f] = Fa[v];
+    if (c1 >= 0)
+      for (int v = 0; v < 4; ++v) E1[v * nf + f] = Fb[v];
   }
 }
 template <typename T, int SH>

@@ -36,6 +36,7 @@ struct ParamsT {
   const int *bc_kind;          // [16]
   const T *bc_uw;              // [16][3] wall velocity (global)
   const T *bc_rho, *bc_u, *bc_p;  // [16], [16][3], [16] free stream (global)
+  int flux_lo;                    // low-level flux: CGKS_FLUX_KFVS or CGKS_FLUX_LF
 };
 
 template <typename T>
@@ -548,30 +549,38 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
     la3[k] = a.u * F.e[k][0] + a.v * F.e[k][1] + a.w * F.e[k][2];
     lb3[k] = b.u * F.e[k][0] + b.v * F.e[k][1] + b.w * F.e[k][2];
   }
-  T Fl[NV], Fg[NV];
-  D3::kfvs(P.K, a.rho, la3[0], la3[1], la3[2], a.i2l, a.sl, a.isp, b.rho, lb3[0], lb3[1], lb3[2], b.i2l, b.sl, b.isp,
-           Fl);
-  D3::rot_out(F, Fl, Fg);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Flo[v * nf + f] = Fg[v];
   const T la = fabs(la3[0]) + a.c + T(2) * (P.mu * a.ir) * S * m.ivol[c0];
   const T lb = fabs(lb3[0]) + b.c + T(2) * (P.mu * b.ir) * S * ivb;
-  lam[f] = la > lb ? la : lb;
+  const T lmax = la > lb ? la : lb;
+  lam[f] = lmax;
+  // Euler normal fluxes of the two sides (the L-F flux, the FP64 cache)
+  const T nx = F.e[0][0], ny = F.e[0][1], nz = F.e[0][2];
+  const T una = la3[0], unb = lb3[0];
+  T Fa[NV], Fb[NV];
+  Fa[0] = a.rho * una; Fa[1] = ra[1] * una + a.p * nx; Fa[2] = ra[2] * una + a.p * ny;
+  Fa[3] = ra[3] * una + a.p * nz; Fa[4] = (ra[4] + a.p) * una;
+  Fb[0] = b.rho * unb; Fb[1] = rb[1] * unb + b.p * nx; Fb[2] = rb[2] * unb + b.p * ny;
+  Fb[3] = rb[3] * unb + b.p * nz; Fb[4] = (rb[4] + b.p) * unb;
+  T Fg[NV];
+  if (P.flux_lo == CGKS_FLUX_LF) {
+    // Lax-Friedrichs alternative of Section 3 with the implicit operator's
+    // lambda_p: (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fg[v] = T(0.5) * (Fa[v] + Fb[v]) - T(0.5) * lmax * (rb[v] - ra[v]);
+  } else {
+    T Fl[NV];
+    D3::kfvs(P.K, a.rho, la3[0], la3[1], la3[2], a.i2l, a.sl, a.isp, b.rho, lb3[0], lb3[1], lb3[2], b.i2l, b.sl,
+             b.isp, Fl);
+    D3::rot_out(F, Fl, Fg);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Flo[v * nf + f] = Fg[v];
   if (E0) {
-    const T nx = F.e[0][0], ny = F.e[0][1], nz = F.e[0][2];
-    const T una = la3[0], unb = lb3[0];
-    E0[f] = a.rho * una;
-    E0[nf + f] = ra[1] * una + a.p * nx;
-    E0[2 * nf + f] = ra[2] * una + a.p * ny;
-    E0[3 * nf + f] = ra[3] * una + a.p * nz;
-    E0[4 * nf + f] = (ra[4] + a.p) * una;
-    if (c1 >= 0) {
-      E1[f] = b.rho * unb;
-      E1[nf + f] = rb[1] * unb + b.p * nx;
-      E1[2 * nf + f] = rb[2] * unb + b.p * ny;
-      E1[3 * nf + f] = rb[3] * unb + b.p * nz;
-      E1[4 * nf + f] = (rb[4] + b.p) * unb;
-    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) E0[v * nf + f] = Fa[v];
+    if (c1 >= 0)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) E1[v * nf + f] = Fb[v];
   }
 }
 template <typename T, int SH>

@@ -177,3 +177,15 @@ def test_sphere_config_mesh_runs(libs):
         s.set_state(np.tile(cons3(1.0, *vel, 1 / GAM), (mesh.n_cells, 1)))
         h = s.pmg_cycle(60)
         assert np.all(np.isfinite(h)) and h[-1] < 0.1 * h[0], (prec, h[::10])
+
+
+@pytest.mark.parametrize("name", ["prism_walls", "sphere"])
+def test_lf_low_level_matches_oracle(libs, name):
+    s, o = pair(libs, name, flux_lo="lf")
+    hg = s.pmg_cycle(3)
+    ho = o.pmg_cycles(3)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9)
+    Wg, Xg = s.get_state()
+    Wo, Xo = o.get_state()
+    assert rel(Wg, Wo) < TOL, rel(Wg, Wo)
+    assert rel(Xg, Xo) < 10 * TOL, rel(Xg, Xo)

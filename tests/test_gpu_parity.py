@@ -251,3 +251,19 @@ def test_fused_low_order_equals_per_phase_launches(name, precision):
     tol = 1e-13 if precision == "fp64" else 1e-5
     assert rel(out[0][0], out[1][0]) < tol, rel(out[0][0], out[1][0])
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=100 * tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["cavity8", "mixed_slip_farfield", "cylinder_viscous"])
+def test_lf_low_level_matches_oracle(libs, name, precision):
+    """Lax-Friedrichs low-level flux (CGKS_FLUX_LF): V-cycles against the
+    oracle's L-F variant, FP64 within 1e-12, mixed within its 1e-5."""
+    mesh, spec, state = case(name)
+    spec = dict(spec, flux_lo="lf")
+    g, o = pair(libs, mesh, dict(spec, precision=precision), state)
+    hg, ho = g.pmg_cycle(3), o.pmg_cycles(3)
+    Wg, Xg = g.get_state()
+    Wo, Xo = o.get_state()
+    tol = TOL if precision == "fp64" else 1e-5
+    assert rel(Wg, Wo) < tol, rel(Wg, Wo)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9 if precision == "fp64" else 1e-3)
