@@ -77,6 +77,9 @@ typedef struct {
   int restrict_mode;          /* reserved, must be 0: R_p0 is re-evaluated at W^{n+1} */
   int n_bc;
   int flux_lo;                /* low-level flux: 0 = KFVS, 1 = Lax-Friedrichs */
+  int sweep_order;            /* 0 = colour classes, 1 = element index (serial),
+                                 2 = index partitions with lagged exchange */
+  int n_parts;                /* partitions of sweep_order 2 (the paper's threads) */
   or_bc bc[MAXBC];
 } or_params;
 
@@ -1202,9 +1205,12 @@ static void fminus(const or_solver *s, const double U[NV], const double n[2], do
 
 /* Point-relaxation update of one cell, Eq. (implicit-local):
  * dU_i = (R_i - sum_p S_p [F^-(U_ip + dU_ip) - F^-(U_ip)]) / D_i,
- * D_i = |Omega_i| / dt_i + 1/2 sum_p lambda_p S_p, ghost increments zero. */
+ * D_i = |Omega_i| / dt_i + 1/2 sum_p lambda_p S_p, ghost increments zero.
+ * Neighbour increments come from dU, or, with a partition map, from dU_old
+ * for neighbours in another partition (the lagged exchange of the paper's
+ * threaded sweep). */
 static void relax_cell(const or_solver *s, long i, const double *U, const double *R, const double *lam,
-                       const double *D, double *dU) {
+                       const double *D, double *dU, const double *dU_old, const int *part) {
   const or_mesh *m = s->m;
   const or_cell *C = &m->cell[i];
   double acc[NV];
@@ -1213,9 +1219,10 @@ static void relax_cell(const or_solver *s, long i, const double *U, const double
     const or_face *F = &m->face[C->face[k]];
     if (F->c1 < 0) continue;
     long j = C->sgn[k] > 0 ? F->c1 : F->c0;
+    const double *dj = (part && part[j] != part[i]) ? &dU_old[j * NV] : &dU[j * NV];
     double n[2] = { C->sgn[k] * F->n[0], C->sgn[k] * F->n[1] };
     double Up[NV], fa[NV], fb[NV];
-    for (int v = 0; v < NV; ++v) Up[v] = U[j * NV + v] + dU[j * NV + v];
+    for (int v = 0; v < NV; ++v) Up[v] = U[j * NV + v] + dj[v];
     fminus(s, Up, n, lam[C->face[k]], fa);
     fminus(s, &U[j * NV], n, lam[C->face[k]], fb);
     for (int v = 0; v < NV; ++v) acc[v] -= F->S * (fa[v] - fb[v]);
@@ -1234,17 +1241,43 @@ static void lo_diag(const or_solver *s, const double *lam, double *D) {
   }
 }
 
-/* Algorithm 1 with colour order: n_sweeps x (colours ascending, then descending) */
+/* Algorithm 1, n_sweeps x (forward pass, backward pass), in one of three
+ * orders.  0: colour classes (colours ascending, then descending); the
+ * default and the GPU's.  1: element index 1..N, then N..1 (Algorithm 1 as
+ * printed, serial).  2: the paper's threaded sweep made deterministic: the
+ * index range cut into n_parts partitions, each swept in index order, with
+ * neighbours in other partitions read as they were at the start of the
+ * pass (Section 4, parallel strategy). */
 static void point_relaxation(const or_solver *s, const double *U, const double *R, const double *lam,
                              const double *D, int n_sweeps, double *dU) {
   const or_mesh *m = s->m;
-  memset(dU, 0, sizeof(double) * m->nc * NV);
-  for (int sw = 0; sw < n_sweeps; ++sw) {
-    for (int col = 0; col < m->ncolour; ++col)
-      for (long i = 0; i < m->nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU);
-    for (int col = m->ncolour - 1; col >= 0; --col)
-      for (long i = 0; i < m->nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU);
+  const long nc = m->nc;
+  memset(dU, 0, sizeof(double) * nc * NV);
+  if (s->P.sweep_order == 0) {
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+      for (int col = 0; col < m->ncolour; ++col)
+        for (long i = 0; i < nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, NULL, NULL);
+      for (int col = m->ncolour - 1; col >= 0; --col)
+        for (long i = 0; i < nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, NULL, NULL);
+    }
+    return;
   }
+  int *part = NULL;
+  double *old = NULL;
+  if (s->P.sweep_order == 2) {
+    const int np = s->P.n_parts > 0 ? s->P.n_parts : 1;
+    part = (int *)malloc(sizeof(int) * nc);
+    old = (double *)malloc(sizeof(double) * nc * NV);
+    for (long i = 0; i < nc; ++i) part[i] = (int)((i * np) / nc);
+  }
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    if (old) memcpy(old, dU, sizeof(double) * nc * NV);
+    for (long i = 0; i < nc; ++i) relax_cell(s, i, U, R, lam, D, dU, old, part);
+    if (old) memcpy(old, dU, sizeof(double) * nc * NV);
+    for (long i = nc - 1; i >= 0; --i) relax_cell(s, i, U, R, lam, D, dU, old, part);
+  }
+  free(part);
+  free(old);
 }
 
 /* Low-order solve of R(W~) + S = 0 from U = W_p0 (Section 3, step 4):
@@ -1342,7 +1375,7 @@ void or_lo_relax(const or_solver *s, const double *U, const double *R, int n_swe
   else {
     memset(dU, 0, sizeof(double) * m->nc * NV);
     for (int col = 0; col < m->ncolour; ++col)
-      for (long i = 0; i < m->nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU);
+      for (long i = 0; i < m->nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, NULL, NULL);
   }
   free(lam); free(D);
 }

@@ -44,7 +44,7 @@ class OrParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
                 ("time_scheme", C.c_int), ("restrict_mode", C.c_int), ("n_bc", C.c_int),
-                ("flux_lo", C.c_int), ("bc", OrBC * 16)]
+                ("flux_lo", C.c_int), ("sweep_order", C.c_int), ("n_parts", C.c_int), ("bc", OrBC * 16)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -106,7 +106,8 @@ def lib():
 def make_params(spec: dict) -> OrParams:
     """spec keys: gamma, mu, cfl_hi, cfl_lo, n_implicit, n_sweeps,
     time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
-    flux_lo ('kfvs' default | 'lf': low-level flux),
+    flux_lo ('kfvs' default | 'lf': low-level flux), sweep_order ('colour'
+    default | 'index' | 'partitioned' with n_parts partitions, default 8),
     bcs: list of dicts {kind: 'slip'|'noslip'|'farfield', uw=(u,v),
     rho, u=(u,v), p}."""
     P = OrParams()
@@ -120,6 +121,8 @@ def make_params(spec: dict) -> OrParams:
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.restrict_mode = 0
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
+    P.sweep_order = {"colour": 0, "index": 1, "partitioned": 2}[spec.get("sweep_order", "colour")]
+    P.n_parts = int(spec.get("n_parts", 8))
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):
