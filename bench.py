@@ -606,6 +606,7 @@ def main():
                             f"layers) to 20 radii: {cm.n_cells} cells, FP64; Res drop 1e-8 relative to the first "
                             "iteration; p-multigrid V-cycles vs explicit S2O4 steps, same GPU")
         line["convergence"] = conv
+        line["validation_re40"] = validation_re40(cgks)
         if not args.no_3d:
             lvl = 4 if args.converge3d_full else 3
             c3 = converge3d(cgks, lvl, 40, 20, 5e-3)
@@ -753,6 +754,47 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
                 "traffic": wm.get("sweep_traffic", SWEEP_TRAFFIC_PER_LAUNCH.get(precision)) if top == "k_sweep" else None,
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     return roof, per
+
+
+def validation_re40(cgks, max_cycles=8000, drop=1e-8):
+    """Section 4's first case: a circular cylinder at Re 40, Ma 0.15 (D = 1),
+    converged by V-cycles (FP64); drag and lift, separation angle and wake
+    length from the GPU's wall loads, beside the paper's Mesh II values
+    (their mesh is not available: context, not a target)."""
+    import torch
+    from paper_2109_09965_gb300 import meshgen, post
+    ma, re, D = 0.15, 40.0, 1.0
+    nt = 160
+    mesh = meshgen.cylinder(nt, 24, 48, growth=1.1, R_far=20.0)
+    spec = dict(gamma=GAMMA, mu=ma * D / re, cfl_hi=0.4,
+                bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(ma, 0.0), p=1.0 / GAMMA)])
+    W0 = np.zeros((mesh.n_cells, 4))
+    W0[:, 0] = 1.0
+    W0[:, 1] = ma
+    W0[:, 3] = 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * ma * ma
+    s = cgks.Solver(cgks.Mesh(mesh), spec)
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hist = []
+    while len(hist) < max_cycles and not (hist and min(hist) <= drop * hist[0]):
+        hist.extend(s.pmg_cycle(500).tolist())
+    el = time.perf_counter() - t
+    h = np.asarray(hist)
+    wall = s.wall_loads(0)
+    W, _ = s.get_state()
+    s.close()
+    cd, cl = post.force_coefficients(wall, rho=1.0, U=ma, ref=D)
+    surf = post.surface_2d(wall, rho=1.0, U=ma, p_inf=1.0 / GAMMA)
+    xc = np.array([mesh.nodes[mesh.cell_nodes[mesh.cell_ptr[c]:mesh.cell_ptr[c + 1]]].mean(0)
+                   for c in range(mesh.n_cells)])
+    return {"workload": f"circular cylinder, Re 40, Ma 0.15, D = 1: hybrid O-mesh {nt} x (24 quad + 48 "
+                        f"split-triangle layers) to 20 D, {mesh.n_cells} cells, FP64 V-cycles",
+            "cycles": int(h.size), "wall_s": el, "res_drop": float(h.min() / h[0]),
+            "Cd": cd, "Cl": cl, "separation_angle_deg": post.separation_angle(surf),
+            "wake_length_D": post.wake_length(xc, W, R=0.5, D=D, angle_band=2 * math.pi / nt),
+            "Cp_front": float(surf["Cp"][0]),
+            "paper_mesh_II": {"Cd": 1.525, "Cl": 3.3e-14, "wake_length_D": 2.22, "separation_angle_deg": 53.3}}
 
 
 def converge3d(cgks, level, n_prism, n_tet, h0, drop=1e-8, max_cycles=6000):

@@ -290,6 +290,30 @@ int cgks_reset_timing(cgks_solver *s);
 int64_t cgks_launch_count(const cgks_solver *s);
 int cgks_launches_per_call(const cgks_solver *s, int cycle);
 
+/* ---- wall loads (post-processing of a converged field) ----
+ * The momentum flux through every boundary face of one tag, evaluated by
+ * the high-order level at the current state: the smooth gas-kinetic flux
+ * F0 of Section 2.2 (pressure and viscous stress together), averaged over
+ * the face's Gauss points, in the global frame, per unit length (2-D) or
+ * area (3-D), in the direction of the face normal out of the fluid.  On a
+ * wall it is the traction the fluid exerts: the body force is
+ * sum(S * traction), and its normal and tangential parts give the surface
+ * pressure and shear (Cd, Cl, Cp, Cf and the separation angle of Section
+ * 4's cylinder and sphere tables).  At a steady state the boundary
+ * tractions of all tags balance to the residual level.
+ *   tag          boundary tag (index into cgks_params.bc[])
+ *   max_faces    capacity of the output arrays (0: count only)
+ *   n_faces      receives the number of faces with this tag
+ *   x, n         [max_faces * dim] face centre and unit normal
+ *   S            [max_faces] face length / area
+ *   traction     [max_faces * dim] momentum flux per unit length / area
+ * Host arrays, caller-owned, in the library's face order.  Runs a
+ * reconstruction and face-flux evaluation on the solver's stream and
+ * synchronises.  Returns CGKS_EINVAL (after setting n_faces) when
+ * max_faces is too small. */
+int cgks_wall_loads(cgks_solver *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *n,
+                    double *S, double *traction);
+
 /* ---- launch-shape autotuner (no counterpart in the paper) ----
  * Four kernels take a launch shape: the compact reconstruction, the
  * gas-kinetic face flux, the low-order (KFVS) face flux and the colour

@@ -105,6 +105,8 @@ SIGNATURES = {
     "cgks_reset_timing": (C.c_int, [C.c_void_p]),
     "cgks_launch_count": (C.c_int64, [C.c_void_p]),
     "cgks_launches_per_call": (C.c_int, [C.c_void_p, C.c_int]),
+    "cgks_wall_loads": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "cgks_tune_shape": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "cgks_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(CgksTuning)]),
     "cgks_set_tuning": (C.c_int, [C.c_void_p, _i32p]),
@@ -136,6 +138,11 @@ def lib(build_if_missing: bool = True):
 
 def _check(rc, what):
     if rc != 0:
+        raise CgksError(rc, what)
+
+
+def _check_or(rc, what, ok):
+    if rc not in ok:
         raise CgksError(rc, what)
 
 
@@ -336,6 +343,20 @@ class Solver:
 
     def launches_per_call(self, cycle: bool) -> int:
         return int(lib().cgks_launches_per_call(self._h, int(bool(cycle))))
+
+    def wall_loads(self, tag: int) -> dict:
+        """Boundary faces of one tag at the current state: centre x, unit
+        normal n (out of the fluid), length / area S and the momentum flux
+        `traction` the fluid exerts there (pressure and viscous stress)."""
+        k = C.c_int64(0)
+        _check_or(lib().cgks_wall_loads(self._h, int(tag), 0, C.byref(k), None, None, None, None),
+                  "cgks_wall_loads", ok=(0, -1))
+        m = k.value
+        x, n = np.zeros((m, self.dim)), np.zeros((m, self.dim))
+        S, t = np.zeros(m), np.zeros((m, self.dim))
+        _check(lib().cgks_wall_loads(self._h, int(tag), m, C.byref(k), _ptr(x), _ptr(n), _ptr(S), _ptr(t)),
+               "cgks_wall_loads")
+        return dict(x=x, n=n, S=S, traction=t)
 
     def tuning(self) -> dict:
         """Per tunable kernel: shape index in use, whether it is final, and

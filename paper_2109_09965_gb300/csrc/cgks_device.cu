@@ -1022,6 +1022,41 @@ double now_s(const cgks_server *v) {
 }  // namespace
 
 // =============================== C ABI ===================================
+// Momentum flux through the boundary faces of one tag at the current state
+// (post-processing; see include/cgks.h).
+template <typename TF>
+int wall_loads_t(cgks_solver *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm,
+                 double *S, double *traction) {
+  Batch *b = s->b;
+  const HostMesh &hm = *b->mem[0].mesh;
+  Bufs<TF> &B = bufs<TF>(b);
+  enqueue_hi_eval<TF>(b, B.W, B.Wx, B.FA);
+  const int64_t F = b->F, nf = hm.n_faces, off = b->mem[0].face_off;
+  std::vector<TF> F0(4 * static_cast<size_t>(F));
+  for (int v = 0; v < 4; ++v)
+    CK(cudaMemcpyAsync(F0.data() + v * F, B.FA + v * F, sizeof(TF) * F, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  int64_t k = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    if (hm.fc1[f] != -1 - tag) continue;
+    if (k < max_faces) {
+      const int c0 = hm.fc0[f];
+      const double h = hm.h[c0];
+      // face midpoint: the mean of its two Gauss points (offsets from c0 scaled by 1/h)
+      x[2 * k] = hm.xc[c0] + 0.5 * h * (hm.fxi[0 * nf + f] + hm.fxi[2 * nf + f]);
+      x[2 * k + 1] = hm.xc[hm.n_cells + c0] + 0.5 * h * (hm.fxi[1 * nf + f] + hm.fxi[3 * nf + f]);
+      nrm[2 * k] = hm.fn[f];
+      nrm[2 * k + 1] = hm.fn[nf + f];
+      S[k] = hm.fS[f];
+      traction[2 * k] = static_cast<double>(F0[1 * F + off + f]);
+      traction[2 * k + 1] = static_cast<double>(F0[2 * F + off + f]);
+    }
+    ++k;
+  }
+  *n_faces = k;
+  return k <= max_faces ? CGKS_OK : CGKS_EINVAL;
+}
+
 extern "C" {
 
 void cgks_default_params(cgks_params *p) {
@@ -1307,6 +1342,20 @@ int cgks_residual(cgks_solver *s, double *res, double *r_l2) {
     }
   }
   return end_call(s);
+}
+
+int cgks_wall_loads(cgks_solver *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm,
+                    double *S, double *traction) {
+  if (!s || !n_faces || tag < 0 || tag >= CGKS_MAX_BC || max_faces < 0 ||
+      (max_faces > 0 && (!x || !nrm || !S || !traction)))
+    return CGKS_EINVAL;
+  int rc = begin_call(s);
+  if (rc) return rc;
+  if (s->s3) rc = s3_wall_loads(s->s3, tag, max_faces, n_faces, x, nrm, S, traction);
+  else if (s->b->mixed) rc = wall_loads_t<float>(s, tag, max_faces, n_faces, x, nrm, S, traction);
+  else rc = wall_loads_t<double>(s, tag, max_faces, n_faces, x, nrm, S, traction);
+  const int rc2 = end_call(s);
+  return rc ? rc : rc2;
 }
 
 int cgks_get_rp0(cgks_solver *s, double *Rp0) {

@@ -68,6 +68,9 @@ struct Solver3 {
   Timer *timer = nullptr;
   long long launches = 0;
   Tuner tune;                     // launch shapes of the tunable kernels
+  // boundary faces (for the wall loads): internal face, tag, centre, normal, area
+  std::vector<int32_t> bf_face, bf_tag;
+  std::vector<double> bf_geo;     // [7] per boundary face
 };
 
 namespace {
@@ -356,6 +359,15 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   s->mixed = p->precision == CGKS_MIXED;
   s->n_colours = m.n_colours;
   s->colour_start = m.colour_start;
+  for (int64_t f = 0; f < m.n_faces; ++f) {
+    if (m.fc1[f] >= 0) continue;
+    s->bf_face.push_back(static_cast<int32_t>(f));
+    s->bf_tag.push_back(-1 - m.fc1[f]);
+    const int64_t nf = m.n_faces;
+    const double geo[7] = { m.fxf[f], m.fxf[nf + f], m.fxf[2 * nf + f], m.fn[f], m.fn[nf + f], m.fn[2 * nf + f],
+                            m.fS[f] };
+    s->bf_geo.insert(s->bf_geo.end(), geo, geo + 7);
+  }
   s->stream = stream;
   s->timer = timer;
   s->tune.on = p->autotune != 0;
@@ -605,6 +617,41 @@ int s3_residual(Solver3 *s, double *res, double *r_l2) {
       r_l2[v] = std::sqrt(a);
     }
   return CGKS_OK;
+}
+
+template <typename TF>
+int s3_wall_loads_t(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm,
+                    double *S, double *traction) {
+  Bufs3<TF> &B = bufs<TF>(s);
+  hi_eval<TF>(s, B.W, B.Wx, B.FA);
+  const int64_t F = s->F;
+  std::vector<TF> F0(3 * static_cast<size_t>(F));
+  for (int v = 1; v <= 3; ++v)
+    CK3(cudaMemcpyAsync(F0.data() + (v - 1) * F, B.FA + v * F, sizeof(TF) * F, cudaMemcpyDeviceToHost, s->stream));
+  CK3(cudaStreamSynchronize(s->stream));
+  int64_t k = 0;
+  for (size_t b = 0; b < s->bf_face.size(); ++b) {
+    if (s->bf_tag[b] != tag) continue;
+    if (k < max_faces) {
+      const double *g = &s->bf_geo[7 * b];
+      const int64_t f = s->bf_face[b];
+      for (int a = 0; a < 3; ++a) {
+        x[3 * k + a] = g[a];
+        nrm[3 * k + a] = g[3 + a];
+        traction[3 * k + a] = static_cast<double>(F0[a * F + f]);
+      }
+      S[k] = g[6];
+    }
+    ++k;
+  }
+  *n_faces = k;
+  return k <= max_faces ? CGKS_OK : CGKS_EINVAL;
+}
+
+int s3_wall_loads(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm, double *S,
+                  double *traction) {
+  return s->mixed ? s3_wall_loads_t<float>(s, tag, max_faces, n_faces, x, nrm, S, traction)
+                  : s3_wall_loads_t<double>(s, tag, max_faces, n_faces, x, nrm, S, traction);
 }
 
 int s3_get_rp0(Solver3 *s, double *Rp0) {

@@ -194,6 +194,8 @@ int s3_status(Solver3 *s, int *status);
 int s3_history(Solver3 *s, double *res_hist, int n);
 int s3_residual(Solver3 *s, double *res, double *r_l2);
 int s3_get_rp0(Solver3 *s, double *Rp0);
+int s3_wall_loads(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm, double *S,
+                  double *traction);
 long long s3_launches(const Solver3 *s);
 int s3_launches_per_call(const Solver3 *s, bool cycle);
 size_t s3_footprint(int64_t n_cells, int64_t n_faces, bool mixed);
