@@ -154,7 +154,7 @@ static int householder_ls(int m, int n, double *A, int nr, double *B, double *X)
     double norm = 0.0;
     for (int i = k; i < m; ++i) norm += A[i * n + k] * A[i * n + k];
     norm = sqrt(norm);
-    if (norm == 0.0) return -1;
+    if (!(norm > 1e-13)) return -1;   /* rank-deficient (columns are O(1) in scaled coordinates) */
     double alpha = A[k * n + k] > 0 ? -norm : norm;
     double v[64];
     for (int i = 0; i < m; ++i) v[i] = 0.0;
@@ -924,7 +924,16 @@ static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, lo
     }
     row += 2;
   }
-  if (householder_ls(neq, NM, A, NV, B, X) != 0) { s->status = 2; }
+  if (householder_ls(neq, NM, A, NV, B, X) != 0) {
+    /* rank-deficient stencil (e.g. a lone cell between two parallel walls):
+     * the same linear reconstruction as for too few neighbours */
+    for (int q = 0; q < NM * NV; ++q) c[q] = 0.0;
+    for (int v = 0; v < NV; ++v) {
+      c[0 * NV + v] = C->h * Wx[(i * 2 + 0) * NV + v];
+      c[1 * NV + v] = C->h * Wx[(i * 2 + 1) * NV + v];
+    }
+    return;
+  }
   for (int q = 0; q < NM * NV; ++q) c[q] = X[q];
 }
 

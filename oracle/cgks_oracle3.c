@@ -165,7 +165,7 @@ static int householder_ls(int m, int n, double *A, int nr, double *B, double *X)
     double norm = 0.0;
     for (int i = k; i < m; ++i) norm += A[i * n + k] * A[i * n + k];
     norm = sqrt(norm);
-    if (norm == 0.0) return -1;
+    if (!(norm > 1e-13)) return -1;   /* rank-deficient (columns are O(1) in scaled coordinates) */
     double alpha = A[k * n + k] > 0 ? -norm : norm;
     double v[MAXROWS + 8];
     for (int i = 0; i < m; ++i) v[i] = 0.0;
@@ -984,7 +984,13 @@ static void reconstruct_cell(o3_solver *s, const double *W, const double *Wx, lo
       for (int v = 0; v < NV; ++v) B[row * NV + v] = C->h * Wx[(i * ND + d) * NV + v];
     }
   }
-  if (householder_ls(row, NM, A, NV, B, X) != 0) s->status = 2;
+  if (householder_ls(row, NM, A, NV, B, X) != 0) {
+    /* rank-deficient stencil: the same linear reconstruction as above */
+    for (int q = 0; q < NM * NV; ++q) c[q] = 0.0;
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < NV; ++v) c[d * NV + v] = C->h * Wx[(i * ND + d) * NV + v];
+    return;
+  }
   for (int q = 0; q < NM * NV; ++q) c[q] = X[q];
 }
 
