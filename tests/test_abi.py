@@ -151,3 +151,18 @@ def test_default_params(cg):
     P = cg.make_params({})
     assert P.gamma == 1.4 and P.cfl_lo == 1000.0 and P.n_implicit == 6 and P.n_sweeps == 2
     assert P.alpha == 0.5 and P.use_graph == 1
+
+
+def test_empty_mesh_is_rejected(cg):
+    """A mesh without cells or nodes is an invalid argument, in 2-D and
+    3-D, before anything touches a device."""
+    import types
+    for dim in (2, 3):
+        e = types.SimpleNamespace(dim=dim, nodes=np.zeros((0, dim)), cell_type=np.zeros(0, np.uint8),
+                                  cell_ptr=np.zeros(1, np.int64), cell_nodes=np.zeros(0, np.int64),
+                                  bface_ptr=np.zeros(1, np.int64), bface_nodes=np.zeros(0, np.int64),
+                                  bface_tag=np.zeros(0, np.int32), n_cells=0, n_nodes=0, n_bfaces=0)
+        with pytest.raises(cg.CgksError) as err:
+            cg.Mesh(e)
+        assert err.value.status == -1
+

@@ -267,3 +267,19 @@ def test_lf_low_level_matches_oracle(libs, name, precision):
     tol = TOL if precision == "fp64" else 1e-5
     assert rel(Wg, Wo) < tol, rel(Wg, Wo)
     np.testing.assert_allclose(hg, ho, rtol=1e-9 if precision == "fp64" else 1e-3)
+
+
+def test_degenerate_meshes(libs):
+    """Smallest meshes against the oracle over V-cycles: two triangles (each
+    cell's only neighbour is the other), and a single quad between two slip
+    walls, whose rank-deficient stencil falls back to the linear
+    reconstruction on both sides."""
+    cgks, O = libs
+    spec = dict(gamma=GAM, mu=0.01, bcs=[dict(kind="slip"), dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)])
+    for cells in ("tri", "quad"):
+        mesh = MG.box(1, 1, cells=cells, tags=(0, 1, 0, 1))
+        W = np.tile(exact.cons_from_prim(GAM, 1.0, 0.3, 0.1, 1 / GAM), (mesh.n_cells, 1))
+        W[0, 0] *= 1.01
+        g, o = pair(libs, mesh, spec, (W, None))
+        np.testing.assert_allclose(g.pmg_cycle(3), o.pmg_cycles(3), rtol=1e-9)
+        check(g, o, cells)
