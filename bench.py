@@ -148,13 +148,19 @@ def dist_barrier(world):
         dist.barrier()
 
 
-def cpu_baseline(mesh, spec, W0, cycles=2):
-    """The FP64 CPU oracle, serial, on a bounded sample of the same workload."""
+def cpu_baseline(mesh, spec, W0, target_s=12.0):
+    """The FP64 CPU oracle, serial, on a bounded sample of the same workload:
+    as many V-cycles as fill about target_s seconds (one to time, then the
+    sample)."""
     from oracle import oracle as O
     O.build()
     om = O.OracleMesh(mesh)
     s = O.OracleSolver(om, spec)
     s.set_state(W0)
+    t = time.perf_counter()
+    s.pmg_cycles(1)
+    one = time.perf_counter() - t
+    cycles = int(max(1, min(30, target_s / max(one, 1e-3))))
     t = time.perf_counter()
     s.pmg_cycles(cycles)
     dt = time.perf_counter() - t
