@@ -59,13 +59,13 @@
 /* ------------------------------------------------------------------ */
 /* parameters (layout mirrored by the Python ctypes wrapper)           */
 /* ------------------------------------------------------------------ */
-enum { OR_BC_SLIP = 0, OR_BC_NOSLIP = 1, OR_BC_FARFIELD = 2 };
+enum { OR_BC_SLIP = 0, OR_BC_NOSLIP = 1, OR_BC_FARFIELD = 2, OR_BC_DIRICHLET = 3, OR_BC_OUTFLOW = 4 };
 
 typedef struct {
   int kind;
   int pad_;
   double uw[2];               /* wall velocity of a no-slip wall */
-  double rho, u[2], p;        /* free stream of a far-field boundary */
+  double rho, u[2], p;        /* free stream of a far-field boundary, state of a Dirichlet one */
 } or_bc;
 
 typedef struct {
@@ -80,6 +80,14 @@ typedef struct {
   int sweep_order;            /* 0 = colour classes, 1 = element index (serial),
                                  2 = index partitions with lagged exchange */
   int n_parts;                /* partitions of sweep_order 2 (the paper's threads) */
+  int flux_hi;                /* high-level flux: 0 = smooth, Eq. (2nd-smooth-flux);
+                                 1 = full, Eq. (2nd-flux) */
+  int pad_;
+  double tau_c1, tau_c2;      /* numerical collision time of the full flux:
+                                 tau_n = tau + C1 dt + C2 dt |p_l - p_r| / (p_l + p_r) */
+  double weno_eps;            /* > 0: nonlinear compact WENO weights with this epsilon;
+                                 <= 0: linear weights */
+  double weno_g0;             /* linear weight of the quadratic candidate */
   or_bc bc[MAXBC];
 } or_params;
 
@@ -394,6 +402,166 @@ void or_gks_flux_point(const or_params *P, const double Wl_g[NV], const double W
   to_global(n, Wtl, Wt_out);
 }
 
+/* ------------------------------------------------------------------ */
+/* Full gas-kinetic flux at one Gauss point, Eq. (2nd-flux), for flows  */
+/* with discontinuities (Section 4: transonic and supersonic cases):    */
+/*   f = (1 - e) g^c + [(t + tau) e - tau] a^c.u g^c                    */
+/*       + (t - tau + tau e) A^c g^c                                    */
+/*       + e g^l [1 - (tau + t) a^l.u - tau A^l] H(u)                   */
+/*       + e g^r [1 - (tau + t) a^r.u - tau A^r] (1 - H(u)),            */
+/* e = exp(-t / tau_n), tau = mu / p^c (Section 2.3).  tau_n (the paper */
+/* adopts the one of its compact-GKS reference without printing it) is  */
+/* read as tau + C1 dt + C2 dt |p_l - p_r| / (p_l + p_r).  The time     */
+/* dependence is brought to the form F0 + t F1 used by the time         */
+/* schemes through the integrals over [0, dt] and [0, dt/2]            */
+/* (two-stage GKS): F0 dt + F1 dt^2/2 = Fhat(dt),                       */
+/* F0 dt/2 + F1 dt^2/8 = Fhat(dt/2); likewise the interface state       */
+/* W_p(t) = <psi f(t)> is represented by the line through its values at */
+/* dt/2 and dt.  Same arguments as or_gks_flux_point plus dt.           */
+/* ------------------------------------------------------------------ */
+typedef struct { double c1, c2, c3, e, te; } or_tcoef;
+
+/* the five coefficient functions of Eq. (2nd-flux) at time t */
+static or_tcoef tcoef_at(double t, double tau, double taun) {
+  or_tcoef c;
+  double e = taun > 0.0 ? exp(-t / taun) : 0.0;
+  c.c1 = 1.0 - e;
+  c.c2 = (t + tau) * e - tau;
+  c.c3 = t - tau + tau * e;
+  c.e = e;
+  c.te = t * e;
+  return c;
+}
+/* their integrals over [0, T] */
+static or_tcoef tcoef_int(double T, double tau, double taun) {
+  or_tcoef c;
+  double E = taun > 0.0 ? exp(-T / taun) : 0.0;
+  double om = taun > 0.0 ? -expm1(-T / taun) : 1.0;      /* 1 - E */
+  c.e = taun * om;                                       /* int e */
+  c.te = taun * taun * om - taun * T * E;                /* int t e */
+  c.c1 = T - c.e;
+  c.c2 = c.te + tau * c.e - tau * T;
+  c.c3 = 0.5 * T * T - tau * T + tau * c.e;
+  return c;
+}
+
+/* Moments of one Maxwellian piece (full or half range table m) with its
+ * slopes an, at, A: Q* the normal fluxes, P* the states, each times rho:
+ *   Q0 = <u psi>, Q1 = <u (an u + at v) psi>, Q2 = <u A psi>,
+ *   P0 = <psi>,   P1 = <(an u + at v) psi>,   P2 = <A psi>. */
+static void piece_moments(double rho, const or_mom *m, const double an[NV], const double at[NV],
+                          const double A[NV], double Q[3][NV], double Pm[3][NV]) {
+  for (int r = 0; r < NV; ++r) {
+    Q[0][r] = rho * mom_psi_uv(r, 1.0, 1, 0, m);
+    Q[1][r] = rho * (mom_psi_uv_slope(r, 2, 0, an, m) + mom_psi_uv_slope(r, 1, 1, at, m));
+    Q[2][r] = rho * mom_psi_uv_slope(r, 1, 0, A, m);
+    Pm[0][r] = rho * mom_psi_uv(r, 1.0, 0, 0, m);
+    Pm[1][r] = rho * (mom_psi_uv_slope(r, 1, 0, an, m) + mom_psi_uv_slope(r, 0, 1, at, m));
+    Pm[2][r] = rho * mom_psi_uv_slope(r, 0, 0, A, m);
+  }
+}
+
+/* spatial slopes of a Maxwellian from its normal / tangential derivatives,
+ * and the temporal slope from <A + a_n u + a_t v> = 0 */
+static void maxw_slopes(const or_mom *m, double rho, const double dn[NV], const double dt[NV], double an[NV],
+                        double at[NV], double A[NV]) {
+  micro_slope(m, rho, dn, an);
+  micro_slope(m, rho, dt, at);
+  double bA[NV];
+  for (int r = 0; r < NV; ++r)
+    bA[r] = -(mom_psi_uv_slope(r, 1, 0, an, m) + mom_psi_uv_slope(r, 0, 1, at, m)) * rho;
+  micro_slope(m, rho, bA, A);
+}
+
+/* the combination of Eq. (2nd-flux) with coefficients c of the pieces
+ * X[piece][moment][r] (piece 0 = equilibrium, 1 = left, 2 = right) */
+static void full_combine(const or_tcoef *c, double tau, double X[3][3][NV], double out[NV]) {
+  for (int r = 0; r < NV; ++r)
+    out[r] = c->c1 * X[0][0][r] + c->c2 * X[0][1][r] + c->c3 * X[0][2][r]
+           + c->e * (X[1][0][r] - tau * X[1][1][r] - tau * X[1][2][r]
+                     + X[2][0][r] - tau * X[2][1][r] - tau * X[2][2][r])
+           - c->te * (X[1][1][r] + X[2][1][r]);
+}
+
+void or_gks_full_flux_point(const or_params *P, const double Wl_g[NV], const double Wr_g[NV],
+                            const double gl[2 * NV], const double gr[2 * NV], const double n[2], double delta,
+                            double dt, double F0[NV], double F1[NV], double Wc_out[NV], double Wt_out[NV]) {
+  double K = or_K(P->gamma);
+  double t[2] = { -n[1], n[0] };
+  double Wl[NV], Wr[NV];
+  to_local(n, Wl_g, Wl);
+  to_local(n, Wr_g, Wr);
+  double dn_l[NV], dt_l[NV], dn_r[NV], dt_r[NV], tmp_n[NV], tmp_t[NV];
+  for (int v = 0; v < NV; ++v) {
+    tmp_n[v] = n[0] * gl[v] + n[1] * gl[NV + v];
+    tmp_t[v] = t[0] * gl[v] + t[1] * gl[NV + v];
+  }
+  to_local(n, tmp_n, dn_l); to_local(n, tmp_t, dt_l);
+  for (int v = 0; v < NV; ++v) {
+    tmp_n[v] = n[0] * gr[v] + n[1] * gr[NV + v];
+    tmp_t[v] = t[0] * gr[v] + t[1] * gr[NV + v];
+  }
+  to_local(n, tmp_n, dn_r); to_local(n, tmp_t, dt_r);
+
+  /* the two initial Maxwellians: half-range tables for the free-transport
+   * terms, full-range tables for their slopes */
+  or_maxw gl_ = maxw_from_W(Wl, K), gr_ = maxw_from_W(Wr, K);
+  or_mom mlh, mrh, mlf, mrf;
+  moments(&gl_, K, +1, &mlh);
+  moments(&gr_, K, -1, &mrh);
+  moments(&gl_, K, 0, &mlf);
+  moments(&gr_, K, 0, &mrf);
+  double an_l[NV], at_l[NV], A_l[NV], an_r[NV], at_r[NV], A_r[NV];
+  maxw_slopes(&mlf, gl_.rho, dn_l, dt_l, an_l, at_l, A_l);
+  maxw_slopes(&mrf, gr_.rho, dn_r, dt_r, an_r, at_r, A_r);
+
+  /* equilibrium W^c and its slopes, as for the smooth flux */
+  double Wc[NV];
+  for (int r = 0; r < NV; ++r)
+    Wc[r] = gl_.rho * mom_psi_uv(r, 1.0, 0, 0, &mlh) + gr_.rho * mom_psi_uv(r, 1.0, 0, 0, &mrh);
+  double dWn[NV], dWt[NV];
+  for (int v = 0; v < NV; ++v) {
+    dWn[v] = 0.5 * (dn_l[v] + dn_r[v]);
+    if (delta > 0.0) dWn[v] += P->alpha * (Wr[v] - Wl[v]) / delta;
+    dWt[v] = 0.5 * (dt_l[v] + dt_r[v]);
+  }
+  or_maxw gc = maxw_from_W(Wc, K);
+  or_mom mc;
+  moments(&gc, K, 0, &mc);
+  double an[NV], at[NV], A[NV];
+  maxw_slopes(&mc, gc.rho, dWn, dWt, an, at, A);
+
+  /* collision times */
+  double pc = gc.rho / (2.0 * gc.lam);
+  double pl = gl_.rho / (2.0 * gl_.lam), pr = gr_.rho / (2.0 * gr_.lam);
+  double tau = P->mu / pc;
+  double taun = tau + P->tau_c1 * dt + P->tau_c2 * dt * fabs(pl - pr) / (pl + pr);
+
+  double Q[3][3][NV], Pm[3][3][NV];
+  piece_moments(gc.rho, &mc, an, at, A, Q[0], Pm[0]);
+  piece_moments(gl_.rho, &mlh, an_l, at_l, A_l, Q[1], Pm[1]);
+  piece_moments(gr_.rho, &mrh, an_r, at_r, A_r, Q[2], Pm[2]);
+
+  or_tcoef I1 = tcoef_int(dt, tau, taun), Ih = tcoef_int(0.5 * dt, tau, taun);
+  or_tcoef C1 = tcoef_at(dt, tau, taun), Ch = tcoef_at(0.5 * dt, tau, taun);
+  double Fd[NV], Fh[NV], Wd[NV], Wh[NV];
+  full_combine(&I1, tau, Q, Fd);
+  full_combine(&Ih, tau, Q, Fh);
+  full_combine(&C1, tau, Pm, Wd);
+  full_combine(&Ch, tau, Pm, Wh);
+  double F0l[NV], F1l[NV], Wcl[NV], Wtl[NV];
+  for (int r = 0; r < NV; ++r) {
+    F0l[r] = (4.0 * Fh[r] - Fd[r]) / dt;
+    F1l[r] = 4.0 * (Fd[r] - 2.0 * Fh[r]) / (dt * dt);
+    Wcl[r] = 2.0 * Wh[r] - Wd[r];
+    Wtl[r] = 2.0 * (Wd[r] - Wh[r]) / dt;
+  }
+  to_global(n, F0l, F0);
+  to_global(n, F1l, F1);
+  to_global(n, Wcl, Wc_out);
+  to_global(n, Wtl, Wt_out);
+}
+
 /* First-order kinetic flux vector splitting (Section 3, step 3): the
  * half-range fluxes of the two cell-average Maxwellians. */
 void or_kfvs(const or_params *P, const double Wl_g[NV], const double Wr_g[NV], const double n[2],
@@ -524,6 +692,15 @@ void or_ghost(const or_params *P, int tag, const double W[NV], const double grad
       double ke_b = ug[0] * dug[0][b] + ug[1] * dug[1][b];
       gradg[b * NV + 3] = dpg[b] / (g - 1.0) + 0.5 * (ug[0] * ug[0] + ug[1] * ug[1]) * drg[b] + rho * ke_b;
     }
+  } else if (bc->kind == OR_BC_DIRICHLET) {
+    /* prescribed state, uniform outside (Section 4, shock reflection) */
+    cons(g, bc->rho, bc->u, bc->p, Wg);
+    for (int k = 0; k < 2 * NV; ++k) gradg[k] = 0.0;
+  } else if (bc->kind == OR_BC_OUTFLOW) {
+    /* supersonic outflow: every characteristic leaves the domain, the
+     * outside continues the inside (state and gradient copied) */
+    for (int v = 0; v < NV; ++v) Wg[v] = W[v];
+    for (int k = 0; k < 2 * NV; ++k) gradg[k] = grad[k];
   } else {
     farfield_state(P, bc, W, n, Wg);
     for (int k = 0; k < 2 * NV; ++k) gradg[k] = 0.0;
@@ -853,7 +1030,76 @@ static void mirror_mean_monomials(const or_mesh *m, long i, const or_face *F, do
 }
 
 static int is_wall(const or_solver *s, const or_face *F) {
-  return F->c1 < 0 && s->P.bc[F->tag].kind != OR_BC_FARFIELD;
+  if (F->c1 >= 0) return 0;
+  int k = s->P.bc[F->tag].kind;
+  return k == OR_BC_SLIP || k == OR_BC_NOSLIP;
+}
+
+/* Smoothness indicator of a candidate polynomial with scaled coefficients
+ * c (monomials of (x - xc)/h, h^2 = |Omega|): the sum over the
+ * derivative multi-indices alpha with 1 <= |alpha| <= 2 of the cell mean of
+ * (h^|alpha| D^alpha P)^2.  The cell mean of the squared first derivatives
+ * is taken by the edge-midpoint rule on a fan of triangles (exact for the
+ * quadratic integrand). */
+static double weno_beta(const or_mesh *m, long i, const double *c, int stride) {
+  const or_cell *C = &m->cell[i];
+  double c0 = c[0], c1 = c[stride], c2 = c[2 * stride], c3 = c[3 * stride], c4 = c[4 * stride];
+  double sum = 0.0, A = 0.0;
+  const double *x0 = &m->x[2 * C->node[0]];
+  for (int k = 1; k + 1 < C->nv; ++k) {
+    const double *x1 = &m->x[2 * C->node[k]], *x2 = &m->x[2 * C->node[k + 1]];
+    double a = 0.5 * ((x1[0] - x0[0]) * (x2[1] - x0[1]) - (x2[0] - x0[0]) * (x1[1] - x0[1]));
+    const double *P[3] = { x0, x1, x2 };
+    for (int e = 0; e < 3; ++e) {
+      double xi = (0.5 * (P[e][0] + P[(e + 1) % 3][0]) - C->xc[0]) / C->h;
+      double eta = (0.5 * (P[e][1] + P[(e + 1) % 3][1]) - C->xc[1]) / C->h;
+      double px = c0 + 2.0 * c2 * xi + c3 * eta, py = c1 + c3 * xi + 2.0 * c4 * eta;
+      sum += a / 3.0 * (px * px + py * py);
+    }
+    A += a;
+  }
+  return sum / A + 4.0 * c2 * c2 + c3 * c3 + 4.0 * c4 * c4;
+}
+
+/* Compact WENO with nonlinear weights (Section 4 names it for the
+ * transonic and supersonic cases and gives its epsilon; the scheme itself
+ * is the cited one, read here as follows).  Candidates of cell i: the
+ * compact quadratic P2 (coefficients X) and the linear polynomials
+ * W_i + h g.(xi, eta) with g the cell-mean gradient of the cell itself and
+ * of each face neighbour.  Linear weights gamma_0 = g0 for P2 and
+ * (1 - g0)/m for each of the m linear ones; nonlinear weights
+ * w_k ~ gamma_k / (beta_k + eps)^2, normalised; the result
+ *   P = (w_0 / gamma_0) (P2 - sum_k gamma_k P1_k) + sum_k w_k P1_k
+ * equals P2 when w = gamma and keeps the cell mean.  Per variable.
+ * X is updated in place. */
+static void weno_combine(const or_solver *s, const double *Wx, long i, double *X) {
+  const or_mesh *m = s->m;
+  const or_cell *C = &m->cell[i];
+  double g0 = s->P.weno_g0, eps = s->P.weno_eps;
+  long cand[5];
+  int nk = 0;
+  cand[nk++] = i;
+  for (int k = 0; k < C->nb; ++k) cand[nk++] = C->nbr[k];
+  double gk = (1.0 - g0) / nk;
+  for (int v = 0; v < NV; ++v) {
+    double G[5][2];
+    double wt[6], wsum = 0.0;
+    wt[0] = g0 / ((weno_beta(m, i, &X[v], NV) + eps) * (weno_beta(m, i, &X[v], NV) + eps));
+    for (int k = 0; k < nk; ++k) {
+      double cl[NM] = { C->h * Wx[(cand[k] * 2 + 0) * NV + v], C->h * Wx[(cand[k] * 2 + 1) * NV + v], 0, 0, 0 };
+      G[k][0] = cl[0]; G[k][1] = cl[1];
+      double b = weno_beta(m, i, cl, 1);
+      wt[k + 1] = gk / ((b + eps) * (b + eps));
+    }
+    for (int k = 0; k <= nk; ++k) wsum += wt[k];
+    for (int k = 0; k <= nk; ++k) wt[k] /= wsum;
+    for (int q = 0; q < NM; ++q) {
+      double lin = 0.0, sel = 0.0;
+      if (q < 2)
+        for (int k = 0; k < nk; ++k) { lin += gk * G[k][q]; sel += wt[k + 1] * G[k][q]; }
+      X[q * NV + v] = wt[0] / g0 * (X[q * NV + v] - lin) + sel;
+    }
+  }
 }
 
 static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, long i) {
@@ -934,6 +1180,7 @@ static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, lo
     }
     return;
   }
+  if (s->P.weno_eps > 0.0) weno_combine(s, Wx, i, X);
   for (int q = 0; q < NM * NV; ++q) c[q] = X[q];
 }
 
@@ -972,7 +1219,7 @@ void or_recon_eval(const or_solver *s, long cell, const double x[2], double val[
 /* High-order evaluation: reconstruction + face fluxes (Sections 2.1-2.3) */
 /* Stores per face the weighted Gauss sums of F0, F1, W^c and W_t.      */
 /* ------------------------------------------------------------------ */
-static void hi_eval(or_solver *s, const double *W, const double *Wx) {
+static void hi_eval(or_solver *s, const double *W, const double *Wx, double dt) {
   const or_mesh *m = s->m;
   reconstruct_all(s, W, Wx);
   for (long f = 0; f < m->nf; ++f) {
@@ -982,15 +1229,18 @@ static void hi_eval(or_solver *s, const double *W, const double *Wx) {
       double Wl[NV], gl[2 * NV], Wr[NV], gr[2 * NV];
       recon_eval(s, W, F->c0, F->xg[k], Wl, gl);
       if (F->c1 >= 0) recon_eval(s, W, F->c1, F->xg[k], Wr, gr);
-      else if (is_wall(s, F)) or_ghost(&s->P, F->tag, Wl, gl, F->n, Wr, gr);
+      else if (is_wall(s, F) || s->P.bc[F->tag].kind == OR_BC_OUTFLOW)
+        or_ghost(&s->P, F->tag, Wl, gl, F->n, Wr, gr);
       else {
         /* far field: Riemann-invariant state from the cell mean and the free
-         * stream, uniform (zero gradient) outside */
+         * stream, uniform (zero gradient) outside; Dirichlet: the given
+         * state, uniform outside */
         double zero[2 * NV] = { 0 };
         or_ghost(&s->P, F->tag, &W[F->c0 * NV], zero, F->n, Wr, gr);
       }
       double f0[NV], f1[NV], wc[NV], wt[NV];
-      or_gks_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, f0, f1, wc, wt);
+      if (s->P.flux_hi) or_gks_full_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, dt, f0, f1, wc, wt);
+      else or_gks_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, f0, f1, wc, wt);
       for (int v = 0; v < NV; ++v) {
         sF0[v] += F->wg[k] * f0[v]; sF1[v] += F->wg[k] * f1[v];
         sWc[v] += F->wg[k] * wc[v]; sWt[v] += F->wg[k] * wt[v];
@@ -1074,7 +1324,7 @@ static void hi_step(or_solver *s, const double *W, const double *Wx, double dt,
                     double *Wn, double *Wxn, double *Rlag) {
   const or_mesh *m = s->m;
   long nc = m->nc, nf = m->nf;
-  hi_eval(s, W, Wx);
+  hi_eval(s, W, Wx, dt);
   if (s->P.time_scheme == 0) {
     /* S1O2 (Section 2.4): W^{n+1} = W^n + dt L + dt^2/2 dL/dt; the
      * interface state at t^{n+1} feeds the Gauss-Green update */
@@ -1097,7 +1347,7 @@ static void hi_step(or_solver *s, const double *W, const double *Wx, double dt,
     for (long c = 0; c < nc; ++c)
       for (int v = 0; v < NV; ++v) Ws[c * NV + v] = W[c * NV + v] + dt / m->cell[c].vol * R[c * NV + v];
     gauss_green(s, Wcn, s->Wt, 0.5 * dt, Wxs);
-    hi_eval(s, Ws, Wxs);
+    hi_eval(s, Ws, Wxs, dt);
     /* Rlag = -sum S (F0^n + dt/6 (F1^n + 2 F1*)) */
     double *F1c = (double *)malloc(sizeof(double) * nf * NV);
     for (long q = 0; q < nf * NV; ++q) F1c[q] = F1n[q] + 2.0 * s->F1[q];
@@ -1135,7 +1385,7 @@ double or_highorder_step(or_solver *s, double dt) {
 /* High-order residual R_i = -sum_p S_p (F0 + dt/2 F1).n at the current
  * state: the time-averaged net flux over [t, t+dt] (Section 3, step 2). */
 void or_hi_residual(or_solver *s, double dt, double *R) {
-  hi_eval(s, s->W, s->Wx);
+  hi_eval(s, s->W, s->Wx, dt);
   net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, R);
 }
 
@@ -1323,7 +1573,7 @@ static void pmg_cycle(or_solver *s) {
   hi_step(s, s->W, s->Wx, dt, Wn, Wxn, Rlag);
   /* 2: restriction W_p0 = W^{n+1}, residual R_p0 = R(W^{n+1}): the
    * time-averaged net flux over [t^{n+1}, t^{n+1} + dt] */
-  hi_eval(s, Wn, Wxn);
+  hi_eval(s, Wn, Wxn, dt);
   net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, s->Rp0);
   /* 3-4: forcing and low-order implicit solve */
   lo_solve(s, Wn, s->Rp0, U);

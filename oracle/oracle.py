@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 NV = 4
-BC_SLIP, BC_NOSLIP, BC_FARFIELD = 0, 1, 2
+BC_SLIP, BC_NOSLIP, BC_FARFIELD, BC_DIRICHLET, BC_OUTFLOW = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +44,9 @@ class OrParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
                 ("time_scheme", C.c_int), ("restrict_mode", C.c_int), ("n_bc", C.c_int),
-                ("flux_lo", C.c_int), ("sweep_order", C.c_int), ("n_parts", C.c_int), ("bc", OrBC * 16)]
+                ("flux_lo", C.c_int), ("sweep_order", C.c_int), ("n_parts", C.c_int),
+                ("flux_hi", C.c_int), ("pad_", C.c_int), ("tau_c1", C.c_double), ("tau_c2", C.c_double),
+                ("weno_eps", C.c_double), ("weno_g0", C.c_double), ("bc", OrBC * 16)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -95,6 +97,8 @@ def lib():
             L.or_set_rp0.argtypes = [vp, _dp]
             L.or_get_rp0.argtypes = [vp, _dp]
             L.or_gks_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
+            L.or_gks_full_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                                 _dp, _dp, _dp, _dp]
             L.or_kfvs.argtypes = [P, _dp, _dp, _dp, _dp]
             L.or_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.or_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -108,8 +112,12 @@ def make_params(spec: dict) -> OrParams:
     time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
     flux_lo ('kfvs' default | 'lf': low-level flux), sweep_order ('colour'
     default | 'index' | 'partitioned' with n_parts partitions, default 8),
-    bcs: list of dicts {kind: 'slip'|'noslip'|'farfield', uw=(u,v),
-    rho, u=(u,v), p}."""
+    flux_hi ('smooth' default | 'full': Eq. (2nd-flux) with
+    tau_n = tau + tau_c1 dt + tau_c2 dt |p_l - p_r| / (p_l + p_r), defaults
+    0.01 and 1), weno_eps (> 0: nonlinear compact WENO weights, default 0 =
+    linear weights), weno_g0 (linear weight of the quadratic, default 0.95),
+    bcs: list of dicts {kind: 'slip'|'noslip'|'farfield'|'dirichlet'|
+    'outflow', uw=(u,v), rho, u=(u,v), p}."""
     P = OrParams()
     P.gamma = float(spec.get("gamma", 1.4))
     P.mu = float(spec.get("mu", 0.0))
@@ -123,10 +131,16 @@ def make_params(spec: dict) -> OrParams:
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
     P.sweep_order = {"colour": 0, "index": 1, "partitioned": 2}[spec.get("sweep_order", "colour")]
     P.n_parts = int(spec.get("n_parts", 8))
+    P.flux_hi = {"smooth": 0, "full": 1}[spec.get("flux_hi", "smooth")]
+    P.tau_c1 = float(spec.get("tau_c1", 0.01))
+    P.tau_c2 = float(spec.get("tau_c2", 1.0))
+    P.weno_eps = float(spec.get("weno_eps", 0.0))
+    P.weno_g0 = float(spec.get("weno_g0", 0.95))
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):
-        P.bc[i].kind = {"slip": BC_SLIP, "noslip": BC_NOSLIP, "farfield": BC_FARFIELD}[b["kind"]]
+        P.bc[i].kind = {"slip": BC_SLIP, "noslip": BC_NOSLIP, "farfield": BC_FARFIELD, "dirichlet": BC_DIRICHLET,
+                        "outflow": BC_OUTFLOW}[b["kind"]]
         uw = b.get("uw", (0.0, 0.0))
         P.bc[i].uw[0], P.bc[i].uw[1] = float(uw[0]), float(uw[1])
         P.bc[i].rho = float(b.get("rho", 1.0))
@@ -287,6 +301,15 @@ def gks_flux_point(spec, Wl, Wr, gl, gr, n, delta=0.0):
     F0 = np.zeros(NV); F1 = np.zeros(NV); Wc = np.zeros(NV); Wt = np.zeros(NV)
     lib().or_gks_flux_point(C.byref(P), _f64(Wl), _f64(Wr), _f64(gl, (2 * NV,)), _f64(gr, (2 * NV,)),
                             _f64(n), float(delta), F0, F1, Wc, Wt)
+    return F0, F1, Wc, Wt
+
+
+def gks_full_flux_point(spec, Wl, Wr, gl, gr, n, delta, dt):
+    """Full flux, Eq. (2nd-flux), as F0 + t F1 and W^c + t W_t over [0, dt]."""
+    P = make_params(spec)
+    F0 = np.zeros(NV); F1 = np.zeros(NV); Wc = np.zeros(NV); Wt = np.zeros(NV)
+    lib().or_gks_full_flux_point(C.byref(P), _f64(Wl), _f64(Wr), _f64(gl, (2 * NV,)), _f64(gr, (2 * NV,)),
+                                 _f64(n), float(delta), float(dt), F0, F1, Wc, Wt)
     return F0, F1, Wc, Wt
 
 

@@ -151,6 +151,43 @@ def box(nx: int, ny: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0, *, jitter=0.0, seed=0,
 # Boundary tags used by the named workloads.
 CAVITY_WALL, CAVITY_LID = 0, 1
 CYL_WALL, CYL_FARFIELD = 0, 1
+SR_WALL, SR_OUTFLOW, SR_TOP, SR_INFLOW = 0, 1, 2, 3
+
+
+def shock_reflection(nx: int = 120, ny: int = 30) -> Mesh:
+    """Regular shock reflection (Section 4): the rectangle [0, 4] x [0, 1]
+    on an nx x ny Cartesian grid of quads (the paper's 120 x 30 x 2 is this
+    grid extruded by two layers).  Tags: 0 = reflective wall (bottom),
+    1 = supersonic outflow (right), 2 = Dirichlet post-shock state (top),
+    3 = Dirichlet free stream (left)."""
+    return box(nx, ny, 0.0, 4.0, 0.0, 1.0, cells="quad", tags=(SR_WALL, SR_OUTFLOW, SR_TOP, SR_INFLOW),
+               name="shock_reflection")
+
+
+# Section 4, shock reflection: free stream on the left, the state behind
+# the incident oblique shock on the top, (rho, u, v, p).
+SR_LEFT = (1.0, 2.9, 0.0, 1.0 / 1.4)
+SR_UP = (1.69997, 2.61934, -0.50632, 1.52819)
+
+
+def shock_reflection_case(nx: int = 120, ny: int = 30, weno_eps: float = 1e-2, gamma: float = 1.4):
+    """Mesh, problem settings (the dict both the library and the oracle
+    read) and initial state (the left state everywhere) of the shock
+    reflection problem: inviscid, full flux of Eq. (2nd-flux), compact
+    WENO with the given epsilon."""
+    mesh = shock_reflection(nx, ny)
+
+    def bc(kind, st=None):
+        d = dict(kind=kind)
+        if st is not None:
+            d.update(rho=st[0], u=(st[1], st[2]), p=st[3])
+        return d
+
+    spec = dict(gamma=gamma, mu=0.0, flux_hi="full", weno_eps=weno_eps, cfl_hi=0.4,
+                bcs=[bc("slip"), bc("outflow"), bc("dirichlet", SR_UP), bc("dirichlet", SR_LEFT)])
+    rho, u, v, p = SR_LEFT
+    w = np.array([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+    return mesh, spec, np.tile(w, (mesh.n_cells, 1))
 
 
 def cavity(n: int = 32, *, jitter: float = 0.1, seed: int = 1) -> Mesh:

@@ -1,0 +1,164 @@
+"""Pins of the oracle's compact WENO reconstruction and of the Dirichlet
+and supersonic-outflow boundaries (Section 4, transonic / supersonic cases
+and the shock reflection problem).
+
+* epsilon -> infinity gives back the linear-weight reconstruction (the
+  nonlinear weights tend to the linear ones, as Section 4 observes);
+* every candidate is exact for linear fields, so the WENO result is too,
+  for any epsilon;
+* across a steep front the nonlinear weights cut the overshoot of the
+  linear-weight quadratic;
+* the boundary ghosts are the given state (Dirichlet) and the inside
+  continued (outflow); a uniform supersonic stream is kept to round-off
+  by the full flux with WENO through these boundaries;
+* the two states of the shock reflection problem satisfy the oblique-shock
+  jump conditions (a check of the case data as printed).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2109_09965_gb300 import meshgen as MG
+from tests import exact
+from tests.test_oracle_scheme import mixed_mesh
+
+GAM = 1.4
+
+
+def recon_at_gauss_points(O, mesh, spec, W, Wx):
+    om = O.OracleMesh(mesh)
+    s = O.OracleSolver(om, spec)
+    s.set_state(W, Wx)
+    s.reconstruct()
+    F = om.faces()
+    vals, grads, pts = [], [], []
+    for f in range(om.n_faces):
+        for side in ("c0", "c1"):
+            c = F[side][f]
+            if c < 0:
+                continue
+            for k in range(2):
+                x = F["xg"][f, k]
+                v, g = s.recon_eval(c, x)
+                vals.append(v); grads.append(g); pts.append((c, x))
+    return np.array(vals), np.array(grads), pts
+
+
+def random_field(mesh, seed):
+    rng = np.random.default_rng(seed)
+    C = rng.normal(size=(6, 4))
+    C[0] += np.array([2.0, 0.5, 0.3, 4.0])
+
+    def q(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        mono = [np.ones_like(x), x, y, x * x, x * y, y * y]
+        return sum(m[..., None] * C[k] for k, m in enumerate(mono)) + 0.3 * np.sin(3 * x + 2 * y)[..., None]
+    return exact.cell_averages(mesh, q)
+
+
+def test_large_epsilon_gives_linear_weights(oracle_lib):
+    O = oracle_lib
+    mesh = mixed_mesh(8)
+    W, Wx = random_field(mesh, 30)
+    base = dict(gamma=GAM, bcs=[dict(kind="farfield")])
+    v0, g0, _ = recon_at_gauss_points(O, mesh, base, W, Wx)
+    v1, g1, _ = recon_at_gauss_points(O, mesh, dict(base, weno_eps=1e30), W, Wx)
+    np.testing.assert_allclose(v1, v0, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(g1, g0, rtol=1e-11, atol=1e-11)
+    # a small epsilon does change the non-linear field
+    v2, _, _ = recon_at_gauss_points(O, mesh, dict(base, weno_eps=1e-6), W, Wx)
+    assert np.abs(v2 - v0).max() > 1e-4
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-6])
+def test_weno_exact_for_linear_fields(oracle_lib, eps):
+    O = oracle_lib
+    mesh = mixed_mesh(8, seed=31)
+    C = np.random.default_rng(32).normal(size=(3, 4))
+    C[0] += np.array([2.0, 0.5, 0.3, 4.0])
+
+    def q(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        return C[0] + x[..., None] * C[1] + y[..., None] * C[2]
+    W, Wx = exact.cell_averages(mesh, q)
+    spec = dict(gamma=GAM, weno_eps=eps, bcs=[dict(kind="farfield")])
+    v, g, pts = recon_at_gauss_points(O, mesh, spec, W, Wx)
+    ref = np.array([q(x[0], x[1]) for _, x in pts])
+    np.testing.assert_allclose(v, ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g, np.broadcast_to(C[1:3], g.shape), rtol=1e-10, atol=1e-10)
+
+
+def test_weno_cuts_overshoot_at_a_front(oracle_lib):
+    O = oracle_lib
+    mesh = MG.box(16, 8, 0.0, 2.0, 0.0, 1.0, jitter=0.2, seed=33, cells="tri", tags=(0, 0, 0, 0))
+
+    def q(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        s = np.tanh((x - 1.03 - 0.2 * y) / 0.01)
+        return np.stack([1.5 + 0.5 * s, 0.2 + 0.1 * s, 0.05 * s, 3.0 + s], -1)
+    W, Wx = exact.cell_averages(mesh, q)
+    lo, hi = W.min(0), W.max(0)
+    base = dict(gamma=GAM, bcs=[dict(kind="farfield")])
+
+    def overshoot(spec):
+        v, _, _ = recon_at_gauss_points(O, mesh, spec, W, Wx)
+        return np.maximum(v - hi, lo - v).max(0).max()
+    lin = overshoot(base)
+    nl = overshoot(dict(base, weno_eps=1e-6))
+    assert lin > 0.05, lin
+    assert nl < 0.25 * lin, (nl, lin)
+
+
+def test_dirichlet_and_outflow_ghosts(oracle_lib):
+    O = oracle_lib
+    rng = np.random.default_rng(34)
+    spec = dict(gamma=GAM, bcs=[dict(kind="dirichlet", rho=1.7, u=(2.6, -0.5), p=1.5), dict(kind="outflow")])
+    ref = exact.cons_from_prim(GAM, 1.7, 2.6, -0.5, 1.5)
+    for _ in range(3):
+        W = np.array([1.2, 0.3, -0.2, 2.5]) + rng.uniform(-0.1, 0.1, 4)
+        G = rng.normal(size=(2, 4))
+        th = rng.uniform(0, 2 * np.pi)
+        n = np.array([math.cos(th), math.sin(th)])
+        Wg, Gg = O.ghost(spec, 0, W, G, n)
+        np.testing.assert_array_equal(Wg, ref)
+        np.testing.assert_array_equal(Gg, 0.0)
+        Wg, Gg = O.ghost(spec, 1, W, G, n)
+        np.testing.assert_array_equal(Wg, W)
+        np.testing.assert_array_equal(Gg, G)
+
+
+@pytest.mark.parametrize("scheme", ["S1O2", "S2O4"])
+def test_supersonic_stream_kept_through_dirichlet_and_outflow(oracle_lib, scheme):
+    O = oracle_lib
+    mesh, spec, W0 = MG.shock_reflection_case(12, 4, weno_eps=1e-2)
+    # the top boundary carries the free stream too: a uniform stream is steady
+    spec["bcs"][MG.SR_TOP] = dict(spec["bcs"][MG.SR_INFLOW])
+    spec["time_scheme"] = scheme
+    s = O.OracleSolver(O.OracleMesh(mesh), spec)
+    s.set_state(W0)
+    s.explicit_steps(3)
+    s.pmg_cycles(2)
+    W, Wx = s.get_state()
+    assert np.abs(W - W0).max() < 1e-13 * np.abs(W0).max()
+    assert np.abs(Wx).max() < 1e-11
+
+
+def test_shock_reflection_states_satisfy_the_jump_conditions():
+    """The two printed states are the two sides of an oblique shock: the
+    velocity jump is normal to the shock, and mass, normal momentum and
+    total enthalpy fluxes agree across it (to the printed 6 digits)."""
+    r1, u1, v1, p1 = MG.SR_LEFT
+    r2, u2, v2, p2 = MG.SR_UP
+    d = np.array([u2 - u1, v2 - v1])
+    n = d / np.hypot(*d)
+    un1, un2 = u1 * n[0] + v1 * n[1], u2 * n[0] + v2 * n[1]
+    t = np.array([-n[1], n[0]])
+    assert abs((u1 * t[0] + v1 * t[1]) - (u2 * t[0] + v2 * t[1])) < 1e-12
+    assert abs(r1 * un1 - r2 * un2) < 2e-5 * abs(r1 * un1)
+    assert abs((p1 + r1 * un1 ** 2) - (p2 + r2 * un2 ** 2)) < 2e-5 * (p1 + r1 * un1 ** 2)
+    h1 = GAM / (GAM - 1) * p1 / r1 + 0.5 * un1 ** 2
+    h2 = GAM / (GAM - 1) * p2 / r2 + 0.5 * un2 ** 2
+    assert abs(h1 - h2) < 2e-5 * h1
+    # the incident shock makes 29 degrees with the stream
+    assert abs(math.degrees(math.atan2(abs(n[0]), abs(n[1]))) - 29.0) < 0.05
