@@ -57,8 +57,11 @@ enum { CGKS_TRI = 0, CGKS_QUAD = 1, CGKS_TET = 2, CGKS_PRISM = 3, CGKS_PYRAMID =
 
 /* boundary conditions, Section 4 of the paper: reflective (slip) wall,
  * non-slip adiabatic wall (optionally moving tangentially), far field with
- * 1-D Riemann invariants against a free stream */
-enum { CGKS_BC_SLIP = 0, CGKS_BC_NOSLIP = 1, CGKS_BC_FARFIELD = 2 };
+ * 1-D Riemann invariants against a free stream, Dirichlet (the given state,
+ * uniform outside) and supersonic outflow (the inside continued: state and
+ * gradient copied), the last two for the shock reflection problem (2-D
+ * only).  Only walls enter the reconstruction stencils. */
+enum { CGKS_BC_SLIP = 0, CGKS_BC_NOSLIP = 1, CGKS_BC_FARFIELD = 2, CGKS_BC_DIRICHLET = 3, CGKS_BC_OUTFLOW = 4 };
 
 /* explicit time schemes: S1O2 (Section 2.4) and the two-stage fourth-order
  * S2O4 named in Section 1 (Li & Du 2016) */
@@ -74,13 +77,24 @@ enum { CGKS_FP64 = 0, CGKS_MIXED = 1 };
  * two sides. */
 enum { CGKS_FLUX_KFVS = 0, CGKS_FLUX_LF = 1 };
 
+/* Gas-kinetic flux of the high-order level (Section 2.3; Section 4 uses the
+ * smooth one for subsonic flow, the full one with WENO weights for
+ * transonic and supersonic flow).
+ *   SMOOTH: Eq. (2nd-smooth-flux).
+ *   FULL:   Eq. (2nd-flux), with numerical collision time
+ *           tau_n = mu/p + tau_c1 dt + tau_c2 dt |p_l - p_r| / (p_l + p_r)
+ *           in the exponentials; its time dependence enters the time
+ *           schemes through the integrals over [0, dt] and [0, dt/2].
+ * FULL and compact WENO weights are 2-D only. */
+enum { CGKS_FLUX_SMOOTH = 0, CGKS_FLUX_FULL = 1 };
+
 #define CGKS_MAX_BC 16
 
 typedef struct {
   int32_t kind;          /* CGKS_BC_* */
   int32_t pad_;
   double u_wall[3];      /* no-slip wall velocity (tangential; 2-D uses x, y) */
-  double rho, u[3], p;   /* far-field free stream (primitive variables; 2-D uses x, y) */
+  double rho, u[3], p;   /* far-field free stream or Dirichlet state (primitive variables; 2-D uses x, y) */
 } cgks_bc;
 
 typedef void *(*cgks_alloc_fn)(size_t bytes, void *ctx);
@@ -106,6 +120,12 @@ typedef struct {
                             predecessor runs and waits on the device for it (programmatic
                             dependent launch, sm_90+); 0: plain stream order.  Same results. */
   int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF */
+  int32_t flux_hi;       /* CGKS_FLUX_SMOOTH (default) or CGKS_FLUX_FULL */
+  int32_t pad_;
+  double tau_c1, tau_c2; /* numerical collision time constants of the full flux (0.01, 1) */
+  double weno_eps;       /* > 0: compact WENO nonlinear weights with this epsilon (Section 4 uses
+                            1e-2 and 1e-6); 0 (default): linear weights */
+  double weno_g0;        /* linear weight of the quadratic candidate of the WENO step (0.95) */
   cgks_bc bc[CGKS_MAX_BC];
   void *stream;          /* cudaStream_t for all device work (NULL = default) */
   cgks_alloc_fn alloc;   /* optional device allocator (NULL = cudaMalloc) */

@@ -88,6 +88,8 @@ typedef struct {
   double weno_eps;            /* > 0: nonlinear compact WENO weights with this epsilon;
                                  <= 0: linear weights */
   double weno_g0;             /* linear weight of the quadratic candidate */
+  int weno_char;              /* 1: WENO weights on characteristic variables, per face side */
+  int pad2_;
   or_bc bc[MAXBC];
 } or_params;
 
@@ -949,6 +951,7 @@ typedef struct {
   double *Wx;                 /* [nc][2][NV] cell-averaged gradients */
   double *coef;               /* [nc][NM][NV] reconstruction coefficients */
   double *mom_self;           /* [nc][NM] own monomial means */
+  unsigned char *quad;        /* [nc] 1: least-squares quadratic, 0: linear fallback */
   /* per-face quadrature sums of one high-order evaluation */
   double *F0, *F1, *Wc, *Wt;  /* [nf][NV] */
   double *Rp0;                /* [nc][NV] transferred residual */
@@ -964,6 +967,7 @@ or_solver *or_solver_create(const or_mesh *m, const or_params *P) {
   s->W = (double *)calloc(nc * NV, sizeof(double));
   s->Wx = (double *)calloc(nc * 2 * NV, sizeof(double));
   s->coef = (double *)calloc(nc * NM * NV, sizeof(double));
+  s->quad = (unsigned char *)calloc(nc, 1);
   s->mom_self = (double *)calloc(nc * NM, sizeof(double));
   s->F0 = (double *)calloc(nf * NV, sizeof(double));
   s->F1 = (double *)calloc(nf * NV, sizeof(double));
@@ -977,7 +981,7 @@ or_solver *or_solver_create(const or_mesh *m, const or_params *P) {
 
 void or_solver_destroy(or_solver *s) {
   if (!s) return;
-  free(s->W); free(s->Wx); free(s->coef); free(s->mom_self);
+  free(s->W); free(s->Wx); free(s->coef); free(s->mom_self); free(s->quad);
   free(s->F0); free(s->F1); free(s->Wc); free(s->Wt); free(s->Rp0); free(s);
 }
 
@@ -1070,36 +1074,115 @@ static double weno_beta(const or_mesh *m, long i, const double *c, int stride) {
  * (1 - g0)/m for each of the m linear ones; nonlinear weights
  * w_k ~ gamma_k / (beta_k + eps)^2, normalised; the result
  *   P = (w_0 / gamma_0) (P2 - sum_k gamma_k P1_k) + sum_k w_k P1_k
- * equals P2 when w = gamma and keeps the cell mean.  Per variable.
- * X is updated in place. */
-static void weno_combine(const or_solver *s, const double *Wx, long i, double *X) {
-  const or_mesh *m = s->m;
-  const or_cell *C = &m->cell[i];
+ * equals P2 when w = gamma and keeps the cell mean.  Per component.
+ * weno_mix does it for the NV components of X (in place, [q][v] layout)
+ * with the m scaled candidate gradients G[k][d][v]. */
+static void weno_mix(const or_solver *s, long i, double *X, int m, double G[5][2][NV]) {
   double g0 = s->P.weno_g0, eps = s->P.weno_eps;
-  long cand[5];
-  int nk = 0;
-  cand[nk++] = i;
-  for (int k = 0; k < C->nb; ++k) cand[nk++] = C->nbr[k];
-  double gk = (1.0 - g0) / nk;
+  double gk = (1.0 - g0) / m;
   for (int v = 0; v < NV; ++v) {
-    double G[5][2];
     double wt[6], wsum = 0.0;
-    wt[0] = g0 / ((weno_beta(m, i, &X[v], NV) + eps) * (weno_beta(m, i, &X[v], NV) + eps));
-    for (int k = 0; k < nk; ++k) {
-      double cl[NM] = { C->h * Wx[(cand[k] * 2 + 0) * NV + v], C->h * Wx[(cand[k] * 2 + 1) * NV + v], 0, 0, 0 };
-      G[k][0] = cl[0]; G[k][1] = cl[1];
-      double b = weno_beta(m, i, cl, 1);
+    double b0 = weno_beta(s->m, i, &X[v], NV);
+    wt[0] = g0 / ((b0 + eps) * (b0 + eps));
+    for (int k = 0; k < m; ++k) {
+      double cl[NM] = { G[k][0][v], G[k][1][v], 0.0, 0.0, 0.0 };
+      double b = weno_beta(s->m, i, cl, 1);
       wt[k + 1] = gk / ((b + eps) * (b + eps));
     }
-    for (int k = 0; k <= nk; ++k) wsum += wt[k];
-    for (int k = 0; k <= nk; ++k) wt[k] /= wsum;
+    for (int k = 0; k <= m; ++k) wsum += wt[k];
+    for (int k = 0; k <= m; ++k) wt[k] /= wsum;
     for (int q = 0; q < NM; ++q) {
       double lin = 0.0, sel = 0.0;
       if (q < 2)
-        for (int k = 0; k < nk; ++k) { lin += gk * G[k][q]; sel += wt[k + 1] * G[k][q]; }
+        for (int k = 0; k < m; ++k) { lin += gk * G[k][q][v]; sel += wt[k + 1] * G[k][q][v]; }
       X[q * NV + v] = wt[0] / g0 * (X[q * NV + v] - lin) + sel;
     }
   }
+}
+
+/* the scaled linear candidates h_i * (mean gradient) of cell i and its
+ * face neighbours; returns their number */
+static int weno_candidates(const or_solver *s, const double *Wx, long i, double G[5][2][NV]) {
+  const or_cell *C = &s->m->cell[i];
+  long cand[5];
+  int m = 0;
+  cand[m++] = i;
+  for (int k = 0; k < C->nb; ++k) cand[m++] = C->nbr[k];
+  for (int k = 0; k < m; ++k)
+    for (int d = 0; d < 2; ++d)
+      for (int v = 0; v < NV; ++v) G[k][d][v] = C->h * Wx[(cand[k] * 2 + d) * NV + v];
+  return m;
+}
+
+static void weno_combine(const or_solver *s, const double *Wx, long i, double *X) {
+  double G[5][2][NV];
+  int m = weno_candidates(s, Wx, i, G);
+  weno_mix(s, i, X, m, G);
+}
+
+/* Right eigenvectors (columns) of the Euler flux Jacobian along the unit
+ * normal n at the conservative state W: the waves u_n - c, u_n (entropy),
+ * u_n (shear) and u_n + c. */
+static void euler_right_eigvecs(double gamma, const double W[NV], const double n[2], double R[NV][NV]) {
+  double rho, u[2], p;
+  prim(gamma, W, &rho, u, &p);
+  double c = sqrt(gamma * p / rho), H = (W[3] + p) / rho;
+  double un = u[0] * n[0] + u[1] * n[1], ut = -u[0] * n[1] + u[1] * n[0];
+  double col[NV][NV] = { { 1.0, u[0] - c * n[0], u[1] - c * n[1], H - c * un },
+                         { 1.0, u[0], u[1], 0.5 * (u[0] * u[0] + u[1] * u[1]) },
+                         { 0.0, -n[1], n[0], ut },
+                         { 1.0, u[0] + c * n[0], u[1] + c * n[1], H + c * un } };
+  for (int r = 0; r < NV; ++r)
+    for (int k = 0; k < NV; ++k) R[r][k] = col[k][r];
+}
+
+/* exposed for the eigenvector pin */
+void or_euler_right_eigvecs(double gamma, const double W[NV], const double n[2], double *R) {
+  double Rm[NV][NV];
+  euler_right_eigvecs(gamma, W, n, Rm);
+  for (int r = 0; r < NV; ++r) for (int k = 0; k < NV; ++k) R[r * NV + k] = Rm[r][k];
+}
+
+/* Compact WENO on characteristic variables (Section 4, shock reflection):
+ * the candidates of cell i are projected on the left eigenvectors L = R^-1
+ * of the Euler flux Jacobian along the face normal, taken at the mean of
+ * the cell averages on the two sides of the face (the cell's own average
+ * on a boundary face); the nonlinear weights are formed per
+ * characteristic field, and the combination is projected back with R.
+ * X: the linear-weight quadratic of cell i; out: the face-side polynomial. */
+static void weno_char_side(const or_solver *s, const double *Wx, long i, const double Wref[NV], const double n[2],
+                           const double *X, double *out) {
+  double R[NV][NV], L[NV][NV];
+  euler_right_eigvecs(s->P.gamma, Wref, n, R);
+  for (int k = 0; k < NV; ++k) {
+    double A[NV * NV], e[NV] = { 0 };
+    for (int r = 0; r < NV; ++r) for (int c = 0; c < NV; ++c) A[r * NV + c] = R[r][c];
+    e[k] = 1.0;
+    gauss_solve(NV, A, e);                 /* column k of R^-1 */
+    for (int r = 0; r < NV; ++r) L[r][k] = e[r];
+  }
+  double G[5][2][NV], GQ[5][2][NV], XQ[NM * NV];
+  int m = weno_candidates(s, Wx, i, G);
+  for (int q = 0; q < NM; ++q)
+    for (int a = 0; a < NV; ++a) {
+      double acc = 0.0;
+      for (int v = 0; v < NV; ++v) acc += L[a][v] * X[q * NV + v];
+      XQ[q * NV + a] = acc;
+    }
+  for (int k = 0; k < m; ++k)
+    for (int d = 0; d < 2; ++d)
+      for (int a = 0; a < NV; ++a) {
+        double acc = 0.0;
+        for (int v = 0; v < NV; ++v) acc += L[a][v] * G[k][d][v];
+        GQ[k][d][a] = acc;
+      }
+  weno_mix(s, i, XQ, m, GQ);
+  for (int q = 0; q < NM; ++q)
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+      for (int a = 0; a < NV; ++a) acc += R[v][a] * XQ[q * NV + a];
+      out[q * NV + v] = acc;
+    }
 }
 
 static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, long i) {
@@ -1109,6 +1192,7 @@ static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, lo
   const double *mi = &s->mom_self[i * NM];
   int nwall = 0;
   for (int k = 0; k < C->nf; ++k) nwall += is_wall(s, &m->face[C->face[k]]);
+  s->quad[i] = 0;
   if (C->nb + nwall < 2) {
     /* too few neighbours for a quadratic: linear from the own gradient */
     for (int q = 0; q < NM * NV; ++q) c[q] = 0.0;
@@ -1180,19 +1264,29 @@ static void reconstruct_cell(or_solver *s, const double *W, const double *Wx, lo
     }
     return;
   }
-  if (s->P.weno_eps > 0.0) weno_combine(s, Wx, i, X);
+  if (s->P.weno_eps > 0.0 && !s->P.weno_char) weno_combine(s, Wx, i, X);
   for (int q = 0; q < NM * NV; ++q) c[q] = X[q];
+  s->quad[i] = 1;
 }
 
 static void reconstruct_all(or_solver *s, const double *W, const double *Wx) {
   for (long i = 0; i < s->m->nc; ++i) reconstruct_cell(s, W, Wx, i);
 }
 
+/* value and gradient at point x of the polynomial of cell i with
+ * coefficients c ([q][v]) */
+static void poly_eval(const or_solver *s, const double *W, long i, const double *c, const double x[2],
+                      double val[NV], double grad[2 * NV]);
+
 /* value and gradient of P_i at point x */
 static void recon_eval(const or_solver *s, const double *W, long i, const double x[2],
                        double val[NV], double grad[2 * NV]) {
+  poly_eval(s, W, i, &s->coef[i * NM * NV], x, val, grad);
+}
+
+static void poly_eval(const or_solver *s, const double *W, long i, const double *c, const double x[2],
+                      double val[NV], double grad[2 * NV]) {
   const or_cell *C = &s->m->cell[i];
-  const double *c = &s->coef[i * NM * NV];
   const double *mi = &s->mom_self[i * NM];
   double xi = (x[0] - C->xc[0]) / C->h, eta = (x[1] - C->xc[1]) / C->h;
   double phi[NM] = { xi, eta, xi * xi, xi * eta, eta * eta };
@@ -1225,10 +1319,21 @@ static void hi_eval(or_solver *s, const double *W, const double *Wx, double dt) 
   for (long f = 0; f < m->nf; ++f) {
     const or_face *F = &m->face[f];
     double sF0[NV] = { 0 }, sF1[NV] = { 0 }, sWc[NV] = { 0 }, sWt[NV] = { 0 };
+    /* the polynomials of the two sides: the cell's own, or with
+     * characteristic WENO one limited for this face */
+    const double *p0 = &s->coef[F->c0 * NM * NV], *p1 = F->c1 >= 0 ? &s->coef[F->c1 * NM * NV] : NULL;
+    double q0[NM * NV], q1[NM * NV];
+    if (s->P.weno_eps > 0.0 && s->P.weno_char) {
+      double Wref[NV];
+      for (int v = 0; v < NV; ++v)
+        Wref[v] = F->c1 >= 0 ? 0.5 * (W[F->c0 * NV + v] + W[F->c1 * NV + v]) : W[F->c0 * NV + v];
+      if (s->quad[F->c0]) { weno_char_side(s, Wx, F->c0, Wref, F->n, p0, q0); p0 = q0; }
+      if (F->c1 >= 0 && s->quad[F->c1]) { weno_char_side(s, Wx, F->c1, Wref, F->n, p1, q1); p1 = q1; }
+    }
     for (int k = 0; k < 2; ++k) {
       double Wl[NV], gl[2 * NV], Wr[NV], gr[2 * NV];
-      recon_eval(s, W, F->c0, F->xg[k], Wl, gl);
-      if (F->c1 >= 0) recon_eval(s, W, F->c1, F->xg[k], Wr, gr);
+      poly_eval(s, W, F->c0, p0, F->xg[k], Wl, gl);
+      if (F->c1 >= 0) poly_eval(s, W, F->c1, p1, F->xg[k], Wr, gr);
       else if (is_wall(s, F) || s->P.bc[F->tag].kind == OR_BC_OUTFLOW)
         or_ghost(&s->P, F->tag, Wl, gl, F->n, Wr, gr);
       else {

@@ -46,7 +46,8 @@ class OrParams(C.Structure):
                 ("time_scheme", C.c_int), ("restrict_mode", C.c_int), ("n_bc", C.c_int),
                 ("flux_lo", C.c_int), ("sweep_order", C.c_int), ("n_parts", C.c_int),
                 ("flux_hi", C.c_int), ("pad_", C.c_int), ("tau_c1", C.c_double), ("tau_c2", C.c_double),
-                ("weno_eps", C.c_double), ("weno_g0", C.c_double), ("bc", OrBC * 16)]
+                ("weno_eps", C.c_double), ("weno_g0", C.c_double), ("weno_char", C.c_int), ("pad2_", C.c_int),
+                ("bc", OrBC * 16)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -100,6 +101,7 @@ def lib():
             L.or_gks_full_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                                  _dp, _dp, _dp, _dp]
             L.or_kfvs.argtypes = [P, _dp, _dp, _dp, _dp]
+            L.or_euler_right_eigvecs.argtypes = [C.c_double, _dp, _dp, _dp]
             L.or_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.or_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
             L.or_micro_slope.argtypes = [C.c_double, _dp, _dp, _dp]
@@ -116,6 +118,8 @@ def make_params(spec: dict) -> OrParams:
     tau_n = tau + tau_c1 dt + tau_c2 dt |p_l - p_r| / (p_l + p_r), defaults
     0.01 and 1), weno_eps (> 0: nonlinear compact WENO weights, default 0 =
     linear weights), weno_g0 (linear weight of the quadratic, default 0.95),
+    weno_vars ('conservative' default | 'characteristic': weights per
+    characteristic field of the face normal, per face side),
     bcs: list of dicts {kind: 'slip'|'noslip'|'farfield'|'dirichlet'|
     'outflow', uw=(u,v), rho, u=(u,v), p}."""
     P = OrParams()
@@ -136,6 +140,7 @@ def make_params(spec: dict) -> OrParams:
     P.tau_c2 = float(spec.get("tau_c2", 1.0))
     P.weno_eps = float(spec.get("weno_eps", 0.0))
     P.weno_g0 = float(spec.get("weno_g0", 0.95))
+    P.weno_char = {"conservative": 0, "characteristic": 1}[spec.get("weno_vars", "conservative")]
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):
@@ -331,6 +336,12 @@ def ghost(spec, tag, W, grad, n):
     Wg = np.zeros(NV); gg = np.zeros(2 * NV)
     lib().or_ghost(C.byref(P), int(tag), _f64(W), _f64(grad, (2 * NV,)), _f64(n), Wg, gg)
     return Wg, gg.reshape(2, NV)
+
+
+def euler_right_eigvecs(gamma, W, n):
+    R = np.zeros(NV * NV)
+    lib().or_euler_right_eigvecs(float(gamma), _f64(W), _f64(n), R)
+    return R.reshape(NV, NV)
 
 
 def micro_slope(gamma, W, dW):

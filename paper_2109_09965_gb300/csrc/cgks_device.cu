@@ -47,7 +47,8 @@ struct Bufs {
 struct Shared {
   double gamma = 1.4, cfl_hi = 0.4, cfl_lo = 1000.0;
   int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 0;
-  int autotune = 1, pdl = 1, flux_lo = CGKS_FLUX_KFVS;
+  int autotune = 1, pdl = 1, flux_lo = CGKS_FLUX_KFVS, flux_hi = CGKS_FLUX_SMOOTH;
+  double tau_c1 = 0.01, tau_c2 = 1.0, weno_eps = 0.0, weno_g0 = 0.95;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -66,7 +67,7 @@ struct DevArrays {
   double *vol, *ivol, *per, *ih, *m2, *op, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs;
   double *mu, *bcuw, *bcrho, *bcu, *bcp;
   int *cface, *cnbr, *fc0, *fc1, *csid, *fsid, *bckind;
-  unsigned char *ccol;
+  unsigned char *ccol, *wenok;
   float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
         *f_fjump = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr, *f_mu = nullptr,
         *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
@@ -186,18 +187,27 @@ void enqueue_res(Batch *b) {
 template <typename TF>
 void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
   Bufs<TF> &B = bufs<TF>(b);
+  // the nonlinear WENO weights and the full flux are separate instantiations,
+  // so the default (linear weights, smooth flux) kernels stay as lean as before
+  const bool weno = b->sh.weno_eps > 0.0, full = b->sh.flux_hi == CGKS_FLUX_FULL;
   tuned_launch(b->tune, TK_RECON, b->stream, [&] {
     with_shape(b->tune.shape(TK_RECON), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
-      launch(b, KI_RECON, k_recon<TF, S>, dim3(nblk(b->N, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-             fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
+      const dim3 g(nblk(b->N, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+      if (weno) launch(b, KI_RECON, k_recon<TF, S, true>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
+      else launch(b, KI_RECON, k_recon<TF, S, false>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
     });
   });
   tuned_launch(b->tune, TK_FACE, b->stream, [&] {
     with_shape(b->tune.shape(TK_FACE), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
-      launch(b, KI_FACE, k_face<TF, S>, dim3(nblk(b->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-             fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout);
+      const dim3 g(nblk(b->F, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+      if (full)
+        launch(b, KI_FACE, k_face<TF, S, true>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout,
+               (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits);
+      else
+        launch(b, KI_FACE, k_face<TF, S, false>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout,
+               (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits);
     });
   });
 }
@@ -441,6 +451,11 @@ void fill_shared_params(const Shared &sh, ParamsT<T> &P) {
   P.kc.c2K = static_cast<T>(2.0 / (K + 2.0));
   P.kc.c4K = static_cast<T>(4.0 / (K + 2.0));
   P.flux_lo = sh.flux_lo;
+  P.flux_hi = sh.flux_hi;
+  P.tau_c1 = static_cast<T>(sh.tau_c1);
+  P.tau_c2 = static_cast<T>(sh.tau_c2);
+  P.weno_eps = static_cast<T>(sh.weno_eps);
+  P.weno_g0 = static_cast<T>(sh.weno_g0);
 }
 
 // The device arena of a batch: one allocation carved into 256-byte aligned
@@ -471,6 +486,7 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   PI(&d.cface, kMaxFace * N); PI(&d.cnbr, kMaxFace * N); PI(&d.fc0, F); PI(&d.fc1, F); PI(&d.csid, N); PI(&d.fsid, F);
   PI(&d.bckind, T); PI(&b->list, std::max<int64_t>(L, 1)); PI(&b->perm, N); PI(&b->blk, 2 * S);
   PV(reinterpret_cast<void **>(&d.ccol), N);
+  PV(reinterpret_cast<void **>(&d.wenok), N);
   PV(reinterpret_cast<void **>(&b->ctl), sizeof(Ctl));
   PV(reinterpret_cast<void **>(&b->dt_bits), sizeof(unsigned long long) * S);
   PI(&b->status, S);
@@ -571,14 +587,14 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   dm.vol = d.vol; dm.ivol = d.ivol; dm.per = d.per; dm.ih = d.ih; dm.m2 = d.m2; dm.op = d.op;
   dm.fn = d.fn; dm.fS = d.fS; dm.fjump = d.fjump; dm.fxi = d.fxi; dm.snx = d.snx; dm.sny = d.sny; dm.shs = d.shs;
   dm.cface = d.cface; dm.cnbr = d.cnbr; dm.fc0 = d.fc0; dm.fc1 = d.fc1; dm.csid = d.csid; dm.fsid = d.fsid;
-  dm.ccol = d.ccol;
+  dm.ccol = d.ccol; dm.wenok = d.wenok;
   MeshT<float> &fm = b->fm;
   fm.nc = dm.nc; fm.nf = dm.nf;
   fm.vol = nullptr; fm.per = nullptr; fm.ivol = d.f_ivol; fm.ih = d.f_ih; fm.m2 = d.f_m2; fm.op = d.f_op;
   fm.fn = d.f_fn; fm.fS = d.f_fS; fm.fjump = d.f_fjump; fm.fxi = d.f_fxi; fm.snx = d.f_snx; fm.sny = d.f_sny;
   fm.shs = d.f_shs;
   fm.cface = d.cface; fm.cnbr = d.cnbr; fm.fc0 = d.fc0; fm.fc1 = d.fc1; fm.csid = d.csid; fm.fsid = d.fsid;
-  fm.ccol = d.ccol;
+  fm.ccol = d.ccol; fm.wenok = d.wenok;
   bool ok = cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
             cudaMemsetAsync(b->status, 0, sizeof(int) * S, st) == cudaSuccess &&
             cudaMemsetAsync(b->res, 0, sizeof(double) * S, st) == cudaSuccess &&
@@ -631,11 +647,13 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
   std::vector<double> fn(2 * nf), fS(nf), fjump(nf), fxi(8 * nf);
   std::vector<int> cface(kMaxFace * np, kNoFace), cnbr(kMaxFace * np, -1), csid(np, -1), perm(np, 0), fc0(nf),
       fc1(nf), fsid(nf, s);
-  std::vector<unsigned char> ccol(np, 255);
+  std::vector<unsigned char> ccol(np, 255), wenok(np, 0);
   std::vector<char> wall(kTagsPerSolve, 0);
-  for (int t = 0; t < p.n_bc; ++t) wall[t] = p.bc[t].kind != CGKS_BC_FARFIELD;
+  for (int t = 0; t < p.n_bc; ++t) wall[t] = is_wall_kind(p.bc[t].kind);
   std::vector<double> ops;
-  build_operator(hm, wall, ops);
+  std::vector<unsigned char> qok;
+  build_operator(hm, wall, ops, &qok);
+  for (int64_t i = 0; i < nc; ++i) wenok[i] = qok[i];
   for (int64_t i = 0; i < nc; ++i) {
     vol[i] = hm.vol[i]; ivol[i] = 1.0 / hm.vol[i]; per[i] = hm.per[i]; ih[i] = 1.0 / hm.h[i];
     for (int q = 0; q < 3; ++q) m2[q * np + i] = hm.m2[q * nc + i];
@@ -690,6 +708,7 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
   up(d.m2, m2, np, N, co); up(d.op, op, np, N, co); up(d.snx, snx, np, N, co); up(d.sny, sny, np, N, co);
   up(d.shs, shs, np, N, co); up(d.cface, cface, np, N, co); up(d.cnbr, cnbr, np, N, co);
   up(d.csid, csid, np, N, co); up(b->perm, perm, np, N, co); up(d.ccol, ccol, np, N, co);
+  up(d.wenok, wenok, np, N, co);
   up(d.fn, fn, nf, F, fo); up(d.fS, fS, nf, F, fo); up(d.fjump, fjump, nf, F, fo); up(d.fxi, fxi, nf, F, fo);
   up(d.fc0, fc0, nf, F, fo); up(d.fc1, fc1, nf, F, fo); up(d.fsid, fsid, nf, F, fo);
   up(d.mu, mu, 1, 1, s); up(d.bcuw, bc_uw, 2 * T, 0, 2 * T * s); up(d.bcrho, bc_rho, T, 0, T * s);
@@ -893,6 +912,8 @@ Shared shared_from(const cgks_params *p) {
   sh.autotune = p->autotune;
   sh.pdl = p->programmatic_launch;
   sh.flux_lo = p->flux_lo;
+  sh.flux_hi = p->flux_hi;
+  sh.tau_c1 = p->tau_c1; sh.tau_c2 = p->tau_c2; sh.weno_eps = p->weno_eps; sh.weno_g0 = p->weno_g0;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -901,14 +922,19 @@ int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_
   if (!(p->gamma > 1.0) || p->mu < 0.0 || !(p->cfl_hi > 0.0) || !(p->cfl_lo > 0.0) || p->n_implicit < 0 ||
       p->n_sweeps < 0 || (p->time_scheme != CGKS_S1O2 && p->time_scheme != CGKS_S2O4) || p->n_bc < 0 ||
       p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0) ||
-      (p->flux_lo != CGKS_FLUX_KFVS && p->flux_lo != CGKS_FLUX_LF))
+      (p->flux_lo != CGKS_FLUX_KFVS && p->flux_lo != CGKS_FLUX_LF) ||
+      (p->flux_hi != CGKS_FLUX_SMOOTH && p->flux_hi != CGKS_FLUX_FULL) || !(p->tau_c1 >= 0.0) ||
+      !(p->tau_c2 >= 0.0) || !(p->weno_eps >= 0.0) || (p->weno_eps > 0.0 && !(p->weno_g0 > 0.0 && p->weno_g0 < 1.0)))
     return CGKS_EINVAL;
   for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
   for (int b = 0; b < p->n_bc; ++b) {
     int k = p->bc[b].kind;
-    if (k != CGKS_BC_SLIP && k != CGKS_BC_NOSLIP && k != CGKS_BC_FARFIELD) return CGKS_EINVAL;
-    if (k == CGKS_BC_FARFIELD && !(p->bc[b].rho > 0.0 && p->bc[b].p > 0.0)) return CGKS_EINVAL;
+    if (k != CGKS_BC_SLIP && k != CGKS_BC_NOSLIP && k != CGKS_BC_FARFIELD && k != CGKS_BC_DIRICHLET &&
+        k != CGKS_BC_OUTFLOW)
+      return CGKS_EINVAL;
+    if ((k == CGKS_BC_FARFIELD || k == CGKS_BC_DIRICHLET) && !(p->bc[b].rho > 0.0 && p->bc[b].p > 0.0))
+      return CGKS_EINVAL;
   }
   return CGKS_OK;
 }
@@ -1030,6 +1056,7 @@ int wall_loads_t(cgks_solver *s, int32_t tag, int64_t max_faces, int64_t *n_face
   Batch *b = s->b;
   const HostMesh &hm = *b->mem[0].mesh;
   Bufs<TF> &B = bufs<TF>(b);
+  if (b->sh.flux_hi == CGKS_FLUX_FULL) enqueue_dt(b, -1.0);   // the full flux integrates over a step
   enqueue_hi_eval<TF>(b, B.W, B.Wx, B.FA);
   const int64_t F = b->F, nf = hm.n_faces, off = b->mem[0].face_off;
   std::vector<TF> F0(4 * static_cast<size_t>(F));
@@ -1075,6 +1102,11 @@ void cgks_default_params(cgks_params *p) {
   p->low_order_fused = 0;
   p->autotune = 1;
   p->programmatic_launch = 1;
+  p->flux_hi = CGKS_FLUX_SMOOTH;
+  p->tau_c1 = 0.01;
+  p->tau_c2 = 1.0;
+  p->weno_eps = 0.0;
+  p->weno_g0 = 0.95;
 }
 
 const char *cgks_strerror(int st) {
@@ -1169,6 +1201,13 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   *out = nullptr;
   int rc = validate_params_tags(p, m->dim == 3 ? m->h3.bface_tags_used : m->h.bface_tags_used);
   if (rc) return rc;
+  if (m->dim == 3) {
+    // the 3-D path runs the smooth flux with linear weights, and walls and far field
+    if (p->flux_hi != CGKS_FLUX_SMOOTH || p->weno_eps > 0.0) return CGKS_EINVAL;
+    for (int b = 0; b < p->n_bc; ++b)
+      if (p->bc[b].kind != CGKS_BC_SLIP && p->bc[b].kind != CGKS_BC_NOSLIP && p->bc[b].kind != CGKS_BC_FARFIELD)
+        return CGKS_EINVAL;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CGKS_ECUDA;
   cgks_solver *s = new (std::nothrow) cgks_solver();
@@ -1548,6 +1587,8 @@ int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p,
   q.time_scheme = v->sh.time_scheme; q.precision = v->sh.precision;
   int rc = validate_params(&q, m->h);
   if (rc) return rc;
+  // served solves run the smooth flux with linear weights (the batch shares its flux)
+  if (q.flux_hi != CGKS_FLUX_SMOOTH || q.weno_eps > 0.0) return CGKS_EINVAL;
   if (std::fabs(q.gamma - v->sh.gamma) > 1e-15) {
     if (v->reqs.empty()) v->sh.gamma = q.gamma;
     else return CGKS_EINVAL;   // every solve of a server shares gamma

@@ -295,9 +295,11 @@ int build_host_mesh(int64_t nn, const double *xy, int64_t nc, const uint8_t *cty
   return CGKS_OK;
 }
 
-void build_operator(const HostMesh &M, const std::vector<char> &tag_is_wall, std::vector<double> &op) {
+void build_operator(const HostMesh &M, const std::vector<char> &tag_is_wall, std::vector<double> &op,
+                    std::vector<unsigned char> *quad_ok) {
   const int64_t nc = M.n_cells, nf = M.n_faces;
   op.assign(static_cast<size_t>(kNCol * kNM) * nc, 0.0);
+  if (quad_ok) quad_ok->assign(nc, 0);
   for (int64_t i = 0; i < nc; ++i) {
     const double hi = M.h[i], xi0 = M.xc[i], yi0 = M.xc[nc + i];
     const double mi[3] = { M.m2[i], M.m2[nc + i], M.m2[2 * nc + i] };
@@ -367,6 +369,7 @@ void build_operator(const HostMesh &M, const std::vector<char> &tag_is_wall, std
       bool grad_col = (col % 3) != 0 || col >= 3 * kMaxFace;
       for (int q = 0; q < kNM; ++q) put(col, q, pinv[q * rows + r] * (grad_col ? hi : 1.0));
     }
+    if (quad_ok) (*quad_ok)[i] = 1;
   }
 }
 

@@ -47,7 +47,10 @@ struct HostMesh {
 // (column-major per cell: op[(col*kNM + q)*n + i]), with h_i folded into the
 // gradient columns.  tag_is_wall[t] selects the boundary tags whose mirror
 // ghost cells enter the fit.
-void build_operator(const HostMesh &m, const std::vector<char> &tag_is_wall, std::vector<double> &op);
+// quad_ok (optional): per cell 1 when the stencil gave a least-squares
+// quadratic, 0 when it fell back to the linear polynomial of the own gradient
+void build_operator(const HostMesh &m, const std::vector<char> &tag_is_wall, std::vector<double> &op,
+                    std::vector<unsigned char> *quad_ok = nullptr);
 
 // Returns CGKS_OK or CGKS_EMESH / CGKS_EINVAL.
 int build_host_mesh(int64_t n_nodes, const double *xy, int64_t n_cells, const uint8_t *ctype,

@@ -48,6 +48,9 @@ struct ParamsT {
   const T *bc_uw;                // [16 S][2] wall velocity
   const T *bc_rho, *bc_u, *bc_p; // [16 S], [16 S][2], [16 S] far-field free stream
   int flux_lo;                   // low-level flux: CGKS_FLUX_KFVS or CGKS_FLUX_LF
+  int flux_hi;                   // high-level flux: CGKS_FLUX_SMOOTH or CGKS_FLUX_FULL
+  T tau_c1, tau_c2;              // numerical collision time constants of the full flux
+  T weno_eps, weno_g0;           // compact WENO epsilon (0: linear weights), linear weight of P2
 };
 
 template <typename T>
@@ -61,6 +64,7 @@ struct MeshT {
   const int *fc0, *fc1;
   const int *csid, *fsid;                    // solve of each cell (-1: padding) and face
   const unsigned char *ccol;                 // colour of each cell (255: padding)
+  const unsigned char *wenok;                // 1: least-squares quadratic (WENO may limit it)
 };
 
 // per-batch control words on the device
@@ -174,9 +178,75 @@ __device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, T n
   D::ghost_farfield(P.gamma, P.bc_rho[tag], une, ute, P.bc_p[tag], wl, wg);
 }
 
+// prescribed state of a Dirichlet boundary in the face frame
+template <typename T>
+__device__ __forceinline__ void dirichlet_ghost(const ParamsT<T> &P, int tag, T nx, T ny, T wg[4]) {
+  const T r = P.bc_rho[tag], p = P.bc_p[tag];
+  const T un = P.bc_u[2 * tag] * nx + P.bc_u[2 * tag + 1] * ny;
+  const T ut = -P.bc_u[2 * tag] * ny + P.bc_u[2 * tag + 1] * nx;
+  wg[0] = r; wg[1] = r * un; wg[2] = r * ut;
+  wg[3] = p / (P.gamma - T(1)) + T(0.5) * r * (un * un + ut * ut);
+}
+
+__host__ __device__ __forceinline__ bool is_wall_kind(int k) { return k == CGKS_BC_SLIP || k == CGKS_BC_NOSLIP; }
+
+// Compact WENO with nonlinear weights (Section 4, transonic and supersonic
+// cases; the scheme is the cited one, read as follows).  Candidates: the
+// compact quadratic P2 (scaled coefficients c[q][v]) and the m linear
+// polynomials W_i + h g.(xi, eta), g the cell-mean gradient of the cell
+// itself and of each face neighbour (h g given in lin[k][0..1][v]).
+// Smoothness: the cell mean of (h D P)^2 over first and second derivative
+// multi-indices; with the centroid at the origin and the cell's second
+// moments M = (xi^2, xi eta, eta^2) means m2 this is, for
+// P_xi = c0 + 2 c2 xi + c3 eta, P_eta = c1 + c3 xi + 2 c4 eta,
+//   c0^2 + c1^2 + (4 c2^2 + c3^2) M_xx + (c3^2 + 4 c4^2) M_yy
+//   + (4 c2 c3 + 4 c3 c4) M_xy + 4 c2^2 + c3^2 + 4 c4^2.
+// Weights w_k ~ gamma_k / (beta_k + eps)^2 (gamma_0 = g0, the rest
+// (1 - g0) / m); result (w_0/gamma_0)(P2 - sum gamma_k P1_k) + sum w_k P1_k.
+template <typename T>
+__device__ __forceinline__ void weno_combine(const ParamsT<T> &P, T mxx, T mxy, T myy, int nk, const T lin[5][2][4],
+                                             T c[kNM][4]) {
+  const T g0 = P.weno_g0, eps = P.weno_eps;
+  const T gk = (T(1) - g0) / T(nk);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const T c0 = c[0][v], c1 = c[1][v], c2 = c[2][v], c3 = c[3][v], c4 = c[4][v];
+    const T b0 = c0 * c0 + c1 * c1 + (T(4) * c2 * c2 + c3 * c3) * mxx + (c3 * c3 + T(4) * c4 * c4) * myy +
+                 (T(4) * c2 * c3 + T(4) * c3 * c4) * mxy + T(4) * c2 * c2 + c3 * c3 + T(4) * c4 * c4;
+    T w0 = g0 / ((b0 + eps) * (b0 + eps));
+    T wk[5], ws = w0;
+    T lin0 = T(0), lin1 = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      if (k < nk) {
+        const T a0 = lin[k][0][v], a1 = lin[k][1][v];
+        const T b = a0 * a0 + a1 * a1;
+        wk[k] = gk / ((b + eps) * (b + eps));
+        ws += wk[k];
+        lin0 += gk * a0;
+        lin1 += gk * a1;
+      }
+    }
+    const T iws = T(1) / ws;
+    const T f0 = w0 * iws / g0;
+    T sel0 = T(0), sel1 = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k < nk) {
+        sel0 += wk[k] * iws * lin[k][0][v];
+        sel1 += wk[k] * iws * lin[k][1][v];
+      }
+    c[0][v] = f0 * (c0 - lin0) + sel0;
+    c[1][v] = f0 * (c1 - lin1) + sel1;
+    c[2][v] = f0 * c2;
+    c[3][v] = f0 * c3;
+    c[4][v] = f0 * c4;
+  }
+}
+
 // K1: compact least-squares quadratic of every cell.
 //   coef[(q*4 + v)*nc + i], q over (xi, eta, xi^2, xi eta, eta^2).
-template <typename T>
+template <typename T, bool WENO>
 __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
                                          const T *__restrict__ Wx, T *__restrict__ coef, const int i) {
   const int n = m.nc;
@@ -186,6 +256,13 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
   for (int q = 0; q < kNM; ++q) {
     T o0 = m.op[((kNCol - 2) * kNM + q) * n + i], o1 = m.op[((kNCol - 1) * kNM + q) * n + i];
     for (int v = 0; v < 4; ++v) c[q][v] = o0 * gxi[v] + o1 * gyi[v];
+  }
+  // linear WENO candidates: h times the cell-mean gradients of the cell and its face neighbours
+  T lin[WENO ? 5 : 1][2][4];
+  int nk = 1;
+  if constexpr (WENO) {
+    const T hi = T(1) / m.ih[i];
+    for (int v = 0; v < 4; ++v) { lin[0][0][v] = hi * gxi[v]; lin[0][1][v] = hi * gyi[v]; }
   }
   for (int s = 0; s < kMaxFace; ++s) {
     int fs = m.cface[s * n + i];
@@ -198,10 +275,15 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
         b1[v] = Wx[v * n + j];
         b2[v] = Wx[(4 + v) * n + j];
       }
+      if constexpr (WENO) {
+        const T hi = T(1) / m.ih[i];
+        for (int v = 0; v < 4; ++v) { lin[nk][0][v] = hi * b1[v]; lin[nk][1][v] = hi * b2[v]; }
+        ++nk;
+      }
     } else {
       int f = fs >= 0 ? fs : ~fs;
       int tag = -1 - m.fc1[f];
-      if (P.bc_kind[tag] == CGKS_BC_FARFIELD) continue;
+      if (!is_wall_kind(P.bc_kind[tag])) continue;
       T wg[4];
       wall_ghost_global(P, tag, m.fn[f], m.fn[m.nf + f], wi, gxi, gyi, wg, b1, b2);
       for (int v = 0; v < 4; ++v) b0[v] = wg[v] - wi[v];
@@ -213,16 +295,21 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
       for (int v = 0; v < 4; ++v) c[q][v] += o0 * b0[v] + o1 * b1[v] + o2 * b2[v];
     }
   }
+  // cells whose stencil fell back to the linear polynomial of their own
+  // gradient (too few neighbours, rank deficiency) carry no quadratic terms
+  // in the operator and keep it; the others may be limited
+  if constexpr (WENO)
+    if (m.wenok[i]) weno_combine(P, m.m2[i], m.m2[n + i], m.m2[2 * n + i], nk, lin, c);
   for (int q = 0; q < kNM; ++q)
     for (int v = 0; v < 4; ++v) coef[(q * 4 + v) * n + i] = c[q][v];
 }
-template <typename T, int SH>
+template <typename T, int SH, bool WENO = false>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_recon(MeshT<T> m, ParamsT<T> P,
                                                                         const T *__restrict__ W,
                                                                         const T *__restrict__ Wx,
                                                                         T *__restrict__ coef) {
   pdl_enter();
-  for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
+  for_items<SH>(m.nc, [&](int i) { recon_at<T, WENO>(m, P, W, Wx, coef, i); });
   pdl_exit();
 }
 
@@ -250,6 +337,10 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T n
   int kind = P.bc_kind[tag];
   if (kind == CGKS_BC_FARFIELD) {
     farfield_ghost(P, tag, nx, ny, wl, wgl);
+  } else if (kind == CGKS_BC_DIRICHLET) {
+    dirichlet_ghost(P, tag, nx, ny, wgl);
+  } else if (kind == CGKS_BC_OUTFLOW) {
+    for (int v = 0; v < 4; ++v) wgl[v] = wl[v];
   } else if (kind == CGKS_BC_SLIP) {
     D::ghost_slip(wl, z, z, wgl, a, b);
   } else {
@@ -263,29 +354,36 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T n
 // K2: gas-kinetic flux and interface state at the two Gauss points of every
 // face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
 //   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
-template <typename T>
+template <typename T, bool FULL>
 __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
-                                        const T *__restrict__ coef, T *__restrict__ out, const int f) {
+                                        const T *__restrict__ coef, T *__restrict__ out, const Ctl *ctl,
+                                        const unsigned long long *dt_bits, const int f) {
   const int sid = m.fsid[f];
   if (sid < 0) return;   // free face space of a batch
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];
   const T mu = P.mu[sid];
+  // the full flux integrates over the step: it needs the step's dt
+  T dt = T(0);
+  if constexpr (FULL) dt = static_cast<T>(dt_of(ctl, dt_bits, sid, static_cast<double>(P.cfl_hi)));
   T acc[4][4];
   for (int k = 0; k < 4; ++k) for (int v = 0; v < 4; ++v) acc[k][v] = T(0);
   T wff[4];
   bool farfield = false;
-  int tag = 0;
+  int tag = 0, kind = -1;
   if (c1 < 0) {
     tag = -1 - c1;
-    farfield = P.bc_kind[tag] == CGKS_BC_FARFIELD;
-    if (farfield) {
+    kind = P.bc_kind[tag];
+    farfield = kind == CGKS_BC_FARFIELD || kind == CGKS_BC_DIRICHLET;
+    if (kind == CGKS_BC_FARFIELD) {
       // Riemann-invariant state from the cell mean and the free stream
       T wm[4], wl[4];
       for (int v = 0; v < 4; ++v) wm[v] = W[v * m.nc + c0];
       D::rot_in(nx, ny, wm, wl);
       farfield_ghost(P, tag, nx, ny, wl, wff);
+    } else if (kind == CGKS_BC_DIRICHLET) {
+      dirichlet_ghost(P, tag, nx, ny, wff);
     }
   }
   for (int k = 0; k < 2; ++k) {
@@ -306,7 +404,9 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
       D::rot_in(nx, ny, t1, dtr);
     } else if (farfield) {
       for (int v = 0; v < 4; ++v) { wr[v] = wff[v]; dnr[v] = T(0); dtr[v] = T(0); }
-    } else if (P.bc_kind[tag] == CGKS_BC_SLIP) {
+    } else if (kind == CGKS_BC_OUTFLOW) {
+      for (int v = 0; v < 4; ++v) { wr[v] = wl[v]; dnr[v] = dnl[v]; dtr[v] = dtl[v]; }
+    } else if (kind == CGKS_BC_SLIP) {
       D::ghost_slip(wl, dnl, dtl, wr, dnr, dtr);
     } else {
       T wn = P.bc_uw[2 * tag] * nx + P.bc_uw[2 * tag + 1] * ny;
@@ -314,7 +414,10 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
       D::ghost_noslip(P.gamma, wn, wt, wl, dnl, dtl, wr, dnr, dtr);
     }
     T F0[4], F1[4], Wc[4], Wt[4];
-    D::gks_point_local(P.kc, mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
+    if constexpr (FULL)
+      D::gks_full_point_local(P.kc, mu, ajump, dt, P.tau_c1, P.tau_c2, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
+    else
+      D::gks_point_local(P.kc, mu, ajump, wl, wr, dnl, dtl, dnr, dtr, F0, F1, Wc, Wt);
     T g[4];
     D::rot_out(nx, ny, F0, g); for (int v = 0; v < 4; ++v) acc[0][v] += T(0.5) * g[v];
     D::rot_out(nx, ny, F1, g); for (int v = 0; v < 4; ++v) acc[1][v] += T(0.5) * g[v];
@@ -324,13 +427,14 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
 }
-template <typename T, int SH>
+template <typename T, int SH, bool FULL = false>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_face(MeshT<T> m, ParamsT<T> P,
                                                                        const T *__restrict__ W,
                                                                        const T *__restrict__ coef,
-                                                                       T *__restrict__ out) {
+                                                                       T *__restrict__ out, const Ctl *ctl,
+                                                                       const unsigned long long *dt_bits) {
   pdl_enter();
-  for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
+  for_items<SH>(m.nf, [&](int f) { face_at<T, FULL>(m, P, W, coef, out, ctl, dt_bits, f); });
   pdl_exit();
 }
 

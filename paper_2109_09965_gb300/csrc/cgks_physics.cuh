@@ -23,6 +23,9 @@ template <> __device__ __forceinline__ float d_erfc<float>(float x) { return erf
 template <typename T> __device__ __forceinline__ T d_exp(T x);
 template <> __device__ __forceinline__ double d_exp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float d_exp<float>(float x) { return expf(x); }
+template <typename T> __device__ __forceinline__ T d_expm1(T x);
+template <> __device__ __forceinline__ double d_expm1<double>(double x) { return expm1(x); }
+template <> __device__ __forceinline__ float d_expm1<float>(float x) { return expm1f(x); }
 template <typename T> __device__ __forceinline__ T d_sqrt(T x);
 template <> __device__ __forceinline__ double d_sqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float d_sqrt<float>(float x) { return sqrtf(x); }
@@ -215,6 +218,156 @@ __device__ __forceinline__ void gks_point_local(const KC<T> &kc, T mu_visc, T aj
     F0[v] = gc.rho * (feq[v] - tau * (gn2[v] + gtuv[v] + gAu[v]));
     F1[v] = gc.rho * gAu[v];
     Wt[v] = gc.rho * gA[v];
+  }
+}
+
+// ---------------- full flux, Eq. (2nd-flux) ----------------
+// Moment table of one Maxwellian whose u-moments are taken over a half
+// range (sgn = +1: u > 0, -1: u < 0); v and xi moments full.
+template <typename T>
+__device__ __forceinline__ void half_table(const Maxw<T> &g, T K, int sgn, Mom<T> &m) {
+  half_moments<T, 6>(g.U, g.i2l, d_sqrt(g.lam), d_rsqrt(g.lam) * T(kInvSqrtPi), sgn, m.mu);
+  m.mv[0] = T(1); m.mv[1] = g.V;
+#pragma unroll
+  for (int k = 2; k < 7; ++k) m.mv[k] = g.V * m.mv[k - 1] + T(k - 1) * g.i2l * m.mv[k - 2];
+  m.x2 = K * g.i2l;
+  m.x4 = K * (K + T(2)) * g.i2l * g.i2l;
+}
+
+// Spatial micro-slopes of a Maxwellian from its normal / tangential
+// derivatives (dn, dt), and the temporal one from <A + a_n u + a_t v> = 0.
+template <typename T>
+__device__ __forceinline__ void maxw_slopes(const Maxw<T> &g, const Mom<T> &mf, const KC<T> &kc, const T dn[NV],
+                                            const T dt[NV], T an[NV], T at[NV], T A[NV]) {
+  SlopeSolver<T> SS = slope_solver(g, kc);
+  T b[NV], g1[NV], g2[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) b[v] = dn[v] * g.ir;
+  micro_slope(SS, b, an);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) b[v] = dt[v] * g.ir;
+  micro_slope(SS, b, at);
+  gpsi(mf, 1, 0, an, g1);
+  gpsi(mf, 0, 1, at, g2);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) b[v] = -(g1[v] + g2[v]);
+  micro_slope(SS, b, A);
+}
+
+// rho-weighted moments of one piece of the distribution: flux moments
+// Q = (<u psi>, <u (a_n u + a_t v) psi>, <u A psi>) and state moments
+// P = (<psi>, <(a_n u + a_t v) psi>, <A psi>).
+template <typename T>
+__device__ __forceinline__ void piece(T rho, const Mom<T> &m, const T an[NV], const T at[NV], const T A[NV],
+                                      T Q[3][NV], T P[3][NV]) {
+  const T one[NV] = { T(1), T(0), T(0), T(0) };
+  T a[NV], b[NV];
+  gpsi(m, 1, 0, one, a);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[0][v] = rho * a[v];
+  gpsi(m, 2, 0, an, a);
+  gpsi(m, 1, 1, at, b);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[1][v] = rho * (a[v] + b[v]);
+  gpsi(m, 1, 0, A, a);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[2][v] = rho * a[v];
+  gpsi(m, 0, 0, one, a);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[0][v] = rho * a[v];
+  gpsi(m, 1, 0, an, a);
+  gpsi(m, 0, 1, at, b);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[1][v] = rho * (a[v] + b[v]);
+  gpsi(m, 0, 0, A, a);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[2][v] = rho * a[v];
+}
+
+// Eq. (2nd-flux) with time coefficients (c1, c2, c3, e, te) applied to the
+// equilibrium (X0), left (XL) and right (XR) pieces.
+template <typename T>
+__device__ __forceinline__ void full_sum(T c1, T c2, T c3, T e, T te, T tau, const T X0[3][NV], const T XL[3][NV],
+                                         const T XR[3][NV], T out[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    out[v] = c1 * X0[0][v] + c2 * X0[1][v] + c3 * X0[2][v] +
+             e * ((XL[0][v] + XR[0][v]) - tau * (XL[1][v] + XR[1][v]) - tau * (XL[2][v] + XR[2][v])) -
+             te * (XL[1][v] + XR[1][v]);
+}
+
+// Full gas-kinetic flux at one Gauss point, Eq. (2nd-flux):
+//   f = (1 - e) g^c + [(t + tau) e - tau] a^c.u g^c + (t - tau + tau e) A^c g^c
+//     + e g^l [1 - (tau + t) a^l.u - tau A^l] H(u) + e g^r [...] (1 - H(u)),
+// e = exp(-t / tau_n), tau = mu / p^c,
+// tau_n = tau + c1 dt + c2 dt |p_l - p_r| / (p_l + p_r).
+// Brought to the linear-in-time form of the time schemes through the time
+// integrals over [0, dt] and [0, dt/2]: F0 dt + F1 dt^2/2 = Fhat(dt),
+// F0 dt/2 + F1 dt^2/8 = Fhat(dt/2); the interface state W_p(t) = <psi f(t)>
+// by the line Wc + t Wt through its values at dt/2 and dt.  Same frame and
+// arguments as gks_point_local, plus dt and the two tau_n constants.
+template <typename T>
+__device__ void gks_full_point_local(const KC<T> &kc, T mu_visc, T ajump, T dt, T tc1, T tc2, const T Wl[NV],
+                                     const T Wr[NV], const T dnl[NV], const T dtl[NV], const T dnr[NV],
+                                     const T dtr[NV], T F0[NV], T F1[NV], T Wc[NV], T Wt[NV]) {
+  const T K = kc.K, c2K = kc.c2K;
+  Maxw<T> gl = maxw(Wl, c2K), gr = maxw(Wr, c2K);
+  T Q0[3][NV], P0[3][NV], QL[3][NV], PL[3][NV], QR[3][NV], PR[3][NV];
+  T anl[NV], atl[NV], Al[NV], anr[NV], atr[NV], Ar[NV];
+  {
+    Mom<T> mf;
+    full_moments(gl, K, mf);
+    maxw_slopes(gl, mf, kc, dnl, dtl, anl, atl, Al);
+    full_moments(gr, K, mf);
+    maxw_slopes(gr, mf, kc, dnr, dtr, anr, atr, Ar);
+  }
+  T W0[NV];
+  {
+    Mom<T> mh;
+    half_table(gl, K, +1, mh);
+    piece(gl.rho, mh, anl, atl, Al, QL, PL);
+    half_table(gr, K, -1, mh);
+    piece(gr.rho, mh, anr, atr, Ar, QR, PR);
+  }
+  // W^c: the collision of the particles of g^l moving right and g^r moving left
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W0[v] = PL[0][v] + PR[0][v];
+  Maxw<T> gc = maxw(W0, c2K);
+  T an[NV], at[NV], A[NV];
+  {
+    Mom<T> m;
+    full_moments(gc, K, m);
+    T dn[NV], dtg[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dn[v] = T(0.5) * (dnl[v] + dnr[v]) + ajump * (Wr[v] - Wl[v]);
+      dtg[v] = T(0.5) * (dtl[v] + dtr[v]);
+    }
+    maxw_slopes(gc, m, kc, dn, dtg, an, at, A);
+    piece(gc.rho, m, an, at, A, Q0, P0);
+  }
+  const T tau = mu_visc * T(2) * gc.lam * gc.ir;          // mu / p^c
+  const T pl = gl.rho * gl.i2l, pr = gr.rho * gr.i2l;
+  const T taun = tau + tc1 * dt + tc2 * dt * fabs(pl - pr) / (pl + pr);
+  T Fd[NV], Fh[NV], Wd[NV], Wh[NV];
+#pragma unroll 1
+  for (int k = 0; k < 2; ++k) {
+    const T t = k == 0 ? dt : T(0.5) * dt;
+    // coefficient functions at t and their integrals over [0, t]
+    const T e = taun > T(0) ? d_exp(-t / taun) : T(0);
+    const T om = taun > T(0) ? -d_expm1(-t / taun) : T(1);
+    const T ie = taun * om, ite = taun * taun * om - taun * t * e;
+    full_sum(t - ie, ite + tau * ie - tau * t, T(0.5) * t * t - tau * t + tau * ie, ie, ite, tau, Q0, QL, QR,
+             k == 0 ? Fd : Fh);
+    full_sum(T(1) - e, (t + tau) * e - tau, t - tau + tau * e, e, t * e, tau, P0, PL, PR, k == 0 ? Wd : Wh);
+  }
+  const T idt = T(1) / dt;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    F0[v] = (T(4) * Fh[v] - Fd[v]) * idt;
+    F1[v] = T(4) * (Fd[v] - T(2) * Fh[v]) * idt * idt;
+    Wc[v] = T(2) * Wh[v] - Wd[v];
+    Wt[v] = T(2) * (Wd[v] - Wh[v]) * idt;
   }
 }
 

@@ -170,11 +170,13 @@ SR_LEFT = (1.0, 2.9, 0.0, 1.0 / 1.4)
 SR_UP = (1.69997, 2.61934, -0.50632, 1.52819)
 
 
-def shock_reflection_case(nx: int = 120, ny: int = 30, weno_eps: float = 1e-2, gamma: float = 1.4):
+def shock_reflection_case(nx: int = 120, ny: int = 30, weno_eps: float = 1e-2, gamma: float = 1.4,
+                          weno_vars: str = "characteristic"):
     """Mesh, problem settings (the dict both the library and the oracle
     read) and initial state (the left state everywhere) of the shock
     reflection problem: inviscid, full flux of Eq. (2nd-flux), compact
-    WENO with the given epsilon."""
+    WENO with the given epsilon on characteristic variables (as the paper
+    runs it) or on the conservative ones."""
     mesh = shock_reflection(nx, ny)
 
     def bc(kind, st=None):
@@ -183,7 +185,7 @@ def shock_reflection_case(nx: int = 120, ny: int = 30, weno_eps: float = 1e-2, g
             d.update(rho=st[0], u=(st[1], st[2]), p=st[3])
         return d
 
-    spec = dict(gamma=gamma, mu=0.0, flux_hi="full", weno_eps=weno_eps, cfl_hi=0.4,
+    spec = dict(gamma=gamma, mu=0.0, flux_hi="full", weno_eps=weno_eps, weno_vars=weno_vars, cfl_hi=0.4,
                 bcs=[bc("slip"), bc("outflow"), bc("dirichlet", SR_UP), bc("dirichlet", SR_LEFT)])
     rho, u, v, p = SR_LEFT
     w = np.array([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])

@@ -166,3 +166,28 @@ def test_empty_mesh_is_rejected(cg):
             cg.Mesh(e)
         assert err.value.status == -1
 
+
+
+def test_full_flux_weno_and_new_boundaries_validated_before_the_device(cg):
+    """Parameter checks run before any device call: bad values and options
+    the 3-D path does not have are invalid arguments (-1); the valid
+    control reaches the device step (-4 here, without a GPU)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    mesh, spec, _ = MG.shock_reflection_case(6, 2, weno_eps=1e-2)
+    gm = cg.Mesh(mesh)
+
+    def status(m, sp):
+        with pytest.raises(cg.CgksError) as e:
+            cg.Solver(m, sp, use_torch=False)
+        return e.value.status
+    assert status(gm, spec) == -4
+    for bad in (dict(weno_eps=-1.0), dict(tau_c1=-0.1), dict(tau_c2=float("nan")), dict(weno_g0=1.0)):
+        assert status(gm, dict(spec, **bad)) == -1, bad
+    g3 = cg.Mesh(MG.box3(2, 2, 2, cells="hex"))
+    ok3 = dict(gamma=1.4, bcs=[dict(kind="slip")] * 6)
+    assert status(g3, ok3) == -4
+    for extra in (dict(flux_hi="full"), dict(weno_eps=1e-2), dict(bcs=[dict(kind="outflow")] * 6),
+                  dict(bcs=[dict(kind="dirichlet", rho=1.0, p=1.0)] * 6)):
+        assert status(g3, dict(ok3, **extra)) == -1, extra

@@ -162,3 +162,62 @@ def test_shock_reflection_states_satisfy_the_jump_conditions():
     assert abs(h1 - h2) < 2e-5 * h1
     # the incident shock makes 29 degrees with the stream
     assert abs(math.degrees(math.atan2(abs(n[0]), abs(n[1]))) - 29.0) < 0.05
+
+
+def test_euler_eigenvectors(oracle_lib):
+    """A_n r_k = lambda_k r_k for the oracle's right eigenvectors, with A_n
+    the complex-step Jacobian of the Euler normal flux and
+    lambda = (u_n - c, u_n, u_n, u_n + c); R is invertible."""
+    O = oracle_lib
+    rng = np.random.default_rng(35)
+    from tests.test_oracle_kinetics import complex_jacobian, rand_state
+    for _ in range(4):
+        W = rand_state(rng, 2.0)
+        th = rng.uniform(0, 2 * np.pi)
+        n = np.array([math.cos(th), math.sin(th)])
+        R = O.euler_right_eigvecs(GAM, W, n)
+        A = complex_jacobian(W, n)
+        rho, u, v = W[0], W[1] / W[0], W[2] / W[0]
+        p = (GAM - 1) * (W[3] - 0.5 * rho * (u * u + v * v))
+        c, un = math.sqrt(GAM * p / rho), u * n[0] + v * n[1]
+        lam = np.array([un - c, un, un, un + c])
+        np.testing.assert_allclose(A @ R, R * lam[None, :], rtol=1e-12, atol=1e-12)
+        assert abs(np.linalg.det(R)) > 1e-3
+
+
+def test_characteristic_weno_limits(oracle_lib):
+    """Characteristic-variable WENO: eps -> infinity gives the linear
+    weights, linear fields stay exact, and a front is limited."""
+    O = oracle_lib
+    mesh = mixed_mesh(8)
+
+    def phys(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        s = 0.2 * np.sin(3 * x + 2 * y) + 0.1 * x * y
+        return exact.cons_from_prim(GAM, 1.0 + s, 0.5 + s, 0.2 - s, (1.0 + 1.5 * s) / GAM)
+    W, Wx = exact.cell_averages(mesh, phys)
+    base = dict(gamma=GAM, bcs=[dict(kind="farfield", rho=1.0, u=(0.5, 0.2), p=1 / GAM)])
+    spec_c = dict(base, weno_vars="characteristic")
+    om = O.OracleMesh(mesh)
+
+    def face_eval(spec, W, Wx):
+        s = O.OracleSolver(om, spec)
+        s.set_state(W, Wx)
+        return s.hi_residual(1e-3)
+    r0 = face_eval(base, W, Wx)
+    r1 = face_eval(dict(spec_c, weno_eps=1e30), W, Wx)
+    # net fluxes of O(1) face fluxes: round-off of the L, R projections is absolute
+    np.testing.assert_allclose(r1, r0, rtol=1e-11, atol=1e-12)
+    r2 = face_eval(dict(spec_c, weno_eps=1e-6), W, Wx)
+    assert np.abs(r2 - r0).max() > 1e-6 * np.abs(r0).max()
+    # a linear field: the limited reconstruction is still exact, so the
+    # residual equals the linear-weight one
+    C = np.random.default_rng(37).normal(size=(3, 4)) * 0.1
+    C[0] += np.array([1.5, 0.3, 0.2, 3.0])
+
+    def q(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        return C[0] + x[..., None] * C[1] + y[..., None] * C[2]
+    Wl, Wxl = exact.cell_averages(mesh, q)
+    np.testing.assert_allclose(face_eval(dict(spec_c, weno_eps=1e-6), Wl, Wxl), face_eval(base, Wl, Wxl),
+                               rtol=1e-10, atol=1e-10)
