@@ -88,6 +88,14 @@ enum { CGKS_FLUX_KFVS = 0, CGKS_FLUX_LF = 1 };
  * FULL and compact WENO weights are 2-D only. */
 enum { CGKS_FLUX_SMOOTH = 0, CGKS_FLUX_FULL = 1 };
 
+/* Variables the compact WENO weights act on (Section 4: conservative by
+ * default, characteristic for the shock reflection problem).
+ *   CONSERVATIVE:   per cell, per conservative component.
+ *   CHARACTERISTIC: per face side, per characteristic field of the Euler
+ *                   flux Jacobian along the face normal at the mean of the
+ *                   two cell averages. */
+enum { CGKS_WENO_CONSERVATIVE = 0, CGKS_WENO_CHARACTERISTIC = 1 };
+
 #define CGKS_MAX_BC 16
 
 typedef struct {
@@ -121,7 +129,7 @@ typedef struct {
                             dependent launch, sm_90+); 0: plain stream order.  Same results. */
   int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF */
   int32_t flux_hi;       /* CGKS_FLUX_SMOOTH (default) or CGKS_FLUX_FULL */
-  int32_t pad_;
+  int32_t weno_vars;     /* CGKS_WENO_CONSERVATIVE (default) or CGKS_WENO_CHARACTERISTIC */
   double tau_c1, tau_c2; /* numerical collision time constants of the full flux (0.01, 1) */
   double weno_eps;       /* > 0: compact WENO nonlinear weights with this epsilon (Section 4 uses
                             1e-2 and 1e-6); 0 (default): linear weights */

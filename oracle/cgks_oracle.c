@@ -19,6 +19,10 @@
  *   FV semi-discretisation, Gauss points ..... Section 2.1, Eq. (semidiscrete)
  *   Maxwellian, micro-slopes a, A ............ Section 2.2
  *   smooth GKS flux .......................... Section 2.2, Eq. (2nd-smooth-flux)
+ *   full GKS flux, tau_n ..................... Section 2.2, Eq. (2nd-flux)
+ *   compact WENO (eps), characteristic vars .. Section 4 (transonic / supersonic
+ *                                              cases, shock reflection)
+ *   Dirichlet, supersonic outflow ............ Section 4 (shock reflection)
  *   interface state W_{p,k}(t) ............... Section 2.3
  *   Gauss-Green gradient update .............. Section 2.3 (gauss-formula)
  *   S1O2 ..................................... Section 2.4, Eqs. (s1o2), (flux-operator)
@@ -43,7 +47,13 @@
  *   walls mirror the reconstructed point state (and enter the wall cell's
  *   reconstruction as mirror-image ghost cells), the far field takes
  *   Riemann invariants of the cell mean and the free stream; the
- *   equilibrium normal slope adds alpha * jump / delta (Nishikawa 2010).
+ *   equilibrium normal slope adds alpha * jump / delta (Nishikawa 2010);
+ *   full flux: tau_n = tau + C1 dt + C2 dt |p_l - p_r| / (p_l + p_r) in the
+ *   exponentials, time dependence through the integrals over [0, dt] and
+ *   [0, dt/2]; WENO: candidates P2 and the linear polynomials of the own
+ *   and neighbours' mean gradients, Jiang-Shu weights gamma/(beta + eps)^2
+ *   with gamma_0 = 0.95; characteristic fields of the Euler Jacobian along
+ *   the face normal at the mean of the two cell averages.
  */
 #include <math.h>
 #include <stdint.h>

@@ -24,6 +24,7 @@ S1O2, S2O4 = 0, 1
 FP64, MIXED = 0, 1
 FLUX_KFVS, FLUX_LF = 0, 1
 FLUX_SMOOTH, FLUX_FULL = 0, 1
+WENO_CONSERVATIVE, WENO_CHARACTERISTIC = 0, 1
 MAX_BC = 16
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "mesh rejected", -4: "CUDA error",
@@ -51,7 +52,7 @@ class CgksParams(C.Structure):
                 ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32), ("time_scheme", C.c_int32),
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
-                ("flux_lo", C.c_int32), ("flux_hi", C.c_int32), ("pad_", C.c_int32),
+                ("flux_lo", C.c_int32), ("flux_hi", C.c_int32), ("weno_vars", C.c_int32),
                 ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_eps", C.c_double), ("weno_g0", C.c_double),
                 ("bc", CgksBC * MAX_BC),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
@@ -197,6 +198,7 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     gamma, mu, alpha, cfl_hi, cfl_lo, n_implicit, n_sweeps, time_scheme,
     precision, use_graph, flux_lo ('kfvs' | 'lf'), flux_hi ('smooth' |
     'full'), tau_c1, tau_c2, weno_eps (0: linear weights), weno_g0,
+    weno_vars ('conservative' | 'characteristic'),
     bcs=[{kind ('slip' | 'noslip' | 'farfield' | 'dirichlet' | 'outflow'),
     uw, rho, u, p}]."""
     P = CgksParams()
@@ -210,6 +212,8 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
     P.flux_lo = {"kfvs": FLUX_KFVS, "lf": FLUX_LF}[spec.get("flux_lo", "kfvs")]
     P.flux_hi = {"smooth": FLUX_SMOOTH, "full": FLUX_FULL}[spec.get("flux_hi", "smooth")]
+    P.weno_vars = {"conservative": WENO_CONSERVATIVE,
+                   "characteristic": WENO_CHARACTERISTIC}[spec.get("weno_vars", "conservative")]
     P.precision = {"fp64": FP64, "mixed": MIXED}[spec.get("precision", "fp64")]
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)

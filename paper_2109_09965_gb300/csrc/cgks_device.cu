@@ -49,6 +49,7 @@ struct Shared {
   int n_implicit = 6, n_sweeps = 2, time_scheme = CGKS_S1O2, precision = CGKS_FP64, use_graph = 1, lo_fused = 0;
   int autotune = 1, pdl = 1, flux_lo = CGKS_FLUX_KFVS, flux_hi = CGKS_FLUX_SMOOTH;
   double tau_c1 = 0.01, tau_c2 = 1.0, weno_eps = 0.0, weno_g0 = 0.95;
+  int weno_vars = CGKS_WENO_CONSERVATIVE;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -189,7 +190,8 @@ void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
   Bufs<TF> &B = bufs<TF>(b);
   // the nonlinear WENO weights and the full flux are separate instantiations,
   // so the default (linear weights, smooth flux) kernels stay as lean as before
-  const bool weno = b->sh.weno_eps > 0.0, full = b->sh.flux_hi == CGKS_FLUX_FULL;
+  const bool chr = b->sh.weno_eps > 0.0 && b->sh.weno_vars == CGKS_WENO_CHARACTERISTIC;
+  const bool weno = b->sh.weno_eps > 0.0 && !chr, full = b->sh.flux_hi == CGKS_FLUX_FULL;
   tuned_launch(b->tune, TK_RECON, b->stream, [&] {
     with_shape(b->tune.shape(TK_RECON), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
@@ -202,12 +204,14 @@ void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
     with_shape(b->tune.shape(TK_FACE), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
       const dim3 g(nblk(b->F, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
-      if (full)
-        launch(b, KI_FACE, k_face<TF, S, true>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout,
+      auto go = [&](auto kern) {
+        launch(b, KI_FACE, kern, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, (const TF *)B.coef, Fout,
                (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits);
-      else
-        launch(b, KI_FACE, k_face<TF, S, false>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, (const TF *)B.coef, Fout,
-               (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits);
+      };
+      if (full && chr) go(k_face<TF, S, true, true>);
+      else if (full) go(k_face<TF, S, true, false>);
+      else if (chr) go(k_face<TF, S, false, true>);
+      else go(k_face<TF, S, false, false>);
     });
   });
 }
@@ -456,6 +460,7 @@ void fill_shared_params(const Shared &sh, ParamsT<T> &P) {
   P.tau_c2 = static_cast<T>(sh.tau_c2);
   P.weno_eps = static_cast<T>(sh.weno_eps);
   P.weno_g0 = static_cast<T>(sh.weno_g0);
+  P.weno_vars = sh.weno_vars;
 }
 
 // The device arena of a batch: one allocation carved into 256-byte aligned
@@ -914,6 +919,7 @@ Shared shared_from(const cgks_params *p) {
   sh.flux_lo = p->flux_lo;
   sh.flux_hi = p->flux_hi;
   sh.tau_c1 = p->tau_c1; sh.tau_c2 = p->tau_c2; sh.weno_eps = p->weno_eps; sh.weno_g0 = p->weno_g0;
+  sh.weno_vars = p->weno_vars;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -924,7 +930,8 @@ int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_
       p->n_bc > CGKS_MAX_BC || (p->precision != CGKS_FP64 && p->precision != CGKS_MIXED) || !(p->alpha >= 0.0) ||
       (p->flux_lo != CGKS_FLUX_KFVS && p->flux_lo != CGKS_FLUX_LF) ||
       (p->flux_hi != CGKS_FLUX_SMOOTH && p->flux_hi != CGKS_FLUX_FULL) || !(p->tau_c1 >= 0.0) ||
-      !(p->tau_c2 >= 0.0) || !(p->weno_eps >= 0.0) || (p->weno_eps > 0.0 && !(p->weno_g0 > 0.0 && p->weno_g0 < 1.0)))
+      !(p->tau_c2 >= 0.0) || !(p->weno_eps >= 0.0) || (p->weno_eps > 0.0 && !(p->weno_g0 > 0.0 && p->weno_g0 < 1.0)) ||
+      (p->weno_vars != CGKS_WENO_CONSERVATIVE && p->weno_vars != CGKS_WENO_CHARACTERISTIC))
     return CGKS_EINVAL;
   for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;

@@ -51,6 +51,7 @@ struct ParamsT {
   int flux_hi;                   // high-level flux: CGKS_FLUX_SMOOTH or CGKS_FLUX_FULL
   T tau_c1, tau_c2;              // numerical collision time constants of the full flux
   T weno_eps, weno_g0;           // compact WENO epsilon (0: linear weights), linear weight of P2
+  int weno_vars;                 // CGKS_WENO_CONSERVATIVE (per cell) or CGKS_WENO_CHARACTERISTIC (per face side)
 };
 
 template <typename T>
@@ -329,6 +330,92 @@ __device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restri
   }
 }
 
+// value and gradient at scaled offset (x, y) of a polynomial of cell i with
+// the given coefficients c[q][v]
+template <typename T>
+__device__ __forceinline__ void poly_point(const MeshT<T> &m, const T *__restrict__ W, const T c[kNM][4], int i, T x,
+                                           T y, T val[4], T gx[4], T gy[4]) {
+  const int n = m.nc;
+  T ih = m.ih[i];
+  T p2 = x * x - m.m2[i], p3 = x * y - m.m2[n + i], p4 = y * y - m.m2[2 * n + i];
+  for (int v = 0; v < 4; ++v) {
+    val[v] = W[v * n + i] + c[0][v] * x + c[1][v] * y + c[2][v] * p2 + c[3][v] * p3 + c[4][v] * p4;
+    gx[v] = (c[0][v] + T(2) * c[2][v] * x + c[3][v] * y) * ih;
+    gy[v] = (c[1][v] + c[3][v] * x + T(2) * c[4][v] * y) * ih;
+  }
+}
+
+// Compact WENO on characteristic variables (Section 4, shock reflection),
+// for the side of a face held by cell i: the candidates of cell i (its
+// linear-weight quadratic from coef, h times the mean gradients of the cell
+// and its face neighbours) are projected on the left eigenvectors of the
+// Euler flux Jacobian along the face normal n at the state wref (the mean
+// of the two cell averages; the cell's own on a boundary face), combined by
+// weno_combine per characteristic field and projected back.  Right
+// eigenvectors (columns): u_n - c, entropy, shear, u_n + c; the left ones
+// in closed form with b1 = (gamma - 1)/c^2, b2 = b1 |u|^2 / 2.
+template <typename T>
+__device__ void char_side(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W, const T *__restrict__ Wx,
+                          const T *__restrict__ coef, int i, const T wref[4], T nx, T ny, T out[kNM][4]) {
+  const int n = m.nc;
+  const T g = P.gamma;
+  const T ir = T(1) / wref[0];
+  const T u = wref[1] * ir, v = wref[2] * ir;
+  const T q2 = u * u + v * v;
+  const T p = (g - T(1)) * (wref[3] - T(0.5) * wref[0] * q2);
+  const T c = D::d_sqrt(g * p * ir), ic = T(1) / c;
+  const T H = (wref[3] + p) * ir;
+  const T un = u * nx + v * ny, ut = -u * ny + v * nx;
+  const T b1 = (g - T(1)) * ic * ic, b2 = T(0.5) * b1 * q2;
+  const T R[4][4] = { { T(1), T(1), T(0), T(1) },
+                      { u - c * nx, u, -ny, u + c * nx },
+                      { v - c * ny, v, nx, v + c * ny },
+                      { H - c * un, T(0.5) * q2, ut, H + c * un } };
+  const T L[4][4] = { { T(0.5) * (b2 + un * ic), T(0.5) * (-b1 * u - nx * ic), T(0.5) * (-b1 * v - ny * ic),
+                        T(0.5) * b1 },
+                      { T(1) - b2, b1 * u, b1 * v, -b1 },
+                      { -ut, -ny, nx, T(0) },
+                      { T(0.5) * (b2 - un * ic), T(0.5) * (-b1 * u + nx * ic), T(0.5) * (-b1 * v + ny * ic),
+                        T(0.5) * b1 } };
+  const T h = T(1) / m.ih[i];
+  T lin[5][2][4];
+  int nk = 0;
+  auto add = [&](int j) {
+    T gx[4], gy[4];
+    for (int a = 0; a < 4; ++a) { gx[a] = Wx[a * n + j]; gy[a] = Wx[(4 + a) * n + j]; }
+    for (int a = 0; a < 4; ++a) {
+      T sx = T(0), sy = T(0);
+      for (int b = 0; b < 4; ++b) { sx += L[a][b] * gx[b]; sy += L[a][b] * gy[b]; }
+      lin[nk][0][a] = h * sx;
+      lin[nk][1][a] = h * sy;
+    }
+    ++nk;
+  };
+  add(i);
+  for (int sl = 0; sl < kMaxFace; ++sl) {
+    if (m.cface[sl * n + i] == kNoFace) continue;
+    const int j = m.cnbr[sl * n + i];
+    if (j >= 0) add(j);
+  }
+  T cq[kNM][4];
+  for (int q = 0; q < kNM; ++q) {
+    T cv[4];
+    for (int b = 0; b < 4; ++b) cv[b] = coef[(q * 4 + b) * n + i];
+    for (int a = 0; a < 4; ++a) {
+      T acc = T(0);
+      for (int b = 0; b < 4; ++b) acc += L[a][b] * cv[b];
+      cq[q][a] = acc;
+    }
+  }
+  weno_combine(P, m.m2[i], m.m2[n + i], m.m2[2 * n + i], nk, lin, cq);
+  for (int q = 0; q < kNM; ++q)
+    for (int b = 0; b < 4; ++b) {
+      T acc = T(0);
+      for (int a = 0; a < 4; ++a) acc += R[b][a] * cq[q][a];
+      out[q][b] = acc;
+    }
+}
+
 // ghost of a cell-mean state (zero gradients)
 template <typename T>
 __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T ny, const T w[4], T wg[4]) {
@@ -354,10 +441,10 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, T nx, T n
 // K2: gas-kinetic flux and interface state at the two Gauss points of every
 // face; writes the weighted sums F0, F1, Wc, Wt (global frame) per face:
 //   out[(k*4 + v)*nf + f], k = 0 F0, 1 F1, 2 Wc, 3 Wt.
-template <typename T, bool FULL>
+template <typename T, bool FULL, bool CHAR>
 __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
-                                        const T *__restrict__ coef, T *__restrict__ out, const Ctl *ctl,
-                                        const unsigned long long *dt_bits, const int f) {
+                                        const T *__restrict__ Wx, const T *__restrict__ coef, T *__restrict__ out,
+                                        const Ctl *ctl, const unsigned long long *dt_bits, const int f) {
   const int sid = m.fsid[f];
   if (sid < 0) return;   // free face space of a batch
   const int nf = m.nf;
@@ -386,9 +473,24 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
       dirichlet_ghost(P, tag, nx, ny, wff);
     }
   }
+  // characteristic WENO: the two sides' polynomials limited for this face
+  T cs0[CHAR ? kNM : 1][4], cs1[CHAR ? kNM : 1][4];
+  bool lim0 = false, lim1 = false;
+  if constexpr (CHAR) {
+    T wref[4];
+    for (int v = 0; v < 4; ++v)
+      wref[v] = c1 >= 0 ? T(0.5) * (W[v * m.nc + c0] + W[v * m.nc + c1]) : W[v * m.nc + c0];
+    lim0 = m.wenok[c0] != 0;
+    if (lim0) char_side(m, P, W, Wx, coef, c0, wref, nx, ny, cs0);
+    lim1 = c1 >= 0 && m.wenok[c1] != 0;
+    if (lim1) char_side(m, P, W, Wx, coef, c1, wref, nx, ny, cs1);
+  }
   for (int k = 0; k < 2; ++k) {
     T wL[4], gxL[4], gyL[4];
-    recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
+    if (CHAR && lim0)
+      poly_point(m, W, cs0, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
+    else
+      recon_point(m, W, coef, c0, m.fxi[(2 * k) * nf + f], m.fxi[(2 * k + 1) * nf + f], wL, gxL, gyL);
     T wl[4], dnl[4], dtl[4], t0[4], t1[4];
     D::rot_in(nx, ny, wL, wl);
     for (int v = 0; v < 4; ++v) { t0[v] = nx * gxL[v] + ny * gyL[v]; t1[v] = -ny * gxL[v] + nx * gyL[v]; }
@@ -397,7 +499,10 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
     T wr[4], dnr[4], dtr[4];
     if (c1 >= 0) {
       T wR[4], gxR[4], gyR[4];
-      recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
+      if (CHAR && lim1)
+        poly_point(m, W, cs1, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
+      else
+        recon_point(m, W, coef, c1, m.fxi[(4 + 2 * k) * nf + f], m.fxi[(5 + 2 * k) * nf + f], wR, gxR, gyR);
       D::rot_in(nx, ny, wR, wr);
       for (int v = 0; v < 4; ++v) { t0[v] = nx * gxR[v] + ny * gyR[v]; t1[v] = -ny * gxR[v] + nx * gyR[v]; }
       D::rot_in(nx, ny, t0, dnr);
@@ -427,14 +532,15 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out[(k * 4 + v) * nf + f] = acc[k][v];
 }
-template <typename T, int SH, bool FULL = false>
+template <typename T, int SH, bool FULL = false, bool CHAR = false>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_face(MeshT<T> m, ParamsT<T> P,
                                                                        const T *__restrict__ W,
+                                                                       const T *__restrict__ Wx,
                                                                        const T *__restrict__ coef,
                                                                        T *__restrict__ out, const Ctl *ctl,
                                                                        const unsigned long long *dt_bits) {
   pdl_enter();
-  for_items<SH>(m.nf, [&](int f) { face_at<T, FULL>(m, P, W, coef, out, ctl, dt_bits, f); });
+  for_items<SH>(m.nf, [&](int f) { face_at<T, FULL, CHAR>(m, P, W, Wx, coef, out, ctl, dt_bits, f); });
   pdl_exit();
 }
 

@@ -43,11 +43,12 @@ def advance_oracle(O, mesh, spec, state, n):
     return o.get_state()
 
 
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
 @pytest.mark.parametrize("scheme", ["S1O2", "S2O4"])
 @pytest.mark.parametrize("eps", [1e-2, 1e-6])
-def test_shock_reflection_explicit_steps_match_oracle(libs, eps, scheme):
+def test_shock_reflection_explicit_steps_match_oracle(libs, eps, scheme, weno_vars):
     cgks, O = libs
-    mesh, spec, state = shock_case(24, 6, eps)
+    mesh, spec, state = shock_case(24, 6, eps, weno_vars)
     spec = dict(spec, time_scheme=scheme)
     state = advance_oracle(O, mesh, spec, state, 20)
     g, o = pair(libs, mesh, spec, state)
@@ -58,11 +59,12 @@ def test_shock_reflection_explicit_steps_match_oracle(libs, eps, scheme):
         assert abs(rg[0] - ro[0]) <= 1e-9 * abs(ro[0])
 
 
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
 @pytest.mark.parametrize("scheme", ["S1O2", "S2O4"])
 @pytest.mark.parametrize("eps", [1e-2, 1e-6])
-def test_shock_reflection_cycles_match_oracle(libs, eps, scheme):
+def test_shock_reflection_cycles_match_oracle(libs, eps, scheme, weno_vars):
     cgks, O = libs
-    mesh, spec, state = shock_case(24, 6, eps)
+    mesh, spec, state = shock_case(24, 6, eps, weno_vars)
     spec = dict(spec, time_scheme=scheme)
     g, o = pair(libs, mesh, spec, state)
     for k in range(4):
@@ -72,11 +74,12 @@ def test_shock_reflection_cycles_match_oracle(libs, eps, scheme):
         assert abs(rg[0] - ro[0]) <= 1e-9 * abs(ro[0]), (rg, ro)
 
 
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
 @pytest.mark.parametrize("flux_lo", ["kfvs", "lf"])
 @pytest.mark.parametrize("name", ["cavity8", "mixed_slip_farfield"])
-def test_viscous_full_flux_with_weno_matches_oracle(libs, name, flux_lo):
+def test_viscous_full_flux_with_weno_matches_oracle(libs, name, flux_lo, weno_vars):
     mesh, spec, state = case(name)
-    spec = dict(spec, flux_hi="full", weno_eps=1e-6, tau_c1=0.05, tau_c2=2.0, flux_lo=flux_lo)
+    spec = dict(spec, flux_hi="full", weno_eps=1e-6, tau_c1=0.05, tau_c2=2.0, flux_lo=flux_lo, weno_vars=weno_vars)
     g, o = pair(libs, mesh, spec, state)
     for k in range(2):
         g.explicit_steps(1)
@@ -87,19 +90,21 @@ def test_viscous_full_flux_with_weno_matches_oracle(libs, name, flux_lo):
     np.testing.assert_allclose(hg, ho, rtol=1e-9)
 
 
-def test_shock_reflection_full_grid_matches_oracle(libs):
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
+def test_shock_reflection_full_grid_matches_oracle(libs, weno_vars):
     """The paper's 120 x 30 grid: two V-cycles from the uniform start."""
-    mesh, spec, state = shock_case(120, 30, 1e-2)
+    mesh, spec, state = shock_case(120, 30, 1e-2, weno_vars)
     g, o = pair(libs, mesh, spec, state)
     hg, ho = g.pmg_cycle(2), o.pmg_cycles(2)
     check(g, o, "120x30")
     np.testing.assert_allclose(hg, ho, rtol=1e-9)
 
 
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
 @pytest.mark.parametrize("scheme", ["S1O2", "S2O4"])
-def test_shock_reflection_mixed_precision(libs, scheme):
+def test_shock_reflection_mixed_precision(libs, scheme, weno_vars):
     cgks, O = libs
-    mesh, spec, state = shock_case(24, 6, 1e-2)
+    mesh, spec, state = shock_case(24, 6, 1e-2, weno_vars)
     spec = dict(spec, time_scheme=scheme)
     state = advance_oracle(O, mesh, spec, state, 20)
     g, o = pair(libs, mesh, dict(spec, precision="mixed"), state)
@@ -126,9 +131,10 @@ def test_supersonic_stream_kept_through_new_boundaries(libs, precision):
     assert np.abs(W - W0).max() < tol * np.abs(W0).max()
 
 
-def test_graph_and_plain_launches_agree_bitwise(libs):
+@pytest.mark.parametrize("weno_vars", ["conservative", "characteristic"])
+def test_graph_and_plain_launches_agree_bitwise(libs, weno_vars):
     cgks, O = libs
-    mesh, spec, state = shock_case(24, 6, 1e-2)
+    mesh, spec, state = shock_case(24, 6, 1e-2, weno_vars)
     out = []
     for graph in (0, 1):
         s = cgks.Solver(cgks.Mesh(mesh), dict(spec, use_graph=graph, autotune=0))
