@@ -595,7 +595,7 @@ def main():
                 cgks, args, world, local, flush, hbm, hbm_src, "sphere3M", 5, 60, 30, 1e-3, 0.2, 1000, 10,
                 "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
                 "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
-                "(throughput only: the Ma 1.5 case needs the limiter, not built)"),
+                "(throughput only: the Ma 1.5 case needs the full flux and WENO, built in 2-D only)"),
         }
     if args.serving == "sample":
         line["serving"] = serving(cgks, 24, 2000, 20000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
