@@ -85,7 +85,8 @@ enum { CGKS_FLUX_KFVS = 0, CGKS_FLUX_LF = 1 };
  *           tau_n = mu/p + tau_c1 dt + tau_c2 dt |p_l - p_r| / (p_l + p_r)
  *           in the exponentials; its time dependence enters the time
  *           schemes through the integrals over [0, dt] and [0, dt/2].
- * FULL and compact WENO weights are 2-D only. */
+ * 3-D takes FULL and conservative WENO weights; characteristic WENO and the
+ * Dirichlet / outflow boundaries are 2-D only. */
 enum { CGKS_FLUX_SMOOTH = 0, CGKS_FLUX_FULL = 1 };
 
 /* Variables the compact WENO weights act on (Section 4: conservative by

@@ -68,7 +68,10 @@ typedef struct {
   double gamma, mu, alpha, cfl_hi, cfl_lo;
   int n_implicit, n_sweeps, time_scheme, n_bc;
   int flux_lo;                /* low-level flux: 0 = KFVS, 1 = Lax-Friedrichs */
-  int pad_;
+  int flux_hi;                /* high-level flux: 0 = smooth, 1 = full, Eq. (2nd-flux) */
+  double tau_c1, tau_c2;      /* tau_n = tau + C1 dt + C2 dt |p_l - p_r| / (p_l + p_r) */
+  double weno_eps;            /* > 0: nonlinear compact WENO weights; <= 0: linear weights */
+  double weno_g0;             /* linear weight of the quadratic candidate */
   o3_bc bc[MAXBC];
 } o3_params;
 
@@ -388,6 +391,138 @@ void o3_gks_flux_point(const o3_params *P, const double Wl_g[NV], const double W
   to_global(E, F0l, F0);
   to_global(E, F1l, F1);
   to_global(E, Wc, Wc_out);
+  to_global(E, Wtl, Wt_out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Full GKS flux at one Gauss point, Eq. (2nd-flux), 3-D:              */
+/*   f = (1 - e) g^c + [(t + tau) e - tau] a^c.u g^c                    */
+/*       + (t - tau + tau e) A^c g^c                                    */
+/*       + e g^l [1 - (tau + t) a^l.u - tau A^l] H(u_n)                 */
+/*       + e g^r [1 - (tau + t) a^r.u - tau A^r] (1 - H(u_n)),          */
+/* e = exp(-t / tau_n), tau = mu / p^c, tau_n = tau + C1 dt             */
+/* + C2 dt |p_l - p_r| / (p_l + p_r) (reading).  As in 2-D, the time    */
+/* dependence is brought to F0 + t F1 through the integrals over        */
+/* [0, dt] and [0, dt/2], and the interface state to the line through   */
+/* its values at dt/2 and dt.                                           */
+/* ------------------------------------------------------------------ */
+typedef struct { double c1, c2, c3, e, te; } o3_tcoef;
+
+static o3_tcoef tcoef_at(double t, double tau, double taun) {
+  o3_tcoef c;
+  double e = taun > 0.0 ? exp(-t / taun) : 0.0;
+  c.c1 = 1.0 - e; c.c2 = (t + tau) * e - tau; c.c3 = t - tau + tau * e; c.e = e; c.te = t * e;
+  return c;
+}
+static o3_tcoef tcoef_int(double T, double tau, double taun) {
+  o3_tcoef c;
+  double E = taun > 0.0 ? exp(-T / taun) : 0.0;
+  double om = taun > 0.0 ? -expm1(-T / taun) : 1.0;
+  c.e = taun * om;
+  c.te = taun * taun * om - taun * T * E;
+  c.c1 = T - c.e;
+  c.c2 = c.te + tau * c.e - tau * T;
+  c.c3 = 0.5 * T * T - tau * T + tau * c.e;
+  return c;
+}
+
+/* slopes a_1..a_3 (local axes) and A of a Maxwellian from its derivatives */
+static void maxw_slopes3(const o3_mom *m, double rho, double dW[3][NV], double a[3][NV], double A[NV]) {
+  double bA[NV];
+  for (int k = 0; k < 3; ++k) micro_slope(m, rho, dW[k], a[k]);
+  for (int r = 0; r < NV; ++r)
+    bA[r] = -(mom_psi_slope(r, 1, 0, 0, a[0], m) + mom_psi_slope(r, 0, 1, 0, a[1], m) +
+              mom_psi_slope(r, 0, 0, 1, a[2], m)) * rho;
+  micro_slope(m, rho, bA, A);
+}
+
+/* Q = rho (<u psi>, <u (a.u) psi>, <u A psi>), Pm = rho (<psi>, <(a.u) psi>, <A psi>) */
+static void piece3(double rho, const o3_mom *m, double a[3][NV], const double A[NV], double Q[3][NV],
+                   double Pm[3][NV]) {
+  for (int r = 0; r < NV; ++r) {
+    Q[0][r] = rho * mom_psi(r, 1.0, 1, 0, 0, m);
+    Q[1][r] = rho * (mom_psi_slope(r, 2, 0, 0, a[0], m) + mom_psi_slope(r, 1, 1, 0, a[1], m) +
+                     mom_psi_slope(r, 1, 0, 1, a[2], m));
+    Q[2][r] = rho * mom_psi_slope(r, 1, 0, 0, A, m);
+    Pm[0][r] = rho * mom_psi(r, 1.0, 0, 0, 0, m);
+    Pm[1][r] = rho * (mom_psi_slope(r, 1, 0, 0, a[0], m) + mom_psi_slope(r, 0, 1, 0, a[1], m) +
+                      mom_psi_slope(r, 0, 0, 1, a[2], m));
+    Pm[2][r] = rho * mom_psi_slope(r, 0, 0, 0, A, m);
+  }
+}
+
+static void full_combine3(const o3_tcoef *c, double tau, double X[3][3][NV], double out[NV]) {
+  for (int r = 0; r < NV; ++r)
+    out[r] = c->c1 * X[0][0][r] + c->c2 * X[0][1][r] + c->c3 * X[0][2][r]
+           + c->e * (X[1][0][r] - tau * X[1][1][r] - tau * X[1][2][r]
+                     + X[2][0][r] - tau * X[2][1][r] - tau * X[2][2][r])
+           - c->te * (X[1][1][r] + X[2][1][r]);
+}
+
+void o3_gks_full_flux_point(const o3_params *P, const double Wl_g[NV], const double Wr_g[NV],
+                            const double gl[ND * NV], const double gr[ND * NV], const double n[3], double delta,
+                            double dt, double F0[NV], double F1[NV], double Wc_out[NV], double Wt_out[NV]) {
+  double K = o3_K(P->gamma);
+  double E[3][3];
+  frame(n, E);
+  double Wl[NV], Wr[NV];
+  to_local(E, Wl_g, Wl);
+  to_local(E, Wr_g, Wr);
+  double dl[3][NV], dr[3][NV];
+  for (int a = 0; a < 3; ++a) {
+    double tl[NV], tr[NV];
+    for (int v = 0; v < NV; ++v) {
+      tl[v] = E[a][0] * gl[v] + E[a][1] * gl[NV + v] + E[a][2] * gl[2 * NV + v];
+      tr[v] = E[a][0] * gr[v] + E[a][1] * gr[NV + v] + E[a][2] * gr[2 * NV + v];
+    }
+    to_local(E, tl, dl[a]);
+    to_local(E, tr, dr[a]);
+  }
+  o3_maxw gL = maxw_from_W(Wl, K), gR = maxw_from_W(Wr, K);
+  o3_mom mlh, mrh, mlf, mrf;
+  moments(&gL, K, +1, &mlh);
+  moments(&gR, K, -1, &mrh);
+  moments(&gL, K, 0, &mlf);
+  moments(&gR, K, 0, &mrf);
+  double al[3][NV], Al[NV], ar[3][NV], Ar[NV];
+  maxw_slopes3(&mlf, gL.rho, dl, al, Al);
+  maxw_slopes3(&mrf, gR.rho, dr, ar, Ar);
+  double Wc[NV];
+  for (int r = 0; r < NV; ++r) Wc[r] = gL.rho * mom_psi(r, 1.0, 0, 0, 0, &mlh) + gR.rho * mom_psi(r, 1.0, 0, 0, 0, &mrh);
+  double dW[3][NV];
+  for (int v = 0; v < NV; ++v) {
+    for (int a = 0; a < 3; ++a) dW[a][v] = 0.5 * (dl[a][v] + dr[a][v]);
+    if (delta > 0.0) dW[0][v] += P->alpha * (Wr[v] - Wl[v]) / delta;
+  }
+  o3_maxw gc = maxw_from_W(Wc, K);
+  o3_mom mc;
+  moments(&gc, K, 0, &mc);
+  double ac[3][NV], Ac[NV];
+  maxw_slopes3(&mc, gc.rho, dW, ac, Ac);
+  double pc = gc.rho / (2.0 * gc.lam), pl = gL.rho / (2.0 * gL.lam), pr = gR.rho / (2.0 * gR.lam);
+  double tau = P->mu / pc;
+  double taun = tau + P->tau_c1 * dt + P->tau_c2 * dt * fabs(pl - pr) / (pl + pr);
+  double Q[3][3][NV], Pm[3][3][NV];
+  piece3(gc.rho, &mc, ac, Ac, Q[0], Pm[0]);
+  piece3(gL.rho, &mlh, al, Al, Q[1], Pm[1]);
+  piece3(gR.rho, &mrh, ar, Ar, Q[2], Pm[2]);
+  o3_tcoef I1 = tcoef_int(dt, tau, taun), Ih = tcoef_int(0.5 * dt, tau, taun);
+  o3_tcoef C1 = tcoef_at(dt, tau, taun), Ch = tcoef_at(0.5 * dt, tau, taun);
+  double Fd[NV], Fh[NV], Wd[NV], Wh[NV];
+  full_combine3(&I1, tau, Q, Fd);
+  full_combine3(&Ih, tau, Q, Fh);
+  full_combine3(&C1, tau, Pm, Wd);
+  full_combine3(&Ch, tau, Pm, Wh);
+  double F0l[NV], F1l[NV], Wcl[NV], Wtl[NV];
+  for (int r = 0; r < NV; ++r) {
+    F0l[r] = (4.0 * Fh[r] - Fd[r]) / dt;
+    F1l[r] = 4.0 * (Fd[r] - 2.0 * Fh[r]) / (dt * dt);
+    Wcl[r] = 2.0 * Wh[r] - Wd[r];
+    Wtl[r] = 2.0 * (Wd[r] - Wh[r]) / dt;
+  }
+  to_global(E, F0l, F0);
+  to_global(E, F1l, F1);
+  to_global(E, Wcl, Wc_out);
   to_global(E, Wtl, Wt_out);
 }
 
@@ -913,6 +1048,64 @@ static void grad_rows(const double mj[NM], double gx[NM], double gy[NM], double 
   memcpy(gx, X, sizeof X); memcpy(gy, Y, sizeof Y); memcpy(gz, Z, sizeof Z);
 }
 
+/* Smoothness indicator of a candidate with scaled coefficients c (stride
+ * between monomials): the cell mean of the squared first derivatives in
+ * the scaled coordinates (linear functions, so the mean is the square of
+ * the centroid value plus the quadratic form of the central second
+ * moments M2 / h^2) plus the squared second derivatives, each multi-index
+ * once. */
+static double weno_beta3(const o3_cell *C, const double *c, int stride) {
+  double q[NM];
+  for (int k = 0; k < NM; ++k) q[k] = c[k * stride];
+  /* gradient of P = g0 + G (xi, eta, zeta) */
+  double g0[3] = { q[0], q[1], q[2] };
+  double G[3][3] = { { 2 * q[3], q[4], q[5] }, { q[4], 2 * q[6], q[7] }, { q[5], q[7], 2 * q[8] } };
+  double h2 = C->h * C->h;
+  double M[3][3] = { { C->M2[0] / h2, C->M2[1] / h2, C->M2[2] / h2 },
+                     { C->M2[1] / h2, C->M2[3] / h2, C->M2[4] / h2 },
+                     { C->M2[2] / h2, C->M2[4] / h2, C->M2[5] / h2 } };
+  double b = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    b += g0[d] * g0[d];
+    for (int a = 0; a < 3; ++a)
+      for (int e = 0; e < 3; ++e) b += G[d][a] * M[a][e] * G[d][e];
+  }
+  return b + 4 * q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + 4 * q[6] * q[6] + q[7] * q[7] + 4 * q[8] * q[8];
+}
+
+/* Compact WENO (conservative variables), as in 2-D: candidates P2 (X) and
+ * the linear polynomials of the mean gradients of the cell and its face
+ * neighbours; gamma_0 = g0, the rest (1 - g0)/m; w ~ gamma/(beta + eps)^2;
+ * P = (w_0/gamma_0)(P2 - sum gamma_k P1_k) + sum w_k P1_k.  In place. */
+static void weno_combine3(const o3_solver *s, const double *Wx, long i, double *X) {
+  const o3_cell *C = &s->m->cell[i];
+  double g0 = s->P.weno_g0, eps = s->P.weno_eps;
+  long cand[MAXFC + 1];
+  int m = 0;
+  cand[m++] = i;
+  for (int k = 0; k < C->nb; ++k) cand[m++] = C->nbr[k];
+  double gk = (1.0 - g0) / m;
+  for (int v = 0; v < NV; ++v) {
+    double G[MAXFC + 1][3], wt[MAXFC + 2], wsum = 0.0;
+    double b0 = weno_beta3(C, &X[v], NV);
+    wt[0] = g0 / ((b0 + eps) * (b0 + eps));
+    for (int k = 0; k < m; ++k) {
+      double cl[NM] = { 0 };
+      for (int d = 0; d < 3; ++d) cl[d] = G[k][d] = C->h * Wx[(cand[k] * ND + d) * NV + v];
+      double b = weno_beta3(C, cl, 1);
+      wt[k + 1] = gk / ((b + eps) * (b + eps));
+    }
+    for (int k = 0; k <= m; ++k) wsum += wt[k];
+    for (int k = 0; k <= m; ++k) wt[k] /= wsum;
+    for (int q = 0; q < NM; ++q) {
+      double lin = 0.0, sel = 0.0;
+      if (q < 3)
+        for (int k = 0; k < m; ++k) { lin += gk * G[k][q]; sel += wt[k + 1] * G[k][q]; }
+      X[q * NV + v] = wt[0] / g0 * (X[q * NV + v] - lin) + sel;
+    }
+  }
+}
+
 static void reconstruct_cell(o3_solver *s, const double *W, const double *Wx, long i) {
   const o3_mesh *m = s->m;
   const o3_cell *C = &m->cell[i];
@@ -991,6 +1184,7 @@ static void reconstruct_cell(o3_solver *s, const double *W, const double *Wx, lo
       for (int v = 0; v < NV; ++v) c[d * NV + v] = C->h * Wx[(i * ND + d) * NV + v];
     return;
   }
+  if (s->P.weno_eps > 0.0) weno_combine3(s, Wx, i, X);
   for (int q = 0; q < NM * NV; ++q) c[q] = X[q];
 }
 
@@ -1024,7 +1218,7 @@ void o3_recon_eval(const o3_solver *s, long cell, const double x[3], double val[
 }
 
 /* reconstruction + face fluxes; per face the weighted Gauss sums */
-static void hi_eval(o3_solver *s, const double *W, const double *Wx) {
+static void hi_eval(o3_solver *s, const double *W, const double *Wx, double dt) {
   const o3_mesh *m = s->m;
   reconstruct_all(s, W, Wx);
   for (long f = 0; f < m->nf; ++f) {
@@ -1040,7 +1234,8 @@ static void hi_eval(o3_solver *s, const double *W, const double *Wx) {
         o3_ghost(&s->P, F->tag, &W[F->c0 * NV], zero, F->n, Wr, gr);
       }
       double f0[NV], f1[NV], wc[NV], wt[NV];
-      o3_gks_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, f0, f1, wc, wt);
+      if (s->P.flux_hi) o3_gks_full_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, dt, f0, f1, wc, wt);
+      else o3_gks_flux_point(&s->P, Wl, Wr, gl, gr, F->n, F->delta, f0, f1, wc, wt);
       for (int v = 0; v < NV; ++v) {
         sF0[v] += F->wg[k] * f0[v]; sF1[v] += F->wg[k] * f1[v];
         sWc[v] += F->wg[k] * wc[v]; sWt[v] += F->wg[k] * wt[v];
@@ -1114,7 +1309,7 @@ static void hi_step(o3_solver *s, const double *W, const double *Wx, double dt, 
                     double *Rlag) {
   const o3_mesh *m = s->m;
   long nc = m->nc, nf = m->nf;
-  hi_eval(s, W, Wx);
+  hi_eval(s, W, Wx, dt);
   if (s->P.time_scheme == 0) {
     net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, Rlag);
     for (long c = 0; c < nc; ++c)
@@ -1132,7 +1327,7 @@ static void hi_step(o3_solver *s, const double *W, const double *Wx, double dt, 
     for (long c = 0; c < nc; ++c)
       for (int v = 0; v < NV; ++v) Ws[c * NV + v] = W[c * NV + v] + dt / m->cell[c].vol * R[c * NV + v];
     gauss_green(s, Wcn, s->Wt, 0.5 * dt, Wxs);
-    hi_eval(s, Ws, Wxs);
+    hi_eval(s, Ws, Wxs, dt);
     for (long q = 0; q < nf * NV; ++q) F1c[q] = F1n[q] + 2.0 * s->F1[q];
     net_flux(s, F0n, F1c, 1.0, dt / 6.0, Rlag);
     for (long c = 0; c < nc; ++c)
@@ -1163,7 +1358,7 @@ double o3_highorder_step(o3_solver *s, double dt) {
 }
 
 void o3_hi_residual(o3_solver *s, double dt, double *R) {
-  hi_eval(s, s->W, s->Wx);
+  hi_eval(s, s->W, s->Wx, dt);
   net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, R);
 }
 
@@ -1287,7 +1482,7 @@ static void pmg_cycle(o3_solver *s) {
   double *Wn = (double *)malloc(sizeof(double) * nc * NV), *Wxn = (double *)malloc(sizeof(double) * nc * ND * NV);
   double *Rlag = (double *)malloc(sizeof(double) * nc * NV), *U = (double *)malloc(sizeof(double) * nc * NV);
   hi_step(s, s->W, s->Wx, dt, Wn, Wxn, Rlag);
-  hi_eval(s, Wn, Wxn);
+  hi_eval(s, Wn, Wxn, dt);
   net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, s->Rp0);
   lo_solve(s, Wn, s->Rp0, U);
   for (long q = 0; q < nc * NV; ++q) Wn[q] += U[q] - Wn[q];

@@ -42,7 +42,8 @@ class O3BC(C.Structure):
 class O3Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("alpha", C.c_double), ("cfl_hi", C.c_double),
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
-                ("time_scheme", C.c_int), ("n_bc", C.c_int), ("flux_lo", C.c_int), ("pad_", C.c_int),
+                ("time_scheme", C.c_int), ("n_bc", C.c_int), ("flux_lo", C.c_int), ("flux_hi", C.c_int),
+                ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_eps", C.c_double), ("weno_g0", C.c_double),
                 ("bc", O3BC * 16)]
 
 
@@ -94,6 +95,8 @@ def lib():
             L.o3_set_rp0.argtypes = [vp, _dp]
             L.o3_get_rp0.argtypes = [vp, _dp]
             L.o3_gks_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
+            L.o3_gks_full_flux_point.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                                 _dp, _dp, _dp, _dp]
             L.o3_kfvs.argtypes = [P, _dp, _dp, _dp, _dp]
             L.o3_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.o3_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -119,6 +122,11 @@ def make_params(spec: dict) -> O3Params:
     P.n_sweeps = int(spec.get("n_sweeps", 2))
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
+    P.flux_hi = {"smooth": 0, "full": 1}[spec.get("flux_hi", "smooth")]
+    P.tau_c1 = float(spec.get("tau_c1", 0.01))
+    P.tau_c2 = float(spec.get("tau_c2", 1.0))
+    P.weno_eps = float(spec.get("weno_eps", 0.0))
+    P.weno_g0 = float(spec.get("weno_g0", 0.95))
     bcs = spec.get("bcs", [])
     P.n_bc = len(bcs)
     for i, b in enumerate(bcs):
@@ -276,6 +284,14 @@ def gks_flux_point(spec, Wl, Wr, gl, gr, n, delta=0.0):
     F0 = np.zeros(NV); F1 = np.zeros(NV); Wc = np.zeros(NV); Wt = np.zeros(NV)
     lib().o3_gks_flux_point(C.byref(P), _f64(Wl), _f64(Wr), _f64(gl, (ND * NV,)), _f64(gr, (ND * NV,)),
                             _f64(n), float(delta), F0, F1, Wc, Wt)
+    return F0, F1, Wc, Wt
+
+
+def gks_full_flux_point(spec, Wl, Wr, gl, gr, n, delta, dt):
+    P = make_params(spec)
+    F0 = np.zeros(NV); F1 = np.zeros(NV); Wc = np.zeros(NV); Wt = np.zeros(NV)
+    lib().o3_gks_full_flux_point(C.byref(P), _f64(Wl), _f64(Wr), _f64(gl, (ND * NV,)), _f64(gr, (ND * NV,)),
+                                 _f64(n), float(delta), float(dt), F0, F1, Wc, Wt)
     return F0, F1, Wc, Wt
 
 

@@ -1209,8 +1209,8 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   int rc = validate_params_tags(p, m->dim == 3 ? m->h3.bface_tags_used : m->h.bface_tags_used);
   if (rc) return rc;
   if (m->dim == 3) {
-    // the 3-D path runs the smooth flux with linear weights, and walls and far field
-    if (p->flux_hi != CGKS_FLUX_SMOOTH || p->weno_eps > 0.0) return CGKS_EINVAL;
+    // the 3-D path has walls and far field, and WENO on conservative variables
+    if (p->weno_eps > 0.0 && p->weno_vars != CGKS_WENO_CONSERVATIVE) return CGKS_EINVAL;
     for (int b = 0; b < p->n_bc; ++b)
       if (p->bc[b].kind != CGKS_BC_SLIP && p->bc[b].kind != CGKS_BC_NOSLIP && p->bc[b].kind != CGKS_BC_FARFIELD)
         return CGKS_EINVAL;

@@ -36,6 +36,7 @@ struct Geo3 {
         *f_fjump = nullptr, *f_fw = nullptr, *f_fxi = nullptr, *f_sn = nullptr, *f_shs = nullptr,
         *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
   int *fng, *cface, *cnbr, *fc0, *fc1, *bckind;
+  unsigned char *wenok;
 };
 
 struct Piece3 { void **dst; size_t bytes; };
@@ -129,18 +130,28 @@ void enqueue_res(Solver3 *s) {
 template <typename TF>
 void hi_eval(Solver3 *s, const TF *W, const TF *Wx, TF *Fout) {
   Bufs3<TF> &B = bufs<TF>(s);
+  // nonlinear weights and the full flux are separate instantiations (the
+  // default kernels stay as before)
+  const bool weno = s->P.weno_eps > 0.0, full = s->P.flux_hi == CGKS_FLUX_FULL;
   tuned_launch(s->tune, TK_RECON, s->stream, [&] {
     with_shape(s->tune.shape(TK_RECON), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
-      launch(s, KI_RECON, k_recon<TF, S>, dim3(nblk(s->N, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-             fmesh<TF>(s), fpar<TF>(s), W, Wx, B.coef);
+      const dim3 gr(nblk(s->N, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+      if (weno)
+        launch(s, KI_RECON, k_recon_weno<TF, S>, gr, blk, fmesh<TF>(s), fpar<TF>(s), W, Wx, B.coef,
+               (const unsigned char *)s->g.wenok);
+      else launch(s, KI_RECON, k_recon<TF, S>, gr, blk, fmesh<TF>(s), fpar<TF>(s), W, Wx, B.coef);
     });
   });
   tuned_launch(s->tune, TK_FACE, s->stream, [&] {
     with_shape(s->tune.shape(TK_FACE), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
-      launch(s, KI_FACE, k_face<TF, S>, dim3(nblk(s->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-             fmesh<TF>(s), fpar<TF>(s), W, (const TF *)B.coef, Fout);
+      const dim3 gr(nblk(s->F, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+      if (full)
+        launch(s, KI_FACE, k_face_full<TF, S>, gr, blk, fmesh<TF>(s), fpar<TF>(s), W, (const TF *)B.coef, Fout,
+               (const Ctl *)s->ctl, (const unsigned long long *)s->dt_bits);
+      else
+        launch(s, KI_FACE, k_face<TF, S>, gr, blk, fmesh<TF>(s), fpar<TF>(s), W, (const TF *)B.coef, Fout);
     });
   });
 }
@@ -274,6 +285,7 @@ void plan(Solver3 *s, std::vector<Piece3> &pc) {
   P8(&g.bcuw, 3 * CGKS_MAX_BC); P8(&g.bcrho, CGKS_MAX_BC); P8(&g.bcu, 3 * CGKS_MAX_BC); P8(&g.bcp, CGKS_MAX_BC);
   PI(&g.fng, F); PI(&g.cface, kMaxFace3 * N); PI(&g.cnbr, kMaxFace3 * N); PI(&g.fc0, F); PI(&g.fc1, F);
   PI(&g.bckind, CGKS_MAX_BC); PI(&s->perm, N); PI(&s->status, 1);
+  pc.push_back({ reinterpret_cast<void **>(&g.wenok), static_cast<size_t>(N) });
   pc.push_back({ reinterpret_cast<void **>(&s->ctl), sizeof(Ctl) });
   pc.push_back({ reinterpret_cast<void **>(&s->dt_bits), sizeof(unsigned long long) });
   if (!s->mixed) {
@@ -312,6 +324,10 @@ void fill_params(const cgks_params &p, ParamsT<T> &P) {
   P.kc.c2K = static_cast<T>(2.0 / (K + 3.0));
   P.kc.c4K = static_cast<T>(4.0 / (K + 3.0));
   P.flux_lo = p.flux_lo;
+  P.tau_c1 = static_cast<T>(p.tau_c1);
+  P.tau_c2 = static_cast<T>(p.tau_c2);
+  P.weno_eps = static_cast<T>(p.weno_eps);
+  P.weno_g0 = static_cast<T>(p.weno_g0);
 }
 
 #define CK3(x)                                  \
@@ -400,7 +416,8 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   std::vector<char> wall(CGKS_MAX_BC, 0);
   for (int t = 0; t < p->n_bc; ++t) wall[t] = p->bc[t].kind != CGKS_BC_FARFIELD;
   std::vector<double> op;
-  build_operator3(m, wall, op);
+  std::vector<unsigned char> wenok;
+  build_operator3(m, wall, op, &wenok);
   std::vector<double> ivol(N), ih(N), hdt(N), fe(9 * F), fjump(F), sn(3 * kMaxFace3 * N, 0.0), shs(kMaxFace3 * N, 0.0);
   for (int64_t i = 0; i < N; ++i) {
     ivol[i] = 1.0 / m.vol[i];
@@ -455,6 +472,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   up(g.bcp, bcp.data(), 8 * bcp.size()); up(g.fng, m.fng.data(), 4 * F); up(g.cface, m.cface.data(), 4 * kMaxFace3 * N);
   up(g.cnbr, m.cnbr.data(), 4 * kMaxFace3 * N); up(g.fc0, m.fc0.data(), 4 * F); up(g.fc1, m.fc1.data(), 4 * F);
   up(g.bckind, bckind.data(), 4 * bckind.size()); up(s->perm, perm.data(), 4 * N);
+  up(g.wenok, wenok.data(), N);
   std::vector<std::vector<float>> keep;
   auto upf = [&](float *dst, const std::vector<double> &src) {
     keep.emplace_back(src.begin(), src.end());
@@ -623,6 +641,7 @@ template <typename TF>
 int s3_wall_loads_t(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces, double *x, double *nrm,
                     double *S, double *traction) {
   Bufs3<TF> &B = bufs<TF>(s);
+  if (s->P.flux_hi == CGKS_FLUX_FULL) enqueue_dt(s, -1.0);   // the full flux integrates over a step
   hi_eval<TF>(s, B.W, B.Wx, B.FA);
   const int64_t F = s->F;
   std::vector<TF> F0(3 * static_cast<size_t>(F));

@@ -459,9 +459,11 @@ int build_host_mesh3(int64_t nn, const double *xyz, int64_t nc, const uint8_t *c
 // Quadratic only when the stencil centroids spread in three directions
 // (normalised det of sum d d^T >= 1e-3), linear from the own gradient
 // otherwise.
-void build_operator3(const HostMesh3 &M, const std::vector<char> &tag_is_wall, std::vector<double> &op) {
+void build_operator3(const HostMesh3 &M, const std::vector<char> &tag_is_wall, std::vector<double> &op,
+                     std::vector<unsigned char> *quad_ok) {
   const int64_t nc = M.n_cells, nf = M.n_faces;
   op.assign(static_cast<size_t>(kNCol3 * kNM3) * nc, 0.0);
+  if (quad_ok) quad_ok->assign(nc, 0);
   double *out = op.data();
   for (int64_t i = 0; i < nc; ++i) {
     const double hi = M.h[i];
@@ -546,6 +548,7 @@ void build_operator3(const HostMesh3 &M, const std::vector<char> &tag_is_wall, s
       const bool grad_col = col >= 4 * kMaxFace3 || (col % 4) != 0;
       for (int q = 0; q < kNM3; ++q) put(col, q, pinv[q * rows + r] * (grad_col ? hi : 1.0));
     }
+    if (quad_ok) (*quad_ok)[i] = 1;
   }
 }
 

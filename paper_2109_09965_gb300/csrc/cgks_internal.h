@@ -93,7 +93,8 @@ int build_host_mesh3(int64_t n_nodes, const double *xyz, int64_t n_cells, const 
                      const int64_t *cptr, const int64_t *cnodes, int64_t n_bfaces, const int64_t *bptr,
                      const int64_t *bnodes, const int32_t *btag, HostMesh3 &out);
 // [kNCol3 * kNM3][n], h_i folded into the gradient columns
-void build_operator3(const HostMesh3 &m, const std::vector<char> &tag_is_wall, std::vector<double> &op);
+void build_operator3(const HostMesh3 &m, const std::vector<char> &tag_is_wall, std::vector<double> &op,
+                     std::vector<unsigned char> *quad_ok = nullptr);
 
 }  // namespace cgks
 

@@ -37,6 +37,8 @@ struct ParamsT {
   const T *bc_uw;              // [16][3] wall velocity (global)
   const T *bc_rho, *bc_u, *bc_p;  // [16], [16][3], [16] free stream (global)
   int flux_lo;                    // low-level flux: CGKS_FLUX_KFVS or CGKS_FLUX_LF
+  T tau_c1, tau_c2;               // numerical collision time constants of the full flux
+  T weno_eps, weno_g0;            // compact WENO epsilon (0: linear weights), linear weight of P2
 };
 
 template <typename T>
@@ -53,6 +55,10 @@ struct Ctl {
   int res_ctr, pad_;
 };
 
+__device__ __forceinline__ double dt_of(const Ctl *ctl, const unsigned long long *dt_bits, double cfl) {
+  if (ctl->dt_fixed > 0.0) return ctl->dt_fixed;
+  return cfl * __longlong_as_double(static_cast<long long>(*dt_bits));
+}
 __device__ __forceinline__ bool state_ok(double gamma, const double w[NV]) {
   const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
   return w[0] > 0.0 && p > 0.0 && isfinite(w[0]) && isfinite(p) && isfinite(w[1]) && isfinite(w[2]) &&
@@ -166,9 +172,56 @@ __device__ __forceinline__ void farfield_ghost(const ParamsT<T> &P, int tag, con
   D3::ghost_farfield(P.gamma, P.bc_rho[tag], ue, P.bc_p[tag], wl, wg);
 }
 
-// K1: compact quadratic per cell: coef[(q*5 + v)][n], 9 monomials
+// Compact WENO (conservative variables), 3-D form of the 2-D weno_combine:
+// candidates P2 (c) and the nk linear polynomials h g.(xi, eta, zeta) of the
+// mean gradients of the cell and its face neighbours (lin[k][d][v]).  beta:
+// cell mean of the squared first derivatives (centroid value squared plus
+// the quadratic form of the cell's second moments M = m2) plus the squared
+// second derivatives, each multi-index once.  w ~ gamma / (beta + eps)^2,
+// gamma_0 = g0, the rest (1 - g0)/nk; result
+// (w_0 / gamma_0)(P2 - sum gamma_k P1_k) + sum w_k P1_k.
 template <typename T>
-__device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef, const int i) {
+__device__ __forceinline__ void weno_combine3(const ParamsT<T> &P, const T M[6], int nk, const T lin[7][3][NV],
+                                              T c[kNM3][NV]) {
+  const T g0 = P.weno_g0, eps = P.weno_eps;
+  const T gk = (T(1) - g0) / T(nk);
+  // symmetric M: xx xy xz yy yz zz
+  const T Mx[3][3] = { { M[0], M[1], M[2] }, { M[1], M[3], M[4] }, { M[2], M[4], M[5] } };
+  for (int v = 0; v < NV; ++v) {
+    const T q[kNM3] = { c[0][v], c[1][v], c[2][v], c[3][v], c[4][v], c[5][v], c[6][v], c[7][v], c[8][v] };
+    const T G[3][3] = { { T(2) * q[3], q[4], q[5] }, { q[4], T(2) * q[6], q[7] }, { q[5], q[7], T(2) * q[8] } };
+    T b0 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    for (int d = 0; d < 3; ++d)
+      for (int a = 0; a < 3; ++a)
+        for (int e = 0; e < 3; ++e) b0 += G[d][a] * Mx[a][e] * G[d][e];
+    b0 += T(4) * q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + T(4) * q[6] * q[6] + q[7] * q[7] + T(4) * q[8] * q[8];
+    const T w0 = g0 / ((b0 + eps) * (b0 + eps));
+    T ws = w0, wk[7];
+    T l[3] = { T(0), T(0), T(0) };
+    for (int k = 0; k < 7; ++k) {
+      if (k >= nk) break;
+      const T b = lin[k][0][v] * lin[k][0][v] + lin[k][1][v] * lin[k][1][v] + lin[k][2][v] * lin[k][2][v];
+      wk[k] = gk / ((b + eps) * (b + eps));
+      ws += wk[k];
+      for (int d = 0; d < 3; ++d) l[d] += gk * lin[k][d][v];
+    }
+    const T iws = T(1) / ws;
+    const T f0 = w0 * iws / g0;
+    T sel[3] = { T(0), T(0), T(0) };
+    for (int k = 0; k < 7; ++k) {
+      if (k >= nk) break;
+      for (int d = 0; d < 3; ++d) sel[d] += wk[k] * iws * lin[k][d][v];
+    }
+    for (int d = 0; d < 3; ++d) c[d][v] = f0 * (q[d] - l[d]) + sel[d];
+    for (int r = 3; r < kNM3; ++r) c[r][v] = f0 * q[r];
+  }
+}
+
+// K1: compact quadratic per cell: coef[(q*5 + v)][n], 9 monomials
+template <typename T, bool WENO>
+__device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
+                                         const T *__restrict__ Wx, T *__restrict__ coef,
+                                         const unsigned char *__restrict__ wenok, const int i) {
   const int n = m.nc;
   T wi[NV], gi[3][NV];
 #pragma unroll
@@ -186,6 +239,13 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[q][v] = o0 * gi[0][v] + o1 * gi[1][v] + o2 * gi[2][v];
   }
+  T lin[WENO ? 7 : 1][3][NV];
+  int nk = 1;
+  if constexpr (WENO) {
+    const T h = T(1) / m.ih[i];
+    for (int v = 0; v < NV; ++v)
+      for (int d = 0; d < 3; ++d) lin[0][d][v] = h * gi[d][v];
+  }
   for (int s = 0; s < kMaxFace3; ++s) {
     const int fs = m.cface[s * n + i];
     if (fs == kNoFace) continue;
@@ -197,6 +257,12 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
         b0[v] = W[v * n + j] - wi[v];
 #pragma unroll
         for (int d = 0; d < 3; ++d) b[d][v] = Wx[(d * NV + v) * n + j];
+      }
+      if constexpr (WENO) {
+        const T h = T(1) / m.ih[i];
+        for (int v = 0; v < NV; ++v)
+          for (int d = 0; d < 3; ++d) lin[nk][d][v] = h * b[d][v];
+        ++nk;
       }
     } else {
       const int f = fs >= 0 ? fs : ~fs;
@@ -216,6 +282,12 @@ __device__ __forceinline__ void recon_at(const MeshT<T> &m, const ParamsT<T> &P,
       for (int v = 0; v < NV; ++v) c[q][v] += o0 * b0[v] + o1 * b[0][v] + o2 * b[1][v] + o3 * b[2][v];
     }
   }
+  if constexpr (WENO) {
+    if (wenok[i]) {
+      const T M[6] = { m.m2[i], m.m2[n + i], m.m2[2 * n + i], m.m2[3 * n + i], m.m2[4 * n + i], m.m2[5 * n + i] };
+      weno_combine3(P, M, nk, lin, c);
+    }
+  }
 #pragma unroll
   for (int q = 0; q < kNM3; ++q)
 #pragma unroll
@@ -225,7 +297,16 @@ template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_recon(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef) {
   pdl_enter();
-  for_items<SH>(m.nc, [&](int i) { recon_at(m, P, W, Wx, coef, i); });
+  for_items<SH>(m.nc, [&](int i) { recon_at<T, false>(m, P, W, Wx, coef, nullptr, i); });
+  pdl_exit();
+}
+// with the compact WENO step; wenok[i] = 1 where the stencil gave a quadratic
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_recon_weno(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ Wx, T *__restrict__ coef,
+                 const unsigned char *__restrict__ wenok) {
+  pdl_enter();
+  for_items<SH>(m.nc, [&](int i) { recon_at<T, true>(m, P, W, Wx, coef, wenok, i); });
   pdl_exit();
 }
 
@@ -253,9 +334,13 @@ __device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restri
 
 // K2: smooth GKS flux and interface state at the Gauss points of every face:
 // out[(k*5 + v)][nf], k = 0 F0, 1 F1, 2 Wc, 3 Wt, weighted sums, global frame
-template <typename T>
-__device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out, const int f) {
+template <typename T, bool FULL>
+__device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
+                                        const T *__restrict__ coef, T *__restrict__ out, const Ctl *ctl,
+                                        const unsigned long long *dt_bits, const int f) {
   const int nf = m.nf;
+  T dt = T(0);
+  if constexpr (FULL) dt = static_cast<T>(dt_of(ctl, dt_bits, static_cast<double>(P.cfl_hi)));
   const int c0 = m.fc0[f], c1 = m.fc1[f], ng = m.fng[f];
   const T ajump = m.fjump[f];
   const D3::Frame<T> F = frame_of(m, f);
@@ -322,7 +407,10 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
       D3::ghost_noslip(P.gamma, uw, wl, dl, wr, dr);
     }
     T F0[NV], F1[NV], Wc[NV], Wt[NV];
-    D3::gks_point_local(P.kc, P.mu, ajump, wl, wr, dl, dr, F0, F1, Wc, Wt);
+    if constexpr (FULL)
+      D3::gks_full_point_local(P.kc, P.mu, ajump, dt, P.tau_c1, P.tau_c2, wl, wr, dl, dr, F0, F1, Wc, Wt);
+    else
+      D3::gks_point_local(P.kc, P.mu, ajump, wl, wr, dl, dr, F0, F1, Wc, Wt);
     const T wk = m.fw[k * nf + f];
     T gq[NV];
     D3::rot_out(F, F0, gq);
@@ -347,16 +435,20 @@ template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
     k_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out) {
   pdl_enter();
-  for_items<SH>(m.nf, [&](int f) { face_at(m, P, W, coef, out, f); });
+  for_items<SH>(m.nf, [&](int f) { face_at<T, false>(m, P, W, coef, out, nullptr, nullptr, f); });
+  pdl_exit();
+}
+// the full flux of Eq. (2nd-flux): the same face loop, with the step's dt
+template <typename T, int SH>
+__global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
+    k_face_full(MeshT<T> m, ParamsT<T> P, const T *__restrict__ W, const T *__restrict__ coef, T *__restrict__ out,
+                const Ctl *ctl, const unsigned long long *dt_bits) {
+  pdl_enter();
+  for_items<SH>(m.nf, [&](int f) { face_at<T, true>(m, P, W, coef, out, ctl, dt_bits, f); });
   pdl_exit();
 }
 
 enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
-
-__device__ __forceinline__ double dt_of(const Ctl *ctl, const unsigned long long *dt_bits, double cfl) {
-  if (ctl->dt_fixed > 0.0) return ctl->dt_fixed;
-  return cfl * __longlong_as_double(static_cast<long long>(*dt_bits));
-}
 
 // K3: per cell gather of the face sums in FP64 (see the 2-D k_update):
 //   R = -sum sgn S (a0 F0A + a1 F1(A, B));  W_out = W_base + dt/|Omega| R;

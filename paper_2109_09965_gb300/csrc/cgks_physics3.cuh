@@ -191,6 +191,152 @@ __device__ __forceinline__ void gks_point_local(const KC<T> &kc, T mu_visc, T aj
   }
 }
 
+// ---------------- full flux, Eq. (2nd-flux), 3-D ----------------
+// u-moments over a half range (sgn +1: u > 0, -1: u < 0), v, w, xi full
+template <typename T>
+__device__ __forceinline__ void half_table(const Maxw<T> &g, T K, int sgn, Mom<T> &m) {
+  half_moments<T, 6>(g.U, g.i2l, d_sqrt(g.lam), d_rsqrt(g.lam) * T(dev::kInvSqrtPi), sgn, m.mu);
+  m.mv[0] = T(1); m.mv[1] = g.V;
+  m.mw[0] = T(1); m.mw[1] = g.W;
+#pragma unroll
+  for (int k = 2; k < 6; ++k) {
+    m.mv[k] = g.V * m.mv[k - 1] + T(k - 1) * g.i2l * m.mv[k - 2];
+    m.mw[k] = g.W * m.mw[k - 1] + T(k - 1) * g.i2l * m.mw[k - 2];
+  }
+  m.x2 = K * g.i2l;
+  m.x4 = K * (K + T(2)) * g.i2l * g.i2l;
+}
+
+// slopes along the three local axes from the derivatives d[k] (local
+// vectors), and A from <A + a.u> = 0; mf the full-range table of g
+template <typename T>
+__device__ __forceinline__ void maxw_slopes(const Maxw<T> &g, const Mom<T> &mf, const KC<T> &kc, const T d[3][NV],
+                                            T a[3][NV], T A[NV]) {
+  SlopeSolver<T> SS = slope_solver(g, kc);
+  T b[NV], g0[NV], g1[NV], g2[NV];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) b[v] = d[k][v] * g.ir;
+    micro_slope(SS, b, a[k]);
+  }
+  gpsi(mf, 1, 0, 0, a[0], g0);
+  gpsi(mf, 0, 1, 0, a[1], g1);
+  gpsi(mf, 0, 0, 1, a[2], g2);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) b[v] = -(g0[v] + g1[v] + g2[v]);
+  micro_slope(SS, b, A);
+}
+
+// rho-weighted flux moments Q = (<u psi>, <u a.u psi>, <u A psi>) and state
+// moments P = (<psi>, <a.u psi>, <A psi>) of one piece
+template <typename T>
+__device__ __forceinline__ void piece(T rho, const Mom<T> &m, const T a[3][NV], const T A[NV], T Q[3][NV],
+                                      T P[3][NV]) {
+  const T one[NV] = { T(1), T(0), T(0), T(0), T(0) };
+  T x[NV], y[NV], z[NV];
+  gpsi(m, 1, 0, 0, one, x);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[0][v] = rho * x[v];
+  gpsi(m, 2, 0, 0, a[0], x);
+  gpsi(m, 1, 1, 0, a[1], y);
+  gpsi(m, 1, 0, 1, a[2], z);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[1][v] = rho * (x[v] + y[v] + z[v]);
+  gpsi(m, 1, 0, 0, A, x);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[2][v] = rho * x[v];
+  gpsi(m, 0, 0, 0, one, x);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[0][v] = rho * x[v];
+  gpsi(m, 1, 0, 0, a[0], x);
+  gpsi(m, 0, 1, 0, a[1], y);
+  gpsi(m, 0, 0, 1, a[2], z);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[1][v] = rho * (x[v] + y[v] + z[v]);
+  gpsi(m, 0, 0, 0, A, x);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[2][v] = rho * x[v];
+}
+
+template <typename T>
+__device__ __forceinline__ void full_sum(T c1, T c2, T c3, T e, T te, T tau, const T X0[3][NV], const T XL[3][NV],
+                                         const T XR[3][NV], T out[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    out[v] = c1 * X0[0][v] + c2 * X0[1][v] + c3 * X0[2][v] +
+             e * ((XL[0][v] + XR[0][v]) - tau * (XL[1][v] + XR[1][v]) - tau * (XL[2][v] + XR[2][v])) -
+             te * (XL[1][v] + XR[1][v]);
+}
+
+// Full gas-kinetic flux at one Gauss point, Eq. (2nd-flux), 3-D, local
+// frame; same construction as the 2-D dev::gks_full_point_local (tau_n in
+// the exponentials, time integrals over [0, dt] and [0, dt/2] fitted to
+// F0 + t F1, the interface state by the line through t = dt/2 and dt).
+template <typename T>
+__device__ void gks_full_point_local(const KC<T> &kc, T mu_visc, T ajump, T dt, T tc1, T tc2, const T Wl[NV],
+                                     const T Wr[NV], const T dl[3][NV], const T dr[3][NV], T F0[NV], T F1[NV],
+                                     T Wc[NV], T Wt[NV]) {
+  const T K = kc.K, c2K = kc.c2K;
+  Maxw<T> gl = maxw(Wl, c2K), gr = maxw(Wr, c2K);
+  T Q0[3][NV], P0[3][NV], QL[3][NV], PL[3][NV], QR[3][NV], PR[3][NV];
+  {
+    T al[3][NV], Al[NV];
+    Mom<T> m;
+    full_moments(gl, K, m);
+    maxw_slopes(gl, m, kc, dl, al, Al);
+    half_table(gl, K, +1, m);
+    piece(gl.rho, m, al, Al, QL, PL);
+  }
+  {
+    T ar[3][NV], Ar[NV];
+    Mom<T> m;
+    full_moments(gr, K, m);
+    maxw_slopes(gr, m, kc, dr, ar, Ar);
+    half_table(gr, K, -1, m);
+    piece(gr.rho, m, ar, Ar, QR, PR);
+  }
+  T W0[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W0[v] = PL[0][v] + PR[0][v];
+  Maxw<T> gc = maxw(W0, c2K);
+  {
+    T d[3][NV], ac[3][NV], Ac[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      d[0][v] = T(0.5) * (dl[0][v] + dr[0][v]) + ajump * (Wr[v] - Wl[v]);
+      d[1][v] = T(0.5) * (dl[1][v] + dr[1][v]);
+      d[2][v] = T(0.5) * (dl[2][v] + dr[2][v]);
+    }
+    Mom<T> m;
+    full_moments(gc, K, m);
+    maxw_slopes(gc, m, kc, d, ac, Ac);
+    piece(gc.rho, m, ac, Ac, Q0, P0);
+  }
+  const T tau = mu_visc * T(2) * gc.lam * gc.ir;
+  const T pl = gl.rho * gl.i2l, pr = gr.rho * gr.i2l;
+  const T taun = tau + tc1 * dt + tc2 * dt * fabs(pl - pr) / (pl + pr);
+  T Fd[NV], Fh[NV], Wd[NV], Wh[NV];
+#pragma unroll 1
+  for (int k = 0; k < 2; ++k) {
+    const T t = k == 0 ? dt : T(0.5) * dt;
+    const T e = taun > T(0) ? dev::d_exp(-t / taun) : T(0);
+    const T om = taun > T(0) ? -dev::d_expm1(-t / taun) : T(1);
+    const T ie = taun * om, ite = taun * taun * om - taun * t * e;
+    full_sum(t - ie, ite + tau * ie - tau * t, T(0.5) * t * t - tau * t + tau * ie, ie, ite, tau, Q0, QL, QR,
+             k == 0 ? Fd : Fh);
+    full_sum(T(1) - e, (t + tau) * e - tau, t - tau + tau * e, e, t * e, tau, P0, PL, PR, k == 0 ? Wd : Wh);
+  }
+  const T idt = T(1) / dt;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    F0[v] = (T(4) * Fh[v] - Fd[v]) * idt;
+    F1[v] = T(4) * (Fd[v] - T(2) * Fh[v]) * idt * idt;
+    Wc[v] = T(2) * Wh[v] - Wd[v];
+    Wt[v] = T(2) * (Wd[v] - Wh[v]) * idt;
+  }
+}
+
 // cell primitives of the low level: rho, u, v, w, p, 1/(2 lambda),
 // sqrt(lambda), 1/sqrt(pi lambda), c, 1/rho
 constexpr int NPRIM = 10;

@@ -170,8 +170,9 @@ def test_empty_mesh_is_rejected(cg):
 
 def test_full_flux_weno_and_new_boundaries_validated_before_the_device(cg):
     """Parameter checks run before any device call: bad values and options
-    the 3-D path does not have are invalid arguments (-1); the valid
-    control reaches the device step (-4 here, without a GPU)."""
+    the 3-D path does not have (characteristic WENO, Dirichlet / outflow)
+    are invalid arguments (-1); valid ones reach the device step (-4 here,
+    without a GPU)."""
     import torch
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
@@ -188,6 +189,7 @@ def test_full_flux_weno_and_new_boundaries_validated_before_the_device(cg):
     g3 = cg.Mesh(MG.box3(2, 2, 2, cells="hex"))
     ok3 = dict(gamma=1.4, bcs=[dict(kind="slip")] * 6)
     assert status(g3, ok3) == -4
-    for extra in (dict(flux_hi="full"), dict(weno_eps=1e-2), dict(bcs=[dict(kind="outflow")] * 6),
+    for extra in (dict(weno_eps=1e-2, weno_vars="characteristic"), dict(bcs=[dict(kind="outflow")] * 6),
                   dict(bcs=[dict(kind="dirichlet", rho=1.0, p=1.0)] * 6)):
         assert status(g3, dict(ok3, **extra)) == -1, extra
+    assert status(g3, dict(ok3, flux_hi="full", weno_eps=1e-2)) == -4
