@@ -556,12 +556,7 @@ def main():
     cgks.lib()
     if args.supersonic_only:
         if rank == 0:
-            print(json.dumps({"supersonic_sphere_128k": supersonic_sphere(cgks, 3, 40, 20, 5e-3, max_cycles=600,
-                                                                          max_steps=3000)}), flush=True)
-            print(json.dumps({"supersonic_sphere_512k": supersonic_sphere(cgks, 4, 40, 20, 5e-3, max_cycles=400,
-                                                                          max_steps=1000)}), flush=True)
-            print(json.dumps({"supersonic_sphere_3M_h0_1.5e-3": supersonic_sphere(
-                cgks, 5, 60, 30, 1.5e-3, max_cycles=150, max_steps=300)}), flush=True)
+            print(json.dumps({"supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)}), flush=True)
         return
     if args.shock_only:
         if rank == 0:
@@ -980,6 +975,11 @@ def supersonic_sphere(cgks, level, n_prism, n_tet, h0, ma=1.5, re=1000.0, max_cy
         if label == "pmg" and err is None:
             cd, cl = post.force_coefficients(s.wall_loads(0), rho=1.0, U=ma, ref=math.pi / 4.0)
             res["Cd"], res["Cl"] = float(cd), float(cl)
+            # bow-shock stand-off on the upstream axis (node-mean cell centres)
+            ptr = mesh.cell_ptr
+            xc = np.add.reduceat(mesh.nodes[mesh.cell_nodes], ptr[:-1], axis=0) / np.diff(ptr)[:, None]
+            d = post.shock_standoff(xc, s.get_state()[0], R=0.5, D=1.0, mach=ma, angle_band=0.08)
+            res["shock_standoff_D"] = None if d is None else float(d)
         s.close()
         out[label] = res
     out["workload"] = (f"supersonic viscous sphere, Ma {ma}, Re {re:g}: icosphere level {level}, {n_prism} prism + "

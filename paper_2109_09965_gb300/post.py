@@ -10,6 +10,8 @@ for the wake, the cell states.  Definitions:
        from the front stagnation point to the rear over the upper surface)
   Cd, Cl = force along / across the free stream / (q_inf * reference)
 with the reference D (2-D, per unit span) or pi D^2 / 4 (3-D).
+Shock stand-off (supersonic bodies): distance from the front of the body
+to the bow shock on the upstream axis, in units of D.
 """
 from __future__ import annotations
 
@@ -95,3 +97,39 @@ def wake_length(xc: np.ndarray, W: np.ndarray, R: float, D: float, band: float |
         return None
     xe = x[k] + (x[k + 1] - x[k]) * (-v[k]) / (v[k + 1] - v[k])
     return (xe - R) / D
+
+
+def shock_standoff(xc: np.ndarray, W: np.ndarray, R: float, D: float, mach: float, gamma: float = 1.4,
+                   rho_inf: float = 1.0, band: float | None = None, angle_band: float | None = None) -> float | None:
+    """Bow-shock stand-off distance in front of a body centred at the
+    origin in a stream along +x, in units of D: on the upstream axis (cells
+    with x < -R and |y| (|z|) < band, or polar angle from the -x axis below
+    angle_band), the shock is where the density coming from upstream first
+    reaches the mean of the free-stream density and the density behind a
+    normal shock at the free-stream Mach number,
+    rho_2 / rho_1 = (gamma + 1) M^2 / ((gamma - 1) M^2 + 2)
+    (linear interpolation between the two cells around it); the stand-off
+    is the distance from there to the body's front point x = -R."""
+    x = xc[:, 0]
+    near = x < -R
+    if angle_band is not None:
+        off = np.sqrt((xc[:, 1:] ** 2).sum(1))
+        near &= np.arctan2(off, -x) < angle_band
+    else:
+        near &= np.abs(xc[:, 1]) < band
+        if xc.shape[1] == 3:
+            near &= np.abs(xc[:, 2]) < band
+    if not near.any():
+        return None
+    xs, rho = x[near], W[near, 0]
+    order = np.argsort(xs)
+    xs, rho = xs[order], rho[order]
+    m2 = mach * mach
+    level = rho_inf * 0.5 * (1.0 + (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0))
+    above = np.nonzero(rho >= level)[0]
+    if above.size == 0 or above[0] == 0:
+        return None
+    k = above[0]
+    xk = xs[k - 1] + (xs[k] - xs[k - 1]) * (level - rho[k - 1]) / (rho[k] - rho[k - 1])
+    return (-R - xk) / D
+

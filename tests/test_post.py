@@ -52,3 +52,25 @@ def test_wake_length_from_the_axis_velocity():
     W = np.stack([np.ones_like(x), u, 0 * x, 0 * x + 2.5], 1)
     L = post.wake_length(xc, W, R=0.5, D=1.0, band=0.01)
     assert abs(L - 2.2) < 0.03
+
+
+def test_shock_standoff_from_the_axis_density():
+    """A bow shock 0.3 D in front of a sphere of radius 0.5: density from 1
+    up to the normal-shock ratio at Ma 1.5 (1.862) over a thin tanh, then
+    the stagnation rise; scattered cells around the upstream axis."""
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-3.0, -0.51, 4000)
+    yz = rng.normal(size=(4000, 2)) * 0.02
+    xc = np.column_stack([x, yz])
+    ratio = 2.4 * 2.25 / (0.4 * 2.25 + 2.0)
+    xs = -0.5 - 0.3
+    rho = 1.0 + (ratio - 1.0) * 0.5 * (1.0 + np.tanh((x - xs) / 0.01)) + 0.1 * np.clip(x - xs, 0.0, None)
+    W = np.column_stack([rho, 1.5 * rho, 0 * x, 0 * x, 2.5 + 0 * x])
+    d = post.shock_standoff(xc, W, R=0.5, D=1.0, mach=1.5, angle_band=0.1)
+    assert abs(d - 0.3) < 0.01, d
+    d2 = post.shock_standoff(xc, W, R=0.5, D=1.0, mach=1.5, band=0.05)
+    assert abs(d2 - 0.3) < 0.01, d2
+    # subsonic-like field without a jump: no shock found
+    assert post.shock_standoff(xc, np.column_stack([1 + 0 * x, 0 * x, 0 * x, 0 * x, 2.5 + 0 * x]), R=0.5, D=1.0,
+                               mach=1.5, band=0.05) is None
+
