@@ -148,9 +148,24 @@ def test_no_cpu_fallback_without_gpu(cg):
 
 
 def test_default_params(cg):
+    """The C library fills the defaults; reading them back through the
+    ctypes mirror checks the mirror's field offsets."""
     P = cg.make_params({})
     assert P.gamma == 1.4 and P.cfl_lo == 1000.0 and P.n_implicit == 6 and P.n_sweeps == 2
     assert P.alpha == 0.5 and P.use_graph == 1
+    assert P.autotune == 1 and P.programmatic_launch == 1 and P.flux_lo == 0 and P.flux_hi == 0
+    assert P.weno_vars == 0 and P.tau_c1 == 0.01 and P.tau_c2 == 1.0 and P.weno_eps == 0.0 and P.weno_g0 == 0.95
+    assert P.stream is None and not P.alloc_ctx
+
+
+def test_params_mapping(cg):
+    P = cg.make_params(dict(flux_hi="full", weno_eps=1e-2, weno_vars="characteristic", tau_c1=0.2, tau_c2=3.0,
+                            flux_lo="lf", bcs=[dict(kind="dirichlet", rho=1.7, u=(2.6, -0.5), p=1.5),
+                                               dict(kind="outflow")]))
+    assert (P.flux_hi, P.weno_vars, P.flux_lo) == (cg.FLUX_FULL, cg.WENO_CHARACTERISTIC, cg.FLUX_LF)
+    assert (P.weno_eps, P.tau_c1, P.tau_c2, P.weno_g0) == (1e-2, 0.2, 3.0, 0.95)
+    assert P.n_bc == 2 and P.bc[0].kind == cg.BC_DIRICHLET and P.bc[1].kind == cg.BC_OUTFLOW
+    assert (P.bc[0].rho, P.bc[0].u[0], P.bc[0].u[1], P.bc[0].u[2], P.bc[0].p) == (1.7, 2.6, -0.5, 0.0, 1.5)
 
 
 def test_empty_mesh_is_rejected(cg):
