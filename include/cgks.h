@@ -321,8 +321,10 @@ int cgks_launches_per_call(const cgks_solver *s, int cycle);
 
 /* ---- wall loads (post-processing of a converged field) ----
  * The momentum flux through every boundary face of one tag, evaluated by
- * the high-order level at the current state: the smooth gas-kinetic flux
- * F0 of Section 2.2 (pressure and viscous stress together), averaged over
+ * the high-order level at the current state: the gas-kinetic flux F0 of
+ * Section 2.2 (the smooth flux at t = 0, or with CGKS_FLUX_FULL the
+ * constant term of its fit over one step of the current CFL time step;
+ * pressure and viscous stress together), averaged over
  * the face's Gauss points, in the global frame, per unit length (2-D) or
  * area (3-D), in the direction of the face normal out of the fluid.  On a
  * wall it is the traction the fluid exerts: the body force is
