@@ -1319,6 +1319,24 @@ void or_recon_eval(const or_solver *s, long cell, const double x[2], double val[
   recon_eval(s, s->W, cell, x, val, grad);
 }
 
+/* test hook: value and gradient at x of the polynomial the face flux uses
+ * on one side of face f (side 0: c0, 1: c1) after or_reconstruct: the
+ * cell's own, or with characteristic WENO the one limited for this face */
+void or_face_side_eval(or_solver *s, long f, int side, const double x[2], double val[NV], double grad[2 * NV]) {
+  const or_face *F = &s->m->face[f];
+  long c = side == 0 ? F->c0 : F->c1;
+  const double *p = &s->coef[c * NM * NV];
+  double q[NM * NV];
+  if (s->P.weno_eps > 0.0 && s->P.weno_char && s->quad[c]) {
+    double Wref[NV];
+    for (int v = 0; v < NV; ++v)
+      Wref[v] = F->c1 >= 0 ? 0.5 * (s->W[F->c0 * NV + v] + s->W[F->c1 * NV + v]) : s->W[F->c0 * NV + v];
+    weno_char_side(s, s->Wx, c, Wref, F->n, p, q);
+    p = q;
+  }
+  poly_eval(s, s->W, c, p, x, val, grad);
+}
+
 /* ------------------------------------------------------------------ */
 /* High-order evaluation: reconstruction + face fluxes (Sections 2.1-2.3) */
 /* Stores per face the weighted Gauss sums of F0, F1, W^c and W_t.      */

@@ -91,6 +91,7 @@ def lib():
             L.or_hi_residual.argtypes = [vp, C.c_double, _dp]
             L.or_reconstruct.argtypes = [vp]
             L.or_recon_eval.argtypes = [vp, C.c_long, _dp, _dp, _dp]
+            L.or_face_side_eval.argtypes = [vp, C.c_long, C.c_int, _dp, _dp, _dp]
             L.or_lo_residual.argtypes = [vp, _dp, _dp]
             L.or_lo_lambda.argtypes = [vp, _dp, _dp]
             L.or_lo_diag.argtypes = [vp, _dp, _dp]
@@ -271,6 +272,13 @@ class OracleSolver:
         v = np.zeros(NV); g = np.zeros((2, NV))
         lib().or_recon_eval(self._s, int(cell), _f64(x), v, g)
         return v, g
+
+    def face_side_eval(self, face: int, side: int, x):
+        """Polynomial the face flux uses on one side of a face (after
+        reconstruct()): value and gradient at x."""
+        v = np.zeros(NV); g = np.zeros(2 * NV)
+        lib().or_face_side_eval(self._s, int(face), int(side), _f64(x), v, g)
+        return v, g.reshape(2, NV)
 
     def lo_residual(self, U):
         R = np.zeros((self.nc, NV))
