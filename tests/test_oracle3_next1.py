@@ -4,7 +4,9 @@ compact WENO weights.
 * With w = 0 and z-independent data the 3-D full flux is the 2-D oracle's
   full flux (pinned by brute-force quadrature in test_oracle_fullflux).
 * Continuous data reduce it to the 3-D smooth flux for any tau_n; tau = 0
-  with tau_n -> infinity gives the 3-D KFVS flux at t = 0; antisymmetry.
+  with tau_n -> infinity gives the 3-D KFVS flux at t = 0; antisymmetry;
+  rotating the whole problem rotates the result (all three slope
+  directions, whatever the face frame).
 * WENO: epsilon -> infinity gives the linear weights; linear fields stay
   exact for any epsilon; a front's overshoot is cut.
 """
@@ -131,3 +133,27 @@ def test_weno3_linear_weight_limit_and_front(O3):
     nl = np.maximum(nl_v - hi, lo - nl_v).max()
     assert lin > 0.02, lin
     assert nl < 0.5 * lin, (nl, lin)
+
+
+def test_full_flux_rotation_invariance(O3):
+    """Rotating the whole problem (states, gradients, normal) by a random
+    rotation rotates the full flux and interface state: exercises the
+    slopes along all three local axes, which the reduction to 2-D leaves
+    out for the second tangent."""
+    rng = np.random.default_rng(45)
+    spec = dict(gamma=GAM, mu=0.01, tau_c1=0.05, tau_c2=1.0)
+    for _ in range(3):
+        Wl, Wr = rand_state(rng), rand_state(rng)
+        Gl, Gr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
+        n = rand_normal(rng)
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+
+        def rotW(W):
+            return np.concatenate([[W[0]], Q @ W[1:4], [W[4]]])
+
+        def rotG(G):
+            return Q @ np.array([rotW(G[d]) for d in range(3)])
+        a = O3.gks_full_flux_point(spec, Wl, Wr, Gl, Gr, n, 0.1, 0.01)
+        b = O3.gks_full_flux_point(spec, rotW(Wl), rotW(Wr), rotG(Gl), rotG(Gr), Q @ n, 0.1, 0.01)
+        for x, y in zip(a, b):
+            np.testing.assert_allclose(y, rotW(x), rtol=1e-10, atol=1e-11 * max(1.0, np.abs(x).max()))
