@@ -53,7 +53,10 @@
  *   [0, dt/2]; WENO: candidates P2 and the linear polynomials of the own
  *   and neighbours' mean gradients, Jiang-Shu weights gamma/(beta + eps)^2
  *   with gamma_0 = 0.95; characteristic fields of the Euler Jacobian along
- *   the face normal at the mean of the two cell averages.
+ *   the face normal at the mean of the two cell averages.  The tau_n
+ *   constants and the WENO weight form are readings of cited schemes:
+ *   parity unpinned against those papers (the tests pin the structure,
+ *   the limits and the exactness of what is implemented).
  */
 #include <math.h>
 #include <stdint.h>

@@ -38,7 +38,11 @@
  *   spread in all three directions -- T = sum_j d_j d_j^T of the scaled
  *   offsets with det(T) / (tr(T)/3)^3 >= 1e-3 -- linear otherwise (a stencil
  *   in one plane leaves the curvature across it undetermined); explicit dt
- *   with h_i = 3|Omega_i| / sum_p S_p.
+ *   with h_i = 3|Omega_i| / sum_p S_p.  Full flux (Eq. (2nd-flux)) and
+ *   compact WENO on conservative variables as in the 2-D oracle, with the
+ *   9-monomial quadratic and the three local slope directions; their tau_n
+ *   constants and weight form are readings, parity unpinned against the
+ *   cited papers.
  */
 #include <math.h>
 #include <stdint.h>
