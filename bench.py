@@ -12,8 +12,8 @@ prolongation, density residual), FP64.
                   [--scheme S1O2|S2O4] [--converge]
 
 Under torchrun every rank runs its own replica (the path has no exchange
-step on one mesh): scaling "weak", value = all ranks' cell
-updates / the slowest rank's time.
+step on one mesh): scaling "weak", value = all ranks' cell updates / the
+slowest rank's time.
 """
 from __future__ import annotations
 
@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BASELINE_METRIC = "cell-updates/s; time to 1e-8 residual drop vs explicit S2O4; p99 solve latency"
+METRIC = "cell-updates/s; time to 1e-8 residual drop vs explicit S2O4; p99 solve latency"
 GAMMA = 1.4
 MA = 0.38
 L2_BYTES = 129 * 1024 * 1024
@@ -192,7 +192,7 @@ def run_reference(args):
     s.pmg_cycles(steps)
     el = time.perf_counter() - t
     value = mesh.n_cells * steps / el
-    line = {"impl": "reference", "metric": BASELINE_METRIC, "value": value, "unit": "cell-updates/s",
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
             "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(mesh, args),
@@ -580,7 +580,7 @@ def main():
                                      "inversion and residual norms; same workload and step"}
     if rank != 0:
         return
-    line = {"metric": BASELINE_METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
