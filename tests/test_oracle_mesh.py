@@ -147,3 +147,21 @@ def test_named_workload_sizes():
     t = np.diff(r)
     np.testing.assert_allclose(t[1:32] / t[:31], 1.08, rtol=1e-12)
     assert abs(t[32] / t[31] - 1.08) < 1e-12
+
+
+def test_shock_reflection_case_layout():
+    """Section 4's shock reflection grid: 120 x 30 quads on [0,4] x [0,1],
+    tags wall (bottom), outflow (right), Dirichlet top and left; the
+    initial state is the left state everywhere."""
+    from paper_2109_09965_gb300 import meshgen as MG
+    mesh, spec, W0 = MG.shock_reflection_case()
+    assert mesh.n_cells == 3600 and mesh.n_bfaces == 300
+    counts = np.bincount(mesh.bface_tag, minlength=4)
+    assert list(counts) == [120, 30, 120, 30]
+    kinds = [b["kind"] for b in spec["bcs"]]
+    assert kinds == ["slip", "outflow", "dirichlet", "dirichlet"]
+    assert spec["flux_hi"] == "full" and spec["weno_vars"] == "characteristic" and spec["mu"] == 0.0
+    rho, u, v, p = MG.SR_LEFT
+    np.testing.assert_allclose(W0[0], [rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * u * u])
+    assert np.all(W0 == W0[0])
+    assert mesh.nodes[:, 0].min() == 0.0 and mesh.nodes[:, 0].max() == 4.0 and mesh.nodes[:, 1].max() == 1.0
