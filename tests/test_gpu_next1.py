@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2109_09965_gb300 import meshgen as MG
-from tests.test_gpu_parity import GAM, TOL, case, check, pair, rel
+from tests.test_gpu_parity import case, check, pair, rel
 
 pytestmark = pytest.mark.gpu
 

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2109_09965_gb300 import meshgen as MG
-from tests.test_oracle3 import GAM, O3, cons3, rand_normal, rand_state  # noqa: F401  (fixture)
+from tests.test_oracle3 import GAM, O3, rand_normal, rand_state  # noqa: F401  (O3 is a fixture)
 
 
 def lift(W):
