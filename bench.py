@@ -38,6 +38,42 @@ MA = 0.38
 L2_BYTES = 129 * 1024 * 1024
 
 
+def finite(obj):
+    """The object with every non-finite float (a diverged run's NaN or inf)
+    replaced by None, so that the printed line is strict JSON."""
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [finite(v) for v in obj]
+    if isinstance(obj, np.generic):
+        return finite(obj.item())
+    return obj
+
+
+def emit(obj):
+    """Print one strict-JSON line (no NaN / Infinity tokens)."""
+    print(json.dumps(finite(obj), allow_nan=False), flush=True)
+
+
+def host_cpu():
+    """CPU model and online core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def workload():
     from paper_2109_09965_gb300 import meshgen
     mesh = meshgen.cylinder(256, 32, 96)
@@ -164,9 +200,9 @@ def cpu_baseline(mesh, spec, W0, target_s=12.0):
     t = time.perf_counter()
     s.pmg_cycles(cycles)
     dt = time.perf_counter() - t
-    return {"value": mesh.n_cells * cycles / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{cycles} V-cycles of the {mesh.n_cells}-cell cylinder, serial FP64 oracle, "
-                      f"{dt:.2f} s"}
+    return dict({"value": mesh.n_cells * cycles / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                 "sample": f"{cycles} V-cycles of the {mesh.n_cells}-cell cylinder, serial FP64 oracle, "
+                           f"{dt:.2f} s"}, **host_cpu())
 
 
 def run_reference(args):
@@ -196,10 +232,11 @@ def run_reference(args):
             "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(mesh, args),
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{steps} V-cycles of the {mesh.n_cells}-cell cylinder (serial FP64 oracle)"},
+            "cpu_baseline": dict({"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"{steps} V-cycles of the {mesh.n_cells}-cell cylinder (serial FP64 "
+                                            "oracle)"}, **host_cpu()),
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def config_block(mesh, args):
@@ -213,7 +250,7 @@ def config_block(mesh, args):
 
 
 def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm, hbm_src, with_e2e,
-            steps=None, work_model=None):
+            steps=None, work_model=None, workload_name="cylinder57k"):
     """Device-timed K V-cycles (per-step events, L2 flushed between steps),
     a per-kernel timing pass, and optionally the end-to-end C-ABI run."""
     import torch
@@ -267,7 +304,7 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     solver.set_timing(False)
     total_k = sum(v[0] for v in kt.values())
     wm = (work_model or globals()["work_model"])(mesh, gm, sp, precision)
-    roof, per_gbs = roofline(kt, wm, precision, hbm, hbm_src, args.steps)
+    roof, per_gbs = roofline(kt, wm, precision, hbm, hbm_src, args.steps, workload_name)
     kernels = {k: dict({"ms_per_step": v[0] / args.steps, "share": v[0] / total_k, "launches": v[1]},
                        **per_gbs.get(k, {}))
                for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0]) if v[1] > 0}
@@ -512,7 +549,7 @@ def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_p
     out = {"workload": note, "n_cells": mesh.n_cells, "n_faces": gm.n_faces, "mesh_prep_s": prep}
     for prec in ("fp64", "mixed"):
         m = measure(cgks, gm, mesh, spec, W0, args, prec, world, local, flush, hbm, hbm_src, with_e2e=False,
-                    steps=steps, work_model=work_model3)
+                    steps=steps, work_model=work_model3, workload_name=name)
         out[prec] = {"value": m["value"], "unit": "cell-updates/s", "ms_per_step": m["ms"] / steps, "steps": steps,
                      "roofline": m["roof"], "kernels": m["kernels"], "gpu_launches": m["launches"],
                      "residual_last": m["res"], "clocks": m["clocks"], "tuning": m["tuning"], "split": m["split"]}
@@ -556,12 +593,12 @@ def main():
     cgks.lib()
     if args.supersonic_only:
         if rank == 0:
-            print(json.dumps({"supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)}), flush=True)
+            emit({"block": "supersonic_sphere", "supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)})
         return
     if args.shock_only:
         if rank == 0:
-            print(json.dumps({"shock_reflection": shock_reflection(
-                cgks, weno_vars=("characteristic", "conservative"))}), flush=True)
+            emit({"block": "shock_reflection", "shock_reflection": shock_reflection(
+                cgks, weno_vars=("characteristic", "conservative"))})
         return
     mesh, spec, W0 = workload()
     spec = dict(spec, time_scheme=args.scheme)
@@ -580,17 +617,17 @@ def main():
                                      "inversion and residual norms; same workload and step"}
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic", "config": config_block(mesh, args), "e2e": m["e2e"],
-            "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roof"],
-            "kernels": m["kernels"], "residual_last": m["res"], "tuning": m["tuning"], "split": m["split"]}
-    if variants:
-        line["variants"] = variants
+    # extended blocks first, one strict-JSON line each; the compact headline
+    # line is printed last
+    emit({"block": "headline_detail", "kernels": m["kernels"], "tuning": m["tuning"], "split": m["split"],
+          "residual_last": m["res"], "variants": variants})
+    legs = {}
+    if world > 1:
+        # replicas: only the headline runs on every rank; the side blocks
+        # (3-D, serving, convergence) are single-GPU runs
+        args.no_3d, args.serving, args.no_convergence, args.converge = True, "none", True, False
     if not args.no_3d:
-        line["workloads_3d"] = {
+        w3 = {
             "sphere512k": sphere_bench(
                 cgks, args, world, local, flush, hbm, hbm_src, "sphere512k", 4, 40, 20, 5e-3, 0.2, 118, 30,
                 "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism layers "
@@ -602,14 +639,18 @@ def main():
                 "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
                 "(throughput of the smooth path; the Ma 1.5 case with the full flux and WENO is the supersonic_sphere entry)"),
         }
-    if args.serving == "sample":
-        line["serving"] = serving(cgks, 24, 2000, 20000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
-    elif args.serving == "full":
-        line["serving"] = serving(cgks, 256, 2000, 260000, 60.0, 1e-5, 2000, 6000, 64, "mixed")
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(mesh, spec, W0)
+        emit({"block": "workloads_3d", "workloads_3d": w3})
+        legs["sphere512k"] = {k: w3["sphere512k"][k]["value"] for k in ("fp64", "mixed")}
+        legs["sphere3M"] = {k: w3["sphere3M"][k]["value"] for k in ("fp64", "mixed")}
+    if args.serving != "none":
+        full = args.serving == "full"
+        sv = serving(cgks, 256 if full else 24, 2000, 260000 if full else 20000, 60.0, 1e-5, 2000, 6000, 64,
+                     "mixed")
+        emit({"block": "serving", "serving": sv})
+        legs["serving"] = {k: sv[k] for k in ("requests", "solves_per_hour", "p50_s", "p99_s", "states")}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(mesh, spec, W0)
     if args.converge:
-        line["convergence_57k"] = converge(cgks, mesh, spec, W0)
+        emit({"block": "convergence_57k", "convergence_57k": converge(cgks, mesh, spec, W0)})
     if not args.no_convergence:
         # time to a 1e-8 drop on a cylinder small enough for both methods to
         # get there within the bench: 64 x (8 quad + 24 triangle layers)
@@ -623,10 +664,15 @@ def main():
         conv["workload"] = (f"inviscid cylinder Ma {MA}, AoA 0, hybrid O-mesh 64 x (8 quad + 24 split-triangle "
                             f"layers) to 20 radii: {cm.n_cells} cells, FP64; Res drop 1e-8 relative to the first "
                             "iteration; p-multigrid V-cycles vs explicit S2O4 steps, same GPU")
-        line["convergence"] = conv
-        line["validation_re40"] = validation_re40(cgks)
+        emit({"block": "convergence", "convergence": conv})
+        legs["time_to_1e-8"] = {"n_cells": cm.n_cells,
+                                "pmg_s": conv["pmg"]["wall_s_to_drop"],
+                                "explicit_S2O4_s": conv["explicit_S2O4"]["wall_s_to_drop"],
+                                "speedup": conv.get("speedup"),
+                                "speedup_lower_bound": conv.get("speedup_lower_bound")}
+        emit({"block": "validation_re40", "validation_re40": validation_re40(cgks)})
         if not args.no_shock:
-            line["shock_reflection"] = shock_reflection(cgks)
+            emit({"block": "shock_reflection", "shock_reflection": shock_reflection(cgks)})
         if not args.no_3d:
             lvl = 4 if args.converge3d_full else 3
             c3 = converge3d(cgks, lvl, 40, 20, 5e-3)
@@ -634,14 +680,21 @@ def main():
                               f"layers (first 5e-3 D, growth 1.1) and 20 split-tet layers to 20 D: {c3['n_cells']} "
                               "cells; p-multigrid to a 1e-8 drop of Res relative to the first cycle (FP64), then "
                               "the mixed path over the same cycles")
-            line["convergence_3d"] = c3
-            # the config-4 construction (level 5, 60 + 30 layers) needs a first layer
-            # of 1.5e-3 D or less, where the V-cycle diverges (thin-layer reading);
-            # the level-4 sphere with the 5e-3 D first layer converges
-            line["supersonic_sphere"] = supersonic_sphere(cgks, 4, 40, 20, 5e-3)
-    print(json.dumps(line), flush=True)
-
-
+            emit({"block": "convergence_3d", "convergence_3d": c3})
+            emit({"block": "supersonic_sphere", "supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)})
+    line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic", "config": config_block(mesh, args), "e2e": m["e2e"],
+            "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roof"]}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if "mixed" in variants:
+        legs["mixed"] = {k: variants["mixed"][k] for k in ("value", "ms_per_step")}
+        legs["mixed"]["roofline_frac"] = variants["mixed"]["roofline"]["frac"]
+    line["legs"] = legs
+    emit(line)
 
 
 def topology(mesh, gm):
@@ -734,13 +787,15 @@ def work_model(mesh, gm, spec, precision):
             "sweep_launches": ni * len(seq), "face_flops": ev * F * 2 * FLOPS_PER_GP2}
 
 
-# DRAM bytes per k_sweep launch (read + write) from one ncu capture of this
-# workload, averaged over the colours of a V-cycle (6 big + 2 small colour
-# launches per implicit step); profiles/k_sweep_cylinder57k.md.
-SWEEP_TRAFFIC_PER_LAUNCH = {"fp64": 7.44e6, "mixed": 3.03e6}
+# DRAM bytes (read + write) per launch of a workload's dominant kernel from
+# one ncu capture of that workload and kernel (--clock-control none, a few
+# launches, averaged over the colours of a V-cycle for k_sweep).  An entry
+# is removed when its kernel changes; a workload with no entry reports
+# traffic null.
+NCU_TRAFFIC = {}
 
 
-def roofline(kt, wm, precision, hbm, hbm_src, steps):
+def roofline(kt, wm, precision, hbm, hbm_src, steps, workload_name="cylinder57k"):
     """Roofline entry of the dominant kernel and achieved GB/s of all."""
     per = {}
     for k, (ms, cnt) in kt.items():
@@ -757,25 +812,25 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps):
     if top == "k_face" and precision == "fp64" and "face_flops" in wm:
         ach = wm["face_flops"] / s_top / 1e12
         return ({"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((workload_name, top, precision)),
                  "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
                                 "1.197 TFLOP/s)"}, per)
     if top == "k_lo_solve" and precision == "fp64" and "lo_flops" in wm:
         ach = wm["lo_flops"] / s_top / 1e12
         return ({"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((workload_name, top, precision)),
                  "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
                                 "1.197 TFLOP/s)"}, per)
     if top == "k_sweep" and precision == "fp64":
         ach = wm["sweep_flops"] / s_top / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_PER_LAUNCH.get(precision),
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((workload_name, top, precision)),
                 "peak_source": "nominal FP64 rate from the recipe's unit counts and clocks (measured FMA loop: "
                                "1.197 TFLOP/s)"}
     else:
         ach = wm["bytes"].get(top, 0.0) / s_top / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": wm.get("sweep_traffic", SWEEP_TRAFFIC_PER_LAUNCH.get(precision)) if top == "k_sweep" else None,
+                "traffic": NCU_TRAFFIC.get((workload_name, top, precision)),
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     return roof, per
 

@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -80,3 +81,28 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=240)
     assert r.returncode == 0 and not [l for l in r.stdout.splitlines() if l.startswith("{")], r.stdout
+
+
+def test_bench_lines_are_strict_json_with_a_diverged_run():
+    """A diverged sub-run (NaN residuals, an empty history) still prints a
+    line that strict JSON parsers read: non-finite floats become null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"value": 1.5e9, "supersonic": {"res_first": float("nan"), "history": [float("nan")],
+                                            "drop": float("inf"), "n": np.int64(3), "x": np.float64(-np.inf)}}
+    text = json.dumps(bench.finite(line), allow_nan=False)
+
+    def refuse(tok):
+        raise ValueError(tok)
+    d = json.loads(text, parse_constant=refuse)
+    assert d["value"] == 1.5e9 and d["supersonic"]["res_first"] is None
+    assert d["supersonic"]["history"] == [None] and d["supersonic"]["drop"] is None
+    assert d["supersonic"]["n"] == 3 and d["supersonic"]["x"] is None
+
+
+def test_host_cpu_names_model_and_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.host_cpu()
+    assert isinstance(h["cpu_model"], str) and h["cpu_model"]
+    assert h["nproc"] == os.cpu_count()
