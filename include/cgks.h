@@ -314,6 +314,15 @@ int cgks_server_destroy(cgks_server *srv);
 int cgks_set_timing(cgks_solver *s, int on);
 int cgks_get_timing(cgks_solver *s, int max, const char **names, double *total_ms, int64_t *count);
 int cgks_reset_timing(cgks_solver *s);
+/* Polls a grid-barrier wait of the persistent low-order launch
+ * (low_order_fused, 2-D) makes before it gives up.  Past the limit the
+ * launch ends early, every slot's status word gets the timeout bit, and the
+ * call that ran it returns CGKS_ETIMEOUT; cgks_set_state clears the status
+ * and the next launch starts from a cleared barrier.  polls = 0 restores
+ * the default of 4,194,304 polls (seconds, far beyond any phase); a small
+ * value makes the wait run out on purpose (tests of the timeout path).
+ * CGKS_EINVAL for polls < 0 or a 3-D solver. */
+int cgks_set_barrier_spin_limit(cgks_solver *s, int64_t polls);
 /* Kernels launched by this solver so far, and kernels per V-cycle (cycle=1)
  * or per explicit step (cycle=0). */
 int64_t cgks_launch_count(const cgks_solver *s);
@@ -382,22 +391,27 @@ int cgks_server_get_tuning(cgks_server *srv, cgks_tuning *t);
  * keep cudaMalloc off the request path (it can block, synchronise the
  * device or fail under the budget), and host frameworks that own all device
  * memory and forbid libraries from allocating.  This entry point computes
- * the density residual Res = sum|rho_new - rho_old| / sum rho_old (the
- * monitor of Section 4) of two device states without allocating anything.
- *   W_new_dev, W_old_dev  device arrays [n_cells*4], the ABI state layout
- *                         (only component 0, rho, is read)
+ * the density residual Res = sum|rho_new - rho_old| / sum rho_old of two
+ * device states without allocating anything.
+ * 2-D states only: the states are read with the 2-D stride of 4 doubles per
+ * cell; a 3-D state ([n_cells*5]) gives a wrong number.
+ *   W_new_dev, W_old_dev  device arrays [n_cells*4], the 2-D ABI state
+ *                         layout (only component 0, rho, is read)
  *   n_cells               1 .. 1,048,576; larger returns CGKS_EINVAL
  *   res_dev               device pointer receiving one double
  *   stream                cudaStream_t the two kernels run on (NULL = default)
  * Its scratch is a fixed 64 KiB __device__ array inside libcgks that every
  * GPU loading the library holds until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress
- * with the device current) and caches it; make that first call before any
- * stream capture.  All calls share the one array and it keeps the last
- * call's partial sums; every call overwrites the slots it reads, so nothing
- * needs clearing, but calls that overlap on the GPU (different streams,
- * or different host threads) race on it and must be serialised by the
- * caller.  Returns CGKS_OK, CGKS_EINVAL or CGKS_ECUDA. */
+ * in a CUDA context looks up that array's address in the context
+ * (cudaGetSymbolAddress) and caches it per context handle; make that first
+ * call before any stream capture.  (A context destroyed and a new one
+ * created under the same handle would reuse a stale address: call from
+ * contexts that live as long as the calls do.)  All calls share the one
+ * array and it keeps the last call's partial sums; every call overwrites
+ * the slots it reads, so nothing needs clearing, but calls that overlap on
+ * the GPU (different streams, contexts or host threads) race on it and
+ * must be serialised by the caller.  Returns CGKS_OK, CGKS_EINVAL or
+ * CGKS_ECUDA. */
 int cgks_density_residual_noalloc(const double *W_new_dev, const double *W_old_dev, int64_t n_cells,
                                   double *res_dev, void *stream);
 

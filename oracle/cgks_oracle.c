@@ -32,7 +32,7 @@
  *   point relaxation ......................... Section 3, Algorithm 1
  *   density residual Res ..................... Section 4 (Res definition)
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   K in 2-D = (4-2*gamma)/(gamma-1); 2-point Gauss-Legendre per edge;
  *   compact least-squares quadratic (cell means + cell-mean gradients of the
  *   face neighbours, own cell-mean gradient); W^c from half-range moments

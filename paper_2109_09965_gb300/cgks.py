@@ -26,6 +26,7 @@ FLUX_KFVS, FLUX_LF = 0, 1
 FLUX_SMOOTH, FLUX_FULL = 0, 1
 WENO_CONSERVATIVE, WENO_CHARACTERISTIC = 0, 1
 MAX_BC = 16
+OK, EINVAL, ENOMEM, EMESH, ECUDA, EDIVERGED, ETIMEOUT, EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "mesh rejected", -4: "CUDA error",
           -5: "diverged", -6: "timeout", -7: "memory budget exceeded"}
@@ -114,6 +115,7 @@ SIGNATURES = {
     "cgks_tune_shape": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "cgks_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(CgksTuning)]),
     "cgks_set_tuning": (C.c_int, [C.c_void_p, _i32p]),
+    "cgks_set_barrier_spin_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "cgks_density_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
@@ -383,6 +385,11 @@ class Solver:
         if a.shape != (TUNE_KERNELS,):
             raise ValueError("one shape per tunable kernel")
         _check(lib().cgks_set_tuning(self._h, a), "cgks_set_tuning")
+
+    def set_barrier_spin_limit(self, polls: int):
+        """Polls per grid-barrier wait of the persistent low-order launch
+        before it gives up (0: the default)."""
+        _check(lib().cgks_set_barrier_spin_limit(self._h, int(polls)), "cgks_set_barrier_spin_limit")
 
 
 def tune_shape(shape: int):

@@ -50,6 +50,7 @@ struct Shared {
   int autotune = 1, pdl = 1, flux_lo = CGKS_FLUX_KFVS, flux_hi = CGKS_FLUX_SMOOTH;
   double tau_c1 = 0.01, tau_c2 = 1.0, weno_eps = 0.0, weno_g0 = 0.95;
   int weno_vars = CGKS_WENO_CONSERVATIVE;
+  long long spin_limit = 0;      // grid-barrier polls of the persistent launch (0: kSpinLimit)
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -258,7 +259,11 @@ void enqueue_lo_fused(Batch *b) {
   a.Wp0 = b->Wn; a.Rp0 = b->Rp0; a.U = b->U; a.Src = b->Src;
   a.dU = B.dU; a.prim = B.prim; a.Um = mirror<TF>(B.U); a.Flo = B.Flo; a.lam = B.lam; a.E0 = B.E0; a.E1 = B.E1;
   a.Rk = B.Rk; a.invD = B.invD; a.lamS = B.lamS;
-  a.gb = b->gb; a.err = b->status;
+  a.gb = b->gb; a.err = b->status; a.n_err = static_cast<int>(b->S);
+  a.spin_limit = b->sh.spin_limit > 0 ? b->sh.spin_limit : kSpinLimit;
+  // a launch that timed out leaves the barrier's arrival count behind: start
+  // every launch from a cleared barrier (a memset node when captured)
+  cudaMemsetAsync(b->gb, 0, sizeof(GridBarrier), b->stream);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->lo_grid);
   cfg.blockDim = dim3(kPersistBlock);
@@ -1479,6 +1484,13 @@ int cgks_get_tuning(cgks_solver *s, cgks_tuning *t) {
   if (!s || !t) return CGKS_EINVAL;
   if (s->s3) return s3_tuner(s->s3)->report(t), CGKS_OK;
   s->b->tune.report(t);
+  return CGKS_OK;
+}
+
+int cgks_set_barrier_spin_limit(cgks_solver *s, int64_t polls) {
+  if (!s || polls < 0 || s->s3) return CGKS_EINVAL;
+  s->b->sh.spin_limit = polls;
+  drop_graphs(s->b);   // the limit is a launch argument baked into captured graphs
   return CGKS_OK;
 }
 

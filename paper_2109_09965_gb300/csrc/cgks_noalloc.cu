@@ -8,8 +8,10 @@
 //
 // In host code the name g_partials is only a host-side stand-in for the
 // device array: passing it to a kernel would fault or silently read the
-// wrong memory.  The device address is obtained once per device with
-// cudaGetSymbolAddress (with that device current) and cached.
+// wrong memory.  The device address is obtained with cudaGetSymbolAddress
+// while the calling context is current and cached per CUDA context (a
+// device address is valid only in the context it was obtained in, and a
+// process may drive one device through several contexts).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -22,13 +24,31 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kMaxBlocks = 4096;                       // scratch capacity in blocks
 constexpr int64_t kMaxCells = int64_t(kMaxBlocks) * kBlock;
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 // [2 * kMaxBlocks] partial sums (numerator, denominator) of one call
 __device__ __align__(256) double g_partials[2 * kMaxBlocks];
 
+// cache of the array's address per CUDA context: (context handle, address)
 std::mutex g_mu;
-double *g_scratch[kMaxDevices] = { nullptr };
+void *g_ctx[kMaxContexts] = { nullptr };
+double *g_scratch[kMaxContexts] = { nullptr };
+int g_n_ctx = 0;
+
+// the driver's cuCtxGetCurrent, looked up through the runtime (no link
+// against libcuda); the context handle is the cache key
+using CtxGetCurrentFn = int (*)(void **);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
 
 __device__ __forceinline__ void warp_block_sum2(double a, double b, double *dst) {
   __shared__ double sa[kBlock / 32], sb[kBlock / 32];
@@ -75,16 +95,31 @@ __global__ void __launch_bounds__(kBlock) k_res_total(const double *__restrict__
   if (threadIdx.x == 0) *res = tot[0] / tot[1];
 }
 
-int scratch_for_current_device(double **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CGKS_ECUDA;
+// Device address of g_partials in the calling thread's current context.
+// The first call in a context makes the runtime initialise that context
+// (if it is not yet) and looks the address up; later calls read the cache.
+// Without a context handle, or once the cache is full, the address is
+// looked up on every call instead (still no allocation).
+int scratch_for_current_context(double **out) {
+  void *ctx = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (get && get(&ctx) != 0) ctx = nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return CGKS_ECUDA;
-    g_scratch[dev] = static_cast<double *>(p);
+  if (ctx) {
+    for (int k = 0; k < g_n_ctx; ++k)
+      if (g_ctx[k] == ctx) { *out = g_scratch[k]; return CGKS_OK; }
   }
-  *out = g_scratch[dev];
+  // with no context current yet this also makes the device's primary
+  // context current (the runtime's lazy initialisation)
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return CGKS_ECUDA;
+  if (!ctx && get && get(&ctx) != 0) ctx = nullptr;
+  if (ctx && g_n_ctx < kMaxContexts) {
+    g_ctx[g_n_ctx] = ctx;
+    g_scratch[g_n_ctx] = static_cast<double *>(p);
+    ++g_n_ctx;
+  }
+  *out = static_cast<double *>(p);
   return CGKS_OK;
 }
 
@@ -95,7 +130,7 @@ extern "C" int cgks_density_residual_noalloc(const double *W_new_dev, const doub
   if (!W_new_dev || !W_old_dev || !res_dev || n_cells <= 0) return CGKS_EINVAL;
   if (n_cells > kMaxCells) return CGKS_EINVAL;
   double *scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
+  int rc = scratch_for_current_context(&scratch);
   if (rc != CGKS_OK) return rc;
   const int nblocks = static_cast<int>((n_cells + kBlock - 1) / kBlock);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -15,9 +15,12 @@
 // launches and the graph already hides their launch gaps, so the library
 // uses it only when asked (cgks_params.low_order_fused).
 //
-// The barrier spins with a bound: past kSpinLimit polls a block records
-// kBarrierTimeout in the batch's status word and leaves; every other block
-// then times out at its next barrier, so the launch always ends.
+// The barrier spins with a bound: past the launch's spin limit (kSpinLimit
+// unless the caller sets one) a block records kBarrierTimeout in the status
+// word of every slot of the batch and leaves; every other block then times
+// out at its next barrier, so the launch always ends.  The host clears the
+// barrier before every launch, so a launch that timed out leaves nothing
+// behind for the next one.
 #pragma once
 
 #include "cgks_kernels.cuh"
@@ -42,8 +45,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-// all blocks of the grid; returns false after a timeout (status bit set)
-__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, int *err) {
+// all blocks of the grid; returns false after a timeout (status bit set in
+// each of the n_err status words)
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long spin_limit, int *err, int n_err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -58,7 +62,11 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb, int *err) {
     } else {
       long long it = 0;
       while (ld_acquire(&gb->gen) == my_gen) {
-        if (++it > kSpinLimit) { atomicOr(err, kBadState | kBarrierTimeout); ok = 0; break; }
+        if (++it > spin_limit) {
+          for (int k = 0; k < n_err; ++k) atomicOr(&err[k], kBadState | kBarrierTimeout);
+          ok = 0;
+          break;
+        }
         __nanosleep(32);
       }
     }
@@ -89,7 +97,9 @@ struct LoArgs {
   double *U, *Src;
   TF *dU, *prim, *Um, *Flo, *lam, *E0, *E1, *Rk, *invD, *lamS;
   GridBarrier *gb;
-  int *err;
+  long long spin_limit;              // polls per barrier wait before giving up
+  int *err;                          // [n_err] status words of the batch's slots
+  int n_err;
 };
 
 template <typename TF>
@@ -261,11 +271,11 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_lo_solve(const __grid_cons
   const int grp = tid >> 2, ngrp = nth >> 2;
   for (int k = 0; k < a.n_implicit; ++k) {
     for (int i = tid; i < n; i += nth) lo_cell_at(a, i, k == 0);
-    if (!grid_barrier(a.gb, a.err)) return;
+    if (!grid_barrier(a.gb, a.spin_limit, a.err, a.n_err)) return;
     for (int f = tid; f < nf; f += nth) lo_face_at(a, f);
-    if (!grid_barrier(a.gb, a.err)) return;
+    if (!grid_barrier(a.gb, a.spin_limit, a.err, a.n_err)) return;
     for (int i = tid; i < n; i += nth) lo_rhs_at(a, i, k == 0);
-    if (!grid_barrier(a.gb, a.err)) return;
+    if (!grid_barrier(a.gb, a.spin_limit, a.err, a.n_err)) return;
     for (int q = 0; q < a.n_seq; ++q) {
       const int c = a.seq[q];
       const int total = a.cr.rpre[a.cr.rstart[c + 1] + c];
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_lo_solve(const __grid_cons
         const int i = g < total ? colour_cell(a.cr, c, g) : -1;
         sweep_at(a, i, lane4);
       }
-      if (!grid_barrier(a.gb, a.err)) return;
+      if (!grid_barrier(a.gb, a.spin_limit, a.err, a.n_err)) return;
     }
   }
   if (a.n_implicit > 0)

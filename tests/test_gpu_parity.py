@@ -253,6 +253,37 @@ def test_fused_low_order_equals_per_phase_launches(name, precision):
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=100 * tol)
 
 
+def test_fused_barrier_timeout_reports_status_and_recovers():
+    """A grid-barrier wait of the persistent low-order launch that runs out
+    (a spin limit of one poll, so the first blocks to arrive give up) ends
+    the launch early and the call returns CGKS_ETIMEOUT, not a hang.  After
+    cgks_set_state and the default limit, the same solver runs V-cycles
+    equal to the per-phase launches: the barrier left half-counted by the
+    timed-out launch is cleared before the next one."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2109_09965_gb300 import cgks
+    mesh, spec, (W, Wx) = case("cylinder_viscous")
+    ref = cgks.Solver(cgks.Mesh(mesh), dict(spec, low_order_fused=0))
+    ref.set_state(W, Wx)
+    h_ref = ref.pmg_cycle(3)
+    W_ref = ref.get_state()[0]
+    s = cgks.Solver(cgks.Mesh(mesh), dict(spec, low_order_fused=1))
+    s.set_state(W, Wx)
+    s.set_barrier_spin_limit(1)
+    with pytest.raises(cgks.CgksError) as e:
+        s.pmg_cycle(1)
+    assert e.value.status == cgks.ETIMEOUT
+    s.set_barrier_spin_limit(0)
+    s.set_state(W, Wx)
+    h = s.pmg_cycle(3)
+    assert rel(s.get_state()[0], W_ref) < 1e-13
+    np.testing.assert_allclose(h, h_ref, rtol=1e-11)
+    with pytest.raises(cgks.CgksError):
+        s.set_barrier_spin_limit(-1)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["cavity8", "mixed_slip_farfield", "cylinder_viscous"])
 def test_lf_low_level_matches_oracle(libs, name, precision):
