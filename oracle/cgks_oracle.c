@@ -91,8 +91,10 @@ typedef struct {
   int n_bc;
   int flux_lo;                /* low-level flux: 0 = KFVS, 1 = Lax-Friedrichs */
   int sweep_order;            /* 0 = colour classes, 1 = element index (serial),
-                                 2 = index partitions with lagged exchange */
-  int n_parts;                /* partitions of sweep_order 2 (the paper's threads) */
+                                 2 = index partitions with lagged exchange,
+                                 3 = RCM partitions, colour classes inside,
+                                     lagged exchange per sweep */
+  int n_parts;                /* partitions of sweep_order 2 and 3 */
   int flux_hi;                /* high-level flux: 0 = smooth, Eq. (2nd-smooth-flux);
                                  1 = full, Eq. (2nd-flux) */
   int pad_;
@@ -1525,6 +1527,35 @@ void or_hi_residual(or_solver *s, double dt, double *R) {
   net_flux(s, s->F0, s->F1, 1.0, 0.5 * dt, R);
 }
 
+/* Wall loads (the surface quantities of Section 4's cylinder tables and
+ * sphere drag): for every boundary face carrying tag, in the oracle's face
+ * order, the face centre (mean of its two Gauss points), the unit normal
+ * out of the fluid, the length, and the momentum part of the face's
+ * high-order flux F0 at the current state (the weighted Gauss-point sum of
+ * Eq. (2nd-smooth-flux), or of Eq. (2nd-flux) over a step dt; global
+ * frame), which on a wall is the traction the fluid exerts.  Arrays hold
+ * max_faces entries; returns the number of faces with the tag. */
+long or_wall_loads(or_solver *s, int tag, double dt, long max_faces, double *x, double *n, double *S,
+                   double *traction) {
+  const or_mesh *m = s->m;
+  hi_eval(s, s->W, s->Wx, dt);
+  long k = 0;
+  for (long f = 0; f < m->nf; ++f) {
+    const or_face *F = &m->face[f];
+    if (F->c1 >= 0 || F->tag != tag) continue;
+    if (k < max_faces) {
+      for (int d = 0; d < 2; ++d) {
+        x[2 * k + d] = 0.5 * (F->xg[0][d] + F->xg[1][d]);
+        n[2 * k + d] = F->n[d];
+        traction[2 * k + d] = s->F0[f * NV + 1 + d];
+      }
+      S[k] = F->S;
+    }
+    ++k;
+  }
+  return k;
+}
+
 /* ------------------------------------------------------------------ */
 /* Low-order level (Section 3): first-order KFVS residual, L-F split,  */
 /* local time step, point relaxation.                                   */
@@ -1636,13 +1667,19 @@ static void lo_diag(const or_solver *s, const double *lam, double *D) {
   }
 }
 
-/* Algorithm 1, n_sweeps x (forward pass, backward pass), in one of three
+/* Algorithm 1, n_sweeps x (forward pass, backward pass), in one of four
  * orders.  0: colour classes (colours ascending, then descending); the
  * default and the GPU's.  1: element index 1..N, then N..1 (Algorithm 1 as
  * printed, serial).  2: the paper's threaded sweep made deterministic: the
  * index range cut into n_parts partitions, each swept in index order, with
  * neighbours in other partitions read as they were at the start of the
- * pass (Section 4, parallel strategy). */
+ * pass (Section 4, parallel strategy).  3: the same idea with colour
+ * classes inside each partition: the reverse Cuthill-McKee order cut into
+ * n_parts partitions (the cell at RCM position k is in partition
+ * floor(k n_parts / N)); each sweep relaxes colours ascending then
+ * descending within every partition, and a neighbour in another partition
+ * is read as it was at the start of the sweep (the forward and backward
+ * pass together). */
 static void point_relaxation(const or_solver *s, const double *U, const double *R, const double *lam,
                              const double *D, int n_sweeps, double *dU) {
   const or_mesh *m = s->m;
@@ -1655,6 +1692,22 @@ static void point_relaxation(const or_solver *s, const double *U, const double *
       for (int col = m->ncolour - 1; col >= 0; --col)
         for (long i = 0; i < nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, NULL, NULL);
     }
+    return;
+  }
+  if (s->P.sweep_order == 3) {
+    const long np = s->P.n_parts > 0 ? s->P.n_parts : 1;
+    int *part = (int *)malloc(sizeof(int) * nc);
+    double *old = (double *)malloc(sizeof(double) * nc * NV);
+    for (long k = 0; k < nc; ++k) part[m->rcm[k]] = (int)((k * np) / nc);
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+      memcpy(old, dU, sizeof(double) * nc * NV);
+      for (int col = 0; col < m->ncolour; ++col)
+        for (long i = 0; i < nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, old, part);
+      for (int col = m->ncolour - 1; col >= 0; --col)
+        for (long i = 0; i < nc; ++i) if (m->colour[i] == col) relax_cell(s, i, U, R, lam, D, dU, old, part);
+    }
+    free(part);
+    free(old);
     return;
   }
   int *part = NULL;

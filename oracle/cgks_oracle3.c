@@ -1252,6 +1252,34 @@ static void hi_eval(o3_solver *s, const double *W, const double *Wx, double dt) 
   }
 }
 
+/* Wall loads (Section 4's sphere drag and surface quantities): for every
+ * boundary face carrying tag, in the oracle's face order, the face centre
+ * (vertex mean), the unit normal out of the fluid, the area, and the
+ * momentum part of the face's high-order flux F0 at the current state
+ * (the weighted Gauss-point sum; with the full flux, of its fit over a
+ * step dt; global frame): on a wall the traction the fluid exerts.
+ * Arrays hold max_faces entries; returns the number of faces with the tag. */
+long o3_wall_loads(o3_solver *s, int tag, double dt, long max_faces, double *x, double *n, double *S,
+                   double *traction) {
+  const o3_mesh *m = s->m;
+  hi_eval(s, s->W, s->Wx, dt);
+  long k = 0;
+  for (long f = 0; f < m->nf; ++f) {
+    const o3_face *F = &m->face[f];
+    if (F->c1 >= 0 || F->tag != tag) continue;
+    if (k < max_faces) {
+      for (int d = 0; d < 3; ++d) {
+        x[3 * k + d] = F->xf[d];
+        n[3 * k + d] = F->n[d];
+        traction[3 * k + d] = s->F0[f * NV + 1 + d];
+      }
+      S[k] = F->S;
+    }
+    ++k;
+  }
+  return k;
+}
+
 static void net_flux(const o3_solver *s, const double *F0, const double *F1, double a, double b, double *out) {
   const o3_mesh *m = s->m;
   memset(out, 0, sizeof(double) * m->nc * NV);

@@ -106,6 +106,8 @@ def lib():
             L.or_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.or_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
             L.or_micro_slope.argtypes = [C.c_double, _dp, _dp, _dp]
+            L.or_wall_loads.restype = C.c_long
+            L.or_wall_loads.argtypes = [vp, C.c_int, C.c_double, C.c_long, _dp, _dp, _dp, _dp]
             _lib = L
     return _lib
 
@@ -114,7 +116,9 @@ def make_params(spec: dict) -> OrParams:
     """spec keys: gamma, mu, cfl_hi, cfl_lo, n_implicit, n_sweeps,
     time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
     flux_lo ('kfvs' default | 'lf': low-level flux), sweep_order ('colour'
-    default | 'index' | 'partitioned' with n_parts partitions, default 8),
+    default | 'index' | 'partitioned' with n_parts index partitions, default
+    8 | 'partitioned_colour': n_parts partitions of the RCM order, colour
+    classes inside, exchange lagged by one sweep),
     flux_hi ('smooth' default | 'full': Eq. (2nd-flux) with
     tau_n = tau + tau_c1 dt + tau_c2 dt |p_l - p_r| / (p_l + p_r), defaults
     0.01 and 1), weno_eps (> 0: nonlinear compact WENO weights, default 0 =
@@ -134,7 +138,8 @@ def make_params(spec: dict) -> OrParams:
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.restrict_mode = 0
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
-    P.sweep_order = {"colour": 0, "index": 1, "partitioned": 2}[spec.get("sweep_order", "colour")]
+    P.sweep_order = {"colour": 0, "index": 1, "partitioned": 2,
+                     "partitioned_colour": 3}[spec.get("sweep_order", "colour")]
     P.n_parts = int(spec.get("n_parts", 8))
     P.flux_hi = {"smooth": 0, "full": 1}[spec.get("flux_hi", "smooth")]
     P.tau_c1 = float(spec.get("tau_c1", 0.01))
@@ -259,6 +264,17 @@ class OracleSolver:
 
     def residual(self) -> float:
         return float(lib().or_last_residual(self._s))
+
+    def wall_loads(self, tag: int) -> dict:
+        """Face centres, normals, lengths and momentum flux F0 of the
+        boundary faces with this tag at the current state (oracle face
+        order); dt of the full flux from CFL_hi."""
+        dt = self.explicit_dt()
+        nf = int(lib().or_wall_loads(self._s, int(tag), dt, 0, np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(1)))
+        x, n, t = np.zeros((max(nf, 1), 2)), np.zeros((max(nf, 1), 2)), np.zeros((max(nf, 1), 2))
+        S = np.zeros(max(nf, 1))
+        lib().or_wall_loads(self._s, int(tag), dt, nf, x, n, S, t)
+        return dict(x=x[:nf], n=n[:nf], S=S[:nf], traction=t[:nf])
 
     def hi_residual(self, dt: float) -> np.ndarray:
         R = np.zeros((self.nc, NV))

@@ -101,6 +101,8 @@ def lib():
             L.o3_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.o3_ghost.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
             L.o3_micro_slope.argtypes = [C.c_double, _dp, _dp, _dp]
+            L.o3_wall_loads.restype = C.c_long
+            L.o3_wall_loads.argtypes = [vp, C.c_int, C.c_double, C.c_long, _dp, _dp, _dp, _dp]
             _lib = L
     return _lib
 
@@ -236,6 +238,18 @@ class OracleSolver3:
 
     def residual(self) -> float:
         return float(lib().o3_last_residual(self._s))
+
+    def wall_loads(self, tag: int) -> dict:
+        """Face centres, normals, areas and momentum flux F0 of the boundary
+        faces with this tag at the current state (oracle face order); dt of
+        the full flux from CFL_hi."""
+        dt = self.explicit_dt()
+        z = np.zeros(1)
+        nf = int(lib().o3_wall_loads(self._s, int(tag), dt, 0, z, z, z, z))
+        x, n, t = (np.zeros((max(nf, 1), 3)) for _ in range(3))
+        S = np.zeros(max(nf, 1))
+        lib().o3_wall_loads(self._s, int(tag), dt, nf, x, n, S, t)
+        return dict(x=x[:nf], n=n[:nf], S=S[:nf], traction=t[:nf])
 
     def hi_residual(self, dt: float) -> np.ndarray:
         R = np.zeros((self.nc, NV))

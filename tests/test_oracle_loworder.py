@@ -283,3 +283,57 @@ def test_sweep_order_barely_changes_convergence(oracle_lib):
     assert hi <= 1.1 * lo, cycles
     for order in ("index", "partitioned"):
         assert np.abs(fields[order] - fields["colour"]).max() < 1e-6 * np.abs(fields["colour"]).max()
+
+
+def _partitioned_colour_dense(om, A, R, colour, part, n_sweeps):
+    """The partitioned colour sweep written out on the dense linearised
+    system: per sweep, cells relax colour by colour (ascending, then
+    descending); a neighbour in the same partition contributes its current
+    increment, one in another partition its increment at the start of the
+    sweep."""
+    nc = R.shape[0]
+    x = np.zeros_like(R)
+    C = int(colour.max()) + 1
+    for _ in range(n_sweeps):
+        old = x.copy()
+        for c in list(range(C)) + list(range(C - 1, -1, -1)):
+            for i in np.nonzero(colour == c)[0]:
+                r = R[i].copy()
+                for j in range(nc):
+                    if j != i:
+                        r -= A[i, :, j, :] @ (x[j] if part[j] == part[i] else old[j])
+                x[i] = np.linalg.solve(A[i, :, i, :], r)
+    return x
+
+
+@pytest.mark.parametrize("n_parts,n_sweeps", [(1, 1), (3, 1), (3, 2), (4, 3)])
+def test_partitioned_colour_sweep_is_lagged_block_gauss_seidel(oracle_lib, n_parts, n_sweeps):
+    """Sweep order 'partitioned_colour' (the GPU's partitioned sweep): the
+    cell at reverse Cuthill-McKee position k belongs to partition
+    floor(k n_parts / N); within a partition colours relax in order,
+    across partitions the exchange is lagged by one sweep.  Checked against
+    that order on the dense linearised system (small R, so the relaxation
+    is linear to O(R^2))."""
+    O = oracle_lib
+    om, s0, U = small_case(oracle_lib, mu=0.01, n=4)
+    spec = dict(gamma=GAM, mu=0.01, cfl_lo=1000.0, sweep_order="partitioned_colour", n_parts=n_parts,
+                bcs=[dict(kind="slip"), dict(kind="farfield", rho=1.0, u=(0.3, 0.1), p=1 / GAM)])
+    s = O.OracleSolver(om, spec)
+    rng = np.random.default_rng(31)
+    eps = 1e-7
+    R = eps * rng.normal(size=U.shape)
+    dU = s.lo_relax(U, R, n_sweeps)
+    A = dense_system(om, U, s.lo_lambda(U), s.lo_diag(U))
+    rcm, colour = om.ordering()
+    nc = U.shape[0]
+    part = np.zeros(nc, np.int64)
+    part[rcm] = (np.arange(nc) * n_parts) // nc
+    assert len(set(part.tolist())) == n_parts
+    x = _partitioned_colour_dense(om, A, R, colour, part, n_sweeps)
+    np.testing.assert_allclose(dU / eps, x / eps, rtol=0, atol=1e-5 * np.abs(x / eps).max())
+    if n_parts == 1:
+        # one partition: the plain colour-class order
+        np.testing.assert_array_equal(dU, s0.lo_relax(U, R, n_sweeps))
+    else:
+        # the lag matters: the colour-class order gives a different result
+        assert np.abs(dU - s0.lo_relax(U, R, n_sweeps)).max() > 1e-3 * np.abs(dU).max()
