@@ -77,6 +77,22 @@ enum { CGKS_FP64 = 0, CGKS_MIXED = 1 };
  * two sides. */
 enum { CGKS_FLUX_KFVS = 0, CGKS_FLUX_LF = 1 };
 
+/* Order of the point relaxation (Algorithm 1), 2-D.
+ *   COLOUR:      colour classes over the whole mesh, colours ascending then
+ *                descending in every sweep (the index order of Algorithm 1
+ *                replaced by a distance-1 colouring; default).
+ *   PARTITIONED: the paper's threaded sweep (Section 3 and the parallel
+ *                cylinder runs of Section 4), made deterministic: the
+ *                reverse Cuthill-McKee order of each mesh is cut into
+ *                P = ceil(n_cells / sweep_part_cells) partitions (the cell
+ *                at RCM position k is in partition floor(k P / n_cells));
+ *                within a partition the colour classes relax in order,
+ *                and a neighbour in another partition is read as it was at
+ *                the start of the sweep (forward and backward pass
+ *                together).  One launch per sweep, one thread-block
+ *                cluster per partition. */
+enum { CGKS_SWEEP_COLOUR = 0, CGKS_SWEEP_PARTITIONED = 1 };
+
 /* Gas-kinetic flux of the high-order level (Section 2.3; Section 4 uses the
  * smooth one for subsonic flow, the full one with WENO weights for
  * transonic and supersonic flow).
@@ -131,6 +147,11 @@ typedef struct {
   int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF */
   int32_t flux_hi;       /* CGKS_FLUX_SMOOTH (default) or CGKS_FLUX_FULL */
   int32_t weno_vars;     /* CGKS_WENO_CONSERVATIVE (default) or CGKS_WENO_CHARACTERISTIC */
+  int32_t sweep_order;   /* CGKS_SWEEP_COLOUR (default) or CGKS_SWEEP_PARTITIONED (2-D only;
+                            not with low_order_fused) */
+  int32_t sweep_part_cells; /* cells per partition of the partitioned sweep, >= 64
+                            (0: 2048; smaller partitions lag more couplings and
+                            converge more slowly) */
   double tau_c1, tau_c2; /* numerical collision time constants of the full flux (0.01, 1) */
   double weno_eps;       /* > 0: compact WENO nonlinear weights with this epsilon (Section 4 uses
                             1e-2 and 1e-6); 0 (default): linear weights */

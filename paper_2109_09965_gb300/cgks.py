@@ -25,6 +25,7 @@ FP64, MIXED = 0, 1
 FLUX_KFVS, FLUX_LF = 0, 1
 FLUX_SMOOTH, FLUX_FULL = 0, 1
 WENO_CONSERVATIVE, WENO_CHARACTERISTIC = 0, 1
+SWEEP_COLOUR, SWEEP_PARTITIONED = 0, 1
 MAX_BC = 16
 OK, EINVAL, ENOMEM, EMESH, ECUDA, EDIVERGED, ETIMEOUT, EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7
 
@@ -54,6 +55,7 @@ class CgksParams(C.Structure):
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("use_graph", C.c_int32),
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
                 ("flux_lo", C.c_int32), ("flux_hi", C.c_int32), ("weno_vars", C.c_int32),
+                ("sweep_order", C.c_int32), ("sweep_part_cells", C.c_int32),
                 ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_eps", C.c_double), ("weno_g0", C.c_double),
                 ("bc", CgksBC * MAX_BC),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
@@ -200,7 +202,8 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     gamma, mu, alpha, cfl_hi, cfl_lo, n_implicit, n_sweeps, time_scheme,
     precision, use_graph, flux_lo ('kfvs' | 'lf'), flux_hi ('smooth' |
     'full'), tau_c1, tau_c2, weno_eps (0: linear weights), weno_g0,
-    weno_vars ('conservative' | 'characteristic'),
+    weno_vars ('conservative' | 'characteristic'), sweep_order ('colour' |
+    'partitioned'), sweep_part_cells,
     bcs=[{kind ('slip' | 'noslip' | 'farfield' | 'dirichlet' | 'outflow'),
     uw, rho, u, p}]."""
     P = CgksParams()
@@ -208,9 +211,11 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
     for key in ("gamma", "mu", "alpha", "cfl_hi", "cfl_lo", "tau_c1", "tau_c2", "weno_eps", "weno_g0"):
         if key in spec:
             setattr(P, key, float(spec[key]))
-    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch"):
+    for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch",
+                "sweep_part_cells"):
         if key in spec:
             setattr(P, key, int(spec[key]))
+    P.sweep_order = {"colour": SWEEP_COLOUR, "partitioned": SWEEP_PARTITIONED}[spec.get("sweep_order", "colour")]
     P.time_scheme = {"S1O2": S1O2, "S2O4": S2O4}[spec.get("time_scheme", "S1O2")]
     P.flux_lo = {"kfvs": FLUX_KFVS, "lf": FLUX_LF}[spec.get("flux_lo", "kfvs")]
     P.flux_hi = {"smooth": FLUX_SMOOTH, "full": FLUX_FULL}[spec.get("flux_hi", "smooth")]

@@ -41,6 +41,7 @@ struct Bufs {
   T *coef = nullptr, *FA = nullptr, *FB = nullptr;
   T *prim = nullptr, *Flo = nullptr, *lam = nullptr, *E0 = nullptr, *E1 = nullptr;
   T *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
+  T *dU2 = nullptr;   // second increment buffer of the partitioned sweep (ping-pong with dU)
 };
 
 // batch-wide settings (every solve of a batch shares them)
@@ -51,6 +52,7 @@ struct Shared {
   double tau_c1 = 0.01, tau_c2 = 1.0, weno_eps = 0.0, weno_g0 = 0.95;
   int weno_vars = CGKS_WENO_CONSERVATIVE;
   long long spin_limit = 0;      // grid-barrier polls of the persistent launch (0: kSpinLimit)
+  int sweep_order = CGKS_SWEEP_COLOUR, part_cells = 2048;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -118,6 +120,9 @@ struct Batch {
   // persistent low-order level: barrier, per-colour ranges, grid size
   GridBarrier *gb = nullptr;
   int *r_start = nullptr, *r_begin = nullptr, *r_pre = nullptr;
+  int *ptab = nullptr;               // partitioned sweep: [n_parts][n_colours][2] cell ranges
+  int64_t ptab_cap = 0;              // ints ptab holds
+  int n_parts = 0;
   int lo_grid = 0;
   bool lo_fused_ok = false;
   Tuner tune;                          // launch shapes of the tunable kernels
@@ -156,6 +161,38 @@ void launch(Batch *b, int id, Kern kern, dim3 grid, dim3 block, Args... args) {
     cudaEventRecord(e0, b->stream);
   }
   launch_on(b->stream, b->sh.pdl != 0, kern, grid, block, args...);
+  if (t) {
+    cudaEventRecord(e1, b->stream);
+    b->timer->ev.push_back({ id, { e0, e1 } });
+  }
+  b->launches++;
+}
+
+// launch with thread-block clusters of cluster_x CTAs along x
+template <typename Kern, typename... Args>
+void launch_cluster(Batch *b, int id, Kern kern, dim3 grid, dim3 block, int cluster_x, Args... args) {
+  if (grid.x == 0) return;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool t = b->timer && b->timer->on;
+  if (t) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->stream);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster_x;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = b->sh.pdl != 0 ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
   if (t) {
     cudaEventRecord(e1, b->stream);
     b->timer->ev.push_back({ id, { e0, e1 } });
@@ -289,7 +326,12 @@ void enqueue_lo_solve(Batch *b) {
   }
   Bufs<TF> &B = bufs<TF>(b);
   const dim3 gc(nblk(b->N, kCellBlock)), blk(kCellBlock);
-  const int colour0 = b->sh.n_sweeps > 0 ? 1 : 0;
+  const bool part = b->sh.sweep_order == CGKS_SWEEP_PARTITIONED;
+  // colour sweeps: k_lo_rhs relaxes colour 0 of the first pass.  Partitioned:
+  // k_lo_rhs zeroes the increments, the sweeps ping-pong between dU and
+  // dU2 starting so that the last one writes dU
+  const int colour0 = !part && b->sh.n_sweeps > 0 ? 1 : 0;
+  TF *dU0 = part && (b->sh.n_sweeps & 1) ? B.dU2 : B.dU;
   for (int k = 0; k < b->sh.n_implicit; ++k) {
     launch(b, KI_LOCELL, k_lo_cell<TF>, gc, blk, static_cast<int>(b->Ncap), fparams<TF>(b), k == 0 ? 1 : 0,
            (const double *)b->Wn, b->U, (const TF *)B.dU, B.prim, mirror<TF>(B.U));
@@ -301,7 +343,18 @@ void enqueue_lo_solve(Batch *b) {
       });
     });
     launch(b, KI_LORHS, k_lo_rhs<TF>, gc, blk, b->dm, b->dp, k == 0 ? 1 : 0, colour0, (const TF *)B.Flo,
-           (const TF *)B.lam, (const double *)b->Rp0, b->Src, B.Rk, B.invD, B.dU, B.lamS);
+           (const TF *)B.lam, (const double *)b->Rp0, b->Src, B.Rk, B.invD, dU0, B.lamS);
+    if (part) {
+      TF *in = dU0, *out = dU0 == B.dU ? B.dU2 : B.dU;
+      for (int sw = 0; sw < b->sh.n_sweeps; ++sw) {
+        launch_cluster(b, KI_SWEEP, k_sweep_part<TF>, dim3(b->n_parts * kPartCluster), dim3(kPartBlock),
+                       kPartCluster, fmesh<TF>(b), fparams<TF>(b), (const int *)b->ptab, b->n_colours,
+                       (const TF *)B.U, (const TF *)B.prim, (const TF *)B.Rk, (const TF *)B.invD,
+                       (const TF *)B.lamS, (const TF *)B.E0, (const TF *)B.E1, (const TF *)in, out);
+        std::swap(in, out);
+      }
+      continue;
+    }
     const int ssh = b->tune.shape(TK_SWEEP);
     for (int c : b->sweep_seq) {
       const int cnt = b->list_off[c + 1] - b->list_off[c];
@@ -374,9 +427,10 @@ long long count_launches(const Batch *b, bool cycle) {
   long long hi = per_eval + 1 + (b->sh.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
   long long dt = 2;
   if (!cycle) return dt + hi + 1;
-  long long lo = b->lo_fused_ok ? 1
-                               : b->sh.n_implicit * (3 + static_cast<long long>(b->sweep_seq.size())) +
-                                     (b->sh.n_implicit > 0 ? 1 : 0);
+  const long long sweeps = b->sh.sweep_order == CGKS_SWEEP_PARTITIONED
+                               ? static_cast<long long>(b->sh.n_sweeps)
+                               : static_cast<long long>(b->sweep_seq.size());
+  long long lo = b->lo_fused_ok ? 1 : b->sh.n_implicit * (3 + sweeps) + (b->sh.n_implicit > 0 ? 1 : 0);
   return dt + hi + per_eval + 1 + lo + 2;
 }
 
@@ -503,17 +557,24 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   PV(reinterpret_cast<void **>(&b->gb), sizeof(GridBarrier));
   PI(&b->r_start, kMaxColFused + 1); PI(&b->r_begin, kMaxColFused * static_cast<int64_t>(S));
   PI(&b->r_pre, kMaxColFused * static_cast<int64_t>(S) + kMaxColFused);
+  if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) {
+    // at most N / part_cells + S partitions (one partial per solve)
+    b->ptab_cap = 2 * kMaxPartColours * (N / std::max(b->sh.part_cells, 1) + S);
+    PI(&b->ptab, b->ptab_cap);
+  }
   if (!mixed) {
     Bufs<double> &X = b->bd;
     P8(&X.coef, 20 * N); P8(&X.FA, 16 * F); P8(&X.FB, 16 * F);
     P8(&X.prim, D::NPRIM * N); P8(&X.Flo, 4 * F); P8(&X.lam, F); P8(&X.E0, 4 * F); P8(&X.E1, 4 * F);
     P8(&X.Rk, 4 * N); P8(&X.invD, N); P8(&X.dU, 4 * N); P8(&X.lamS, kMaxFace * N);
+    if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) P8(&X.dU2, 4 * N);
   } else {
     Bufs<float> &X = b->bf;
     P4(&X.W, 4 * N); P4(&X.Wx, 8 * N); P4(&X.Wn, 4 * N); P4(&X.Ws, 4 * N); P4(&X.Wxs, 8 * N); P4(&X.U, 4 * N);
     P4(&X.coef, 20 * N); P4(&X.FA, 16 * F); P4(&X.FB, 16 * F);
     P4(&X.prim, D::NPRIM * N); P4(&X.Flo, 4 * F); P4(&X.lam, F);
     P4(&X.Rk, 4 * N); P4(&X.invD, N); P4(&X.dU, 4 * N); P4(&X.lamS, kMaxFace * N);
+    if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) P4(&X.dU2, 4 * N);
     P4(&d.f_ivol, N); P4(&d.f_ih, N); P4(&d.f_m2, 3 * N); P4(&d.f_op, kNCol * kNM * N);
     P4(&d.f_snx, kMaxFace * N); P4(&d.f_sny, kMaxFace * N); P4(&d.f_shs, kMaxFace * N);
     P4(&d.f_fn, 2 * F); P4(&d.f_fS, F); P4(&d.f_fjump, F); P4(&d.f_fxi, 8 * F);
@@ -552,6 +613,18 @@ void clear_cells(Batch *b, int64_t c0, int64_t c1) {
       static_cast<int>(c0), static_cast<int>(c1), static_cast<int>(b->Ncap), b->d.csid, b->d.ccol, b->d.cface,
       b->d.cnbr, b->W, b->Wx, b->Wn, b->Ws, b->Wxs, b->mixed ? b->bf.W : nullptr, b->mixed ? b->bf.Wx : nullptr,
       b->mixed ? b->bf.Wn : nullptr, b->mixed ? b->bf.Ws : nullptr, b->mixed ? b->bf.Wxs : nullptr);
+  // the second increment buffer of the partitioned sweep is written only at
+  // partition cells: clear it (and the first) where cells become inert
+  for (int v = 0; v < 4; ++v) {
+    if (b->bd.dU2) {
+      cudaMemsetAsync(b->bd.dU + v * b->Ncap + c0, 0, sizeof(double) * (c1 - c0), b->stream);
+      cudaMemsetAsync(b->bd.dU2 + v * b->Ncap + c0, 0, sizeof(double) * (c1 - c0), b->stream);
+    }
+    if (b->bf.dU2) {
+      cudaMemsetAsync(b->bf.dU + v * b->Ncap + c0, 0, sizeof(float) * (c1 - c0), b->stream);
+      cudaMemsetAsync(b->bf.dU2 + v * b->Ncap + c0, 0, sizeof(float) * (c1 - c0), b->stream);
+    }
+  }
 }
 
 // Allocate a batch with capacity for Ncap cells, Fcap faces and S slots;
@@ -617,6 +690,8 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   if (ok) {
     if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * Ncap, st) == cudaSuccess;
     else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess;
+    if (ok && b->bf.dU2) ok = cudaMemsetAsync(b->bf.dU2, 0, sizeof(float) * 4 * Ncap, st) == cudaSuccess;
+    if (ok && b->bd.dU2) ok = cudaMemsetAsync(b->bd.dU2, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess;
   }
   if (ok) {
     clear_cells(b, 0, Ncap);
@@ -826,6 +901,46 @@ int finalize_batch(Batch *b) {
   }
   if (need_list && !list.empty())
     CK(cudaMemcpyAsync(b->list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream));
+  // partitioned sweep: each solve's RCM order cut into ceil(n / part_cells)
+  // partitions (RCM position k in partition floor(k P / n)); inside a
+  // colour's internal range (RCM order) a partition is a contiguous run
+  b->n_parts = 0;
+  if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) {
+    if (C > kMaxPartColours) return CGKS_EMESH;
+    std::vector<int> tab;
+    for (int s : order) {
+      const Member &M = b->mem[s];
+      const HostMesh &hm = *M.mesh;
+      const int64_t n = hm.n_cells;
+      const int64_t P = (n + b->sh.part_cells - 1) / b->sh.part_cells;
+      std::vector<int64_t> pos(n);
+      for (int64_t k = 0; k < n; ++k) pos[hm.rcm[k]] = k;
+      const size_t q0 = tab.size() / (2 * C);
+      tab.resize(tab.size() + static_cast<size_t>(2 * C * P), 0);
+      for (int c = 0; c < C; ++c) {
+        const int beg = c < hm.n_colours ? hm.colour_start[c] : 0;
+        const int end = c < hm.n_colours ? hm.colour_start[c + 1] : 0;
+        // first internal index of each partition in this colour's range
+        int cur = beg;
+        for (int64_t q = 0; q < P; ++q) {
+          int e = cur;
+          while (e < end && (pos[hm.perm[e]] * P) / n == q) ++e;
+          int *t = &tab[2 * ((q0 + q) * C + c)];
+          t[0] = static_cast<int>(M.cell_off) + cur;
+          t[1] = static_cast<int>(M.cell_off) + e;
+          cur = e;
+        }
+        if (cur != end) return CGKS_EMESH;   // not monotone in RCM position: never for this layout
+      }
+    }
+    b->n_parts = static_cast<int>(tab.size() / (2 * std::max(C, 1)));
+    if (static_cast<int64_t>(tab.size()) > b->ptab_cap) return CGKS_EINVAL;
+    if (!tab.empty())
+      CK(cudaMemcpyAsync(b->ptab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    // the colour-launch shapes are not used: nothing to tune for the sweep
+    b->tune.unit[TK_SWEEP] = Tuner::kRounds * kNShape;
+    b->tune.decided[TK_SWEEP] = true;
+  }
   // the fused low-order launch: per-colour ranges of every active solve
   b->lo_fused_ok = false;
   // (the fused launch implements the KFVS low level only)
@@ -925,6 +1040,8 @@ Shared shared_from(const cgks_params *p) {
   sh.flux_hi = p->flux_hi;
   sh.tau_c1 = p->tau_c1; sh.tau_c2 = p->tau_c2; sh.weno_eps = p->weno_eps; sh.weno_g0 = p->weno_g0;
   sh.weno_vars = p->weno_vars;
+  sh.sweep_order = p->sweep_order;
+  sh.part_cells = p->sweep_part_cells > 0 ? p->sweep_part_cells : 2048;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
 }
@@ -936,7 +1053,10 @@ int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_
       (p->flux_lo != CGKS_FLUX_KFVS && p->flux_lo != CGKS_FLUX_LF) ||
       (p->flux_hi != CGKS_FLUX_SMOOTH && p->flux_hi != CGKS_FLUX_FULL) || !(p->tau_c1 >= 0.0) ||
       !(p->tau_c2 >= 0.0) || !(p->weno_eps >= 0.0) || (p->weno_eps > 0.0 && !(p->weno_g0 > 0.0 && p->weno_g0 < 1.0)) ||
-      (p->weno_vars != CGKS_WENO_CONSERVATIVE && p->weno_vars != CGKS_WENO_CHARACTERISTIC))
+      (p->weno_vars != CGKS_WENO_CONSERVATIVE && p->weno_vars != CGKS_WENO_CHARACTERISTIC) ||
+      (p->sweep_order != CGKS_SWEEP_COLOUR && p->sweep_order != CGKS_SWEEP_PARTITIONED) ||
+      (p->sweep_order == CGKS_SWEEP_PARTITIONED && p->low_order_fused) ||
+      (p->sweep_part_cells != 0 && p->sweep_part_cells < 64))
     return CGKS_EINVAL;
   for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
@@ -1216,6 +1336,7 @@ int cgks_solver_create(const cgks_mesh *m, const cgks_params *p, cgks_solver **o
   if (m->dim == 3) {
     // the 3-D path has walls and far field, and WENO on conservative variables
     if (p->weno_eps > 0.0 && p->weno_vars != CGKS_WENO_CONSERVATIVE) return CGKS_EINVAL;
+    if (p->sweep_order != CGKS_SWEEP_COLOUR) return CGKS_EINVAL;   // the partitioned sweep is 2-D
     for (int b = 0; b < p->n_bc; ++b)
       if (p->bc[b].kind != CGKS_BC_SLIP && p->bc[b].kind != CGKS_BC_NOSLIP && p->bc[b].kind != CGKS_BC_FARFIELD)
         return CGKS_EINVAL;

@@ -890,13 +890,16 @@ __device__ __forceinline__ SweepGeo<T> sweep_geo(const MeshT<T> &m, const int i,
   }
   return g;
 }
+// The relaxation of cell i by its 4-lane group; the neighbour's increment
+// is read from dn (through L2 when l2 is set: values another CTA of the
+// launch wrote), the cell's new increment written to dU.
 template <typename T>
-__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
-                                           const int i, const int s, const T *__restrict__ U,
-                                           const T *__restrict__ prim, const T *__restrict__ Rk,
-                                           const T *__restrict__ invD, const T *__restrict__ lamS,
-                                           const T *__restrict__ E0, const T *__restrict__ E1,
-                                           T *__restrict__ dU) {
+__device__ __forceinline__ void sweep_cell_from(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
+                                                const int i, const int s, const T *__restrict__ U,
+                                                const T *__restrict__ prim, const T *__restrict__ Rk,
+                                                const T *__restrict__ invD, const T *__restrict__ lamS,
+                                                const T *__restrict__ E0, const T *__restrict__ E1,
+                                                const T *dn, const bool l2, T *dU) {
   const int n = m.nc, nf = m.nf;
   const int j = g.j;
   // every lane stays to the shuffles; lanes of absent cells or slots add 0
@@ -905,7 +908,10 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
     const T nx = g.nx, ny = g.ny, hS = g.hS, lp = lamS[s * n + i];
     T uj[4], du[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { uj[v] = U[v * n + j]; du[v] = dU[v * n + j]; }
+    for (int v = 0; v < 4; ++v) {
+      uj[v] = U[v * n + j];
+      du[v] = l2 ? __ldcg(&dn[v * n + j]) : dn[v * n + j];
+    }
     if constexpr (is_f32<T>()) {
       T dF[4];
       D::euler_flux_delta(P.gamma, uj, prim[1 * n + j], prim[2 * n + j], prim[3 * n + j], du, nx, ny, dF);
@@ -931,6 +937,14 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
   const T k1 = (b0 ? c[3] : c[2]) + __shfl_xor_sync(0xffffffffu, b0 ? c[2] : c[3], 1);   // component b0 + 2
   const T mine = (b1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
   if (i >= 0) dU[s * n + i] = (Rk[s * n + i] - mine) * invD[i];
+}
+template <typename T>
+__device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &P, const SweepGeo<T> &g,
+                                           const int i, const int s, const T *__restrict__ U,
+                                           const T *__restrict__ prim, const T *__restrict__ Rk,
+                                           const T *__restrict__ invD, const T *__restrict__ lamS,
+                                           const T *__restrict__ E0, const T *__restrict__ E1, T *dU) {
+  sweep_cell_from(m, P, g, i, s, U, prim, Rk, invD, lamS, E0, E1, dU, false, dU);
 }
 // cells per block of a sweep launch of shape SH
 __host__ __device__ constexpr int sweep_cpb(int sh) { return shape_bs(sh) / kMaxFace * shape_ipt(sh); }
@@ -962,6 +976,84 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_sweep(MeshT<T>
     const SweepGeo<T> geo = sweep_geo(m, i, s);
     pdl_enter();
     sweep_cell(m, P, geo, i, s, U, prim, Rk, invD, lamS, E0, E1, dU);
+  }
+  pdl_exit();
+}
+
+// ---- the partitioned sweep (CGKS_SWEEP_PARTITIONED) ----
+// One launch is one sweep of Algorithm 1 -- a forward pass over the
+// colours, then a backward pass -- over every partition at once.  A
+// thread-block cluster owns one partition: its CTAs share out each
+// colour's cells of the partition, and a cluster barrier (release /
+// acquire at cluster scope) separates consecutive colours, so a cell sees
+// the increments its partition's earlier colours just wrote to dU_out
+// (read through L2).  Neighbours in other partitions, and cells of this
+// partition not yet relaxed in this sweep, are read from dU_in, the
+// increments at the start of the sweep: partitions exchange once per
+// sweep, lagged, like the paper's threads.  Every cell of every partition
+// is written to dU_out.  The colour C-1 ending the forward pass is not
+// relaxed again at the start of the backward pass: with its inputs
+// unchanged it would recompute the same values.
+constexpr int kPartBlock = 256;        // threads per CTA: 64 cells per pass of a CTA
+constexpr int kPartCluster = 8;        // CTAs per partition (portable cluster size)
+constexpr int kMaxPartColours = 16;
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders the global writes before
+// it (release) before the reads after it (acquire), cluster scope
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ptab [Q][C][2]: first and end cell (internal index) of colour c in
+// partition q; C colours
+template <typename T>
+__global__ void __launch_bounds__(kPartBlock) k_sweep_part(MeshT<T> m, ParamsT<T> P, const int *__restrict__ ptab,
+                                                           int C, const T *__restrict__ U,
+                                                           const T *__restrict__ prim, const T *__restrict__ Rk,
+                                                           const T *__restrict__ invD,
+                                                           const T *__restrict__ lamS, const T *__restrict__ E0,
+                                                           const T *__restrict__ E1, const T *__restrict__ dU_in,
+                                                           T *dU_out) {
+  __shared__ int sb[kMaxPartColours], se[kMaxPartColours];
+  const unsigned K = cluster_nctarank(), rank = cluster_ctarank();
+  const int q = static_cast<int>(blockIdx.x / K);
+  if (static_cast<int>(threadIdx.x) < C) {
+    sb[threadIdx.x] = ptab[2 * (q * C + threadIdx.x)];
+    se[threadIdx.x] = ptab[2 * (q * C + threadIdx.x) + 1];
+  }
+  __syncthreads();
+  constexpr int G = kPartBlock / kMaxFace;          // cells per pass of a CTA
+  const int s = threadIdx.x & (kMaxFace - 1);
+  const int cl = static_cast<int>(threadIdx.x) / kMaxFace;
+  pdl_enter();
+  const int steps = 2 * C - 1;
+  for (int step = 0; step < steps; ++step) {
+    const bool fwd = step < C;
+    const int c = fwd ? step : 2 * C - 2 - step;
+    const int b = sb[c], e = se[c];
+    // the CTA's passes are uniform over its threads (the shuffles need
+    // whole lane groups)
+    for (int base = b + static_cast<int>(rank) * G; base < e; base += static_cast<int>(K) * G) {
+      const int i = base + cl < e ? base + cl : -1;
+      const SweepGeo<T> g = sweep_geo(m, i, s);
+      bool fresh = false;
+      if (g.j >= 0) {
+        const int cj = m.ccol[g.j];
+        fresh = cj < C && g.j >= sb[cj] && g.j < se[cj] && (!fwd || cj < c);
+      }
+      sweep_cell_from(m, P, g, i, s, U, prim, Rk, invD, lamS, E0, E1, fresh ? dU_out : dU_in, fresh, dU_out);
+    }
+    if (step + 1 < steps) cluster_sync();
   }
   pdl_exit();
 }

@@ -26,7 +26,7 @@ def test_full_flux_weno_explicit_steps_match_oracle(libs, name, scheme):
         Wg, Xg = s.get_state()
         Wo, Xo = o.get_state()
         assert rel(Wg, Wo) < TOL, (k, rel(Wg, Wo))
-        assert rel(Xg, Xo) < 10 * TOL, (k, rel(Xg, Xo))
+        assert rel(Xg, Xo) < TOL, (k, rel(Xg, Xo))
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -36,7 +36,7 @@ def test_full_flux_weno_cycles_match_oracle(libs, name):
     Wg, Xg = s.get_state()
     Wo, Xo = o.get_state()
     assert rel(Wg, Wo) < TOL, rel(Wg, Wo)
-    assert rel(Xg, Xo) < 10 * TOL, rel(Xg, Xo)
+    assert rel(Xg, Xo) < TOL, rel(Xg, Xo)
 
 
 def supersonic_sphere():

@@ -127,17 +127,17 @@ def test_wall_loads_match_oracle_2d(cg, oracles, precision, flux):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_wall_loads_match_oracle_3d(cg, oracles, precision):
-    """3-D: a viscous sphere shell (icosphere level 1, prism and split-tet
-    layers) after 15 V-cycles; wall and far-field loads against the 3-D
-    oracle from the same state."""
+    """3-D: a viscous sphere shell (icosphere level 2, 12 prism and 4
+    split-tet layers) after 20 V-cycles; wall and far-field loads against
+    the 3-D oracle from the same state."""
     _, O3 = oracles
-    mesh = MG.sphere(1, 4, 2, h0=0.02, growth=1.4, R_far=4.0)
+    mesh = MG.sphere(2, 12, 4, h0=5e-3, growth=1.35, R_far=5.0)
     ma = 0.2
     spec = dict(gamma=GAM, mu=ma / 118, bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0),
                                                                       p=1 / GAM)])
     s = cg.Solver(cg.Mesh(mesh), dict(spec, precision=precision))
     s.set_state(np.tile([1.0, ma, 0.0, 0.0, 1 / GAM / (GAM - 1) + 0.5 * ma * ma], (mesh.n_cells, 1)))
-    s.pmg_cycle(15)
+    s.pmg_cycle(20)
     W, Wx = s.get_state()
     o = O3.OracleSolver3(O3.OracleMesh3(mesh), spec)
     o.set_state(W, Wx)
