@@ -540,14 +540,29 @@ def sphere_case(level, n_prism, n_tet, h0, ma, re):
     return mesh, spec, W
 
 
+# the 3-D throughput workloads: (level, prism layers, split-tet layers, first
+# layer / D, Ma, Re, timed cycles, description)
+SPHERES = {
+    "sphere512k": (4, 40, 20, 5e-3, 0.2, 118, 30,
+                   "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism "
+                   "layers (growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: 512,000 cells; "
+                   "first layer 5e-3 D instead of 1e-3 D (the V-cycle diverges on the thinner layer)"),
+    "sphere3M": (5, 60, 30, 1e-3, 0.2, 1000, 10,
+                 "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
+                 "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
+                 "(throughput of the smooth path; the Ma 1.5 case with the full flux and WENO is the "
+                 "supersonic_sphere entry)"),
+}
+
+
 def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_prism, n_tet, h0, ma, re, steps,
-                 note):
+                 note, precisions=("fp64", "mixed")):
     t0 = time.perf_counter()
     mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, ma, re)
     gm = cgks.Mesh(mesh)
     prep = time.perf_counter() - t0
     out = {"workload": note, "n_cells": mesh.n_cells, "n_faces": gm.n_faces, "mesh_prep_s": prep}
-    for prec in ("fp64", "mixed"):
+    for prec in precisions:
         m = measure(cgks, gm, mesh, spec, W0, args, prec, world, local, flush, hbm, hbm_src, with_e2e=False,
                     steps=steps, work_model=work_model3, workload_name=name)
         out[prec] = {"value": m["value"], "unit": "cell-updates/s", "ms_per_step": m["ms"] / steps, "steps": steps,
@@ -579,6 +594,8 @@ def main():
     ap.add_argument("--supersonic-only", action="store_true", help="only the supersonic sphere runs")
     ap.add_argument("--converge3d-full", action="store_true",
                     help="3-D convergence on the 512,000-cell sphere instead of the 128,000-cell one")
+    ap.add_argument("--only-3d", default="", choices=["", "sphere512k", "sphere3M"],
+                    help="only this 3-D throughput workload (for profiling), in --precision")
     ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
                     help="serving run: a small sample in the line (default), or the full 256-request mix")
     args = ap.parse_args()
@@ -594,6 +611,16 @@ def main():
     if args.supersonic_only:
         if rank == 0:
             emit({"block": "supersonic_sphere", "supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)})
+        return
+    if args.only_3d:
+        if rank == 0:
+            import torch
+            flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+            hbm, hbm_src = peaks()
+            case3 = SPHERES[args.only_3d]
+            emit({"block": "workloads_3d", "workloads_3d": {args.only_3d: sphere_bench(
+                cgks, args, 1, local, flush, hbm, hbm_src, args.only_3d, *case3[:7], case3[7],
+                precisions=(args.precision,))}})
         return
     if args.shock_only:
         if rank == 0:
@@ -627,18 +654,8 @@ def main():
         # (3-D, serving, convergence) are single-GPU runs
         args.no_3d, args.serving, args.no_convergence, args.converge = True, "none", True, False
     if not args.no_3d:
-        w3 = {
-            "sphere512k": sphere_bench(
-                cgks, args, world, local, flush, hbm, hbm_src, "sphere512k", 4, 40, 20, 5e-3, 0.2, 118, 30,
-                "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism layers "
-                "(growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: 512,000 cells; first "
-                "layer 5e-3 D instead of 1e-3 D (the V-cycle diverges on the thinner layer)"),
-            "sphere3M": sphere_bench(
-                cgks, args, world, local, flush, hbm, hbm_src, "sphere3M", 5, 60, 30, 1e-3, 0.2, 1000, 10,
-                "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
-                "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
-                "(throughput of the smooth path; the Ma 1.5 case with the full flux and WENO is the supersonic_sphere entry)"),
-        }
+        w3 = {name: sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, *c[:7], c[7])
+              for name, c in SPHERES.items()}
         emit({"block": "workloads_3d", "workloads_3d": w3})
         legs["sphere512k"] = {k: w3["sphere512k"][k]["value"] for k in ("fp64", "mixed")}
         legs["sphere3M"] = {k: w3["sphere3M"][k]["value"] for k in ("fp64", "mixed")}
@@ -792,7 +809,12 @@ def work_model(mesh, gm, spec, precision):
 # launches, averaged over the colours of a V-cycle for k_sweep).  An entry
 # is removed when its kernel changes; a workload with no entry reports
 # traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 57,344-cell cylinder, per V-cycle 6 x (6 big-colour + 2 small-colour)
+    # launches: (6 x 9.62 MB + 2 x 0.88 MB) / 8 and (6 x 3.78 MB + 2 x 0.78 MB) / 8
+    ("cylinder57k", "k_sweep", "fp64"): 7.43e6,
+    ("cylinder57k", "k_sweep", "mixed"): 3.03e6,
+}
 
 
 def roofline(kt, wm, precision, hbm, hbm_src, steps, workload_name="cylinder57k"):
