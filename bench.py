@@ -345,12 +345,20 @@ def measure(cgks, gm, mesh, spec, W0, args, precision, world, local, flush, hbm,
     return out
 
 
-def serving_requests(n_req, n_lo, n_hi, seed=5):
+# the limited flux class of a served request: the full flux of Eq. (2nd-flux)
+# with compact WENO (conservative variables, eps 1e-2), Section 4's setting
+# for transonic flow
+LIMITED = dict(flux_hi="full", weno_eps=1e-2)
+
+
+def serving_requests(n_req, n_lo, n_hi, seed=5, ma_hi=0.5):
     """Request mix of the serving workload: half lid-driven cavities (n x n
     quads split into triangles, n chosen for the cell count, Re
-    log-uniform in [100, 3200], Ma 0.15), half inviscid cylinders (hybrid
-    O-mesh with N_theta for the cell count, Ma U[0.2, 0.4], AoA U[0, 10]
-    deg).  Cell counts log-uniform in [n_lo, n_hi]; mesh seed 1000 + id."""
+    log-uniform in [100, 3200], Ma 0.15; smooth flux), half inviscid
+    cylinders (hybrid O-mesh with N_theta for the cell count, Ma U[0.2,
+    ma_hi], AoA U[0, 10] deg; the limited flux class).  Cell counts
+    log-uniform in [n_lo, n_hi]; mesh seed 1000 + id; uniform free-stream
+    (or rest) starts."""
     from paper_2109_09965_gb300 import meshgen
     rng = np.random.default_rng(seed)
     out = []
@@ -366,19 +374,20 @@ def serving_requests(n_req, n_lo, n_hi, seed=5):
             out.append(dict(kind="cavity", Re=re, mesh=mesh, spec=spec, W=W))
         else:
             nt = max(16, 8 * int(round(math.sqrt(cells * 8.0 / 7.0) / 8.0)))
-            ma = rng.uniform(0.2, 0.4)
+            ma = rng.uniform(0.2, ma_hi)
             aoa = math.radians(rng.uniform(0.0, 10.0))
             mesh = meshgen.cylinder(nt, nt // 8, 3 * nt // 8)
             u, v = ma * math.cos(aoa), ma * math.sin(aoa)
             spec = dict(gamma=GAMMA, mu=0.0, bcs=[dict(kind="slip"),
-                                                  dict(kind="farfield", rho=1.0, u=(u, v), p=1.0 / GAMMA)])
+                                                  dict(kind="farfield", rho=1.0, u=(u, v), p=1.0 / GAMMA)],
+                        **LIMITED)
             W = np.tile([1.0, u, v, 1.0 / GAMMA / (GAMMA - 1.0) + 0.5 * ma * ma], (mesh.n_cells, 1))
             out.append(dict(kind="cylinder", Ma=ma, mesh=mesh, spec=spec, W=W))
     return out
 
 
 def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles, max_active, precision,
-            load=0.8, seed=5):
+            load=0.8, seed=5, ma_hi=0.5):
     """Continuous-batching serving run: requests arrive by a Poisson process
     on the server's clock and are submitted when due; the server admits by
     device footprint within the budget, runs one batched V-cycle per step
@@ -386,7 +395,7 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
     measured from arrival to retirement."""
     import torch
     t_prep = time.perf_counter()
-    reqs = serving_requests(n_req, n_lo, n_hi, seed)
+    reqs = serving_requests(n_req, n_lo, n_hi, seed, ma_hi)
     meshes = [cgks.Mesh(r["mesh"]) for r in reqs]
     t_prep = time.perf_counter() - t_prep
     srv = cgks.Server(int(budget_gb * 2**30), precision=precision, max_active=max_active, max_cycles=max_cycles)
@@ -419,12 +428,19 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
             time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
     lat, states, cells_done = [], {}, 0
-    t_server0 = None
+    by_kind = {}
+    conv_lat = []
     for k, rid in enumerate(ids):
         st, _ = srv.poll(rid, want_state=False)
         states[st["state"]] = states.get(st["state"], 0) + 1
+        r = reqs[k]
+        key = r["kind"] if r["kind"] == "cavity" else f"cylinder Ma {'<= 0.4' if r['Ma'] <= 0.4 else '> 0.4'}"
+        by_kind.setdefault(key, {})
+        by_kind[key][st["state"]] = by_kind[key].get(st["state"], 0) + 1
         cells_done += st["n_cells"] * st["cycles"]
         lat.append(st["t_done"] - st["t_submit"])
+        if st["state"] == "converged":
+            conv_lat.append(lat[-1])
     lat = np.asarray(lat)
     tuned = {k: v["shape"] for k, v in srv.tuning().items()}
     srv.close()
@@ -432,11 +448,13 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
                                                int(max(r["mesh"].n_cells for r in reqs))],
             "wall_s": wall, "solves_per_hour": n_req / wall * 3600.0,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "states": states, "steps": steps,
+            "mean_s": float(lat.mean()), "states": states, "states_by_kind": by_kind, "steps": steps,
+            "converged_p50_s": float(np.percentile(conv_lat, 50)) if conv_lat else None,
+            "converged_p99_s": float(np.percentile(conv_lat, 99)) if conv_lat else None,
             "cell_updates_per_s": cells_done / wall, "peak_device_bytes": int(peak_bytes),
             "peak_active": int(peak_active), "budget_bytes": int(budget_gb * 2**30), "precision": precision,
-            "criterion": f"cylinders: Res drop {drop:g} relative to the first cycle (cap {max_cycles}); "
-                         f"cavities: {cavity_cycles} cycles",
+            "criterion": f"cylinders (Ma U[0.2, {ma_hi:g}], limited flux class): Res drop {drop:g} relative to "
+                         f"the first cycle (cap {max_cycles}); cavities (smooth flux): {cavity_cycles} cycles",
             "mesh_prep_s": t_prep, "tuned_shapes": tuned}
 
 
@@ -665,6 +683,12 @@ def main():
                      "mixed")
         emit({"block": "serving", "serving": sv})
         legs["serving"] = {k: sv[k] for k in ("requests", "solves_per_hour", "p50_s", "p99_s", "states")}
+        # FP64 serving retiring at the configured 1e-8 drop (below the mixed
+        # path's floor): cylinders up to Ma 0.4, where the V-cycle reaches it
+        sv64 = serving(cgks, 64 if full else 16, 2000, 60000 if full else 12000, 60.0, 1e-8, 2000, 8000, 64,
+                       "fp64", ma_hi=0.4)
+        emit({"block": "serving_fp64", "serving_fp64": sv64})
+        legs["serving_fp64"] = {k: sv64[k] for k in ("requests", "solves_per_hour", "p50_s", "p99_s", "states")}
     cpu = None if args.no_cpu_baseline else cpu_baseline(mesh, spec, W0)
     if args.converge:
         emit({"block": "convergence_57k", "convergence_57k": converge(cgks, mesh, spec, W0)})

@@ -304,8 +304,14 @@ typedef struct {
 void cgks_server_default_opts(cgks_server_opts *o);
 int cgks_server_create(size_t hbm_budget, const cgks_server_opts *opts, cgks_server **out);
 /* Queue a request.  The mesh and W0 ([n_cells*4], caller order, host) are
- * copied; p supplies gamma, mu, alpha and the boundary conditions (the
- * batch-wide fields come from the server options).  max_cycles > 0 caps
+ * copied; p supplies gamma, mu, alpha, the boundary conditions and the
+ * flux class (the batch-wide fields come from the server options).  Each
+ * request picks one of two flux classes, which share a batch: smooth
+ * (CGKS_FLUX_SMOOTH, weno_eps 0: Section 4's subsonic setting) or limited
+ * (CGKS_FLUX_FULL with weno_eps > 0 on conservative variables: its
+ * transonic and supersonic setting); every limited request of a server
+ * must carry the same weno_eps, weno_g0, tau_c1 and tau_c2 (CGKS_EINVAL
+ * otherwise, and for any other flux setting).  max_cycles > 0 caps
  * this request's cycles below the server's max_cycles.  A request whose
  * footprint alone exceeds the budget is rejected (CGKS_EBUDGET); so are
  * the requests of a batch the server fails to allocate (the step that

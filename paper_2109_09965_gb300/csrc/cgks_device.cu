@@ -53,6 +53,10 @@ struct Shared {
   int weno_vars = CGKS_WENO_CONSERVATIVE;
   long long spin_limit = 0;      // grid-barrier polls of the persistent launch (0: kSpinLimit)
   int sweep_order = CGKS_SWEEP_COLOUR, part_cells = 2048;
+  // serving batches: a per-solve flux class (smooth / limited) instead of
+  // the batch-wide flux_hi and weno_eps; the limited class takes the full
+  // flux with conservative compact WENO and the constants above
+  bool per_slot_flux = false;
   cgks_alloc_fn alloc = nullptr;
   cgks_free_fn free = nullptr;
   void *alloc_ctx = nullptr;
@@ -121,6 +125,9 @@ struct Batch {
   GridBarrier *gb = nullptr;
   int *r_start = nullptr, *r_begin = nullptr, *r_pre = nullptr;
   int *ptab = nullptr;               // partitioned sweep: [n_parts][n_colours][2] cell ranges
+  int *slim = nullptr;               // [S] flux class per slot (per_slot_flux batches)
+  std::vector<int> slim_host;
+  int n_lim = 0, n_smooth = 0;       // active solves of each class
   int64_t ptab_cap = 0;              // ints ptab holds
   int n_parts = 0;
   int lo_grid = 0;
@@ -230,6 +237,30 @@ void enqueue_hi_eval(Batch *b, const TF *W, const TF *Wx, TF *Fout) {
   // so the default (linear weights, smooth flux) kernels stay as lean as before
   const bool chr = b->sh.weno_eps > 0.0 && b->sh.weno_vars == CGKS_WENO_CHARACTERISTIC;
   const bool weno = b->sh.weno_eps > 0.0 && !chr, full = b->sh.flux_hi == CGKS_FLUX_FULL;
+  if (b->sh.per_slot_flux) {
+    // one launch per flux class present; each skips the other class's solves
+    tuned_launch(b->tune, TK_RECON, b->stream, [&] {
+      with_shape(b->tune.shape(TK_RECON), [&](auto sh) {
+        constexpr int S = decltype(sh)::value;
+        const dim3 g(nblk(b->N, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+        if (b->n_smooth) launch(b, KI_RECON, k_recon<TF, S, false>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
+        if (b->n_lim) launch(b, KI_RECON, k_recon<TF, S, true>, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, B.coef);
+      });
+    });
+    tuned_launch(b->tune, TK_FACE, b->stream, [&] {
+      with_shape(b->tune.shape(TK_FACE), [&](auto sh) {
+        constexpr int S = decltype(sh)::value;
+        const dim3 g(nblk(b->F, shape_bs(S) * shape_ipt(S))), blk(shape_bs(S));
+        auto go = [&](auto kern) {
+          launch(b, KI_FACE, kern, g, blk, fmesh<TF>(b), fparams<TF>(b), W, Wx, (const TF *)B.coef, Fout,
+                 (const Ctl *)b->ctl, (const unsigned long long *)b->dt_bits);
+        };
+        if (b->n_smooth) go(k_face<TF, S, false, false>);
+        if (b->n_lim) go(k_face<TF, S, true, false>);
+      });
+    });
+    return;
+  }
   tuned_launch(b->tune, TK_RECON, b->stream, [&] {
     with_shape(b->tune.shape(TK_RECON), [&](auto sh) {
       constexpr int S = decltype(sh)::value;
@@ -423,7 +454,7 @@ void enqueue_lo_smooth(Batch *b) {
 }
 
 long long count_launches(const Batch *b, bool cycle) {
-  long long per_eval = 2;
+  long long per_eval = b->sh.per_slot_flux ? 2 * ((b->n_smooth > 0) + (b->n_lim > 0)) : 2;
   long long hi = per_eval + 1 + (b->sh.time_scheme == CGKS_S2O4 ? per_eval + 1 : 0);
   long long dt = 2;
   if (!cycle) return dt + hi + 1;
@@ -555,6 +586,7 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   PV(reinterpret_cast<void **>(&b->dt_bits), sizeof(unsigned long long) * S);
   PI(&b->status, S);
   PV(reinterpret_cast<void **>(&b->gb), sizeof(GridBarrier));
+  PI(&b->slim, S);
   PI(&b->r_start, kMaxColFused + 1); PI(&b->r_begin, kMaxColFused * static_cast<int64_t>(S));
   PI(&b->r_pre, kMaxColFused * static_cast<int64_t>(S) + kMaxColFused);
   if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) {
@@ -665,6 +697,9 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   b->dp.bc_p = d.bcp;
   b->fp.mu = d.f_mu; b->fp.bc_kind = d.bckind; b->fp.bc_uw = d.f_bcuw; b->fp.bc_rho = d.f_bcrho; b->fp.bc_u = d.f_bcu;
   b->fp.bc_p = d.f_bcp;
+  b->dp.slim = sh.per_slot_flux ? b->slim : nullptr;
+  b->fp.slim = sh.per_slot_flux ? b->slim : nullptr;
+  b->slim_host.assign(S, 0);
   MeshT<double> &dm = b->dm;
   dm.nc = static_cast<int>(Ncap); dm.nf = static_cast<int>(Fcap);
   dm.vol = d.vol; dm.ivol = d.ivol; dm.per = d.per; dm.ih = d.ih; dm.m2 = d.m2; dm.op = d.op;
@@ -686,7 +721,8 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
             cudaMemsetAsync(b->Rp0, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess &&
             cudaMemsetAsync(d.fsid, 0xff, sizeof(int) * Fcap, st) == cudaSuccess &&
             cudaMemsetAsync(d.bckind, 0, sizeof(int) * kTagsPerSolve * S, st) == cudaSuccess &&
-            cudaMemsetAsync(b->gb, 0, sizeof(GridBarrier), st) == cudaSuccess;
+            cudaMemsetAsync(b->gb, 0, sizeof(GridBarrier), st) == cudaSuccess &&
+            cudaMemsetAsync(b->slim, 0, sizeof(int) * S, st) == cudaSuccess;
   if (ok) {
     if (b->mixed) ok = cudaMemsetAsync(b->bf.dU, 0, sizeof(float) * 4 * Ncap, st) == cudaSuccess;
     else ok = cudaMemsetAsync(b->bd.dU, 0, sizeof(double) * 4 * Ncap, st) == cudaSuccess;
@@ -851,6 +887,19 @@ int finalize_batch(Batch *b) {
   }
   std::sort(order.begin(), order.end(), [&](int x, int y) { return b->mem[x].cell_off < b->mem[y].cell_off; });
   b->N = N; b->F = F; b->n_colours = C;
+  // flux class per slot (serving batches): smooth, or limited (full flux +
+  // conservative compact WENO); the class constants are batch-wide
+  b->n_lim = b->n_smooth = 0;
+  if (b->sh.per_slot_flux) {
+    for (int s = 0; s < b->S; ++s) {
+      const Member &M = b->mem[s];
+      b->slim_host[s] = M.active && M.params.flux_hi == CGKS_FLUX_FULL ? 1 : 0;
+      if (M.active) (b->slim_host[s] ? b->n_lim : b->n_smooth)++;
+    }
+    CK(cudaMemcpyAsync(b->slim, b->slim_host.data(), sizeof(int) * b->S, cudaMemcpyHostToDevice, b->stream));
+    fill_shared_params(b->sh, b->dp);
+    fill_shared_params(b->sh, b->fp);
+  }
   std::vector<int> blk(2 * b->S, 0);
   for (int s : order) {
     blk[2 * s] = static_cast<int>(b->mem[s].cell_off / kCellBlock);
@@ -1136,6 +1185,7 @@ struct cgks_server {
   std::map<int64_t, std::unique_ptr<Req>> reqs;
   std::deque<int64_t> queue;
   std::vector<int64_t> slot_req;   // request in each slot of the batch, -1 free
+  bool lim_set = false;            // the limited class's constants are fixed (sh)
   RangeAlloc cells, faces;
   Batch *b = nullptr;              // created at the first admission
   std::chrono::steady_clock::time_point t0;
@@ -1668,6 +1718,8 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->sh.autotune = o->autotune;
   v->sh.pdl = o->programmatic_launch;
   v->sh.flux_lo = o->flux_lo;
+  v->sh.per_slot_flux = true;
+  v->sh.weno_vars = CGKS_WENO_CONSERVATIVE;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
   v->max_active = o->max_active;
   v->max_cycles = o->max_cycles;
@@ -1727,8 +1779,21 @@ int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p,
   q.time_scheme = v->sh.time_scheme; q.precision = v->sh.precision;
   int rc = validate_params(&q, m->h);
   if (rc) return rc;
-  // served solves run the smooth flux with linear weights (the batch shares its flux)
-  if (q.flux_hi != CGKS_FLUX_SMOOTH || q.weno_eps > 0.0) return CGKS_EINVAL;
+  // two flux classes per batch: smooth flux with linear weights, or the
+  // limited one (full flux with conservative compact WENO) whose constants
+  // every limited request of the server shares
+  const bool smooth = q.flux_hi == CGKS_FLUX_SMOOTH && q.weno_eps == 0.0;
+  const bool limited = q.flux_hi == CGKS_FLUX_FULL && q.weno_eps > 0.0 && q.weno_vars == CGKS_WENO_CONSERVATIVE;
+  if (!smooth && !limited) return CGKS_EINVAL;
+  if (limited) {
+    if (!v->lim_set) {
+      v->sh.tau_c1 = q.tau_c1; v->sh.tau_c2 = q.tau_c2; v->sh.weno_eps = q.weno_eps; v->sh.weno_g0 = q.weno_g0;
+      v->lim_set = true;
+    } else if (q.tau_c1 != v->sh.tau_c1 || q.tau_c2 != v->sh.tau_c2 || q.weno_eps != v->sh.weno_eps ||
+               q.weno_g0 != v->sh.weno_g0) {
+      return CGKS_EINVAL;
+    }
+  }
   if (std::fabs(q.gamma - v->sh.gamma) > 1e-15) {
     if (v->reqs.empty()) v->sh.gamma = q.gamma;
     else return CGKS_EINVAL;   // every solve of a server shares gamma
@@ -1823,7 +1888,11 @@ static int server_update(cgks_server *v, double t, bool *changed) {
     v->queue.pop_front();
     *changed = true;
   }
-  if (*changed && b) return finalize_batch(b);
+  if (*changed && b) {
+    b->sh.tau_c1 = v->sh.tau_c1; b->sh.tau_c2 = v->sh.tau_c2;
+    b->sh.weno_eps = v->sh.weno_eps; b->sh.weno_g0 = v->sh.weno_g0;
+    return finalize_batch(b);
+  }
   return CGKS_OK;
 }
 

@@ -52,6 +52,11 @@ struct ParamsT {
   T tau_c1, tau_c2;              // numerical collision time constants of the full flux
   T weno_eps, weno_g0;           // compact WENO epsilon (0: linear weights), linear weight of P2
   int weno_vars;                 // CGKS_WENO_CONSERVATIVE (per cell) or CGKS_WENO_CHARACTERISTIC (per face side)
+  // [S] per solve: 1 = limited (full flux + compact WENO), 0 = smooth flux,
+  // linear weights; null when every solve of the batch takes the batch-wide
+  // flux.  With it each instantiation of k_recon / k_face treats only the
+  // solves of its own class.
+  const int *slim;
 };
 
 template <typename T>
@@ -310,7 +315,13 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH)) k_recon(MeshT<T>
                                                                         const T *__restrict__ Wx,
                                                                         T *__restrict__ coef) {
   pdl_enter();
-  for_items<SH>(m.nc, [&](int i) { recon_at<T, WENO>(m, P, W, Wx, coef, i); });
+  for_items<SH>(m.nc, [&](int i) {
+    if (P.slim) {
+      const int sid = m.csid[i];
+      if (sid >= 0 && (P.slim[sid] != 0) != WENO) return;
+    }
+    recon_at<T, WENO>(m, P, W, Wx, coef, i);
+  });
   pdl_exit();
 }
 
@@ -447,6 +458,7 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
                                         const Ctl *ctl, const unsigned long long *dt_bits, const int f) {
   const int sid = m.fsid[f];
   if (sid < 0) return;   // free face space of a batch
+  if (P.slim && (P.slim[sid] != 0) != FULL) return;   // the other flux class's launch
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
   const T nx = m.fn[f], ny = m.fn[nf + f], ajump = m.fjump[f];

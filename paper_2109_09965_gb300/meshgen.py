@@ -279,6 +279,28 @@ def cylinder(n_theta: int = 256, n_quad: int = 32, n_tri: int = 96, *, growth=1.
     return _finish(nodes, tris, quads, bedges, btags, meta)
 
 
+def cylinder_potential_state(mesh: Mesh, ma: float, aoa: float = 0.0, *, gamma: float = 1.4,
+                             R: float = 0.5) -> np.ndarray:
+    """Initial state for a cylinder request: the incompressible potential
+    flow around a circle of radius R at the cell centres (node means),
+    u - i v = U (e^{-i aoa} - R^2 e^{i aoa} / z^2), with density and
+    pressure from the isentropic energy balance of a free stream with
+    rho = 1, c = 1: c^2 = 1 + (gamma - 1)/2 (Ma^2 - q^2), rho = c^{2/(gamma-1)},
+    p = rho c^2 / gamma (c^2 floored at 0.2 where the potential flow is
+    too fast).  Conservative variables [n_cells, 4].  A starting guess
+    without the impulsive start of a uniform stream at a wall; the steady
+    solution does not depend on it."""
+    ptr = mesh.cell_ptr
+    xc = np.add.reduceat(mesh.nodes[mesh.cell_nodes], ptr[:-1], axis=0) / np.diff(ptr)[:, None]
+    z = xc[:, 0] + 1j * xc[:, 1]
+    w = ma * (np.exp(-1j * aoa) - R * R * np.exp(1j * aoa) / (z * z))
+    u, v = w.real, -w.imag
+    c2 = np.maximum(1.0 + 0.5 * (gamma - 1.0) * (ma * ma - (u * u + v * v)), 0.2)
+    rho = c2 ** (1.0 / (gamma - 1.0))
+    p = rho * c2 / gamma
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)], axis=1)
+
+
 def cylinder_cells(n_theta: int, n_quad: int, n_tri: int) -> int:
     return n_theta * (n_quad + 2 * n_tri)
 
@@ -564,3 +586,29 @@ def sphere(level=4, n_prism=40, n_tet=20, *, h0=1e-3, growth=1.1, R=0.5, R_far=2
 
 
 SPHERE_WALL, SPHERE_FARFIELD = 0, 1
+
+
+def sphere_potential_state(mesh: Mesh, ma: float, *, gamma: float = 1.4, R: float = 0.5,
+                           delta: float = 0.0) -> np.ndarray:
+    """Initial state for a sphere: the incompressible potential flow past a
+    sphere of radius R with free stream Ma along x, at the cell centres
+    (node means): u = Ma (e_x (1 + R^3 / (2 r^3)) - 3 R^3 x x_vec / (2 r^5)),
+    damped towards a no-slip wall by tanh((r - R) / delta) when delta > 0;
+    density and pressure from the isentropic energy balance of a free
+    stream with rho = 1, c = 1 (c^2 floored at 0.2).  Conservative
+    variables [n_cells, 5].  A starting guess without an impulsive start;
+    the steady solution does not depend on it."""
+    ptr = mesh.cell_ptr
+    x = np.add.reduceat(mesh.nodes[mesh.cell_nodes], ptr[:-1], axis=0) / np.diff(ptr)[:, None]
+    r = np.linalg.norm(x, axis=1)
+    a = R ** 3 / (2.0 * r ** 3)
+    vel = -3.0 * a[:, None] * x[:, 0:1] * x / (r * r)[:, None]
+    vel[:, 0] += 1.0 + a
+    vel *= ma
+    if delta > 0.0:
+        vel *= np.tanh(np.maximum(r - R, 0.0) / delta)[:, None]
+    q2 = (vel * vel).sum(1)
+    c2 = np.maximum(1.0 + 0.5 * (gamma - 1.0) * (ma * ma - q2), 0.2)
+    rho = c2 ** (1.0 / (gamma - 1.0))
+    p = rho * c2 / gamma
+    return np.concatenate([rho[:, None], rho[:, None] * vel, (p / (gamma - 1.0) + 0.5 * rho * q2)[:, None]], axis=1)

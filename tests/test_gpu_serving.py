@@ -198,3 +198,63 @@ def test_per_request_cycle_cap(cg):
     assert srv.poll(a)[0]["cycles"] == 2 and srv.poll(b)[0]["cycles"] == 6
     Ws, _ = standalone(cg, reqs[0][1], reqs[0][2], reqs[0][3], 2, "fp64")
     assert np.array_equal(srv.poll(a)[1], Ws)
+
+
+LIMITED = dict(flux_hi="full", weno_eps=1e-2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_flux_classes_in_one_batch(cg, precision):
+    """Smooth and limited requests (the full flux of Eq. (2nd-flux) with
+    compact WENO, Section 4's setting for transonic flow) share one batch:
+    each class's launches skip the other class's solves, and every result
+    is bitwise the standalone solver's with the same settings."""
+    K = 5
+    reqs = requests()
+    reqs = [(n, m, dict(s, **LIMITED) if k % 2 else s, W) for k, (n, m, s, W) in enumerate(reqs)]
+    srv = cg.Server(8 << 30, precision=precision, max_active=8, max_cycles=K)
+    meshes = [cg.Mesh(m) for _, m, _, _ in reqs]
+    ids = [srv.submit(gm, spec, W, NEVER) for gm, (_, _, spec, W) in zip(meshes, reqs)]
+    for _ in range(K):
+        assert srv.step() == len(reqs)
+    for rid, (name, mesh, spec, W) in zip(ids, reqs):
+        st, Wb = srv.poll(rid)
+        assert st["state"] == "stopped" and st["cycles"] == K, (name, st)
+        Ws, hist = standalone(cg, mesh, spec, W, K, precision)
+        assert np.array_equal(Wb, Ws), (name, spec.get("flux_hi"), np.abs(Wb - Ws).max())
+        assert st["res_last"] == hist[-1]
+    # a limited request with other constants, or characteristic WENO, is refused
+    name, mesh, spec, W = reqs[0]
+    for bad in (dict(LIMITED, weno_eps=1e-3), dict(LIMITED, weno_vars="characteristic"), dict(flux_hi="full")):
+        with pytest.raises(cg.CgksError):
+            srv.submit(meshes[0], dict(spec, **bad), W, NEVER)
+
+
+@pytest.mark.parametrize("limited", [False, True])
+def test_server_result_matches_oracle(cg, oracle_lib, limited):
+    """A served FP64 request against the CPU oracle: a viscous cylinder run
+    for 6 batched V-cycles (the per-request cap), its final state within the
+    FP64 bar of the oracle's 6 V-cycles; smooth and limited classes, each
+    batched with a request of the other class."""
+    O = oracle_lib
+    K = 6
+    _, mesh, spec, W = requests()[2]                     # cylinder_viscous
+    other = requests()[0]
+    if limited:
+        spec = dict(spec, **LIMITED)
+    else:
+        other = (other[0], other[1], dict(other[2], **LIMITED), other[3])
+    srv = cg.Server(8 << 30, precision="fp64", max_active=4, max_cycles=K)
+    rid = srv.submit(cg.Mesh(mesh), spec, W, NEVER)
+    srv.submit(cg.Mesh(other[1]), other[2], other[3], NEVER)
+    for _ in range(K):
+        srv.step()
+    st, Wb = srv.poll(rid)
+    assert st["state"] == "stopped" and st["cycles"] == K
+    o = O.OracleSolver(O.OracleMesh(mesh), spec)
+    o.set_state(W)
+    h = o.pmg_cycles(K)
+    Wo, _ = o.get_state()
+    e = np.linalg.norm(Wb - Wo) / np.linalg.norm(Wo)
+    assert e < 1e-12, e
+    assert abs(st["res_last"] - h[-1]) <= 1e-9 * h[-1]
