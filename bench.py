@@ -712,6 +712,9 @@ def main():
                                 "speedup": conv.get("speedup"),
                                 "speedup_lower_bound": conv.get("speedup_lower_bound")}
         emit({"block": "validation_re40", "validation_re40": validation_re40(cgks)})
+        c1 = cavity_config1(cgks)
+        emit({"block": "cavity_config1", "cavity_config1": c1})
+        legs["cavity2048"] = {k: c1[k]["cell_updates_per_s"] for k in ("fp64", "mixed")}
         if not args.no_shock:
             emit({"block": "shock_reflection", "shock_reflection": shock_reflection(cgks)})
         if not args.no_3d:
@@ -879,6 +882,36 @@ def roofline(kt, wm, precision, hbm, hbm_src, steps, workload_name="cylinder57k"
                 "traffic": NCU_TRAFFIC.get((workload_name, top, precision)),
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     return roof, per
+
+
+def cavity_config1(cgks, cycles=2000):
+    """Configuration 1: the 2048-cell lid-driven cavity (32 x 32 quads split
+    in two, 10 % node jitter, Re 1000, Ma 0.15), 2000 V-cycles from rest,
+    FP64 and mixed: wall time, cell-updates/s, the residual history."""
+    import torch
+    from paper_2109_09965_gb300 import meshgen
+    mesh = meshgen.cavity(32)
+    spec = dict(gamma=GAMMA, mu=0.15 / 1000.0, cfl_hi=0.5,
+                bcs=[dict(kind="noslip"), dict(kind="noslip", uw=(0.15, 0.0))])
+    W0 = np.tile([1.0, 0.0, 0.0, 1.0 / GAMMA / (GAMMA - 1.0)], (mesh.n_cells, 1))
+    out = {"workload": "lid-driven cavity, Re 1000, Ma 0.15: 32 x 32 quads split into 2048 triangles, 10 % node "
+                       f"jitter (seed 1); {cycles} p-multigrid V-cycles from rest", "n_cells": mesh.n_cells}
+    gm = cgks.Mesh(mesh)
+    for prec in ("fp64", "mixed"):
+        s = cgks.Solver(gm, dict(spec, precision=prec))
+        s.set_state(W0)
+        s.pmg_cycle(20, record=False)        # autotuner and graph capture
+        s.set_state(W0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h = s.pmg_cycle(cycles)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        s.close()
+        out[prec] = {"wall_s": el, "ms_per_cycle": 1e3 * el / cycles,
+                     "cell_updates_per_s": mesh.n_cells * cycles / el, "res_first": float(h[0]),
+                     "res_last": float(h[-1]), "history": [float(x) for x in h[::max(1, cycles // 20)]]}
+    return out
 
 
 def validation_re40(cgks, max_cycles=8000, drop=1e-8):
