@@ -355,8 +355,10 @@ def serving_requests(n_req, n_lo, n_hi, seed=5, ma_hi=0.5):
     """Request mix of the serving workload: half lid-driven cavities (n x n
     quads split into triangles, n chosen for the cell count, Re
     log-uniform in [100, 3200], Ma 0.15; smooth flux), half inviscid
-    cylinders (hybrid O-mesh with N_theta for the cell count, Ma U[0.2,
-    ma_hi], AoA U[0, 10] deg; the limited flux class).  Cell counts
+    cylinders (hybrid O-mesh with N_theta for the cell count, N_theta / 8
+    quad layers whose growth keeps the interface cells square, 3 N_theta / 8
+    triangle layers to 20 radii; Ma U[0.2, ma_hi], AoA U[0, 10] deg; the
+    limited flux class).  Cell counts
     log-uniform in [n_lo, n_hi]; mesh seed 1000 + id; uniform free-stream
     (or rest) starts."""
     from paper_2109_09965_gb300 import meshgen
@@ -376,7 +378,8 @@ def serving_requests(n_req, n_lo, n_hi, seed=5, ma_hi=0.5):
             nt = max(16, 8 * int(round(math.sqrt(cells * 8.0 / 7.0) / 8.0)))
             ma = rng.uniform(0.2, ma_hi)
             aoa = math.radians(rng.uniform(0.0, 10.0))
-            mesh = meshgen.cylinder(nt, nt // 8, 3 * nt // 8)
+            mesh = meshgen.cylinder(nt, nt // 8, 3 * nt // 8,
+                                    growth=meshgen.cylinder_growth_isotropic(nt, nt // 8))
             u, v = ma * math.cos(aoa), ma * math.sin(aoa)
             spec = dict(gamma=GAMMA, mu=0.0, bcs=[dict(kind="slip"),
                                                   dict(kind="farfield", rho=1.0, u=(u, v), p=1.0 / GAMMA)],

@@ -106,6 +106,8 @@ typedef struct {
   int weno_char;              /* 1: WENO weights on characteristic variables, per face side */
   int pad2_;
   or_bc bc[MAXBC];
+  int lo_viscous;             /* 1: the low-order residual carries a first-order viscous flux */
+  int pad3_;
 } or_params;
 
 /* ------------------------------------------------------------------ */
@@ -1586,6 +1588,31 @@ static void lo_lf(const or_solver *s, const double Ul[NV], const double Ur[NV], 
 }
 
 /* R_lo,i(U) = -sum_p S_p F_lo(U_i, U_ip; n_p), F_lo = KFVS or L-F */
+/* First-order viscous flux of the low-order level (reading: Section 3's
+ * "first-order finite volume scheme" for the Navier-Stokes equations; its
+ * implicit operator already carries the viscous spectral radius in lambda).
+ * Gradients along the face normal from the two cell states over the
+ * distance delta of the cell centres along n (a boundary face: twice the
+ * centre-to-face distance, against the ghost state): with du = u_r - u_l,
+ *   tau.n = mu / delta (du + (n.du) n / 3)          (Stokes' hypothesis),
+ *   q.n   = -kappa (T_r - T_l) / delta,  T = p / rho, kappa = mu c_p (Pr = 1),
+ * subtracted from the inviscid flux: F -= (0, tau.n, tau.n . (u_l + u_r)/2 - q.n). */
+static void lo_viscous_flux(const or_solver *s, const double Ul[NV], const double Ur[NV], const double n[2],
+                            double delta, double F[NV]) {
+  double rl, ul[2], pl, rr, ur[2], pr;
+  prim(s->P.gamma, Ul, &rl, ul, &pl);
+  prim(s->P.gamma, Ur, &rr, ur, &pr);
+  const double mu = s->P.mu, kappa = mu * s->P.gamma / (s->P.gamma - 1.0);
+  const double du[2] = { ur[0] - ul[0], ur[1] - ul[1] };
+  const double dn = du[0] * n[0] + du[1] * n[1];
+  double tau[2];
+  for (int d = 0; d < 2; ++d) tau[d] = mu / delta * (du[d] + dn * n[d] / 3.0);
+  const double qn = -kappa * (pr / rr - pl / rl) / delta;
+  F[1] -= tau[0];
+  F[2] -= tau[1];
+  F[3] -= tau[0] * 0.5 * (ul[0] + ur[0]) + tau[1] * 0.5 * (ul[1] + ur[1]) - qn;
+}
+
 static void lo_residual(const or_solver *s, const double *U, double *R) {
   const or_mesh *m = s->m;
   memset(R, 0, sizeof(double) * m->nc * NV);
@@ -1602,6 +1629,7 @@ static void lo_residual(const or_solver *s, const double *U, double *R) {
     } else {
       or_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
     }
+    if (s->P.lo_viscous && s->P.mu > 0.0) lo_viscous_flux(s, &U[F->c0 * NV], Ur, F->n, F->delta, Fl);
     for (int v = 0; v < NV; ++v) {
       R[F->c0 * NV + v] -= F->S * Fl[v];
       if (F->c1 >= 0) R[F->c1 * NV + v] += F->S * Fl[v];

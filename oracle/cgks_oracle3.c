@@ -77,6 +77,8 @@ typedef struct {
   double weno_eps;            /* > 0: nonlinear compact WENO weights; <= 0: linear weights */
   double weno_g0;             /* linear weight of the quadratic candidate */
   o3_bc bc[MAXBC];
+  int lo_viscous;             /* 1: the low-order residual carries a first-order viscous flux */
+  int pad2_;
 } o3_params;
 
 typedef struct {
@@ -1407,6 +1409,31 @@ static double lo_lambda_side(const o3_solver *s, const double U[NV], const doubl
 /* R_lo,i(U) = -sum_p S_p F_lo(U_i, U_ip; n_p): KFVS, or the Lax-Friedrichs
  * alternative of Section 3 with the implicit operator's lambda_p,
  * (F_n(U_l) + F_n(U_r)) / 2 - lambda_p (U_r - U_l) / 2 */
+/* First-order viscous flux of the low-order level, as in 2-D: normal
+ * gradients from the two cell states over the centre distance delta along
+ * n (boundary faces: twice the centre-to-face distance, ghost state),
+ *   tau.n = mu / delta (du + (n.du) n / 3),  q.n = -kappa (T_r - T_l) / delta,
+ * F -= (0, tau.n, tau.n . (u_l + u_r)/2 - q.n). */
+static void lo_viscous_flux(const o3_solver *s, const double Ul[NV], const double Ur[NV], const double n[3],
+                            double delta, double F[NV]) {
+  double rl, ul[3], pl, rr, ur[3], pr;
+  prim3(s->P.gamma, Ul, &rl, ul, &pl);
+  prim3(s->P.gamma, Ur, &rr, ur, &pr);
+  const double mu = s->P.mu, kappa = mu * s->P.gamma / (s->P.gamma - 1.0);
+  const double du[3] = { ur[0] - ul[0], ur[1] - ul[1], ur[2] - ul[2] };
+  const double dn = dot3(du, n);
+  double tau[3], work = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    tau[d] = mu / delta * (du[d] + dn * n[d] / 3.0);
+    work += tau[d] * 0.5 * (ul[d] + ur[d]);
+  }
+  const double qn = -kappa * (pr / rr - pl / rl) / delta;
+  F[1] -= tau[0];
+  F[2] -= tau[1];
+  F[3] -= tau[2];
+  F[4] -= work - qn;
+}
+
 static void lo_residual(const o3_solver *s, const double *U, double *R) {
   const o3_mesh *m = s->m;
   memset(R, 0, sizeof(double) * m->nc * NV);
@@ -1427,6 +1454,7 @@ static void lo_residual(const o3_solver *s, const double *U, double *R) {
     } else {
       o3_kfvs(&s->P, &U[F->c0 * NV], Ur, F->n, Fl);
     }
+    if (s->P.lo_viscous && s->P.mu > 0.0) lo_viscous_flux(s, &U[F->c0 * NV], Ur, F->n, F->delta, Fl);
     for (int v = 0; v < NV; ++v) {
       R[F->c0 * NV + v] -= F->S * Fl[v];
       if (F->c1 >= 0) R[F->c1 * NV + v] += F->S * Fl[v];

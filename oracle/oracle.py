@@ -47,7 +47,7 @@ class OrParams(C.Structure):
                 ("flux_lo", C.c_int), ("sweep_order", C.c_int), ("n_parts", C.c_int),
                 ("flux_hi", C.c_int), ("pad_", C.c_int), ("tau_c1", C.c_double), ("tau_c2", C.c_double),
                 ("weno_eps", C.c_double), ("weno_g0", C.c_double), ("weno_char", C.c_int), ("pad2_", C.c_int),
-                ("bc", OrBC * 16)]
+                ("bc", OrBC * 16), ("lo_viscous", C.c_int), ("pad3_", C.c_int)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -115,7 +115,8 @@ def lib():
 def make_params(spec: dict) -> OrParams:
     """spec keys: gamma, mu, cfl_hi, cfl_lo, n_implicit, n_sweeps,
     time_scheme ('S1O2'|'S2O4'), alpha (jump coefficient, default 1/2),
-    flux_lo ('kfvs' default | 'lf': low-level flux), sweep_order ('colour'
+    flux_lo ('kfvs' default | 'lf': low-level flux), lo_viscous (1: the
+    low-order residual carries a first-order viscous flux), sweep_order ('colour'
     default | 'index' | 'partitioned' with n_parts index partitions, default
     8 | 'partitioned_colour': n_parts partitions of the RCM order, colour
     classes inside, exchange lagged by one sweep),
@@ -138,6 +139,7 @@ def make_params(spec: dict) -> OrParams:
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.restrict_mode = 0
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
+    P.lo_viscous = int(spec.get("lo_viscous", 0))
     P.sweep_order = {"colour": 0, "index": 1, "partitioned": 2,
                      "partitioned_colour": 3}[spec.get("sweep_order", "colour")]
     P.n_parts = int(spec.get("n_parts", 8))

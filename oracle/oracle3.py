@@ -44,7 +44,7 @@ class O3Params(C.Structure):
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int), ("n_sweeps", C.c_int),
                 ("time_scheme", C.c_int), ("n_bc", C.c_int), ("flux_lo", C.c_int), ("flux_hi", C.c_int),
                 ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_eps", C.c_double), ("weno_g0", C.c_double),
-                ("bc", O3BC * 16)]
+                ("bc", O3BC * 16), ("lo_viscous", C.c_int), ("pad2_", C.c_int)]
 
 
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -124,6 +124,7 @@ def make_params(spec: dict) -> O3Params:
     P.n_sweeps = int(spec.get("n_sweeps", 2))
     P.time_scheme = {"S1O2": 0, "S2O4": 1}[spec.get("time_scheme", "S1O2")]
     P.flux_lo = {"kfvs": 0, "lf": 1}[spec.get("flux_lo", "kfvs")]
+    P.lo_viscous = int(spec.get("lo_viscous", 0))
     P.flux_hi = {"smooth": 0, "full": 1}[spec.get("flux_hi", "smooth")]
     P.tau_c1 = float(spec.get("tau_c1", 0.01))
     P.tau_c2 = float(spec.get("tau_c2", 1.0))

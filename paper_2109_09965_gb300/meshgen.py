@@ -279,6 +279,31 @@ def cylinder(n_theta: int = 256, n_quad: int = 32, n_tri: int = 96, *, growth=1.
     return _finish(nodes, tris, quads, bedges, btags, meta)
 
 
+def cylinder_growth_isotropic(n_theta: int, n_quad: int, *, R: float = 0.5, cap: float = 1.08) -> float:
+    """Quad-layer growth of an O-mesh family scaled by N_theta: the ratio g
+    (at most ``cap``) at which the last of n_quad quad layers, starting at
+    a quarter of the wall's circumferential spacing, is as thick as the
+    circumferential spacing at its radius, so the quad / triangle interface
+    cells are about square.  With the fixed growth of the 256-cell ring
+    (1.08), rings of a few hundred cells and n_quad = N_theta / 8 push the
+    quad stack out to several radii and leave the triangle layers
+    shrinking outwards (cells of aspect ratio in the thousands at the far
+    field); this keeps every ring's grading sane.  Bisection on g."""
+    h0 = 2.0 * math.pi * R / n_theta / 4.0
+
+    def excess(g):
+        r = R + h0 * (g ** n_quad - 1.0) / (g - 1.0)
+        return h0 * g ** (n_quad - 1) - 2.0 * math.pi * r / n_theta
+    lo, hi = 1.0 + 1e-9, 1.5
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if excess(mid) > 0.0:
+            hi = mid
+        else:
+            lo = mid
+    return min(cap, 0.5 * (lo + hi))
+
+
 def cylinder_potential_state(mesh: Mesh, ma: float, aoa: float = 0.0, *, gamma: float = 1.4,
                              R: float = 0.5) -> np.ndarray:
     """Initial state for a cylinder request: the incompressible potential
