@@ -152,6 +152,15 @@ typedef struct {
   int32_t sweep_part_cells; /* cells per partition of the partitioned sweep, >= 64
                             (0: 2048; smaller partitions lag more couplings and
                             converge more slowly) */
+  int32_t lo_viscous;    /* 1: the low-order residual carries a first-order viscous flux
+                            (reading of Section 3's first-order finite volume scheme for
+                            viscous flow): normal gradients from the two cell states over
+                            their centre distance along the face normal, Stokes'
+                            hypothesis, Pr = 1 heat flux.  Needed on wall cells thinner
+                            than the viscous length mu / (rho c), where the inviscid
+                            correction overshoots; 0 (default): inviscid KFVS / L-F.
+                            Not with low_order_fused. */
+  int32_t pad2_;
   double tau_c1, tau_c2; /* numerical collision time constants of the full flux (0.01, 1) */
   double weno_eps;       /* > 0: compact WENO nonlinear weights with this epsilon (Section 4 uses
                             1e-2 and 1e-6); 0 (default): linear weights */
@@ -281,7 +290,7 @@ typedef struct {
   int32_t autotune;      /* 1 (default): autotuned launch shapes for the batch */
   int32_t programmatic_launch; /* 1 (default): programmatic dependent launch (see cgks_params) */
   int32_t flux_lo;       /* CGKS_FLUX_KFVS (default) or CGKS_FLUX_LF for every solve */
-  int32_t pad_;
+  int32_t lo_viscous;    /* 1: first-order viscous flux on the low-order level (see cgks_params) */
   void *stream;          /* cudaStream_t (NULL = default) */
   cgks_alloc_fn alloc;
   cgks_free_fn free;

@@ -56,6 +56,7 @@ class CgksParams(C.Structure):
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
                 ("flux_lo", C.c_int32), ("flux_hi", C.c_int32), ("weno_vars", C.c_int32),
                 ("sweep_order", C.c_int32), ("sweep_part_cells", C.c_int32),
+                ("lo_viscous", C.c_int32), ("pad2_", C.c_int32),
                 ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_eps", C.c_double), ("weno_g0", C.c_double),
                 ("bc", CgksBC * MAX_BC),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
@@ -212,7 +213,7 @@ def make_params(spec: dict, stream=None, allocator=None) -> CgksParams:
         if key in spec:
             setattr(P, key, float(spec[key]))
     for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch",
-                "sweep_part_cells"):
+                "sweep_part_cells", "lo_viscous"):
         if key in spec:
             setattr(P, key, int(spec[key]))
     P.sweep_order = {"colour": SWEEP_COLOUR, "partitioned": SWEEP_PARTITIONED}[spec.get("sweep_order", "colour")]
@@ -410,7 +411,7 @@ class CgksServerOpts(C.Structure):
                 ("cfl_lo", C.c_double), ("n_implicit", C.c_int32), ("n_sweeps", C.c_int32),
                 ("max_active", C.c_int32), ("max_cycles", C.c_int32), ("use_graph", C.c_int32),
                 ("low_order_fused", C.c_int32), ("autotune", C.c_int32), ("programmatic_launch", C.c_int32),
-                ("flux_lo", C.c_int32), ("pad_", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("flux_lo", C.c_int32), ("lo_viscous", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class CgksReqStatus(C.Structure):
@@ -452,7 +453,8 @@ class Server:
         for key in ("cfl_hi", "cfl_lo"):
             if key in kw:
                 setattr(o, key, float(kw[key]))
-        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch"):
+        for key in ("n_implicit", "n_sweeps", "use_graph", "low_order_fused", "autotune", "programmatic_launch",
+                    "lo_viscous"):
             if key in kw:
                 setattr(o, key, int(kw[key]))
         self._alloc = None

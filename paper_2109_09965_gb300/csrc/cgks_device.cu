@@ -53,6 +53,7 @@ struct Shared {
   int weno_vars = CGKS_WENO_CONSERVATIVE;
   long long spin_limit = 0;      // grid-barrier polls of the persistent launch (0: kSpinLimit)
   int sweep_order = CGKS_SWEEP_COLOUR, part_cells = 2048;
+  int lo_viscous = 0;            // first-order viscous flux on the low-order level
   // serving batches: a per-solve flux class (smooth / limited) instead of
   // the batch-wide flux_hi and weno_eps; the limited class takes the full
   // flux with conservative compact WENO and the constants above
@@ -72,12 +73,12 @@ struct Member {
 
 // device tables of a batch (views into its arena)
 struct DevArrays {
-  double *vol, *ivol, *per, *ih, *m2, *op, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs;
+  double *vol, *ivol, *per, *ih, *m2, *op, *fn, *fS, *fjump, *fxi, *snx, *sny, *shs, *fidl = nullptr;
   double *mu, *bcuw, *bcrho, *bcu, *bcp;
   int *cface, *cnbr, *fc0, *fc1, *csid, *fsid, *bckind;
   unsigned char *ccol, *wenok;
   float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fn = nullptr, *f_fS = nullptr,
-        *f_fjump = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr, *f_mu = nullptr,
+        *f_fjump = nullptr, *f_fidl = nullptr, *f_fxi = nullptr, *f_snx = nullptr, *f_sny = nullptr, *f_shs = nullptr, *f_mu = nullptr,
         *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
 };
 
@@ -551,6 +552,7 @@ void fill_shared_params(const Shared &sh, ParamsT<T> &P) {
   P.weno_eps = static_cast<T>(sh.weno_eps);
   P.weno_g0 = static_cast<T>(sh.weno_g0);
   P.weno_vars = sh.weno_vars;
+  P.lo_viscous = sh.lo_viscous;
 }
 
 // The device arena of a batch: one allocation carved into 256-byte aligned
@@ -576,7 +578,7 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
   P8(&b->partial, 2 * std::max<int64_t>(N / kCellBlock, 1)); P8(&b->last, 4); P8(&b->res, S);
   P8(&d.vol, N); P8(&d.ivol, N); P8(&d.per, N); P8(&d.ih, N); P8(&d.m2, 3 * N); P8(&d.op, kNCol * kNM * N);
   P8(&d.snx, kMaxFace * N); P8(&d.sny, kMaxFace * N); P8(&d.shs, kMaxFace * N);
-  P8(&d.fn, 2 * F); P8(&d.fS, F); P8(&d.fjump, F); P8(&d.fxi, 8 * F);
+  P8(&d.fn, 2 * F); P8(&d.fS, F); P8(&d.fjump, F); P8(&d.fxi, 8 * F); P8(&d.fidl, F);
   P8(&d.mu, S); P8(&d.bcuw, 2 * T); P8(&d.bcrho, T); P8(&d.bcu, 2 * T); P8(&d.bcp, T);
   PI(&d.cface, kMaxFace * N); PI(&d.cnbr, kMaxFace * N); PI(&d.fc0, F); PI(&d.fc1, F); PI(&d.csid, N); PI(&d.fsid, F);
   PI(&d.bckind, T); PI(&b->list, std::max<int64_t>(L, 1)); PI(&b->perm, N); PI(&b->blk, 2 * S);
@@ -609,7 +611,7 @@ void plan_arena(Batch *b, int64_t N, int64_t F, int S, int64_t L, bool mixed, st
     if (b->sh.sweep_order == CGKS_SWEEP_PARTITIONED) P4(&X.dU2, 4 * N);
     P4(&d.f_ivol, N); P4(&d.f_ih, N); P4(&d.f_m2, 3 * N); P4(&d.f_op, kNCol * kNM * N);
     P4(&d.f_snx, kMaxFace * N); P4(&d.f_sny, kMaxFace * N); P4(&d.f_shs, kMaxFace * N);
-    P4(&d.f_fn, 2 * F); P4(&d.f_fS, F); P4(&d.f_fjump, F); P4(&d.f_fxi, 8 * F);
+    P4(&d.f_fn, 2 * F); P4(&d.f_fS, F); P4(&d.f_fjump, F); P4(&d.f_fxi, 8 * F); P4(&d.f_fidl, F);
     P4(&d.f_mu, S); P4(&d.f_bcuw, 2 * T); P4(&d.f_bcrho, T); P4(&d.f_bcu, 2 * T); P4(&d.f_bcp, T);
   }
 }
@@ -704,12 +706,14 @@ int create_batch(const Shared &sh, int64_t Ncap, int64_t Fcap, int S, cudaStream
   dm.nc = static_cast<int>(Ncap); dm.nf = static_cast<int>(Fcap);
   dm.vol = d.vol; dm.ivol = d.ivol; dm.per = d.per; dm.ih = d.ih; dm.m2 = d.m2; dm.op = d.op;
   dm.fn = d.fn; dm.fS = d.fS; dm.fjump = d.fjump; dm.fxi = d.fxi; dm.snx = d.snx; dm.sny = d.sny; dm.shs = d.shs;
+  dm.fidl = d.fidl;
   dm.cface = d.cface; dm.cnbr = d.cnbr; dm.fc0 = d.fc0; dm.fc1 = d.fc1; dm.csid = d.csid; dm.fsid = d.fsid;
   dm.ccol = d.ccol; dm.wenok = d.wenok;
   MeshT<float> &fm = b->fm;
   fm.nc = dm.nc; fm.nf = dm.nf;
   fm.vol = nullptr; fm.per = nullptr; fm.ivol = d.f_ivol; fm.ih = d.f_ih; fm.m2 = d.f_m2; fm.op = d.f_op;
   fm.fn = d.f_fn; fm.fS = d.f_fS; fm.fjump = d.f_fjump; fm.fxi = d.f_fxi; fm.snx = d.f_snx; fm.sny = d.f_sny;
+  fm.fidl = d.f_fidl;
   fm.shs = d.f_shs;
   fm.cface = d.cface; fm.cnbr = d.cnbr; fm.fc0 = d.fc0; fm.fc1 = d.fc1; fm.csid = d.csid; fm.fsid = d.fsid;
   fm.ccol = d.ccol; fm.wenok = d.wenok;
@@ -765,7 +769,7 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
   // local tables (np cells, nf faces) with global indices
   std::vector<double> vol(np, 1.0), ivol(np, 1.0), per(np, 4.0), ih(np, 1.0), m2(3 * np, 0.0),
       op(kNCol * kNM * np, 0.0), snx(kMaxFace * np, 0.0), sny(kMaxFace * np, 0.0), shs(kMaxFace * np, 0.0);
-  std::vector<double> fn(2 * nf), fS(nf), fjump(nf), fxi(8 * nf);
+  std::vector<double> fn(2 * nf), fS(nf), fjump(nf), fxi(8 * nf), fidl(nf);
   std::vector<int> cface(kMaxFace * np, kNoFace), cnbr(kMaxFace * np, -1), csid(np, -1), perm(np, 0), fc0(nf),
       fc1(nf), fsid(nf, s);
   std::vector<unsigned char> ccol(np, 255), wenok(np, 0);
@@ -803,6 +807,7 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
     fn[f] = hm.fn[f]; fn[nf + f] = hm.fn[nf + f];
     fS[f] = hm.fS[f];
     fjump[f] = hm.fdelta[f] > 0.0 ? p.alpha / hm.fdelta[f] : 0.0;
+    fidl[f] = hm.fdelta[f] > 0.0 ? 1.0 / hm.fdelta[f] : 0.0;
     for (int q = 0; q < 8; ++q) fxi[q * nf + f] = hm.fxi[q * nf + f];
   }
   std::vector<double> mu(1, p.mu), bc_uw(2 * kTagsPerSolve, 0.0), bc_rho(kTagsPerSolve, 1.0),
@@ -831,6 +836,7 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
   up(d.csid, csid, np, N, co); up(b->perm, perm, np, N, co); up(d.ccol, ccol, np, N, co);
   up(d.wenok, wenok, np, N, co);
   up(d.fn, fn, nf, F, fo); up(d.fS, fS, nf, F, fo); up(d.fjump, fjump, nf, F, fo); up(d.fxi, fxi, nf, F, fo);
+  up(d.fidl, fidl, nf, F, fo);
   up(d.fc0, fc0, nf, F, fo); up(d.fc1, fc1, nf, F, fo); up(d.fsid, fsid, nf, F, fo);
   up(d.mu, mu, 1, 1, s); up(d.bcuw, bc_uw, 2 * T, 0, 2 * T * s); up(d.bcrho, bc_rho, T, 0, T * s);
   up(d.bcu, bc_u, 2 * T, 0, 2 * T * s); up(d.bcp, bc_p, T, 0, T * s); up(d.bckind, bc_kind, T, 0, T * s);
@@ -845,6 +851,7 @@ int insert_solve(Batch *b, int s, const Member &m, int64_t cell_off, int64_t fac
     upf(d.f_op, op, np, N, co); upf(d.f_snx, snx, np, N, co); upf(d.f_sny, sny, np, N, co);
     upf(d.f_shs, shs, np, N, co);
     upf(d.f_fn, fn, nf, F, fo); upf(d.f_fS, fS, nf, F, fo); upf(d.f_fjump, fjump, nf, F, fo);
+    upf(d.f_fidl, fidl, nf, F, fo);
     upf(d.f_fxi, fxi, nf, F, fo);
     upf(d.f_mu, mu, 1, 1, s); upf(d.f_bcuw, bc_uw, 2 * T, 0, 2 * T * s); upf(d.f_bcrho, bc_rho, T, 0, T * s);
     upf(d.f_bcu, bc_u, 2 * T, 0, 2 * T * s); upf(d.f_bcp, bc_p, T, 0, T * s);
@@ -993,7 +1000,7 @@ int finalize_batch(Batch *b) {
   // the fused low-order launch: per-colour ranges of every active solve
   b->lo_fused_ok = false;
   // (the fused launch implements the KFVS low level only)
-  if (b->sh.lo_fused && b->sh.flux_lo == CGKS_FLUX_KFVS && b->lo_grid > 0 && C <= kMaxColFused &&
+  if (b->sh.lo_fused && b->sh.flux_lo == CGKS_FLUX_KFVS && !b->sh.lo_viscous && b->lo_grid > 0 && C <= kMaxColFused &&
       b->sweep_seq.size() <= 48 && N > 0) {
     std::vector<int> rstart(kMaxColFused + 1, 0), rbegin, rpre;
     for (int c = 0; c < C; ++c) {
@@ -1090,6 +1097,7 @@ Shared shared_from(const cgks_params *p) {
   sh.tau_c1 = p->tau_c1; sh.tau_c2 = p->tau_c2; sh.weno_eps = p->weno_eps; sh.weno_g0 = p->weno_g0;
   sh.weno_vars = p->weno_vars;
   sh.sweep_order = p->sweep_order;
+  sh.lo_viscous = p->lo_viscous;
   sh.part_cells = p->sweep_part_cells > 0 ? p->sweep_part_cells : 2048;
   sh.alloc = p->alloc; sh.free = p->free; sh.alloc_ctx = p->alloc_ctx;
   return sh;
@@ -1105,7 +1113,7 @@ int validate_params_tags(const cgks_params *p, const std::vector<int32_t> &tags_
       (p->weno_vars != CGKS_WENO_CONSERVATIVE && p->weno_vars != CGKS_WENO_CHARACTERISTIC) ||
       (p->sweep_order != CGKS_SWEEP_COLOUR && p->sweep_order != CGKS_SWEEP_PARTITIONED) ||
       (p->sweep_order == CGKS_SWEEP_PARTITIONED && p->low_order_fused) ||
-      (p->sweep_part_cells != 0 && p->sweep_part_cells < 64))
+      (p->sweep_part_cells != 0 && p->sweep_part_cells < 64) || (p->lo_viscous != 0 && p->lo_viscous != 1))
     return CGKS_EINVAL;
   for (int t : tags_used)
     if (t >= p->n_bc) return CGKS_EINVAL;
@@ -1705,7 +1713,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
       !(o->cfl_lo > 0.0) || o->n_implicit < 0 || o->n_sweeps < 0 ||
       (o->precision != CGKS_FP64 && o->precision != CGKS_MIXED) ||
       (o->time_scheme != CGKS_S1O2 && o->time_scheme != CGKS_S2O4) ||
-      (o->flux_lo != CGKS_FLUX_KFVS && o->flux_lo != CGKS_FLUX_LF))
+      (o->flux_lo != CGKS_FLUX_KFVS && o->flux_lo != CGKS_FLUX_LF) || (o->lo_viscous != 0 && o->lo_viscous != 1))
     return CGKS_EINVAL;
   *out = nullptr;
   int ndev = 0;
@@ -1718,6 +1726,7 @@ int cgks_server_create(size_t hbm_budget, const cgks_server_opts *o, cgks_server
   v->sh.autotune = o->autotune;
   v->sh.pdl = o->programmatic_launch;
   v->sh.flux_lo = o->flux_lo;
+  v->sh.lo_viscous = o->lo_viscous;
   v->sh.per_slot_flux = true;
   v->sh.weno_vars = CGKS_WENO_CONSERVATIVE;
   v->sh.alloc = o->alloc; v->sh.free = o->free; v->sh.alloc_ctx = o->alloc_ctx;
@@ -1777,6 +1786,7 @@ int cgks_server_submit(cgks_server *v, const cgks_mesh *m, const cgks_params *p,
   cgks_params q = *p;   // batch-wide fields come from the server
   q.cfl_hi = v->sh.cfl_hi; q.cfl_lo = v->sh.cfl_lo; q.n_implicit = v->sh.n_implicit; q.n_sweeps = v->sh.n_sweeps;
   q.time_scheme = v->sh.time_scheme; q.precision = v->sh.precision;
+  q.lo_viscous = v->sh.lo_viscous; q.flux_lo = v->sh.flux_lo;
   int rc = validate_params(&q, m->h);
   if (rc) return rc;
   // two flux classes per batch: smooth flux with linear weights, or the

@@ -32,8 +32,9 @@ struct Bufs3 {
 
 struct Geo3 {
   double *vol, *ivol, *ih, *hdt, *m2, *op, *fe, *fS, *fjump, *fw, *fxi, *sn, *shs, *bcuw, *bcrho, *bcu, *bcp;
+  double *fidl = nullptr;
   float *f_ivol = nullptr, *f_ih = nullptr, *f_m2 = nullptr, *f_op = nullptr, *f_fe = nullptr, *f_fS = nullptr,
-        *f_fjump = nullptr, *f_fw = nullptr, *f_fxi = nullptr, *f_sn = nullptr, *f_shs = nullptr,
+        *f_fjump = nullptr, *f_fidl = nullptr, *f_fw = nullptr, *f_fxi = nullptr, *f_sn = nullptr, *f_shs = nullptr,
         *f_bcuw = nullptr, *f_bcrho = nullptr, *f_bcu = nullptr, *f_bcp = nullptr;
   int *fng, *cface, *cnbr, *fc0, *fc1, *bckind;
   unsigned char *wenok;
@@ -280,7 +281,7 @@ void plan(Solver3 *s, std::vector<Piece3> &pc) {
   P8(&s->U, NV * N); P8(&s->Rp0, NV * N); P8(&s->Src, NV * N); P8(&s->stage, 4 * NV * N);
   P8(&s->partial, 2 * std::max<int64_t>(nblk(N, kCellBlock), 1)); P8(&s->last, 4);
   P8(&g.vol, N); P8(&g.ivol, N); P8(&g.ih, N); P8(&g.hdt, N); P8(&g.m2, 6 * N); P8(&g.op, kNCol3 * kNM3 * N);
-  P8(&g.fe, 9 * F); P8(&g.fS, F); P8(&g.fjump, F); P8(&g.fw, 4 * F); P8(&g.fxi, 24 * F);
+  P8(&g.fe, 9 * F); P8(&g.fS, F); P8(&g.fjump, F); P8(&g.fw, 4 * F); P8(&g.fxi, 24 * F); P8(&g.fidl, F);
   P8(&g.sn, 3 * kMaxFace3 * N); P8(&g.shs, kMaxFace3 * N);
   P8(&g.bcuw, 3 * CGKS_MAX_BC); P8(&g.bcrho, CGKS_MAX_BC); P8(&g.bcu, 3 * CGKS_MAX_BC); P8(&g.bcp, CGKS_MAX_BC);
   PI(&g.fng, F); PI(&g.cface, kMaxFace3 * N); PI(&g.cnbr, kMaxFace3 * N); PI(&g.fc0, F); PI(&g.fc1, F);
@@ -300,7 +301,7 @@ void plan(Solver3 *s, std::vector<Piece3> &pc) {
     P4(&X.rec, kRec * N); P4(&X.Flo, NV * F); P4(&X.lam, F); P4(&X.Rk, NV * N); P4(&X.invD, N);
     P4(&X.dU, kDU * N); P4(&X.lamS, kMaxFace3 * N);
     P4(&g.f_ivol, N); P4(&g.f_ih, N); P4(&g.f_m2, 6 * N); P4(&g.f_op, kNCol3 * kNM3 * N); P4(&g.f_fe, 9 * F);
-    P4(&g.f_fS, F); P4(&g.f_fjump, F); P4(&g.f_fw, 4 * F); P4(&g.f_fxi, 24 * F); P4(&g.f_sn, 3 * kMaxFace3 * N);
+    P4(&g.f_fS, F); P4(&g.f_fjump, F); P4(&g.f_fw, 4 * F); P4(&g.f_fxi, 24 * F); P4(&g.f_fidl, F); P4(&g.f_sn, 3 * kMaxFace3 * N);
     P4(&g.f_shs, kMaxFace3 * N); P4(&g.f_bcuw, 3 * CGKS_MAX_BC); P4(&g.f_bcrho, CGKS_MAX_BC);
     P4(&g.f_bcu, 3 * CGKS_MAX_BC); P4(&g.f_bcp, CGKS_MAX_BC);
   }
@@ -328,6 +329,7 @@ void fill_params(const cgks_params &p, ParamsT<T> &P) {
   P.tau_c2 = static_cast<T>(p.tau_c2);
   P.weno_eps = static_cast<T>(p.weno_eps);
   P.weno_g0 = static_cast<T>(p.weno_g0);
+  P.lo_viscous = p.lo_viscous;
 }
 
 #define CK3(x)                                  \
@@ -418,7 +420,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   std::vector<double> op;
   std::vector<unsigned char> wenok;
   build_operator3(m, wall, op, &wenok);
-  std::vector<double> ivol(N), ih(N), hdt(N), fe(9 * F), fjump(F), sn(3 * kMaxFace3 * N, 0.0), shs(kMaxFace3 * N, 0.0);
+  std::vector<double> ivol(N), ih(N), hdt(N), fe(9 * F), fjump(F), fidl(F), sn(3 * kMaxFace3 * N, 0.0), shs(kMaxFace3 * N, 0.0);
   for (int64_t i = 0; i < N; ++i) {
     ivol[i] = 1.0 / m.vol[i];
     ih[i] = 1.0 / m.h[i];
@@ -437,6 +439,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
     const double t2[3] = { n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0] };
     for (int d = 0; d < 3; ++d) { fe[d * F + f] = n[d]; fe[(3 + d) * F + f] = t1[d]; fe[(6 + d) * F + f] = t2[d]; }
     fjump[f] = m.fdelta[f] > 0.0 ? p->alpha / m.fdelta[f] : 0.0;
+    fidl[f] = m.fdelta[f] > 0.0 ? 1.0 / m.fdelta[f] : 0.0;
   }
   for (int64_t i = 0; i < N; ++i)
     for (int sl = 0; sl < kMaxFace3; ++sl) {
@@ -466,6 +469,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   up(g.vol, m.vol.data(), 8 * N); up(g.ivol, ivol.data(), 8 * N); up(g.ih, ih.data(), 8 * N);
   up(g.hdt, hdt.data(), 8 * N); up(g.m2, m.m2.data(), 8 * 6 * N); up(g.op, op.data(), 8 * op.size());
   up(g.fe, fe.data(), 8 * fe.size()); up(g.fS, m.fS.data(), 8 * F); up(g.fjump, fjump.data(), 8 * F);
+  up(g.fidl, fidl.data(), 8 * F);
   up(g.fw, m.fw.data(), 8 * 4 * F); up(g.fxi, m.fxi.data(), 8 * 24 * F); up(g.sn, sn.data(), 8 * sn.size());
   up(g.shs, shs.data(), 8 * shs.size()); up(g.bcuw, bcuw.data(), 8 * bcuw.size());
   up(g.bcrho, bcrho.data(), 8 * bcrho.size()); up(g.bcu, bcu.data(), 8 * bcu.size());
@@ -480,7 +484,7 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   };
   if (s->mixed) {
     upf(g.f_ivol, ivol); upf(g.f_ih, ih); upf(g.f_m2, m.m2); upf(g.f_op, op); upf(g.f_fe, fe);
-    upf(g.f_fS, m.fS); upf(g.f_fjump, fjump); upf(g.f_fw, m.fw); upf(g.f_fxi, m.fxi); upf(g.f_sn, sn);
+    upf(g.f_fS, m.fS); upf(g.f_fjump, fjump); upf(g.f_fidl, fidl); upf(g.f_fw, m.fw); upf(g.f_fxi, m.fxi); upf(g.f_sn, sn);
     upf(g.f_shs, shs); upf(g.f_bcuw, bcuw); upf(g.f_bcrho, bcrho); upf(g.f_bcu, bcu); upf(g.f_bcp, bcp);
   }
   if (ok) ok = cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), stream) == cudaSuccess &&
@@ -500,11 +504,13 @@ int s3_create(const HostMesh3 &m, const cgks_params *p, cudaStream_t stream, Tim
   dm.nc = static_cast<int>(N); dm.nf = static_cast<int>(F);
   dm.vol = g.vol; dm.ivol = g.ivol; dm.ih = g.ih; dm.hdt = g.hdt; dm.m2 = g.m2; dm.op = g.op;
   dm.fe = g.fe; dm.fS = g.fS; dm.fjump = g.fjump; dm.fw = g.fw; dm.fxi = g.fxi; dm.sn = g.sn; dm.shs = g.shs;
+  dm.fidl = g.fidl;
   dm.fng = g.fng; dm.cface = g.cface; dm.cnbr = g.cnbr; dm.fc0 = g.fc0; dm.fc1 = g.fc1;
   MeshT<float> &fm = s->fm;
   fm.nc = dm.nc; fm.nf = dm.nf;
   fm.vol = nullptr; fm.hdt = nullptr; fm.ivol = g.f_ivol; fm.ih = g.f_ih; fm.m2 = g.f_m2; fm.op = g.f_op;
   fm.fe = g.f_fe; fm.fS = g.f_fS; fm.fjump = g.f_fjump; fm.fw = g.f_fw; fm.fxi = g.f_fxi; fm.sn = g.f_sn;
+  fm.fidl = g.f_fidl;
   fm.shs = g.f_shs; fm.fng = g.fng; fm.cface = g.cface; fm.cnbr = g.cnbr; fm.fc0 = g.fc0; fm.fc1 = g.fc1;
   *out = S.release();
   return CGKS_OK;

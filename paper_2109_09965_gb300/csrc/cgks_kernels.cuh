@@ -57,6 +57,7 @@ struct ParamsT {
   // flux.  With it each instantiation of k_recon / k_face treats only the
   // solves of its own class.
   const int *slim;
+  int lo_viscous;                // 1: the low-order residual carries a first-order viscous flux
 };
 
 template <typename T>
@@ -65,6 +66,7 @@ struct MeshT {
   const T *vol, *ivol, *per, *ih, *m2;       // ih = 1/h; m2: [3][nc]
   const T *op;                               // [kNCol*kNM][nc]
   const T *fn, *fS, *fjump, *fxi;            // fn [2][nf], fjump = alpha/delta, fxi [8][nf]
+  const T *fidl;                             // 1/delta: the centre distance along n (boundary: twice to the face)
   const T *snx, *sny, *shs;                  // [4][nc] per face slot: outward normal of the cell, S/2
   const int *cface, *cnbr;                   // [4][nc]
   const int *fc0, *fc1;
@@ -765,6 +767,19 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
     T Fl[4];
     D::kfvs_prims(P.K, a.rho, una, uta, a.i2l, a.sl, a.isp, b.rho, unb, utb, b.i2l, b.sl, b.isp, Fl);
     D::rot_out(nx, ny, Fl, F);
+  }
+  if (P.lo_viscous && mu > T(0)) {
+    // first-order viscous flux: normal gradients from the two cell states
+    // over the centre distance delta, Stokes' hypothesis, Pr = 1 heat flux
+    //   tau.n = mu / delta (du + (n.du) n / 3),  q.n = -kappa (T_r - T_l) / delta
+    const T md = mu * m.fidl[f];
+    const T dux = b.u - a.u, duy = b.v - a.v;
+    const T dn = (dux * nx + duy * ny) / T(3);
+    const T tx = md * (dux + dn * nx), ty = md * (duy + dn * ny);
+    const T qn = -md * P.gamma / (P.gamma - T(1)) * (b.p * b.ir - a.p * a.ir);
+    F[1] -= tx;
+    F[2] -= ty;
+    F[3] -= tx * (T(0.5) * (a.u + b.u)) + ty * (T(0.5) * (a.v + b.v)) - qn;
   }
   for (int v = 0; v < 4; ++v) Flo[v * nf + f] = F[v];
   if (E0) {

@@ -39,6 +39,7 @@ struct ParamsT {
   int flux_lo;                    // low-level flux: CGKS_FLUX_KFVS or CGKS_FLUX_LF
   T tau_c1, tau_c2;               // numerical collision time constants of the full flux
   T weno_eps, weno_g0;            // compact WENO epsilon (0: linear weights), linear weight of P2
+  int lo_viscous;                 // 1: the low-order residual carries a first-order viscous flux
 };
 
 template <typename T>
@@ -46,6 +47,7 @@ struct MeshT {
   int nc, nf;
   const T *vol, *ivol, *ih, *hdt, *m2, *op;       // m2 [6][nc], op [27*9][nc]
   const T *fe, *fS, *fjump, *fw, *fxi;            // fe [9][nf] (n, t1, t2), fw [4][nf], fxi [24][nf]
+  const T *fidl;                                  // 1/delta: centre distance along n (boundary: twice to the face)
   const T *sn, *shs;                              // [6*3][nc] outward normal per slot, [6][nc] S/2
   const int *fng, *cface, *cnbr, *fc0, *fc1;
 };
@@ -664,6 +666,25 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
     D3::kfvs(P.K, a.rho, la3[0], la3[1], la3[2], a.i2l, a.sl, a.isp, b.rho, lb3[0], lb3[1], lb3[2], b.i2l, b.sl,
              b.isp, Fl);
     D3::rot_out(F, Fl, Fg);
+  }
+  if (P.lo_viscous && P.mu > T(0)) {
+    // first-order viscous flux: normal gradients from the two cell states
+    // over the centre distance delta, Stokes' hypothesis, Pr = 1 heat flux
+    //   tau.n = mu / delta (du + (n.du) n / 3),  q.n = -kappa (T_r - T_l) / delta
+    const T md = P.mu * m.fidl[f];
+    const T du[3] = { b.u - a.u, b.v - a.v, b.w - a.w };
+    const T nn[3] = { nx, ny, nz };
+    const T dn = (du[0] * nx + du[1] * ny + du[2] * nz) / T(3);
+    const T um[3] = { T(0.5) * (a.u + b.u), T(0.5) * (a.v + b.v), T(0.5) * (a.w + b.w) };
+    T work = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T tau = md * (du[d] + dn * nn[d]);
+      Fg[1 + d] -= tau;
+      work += tau * um[d];
+    }
+    const T qn = -md * P.gamma / (P.gamma - T(1)) * (b.p * b.ir - a.p * a.ir);
+    Fg[4] -= work - qn;
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) Flo[v * nf + f] = Fg[v];
