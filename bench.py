@@ -548,12 +548,13 @@ def work_model3(mesh, gm, spec, precision, _cache={}):
             "gauss_points": gps, "colours": C, "sweep_launches": ni * len(seq)}
 
 
-def sphere_case(level, n_prism, n_tet, h0, ma, re):
+def sphere_case(level, n_prism, n_tet, h0, ma, re, extra=None):
     from paper_2109_09965_gb300 import meshgen
     mesh = meshgen.sphere(level, n_prism, n_tet, h0=h0)
     spec = dict(gamma=GAMMA, mu=ma * 1.0 / re, cfl_hi=0.4, cfl_lo=1000.0, n_implicit=6, n_sweeps=2,
                 time_scheme="S1O2", bcs=[dict(kind="noslip"),
-                                         dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0), p=1.0 / GAMMA)])
+                                         dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0), p=1.0 / GAMMA)],
+                **(extra or {}))
     W = np.zeros((mesh.n_cells, 5))
     W[:, 0] = 1.0
     W[:, 1] = ma
@@ -561,25 +562,29 @@ def sphere_case(level, n_prism, n_tet, h0, ma, re):
     return mesh, spec, W
 
 
+# the thin-wall-layer setting of the stated sphere construction: the viscous
+# low-order flux and the compact WENO weights (eps 1e-2), the settings under
+# which its V-cycle converges furthest
+THIN_LAYER = dict(lo_viscous=1, weno_eps=1e-2)
 # the 3-D throughput workloads: (level, prism layers, split-tet layers, first
-# layer / D, Ma, Re, timed cycles, description)
+# layer / D, Ma, Re, timed cycles, description, extra settings)
 SPHERES = {
-    "sphere512k": (4, 40, 20, 5e-3, 0.2, 118, 30,
+    "sphere512k": (4, 40, 20, 1e-3, 0.2, 118, 30,
                    "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism "
-                   "layers (growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: 512,000 cells; "
-                   "first layer 5e-3 D instead of 1e-3 D (the V-cycle diverges on the thinner layer)"),
+                   "layers (first 1e-3 D, growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: "
+                   "512,000 cells; viscous low-order flux and compact WENO (eps 1e-2)", THIN_LAYER),
     "sphere3M": (5, 60, 30, 1e-3, 0.2, 1000, 10,
                  "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
                  "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
                  "(throughput of the smooth path; the Ma 1.5 case with the full flux and WENO is the "
-                 "supersonic_sphere entry)"),
+                 "supersonic_sphere entry)", {}),
 }
 
 
 def sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, level, n_prism, n_tet, h0, ma, re, steps,
-                 note, precisions=("fp64", "mixed")):
+                 note, extra=None, precisions=("fp64", "mixed")):
     t0 = time.perf_counter()
-    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, ma, re)
+    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, ma, re, extra)
     gm = cgks.Mesh(mesh)
     prep = time.perf_counter() - t0
     out = {"workload": note, "n_cells": mesh.n_cells, "n_faces": gm.n_faces, "mesh_prep_s": prep}
@@ -640,7 +645,7 @@ def main():
             hbm, hbm_src = peaks()
             case3 = SPHERES[args.only_3d]
             emit({"block": "workloads_3d", "workloads_3d": {args.only_3d: sphere_bench(
-                cgks, args, 1, local, flush, hbm, hbm_src, args.only_3d, *case3[:7], case3[7],
+                cgks, args, 1, local, flush, hbm, hbm_src, args.only_3d, *case3[:7], case3[7], case3[8],
                 precisions=(args.precision,))}})
         return
     if args.shock_only:
@@ -675,7 +680,7 @@ def main():
         # (3-D, serving, convergence) are single-GPU runs
         args.no_3d, args.serving, args.no_convergence, args.converge = True, "none", True, False
     if not args.no_3d:
-        w3 = {name: sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, *c[:7], c[7])
+        w3 = {name: sphere_bench(cgks, args, world, local, flush, hbm, hbm_src, name, *c[:7], c[7], c[8])
               for name, c in SPHERES.items()}
         emit({"block": "workloads_3d", "workloads_3d": w3})
         legs["sphere512k"] = {k: w3["sphere512k"][k]["value"] for k in ("fp64", "mixed")}
@@ -728,6 +733,9 @@ def main():
                               "cells; p-multigrid to a 1e-8 drop of Res relative to the first cycle (FP64), then "
                               "the mixed path over the same cycles")
             emit({"block": "convergence_3d", "convergence_3d": c3})
+            c3s = config3_stated(cgks)
+            emit({"block": "config3_stated", "config3_stated": c3s})
+            legs["config3_stated"] = {k: c3s.get(k) for k in ("cycles", "drop_min", "Cd", "diverged")}
             emit({"block": "supersonic_sphere", "supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)})
     line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
@@ -956,6 +964,41 @@ def validation_re40(cgks, max_cycles=8000, drop=1e-8):
             "wake_length_D": post.wake_length(xc, W, R=0.5, D=D, angle_band=2 * math.pi / nt),
             "Cp_front": float(surf["Cp"][0]),
             "paper_mesh_II": {"Cd": 1.525, "Cl": 3.3e-14, "wake_length_D": 2.22, "separation_angle_deg": 53.3}}
+
+
+def config3_stated(cgks, cycles=1500):
+    """Configuration 3 at its stated construction (icosphere level 4, 40
+    prism layers from a first layer of 1e-3 D, 20 split-tet layers;
+    512,000 cells), Re 118, Ma 0.2, mixed precision, viscous low-order flux
+    and compact WENO: V-cycles from the impulsive start, the Res drop they
+    reach and the drag from the wall loads."""
+    import torch
+    from paper_2109_09965_gb300 import post
+    mesh, spec, W0 = sphere_case(4, 40, 20, 1e-3, 0.2, 118, THIN_LAYER)
+    s = cgks.Solver(cgks.Mesh(mesh), dict(spec, precision="mixed"))
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h, err = [], None
+    try:
+        while len(h) < cycles:
+            h.extend(s.pmg_cycle(100).tolist())
+    except cgks.CgksError as e:
+        err = str(e).split(":")[-1].strip()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    out = {"workload": "3-D laminar sphere, Re 118, Ma 0.2, configuration 3 as stated: icosphere level 4, 40 prism "
+                       "layers from 1e-3 D (growth 1.1), 20 split-tet layers, 512,000 cells; mixed precision, "
+                       "viscous low-order flux, compact WENO eps 1e-2, impulsive start",
+           "cycles": len(h), "wall_s": el, "diverged": err}
+    if h:
+        hh = np.asarray(h)
+        out.update(res_first=float(hh[0]), drop_min=float(hh.min() / hh[0]), drop_last=float(hh[-1] / hh[0]),
+                   history=[float(x / hh[0]) for x in hh[::max(1, len(hh) // 15)]])
+    if err is None:
+        out["Cd"] = float(post.force_coefficients(s.wall_loads(0), rho=1.0, U=0.2, ref=math.pi / 4.0)[0])
+    s.close()
+    return out
 
 
 def converge3d(cgks, level, n_prism, n_tet, h0, drop=1e-8, max_cycles=6000):
