@@ -26,7 +26,8 @@ inline int nblk(int64_t n, int b) { return static_cast<int>((n + b - 1) / b); }
 template <typename T>
 struct Bufs3 {
   T *W = nullptr, *Wx = nullptr, *Wn = nullptr, *Ws = nullptr, *Wxs = nullptr, *U = nullptr;
-  T *coef = nullptr, *FA = nullptr, *FB = nullptr, *rec = nullptr, *Flo = nullptr, *lam = nullptr;
+  T *coef = nullptr, *FA = nullptr, *FB = nullptr, *rec = nullptr;
+  T *Flo = nullptr;   // [F][kLo]: low-level flux and lambda_p per face
   T *E0 = nullptr, *E1 = nullptr, *Rk = nullptr, *invD = nullptr, *dU = nullptr, *lamS = nullptr;
 };
 
@@ -164,15 +165,15 @@ void hi_step(Solver3 *s, double *Wout, TF *Wout_m, bool want_res) {
   const dim3 g(nblk(s->N, kCellBlock)), blk(kCellBlock);
   hi_eval<TF>(s, B.W, B.Wx, B.FA);
   if (s->P.time_scheme == CGKS_S1O2) {
-    launch(s, KI_UPDATE, k_update<TF>, g, blk, s->dm, s->dp, (int)kS1O2, (const double *)s->W, (const TF *)B.FA,
+    launch(s, KI_UPDATE, k_update<TF, kS1O2>, g, blk, s->dm, s->dp, (const double *)s->W, (const TF *)B.FA,
            (const TF *)B.FA, (const Ctl *)s->ctl, (const unsigned long long *)s->dt_bits, s->status, Wout, s->Wx,
            part, s->Rp0, Wout_m, mirror<TF>(B.Wx));
   } else {
-    launch(s, KI_UPDATE, k_update<TF>, g, blk, s->dm, s->dp, (int)kS2O4Stage, (const double *)s->W, (const TF *)B.FA,
+    launch(s, KI_UPDATE, k_update<TF, kS2O4Stage>, g, blk, s->dm, s->dp, (const double *)s->W, (const TF *)B.FA,
            (const TF *)B.FA, (const Ctl *)s->ctl, (const unsigned long long *)s->dt_bits, s->status, s->Ws, s->Wxs,
            (double *)nullptr, (double *)nullptr, mirror<TF>(B.Ws), mirror<TF>(B.Wxs));
     hi_eval<TF>(s, B.Ws, B.Wxs, B.FB);
-    launch(s, KI_UPDATE, k_update<TF>, g, blk, s->dm, s->dp, (int)kS2O4Final, (const double *)s->W, (const TF *)B.FA,
+    launch(s, KI_UPDATE, k_update<TF, kS2O4Final>, g, blk, s->dm, s->dp, (const double *)s->W, (const TF *)B.FA,
            (const TF *)B.FB, (const Ctl *)s->ctl, (const unsigned long long *)s->dt_bits, s->status, Wout, s->Wx,
            part, s->Rp0, Wout_m, mirror<TF>(B.Wx));
   }
@@ -191,11 +192,11 @@ void lo_solve(Solver3 *s) {
       with_shape(s->tune.shape(TK_LOFACE), [&](auto sh) {
         constexpr int S = decltype(sh)::value;
         launch(s, KI_LOFACE, k_lo_face<TF, S>, dim3(nblk(s->F, shape_bs(S) * shape_ipt(S))), dim3(shape_bs(S)),
-               fmesh<TF>(s), fpar<TF>(s), (const TF *)B.rec, B.Flo, B.lam, B.E0, B.E1);
+               fmesh<TF>(s), fpar<TF>(s), (const TF *)B.rec, B.Flo, B.E0, B.E1);
       });
     });
     launch(s, KI_LORHS, k_lo_rhs<TF>, gc, blk, s->dm, s->dp, k == 0 ? 1 : 0, colour0_end, (const TF *)B.Flo,
-           (const TF *)B.lam, (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU, B.lamS);
+           (const double *)s->Rp0, s->Src, B.Rk, B.invD, B.dU, B.lamS);
     for (int c : s->sweep_seq) {
       const int beg = s->colour_start[c], cnt = s->colour_start[c + 1] - beg;
       tuned_launch(s->tune, TK_SWEEP, s->stream, [&] {
@@ -228,7 +229,7 @@ void cycle_t(Solver3 *s) {
   enqueue_dt(s, -1.0);
   hi_step<TF>(s, s->Wn, mirror<TF>(B.Wn), false);
   hi_eval<TF>(s, B.Wn, B.Wx, B.FB);
-  launch(s, KI_UPDATE, k_update<TF>, dim3(nblk(s->N, kCellBlock)), dim3(kCellBlock), s->dm, s->dp, (int)kResidual,
+  launch(s, KI_UPDATE, k_update<TF, kResidual>, dim3(nblk(s->N, kCellBlock)), dim3(kCellBlock), s->dm, s->dp,
          (const double *)s->Wn, (const TF *)B.FB, (const TF *)B.FB, (const Ctl *)s->ctl,
          (const unsigned long long *)s->dt_bits, s->status, (double *)nullptr, (double *)nullptr, (double *)nullptr,
          s->Rp0, (TF *)nullptr, (TF *)nullptr);
@@ -292,13 +293,13 @@ void plan(Solver3 *s, std::vector<Piece3> &pc) {
   if (!s->mixed) {
     Bufs3<double> &X = s->bd;
     P8(&X.coef, kNM3 * NV * N); P8(&X.FA, 4 * NV * F); P8(&X.FB, 4 * NV * F); P8(&X.rec, kRec * N);
-    P8(&X.Flo, NV * F); P8(&X.lam, F); P8(&X.E0, NV * F); P8(&X.E1, NV * F); P8(&X.Rk, NV * N); P8(&X.invD, N);
+    P8(&X.Flo, kLo * F); P8(&X.E0, kEu * F); P8(&X.E1, kEu * F); P8(&X.Rk, NV * N); P8(&X.invD, N);
     P8(&X.dU, kDU * N); P8(&X.lamS, kMaxFace3 * N);
   } else {
     Bufs3<float> &X = s->bf;
     P4(&X.W, NV * N); P4(&X.Wx, 3 * NV * N); P4(&X.Wn, NV * N); P4(&X.Ws, NV * N); P4(&X.Wxs, 3 * NV * N);
     P4(&X.coef, kNM3 * NV * N); P4(&X.FA, 4 * NV * F); P4(&X.FB, 4 * NV * F);
-    P4(&X.rec, kRec * N); P4(&X.Flo, NV * F); P4(&X.lam, F); P4(&X.Rk, NV * N); P4(&X.invD, N);
+    P4(&X.rec, kRec * N); P4(&X.Flo, kLo * F); P4(&X.Rk, NV * N); P4(&X.invD, N);
     P4(&X.dU, kDU * N); P4(&X.lamS, kMaxFace3 * N);
     P4(&g.f_ivol, N); P4(&g.f_ih, N); P4(&g.f_m2, 6 * N); P4(&g.f_op, kNCol3 * kNM3 * N); P4(&g.f_fe, 9 * F);
     P4(&g.f_fS, F); P4(&g.f_fjump, F); P4(&g.f_fw, 4 * F); P4(&g.f_fxi, 24 * F); P4(&g.f_fidl, F); P4(&g.f_sn, 3 * kMaxFace3 * N);
@@ -650,9 +651,9 @@ int s3_wall_loads_t(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces
   if (s->P.flux_hi == CGKS_FLUX_FULL) enqueue_dt(s, -1.0);   // the full flux integrates over a step
   hi_eval<TF>(s, B.W, B.Wx, B.FA);
   const int64_t F = s->F;
-  std::vector<TF> F0(3 * static_cast<size_t>(F));
-  for (int v = 1; v <= 3; ++v)
-    CK3(cudaMemcpyAsync(F0.data() + (v - 1) * F, B.FA + v * F, sizeof(TF) * F, cudaMemcpyDeviceToHost, s->stream));
+  // the face outputs, one run of kFO values per face: F0 is the first NV
+  std::vector<TF> FO(static_cast<size_t>(kFO) * F);
+  CK3(cudaMemcpyAsync(FO.data(), B.FA, sizeof(TF) * FO.size(), cudaMemcpyDeviceToHost, s->stream));
   CK3(cudaStreamSynchronize(s->stream));
   int64_t k = 0;
   for (size_t b = 0; b < s->bf_face.size(); ++b) {
@@ -663,7 +664,7 @@ int s3_wall_loads_t(Solver3 *s, int32_t tag, int64_t max_faces, int64_t *n_faces
       for (int a = 0; a < 3; ++a) {
         x[3 * k + a] = g[a];
         nrm[3 * k + a] = g[3 + a];
-        traction[3 * k + a] = static_cast<double>(F0[a * F + f]);
+        traction[3 * k + a] = static_cast<double>(FO[static_cast<size_t>(f) * kFO + 1 + a]);
       }
       S[k] = g[6];
     }

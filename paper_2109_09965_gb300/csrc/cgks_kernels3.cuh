@@ -24,6 +24,9 @@ namespace D3 = cgks::dev3;
 constexpr int NV = 5;
 constexpr int kCellBlock = 256;
 constexpr int kSweepLanes = 8;                     // lanes per cell (6 face slots)
+constexpr int kFO = 4 * NV;                        // face outputs of the high level: F0, F1, Wc, Wt
+constexpr int kLo = 8;                             // low-level face run: flux (NV), lambda_p, 2 pad
+constexpr int kEu = 6;                             // Euler flux cache run of one face side: NV, 1 pad
 constexpr int kBadState = 1;
 
 template <typename T>
@@ -335,7 +338,9 @@ __device__ __forceinline__ void recon_point(const MeshT<T> &m, const T *__restri
 }
 
 // K2: smooth GKS flux and interface state at the Gauss points of every face:
-// out[(k*5 + v)][nf], k = 0 F0, 1 F1, 2 Wc, 3 Wt, weighted sums, global frame
+// out[f][k*5 + v], k = 0 F0, 1 F1, 2 Wc, 3 Wt, weighted sums, global frame:
+// one run of kFO values per face (AoS), so that the cells gathering a face
+// read it in one piece
 template <typename T, bool FULL>
 __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ W,
                                         const T *__restrict__ coef, T *__restrict__ out, const Ctl *ctl,
@@ -428,10 +433,12 @@ __device__ __forceinline__ void face_at(const MeshT<T> &m, const ParamsT<T> &P, 
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[3][v] += wk * gq[v];
   }
+  T o[kFO];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[(k * NV + v) * nf + f] = acc[k][v];
+    for (int v = 0; v < NV; ++v) o[k * NV + v] = acc[k][v];
+  vstore<T, kFO>(out + static_cast<size_t>(f) * kFO, o);
 }
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
@@ -455,8 +462,11 @@ enum UpdMode { kS1O2 = 0, kS2O4Stage = 1, kS2O4Final = 2, kResidual = 3 };
 // K3: per cell gather of the face sums in FP64 (see the 2-D k_update):
 //   R = -sum sgn S (a0 F0A + a1 F1(A, B));  W_out = W_base + dt/|Omega| R;
 //   Wx_out = 1/|Omega| sum sgn S n (WcA + b1 Wt)
-template <typename TF>
-__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P, int mode,
+// The mode is a template argument so that each variant holds only the runs
+// it reads: the residual reads F0 and F1 of one buffer, the stages one
+// whole run, the final S2O4 stage two.
+template <typename TF, int mode>
+__global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<double> P,
                                                        const double *__restrict__ Wbase, const TF *__restrict__ FA,
                                                        const TF *__restrict__ FB, const Ctl *ctl,
                                                        const unsigned long long *dt_bits, int *status,
@@ -465,16 +475,15 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
                                                        TF *__restrict__ Wout_m, TF *__restrict__ Wxout_m) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = m.nc, nf = m.nf;
+  const int n = m.nc;
   double num = 0.0, den = 0.0;
   if (i < n) {
     const double dt = dt_of(ctl, dt_bits, P.cfl_hi);
     double a0, a1, b1;
-    const TF *FW = FA;
     switch (mode) {
       case kS1O2: a0 = 1.0; a1 = 0.5 * dt; b1 = dt; break;
       case kS2O4Stage: a0 = 0.5; a1 = 0.125 * dt; b1 = 0.5 * dt; break;
-      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; FW = FB; break;
+      case kS2O4Final: a0 = 1.0; a1 = dt / 6.0; b1 = dt; break;
       default: a0 = 1.0; a1 = 0.5 * dt; b1 = 0.0; break;
     }
     double R[NV] = { 0, 0, 0, 0, 0 }, g[3][NV] = { { 0 } };
@@ -483,15 +492,26 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
       if (fs == kNoFace) continue;
       const int f = fs >= 0 ? fs : ~fs;
       const double sg = fs >= 0 ? 1.0 : -1.0;
-      const double S = m.fS[f];
-      const double nx = m.fe[f], ny = m.fe[nf + f], nz = m.fe[2 * nf + f];
+      // the slot's area and outward normal from the per-cell slot arrays
+      // (coalesced; the same values as S_f and sg n_f, exactly)
+      const double S = 2.0 * m.shs[s * n + i];
+      const double nx = sg * m.sn[(3 * s) * n + i], ny = sg * m.sn[(3 * s + 1) * n + i],
+                   nz = sg * m.sn[(3 * s + 2) * n + i];
+      // the face's run of F0, F1, Wc, Wt (and the second stage's, when used);
+      // the residual reads the leading F0, F1 part only
+      constexpr int kRes = (2 * NV + VecOf<TF>::W - 1) / VecOf<TF>::W * VecOf<TF>::W;
+      TF a[kFO], b[kFO];
+      if constexpr (mode == kResidual) vload<TF, kRes>(FA + static_cast<size_t>(f) * kFO, a);
+      else vload<TF, kFO>(FA + static_cast<size_t>(f) * kFO, a);
+      if constexpr (mode == kS2O4Final) vload<TF, kFO>(FB + static_cast<size_t>(f) * kFO, b);
+      const TF *wt = mode == kS2O4Final ? b : a;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double f1 = static_cast<double>(FA[(NV + v) * nf + f]);
-        if (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(FB[(NV + v) * nf + f]);
-        R[v] -= sg * S * (a0 * static_cast<double>(FA[v * nf + f]) + a1 * f1);
-        if (mode != kResidual) {
-          const double wp = static_cast<double>(FA[(2 * NV + v) * nf + f]) + b1 * static_cast<double>(FW[(3 * NV + v) * nf + f]);
+        double f1 = static_cast<double>(a[NV + v]);
+        if constexpr (mode == kS2O4Final) f1 += 2.0 * static_cast<double>(b[NV + v]);
+        R[v] -= sg * S * (a0 * static_cast<double>(a[v]) + a1 * f1);
+        if constexpr (mode != kResidual) {
+          const double wp = static_cast<double>(a[2 * NV + v]) + b1 * static_cast<double>(wt[3 * NV + v]);
           g[0][v] += sg * S * nx * wp;
           g[1][v] += sg * S * ny * wp;
           g[2][v] += sg * S * nz * wp;
@@ -501,7 +521,7 @@ __global__ void __launch_bounds__(kCellBlock) k_update(MeshT<double> m, ParamsT<
     if (Rout)
 #pragma unroll
       for (int v = 0; v < NV; ++v) Rout[v * n + i] = R[v];
-    if (mode != kResidual) {
+    if constexpr (mode != kResidual) {
       const double iv = m.ivol[i];
       double w[NV];
 #pragma unroll
@@ -615,7 +635,7 @@ __device__ __forceinline__ void lo_ghost(const ParamsT<T> &P, int tag, const D3:
 // KFVS flux, lambda_p = max of both sides, Euler flux cache (FP64 mode)
 template <typename T>
 __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &P, const T *__restrict__ rec,
-                                           T *__restrict__ Flo, T *__restrict__ lam, T *__restrict__ E0,
+                                           T *__restrict__ Flo, T *__restrict__ E0,
                                            T *__restrict__ E1, const int f) {
   const int nf = m.nf;
   const int c0 = m.fc0[f], c1 = m.fc1[f];
@@ -646,7 +666,6 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
   const T la = fabs(la3[0]) + a.c + T(2) * (P.mu * a.ir) * S * m.ivol[c0];
   const T lb = fabs(lb3[0]) + b.c + T(2) * (P.mu * b.ir) * S * ivb;
   const T lmax = la > lb ? la : lb;
-  lam[f] = lmax;
   // Euler normal fluxes of the two sides (the L-F flux, the FP64 cache)
   const T nx = F.e[0][0], ny = F.e[0][1], nz = F.e[0][2];
   const T una = la3[0], unb = lb3[0];
@@ -686,22 +705,34 @@ __device__ __forceinline__ void lo_face_at(const MeshT<T> &m, const ParamsT<T> &
     const T qn = -md * P.gamma / (P.gamma - T(1)) * (b.p * b.ir - a.p * a.ir);
     Fg[4] -= work - qn;
   }
+  // one run per face (AoS): the flux and lambda_p, read together by the
+  // right-hand side of each cell
+  T o[kLo];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Flo[v * nf + f] = Fg[v];
-  if (E0) {
+  for (int v = 0; v < NV; ++v) o[v] = Fg[v];
+  o[NV] = lmax;
+  o[NV + 1] = o[NV + 2] = T(0);
+  vstore<T, kLo>(Flo + static_cast<size_t>(f) * kLo, o);
+  if constexpr (!is_f32<T>())
+  if (E0) {   // the FP64 path's cache (the mixed path has none)
+    T e[kEu];
+    e[NV] = T(0);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) E0[v * nf + f] = Fa[v];
-    if (c1 >= 0)
+    for (int v = 0; v < NV; ++v) e[v] = Fa[v];
+    vstore<T, kEu>(E0 + static_cast<size_t>(f) * kEu, e);
+    if (c1 >= 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) E1[v * nf + f] = Fb[v];
+      for (int v = 0; v < NV; ++v) e[v] = Fb[v];
+      vstore<T, kEu>(E1 + static_cast<size_t>(f) * kEu, e);
+    }
   }
 }
 template <typename T, int SH>
 __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
-    k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ rec, T *__restrict__ Flo, T *__restrict__ lam,
+    k_lo_face(MeshT<T> m, ParamsT<T> P, const T *__restrict__ rec, T *__restrict__ Flo,
               T *__restrict__ E0, T *__restrict__ E1) {
   pdl_enter();
-  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, rec, Flo, lam, E0, E1, f); });
+  for_items<SH>(m.nf, [&](int f) { lo_face_at(m, P, rec, Flo, E0, E1, f); });
   pdl_exit();
 }
 
@@ -709,24 +740,26 @@ __global__ void __launch_bounds__(shape_bs(SH), shape_minb(SH))
 // first colour pass (dU = R / D on colour 0, zero elsewhere)
 template <typename TF>
 __global__ void __launch_bounds__(kCellBlock) k_lo_rhs(MeshT<double> m, ParamsT<double> P, int first, int colour0_end,
-                                                       const TF *__restrict__ Flo, const TF *__restrict__ lam,
+                                                       const TF *__restrict__ Flo,
                                                        const double *__restrict__ Rp0, double *__restrict__ Src,
                                                        TF *__restrict__ Rk, TF *__restrict__ invD, TF *__restrict__ dU,
                                                        TF *__restrict__ lamS) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.nc) return;
-  const int n = m.nc, nf = m.nf;
+  const int n = m.nc;
   double R[NV] = { 0, 0, 0, 0, 0 }, sum = 0.0;
   for (int s = 0; s < kMaxFace3; ++s) {
     const int fs = m.cface[s * n + i];
     if (fs == kNoFace) { lamS[s * n + i] = TF(0); continue; }
     const int f = fs >= 0 ? fs : ~fs;
     const double sg = fs >= 0 ? 1.0 : -1.0;
-    const double S = m.fS[f];
+    const double S = 2.0 * m.shs[s * n + i];   // S_f, from the per-cell slot array (coalesced)
+    TF fl[kLo];
+    vload<TF, kLo>(Flo + static_cast<size_t>(f) * kLo, fl);   // flux and lambda_p
 #pragma unroll
-    for (int v = 0; v < NV; ++v) R[v] -= sg * S * static_cast<double>(Flo[v * nf + f]);
-    const TF l = lam[f];
+    for (int v = 0; v < NV; ++v) R[v] -= sg * S * static_cast<double>(fl[v]);
+    const TF l = fl[NV];
     lamS[s * n + i] = l;
     sum += static_cast<double>(l) * S;
   }
@@ -812,13 +845,14 @@ __device__ __forceinline__ void sweep_cell(const MeshT<T> &m, const ParamsT<T> &
       for (int v = 0; v < NV; ++v) c[v] = hS * (dF[v] - lp * du[v]);
     } else {
       const int f = g.f;
-      T up[NV], fa[NV];
+      T up[NV], fa[NV], e[kEu];
+      vload<T, kEu>((g.is0 ? E1 : E0) + static_cast<size_t>(f) * kEu, e);
 #pragma unroll
       for (int v = 0; v < NV; ++v) up[v] = uj[v] + du[v];
       D3::euler_flux(P.gamma, up, g.nn, fa);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T fb = g.is0 ? E1[v * nf + f] : -E0[v * nf + f];
+        const T fb = g.is0 ? e[v] : -e[v];
         c[v] = hS * ((fa[v] - fb) - lp * du[v]);   // (U + dU) - U = dU
       }
     }
