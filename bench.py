@@ -549,12 +549,17 @@ def work_model3(mesh, gm, spec, precision, _cache={}):
 
 
 def sphere_case(level, n_prism, n_tet, h0, ma, re, extra=None):
+    """Sphere shell of ``meshgen.sphere`` and the solver settings; ``extra``
+    adds settings, and its key ``r_far`` (far-field radius in D, default
+    20) goes to the mesh."""
     from paper_2109_09965_gb300 import meshgen
-    mesh = meshgen.sphere(level, n_prism, n_tet, h0=h0)
+    extra = dict(extra or {})
+    r_far = extra.pop("r_far", 20.0)
+    mesh = meshgen.sphere(level, n_prism, n_tet, h0=h0, R_far=r_far)
     spec = dict(gamma=GAMMA, mu=ma * 1.0 / re, cfl_hi=0.4, cfl_lo=1000.0, n_implicit=6, n_sweeps=2,
                 time_scheme="S1O2", bcs=[dict(kind="noslip"),
                                          dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0), p=1.0 / GAMMA)],
-                **(extra or {}))
+                **extra)
     W = np.zeros((mesh.n_cells, 5))
     W[:, 0] = 1.0
     W[:, 1] = ma
@@ -562,17 +567,20 @@ def sphere_case(level, n_prism, n_tet, h0, ma, re, extra=None):
     return mesh, spec, W
 
 
-# the thin-wall-layer setting of the stated sphere construction: the viscous
-# low-order flux and the compact WENO weights (eps 1e-2), the settings under
-# which its V-cycle converges furthest
-THIN_LAYER = dict(lo_viscous=1, weno_eps=1e-2)
+# the stated construction of the 512,000-cell sphere (wall cells thinner
+# than the viscous length): the viscous low-order flux, linear weights, and
+# the 20 split-tet layers ending at a far field of 5 D, where they stay
+# nearly isotropic (radial / lateral size <= 1.6); with the far field at
+# 6.5-20 D the radially stretched outer tets make the V-cycle diverge once
+# the wake reaches the outflow
+CONFIG3 = dict(lo_viscous=1, r_far=5.0)
 # the 3-D throughput workloads: (level, prism layers, split-tet layers, first
 # layer / D, Ma, Re, timed cycles, description, extra settings)
 SPHERES = {
     "sphere512k": (4, 40, 20, 1e-3, 0.2, 118, 30,
                    "3-D laminar sphere, Re 118, Ma 0.2: icosphere level 4 (5120 triangles) extruded by 40 prism "
-                   "layers (first 1e-3 D, growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 20 D: "
-                   "512,000 cells; viscous low-order flux and compact WENO (eps 1e-2)", THIN_LAYER),
+                   "layers (first 1e-3 D, growth 1.1) then 20 layers of prisms cut into 3 tets, far field at 5 D: "
+                   "512,000 cells; viscous low-order flux", CONFIG3),
     "sphere3M": (5, 60, 30, 1e-3, 0.2, 1000, 10,
                  "3-D sphere mesh of the supersonic configuration: icosphere level 5 (20480 triangles), 60 prism + "
                  "30 split-tet layers, first layer 1e-3 D: 3,072,000 cells; smooth flux at Ma 0.2, Re 1000 "
@@ -618,8 +626,6 @@ def main():
     ap.add_argument("--no-shock", action="store_true", help="skip the shock reflection convergence run")
     ap.add_argument("--shock-only", action="store_true", help="only the shock reflection convergence run")
     ap.add_argument("--supersonic-only", action="store_true", help="only the supersonic sphere runs")
-    ap.add_argument("--converge3d-full", action="store_true",
-                    help="3-D convergence on the 512,000-cell sphere instead of the 128,000-cell one")
     ap.add_argument("--only-3d", default="", choices=["", "sphere512k", "sphere3M"],
                     help="only this 3-D throughput workload (for profiling), in --precision")
     ap.add_argument("--serving", default="sample", choices=["none", "sample", "full"],
@@ -726,16 +732,14 @@ def main():
         if not args.no_shock:
             emit({"block": "shock_reflection", "shock_reflection": shock_reflection(cgks)})
         if not args.no_3d:
-            lvl = 4 if args.converge3d_full else 3
-            c3 = converge3d(cgks, lvl, 40, 20, 5e-3)
-            c3["workload"] = (f"3-D laminar sphere, Re 118, Ma 0.2, icosphere level {lvl} extruded by 40 prism "
-                              f"layers (first 5e-3 D, growth 1.1) and 20 split-tet layers to 20 D: {c3['n_cells']} "
-                              "cells; p-multigrid to a 1e-8 drop of Res relative to the first cycle (FP64), then "
-                              "the mixed path over the same cycles")
-            emit({"block": "convergence_3d", "convergence_3d": c3})
             c3s = config3_stated(cgks)
             emit({"block": "config3_stated", "config3_stated": c3s})
-            legs["config3_stated"] = {k: c3s.get(k) for k in ("cycles", "drop_min", "Cd", "diverged")}
+            f3 = c3s["fp64"]
+            legs["config3_stated"] = {"n_cells": c3s["n_cells"], "converged_1e-8": f3["converged"],
+                                      "cycles": f3.get("iterations"), "wall_s": f3.get("wall_s"),
+                                      "Cd": f3.get("Cd"), "wake_length_D": f3.get("wake_length_D"),
+                                      "diverged": f3.get("diverged"),
+                                      "mixed_res_floor": c3s.get("mixed", {}).get("res_floor")}
             emit({"block": "supersonic_sphere", "supersonic_sphere": supersonic_sphere(cgks, 4, 40, 20, 5e-3)})
     line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
@@ -966,67 +970,68 @@ def validation_re40(cgks, max_cycles=8000, drop=1e-8):
             "paper_mesh_II": {"Cd": 1.525, "Cl": 3.3e-14, "wake_length_D": 2.22, "separation_angle_deg": 53.3}}
 
 
-def config3_stated(cgks, cycles=1500):
+def config3_stated(cgks):
     """Configuration 3 at its stated construction (icosphere level 4, 40
-    prism layers from a first layer of 1e-3 D, 20 split-tet layers;
-    512,000 cells), Re 118, Ma 0.2, mixed precision, viscous low-order flux
-    and compact WENO: V-cycles from the impulsive start, the Res drop they
-    reach and the drag from the wall loads."""
-    import torch
-    from paper_2109_09965_gb300 import post
-    mesh, spec, W0 = sphere_case(4, 40, 20, 1e-3, 0.2, 118, THIN_LAYER)
-    s = cgks.Solver(cgks.Mesh(mesh), dict(spec, precision="mixed"))
-    s.set_state(W0)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    h, err = [], None
-    try:
-        while len(h) < cycles:
-            h.extend(s.pmg_cycle(100).tolist())
-    except cgks.CgksError as e:
-        err = str(e).split(":")[-1].strip()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t
-    out = {"workload": "3-D laminar sphere, Re 118, Ma 0.2, configuration 3 as stated: icosphere level 4, 40 prism "
-                       "layers from 1e-3 D (growth 1.1), 20 split-tet layers, 512,000 cells; mixed precision, "
-                       "viscous low-order flux, compact WENO eps 1e-2, impulsive start",
-           "cycles": len(h), "wall_s": el, "diverged": err}
-    if h:
-        hh = np.asarray(h)
-        out.update(res_first=float(hh[0]), drop_min=float(hh.min() / hh[0]), drop_last=float(hh[-1] / hh[0]),
-                   history=[float(x / hh[0]) for x in hh[::max(1, len(hh) // 15)]])
-    if err is None:
-        out["Cd"] = float(post.force_coefficients(s.wall_loads(0), rho=1.0, U=0.2, ref=math.pi / 4.0)[0])
-    s.close()
+    prism layers from a first layer of 1e-3 D, 20 split-tet layers; 512,000
+    cells), Re 118, Ma 0.2, far field at 5 D, viscous low-order flux:
+    FP64 V-cycles from the impulsive start to a 1e-8 drop of Res, then the
+    mixed path over the same cycles; drag and wake length beside the
+    paper's values for its own 184,320-cell sphere at Ma 0.2535."""
+    out = converge3d(cgks, 4, 40, 20, 1e-3, max_cycles=4000, extra=CONFIG3)
+    out["workload"] = ("3-D laminar sphere, Re 118, Ma 0.2, configuration 3 as stated: icosphere level 4 "
+                       "(5120 triangles), 40 prism layers from 1e-3 D (growth 1.1), 20 split-tet layers to a far "
+                       "field at 5 D; 512,000 cells; viscous low-order flux, linear weights, impulsive start; "
+                       "p-multigrid to a 1e-8 drop of Res relative to the first cycle (FP64), then the mixed "
+                       "path over the same cycles")
+    out["paper_sphere_Re118"] = {"Ma": 0.2535, "cells": 184320, "Cd": 1.002, "wake_length_D": 0.94}
     return out
 
 
-def converge3d(cgks, level, n_prism, n_tet, h0, drop=1e-8, max_cycles=6000):
+def converge3d(cgks, level, n_prism, n_tet, h0, drop=1e-8, max_cycles=6000, extra=None):
     """3-D sphere (Re 118, Ma 0.2) to a 1e-8 drop of Res: FP64 p-multigrid,
     then the mixed path over the same cycles (its Res floor and its field
-    against the FP64 field)."""
+    against the FP64 field); drag and wake length of the FP64 field."""
+    import math
     import torch
-    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, 0.2, 118)
+    from paper_2109_09965_gb300 import post
+    mesh, spec, W0 = sphere_case(level, n_prism, n_tet, h0, 0.2, 118, extra)
     gm = cgks.Mesh(mesh)
     out = {"n_cells": mesh.n_cells}
     s = cgks.Solver(gm, dict(spec, precision="fp64"))
     s.set_state(W0)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    hist, done = [], False
+    hist, done, err = [], False, None
     while len(hist) < max_cycles and not done:
-        r = s.pmg_cycle(100)
+        try:
+            r = s.pmg_cycle(100)
+        except cgks.CgksError as e:
+            err = str(e).split(":")[-1].strip()
+            break
         hist.extend(r.tolist())
-        done = min(hist) <= drop * hist[0] or not np.all(np.isfinite(r))
+        done = min(hist) <= drop * hist[0]
     el = time.perf_counter() - t
+    if not hist:
+        s.close()
+        out["fp64"] = {"converged": False, "diverged": err}
+        return out
     h = np.asarray(hist)
     hit = np.nonzero(h <= drop * h[0])[0]
     W64 = s.get_state()[0]
-    s.close()
     out["fp64"] = {"converged": bool(hit.size), "iterations": int(hit[0]) + 1 if hit.size else len(h),
                    "cycles_run": len(h), "wall_s": el, "res_first": float(h[0]),
-                   "res_min_drop": float(h.min() / h[0]),
+                   "res_min_drop": float(h.min() / h[0]), "diverged": err,
                    "history": [float(x / h[0]) for x in h[::max(1, len(h) // 30)]]}
+    if err is not None:
+        s.close()
+        return out
+    if np.all(np.isfinite(W64)):
+        cd, cl = post.force_coefficients(s.wall_loads(0), rho=1.0, U=0.2, ref=math.pi / 4.0)
+        ptr = mesh.cell_ptr
+        xc = np.add.reduceat(mesh.nodes[mesh.cell_nodes], ptr[:-1], axis=0) / np.diff(ptr)[:, None]
+        out["fp64"].update(Cd=float(cd), Cl=float(cl),
+                           wake_length_D=post.wake_length(xc, W64, R=0.5, D=1.0, angle_band=0.06))
+    s.close()
     s = cgks.Solver(gm, dict(spec, precision="mixed"))
     s.set_state(W0)
     torch.cuda.synchronize()

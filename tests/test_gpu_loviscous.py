@@ -84,6 +84,31 @@ def test_thin_wall_layer_converges_with_viscous_low_order(libs):
     assert np.all(np.isfinite(h)) and h[-20:].max() < 0.05 * h[0], h[::40] / h[0]
 
 
+def test_config3_construction_converges_with_far_field_at_5_diameters(libs):
+    """The 512,000-cell construction itself (icosphere level 4, 40 prism
+    layers from 1e-3 D, 20 split-tet layers), viscous low-order flux: with
+    the split-tet layers ending at 5 D the mixed V-cycle falls below 2e-3 of
+    its first Res in 400 cycles; ending at 20 D (outer tets stretched ~3.4x
+    radially) it diverges once the wake reaches the outflow."""
+    cgks, _, _ = libs
+    ma = 0.2
+    spec = dict(gamma=GAM, mu=ma / 118, precision="mixed", lo_viscous=1,
+                bcs=[dict(kind="noslip"), dict(kind="farfield", rho=1.0, u=(ma, 0.0, 0.0), p=1 / GAM)])
+    near = MG.sphere(4, 40, 20, h0=1e-3, R_far=5.0)
+    W = np.tile([1.0, ma, 0.0, 0.0, 1 / GAM / (GAM - 1) + 0.5 * ma * ma], (near.n_cells, 1))
+    s = cgks.Solver(cgks.Mesh(near), spec)
+    s.set_state(W)
+    h = s.pmg_cycle(400)
+    s.close()
+    assert np.all(np.isfinite(h)) and h[-20:].max() < 2e-3 * h[0], h[::40] / h[0]
+    far = MG.sphere(4, 40, 20, h0=1e-3, R_far=20.0)
+    s = cgks.Solver(cgks.Mesh(far), spec)
+    s.set_state(W)
+    with pytest.raises(cgks.CgksError):
+        s.pmg_cycle(600)
+    s.close()
+
+
 def test_server_with_viscous_low_order_equals_standalone(libs):
     cgks, _, _ = libs
     mesh, spec, (W, _) = case("cylinder_viscous")
