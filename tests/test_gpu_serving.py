@@ -164,6 +164,47 @@ def test_diverged_solve_does_not_disturb_others(cg):
         assert np.array_equal(Wb, Ws), name
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_admitted_into_a_diverged_solves_space(cg, precision):
+    """A solve that diverges leaves NaN in its part of the arena; the solves
+    admitted into that space afterwards (one of the same size, one smaller,
+    so that its padding cells cover stale NaN) must still be bitwise the
+    standalone ones."""
+    K = 6
+    def cavity(n, seed, lid):
+        mesh = MG.cavity(n, jitter=0.1, seed=seed)
+        spec = dict(gamma=GAM, mu=lid / 400.0, bcs=[dict(kind="noslip"), dict(kind="noslip", uw=(lid, 0.0))])
+        W = np.tile(exact.cons_from_prim(GAM, 1.0, 0.0, 0.0, 1 / GAM), (mesh.n_cells, 1))
+        return mesh, spec, W
+    good = cavity(24, 20, 0.1)
+    bad_mesh, bad_spec, bad_W = cavity(24, 21, 0.1)
+    bad_W[:, 3] = 0.01 * bad_W[:, 3]
+    bad_W[:, 1] = 0.5        # kinetic energy above total energy: p < 0
+    late = [cavity(24, 22, 0.12), cavity(21, 23, 0.14)]
+    probe = cg.Server(1 << 30, precision=precision, max_cycles=K)
+    fp = probe.footprint(cg.Mesh(good[0]))
+    probe.close()
+    srv = cg.Server(int(4 * fp), precision=precision, max_active=2, max_cycles=K)
+    g = srv.submit(cg.Mesh(good[0]), good[1], good[2], NEVER)
+    b = srv.submit(cg.Mesh(bad_mesh), bad_spec, bad_W, NEVER)
+    for _ in range(3):
+        srv.step()
+        st, _ = srv.poll(b)
+        if st["state"] != "queued":
+            break
+    assert st["state"] == "diverged" and st["cycles"] == 1, st
+    ids = [srv.submit(cg.Mesh(m), sp, W, NEVER) for m, sp, W in late]
+    for _ in range(4 * K):
+        if srv.step() == 0 and srv.info()["n_queued"] == 0:
+            break
+    for rid, (m, sp, W) in zip([g] + ids, [good] + late):
+        st, Wb = srv.poll(rid)
+        assert st["state"] == "stopped" and st["cycles"] == K, st
+        Ws, hist = standalone(cg, m, sp, W, K, precision)
+        assert np.array_equal(Wb, Ws), np.nanmax(np.abs(Wb - Ws))
+        assert st["res_last"] == hist[-1]
+
+
 def test_many_solves_use_cell_lists(cg):
     """More solves than the sweep's per-launch range table holds (64): the
     sweeps switch to cell lists; results stay bitwise the standalone ones."""
