@@ -401,7 +401,11 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
     reqs = serving_requests(n_req, n_lo, n_hi, seed, ma_hi)
     meshes = [cgks.Mesh(r["mesh"]) for r in reqs]
     t_prep = time.perf_counter() - t_prep
-    srv = cgks.Server(int(budget_gb * 2**30), precision=precision, max_active=max_active, max_cycles=max_cycles)
+    # the viscous low-order flux: the most viscous-dominated cavities of the
+    # mix (Re ~100 on ~200k cells) diverge in their first cycles without it;
+    # the inviscid cylinders (mu = 0) are unaffected
+    srv = cgks.Server(int(budget_gb * 2**30), precision=precision, max_active=max_active, max_cycles=max_cycles,
+                      lo_viscous=1)
     # mean inter-arrival: load x (mean cells x cycles) / a nominal 2e8 cell-updates/s
     mean_cells = float(np.mean([r["mesh"].n_cells for r in reqs]))
     mean_service = mean_cells * 0.5 * (cavity_cycles + 1500) / 2e8
@@ -457,7 +461,8 @@ def serving(cgks, n_req, n_lo, n_hi, budget_gb, drop, cavity_cycles, max_cycles,
             "cell_updates_per_s": cells_done / wall, "peak_device_bytes": int(peak_bytes),
             "peak_active": int(peak_active), "budget_bytes": int(budget_gb * 2**30), "precision": precision,
             "criterion": f"cylinders (Ma U[0.2, {ma_hi:g}], limited flux class): Res drop {drop:g} relative to "
-                         f"the first cycle (cap {max_cycles}); cavities (smooth flux): {cavity_cycles} cycles",
+                         f"the first cycle (cap {max_cycles}); cavities (smooth flux): {cavity_cycles} cycles; "
+                         "viscous low-order flux",
             "mesh_prep_s": t_prep, "tuned_shapes": tuned}
 
 
