@@ -149,6 +149,29 @@ def test_named_workload_sizes():
     assert abs(t[32] / t[31] - 1.08) < 1e-12
 
 
+def test_sphere_construction_of_configuration_3():
+    """Icosphere level 4 (5120 triangles), 40 prism layers from 1e-3 D
+    growing by 1.1, 20 split-tet layers: 512,000 cells.  With the far field
+    at 5 D the outermost split prisms are about 1.5 times longer radially
+    than wide (width: the mean surface triangle's edge scaled to the
+    layer's mid radius); at 20 D about 3 times (the stretched outer cells
+    with which the V-cycle diverges once the wake reaches them)."""
+    r5 = MG.sphere_radii(40, 20, 1e-3, 1.1, 0.5, 5.0)
+    r20 = MG.sphere_radii(40, 20, 1e-3, 1.1, 0.5, 20.0)
+    for r, far in ((r5, 5.0), (r20, 20.0)):
+        assert len(r) == 61 and abs(r[-1] - far) < 1e-12 and abs(r[0] - 0.5) < 1e-15
+        t = np.diff(r)
+        np.testing.assert_allclose(t[:40], 1e-3 * 1.1 ** np.arange(40), rtol=1e-12)
+        assert np.all(t > 0)
+    # lateral size of a level-4 surface triangle scaled to radius r: the
+    # edge of the icosphere's mean triangle, sqrt(4 A / sqrt(3)), A = 4 pi R^2 / 5120
+    lateral = lambda rad: math.sqrt(4.0 * (4.0 * math.pi * rad * rad / 5120) / math.sqrt(3.0))
+    ratio = lambda r: np.diff(r)[-1] / lateral(0.5 * (r[-1] + r[-2]))
+    assert ratio(r5) < 1.6 and ratio(r20) > 2.8
+    mesh = MG.sphere(4, 40, 20, h0=1e-3, R_far=5.0)
+    assert mesh.n_cells == 512000
+
+
 def test_shock_reflection_case_layout():
     """Section 4's shock reflection grid: 120 x 30 quads on [0,4] x [0,1],
     tags wall (bottom), outflow (right), Dirichlet top and left; the
